@@ -1,0 +1,727 @@
+/*
+ * Oracle for implicit-depletant hard-particle Monte Carlo
+ * (Glaser, Karas & Glotzer, "A parallel algorithm for implicit depletant
+ * simulations", arXiv:1508.07077).
+ *
+ * TEST INFRASTRUCTURE.  This file is the plain, serial, FP64 statement of what
+ * the GPU library computes.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference leg of bench.py may load it.  It shares no code,
+ * header, table or constant generator with the CUDA library: the two sides
+ * implement the same written specification independently.
+ *
+ * What it computes, step by step, in the paper's order:
+ *   - Sec. III.E: checkerboard sweep.  Cells of width >= d_colloid + d_depletant,
+ *     2x2x2 colouring, random colour order and random grid shift per sweep,
+ *     particles may not leave their cell.
+ *   - Sec. III.B, Eqs. (3)-(4): propose a colloid move; reject on colloid overlap
+ *     (U_ij = infinity); draw N_p ~ Poisson(z_p V_0) depletants uniformly in V_0.
+ *   - Sec. III.C (choice of V_0): V_0 is the circumsphere of diameter
+ *     d_colloid + d_depletant around the moved colloid in its NEW pose.
+ *     Depletants overlapping the old configuration (old pose of the moved
+ *     colloid or any other colloid) are ignored; a depletant overlapping only
+ *     the new pose blocks the move.
+ *   - Sec. III.D, Eq. (12): with n_trial > 0 each blocking depletant is
+ *     reinserted (configurational bias) and the move is accepted with the
+ *     product of per-depletant weights.
+ *
+ * Readings where the paper is silent (RNG, op order, sampling details) are the
+ * ones listed in the design notes; every floating-point expression below is
+ * written in the exact operation order that specification fixes, and must be
+ * compiled with -ffp-contract=off (no fused multiply-add).
+ *
+ * Parity pins (tests/test_oracle_*.py): Poisson moments and pmf (chi^2),
+ * Philox uniformity, brute-force neighbour enumeration, the two-colloid
+ * Asakura-Oosawa distribution (detailed balance, Eqs. 5-11 and 12), the
+ * hard-sphere Carnahan-Starling contact value at z_p = 0, and the exact
+ * free-volume fraction of a single colloid.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Counter-based RNG: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11).    */
+/* The paper does not name its RNG; this is the chosen reading.              */
+/* ------------------------------------------------------------------------ */
+
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                          uint32_t out[4])
+{
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c[0];
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c[3] ^ k1;
+        uint32_t n3 = lo0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+        k0 += PHILOX_W0;
+        k1 += PHILOX_W1;
+    }
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+/* Purposes, placed in the top byte of counter word 2. */
+enum { P_SCHED = 0, P_MOVE = 1, P_ROT = 2, P_POISSON = 3, P_DEP = 4,
+       P_CB_FWD = 5, P_CB_REV = 6, P_ACCEPT = 7, P_PROBE = 8 };
+
+typedef struct { uint32_t k[2]; } okey;
+
+static void draw(okey key, uint32_t sweep, uint32_t stream, uint32_t purpose,
+                 uint32_t sub, uint32_t t, uint32_t w[4])
+{
+    uint32_t ctr[4] = {sweep, stream, (purpose << 24) | (sub & 0xFFFFFFu), t};
+    oracle_philox4x32_10(ctr, key.k, w);
+}
+
+/* uniform in (0,1): (w + 1/2) 2^-32 */
+static double u01(uint32_t w) { return ((double)w + 0.5) * (1.0 / 4294967296.0); }
+/* uniform in (-1,1): 2 u01(w) - 1, exact in double */
+static double s11(uint32_t w) { return ((double)w + 0.5) * (1.0 / 2147483648.0) - 1.0; }
+/* uniform in [0,1) with 53 bits */
+static double u53(uint32_t w0, uint32_t w1)
+{
+    return ((double)(w0 >> 5) * 67108864.0 + (double)(w1 >> 6)) *
+           (1.0 / 9007199254740992.0);
+}
+
+double oracle_u01(uint32_t w) { return u01(w); }
+double oracle_s11(uint32_t w) { return s11(w); }
+double oracle_u53(uint32_t w0, uint32_t w1) { return u53(w0, w1); }
+
+/* ------------------------------------------------------------------------ */
+/* Poisson(lambda) by inversion, Sec. III.B step 2 ("N_p ~ Poisson(z_p V)")  */
+/* ------------------------------------------------------------------------ */
+
+#define ORACLE_PI 3.141592653589793
+
+/* lambda = z_p |V_0|, V_0 the sphere of radius R_s (Sec. III.C). */
+double oracle_lambda(double R_s, double n_r)
+{
+    double v0 = ((4.0 / 3.0) * ORACLE_PI) * ((R_s * R_s) * R_s);
+    return n_r * v0;
+}
+
+/* Cumulative table F[k] = sum_{m<=k} e^-lambda lambda^m / m!, built by the
+ * recurrence p_0 = exp(-lambda), p_k = p_{k-1} * lambda / k.  Stops after the
+ * first k > lambda with p_k < 2^-64.  Returns the length or -1 if cap is hit. */
+int oracle_poisson_table(double lambda, double *F, int cap)
+{
+    if (!(lambda >= 0.0) || lambda > 700.0) return -1;
+    double p = exp(-lambda);
+    double cdf = p;
+    int n = 0;
+    if (cap < 1) return -1;
+    F[n++] = cdf;
+    for (int k = 1;; ++k) {
+        p = (p * lambda) / (double)k;
+        cdf = cdf + p;
+        if (n >= cap) return -1;
+        F[n++] = cdf;
+        if ((double)k > lambda && p < 5.421010862427522e-20 /* 2^-64 */) break;
+    }
+    return n;
+}
+
+/* N_p = number of table entries F[k] <= u (inversion: min{k : u < F[k]}). */
+static int poisson_invert(const double *F, int n, double u)
+{
+    int k = 0;
+    while (k < n && F[k] <= u) ++k;
+    return k;
+}
+
+int oracle_poisson_sample(const double *F, int n, double u)
+{
+    return poisson_invert(F, n, u);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Shapes.  Only spheres here: colloid of diameter d, depletant diameter q.  */
+/* ------------------------------------------------------------------------ */
+
+enum { SHAPE_SPHERE = 0, SHAPE_HEMISPHERE = 1, SHAPE_SPHEROID = 2 };
+
+typedef struct {
+    int kind;
+    double d;       /* sphere diameter */
+    double R_circ;  /* circumsphere radius about the reference point */
+} oshape;
+
+/* Does a depletant (penetrable sphere of diameter q) at v, given relative to
+ * the colloid's reference point, overlap the colloid?  Strict inequality:
+ * touching is not an overlap. */
+static int dep_overlap(const oshape *sh, double q, const double v[3],
+                       const double quat[4])
+{
+    (void)quat;
+    double R = 0.5 * sh->d + 0.5 * q;
+    double r2 = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2];
+    return r2 < R * R;
+}
+
+/* Do two colloids whose reference points are separated by r (from the first
+ * to the second) overlap?  U_ij = infinity for overlapping hard colloids. */
+static int pair_overlap(const oshape *sh, const double r[3], const double qa[4],
+                        const double qb[4])
+{
+    (void)qa; (void)qb;
+    double r2 = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
+    return r2 < sh->d * sh->d;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Checkerboard geometry, Sec. III.E                                         */
+/* ------------------------------------------------------------------------ */
+
+static int cell_coord(double x, double sigma, double L, double w, int nc)
+{
+    double s = x - sigma;
+    if (s < 0.0) s = s + L;
+    int c = (int)(s / w);
+    if (c >= nc) c = nc - 1;
+    return c;
+}
+
+static double min_image(double d, double L)
+{
+    double h = 0.5 * L;
+    if (d > h) d = d - L;
+    else if (d < -h) d = d + L;
+    return d;
+}
+
+/* Grid shift sigma in [0,w)^3 and colour order perm[8] for one sweep. */
+void oracle_schedule(uint64_t seed, uint32_t replica, uint32_t sweep, double w,
+                     double sigma[3], int perm[8])
+{
+    okey key = {{(uint32_t)seed, (uint32_t)(seed >> 32) ^ replica}};
+    uint32_t a[4], b[4], c[4];
+    draw(key, sweep, 0xFFFFFFFFu, P_SCHED, 0, 0, a);
+    sigma[0] = w * u01(a[0]);
+    sigma[1] = w * u01(a[1]);
+    sigma[2] = w * u01(a[2]);
+    draw(key, sweep, 0xFFFFFFFFu, P_SCHED, 1, 0, b);
+    draw(key, sweep, 0xFFFFFFFFu, P_SCHED, 2, 0, c);
+    uint32_t words[8] = {b[0], b[1], b[2], b[3], c[0], c[1], c[2], c[3]};
+    for (int i = 0; i < 8; ++i) perm[i] = i;
+    for (int i = 7; i >= 1; --i) {
+        int j = (int)(((uint64_t)words[7 - i] * (uint64_t)(i + 1)) >> 32);
+        int t = perm[i]; perm[i] = perm[j]; perm[j] = t;
+    }
+}
+
+/* Cell list for one sweep: cell_start[nc^3 + 1], cell_idx[n], particles of a
+ * cell in ascending tag order. */
+int oracle_cell_list(int n, double L, int nc, const double *pos, uint64_t seed,
+                     uint32_t replica, uint32_t sweep, int *cell_start,
+                     int *cell_idx)
+{
+    if (n < 0 || nc < 2 || (nc & 1)) return -1;
+    double w = L / (double)nc;
+    double sigma[3];
+    int perm[8];
+    oracle_schedule(seed, replica, sweep, w, sigma, perm);
+    int ncell = nc * nc * nc;
+    int *cnt = (int *)calloc((size_t)ncell, sizeof(int));
+    int *cell_of = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    if (!cnt || !cell_of) { free(cnt); free(cell_of); return -1; }
+    for (int i = 0; i < n; ++i) {
+        int cx = cell_coord(pos[3 * i + 0], sigma[0], L, w, nc);
+        int cy = cell_coord(pos[3 * i + 1], sigma[1], L, w, nc);
+        int cz = cell_coord(pos[3 * i + 2], sigma[2], L, w, nc);
+        cell_of[i] = cx + nc * (cy + nc * cz);
+        cnt[cell_of[i]]++;
+    }
+    cell_start[0] = 0;
+    for (int c = 0; c < ncell; ++c) cell_start[c + 1] = cell_start[c] + cnt[c];
+    memset(cnt, 0, sizeof(int) * (size_t)ncell);
+    for (int i = 0; i < n; ++i) {
+        int c = cell_of[i];
+        cell_idx[cell_start[c] + cnt[c]++] = i;
+    }
+    free(cnt);
+    free(cell_of);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The sampler                                                               */
+/* ------------------------------------------------------------------------ */
+
+enum {
+    C_MOVES = 0, C_ACCEPT, C_REJ_CELL, C_REJ_OVERLAP, C_REJ_DEP, C_REJ_CB,
+    C_DEP_DRAWN, C_DEP_BLOCKING, C_CB_FWD_OK, C_CB_REV_OK, C_CAP, C_TRANSLATE,
+    C_N = 16
+};
+
+typedef struct {
+    int n;
+    double L;
+    oshape sh;
+    double q, n_r, R_s, R_s2, lambda;
+    int n_trial, cb_mode;
+    double d_max, a_max, p_translate, alpha;
+    okey key;
+    int nc;
+    double w;
+    int brute_force;
+    double *F;
+    int nF;
+} osim;
+
+typedef struct {
+    int j;
+    double d[3];     /* r_j - r_i' (minimum image) */
+    const double *qj;
+} onb;
+
+/* All colloids j != i that can interact with colloid i at reference point xn:
+ * every particle of the (deduplicated) 27 neighbouring cells, or every other
+ * particle in brute-force mode.  Extra far-away entries are harmless: every
+ * test against them is false. */
+static int gather_neighbours(const osim *S, int i, const double xn[3],
+                             const int ci[3], const double *pos,
+                             const double *quat, const int *cell_start,
+                             const int *cell_idx, onb *out)
+{
+    int m = 0;
+    if (S->brute_force) {
+        for (int j = 0; j < S->n; ++j) {
+            if (j == i) continue;
+            out[m].j = j;
+            for (int d = 0; d < 3; ++d)
+                out[m].d[d] = min_image(pos[3 * j + d] - xn[d], S->L);
+            out[m].qj = quat ? quat + 4 * j : NULL;
+            ++m;
+        }
+        return m;
+    }
+    int nc = S->nc;
+    int off_n = nc == 2 ? 2 : 3;
+    for (int oz = 0; oz < off_n; ++oz)
+        for (int oy = 0; oy < off_n; ++oy)
+            for (int ox = 0; ox < off_n; ++ox) {
+                int cx, cy, cz;
+                if (nc == 2) { cx = ox; cy = oy; cz = oz; }
+                else {
+                    cx = (ci[0] + ox - 1 + nc) % nc;
+                    cy = (ci[1] + oy - 1 + nc) % nc;
+                    cz = (ci[2] + oz - 1 + nc) % nc;
+                }
+                int c = cx + nc * (cy + nc * cz);
+                for (int s = cell_start[c]; s < cell_start[c + 1]; ++s) {
+                    int j = cell_idx[s];
+                    if (j == i) continue;
+                    out[m].j = j;
+                    for (int d = 0; d < 3; ++d)
+                        out[m].d[d] = min_image(pos[3 * j + d] - xn[d], S->L);
+                    out[m].qj = quat ? quat + 4 * j : NULL;
+                    ++m;
+                }
+            }
+    return m;
+}
+
+/* Next point of an attempt stream, uniform in the ball |e| < R_s (rejection
+ * from the cube [-R_s, R_s]^3).  *t is the running attempt index; returns 0
+ * once *t reaches t_max. */
+static int next_in_ball(const osim *S, uint32_t sweep, uint32_t tag,
+                        uint32_t purpose, uint32_t sub, uint32_t *t,
+                        uint32_t t_max, double e[3])
+{
+    while (*t < t_max) {
+        uint32_t w[4];
+        draw(S->key, sweep, tag, purpose, sub, *t, w);
+        *t += 1;
+        e[0] = S->R_s * s11(w[0]);
+        e[1] = S->R_s * s11(w[1]);
+        e[2] = S->R_s * s11(w[2]);
+        double r2 = (e[0] * e[0] + e[1] * e[1]) + e[2] * e[2];
+        if (r2 < S->R_s2) return 1;
+    }
+    return 0;
+}
+
+/* Is v (relative to the new reference point) free of every other colloid? */
+static int free_of_neighbours(const osim *S, const double v[3], const onb *nb,
+                              int m)
+{
+    for (int a = 0; a < m; ++a) {
+        double u[3] = {v[0] - nb[a].d[0], v[1] - nb[a].d[1], v[2] - nb[a].d[2]};
+        if (dep_overlap(&S->sh, S->q, u, nb[a].qj)) return 0;
+    }
+    return 1;
+}
+
+/* Configurational-bias weight of blocking depletant k, Sec. III.D, Eq. (12).
+ * Forward: n_trial reinsertion trials uniform in the old circumsphere; a
+ * success overlaps the old pose, not the new pose and no other colloid
+ * (N'_insert).  Reverse: the original depletant plus n_trial - 1 trials
+ * uniform in the new circumsphere; a success overlaps the new pose, not the
+ * old pose and no other colloid (N_insert + 1).  cb_mode 1 is the literal
+ * printed form with the lens counts N_k. */
+static double cb_factor(const osim *S, uint32_t sweep, uint32_t tag, uint32_t k,
+                        const double o[3], const double *q_old,
+                        const double *q_new, const onb *nb, int m,
+                        uint64_t *cnt)
+{
+    int n_fwd_trials = S->n_trial;
+    int n_rev_trials = S->cb_mode == 0 ? S->n_trial - 1 : S->n_trial;
+    uint32_t t = 0, t_max = 64u * (uint32_t)(n_fwd_trials + 1);
+    int n_ins_fwd = 0, n_lens_fwd = 0, found = 0;
+    double e[3];
+    while (found < n_fwd_trials &&
+           next_in_ball(S, sweep, tag, P_CB_FWD, k, &t, t_max, e)) {
+        ++found;
+        double y[3] = {o[0] + e[0], o[1] + e[1], o[2] + e[2]};
+        if (!dep_overlap(&S->sh, S->q, e, q_old)) continue;
+        if (dep_overlap(&S->sh, S->q, y, q_new)) continue;
+        ++n_lens_fwd;
+        if (!free_of_neighbours(S, y, nb, m)) continue;
+        ++n_ins_fwd;
+    }
+    if (found < n_fwd_trials) cnt[C_CAP]++;
+    t = 0;
+    t_max = 64u * (uint32_t)(n_rev_trials + 1);
+    found = 0;
+    int n_ins_rev = 0;
+    while (found < n_rev_trials &&
+           next_in_ball(S, sweep, tag, P_CB_REV, k, &t, t_max, e)) {
+        ++found;
+        double u[3] = {e[0] - o[0], e[1] - o[1], e[2] - o[2]};
+        if (!dep_overlap(&S->sh, S->q, e, q_new)) continue;
+        if (dep_overlap(&S->sh, S->q, u, q_old)) continue;
+        if (!free_of_neighbours(S, e, nb, m)) continue;
+        ++n_ins_rev;
+    }
+    if (found < n_rev_trials) cnt[C_CAP]++;
+    cnt[C_CB_FWD_OK] += (uint64_t)n_ins_fwd;
+    cnt[C_CB_REV_OK] += (uint64_t)n_ins_rev;
+    if (S->cb_mode == 0)
+        return (double)n_ins_fwd / (double)(n_ins_rev + 1);
+    if (n_lens_fwd == 0) return 0.0;
+    return ((double)n_ins_fwd * (double)(n_lens_fwd + 1)) /
+           ((double)(n_ins_rev + 1) * (double)n_lens_fwd);
+}
+
+/* Acceptance of one proposed move of colloid i to the pose (xn, qn); o is the
+ * old reference point relative to the new one (zero for a rotation).
+ * Sec. III.B-III.D.  Returns 1 to accept, 0 to reject. */
+static int accept_move(const osim *S, uint32_t sweep, int i, const double xn[3],
+                       const double qn[4], const double o[3], const double *qo,
+                       const int ci[3], const double *pos, const double *quat,
+                       const int *cell_start, const int *cell_idx, onb *nb,
+                       uint64_t *cnt)
+{
+    uint32_t tag = (uint32_t)i;
+
+    /* Colloid-colloid overlap at the new pose: Delta H_cc = infinity. */
+    int m = gather_neighbours(S, i, xn, ci, pos, quat, cell_start, cell_idx, nb);
+    for (int a = 0; a < m; ++a) {
+        if (pair_overlap(&S->sh, nb[a].d, qn, nb[a].qj)) {
+            cnt[C_REJ_OVERLAP]++;
+            return 0;
+        }
+    }
+    if (!(S->lambda > 0.0)) return 1;
+
+    /* N_p ~ Poisson(z_p |V_0|) depletants uniform in V_0 (Sec. III.B step 2). */
+    uint32_t wp[4];
+    draw(S->key, sweep, tag, P_POISSON, 0, 0, wp);
+    int n_p = poisson_invert(S->F, S->nF, u53(wp[0], wp[1]));
+    cnt[C_DEP_DRAWN] += (uint64_t)n_p;
+    uint32_t t = 0, t_max = 64u * (uint32_t)(n_p + 1);
+    int n_block = 0;
+    double W = 1.0;
+    for (int k = 0; k < n_p; ++k) {
+        double e[3];
+        if (!next_in_ball(S, sweep, tag, P_DEP, 0, &t, t_max, e)) {
+            cnt[C_CAP]++;
+            break;
+        }
+        /* irrelevant unless it overlaps the new pose */
+        if (!dep_overlap(&S->sh, S->q, e, qn)) continue;
+        /* ignored if it overlaps the old configuration */
+        double u[3] = {e[0] - o[0], e[1] - o[1], e[2] - o[2]};
+        if (dep_overlap(&S->sh, S->q, u, qo)) continue;
+        if (!free_of_neighbours(S, e, nb, m)) continue;
+        /* overlaps only the new configuration: blocks the move */
+        cnt[C_DEP_BLOCKING]++;
+        ++n_block;
+        if (S->n_trial == 0) {
+            cnt[C_REJ_DEP]++;
+            return 0;
+        }
+        double f = cb_factor(S, sweep, tag, (uint32_t)k, o, qo, qn, nb, m, cnt);
+        if (f == 0.0) {
+            cnt[C_REJ_CB]++;
+            return 0;
+        }
+        W = W * f;
+    }
+    if (n_block > 0) {
+        uint32_t wa[4];
+        draw(S->key, sweep, tag, P_ACCEPT, 0, 0, wa);
+        if (!(u53(wa[0], wa[1]) < W)) {
+            cnt[C_REJ_CB]++;
+            return 0;
+        }
+    }
+    return 1;
+}
+
+/* One trial move of colloid i in the active cell ci: proposal, cell check,
+ * acceptance, commit. */
+static void trial_move(const osim *S, uint32_t sweep, int i, const int ci[3],
+                       const double sigma[3], double *pos, double *quat,
+                       const int *cell_start, const int *cell_idx, onb *nb,
+                       uint64_t *cnt)
+{
+    uint32_t tag = (uint32_t)i;
+    uint32_t w[4];
+    cnt[C_MOVES]++;
+    draw(S->key, sweep, tag, P_MOVE, 0, 0, w);
+
+    int translate = 1;
+    if (S->sh.kind != SHAPE_SPHERE && S->a_max > 0.0) {
+        if (S->p_translate <= 0.0) translate = 0;
+        else if (S->p_translate < 1.0) translate = u01(w[3]) < S->p_translate;
+    }
+
+    double xn[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    double qn[4] = {1.0, 0.0, 0.0, 0.0};
+    const double *qo = quat ? quat + 4 * i : NULL;
+    if (qo) { qn[0] = qo[0]; qn[1] = qo[1]; qn[2] = qo[2]; qn[3] = qo[3]; }
+    double o[3] = {0.0, 0.0, 0.0};
+
+    if (translate) {
+        cnt[C_TRANSLATE]++;
+        for (int d = 0; d < 3; ++d) {
+            double x = pos[3 * i + d] + S->d_max * s11(w[d]);
+            if (x < 0.0) x = x + S->L;
+            if (x >= S->L) x = x - S->L;
+            xn[d] = x;
+        }
+        /* Sec. III.E: particles are not allowed to move outside their cells. */
+        for (int d = 0; d < 3; ++d) {
+            if (cell_coord(xn[d], sigma[d], S->L, S->w, S->nc) != ci[d]) {
+                cnt[C_REJ_CELL]++;
+                return;
+            }
+        }
+        for (int d = 0; d < 3; ++d) o[d] = min_image(pos[3 * i + d] - xn[d], S->L);
+    }
+
+    if (!accept_move(S, sweep, i, xn, qn, o, qo, ci, pos, quat, cell_start,
+                     cell_idx, nb, cnt))
+        return;
+
+    pos[3 * i] = xn[0];
+    pos[3 * i + 1] = xn[1];
+    pos[3 * i + 2] = xn[2];
+    if (quat) {
+        quat[4 * i] = qn[0]; quat[4 * i + 1] = qn[1];
+        quat[4 * i + 2] = qn[2]; quat[4 * i + 3] = qn[3];
+    }
+    cnt[C_ACCEPT]++;
+}
+
+/* Largest even cell count with cell width >= 2 R_circ + q (Sec. III.E). */
+int oracle_auto_cells(double L, double R_circ, double q)
+{
+    double w_min = 2.0 * R_circ + q;
+    int nc = (int)(L / w_min);
+    if (nc & 1) nc -= 1;
+    return nc;
+}
+
+static void sim_free(osim *S) { free(S->F); S->F = NULL; }
+
+static int sim_init(osim *S, int n, double L, int shape,
+                    const double *shape_params, int n_shape_params, double q,
+                    double n_r, int n_trial, int cb_mode, double d_max,
+                    double a_max, double p_translate, uint64_t seed,
+                    uint32_t replica, int n_cell, int brute_force)
+{
+    memset(S, 0, sizeof *S);
+    if (n < 1 || !(L > 0.0) || !shape_params) return -1;
+    if (shape != SHAPE_SPHERE || n_shape_params < 1) return -1;
+    S->n = n;
+    S->L = L;
+    S->sh.kind = shape;
+    S->sh.d = shape_params[0];
+    S->sh.R_circ = 0.5 * S->sh.d;
+    S->q = q;
+    S->n_r = n_r;
+    S->R_s = S->sh.R_circ + 0.5 * q;
+    S->R_s2 = S->R_s * S->R_s;
+    S->lambda = n_r > 0.0 ? oracle_lambda(S->R_s, n_r) : 0.0;
+    S->n_trial = n_trial;
+    S->cb_mode = cb_mode;
+    S->d_max = d_max;
+    S->a_max = a_max;
+    S->p_translate = p_translate;
+    S->key.k[0] = (uint32_t)seed;
+    S->key.k[1] = (uint32_t)(seed >> 32) ^ replica;
+    S->nc = n_cell > 0 ? n_cell : oracle_auto_cells(L, S->sh.R_circ, q);
+    S->brute_force = brute_force;
+    if (S->nc < 2 || (S->nc & 1) || n_trial < 0 || q < 0.0 || n_r < 0.0) return -1;
+    S->w = L / (double)S->nc;
+    if (S->w < 2.0 * S->sh.R_circ + q) return -1;
+    if (!(d_max >= 0.0) || d_max >= S->w) return -1;
+    if (S->lambda > 0.0) {
+        int cap = 8192;
+        S->F = (double *)malloc(sizeof(double) * (size_t)cap);
+        if (!S->F) return -1;
+        S->nF = oracle_poisson_table(S->lambda, S->F, cap);
+        if (S->nF < 0) { sim_free(S); return -1; }
+    }
+    return 0;
+}
+
+/*
+ * Run n_sweeps sweeps starting at sweep index sweep0, in place on pos (n x 3)
+ * and quat (n x 4 or NULL).  counters: C_N uint64 accumulated.  If hist is
+ * non-NULL, after every sweep all pair distances r < hist_rmax are binned into
+ * hist[hist_bins] (minimum image).  Returns 0 or a negative error.
+ */
+int oracle_run(int n, double L, int shape, const double *shape_params,
+               int n_shape_params, double q, double n_r, int n_trial,
+               int cb_mode, double d_max, double a_max, double p_translate,
+               uint64_t seed, uint32_t replica, int n_cell, int brute_force,
+               double *pos, double *quat, uint64_t sweep0, int n_sweeps,
+               uint64_t *counters, int hist_bins, double hist_rmax,
+               uint64_t *hist)
+{
+    osim S;
+    if (!pos || !counters || n_sweeps < 0) return -1;
+    if (sim_init(&S, n, L, shape, shape_params, n_shape_params, q, n_r, n_trial,
+                 cb_mode, d_max, a_max, p_translate, seed, replica, n_cell,
+                 brute_force) != 0)
+        return -1;
+    int ncell = S.nc * S.nc * S.nc;
+    int *cell_start = (int *)malloc(sizeof(int) * (size_t)(ncell + 1));
+    int *cell_idx = (int *)malloc(sizeof(int) * (size_t)n);
+    onb *nb = (onb *)malloc(sizeof(onb) * (size_t)n);
+    int rc = 0;
+    if (!cell_start || !cell_idx || !nb) { rc = -1; goto out; }
+
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+        uint32_t sweep = (uint32_t)(sweep0 + (uint64_t)sw);
+        double sigma[3];
+        int perm[8];
+        oracle_schedule(seed, replica, sweep, S.w, sigma, perm);
+        if (oracle_cell_list(n, L, S.nc, pos, seed, replica, sweep, cell_start,
+                             cell_idx) != 0) { rc = -1; goto out; }
+        for (int p = 0; p < 8; ++p) {
+            int colour = perm[p];
+            for (int c = 0; c < ncell; ++c) {
+                int cx = c % S.nc, cy = (c / S.nc) % S.nc, cz = c / (S.nc * S.nc);
+                int col = (cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2);
+                if (col != colour) continue;
+                int ci[3] = {cx, cy, cz};
+                for (int s = cell_start[c]; s < cell_start[c + 1]; ++s)
+                    trial_move(&S, sweep, cell_idx[s], ci, sigma, pos, quat,
+                               cell_start, cell_idx, nb, counters);
+            }
+        }
+        if (hist && hist_bins > 0) {
+            double binw = hist_rmax / (double)hist_bins;
+            for (int a = 0; a < n; ++a)
+                for (int b = a + 1; b < n; ++b) {
+                    double r2 = 0.0;
+                    for (int d = 0; d < 3; ++d) {
+                        double dd = min_image(pos[3 * b + d] - pos[3 * a + d], L);
+                        r2 += dd * dd;
+                    }
+                    double r = sqrt(r2);
+                    if (r < hist_rmax) {
+                        int bin = (int)(r / binw);
+                        if (bin < hist_bins) hist[bin]++;
+                    }
+                }
+        }
+    }
+out:
+    sim_free(&S);
+    free(cell_start);
+    free(cell_idx);
+    free(nb);
+    return rc;
+}
+
+/*
+ * Acceptance count of one fixed proposed move: colloid i from its pose in
+ * (pos, quat) to (xn, qn), evaluated n_rep times with the independent random
+ * streams of sweep indices sweep0 .. sweep0 + n_rep - 1.  Neighbours by brute
+ * force.  Used to check detailed balance of the acceptance rule directly.
+ */
+long oracle_acceptance(int n, double L, int shape, const double *shape_params,
+                       int n_shape_params, double q, double n_r, int n_trial,
+                       int cb_mode, uint64_t seed, const double *pos,
+                       const double *quat, int i, const double *xn_in,
+                       const double *qn_in, uint64_t sweep0, long n_rep,
+                       uint64_t *counters)
+{
+    osim S;
+    if (!pos || !xn_in || i < 0 || i >= n || n_rep < 0 || !counters) return -1;
+    if (sim_init(&S, n, L, shape, shape_params, n_shape_params, q, n_r, n_trial,
+                 cb_mode, 0.0, 0.0, 1.0, seed, 0, 0, 1) != 0)
+        return -1;
+    onb *nb = (onb *)malloc(sizeof(onb) * (size_t)n);
+    if (!nb) { sim_free(&S); return -1; }
+    double xn[3] = {xn_in[0], xn_in[1], xn_in[2]};
+    double qn[4] = {1.0, 0.0, 0.0, 0.0};
+    const double *qo = quat ? quat + 4 * i : NULL;
+    if (qn_in) { qn[0] = qn_in[0]; qn[1] = qn_in[1]; qn[2] = qn_in[2]; qn[3] = qn_in[3]; }
+    else if (qo) { qn[0] = qo[0]; qn[1] = qo[1]; qn[2] = qo[2]; qn[3] = qo[3]; }
+    double o[3];
+    for (int d = 0; d < 3; ++d) o[d] = min_image(pos[3 * i + d] - xn[d], L);
+    int ci[3] = {0, 0, 0};
+    long acc = 0;
+    for (long r = 0; r < n_rep; ++r)
+        acc += accept_move(&S, (uint32_t)(sweep0 + (uint64_t)r), i, xn, qn, o, qo,
+                           ci, pos, quat, NULL, NULL, nb, counters);
+    free(nb);
+    sim_free(&S);
+    return acc;
+}
+
+/*
+ * Depletant free-volume probe (Sec. IV.A observable): count how many of
+ * n_probe uniform points in the box overlap no colloid.  Brute force over
+ * all colloids.  Probe points use purpose P_PROBE with stream = probe index.
+ */
+long oracle_free_volume(int n, double L, int shape, const double *shape_params,
+                        double q, const double *pos, const double *quat,
+                        uint64_t seed, uint32_t sample, long n_probe)
+{
+    if (shape != SHAPE_SPHERE) return -1;
+    oshape sh = {SHAPE_SPHERE, shape_params[0], 0.5 * shape_params[0]};
+    okey key = {{(uint32_t)seed, (uint32_t)(seed >> 32)}};
+    long free_count = 0;
+    for (long m = 0; m < n_probe; ++m) {
+        uint32_t w[4];
+        draw(key, sample, (uint32_t)m, P_PROBE, (uint32_t)(m >> 32), 0, w);
+        double p[3] = {L * u01(w[0]), L * u01(w[1]), L * u01(w[2])};
+        int hit = 0;
+        for (int j = 0; j < n && !hit; ++j) {
+            double v[3];
+            for (int d = 0; d < 3; ++d) v[d] = min_image(p[d] - pos[3 * j + d], L);
+            hit = dep_overlap(&sh, q, v, quat ? quat + 4 * j : NULL);
+        }
+        if (!hit) ++free_count;
+    }
+    return free_count;
+}

@@ -1,0 +1,125 @@
+"""Statistical pins of the oracle against what the paper and textbook
+statistical mechanics fix.
+
+* Detailed balance (Sec. III.B-C, Eqs. 5-11): for a fixed pair of colloid
+  configurations, P_acc(M->M') / P_acc(M'->M) = exp(z_p [V_f(M') - V_f(M)]).
+  With two spheres V_f changes only by the Asakura-Oosawa lens volume.
+  Checked for n_trial = 0 and for the configurational-bias weight (Eq. 12).
+* The Asakura-Oosawa two-colloid distribution P(r) ~ r^2 exp(z_p V_lens(r))
+  that the semigrand weight exp(z_p V_f - beta H_cc) (Eq. 2) implies.
+* The hard-sphere limit z_p = 0: contact value vs Carnahan-Starling, and the
+  scaled-particle-theory free-volume fraction (Sec. IV.A observable).
+* The exact free-volume fraction of a single colloid.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1508_07077_gb300 import workloads as W
+
+Q, R_S, Z_P, L2 = 0.2, 0.6, 47.7464829275686, 2.4
+
+
+def lens(r, R=R_S):
+    """Overlap volume of two spheres of radius R at centre distance r."""
+    r = np.asarray(r, dtype=float)
+    return np.where(r < 2 * R, math.pi / 12.0 * (4 * R + r) * (2 * R - r) ** 2, 0.0)
+
+
+def _pair(r):
+    a = np.array([0.2, 0.2, 0.2])
+    d = np.array([1.0, 1.0, 1.0]) / math.sqrt(3.0)
+    return a, a + r * d
+
+
+def _ratio(oracle, r0, r1, n_trial, cb_mode, n_rep):
+    a, b0 = _pair(r0)
+    _, b1 = _pair(r1)
+    f, _ = oracle.acceptance(np.array([a, b0]), L2, 1, b1, q=Q, n_r=Z_P,
+                             n_trial=n_trial, cb_mode=cb_mode, n_rep=n_rep)
+    b, _ = oracle.acceptance(np.array([a, b1]), L2, 1, b0, q=Q, n_r=Z_P,
+                             n_trial=n_trial, cb_mode=cb_mode, n_rep=n_rep,
+                             sweep0=10 ** 7)
+    ratio = f / b
+    se = ratio * math.sqrt(1.0 / f + 1.0 / b)
+    expect = math.exp(Z_P * float(lens(r1) - lens(r0)))
+    return ratio, se, expect
+
+
+@pytest.mark.parametrize("n_trial", [0, 1, 3, 10])
+@pytest.mark.parametrize("r0,r1", [(1.05, 1.10), (1.02, 1.09)])
+def test_detailed_balance_of_acceptance(oracle, n_trial, r0, r1):
+    ratio, se, expect = _ratio(oracle, r0, r1, n_trial, 0, 150000)
+    assert abs(ratio - expect) < 4.0 * se, (ratio, expect, se)
+
+
+def test_literal_printed_cb_weight_breaks_detailed_balance(oracle):
+    """The alternative, literal reading of Eq. (12), with the extra factor
+    (N_i + 1)/N_i and n_trial fresh reverse trials, fails the same test: the
+    test has the power to reject a wrong weight."""
+    ratio, se, expect = _ratio(oracle, 1.02, 1.09, 10, 1, 150000)
+    assert abs(ratio - expect) > 6.0 * se, (ratio, expect, se)
+
+
+@pytest.mark.parametrize("n_trial", [0, 5])
+def test_asakura_oosawa_pair_distribution(oracle, n_trial):
+    bins, rmax, lo = 24, 1.2, 20          # bins of 0.05 starting at contact
+    edges = np.linspace(0.0, rmax, bins + 1)
+    expect = []
+    for b in range(lo, bins):
+        r = np.linspace(edges[b], edges[b + 1], 401)
+        expect.append(np.trapezoid(r ** 2 * np.exp(Z_P * lens(r)), r))
+    expect = np.array(expect) / np.sum(expect)
+    a, b = _pair(1.5)
+    hs = []
+    for seed in range(1, 9):
+        _, _, _, h = oracle.run(np.array([a, b]), L2, q=Q, n_r=Z_P, n_trial=n_trial,
+                                d_max=0.03, seed=seed, n_sweeps=60000,
+                                hist_bins=bins, hist_rmax=rmax)
+        h = h[lo:].astype(float)
+        hs.append(h / h.sum())
+    hs = np.array(hs)
+    m, se = hs.mean(0), hs.std(0, ddof=1) / math.sqrt(len(hs))
+    z = (m - expect) / se
+    assert np.all(np.abs(z) < 4.0), z
+    # the depletion attraction is visible: contact bin well above r^2 alone
+    r2 = np.array([(edges[b + 1] ** 3 - edges[b] ** 3) for b in range(lo, bins)])
+    assert m[0] / m[-1] > 2.0 * r2[0] / r2[-1]
+
+
+def _hard_spheres(oracle, phi, n_eq=2000, n_run=8000):
+    s = W.make_system("hs", W.SPHERE, 256, phi, 0.2, 0.0)
+    pos, _, _, _ = oracle.run(s.pos, s.L, q=0.2, n_r=0.0, d_max=0.1, n_sweeps=n_eq)
+    bins, rmax = 130, 1.3
+    pos2, _, _, h = oracle.run(pos, s.L, q=0.2, n_r=0.0, d_max=0.1, n_sweeps=n_run,
+                               sweep0=n_eq, hist_bins=bins, hist_rmax=rmax)
+    return s, pos2, h, bins, rmax, n_run
+
+
+@pytest.mark.parametrize("phi", [0.2, 0.3])
+def test_hard_sphere_limit_carnahan_starling(oracle, phi):
+    s, pos, h, bins, rmax, n_run = _hard_spheres(oracle, phi)
+    edges = np.linspace(0.0, rmax, bins + 1)
+    rho = s.n / s.L ** 3
+    shell = 4.0 * math.pi / 3.0 * (edges[1:] ** 3 - edges[:-1] ** 3)
+    g = h / (n_run * s.n / 2.0 * rho * shell)
+    mid = 0.5 * (edges[1:] + edges[:-1])
+    sel = (mid > 1.0) & (mid < 1.08)
+    g1 = np.polyval(np.polyfit(mid[sel], g[sel], 2), 1.0)
+    Z = 1.0 + 4.0 * phi * g1
+    Z_cs = (1 + phi + phi ** 2 - phi ** 3) / (1 - phi) ** 3
+    assert abs(Z / Z_cs - 1.0) < 0.025, (Z, Z_cs)
+    # free-volume fraction of a q=0.2 test sphere vs scaled-particle theory
+    alpha = oracle.free_volume(pos, s.L, 0.2, n_probe=100000)
+    gam, q = phi / (1 - phi), 0.2
+    A, B, C = 3 * q + 3 * q * q + q ** 3, 4.5 * q * q + 3 * q ** 3, 3 * q ** 3
+    spt = (1 - phi) * math.exp(-A * gam - B * gam ** 2 - C * gam ** 3)
+    assert abs(alpha / spt - 1.0) < 0.02, (alpha, spt)
+
+
+def test_single_colloid_free_volume_exact(oracle):
+    L, q = 3.0, 0.3
+    alpha = oracle.free_volume(np.array([[1.0, 2.0, 0.5]]), L, q, n_probe=400000)
+    exact = 1.0 - 4.0 / 3.0 * math.pi * (0.5 + q / 2) ** 3 / L ** 3
+    assert abs(alpha - exact) < 4.0 * math.sqrt(exact * (1 - exact) / 400000)

@@ -1,0 +1,74 @@
+"""Pins of the counter-based RNG (Philox4x32-10) and its word-to-real maps.
+
+The paper names no RNG; Philox4x32-10 is the chosen reading.  What matters for
+the method is that the streams are uniform and independent, and that the
+word-to-real maps hit exactly the intervals the specification states.  These
+are checked against properties, not against a retyped formula."""
+import numpy as np
+from scipy import stats
+
+
+def _words(oracle, n, key=(1, 0), vary=0):
+    out = np.empty((n, 4), dtype=np.uint64)
+    for i in range(n):
+        ctr = [0, 0, 0, 0]
+        ctr[vary] = i
+        out[i] = oracle.philox(ctr, key)
+    return out
+
+
+def test_uniformity_chi2(oracle):
+    w = _words(oracle, 8192)
+    for col in range(4):
+        top = (w[:, col] >> np.uint64(24)).astype(np.int64)
+        hist = np.bincount(top, minlength=256)
+        p = stats.chisquare(hist).pvalue
+        assert p > 1e-4, (col, p)
+
+
+def test_bit_balance_and_counter_words(oracle):
+    for vary in range(4):
+        w = _words(oracle, 4096, vary=vary)
+        for col in range(4):
+            bits = ((w[:, col][:, None] >> np.arange(32, dtype=np.uint64)) & np.uint64(1))
+            mean = bits.mean(axis=0)
+            # each of the 32 bits is a fair coin: 5 sigma of a binomial(4096, 1/2)
+            assert np.all(np.abs(mean - 0.5) < 5 * 0.5 / np.sqrt(4096)), (vary, col)
+
+
+def test_avalanche(oracle):
+    """Flipping one counter bit flips about half of the 128 output bits."""
+    rng = np.random.default_rng(5)
+    flips = []
+    for _ in range(300):
+        ctr = rng.integers(0, 2 ** 32, size=4, dtype=np.uint64)
+        word, bit = rng.integers(0, 4), rng.integers(0, 32)
+        ctr2 = ctr.copy()
+        ctr2[word] ^= np.uint64(1) << np.uint64(bit)
+        a = oracle.philox(ctr, (7, 9)).astype(np.uint64)
+        b = oracle.philox(ctr2, (7, 9)).astype(np.uint64)
+        flips.append(sum(bin(int(x ^ y)).count("1") for x, y in zip(a, b)))
+    assert abs(np.mean(flips) - 64.0) < 2.0
+
+
+def test_key_changes_stream(oracle):
+    a = oracle.philox([3, 4, 5, 6], (1, 0))
+    b = oracle.philox([3, 4, 5, 6], (1, 1))
+    c = oracle.philox([3, 4, 5, 6], (2, 0))
+    assert not np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+def test_word_to_real_maps(oracle):
+    two32 = 2.0 ** 32
+    # open interval (0,1), midpoints of 2^32 equal slices
+    assert oracle.u01(0) == 0.5 / two32
+    assert oracle.u01(2 ** 32 - 1) == 1.0 - 0.5 / two32
+    # symmetric (-1,1): s11(w) = 2 u01(w) - 1 exactly, odd symmetry w <-> ~w
+    for w in (0, 1, 12345, 2 ** 31 - 1, 2 ** 31, 2 ** 32 - 1):
+        assert oracle.s11(w) == 2.0 * oracle.u01(w) - 1.0
+        assert oracle.s11(w) == -oracle.s11(2 ** 32 - 1 - w)
+    # 53-bit [0,1)
+    assert oracle.u53(0, 0) == 0.0
+    assert oracle.u53(2 ** 32 - 1, 2 ** 32 - 1) == 1.0 - 2.0 ** -53
+    assert oracle.u53(2 ** 5, 0) == 2.0 ** -27      # lowest kept bit of word 0
+    assert oracle.u53(0, 2 ** 6) == 2.0 ** -53      # lowest kept bit of word 1
