@@ -1,0 +1,165 @@
+/*
+ * hpmc_dep.h — C ABI of the GB300 implicit-depletant hard-particle Monte Carlo
+ * library (libhpmc_dep.so).
+ *
+ * The method is that of Glaser, Karas & Glotzer, "A parallel algorithm for
+ * implicit depletant simulations" (arXiv:1508.07077):
+ *   - N hard colloids in a cubic periodic box of side L, in a grand-canonical
+ *     bath of ideal-gas (penetrable) depletants of diameter q and fugacity
+ *     z_p, sampled with the semigrand weight exp(z_p V_f - beta H_cc)
+ *     (Sec. III.A, Eq. 2);
+ *   - single-colloid trial moves in a checkerboard of active cells
+ *     (Sec. III.E); for each move a Poisson number of depletants is inserted
+ *     in the circumsphere of the moved colloid's new pose (Sec. III.B-C), and
+ *     the move is accepted with the configurational-bias weight (Sec. III.D,
+ *     Eq. 12) or, for n_trial = 0, rejected on any blocking depletant.
+ *
+ * Conventions for every entry point:
+ *   - Return value: HPMC_OK (0) or a negative HPMC_ERR_* code; nothing throws
+ *     or aborts across this boundary.  hpmc_strerror() names the code.
+ *   - Pointers are plain host or device addresses as each argument states;
+ *     arguments with a `mem` flag accept either (HPMC_HOST / HPMC_DEVICE).
+ *     Positions are row-major n x 3 doubles (x, y, z), orientations n x 4
+ *     doubles (w, x, y, z) unit quaternions, body frame -> box frame.
+ *   - The library owns all device memory it allocates; inputs are copied.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously on it unless stated.
+ *   - Errors raised inside kernels (e.g. a neighbourhood larger than the
+ *     on-chip capacity) are sticky and reported by the next synchronising
+ *     call (hpmc_get_state, hpmc_sync) as HPMC_ERR_DEVICE.
+ */
+#ifndef HPMC_DEP_H
+#define HPMC_DEP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HPMC_OK 0
+#define HPMC_ERR_ARG (-1)      /* invalid argument or parameter combination */
+#define HPMC_ERR_OVERLAP (-2)  /* the configuration has overlapping colloids */
+#define HPMC_ERR_CUDA (-3)     /* a CUDA runtime call failed */
+#define HPMC_ERR_TIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define HPMC_ERR_STATE (-5)    /* call not valid in the context's state */
+#define HPMC_ERR_CAP (-6)      /* a size exceeds a documented capacity */
+#define HPMC_ERR_DEVICE (-7)   /* a kernel recorded an error (sticky) */
+
+#define HPMC_SPHERE 0          /* params: {diameter} */
+#define HPMC_HEMISPHERE 1      /* params: {diameter}; reference point = centre of the flat face */
+#define HPMC_SPHEROID 2        /* params: {a, c}: semi-axes a = b (equator), c (body z) */
+
+#define HPMC_FP64 0            /* every overlap test in FP64 */
+#define HPMC_FP32_RECHECK 1    /* FP32 tests with a certified margin, FP64 recheck near contact */
+
+#define HPMC_HOST 0
+#define HPMC_DEVICE 1
+
+typedef struct hpmc_ctx hpmc_ctx;
+
+/* Event counters, accumulated since creation or hpmc_reset_counters().
+ * The first eight are a pure function of the trajectory and are identical
+ * on every correct implementation of the method; the rest depend on the
+ * evaluation order (early exit) or on the precision form. */
+typedef struct hpmc_counters {
+    uint64_t moves;            /* trial moves proposed */
+    uint64_t accept;           /* accepted */
+    uint64_t reject_cell;      /* proposal left its cell (Sec. III.E) */
+    uint64_t reject_overlap;   /* colloid-colloid overlap at the new pose */
+    uint64_t reject_depletant; /* n_trial = 0 and a depletant blocks the move */
+    uint64_t reject_cb;        /* n_trial > 0: CB weight W = 0 or u >= W */
+    uint64_t dep_drawn;        /* sum of Poisson counts N_p over moves that drew them */
+    uint64_t translate;        /* translation (not rotation) proposals */
+    uint64_t dep_evaluated;    /* depletants classified before an early exit */
+    uint64_t dep_blocking;     /* blocking depletants found */
+    uint64_t cb_fwd_ok;        /* successful forward CB reinsertions */
+    uint64_t cb_rev_ok;        /* successful reverse CB reinsertions */
+    uint64_t cap_hits;         /* attempt-stream caps reached (expected 0) */
+    uint64_t rechecks;         /* FP32 decisions re-taken in FP64 (HPMC_FP32_RECHECK) */
+    uint64_t reserved[2];
+} hpmc_counters;
+
+/* Create a context on CUDA device `device` for n colloids in a cubic box of
+ * side box_l with positions pos (n x 3, each in [0, box_l)) and orientations
+ * quat (n x 4, or NULL = identity), both in memory `mem`.  seed and replica
+ * key the counter-based random streams (Philox4x32-10): a trajectory is a
+ * pure function of (inputs, parameters, seed, replica, sweep index).
+ * precision: HPMC_FP64 or HPMC_FP32_RECHECK.  Defaults: unit spheres, no
+ * depletants (z_p = 0), translations d_max = 0.1.  Overlaps are checked at the
+ * first hpmc_sweep.  *out receives the context (NULL on failure). */
+int hpmc_init(hpmc_ctx **out, int n, double box_l, const double *pos,
+              const double *quat, int mem, uint64_t seed, uint32_t replica,
+              int precision, int device);
+
+/* Colloid shape (Sec. II; hemisphere Sec. V.A; discoid = oblate spheroid
+ * a = b, c < a, Sec. V.B).  params/nparams as listed at HPMC_SPHERE etc. */
+int hpmc_set_shape(hpmc_ctx *ctx, int kind, const double *params, int nparams);
+
+/* Penetrable ideal-gas depletants of diameter q (q >= 0) at reservoir number
+ * density / fugacity n_r = z_p (Sec. III.A; phi_p^r = (pi/6) q^3 z_p), and
+ * n_trial configurational-bias reinsertions per blocking depletant
+ * (Sec. III.D, Eq. 12; 0 = plain rejection).  The mean number of depletants
+ * per move, lambda = z_p (4 pi / 3) (R_circ + q/2)^3, must not exceed 700. */
+int hpmc_set_depletant(hpmc_ctx *ctx, double q, double n_r, int n_trial);
+
+/* Trial moves: translation uniform in [-d_max, d_max]^3, rotation by at most
+ * a_max radians about a uniformly random axis (anisotropic shapes only),
+ * translation chosen with probability p_translate when both are enabled.
+ * d_max must be below the cell width. */
+int hpmc_set_moves(hpmc_ctx *ctx, double d_max, double a_max, double p_translate);
+
+/* Checkerboard cells per box side (even, width >= 2 R_circ + q), or 0 for the
+ * largest valid count.  Part of the trajectory's definition (Sec. III.E). */
+int hpmc_set_cells(hpmc_ctx *ctx, int n_cell);
+
+/* Launch shape: warps cooperating on one moved colloid's depletants (1..8).
+ * A performance knob only: results are identical for every value. */
+int hpmc_set_launch(hpmc_ctx *ctx, int warps_per_colloid);
+
+/* Enqueue n_sweeps checkerboard sweeps (each colloid gets one trial move per
+ * sweep) on `stream`.  The first call after a parameter change validates the
+ * configuration (synchronously: HPMC_ERR_OVERLAP if colloids overlap) and
+ * records the sweep as a CUDA graph. */
+int hpmc_sweep(hpmc_ctx *ctx, int n_sweeps, void *stream);
+
+/* Copy the state out (synchronises `stream`): positions (n x 3) and
+ * orientations (n x 4, may be NULL) into memory `mem`; *sweep (may be NULL)
+ * receives the next sweep index; *counters (may be NULL) the counters.
+ * Returns HPMC_ERR_DEVICE if a kernel recorded an error. */
+int hpmc_get_state(hpmc_ctx *ctx, double *pos, double *quat, int mem,
+                   uint64_t *sweep, hpmc_counters *counters, void *stream);
+
+/* Replace positions / orientations (quat may be NULL to keep them) and the
+ * sweep index (checkpoint / resume: bit-exact continuation). */
+int hpmc_set_state(hpmc_ctx *ctx, const double *pos, const double *quat, int mem,
+                   uint64_t sweep, void *stream);
+
+/* Zero the counters. */
+int hpmc_reset_counters(hpmc_ctx *ctx);
+
+/* Block until all work of the context has finished; report sticky errors. */
+int hpmc_sync(hpmc_ctx *ctx);
+
+/* Standalone checkerboard cell list of one sweep (Sec. III.E): the grid shift
+ * of sweep `sweep` under (seed, replica), cells of width box_l / n_cell.
+ * pos_dev: device n x 3 doubles in [0, box_l).  Outputs (device):
+ * cell_start[n_cell^3 + 1] (exclusive prefix of counts), cell_idx[n] (the
+ * colloids of each cell in ascending index).  Allocates its scratch (cell
+ * counts and per-colloid cell ids) with cudaMallocAsync / cudaFreeAsync on
+ * `stream`. */
+int hpmc_cell_list(int n, double box_l, int n_cell, const double *pos_dev,
+                   uint64_t seed, uint32_t replica, uint64_t sweep,
+                   int *cell_start_dev, int *cell_idx_dev, void *stream);
+
+/* Human-readable name of an HPMC_* code. */
+const char *hpmc_strerror(int code);
+
+/* Free the context and its device memory (synchronises its work). */
+void hpmc_destroy(hpmc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPMC_DEP_H */

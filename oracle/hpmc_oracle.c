@@ -190,6 +190,7 @@ static int cell_coord(double x, double sigma, double L, double w, int nc)
     if (s < 0.0) s = s + L;
     int c = (int)(s / w);
     if (c >= nc) c = nc - 1;
+    if (c < 0) c = 0;
     return c;
 }
 

@@ -1,0 +1,638 @@
+// C ABI of the GB300 implicit-depletant HPMC library (see include/hpmc_dep.h).
+//
+// Host side: parameter validation, the Poisson table (Sec. III.B step 2), the
+// checkerboard geometry (Sec. III.E), device buffers, and one CUDA graph per
+// sweep (cell list, 8 colour phases, sweep counter).  All per-step arithmetic
+// runs in the kernels of hpmc_kernels.cuh.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hpmc_dep.h"
+#include "hpmc_kernels.cuh"
+
+using namespace hpmc;
+
+namespace {
+
+constexpr double kPi = 3.141592653589793;
+constexpr int kTableCap = 32768;
+
+struct Params {
+    int shape = HPMC_SPHERE;
+    double sp[4] = {1.0, 0.0, 0.0, 0.0};
+    int nsp = 1;
+    double q = 0.0, n_r = 0.0;
+    int n_trial = 0;
+    double d_max = 0.1, a_max = 0.0, p_translate = 1.0;
+    int nc_req = 0;
+    int warps = 2;
+};
+
+}  // namespace
+
+struct hpmc_ctx {
+    int device = 0;
+    int n = 0;
+    double L = 0.0;
+    uint64_t seed = 0;
+    uint32_t replica = 0;
+    int precision = HPMC_FP64;
+    Params prm;
+
+    // derived
+    int nc = 0;
+    double w = 0.0, R_circ = 0.5, R_s = 0.5, lambda = 0.0;
+    int nF = 0;
+
+    // device buffers
+    double4 *d_pos = nullptr, *d_quat = nullptr;
+    double *d_stage = nullptr;  // n x 4 doubles: layout conversion for device callers
+    int *d_cell_start = nullptr, *d_cell_idx = nullptr, *d_count = nullptr, *d_cell_of = nullptr;
+    int ncell_alloc = -1;
+    Sched *d_sched = nullptr;
+    double *d_F = nullptr;
+    unsigned long long *d_sweep = nullptr, *d_counters = nullptr;
+    int *d_err = nullptr, *d_flag = nullptr;
+
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool dirty = true;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return HPMC_OK;
+    if (getenv("HPMC_VERBOSE")) fprintf(stderr, "hpmc: %s: %s\n", what, cudaGetErrorString(e));
+    return HPMC_ERR_CUDA;
+}
+
+#define CK(call)                                                \
+    do {                                                        \
+        int _rc = cuda_fail((call), #call);                     \
+        if (_rc != HPMC_OK) return _rc;                         \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Circumsphere radius of the shape about its reference point.
+double circum_radius(const Params &p)
+{
+    switch (p.shape) {
+    case HPMC_SPHERE: return 0.5 * p.sp[0];
+    case HPMC_HEMISPHERE: return 0.5 * p.sp[0];
+    case HPMC_SPHEROID: return p.sp[0] > p.sp[1] ? p.sp[0] : p.sp[1];
+    default: return -1.0;
+    }
+}
+
+// Poisson CDF table: p_0 = exp(-lambda), p_k = p_{k-1} lambda / k, cumulative
+// sum; stop after the first k > lambda with p_k < 2^-64.
+int build_table(double lambda, std::vector<double> &F)
+{
+    F.clear();
+    if (!(lambda >= 0.0) || lambda > 700.0) return HPMC_ERR_ARG;
+    double p = std::exp(-lambda);
+    double cdf = p;
+    F.push_back(cdf);
+    for (int k = 1;; ++k) {
+        p = (p * lambda) / (double)k;
+        cdf = cdf + p;
+        if ((int)F.size() >= kTableCap) return HPMC_ERR_CAP;
+        F.push_back(cdf);
+        if ((double)k > lambda && p < 5.421010862427522e-20) break;
+    }
+    return HPMC_OK;
+}
+
+SimParams make_params(hpmc_ctx *c)
+{
+    SimParams P;
+    std::memset(&P, 0, sizeof P);
+    const Params &p = c->prm;
+    P.n = c->n;
+    P.nc = c->nc;
+    P.half_nc = c->nc / 2;
+    P.n_stencil = c->nc == 2 ? 2 : 3;
+    P.L = c->L;
+    P.half_L = 0.5 * c->L;
+    P.w = c->w;
+    P.shape = p.shape;
+    P.n_trial = p.n_trial;
+    P.has_dep = c->lambda > 0.0 ? 1 : 0;
+    P.nF = c->nF;
+    P.R_s = c->R_s;
+    P.R_s2 = c->R_s * c->R_s;
+    const double Rd = 0.5 * p.sp[0] + 0.5 * p.q;
+    P.R_dep2 = Rd * Rd;
+    P.contact2 = p.sp[0] * p.sp[0];
+    const double cut = 2.0 * c->R_s + 0.01;
+    P.nb_cut2 = cut * cut;
+    P.d_max = p.d_max;
+    P.alpha = std::tan(0.5 * p.a_max);
+    P.p_translate = p.p_translate;
+    P.move_mode = 0;
+    P.key0 = (uint32_t)c->seed;
+    P.key1 = (uint32_t)(c->seed >> 32) ^ c->replica;
+    P.pos = c->d_pos;
+    P.quat = c->d_quat;
+    P.cell_start = c->d_cell_start;
+    P.cell_idx = c->d_cell_idx;
+    P.F = c->d_F;
+    P.sched = c->d_sched;
+    P.sweep = c->d_sweep;
+    P.counters = c->d_counters;
+    P.err = c->d_err;
+    return P;
+}
+
+// Enqueue the cell list of the sweep whose index is in *d_sweep.
+int enqueue_cells(hpmc_ctx *c, cudaStream_t s)
+{
+    const int ncell = c->nc * c->nc * c->nc;
+    CK(cudaMemsetAsync(c->d_count, 0, sizeof(int) * (size_t)ncell, s));
+    const int nb = (c->n + 255) / 256;
+    k_cells_count<<<nb, 256, 0, s>>>(c->n, c->L, c->w, c->nc, (const double *)c->d_pos, 4,
+                                     (uint32_t)c->seed, (uint32_t)(c->seed >> 32) ^ c->replica,
+                                     c->d_sweep, 0ull, c->d_cell_of, c->d_count, c->d_sched);
+    k_cells_scan<<<1, 1024, 0, s>>>(ncell, c->d_count, c->d_cell_start);
+    k_cells_scatter<<<nb, 256, 0, s>>>(c->n, c->d_cell_of, c->d_count, c->d_cell_idx);
+    k_cells_sort<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, c->d_cell_start, c->d_cell_idx);
+    CK(cudaGetLastError());
+    return HPMC_OK;
+}
+
+int enqueue_sweep(hpmc_ctx *c, cudaStream_t s)
+{
+    int rc = enqueue_cells(c, s);
+    if (rc != HPMC_OK) return rc;
+    SimParams P = make_params(c);
+    const int h = c->nc / 2;
+    const int n_active = h * h * h;
+    const int threads = 32 * c->prm.warps;
+    for (int phase = 0; phase < 8; ++phase)
+        k_phase_sphere_fp64<<<n_active, threads, 0, s>>>(P, phase);
+    k_sweep_end<<<1, 1, 0, s>>>(c->d_sweep);
+    CK(cudaGetLastError());
+    return HPMC_OK;
+}
+
+void free_graph(hpmc_ctx *c)
+{
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->exec = nullptr;
+    c->graph = nullptr;
+}
+
+// Validate parameters, derive geometry, upload the table, check the
+// configuration, record the sweep graph.
+int prepare(hpmc_ctx *c)
+{
+    const Params &p = c->prm;
+    if (p.shape != HPMC_SPHERE) return HPMC_ERR_ARG;  // other shapes: later forms
+    if (c->precision != HPMC_FP64) return HPMC_ERR_ARG;
+    c->R_circ = circum_radius(p);
+    if (!(c->R_circ > 0.0)) return HPMC_ERR_ARG;
+    if (!(p.q >= 0.0) || !(p.n_r >= 0.0) || p.n_trial < 0 || p.n_trial > 100000) return HPMC_ERR_ARG;
+    c->R_s = c->R_circ + 0.5 * p.q;
+    const double v0 = ((4.0 / 3.0) * kPi) * ((c->R_s * c->R_s) * c->R_s);
+    c->lambda = p.n_r > 0.0 ? p.n_r * v0 : 0.0;
+    const double w_min = 2.0 * c->R_circ + p.q;
+    int nc = p.nc_req;
+    if (nc == 0) {
+        nc = (int)(c->L / w_min);
+        if (nc & 1) nc -= 1;
+    }
+    if (nc < 2 || (nc & 1)) return HPMC_ERR_ARG;
+    if (nc > 1024) return HPMC_ERR_CAP;
+    const double w = c->L / (double)nc;
+    if (w < w_min) return HPMC_ERR_ARG;
+    if (!(p.d_max >= 0.0) || p.d_max >= w) return HPMC_ERR_ARG;
+    c->nc = nc;
+    c->w = w;
+
+    std::vector<double> F;
+    if (c->lambda > 0.0) {
+        int rc = build_table(c->lambda, F);
+        if (rc != HPMC_OK) return rc;
+    }
+    c->nF = (int)F.size();
+
+    DeviceGuard g(c->device);
+    const int ncell = nc * nc * nc;
+    if (ncell != c->ncell_alloc) {
+        cudaFree(c->d_cell_start);
+        cudaFree(c->d_count);
+        c->d_cell_start = nullptr;
+        c->d_count = nullptr;
+        CK(cudaMalloc(&c->d_cell_start, sizeof(int) * (size_t)(ncell + 1)));
+        CK(cudaMalloc(&c->d_count, sizeof(int) * (size_t)ncell));
+        c->ncell_alloc = ncell;
+    }
+    cudaFree(c->d_F);
+    c->d_F = nullptr;
+    if (c->nF > 0) {
+        CK(cudaMalloc(&c->d_F, sizeof(double) * (size_t)c->nF));
+        CK(cudaMemcpy(c->d_F, F.data(), sizeof(double) * (size_t)c->nF, cudaMemcpyHostToDevice));
+    }
+
+    // configuration check on a cell list of the current sweep index
+    CK(cudaStreamSynchronize(c->cap_stream));
+    int rc = enqueue_cells(c, c->cap_stream);
+    if (rc != HPMC_OK) return rc;
+    CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->cap_stream));
+    SimParams P = make_params(c);
+    k_check_spheres<<<(c->n + 255) / 256, 256, 0, c->cap_stream>>>(P, c->d_flag);
+    CK(cudaGetLastError());
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->cap_stream));
+    CK(cudaStreamSynchronize(c->cap_stream));
+    if (flag & 2) return HPMC_ERR_ARG;
+    if (flag & 1) return HPMC_ERR_OVERLAP;
+
+    free_graph(c);
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue_sweep(c, c->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (rc != HPMC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    CK(e);
+    c->graph = graph;
+    CK(cudaGraphInstantiate(&c->exec, c->graph, 0));
+    c->dirty = false;
+    return HPMC_OK;
+}
+
+int copy_in(hpmc_ctx *c, const double *pos, const double *quat, int mem, cudaStream_t s)
+{
+    const int n = c->n;
+    const int nb = (n + 255) / 256;
+    if (mem == HPMC_DEVICE) {
+        k_unpack<<<nb, 256, 0, s>>>(n, pos, quat, c->d_pos, quat ? c->d_quat : nullptr);
+        CK(cudaGetLastError());
+        return HPMC_OK;
+    }
+    if (mem != HPMC_HOST) return HPMC_ERR_ARG;
+    if (pos) {
+        CK(cudaMemcpyAsync(c->d_stage, pos, sizeof(double) * 3 * (size_t)n,
+                           cudaMemcpyHostToDevice, s));
+        k_unpack<<<nb, 256, 0, s>>>(n, c->d_stage, nullptr, c->d_pos, nullptr);
+        CK(cudaGetLastError());
+    }
+    if (quat) {
+        CK(cudaMemcpyAsync(c->d_stage, quat, sizeof(double) * 4 * (size_t)n,
+                           cudaMemcpyHostToDevice, s));
+        k_unpack<<<nb, 256, 0, s>>>(n, nullptr, c->d_stage, nullptr, c->d_quat);
+        CK(cudaGetLastError());
+    }
+    return HPMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hpmc_strerror(int code)
+{
+    switch (code) {
+    case HPMC_OK: return "ok";
+    case HPMC_ERR_ARG: return "invalid argument";
+    case HPMC_ERR_OVERLAP: return "overlapping colloids in the configuration";
+    case HPMC_ERR_CUDA: return "CUDA runtime error";
+    case HPMC_ERR_TIMEOUT: return "device-side wait timed out";
+    case HPMC_ERR_STATE: return "call not valid in this state";
+    case HPMC_ERR_CAP: return "size exceeds a documented capacity";
+    case HPMC_ERR_DEVICE: return "a kernel recorded an error";
+    default: return "unknown error";
+    }
+}
+
+int hpmc_init(hpmc_ctx **out, int n, double box_l, const double *pos, const double *quat,
+              int mem, uint64_t seed, uint32_t replica, int precision, int device)
+{
+    if (!out) return HPMC_ERR_ARG;
+    *out = nullptr;
+    if (n < 1 || !(box_l > 0.0) || !std::isfinite(box_l) || !pos) return HPMC_ERR_ARG;
+    if (mem != HPMC_HOST && mem != HPMC_DEVICE) return HPMC_ERR_ARG;
+    if (precision != HPMC_FP64 && precision != HPMC_FP32_RECHECK) return HPMC_ERR_ARG;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return HPMC_ERR_ARG;
+    hpmc_ctx *c = new (std::nothrow) hpmc_ctx();
+    if (!c) return HPMC_ERR_ARG;
+    c->device = device;
+    c->n = n;
+    c->L = box_l;
+    c->seed = seed;
+    c->replica = replica;
+    c->precision = precision;
+    DeviceGuard g(device);
+    int rc = HPMC_OK;
+#define CKI(call)                                  \
+    do {                                           \
+        rc = cuda_fail((call), #call);             \
+        if (rc != HPMC_OK) goto fail;              \
+    } while (0)
+    CKI(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    CKI(cudaMalloc(&c->d_pos, sizeof(double4) * (size_t)n));
+    CKI(cudaMalloc(&c->d_quat, sizeof(double4) * (size_t)n));
+    CKI(cudaMalloc(&c->d_stage, sizeof(double) * 4 * (size_t)n));
+    CKI(cudaMalloc(&c->d_cell_idx, sizeof(int) * (size_t)n));
+    CKI(cudaMalloc(&c->d_cell_of, sizeof(int) * (size_t)n));
+    CKI(cudaMalloc(&c->d_sched, sizeof(Sched)));
+    CKI(cudaMalloc(&c->d_sweep, sizeof(unsigned long long)));
+    CKI(cudaMalloc(&c->d_counters, sizeof(unsigned long long) * kCounterSlots * kNumCounters));
+    CKI(cudaMalloc(&c->d_err, sizeof(int)));
+    CKI(cudaMalloc(&c->d_flag, sizeof(int)));
+    CKI(cudaMemsetAsync(c->d_sweep, 0, sizeof(unsigned long long), c->cap_stream));
+    CKI(cudaMemsetAsync(c->d_counters, 0,
+                        sizeof(unsigned long long) * kCounterSlots * kNumCounters, c->cap_stream));
+    CKI(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->cap_stream));
+    {
+        // identity orientations unless given
+        std::vector<double> ident(4 * (size_t)n, 0.0);
+        for (int i = 0; i < n; ++i) ident[4 * (size_t)i] = 1.0;
+        CKI(cudaMemcpy(c->d_stage, ident.data(), sizeof(double) * 4 * (size_t)n,
+                       cudaMemcpyHostToDevice));
+        k_unpack<<<(n + 255) / 256, 256, 0, c->cap_stream>>>(n, nullptr, c->d_stage, nullptr,
+                                                             c->d_quat);
+        CKI(cudaGetLastError());
+        CKI(cudaStreamSynchronize(c->cap_stream));
+    }
+    rc = copy_in(c, pos, quat, mem, c->cap_stream);
+    if (rc != HPMC_OK) goto fail;
+    CKI(cudaStreamSynchronize(c->cap_stream));
+#undef CKI
+    *out = c;
+    return HPMC_OK;
+fail:
+    hpmc_destroy(c);
+    return rc;
+}
+
+int hpmc_set_shape(hpmc_ctx *c, int kind, const double *params, int nparams)
+{
+    if (!c || !params) return HPMC_ERR_ARG;
+    Params p = c->prm;
+    if (kind == HPMC_SPHERE || kind == HPMC_HEMISPHERE) {
+        if (nparams < 1 || !(params[0] > 0.0)) return HPMC_ERR_ARG;
+        p.sp[0] = params[0];
+        p.nsp = 1;
+    } else if (kind == HPMC_SPHEROID) {
+        if (nparams < 2 || !(params[0] > 0.0) || !(params[1] > 0.0)) return HPMC_ERR_ARG;
+        p.sp[0] = params[0];
+        p.sp[1] = params[1];
+        p.nsp = 2;
+    } else {
+        return HPMC_ERR_ARG;
+    }
+    p.shape = kind;
+    c->prm = p;
+    c->dirty = true;
+    return HPMC_OK;
+}
+
+int hpmc_set_depletant(hpmc_ctx *c, double q, double n_r, int n_trial)
+{
+    if (!c || !(q >= 0.0) || !(n_r >= 0.0) || !std::isfinite(n_r) || n_trial < 0)
+        return HPMC_ERR_ARG;
+    c->prm.q = q;
+    c->prm.n_r = n_r;
+    c->prm.n_trial = n_trial;
+    c->dirty = true;
+    return HPMC_OK;
+}
+
+int hpmc_set_moves(hpmc_ctx *c, double d_max, double a_max, double p_translate)
+{
+    if (!c || !(d_max >= 0.0) || !(a_max >= 0.0) || a_max > 3.0 || !(p_translate >= 0.0) ||
+        p_translate > 1.0)
+        return HPMC_ERR_ARG;
+    c->prm.d_max = d_max;
+    c->prm.a_max = a_max;
+    c->prm.p_translate = p_translate;
+    c->dirty = true;
+    return HPMC_OK;
+}
+
+int hpmc_set_cells(hpmc_ctx *c, int n_cell)
+{
+    if (!c || n_cell < 0 || (n_cell & 1) || n_cell == 1) return HPMC_ERR_ARG;
+    c->prm.nc_req = n_cell;
+    c->dirty = true;
+    return HPMC_OK;
+}
+
+int hpmc_set_launch(hpmc_ctx *c, int warps_per_colloid)
+{
+    if (!c || warps_per_colloid < 1 || warps_per_colloid > kMaxThreads / 32) return HPMC_ERR_ARG;
+    c->prm.warps = warps_per_colloid;
+    c->dirty = true;
+    return HPMC_OK;
+}
+
+int hpmc_sweep(hpmc_ctx *c, int n_sweeps, void *stream)
+{
+    if (!c || n_sweeps < 0) return HPMC_ERR_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->dirty) {
+        // order the preparation after the caller's pending work
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, s));
+        CK(cudaStreamWaitEvent(c->cap_stream, ev, 0));
+        cudaEventDestroy(ev);
+        int rc = prepare(c);
+        if (rc != HPMC_OK) return rc;
+    }
+    for (int k = 0; k < n_sweeps; ++k) CK(cudaGraphLaunch(c->exec, s));
+    return HPMC_OK;
+}
+
+static int read_err(hpmc_ctx *c, cudaStream_t s)
+{
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return e ? HPMC_ERR_DEVICE : HPMC_OK;
+}
+
+int hpmc_get_state(hpmc_ctx *c, double *pos, double *quat, int mem, uint64_t *sweep,
+                   hpmc_counters *counters, void *stream)
+{
+    if (!c || (mem != HPMC_HOST && mem != HPMC_DEVICE)) return HPMC_ERR_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = c->n, nb = (n + 255) / 256;
+    if (mem == HPMC_DEVICE) {
+        if (pos || quat) {
+            k_pack<<<nb, 256, 0, s>>>(n, c->d_pos, c->d_quat, pos, quat);
+            CK(cudaGetLastError());
+        }
+    } else {
+        if (pos) {
+            k_pack<<<nb, 256, 0, s>>>(n, c->d_pos, nullptr, c->d_stage, nullptr);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(pos, c->d_stage, sizeof(double) * 3 * (size_t)n,
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        if (quat) {
+            k_pack<<<nb, 256, 0, s>>>(n, nullptr, c->d_quat, nullptr, c->d_stage);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(quat, c->d_stage, sizeof(double) * 4 * (size_t)n,
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
+    }
+    if (sweep) {
+        unsigned long long v = 0;
+        CK(cudaMemcpyAsync(&v, c->d_sweep, sizeof v, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        *sweep = v;
+    }
+    if (counters) {
+        std::vector<unsigned long long> h((size_t)kCounterSlots * kNumCounters);
+        CK(cudaMemcpyAsync(h.data(), c->d_counters, sizeof(unsigned long long) * h.size(),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        uint64_t tot[kNumCounters] = {0};
+        for (int slot = 0; slot < kCounterSlots; ++slot)
+            for (int k = 0; k < kNumCounters; ++k) tot[k] += h[(size_t)slot * kNumCounters + k];
+        std::memset(counters, 0, sizeof *counters);
+        counters->moves = tot[kMoves];
+        counters->accept = tot[kAccept];
+        counters->reject_cell = tot[kRejCell];
+        counters->reject_overlap = tot[kRejOverlap];
+        counters->reject_depletant = tot[kRejDep];
+        counters->reject_cb = tot[kRejCb];
+        counters->dep_drawn = tot[kDepDrawn];
+        counters->translate = tot[kTranslate];
+        counters->dep_evaluated = tot[kDepEval];
+        counters->dep_blocking = tot[kDepBlocking];
+        counters->cb_fwd_ok = tot[kCbFwdOk];
+        counters->cb_rev_ok = tot[kCbRevOk];
+        counters->cap_hits = tot[kCapHits];
+        counters->rechecks = tot[kRechecks];
+    }
+    return read_err(c, s);
+}
+
+int hpmc_set_state(hpmc_ctx *c, const double *pos, const double *quat, int mem, uint64_t sweep,
+                   void *stream)
+{
+    if (!c || (mem != HPMC_HOST && mem != HPMC_DEVICE)) return HPMC_ERR_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = copy_in(c, pos, quat, mem, s);
+    if (rc != HPMC_OK) return rc;
+    unsigned long long v = sweep;
+    CK(cudaMemcpyAsync(c->d_sweep, &v, sizeof v, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    c->dirty = true;  // re-validate the new configuration at the next sweep
+    return HPMC_OK;
+}
+
+int hpmc_reset_counters(hpmc_ctx *c)
+{
+    if (!c) return HPMC_ERR_ARG;
+    DeviceGuard g(c->device);
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemset(c->d_counters, 0, sizeof(unsigned long long) * kCounterSlots * kNumCounters));
+    return HPMC_OK;
+}
+
+int hpmc_sync(hpmc_ctx *c)
+{
+    if (!c) return HPMC_ERR_ARG;
+    DeviceGuard g(c->device);
+    CK(cudaDeviceSynchronize());
+    return read_err(c, c->cap_stream);
+}
+
+int hpmc_cell_list(int n, double box_l, int n_cell, const double *pos_dev, uint64_t seed,
+                   uint32_t replica, uint64_t sweep, int *cell_start_dev, int *cell_idx_dev,
+                   void *stream)
+{
+    if (n < 0 || !(box_l > 0.0) || n_cell < 2 || (n_cell & 1) || n_cell > 1024) return HPMC_ERR_ARG;
+    if (n > 0 && (!pos_dev || !cell_idx_dev)) return HPMC_ERR_ARG;
+    if (!cell_start_dev) return HPMC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ncell = n_cell * n_cell * n_cell;
+    const double w = box_l / (double)n_cell;
+    int *count = nullptr, *cell_of = nullptr;
+    CK(cudaMallocAsync(&count, sizeof(int) * (size_t)ncell, s));
+    cudaError_t e = cudaMallocAsync(&cell_of, sizeof(int) * (size_t)(n > 0 ? n : 1), s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(count, s);
+        return cuda_fail(e, "cudaMallocAsync");
+    }
+    int rc = HPMC_OK;
+    e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncell, s);
+    if (e == cudaSuccess) {
+        if (n > 0)
+            k_cells_count<<<(n + 255) / 256, 256, 0, s>>>(n, box_l, w, n_cell, pos_dev, 3,
+                                                          (uint32_t)seed,
+                                                          (uint32_t)(seed >> 32) ^ replica,
+                                                          nullptr, sweep, cell_of, count, nullptr);
+        k_cells_scan<<<1, 1024, 0, s>>>(ncell, count, cell_start_dev);
+        if (n > 0) {
+            k_cells_scatter<<<(n + 255) / 256, 256, 0, s>>>(n, cell_of, count, cell_idx_dev);
+            k_cells_sort<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, cell_start_dev, cell_idx_dev);
+        }
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) rc = cuda_fail(e, "hpmc_cell_list");
+    cudaFreeAsync(cell_of, s);
+    cudaFreeAsync(count, s);
+    return rc;
+}
+
+void hpmc_destroy(hpmc_ctx *c)
+{
+    if (!c) return;
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    free_graph(c);
+    cudaFree(c->d_pos);
+    cudaFree(c->d_quat);
+    cudaFree(c->d_stage);
+    cudaFree(c->d_cell_start);
+    cudaFree(c->d_cell_idx);
+    cudaFree(c->d_count);
+    cudaFree(c->d_cell_of);
+    cudaFree(c->d_sched);
+    cudaFree(c->d_F);
+    cudaFree(c->d_sweep);
+    cudaFree(c->d_counters);
+    cudaFree(c->d_err);
+    cudaFree(c->d_flag);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+}  // extern "C"

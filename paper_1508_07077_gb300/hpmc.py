@@ -1,0 +1,245 @@
+"""Thin Python binding of ``libhpmc_dep.so`` (see ``include/hpmc_dep.h``).
+
+Argument marshalling only: every step of the Monte Carlo path runs in the
+library's CUDA kernels.  Functions carry the C names; negative return codes
+raise :class:`HPMCError`.  Device buffers may be torch CUDA tensors (their
+``data_ptr()`` is passed), host buffers numpy arrays.  The library is loaded
+from the package's in-tree ``_lib/``; if it is missing the import fails loudly
+(there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIBDIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib")
+LIB_PATH = os.path.join(_LIBDIR, "libhpmc_dep.so")
+
+HPMC_OK = 0
+HPMC_SPHERE, HPMC_HEMISPHERE, HPMC_SPHEROID = 0, 1, 2
+HPMC_FP64, HPMC_FP32_RECHECK = 0, 1
+HPMC_HOST, HPMC_DEVICE = 0, 1
+
+EXPORTS = ("hpmc_init", "hpmc_set_shape", "hpmc_set_depletant", "hpmc_set_moves",
+           "hpmc_set_cells", "hpmc_set_launch", "hpmc_sweep", "hpmc_get_state",
+           "hpmc_set_state", "hpmc_reset_counters", "hpmc_sync", "hpmc_cell_list",
+           "hpmc_strerror", "hpmc_destroy")
+
+
+class HPMCError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (where, strerror(code), code))
+
+
+class hpmc_counters(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in (
+        "moves", "accept", "reject_cell", "reject_overlap", "reject_depletant",
+        "reject_cb", "dep_drawn", "translate", "dep_evaluated", "dep_blocking",
+        "cb_fwd_ok", "cb_rev_ok", "cap_hits", "rechecks")] + [
+        ("reserved", ctypes.c_uint64 * 2)]
+
+    def as_dict(self) -> dict:
+        return {name: int(getattr(self, name)) for name, _ in self._fields_
+                if name != "reserved"}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the shared library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libhpmc_dep.so not built (run __graft_entry__.build()): " + path)
+    L = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    L.hpmc_init.argtypes = [ctypes.POINTER(vp), ip, ctypes.c_double, vp, vp, ip,
+                            ctypes.c_uint64, ctypes.c_uint32, ip, ip]
+    L.hpmc_set_shape.argtypes = [vp, ip, dp, ip]
+    L.hpmc_set_depletant.argtypes = [vp, ctypes.c_double, ctypes.c_double, ip]
+    L.hpmc_set_moves.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    L.hpmc_set_cells.argtypes = [vp, ip]
+    L.hpmc_set_launch.argtypes = [vp, ip]
+    L.hpmc_sweep.argtypes = [vp, ip, vp]
+    L.hpmc_get_state.argtypes = [vp, vp, vp, ip, ctypes.POINTER(ctypes.c_uint64),
+                                 ctypes.POINTER(hpmc_counters), vp]
+    L.hpmc_set_state.argtypes = [vp, vp, vp, ip, ctypes.c_uint64, vp]
+    L.hpmc_reset_counters.argtypes = [vp]
+    L.hpmc_sync.argtypes = [vp]
+    L.hpmc_cell_list.argtypes = [ip, ctypes.c_double, ip, vp, ctypes.c_uint64,
+                                 ctypes.c_uint32, ctypes.c_uint64, vp, vp, vp]
+    L.hpmc_strerror.argtypes = [ip]
+    L.hpmc_strerror.restype = ctypes.c_char_p
+    L.hpmc_destroy.argtypes = [vp]
+    L.hpmc_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("hpmc_strerror", "hpmc_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    return load().hpmc_strerror(int(code)).decode()
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != HPMC_OK:
+        raise HPMCError(rc, where)
+
+
+def _ptr(buf):
+    """(address, mem kind) of a numpy array (host) or torch tensor / raw int."""
+    if buf is None:
+        return None, HPMC_HOST
+    if isinstance(buf, np.ndarray):
+        if not buf.flags.c_contiguous or buf.dtype != np.float64:
+            raise ValueError("host arrays must be C-contiguous float64")
+        return buf.ctypes.data, HPMC_HOST
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return buf.data_ptr(), (HPMC_DEVICE if buf.is_cuda else HPMC_HOST)
+    raise TypeError("unsupported buffer type %r" % type(buf))
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def hpmc_init(n, box_l, pos, quat=None, seed=1, replica=0, precision=HPMC_FP64, device=0):
+    p, mem = _ptr(pos)
+    q, mem_q = _ptr(quat)
+    if quat is not None and mem_q != mem:
+        raise ValueError("pos and quat must live in the same memory")
+    ctx = ctypes.c_void_p()
+    _check(load().hpmc_init(ctypes.byref(ctx), int(n), float(box_l), p, q, mem,
+                            int(seed), int(replica), int(precision), int(device)),
+           "hpmc_init")
+    return ctx
+
+
+def hpmc_set_shape(ctx, kind, params):
+    a = np.ascontiguousarray(params, dtype=np.float64)
+    _check(load().hpmc_set_shape(ctx, int(kind), a.ctypes.data_as(
+        ctypes.POINTER(ctypes.c_double)), len(a)), "hpmc_set_shape")
+
+
+def hpmc_set_depletant(ctx, q, n_r, n_trial=0):
+    _check(load().hpmc_set_depletant(ctx, float(q), float(n_r), int(n_trial)),
+           "hpmc_set_depletant")
+
+
+def hpmc_set_moves(ctx, d_max, a_max=0.0, p_translate=1.0):
+    _check(load().hpmc_set_moves(ctx, float(d_max), float(a_max), float(p_translate)),
+           "hpmc_set_moves")
+
+
+def hpmc_set_cells(ctx, n_cell):
+    _check(load().hpmc_set_cells(ctx, int(n_cell)), "hpmc_set_cells")
+
+
+def hpmc_set_launch(ctx, warps_per_colloid):
+    _check(load().hpmc_set_launch(ctx, int(warps_per_colloid)), "hpmc_set_launch")
+
+
+def hpmc_sweep(ctx, n_sweeps=1, stream=None):
+    _check(load().hpmc_sweep(ctx, int(n_sweeps), _stream(stream)), "hpmc_sweep")
+
+
+def hpmc_get_state(ctx, pos=None, quat=None, stream=None):
+    """Fill pos (n x 3) / quat (n x 4) buffers (numpy or CUDA tensors, same
+    memory); returns (sweep, counters dict)."""
+    p, mem = _ptr(pos)
+    q, mem_q = _ptr(quat)
+    if pos is not None and quat is not None and mem != mem_q:
+        raise ValueError("pos and quat must live in the same memory")
+    if pos is None:
+        mem = mem_q
+    sweep = ctypes.c_uint64()
+    cnt = hpmc_counters()
+    _check(load().hpmc_get_state(ctx, p, q, mem, ctypes.byref(sweep), ctypes.byref(cnt),
+                                 _stream(stream)), "hpmc_get_state")
+    return int(sweep.value), cnt.as_dict()
+
+
+def hpmc_set_state(ctx, pos=None, quat=None, sweep=0, stream=None):
+    p, mem = _ptr(pos)
+    q, mem_q = _ptr(quat)
+    if pos is None:
+        mem = mem_q
+    _check(load().hpmc_set_state(ctx, p, q, mem, int(sweep), _stream(stream)),
+           "hpmc_set_state")
+
+
+def hpmc_reset_counters(ctx):
+    _check(load().hpmc_reset_counters(ctx), "hpmc_reset_counters")
+
+
+def hpmc_sync(ctx):
+    _check(load().hpmc_sync(ctx), "hpmc_sync")
+
+
+def hpmc_cell_list(n, box_l, n_cell, pos_dev, seed, replica, sweep, cell_start_dev,
+                   cell_idx_dev, stream=None):
+    _check(load().hpmc_cell_list(int(n), float(box_l), int(n_cell), _ptr(pos_dev)[0],
+                                 int(seed), int(replica), int(sweep),
+                                 cell_start_dev.data_ptr(), cell_idx_dev.data_ptr(),
+                                 _stream(stream)), "hpmc_cell_list")
+
+
+def hpmc_destroy(ctx):
+    if ctx:
+        load().hpmc_destroy(ctx)
+
+
+class Sampler:
+    """Owns one context: a convenience wrapper over the calls above."""
+
+    def __init__(self, pos, box_l, *, quat=None, shape=HPMC_SPHERE, shape_params=(1.0,),
+                 q=0.0, n_r=0.0, n_trial=0, d_max=0.1, a_max=0.0, p_translate=1.0,
+                 seed=1, replica=0, precision=HPMC_FP64, n_cell=0, warps=2, device=0):
+        pos = np.ascontiguousarray(pos, dtype=np.float64) if isinstance(pos, np.ndarray) else pos
+        if isinstance(quat, np.ndarray):
+            quat = np.ascontiguousarray(quat, dtype=np.float64)
+        self.n = int(pos.shape[0])
+        self.L = float(box_l)
+        self.ctx = hpmc_init(self.n, box_l, pos, quat, seed, replica, precision, device)
+        try:
+            hpmc_set_shape(self.ctx, shape, shape_params)
+            hpmc_set_depletant(self.ctx, q, n_r, n_trial)
+            hpmc_set_moves(self.ctx, d_max, a_max, p_translate)
+            hpmc_set_cells(self.ctx, n_cell)
+            hpmc_set_launch(self.ctx, warps)
+        except Exception:
+            self.close()
+            raise
+
+    def sweep(self, n=1, stream=None):
+        hpmc_sweep(self.ctx, n, stream)
+
+    def state(self, with_quat=False):
+        pos = np.empty((self.n, 3))
+        quat = np.empty((self.n, 4)) if with_quat else None
+        sweep, cnt = hpmc_get_state(self.ctx, pos, quat)
+        return pos, quat, sweep, cnt
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            hpmc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

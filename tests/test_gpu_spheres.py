@@ -1,0 +1,148 @@
+"""GPU parity of the sphere path against the oracle, through the C-ABI.
+
+Decisions (all trajectory counters) and positions must be bit-identical: both
+sides implement the same specification with correctly rounded FP64 and no
+contraction.  Sizes span several CTAs/tiles and ragged (empty, crowded)
+cells; the full-size 16384-sphere system is checked on its first sweeps."""
+import numpy as np
+import pytest
+
+from paper_1508_07077_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1508_07077_gb300 import build, hpmc
+    build.build()
+    hpmc.load()
+    return hpmc
+
+
+def _compare(oracle, lib, s, sweeps, *, n_trial=0, d_max=0.05, warps=2, n_cell=0,
+             seed=1, precision=0, sweep0=0):
+    smp = lib.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, n_trial=n_trial, d_max=d_max,
+                      seed=seed, warps=warps, n_cell=n_cell, precision=precision)
+    if sweep0:
+        lib.hpmc_set_state(smp.ctx, s.pos, None, sweep0)
+    smp.sweep(sweeps)
+    pos, _, sweep, cnt = smp.state()
+    smp.close()
+    ref, _, rc, _ = oracle.run(s.pos, s.L, q=s.q, n_r=s.n_r, n_trial=n_trial, d_max=d_max,
+                               seed=seed, n_cell=n_cell, n_sweeps=sweeps, sweep0=sweep0)
+    assert sweep == sweep0 + sweeps
+    for k in oracle.PARITY_COUNTERS:
+        assert cnt[k] == rc[k], (k, cnt[k], rc[k])
+    assert np.array_equal(pos, ref)
+    return cnt
+
+
+def test_cell_list_matches_oracle(oracle, lib):
+    for s in (W.spheres_256(), W.spheres_16384(0.2)):
+        nc = oracle.auto_cells(s.L, 0.5, s.q)
+        pos = torch.tensor(s.pos, device="cuda")
+        start = torch.empty(nc ** 3 + 1, dtype=torch.int32, device="cuda")
+        idx = torch.empty(s.n, dtype=torch.int32, device="cuda")
+        for sweep in (0, 7, 1234):
+            lib.hpmc_cell_list(s.n, s.L, nc, pos, 1, 0, sweep, start, idx)
+            torch.cuda.synchronize()
+            rs, ri = oracle.cell_list(s.pos, s.L, nc, 1, 0, sweep)
+            assert np.array_equal(start.cpu().numpy(), rs)
+            assert np.array_equal(idx.cpu().numpy(), ri)
+
+
+def test_cell_list_empty_and_single(oracle, lib):
+    start = torch.empty(4 ** 3 + 1, dtype=torch.int32, device="cuda")
+    idx = torch.empty(1, dtype=torch.int32, device="cuda")
+    pos = torch.tensor([[0.3, 4.9, 2.0]], dtype=torch.float64, device="cuda")
+    lib.hpmc_cell_list(1, 5.0, 4, pos, 3, 1, 9, start, idx)
+    rs, ri = oracle.cell_list(pos.cpu().numpy(), 5.0, 4, 3, 1, 9)
+    assert np.array_equal(start.cpu().numpy(), rs) and np.array_equal(idx.cpu().numpy(), ri)
+    lib.hpmc_cell_list(0, 5.0, 4, pos, 3, 1, 9, start, idx)
+    assert int(start.cpu().numpy().max()) == 0
+
+
+def test_spheres_256_plain_100_sweeps(oracle, lib):
+    """The 256-sphere system (phi .2, q .2, eta .2), max displacement 0.1, all
+    100 sweeps, n_trial = 0: bit-identical trajectory."""
+    cnt = _compare(oracle, lib, W.spheres_256(), 100, d_max=0.1)
+    assert cnt["reject_depletant"] > 0 and cnt["accept"] > 0
+
+
+@pytest.mark.parametrize("n_trial", [1, 4])
+def test_spheres_256_configurational_bias(oracle, lib, n_trial):
+    cnt = _compare(oracle, lib, W.spheres_256(), 25, n_trial=n_trial, d_max=0.08)
+    assert cnt["reject_cb"] > 0 and cnt["reject_depletant"] == 0
+
+
+@pytest.mark.parametrize("warps", [1, 3, 8])
+def test_launch_shape_does_not_change_results(oracle, lib, warps):
+    _compare(oracle, lib, W.spheres_256(), 10, warps=warps, n_trial=2)
+
+
+def test_tiny_box_two_cells(oracle, lib):
+    """n_c = 2: the 27-cell stencil collapses to 8 distinct cells."""
+    pos = W.tiny_spheres(8, 2.6)
+    s = W.System("tiny", W.SPHERE, 8, 2.6, 0.2, 30.0, pos, None)
+    _compare(oracle, lib, s, 40, d_max=0.08)
+    _compare(oracle, lib, s, 20, d_max=0.08, n_trial=3)
+
+
+def test_explicit_cell_count_and_resume_index(oracle, lib):
+    s = W.spheres_256()
+    _compare(oracle, lib, s, 12, n_cell=4, d_max=0.1)
+    _compare(oracle, lib, s, 12, d_max=0.1, sweep0=5000)
+
+
+def test_zero_fugacity_and_zero_step(oracle, lib):
+    s = W.spheres_256()
+    s0 = W.System("hs", W.SPHERE, s.n, s.L, s.q, 0.0, s.pos, None)
+    _compare(oracle, lib, s0, 30, d_max=0.1)
+    cnt = _compare(oracle, lib, s, 3, d_max=0.0)
+    assert cnt["reject_cell"] == 0
+
+
+@pytest.mark.parametrize("eta", [0.1, 0.4])
+def test_spheres_16384_first_sweeps(oracle, lib, eta):
+    """Full-size 16384-sphere system (phi .3, q .15): first sweeps bit-exact."""
+    _compare(oracle, lib, W.spheres_16384(eta), 3, d_max=0.05)
+
+
+def test_resume_and_device_io(oracle, lib):
+    s = W.spheres_256()
+    a = lib.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=0.05)
+    a.sweep(10)
+    pa, _, _, _ = a.state()
+    a.close()
+    b = lib.Sampler(torch.tensor(s.pos, device="cuda"), s.L, q=s.q, n_r=s.n_r, d_max=0.05)
+    b.sweep(5)
+    mid = torch.empty((s.n, 3), dtype=torch.float64, device="cuda")
+    sweep, _ = lib.hpmc_get_state(b.ctx, mid)
+    b.close()
+    c = lib.Sampler(mid, s.L, q=s.q, n_r=s.n_r, d_max=0.05)
+    lib.hpmc_set_state(c.ctx, mid, None, sweep)
+    c.sweep(5)
+    pc, _, sw, _ = c.state()
+    c.close()
+    assert sw == 10 and np.array_equal(pa, pc)
+
+
+def test_errors_are_reported(lib):
+    s = W.spheres_256()
+    bad = s.pos.copy()
+    bad[1] = bad[0] + np.array([0.3, 0.0, 0.0])
+    bad[1] %= s.L
+    smp = lib.Sampler(bad, s.L, q=s.q, n_r=s.n_r)
+    with pytest.raises(lib.HPMCError) as e:
+        smp.sweep(1)
+    assert e.value.code == -2
+    smp.close()
+    with pytest.raises(lib.HPMCError):
+        lib.Sampler(s.pos, s.L, q=s.q, n_r=1e7).sweep(1)  # lambda beyond the table
+    with pytest.raises(lib.HPMCError):
+        lib.Sampler(s.pos, 1.5, q=s.q, n_r=1.0).sweep(1)  # box smaller than two cells
