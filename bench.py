@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Throughput of the implicit-depletant HPMC hot path on one or more GB300s.
+
+Metric: colloid trial moves/s (whole job), with depletant insertions/s (drawn
+and evaluated) alongside, at fixed (phi_c, q, eta_r).
+
+Workload: 16384 hard spheres, phi_c = 0.30, depletant size ratio q = 0.15,
+reservoir packing fraction eta_r in {0.1, 0.2, 0.3, 0.4} (four independent
+systems), translation step tuned (untimed) to ~30% acceptance, n_trial = 0,
+FP32 + certified-margin form (``--precision fp64`` for the plain FP64 form).
+One step = one checkerboard sweep of each of the four systems (4 x 16384
+trial moves).  Synthetic, seeded inputs (fcc start, melted during tuning).
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on
+the launching stream, with a 256 MB buffer written between steps to flush L2
+(the working set itself is L2-resident).  Multi-GPU (torchrun): every rank
+runs its own replicas (weak scaling); barrier + max over ranks.
+
+``--impl reference`` times the CPU oracle (oracle/) on this host on a bounded
+sample of the same workload: it is the reference arm of this repository.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ETAS = (0.1, 0.2, 0.3, 0.4)
+N, PHI, Q = 16384, 0.30, 0.15
+WORKLOAD = "spheres_16384_phi0.30_q0.15_eta0.1-0.4"
+# Translation steps giving ~30% acceptance at each eta_r (from the untimed
+# tuner on the GPU); the reference arm uses them as fixed values.
+D_MAX_TUNED = {0.1: 0.0160, 0.2: 0.0080, 0.3: 0.0053, 0.4: 0.0040}
+ACC_TARGET = 0.30
+
+# Algorithmic ALU lane-operations (roofline):
+#  per evaluated depletant: 6/pi attempts x (Philox4x32-10: 40, point in the
+#  cube + ball test: 11) + old-pose test (8)
+OPS_PER_DEP = 6.0 / math.pi * (40.0 + 11.0) + 8.0
+#  per trial move: move + Poisson Philox (2 x 40), proposal and cell check
+#  (20), Poisson search (12), ~25 neighbour candidates x 8
+OPS_PER_MOVE = 2 * 40.0 + 20.0 + 12.0 + 25 * 8.0
+ISSUE_LANES_PER_SM = 128        # 4 SM sub-partitions x 32 lanes, one instruction / clock
+BYTES_PER_MOVE = 2 * 32 + 16 + 2 * 4   # pos (double4) read + cell-local copy + cell list ids
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sms, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def cpu_oracle_rate(systems, d_max, sweeps, first_sweep=0):
+    """Moves/s and insertions/s of the serial oracle on this host (1 core)."""
+    from oracle import oracle as O
+    O.build()
+    t0 = time.perf_counter()
+    moves = drawn = evaluated = 0
+    for s in systems:
+        _, _, c, _ = O.run(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=d_max[s.extra["eta_r"]],
+                           seed=s.seed, replica=s.replica, n_sweeps=sweeps, sweep0=first_sweep)
+        moves += c["moves"]
+        drawn += c["dep_drawn"]
+        evaluated += c["dep_evaluated"]
+    dt = time.perf_counter() - t0
+    return moves / dt, drawn / dt, evaluated / dt, dt, moves
+
+
+def run_reference(args, ws, rank):
+    from paper_1508_07077_gb300 import workloads as W
+    if rank != 0:
+        return
+    systems = [W.spheres_16384(eta, seed=1) for eta in ETAS]
+    for s in systems:
+        s.extra["eta_r"] = round(s.extra["eta_r"], 1)
+    # each step: one sweep of one of the four systems (bounded CPU sample)
+    times, moves = [], 0
+    drawn = evaluated = 0
+    from oracle import oracle as O
+    O.build()
+    pos = {s.extra["eta_r"]: s.pos.copy() for s in systems}
+    for step in range(args.warmup + args.steps):
+        s = systems[step % len(systems)]
+        eta = s.extra["eta_r"]
+        t0 = time.perf_counter()
+        p, _, c, _ = O.run(pos[eta], s.L, q=s.q, n_r=s.n_r, d_max=D_MAX_TUNED[eta], seed=1,
+                           n_sweeps=1, sweep0=step // len(systems))
+        dt = time.perf_counter() - t0
+        pos[eta] = p
+        if step >= args.warmup:
+            times.append(dt)
+            moves += c["moves"]
+            drawn += c["dep_drawn"]
+            evaluated += c["dep_evaluated"]
+    total = sum(times)
+    value = moves / total
+    line = {
+        "impl": "reference", "metric": "colloid trial moves/s", "value": value,
+        "unit": "moves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "serial CPU oracle",
+                   "step": "one sweep of one of the four eta_r systems (16384 moves)"},
+        "insertions_drawn_per_s": drawn / total,
+        "insertions_evaluated_per_s": evaluated / total,
+        "cpu_baseline": {"value": value, "unit": "moves/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d sweeps x 16384 spheres, eta_r cycling 0.1..0.4"
+                                   % args.steps},
+        "e2e": {"value": value, "unit": "moves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def tune(smp, hpmc, d0, rounds=12, sweeps=15):
+    """Untimed: melt the lattice start and tune d_max to ~30% acceptance."""
+    d = d0
+    for _ in range(rounds):
+        hpmc.hpmc_set_moves(smp.ctx, d, 0.0, 1.0)
+        hpmc.hpmc_reset_counters(smp.ctx)
+        smp.sweep(sweeps)
+        _, cnt = hpmc.hpmc_get_state(smp.ctx)
+        acc = cnt["accept"] / max(1, cnt["moves"])
+        d = d * min(2.0, max(0.5, (acc + 0.02) / (ACC_TARGET + 0.02)))
+    hpmc.hpmc_set_moves(smp.ctx, d, 0.0, 1.0)
+    return d
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import torch.distributed as dist
+    from paper_1508_07077_gb300 import build, hpmc, workloads as W
+
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    try:
+        hpmc.load()
+    except ImportError:
+        build.build()
+        hpmc.load()
+    prec = hpmc.HPMC_FP32_RECHECK if args.precision == "fp32" else hpmc.HPMC_FP64
+    stream = torch.cuda.current_stream()
+
+    systems = [W.spheres_16384(eta, seed=1) for eta in ETAS]
+    smps, dmax = [], {}
+    for s in systems:
+        eta = round(s.extra["eta_r"], 1)
+        smp = hpmc.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=D_MAX_TUNED[eta], seed=1,
+                           replica=rank, precision=prec, warps=args.warps, device=local)
+        dmax[eta] = tune(smp, hpmc, D_MAX_TUNED[eta]) if not args.no_tune else D_MAX_TUNED[eta]
+        smps.append(smp)
+    torch.cuda.synchronize()
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        for smp in smps:
+            smp.sweep(1, stream)
+
+    for _ in range(args.warmup):
+        step()
+    for smp in smps:
+        hpmc.hpmc_reset_counters(smp.ctx)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        time.sleep(0.25)
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    counters = [hpmc.hpmc_get_state(smp.ctx)[1] for smp in smps]
+    moves = sum(c["moves"] for c in counters)
+    drawn = sum(c["dep_drawn"] for c in counters)
+    evaluated = sum(c["dep_evaluated"] for c in counters)
+    rechecks = sum(c["rechecks"] for c in counters)
+    accept = sum(c["accept"] for c in counters)
+
+    # per-kernel durations (events around each launch, kernels launched one by one)
+    for smp in smps:
+        hpmc.hpmc_reset_counters(smp.ctx)
+        hpmc.hpmc_set_timing(smp.ctx, True)
+    timing_steps = min(args.steps, 50)
+    for k in range(timing_steps):
+        flush.zero_()
+        step()
+    kern_ms = [0.0, 0.0]
+    kern_n = [0, 0]
+    for smp in smps:
+        t, n = hpmc.hpmc_get_timing(smp.ctx)
+        hpmc.hpmc_set_timing(smp.ctx, False)
+        kern_ms = [a + b for a, b in zip(kern_ms, t)]
+        kern_n = [a + b for a, b in zip(kern_n, n)]
+    tc = [hpmc.hpmc_get_state(smp.ctx)[1] for smp in smps]
+    t_moves = sum(c["moves"] for c in tc)
+    t_eval = sum(c["dep_evaluated"] for c in tc)
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    host_pos = [torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy() for _ in smps]
+    for smp, hp in zip(smps, host_pos):
+        hpmc.hpmc_get_state(smp.ctx, hp)
+    sweeps_now = [hpmc.hpmc_get_state(smp.ctx)[0] for smp in smps]
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        for j, (smp, hp) in enumerate(zip(smps, host_pos)):
+            hpmc.hpmc_set_state(smp.ctx, hp, None, sweeps_now[j] + k, stream)
+            smp.sweep(1, stream)
+            hpmc.hpmc_get_state(smp.ctx, hp, None, stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+
+    # max over ranks
+    t_local = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms, e2e_s = float(t_local[0]), float(t_local[1])
+
+    if rank == 0:
+        clocks = clk.summary()
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        phase_launch_ms = kern_ms[1] / max(1, kern_n[1])
+        ops_per_launch = (OPS_PER_DEP * t_eval + OPS_PER_MOVE * t_moves) / max(1, kern_n[1])
+        achieved = ops_per_launch / (phase_launch_ms * 1e-3) / 1e12
+        f_peak = 2070.0e6
+        peak = sms * ISSUE_LANES_PER_SM * f_peak / 1e12
+        bytes_per_launch = BYTES_PER_MOVE * t_moves / max(1, kern_n[1])
+        value = ws * moves / (ms * 1e-3)
+        e2e_moves = ws * e2e_steps * len(smps) * N
+        line = {
+            "metric": "colloid trial moves/s", "value": value, "unit": "moves/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": "FP32+FP64 recheck" if prec == 1 else "FP64",
+                       "n_trial": 0, "step": "1 sweep of each of 4 systems (65536 moves)",
+                       "d_max": {str(k): round(v, 5) for k, v in dmax.items()},
+                       "l2": "flushed between steps (256 MB write)",
+                       "warps_per_colloid": args.warps},
+            "insertions_drawn_per_s": ws * drawn / (ms * 1e-3),
+            "insertions_evaluated_per_s": ws * evaluated / (ms * 1e-3),
+            "acceptance": accept / max(1, moves),
+            "fp64_rechecks_per_move": rechecks / max(1, moves),
+            "gpu_launches": args.steps * len(smps) * (1 + 4 + 8 + 1),
+            "kernels": {"phase_ms_per_launch": phase_launch_ms,
+                        "cells_ms_per_sweep": kern_ms[0] / max(1, kern_n[0]),
+                        "phase_share": kern_ms[1] / max(1e-9, sum(kern_ms))},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_phase_sphere_%s" % ("fp32" if prec == 1 else "fp64"),
+                         "peak_basis": "%d SMs x 128 lanes x 2070 MHz (issue rate)" % sms,
+                         "hbm_achieved_gbs": bytes_per_launch / (phase_launch_ms * 1e-3) / 1e9},
+            "clocks": clocks,
+            "e2e": {"value": e2e_moves / e2e_s, "unit": "moves/s",
+                    "h2d_bytes_per_step": len(smps) * N * 3 * 8,
+                    "d2h_bytes_per_step": len(smps) * (N * 3 * 8 + 8 * 16)},
+        }
+        if not args.no_cpu_baseline:
+            # the oracle on the host on a bounded sample of the same workload
+            for s in systems:
+                s.extra["eta_r"] = round(s.extra["eta_r"], 1)
+            mv, dr, ev, dt, nm = cpu_oracle_rate(systems, dmax, args.cpu_sweeps)
+            line["cpu_baseline"] = {
+                "value": mv, "unit": "moves/s", "cores": 1, "kind": "oracle",
+                "sample": "%d sweep(s) of each of the 4 systems from the fcc start "
+                          "(%d moves, %.1f s)" % (args.cpu_sweeps, nm, dt),
+                "insertions_evaluated_per_s": ev}
+        print(json.dumps(line))
+    for smp in smps:
+        smp.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
+    ap.add_argument("--warps", type=int, default=1)
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sweeps", type=int, default=25)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

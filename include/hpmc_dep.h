@@ -117,6 +117,21 @@ int hpmc_set_cells(hpmc_ctx *ctx, int n_cell);
  * A performance knob only: results are identical for every value. */
 int hpmc_set_launch(hpmc_ctx *ctx, int warps_per_colloid);
 
+/* FP32 form only: margin on squared distances inside which an FP32 decision
+ * is re-taken in FP64.  0 selects the derived certified bound (default);
+ * a value below that bound is rejected with HPMC_ERR_ARG at the next sweep.
+ * Larger margins only move more decisions to the exact FP64 path. */
+int hpmc_set_fp32_margin(hpmc_ctx *ctx, double margin);
+
+/* Per-kernel timing.  While on, hpmc_sweep launches its kernels one by one
+ * (no graph) with CUDA events around the cell-list kernels and around every
+ * colour-phase kernel.  hpmc_get_timing synchronises and returns the summed
+ * milliseconds and launch counts for kinds 0 = cell list (memset + 4 kernels,
+ * one bracket), 1 = colour-phase kernel, then clears them.  ms/launches may
+ * be NULL; nkinds is the length of both arrays (up to 2 are filled). */
+int hpmc_set_timing(hpmc_ctx *ctx, int on);
+int hpmc_get_timing(hpmc_ctx *ctx, double *ms, uint64_t *launches, int nkinds);
+
 /* Enqueue n_sweeps checkerboard sweeps (each colloid gets one trial move per
  * sweep) on `stream`.  The first call after a parameter change validates the
  * configuration (synchronously: HPMC_ERR_OVERLAP if colloids overlap) and

@@ -263,7 +263,7 @@ int oracle_cell_list(int n, double L, int nc, const double *pos, uint64_t seed,
 enum {
     C_MOVES = 0, C_ACCEPT, C_REJ_CELL, C_REJ_OVERLAP, C_REJ_DEP, C_REJ_CB,
     C_DEP_DRAWN, C_DEP_BLOCKING, C_CB_FWD_OK, C_CB_REV_OK, C_CAP, C_TRANSLATE,
-    C_N = 16
+    C_DEP_EVAL, C_N = 16
 };
 
 typedef struct {
@@ -451,6 +451,7 @@ static int accept_move(const osim *S, uint32_t sweep, int i, const double xn[3],
             cnt[C_CAP]++;
             break;
         }
+        cnt[C_DEP_EVAL]++;
         /* irrelevant unless it overlaps the new pose */
         if (!dep_overlap(&S->sh, S->q, e, qn)) continue;
         /* ignored if it overlaps the old configuration */

@@ -29,12 +29,13 @@ SHAPE_SPHERE, SHAPE_HEMISPHERE, SHAPE_SPHEROID = 0, 1, 2
 # counter slots of oracle_run
 COUNTERS = ("moves", "accept", "reject_cell", "reject_overlap", "reject_depletant",
             "reject_cb", "dep_drawn", "dep_blocking", "cb_fwd_ok", "cb_rev_ok",
-            "cap_hits", "translate")
+            "cap_hits", "translate", "dep_evaluated")
 N_COUNTERS = 16
 # counters that are a pure function of the trajectory (identical on any
 # correct implementation of the specification)
 PARITY_COUNTERS = ("moves", "accept", "reject_cell", "reject_overlap",
-                   "reject_depletant", "reject_cb", "dep_drawn", "translate")
+                   "reject_depletant", "reject_cb", "dep_drawn", "translate",
+                   "dep_evaluated")
 
 
 def build(force: bool = False) -> str:

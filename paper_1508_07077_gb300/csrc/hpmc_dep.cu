@@ -32,6 +32,7 @@ struct Params {
     double d_max = 0.1, a_max = 0.0, p_translate = 1.0;
     int nc_req = 0;
     int warps = 2;
+    double margin = 0.0;
 };
 
 }  // namespace
@@ -52,18 +53,25 @@ struct hpmc_ctx {
 
     // device buffers
     double4 *d_pos = nullptr, *d_quat = nullptr;
+    float4 *d_rel = nullptr;
     double *d_stage = nullptr;  // n x 4 doubles: layout conversion for device callers
     int *d_cell_start = nullptr, *d_cell_idx = nullptr, *d_count = nullptr, *d_cell_of = nullptr;
     int ncell_alloc = -1;
     Sched *d_sched = nullptr;
-    double *d_F = nullptr;
+    unsigned long long *d_T = nullptr;
     unsigned long long *d_sweep = nullptr, *d_counters = nullptr;
     int *d_err = nullptr, *d_flag = nullptr;
+
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;   // pairs (start, stop)
+    std::vector<int> tkind;         // kind of each pair
+    std::vector<cudaEvent_t> tpool; // reusable events
 
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    bool dirty = true;
+    bool dirty = true;        // parameters changed: re-derive and re-record the graph
+    bool state_dirty = true;  // configuration replaced: re-check overlaps only
 };
 
 namespace {
@@ -157,7 +165,33 @@ SimParams make_params(hpmc_ctx *c)
     P.quat = c->d_quat;
     P.cell_start = c->d_cell_start;
     P.cell_idx = c->d_cell_idx;
-    P.F = c->d_F;
+    P.T = c->d_T;
+    P.rel = c->d_rel;
+    // FP32 form: thresholds in float and the certified margin.  Every vector a
+    // test forms is a difference of cell-relative coordinates; each component
+    // carries at most E = 21 u max(w, 1) of FP32 error (rounding of the
+    // cell-relative copies, of the displacement, of the depletant coordinate
+    // and of the differences).  For |v| near a threshold radius R the squared
+    // length then errs by at most 2 sqrt(3) R E + 3 E^2 + 3 u R^2, plus u R^2
+    // for rounding the threshold itself; the margin is twice that, and at
+    // least 1e-5.
+    const double u = 0x1p-24;
+    const double Wc = c->w > 1.0 ? c->w : 1.0;
+    const double E = 21.0 * u * Wc;
+    const double Rmax = std::sqrt(std::fmax(P.R_s2, P.contact2));
+    const double bound = 2.0 * std::sqrt(3.0) * Rmax * E + 3.0 * E * E + 4.0 * u * Rmax * Rmax + 1e-12;
+    P.m_r2 = (float)std::fmax(1e-5, 2.0 * bound);
+    if (p.margin > 0.0) P.m_r2 = (float)p.margin;
+    P.m_cell = (float)(1e-5 * Wc);
+    P.w32 = (float)c->w;
+    P.L32 = (float)c->L;
+    P.half_L32 = (float)(0.5 * c->L);
+    P.R_s32 = (float)c->R_s;
+    P.T_s32 = (float)P.R_s2;
+    P.T_dep32 = (float)P.R_dep2;
+    P.T_contact32 = (float)P.contact2;
+    P.nb_cut2_32 = (float)P.nb_cut2;
+    P.d_max32 = (float)p.d_max;
     P.sched = c->d_sched;
     P.sweep = c->d_sweep;
     P.counters = c->d_counters;
@@ -173,7 +207,8 @@ int enqueue_cells(hpmc_ctx *c, cudaStream_t s)
     const int nb = (c->n + 255) / 256;
     k_cells_count<<<nb, 256, 0, s>>>(c->n, c->L, c->w, c->nc, (const double *)c->d_pos, 4,
                                      (uint32_t)c->seed, (uint32_t)(c->seed >> 32) ^ c->replica,
-                                     c->d_sweep, 0ull, c->d_cell_of, c->d_count, c->d_sched);
+                                     c->d_sweep, 0ull, c->d_cell_of, c->d_count, c->d_sched,
+                                     c->d_rel);
     k_cells_scan<<<1, 1024, 0, s>>>(ncell, c->d_count, c->d_cell_start);
     k_cells_scatter<<<nb, 256, 0, s>>>(c->n, c->d_cell_of, c->d_count, c->d_cell_idx);
     k_cells_sort<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, c->d_cell_start, c->d_cell_idx);
@@ -189,8 +224,57 @@ int enqueue_sweep(hpmc_ctx *c, cudaStream_t s)
     const int h = c->nc / 2;
     const int n_active = h * h * h;
     const int threads = 32 * c->prm.warps;
-    for (int phase = 0; phase < 8; ++phase)
-        k_phase_sphere_fp64<<<n_active, threads, 0, s>>>(P, phase);
+    for (int phase = 0; phase < 8; ++phase) {
+        if (c->precision == HPMC_FP32_RECHECK)
+            k_phase_sphere_fp32<<<n_active, threads, 0, s>>>(P, phase);
+        else
+            k_phase_sphere_fp64<<<n_active, threads, 0, s>>>(P, phase);
+    }
+    k_sweep_end<<<1, 1, 0, s>>>(c->d_sweep);
+    CK(cudaGetLastError());
+    return HPMC_OK;
+}
+
+cudaEvent_t pool_event(hpmc_ctx *c)
+{
+    if (!c->tpool.empty()) {
+        cudaEvent_t e = c->tpool.back();
+        c->tpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// One sweep launched kernel by kernel with events around the cell list and
+// around each colour-phase kernel.
+int enqueue_sweep_timed(hpmc_ctx *c, cudaStream_t s)
+{
+    cudaEvent_t a = pool_event(c), b = pool_event(c);
+    CK(cudaEventRecord(a, s));
+    int rc = enqueue_cells(c, s);
+    if (rc != HPMC_OK) return rc;
+    CK(cudaEventRecord(b, s));
+    c->tev.push_back(a);
+    c->tev.push_back(b);
+    c->tkind.push_back(0);
+    SimParams P = make_params(c);
+    const int h = c->nc / 2;
+    const int n_active = h * h * h;
+    const int threads = 32 * c->prm.warps;
+    for (int phase = 0; phase < 8; ++phase) {
+        cudaEvent_t x = pool_event(c), y = pool_event(c);
+        CK(cudaEventRecord(x, s));
+        if (c->precision == HPMC_FP32_RECHECK)
+            k_phase_sphere_fp32<<<n_active, threads, 0, s>>>(P, phase);
+        else
+            k_phase_sphere_fp64<<<n_active, threads, 0, s>>>(P, phase);
+        CK(cudaEventRecord(y, s));
+        c->tev.push_back(x);
+        c->tev.push_back(y);
+        c->tkind.push_back(1);
+    }
     k_sweep_end<<<1, 1, 0, s>>>(c->d_sweep);
     CK(cudaGetLastError());
     return HPMC_OK;
@@ -204,13 +288,32 @@ void free_graph(hpmc_ctx *c)
     c->graph = nullptr;
 }
 
+// Configuration check on a cell list of the current sweep index: positions in
+// [0, L) and no overlapping colloids.  Synchronous.
+int check_config(hpmc_ctx *c)
+{
+    CK(cudaStreamSynchronize(c->cap_stream));
+    int rc = enqueue_cells(c, c->cap_stream);
+    if (rc != HPMC_OK) return rc;
+    CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->cap_stream));
+    SimParams P = make_params(c);
+    k_check_spheres<<<(c->n + 255) / 256, 256, 0, c->cap_stream>>>(P, c->d_flag);
+    CK(cudaGetLastError());
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->cap_stream));
+    CK(cudaStreamSynchronize(c->cap_stream));
+    if (flag & 2) return HPMC_ERR_ARG;
+    if (flag & 1) return HPMC_ERR_OVERLAP;
+    c->state_dirty = false;
+    return HPMC_OK;
+}
+
 // Validate parameters, derive geometry, upload the table, check the
 // configuration, record the sweep graph.
 int prepare(hpmc_ctx *c)
 {
     const Params &p = c->prm;
     if (p.shape != HPMC_SPHERE) return HPMC_ERR_ARG;  // other shapes: later forms
-    if (c->precision != HPMC_FP64) return HPMC_ERR_ARG;
     c->R_circ = circum_radius(p);
     if (!(c->R_circ > 0.0)) return HPMC_ERR_ARG;
     if (!(p.q >= 0.0) || !(p.n_r >= 0.0) || p.n_trial < 0 || p.n_trial > 100000) return HPMC_ERR_ARG;
@@ -230,6 +333,17 @@ int prepare(hpmc_ctx *c)
     if (!(p.d_max >= 0.0) || p.d_max >= w) return HPMC_ERR_ARG;
     c->nc = nc;
     c->w = w;
+    if (p.margin > 0.0) {
+        Params def = p;
+        def.margin = 0.0;
+        hpmc_ctx probe = {};
+        probe.prm = def;
+        probe.w = w;
+        probe.R_s = c->R_s;
+        probe.nc = nc;
+        probe.L = c->L;
+        if ((float)p.margin < make_params(&probe).m_r2) return HPMC_ERR_ARG;
+    }
 
     std::vector<double> F;
     if (c->lambda > 0.0) {
@@ -249,26 +363,20 @@ int prepare(hpmc_ctx *c)
         CK(cudaMalloc(&c->d_count, sizeof(int) * (size_t)ncell));
         c->ncell_alloc = ncell;
     }
-    cudaFree(c->d_F);
-    c->d_F = nullptr;
+    cudaFree(c->d_T);
+    c->d_T = nullptr;
     if (c->nF > 0) {
-        CK(cudaMalloc(&c->d_F, sizeof(double) * (size_t)c->nF));
-        CK(cudaMemcpy(c->d_F, F.data(), sizeof(double) * (size_t)c->nF, cudaMemcpyHostToDevice));
+        // F[k] <= m 2^-53  <=>  m >= ceil(F[k] 2^53): exact integer form of the table
+        std::vector<unsigned long long> T((size_t)c->nF);
+        for (int k = 0; k < c->nF; ++k)
+            T[(size_t)k] = (unsigned long long)std::ceil(std::ldexp(F[(size_t)k], 53));
+        CK(cudaMalloc(&c->d_T, sizeof(unsigned long long) * (size_t)c->nF));
+        CK(cudaMemcpy(c->d_T, T.data(), sizeof(unsigned long long) * (size_t)c->nF,
+                      cudaMemcpyHostToDevice));
     }
 
-    // configuration check on a cell list of the current sweep index
-    CK(cudaStreamSynchronize(c->cap_stream));
-    int rc = enqueue_cells(c, c->cap_stream);
+    int rc = check_config(c);
     if (rc != HPMC_OK) return rc;
-    CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->cap_stream));
-    SimParams P = make_params(c);
-    k_check_spheres<<<(c->n + 255) / 256, 256, 0, c->cap_stream>>>(P, c->d_flag);
-    CK(cudaGetLastError());
-    int flag = 0;
-    CK(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->cap_stream));
-    CK(cudaStreamSynchronize(c->cap_stream));
-    if (flag & 2) return HPMC_ERR_ARG;
-    if (flag & 1) return HPMC_ERR_OVERLAP;
 
     free_graph(c);
     CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -359,6 +467,7 @@ int hpmc_init(hpmc_ctx **out, int n, double box_l, const double *pos, const doub
     CKI(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     CKI(cudaMalloc(&c->d_pos, sizeof(double4) * (size_t)n));
     CKI(cudaMalloc(&c->d_quat, sizeof(double4) * (size_t)n));
+    CKI(cudaMalloc(&c->d_rel, sizeof(float4) * (size_t)n));
     CKI(cudaMalloc(&c->d_stage, sizeof(double) * 4 * (size_t)n));
     CKI(cudaMalloc(&c->d_cell_idx, sizeof(int) * (size_t)n));
     CKI(cudaMalloc(&c->d_cell_of, sizeof(int) * (size_t)n));
@@ -459,17 +568,62 @@ int hpmc_sweep(hpmc_ctx *c, int n_sweeps, void *stream)
     if (!c || n_sweeps < 0) return HPMC_ERR_ARG;
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
-    if (c->dirty) {
+    if (c->dirty || c->state_dirty) {
         // order the preparation after the caller's pending work
         cudaEvent_t ev;
         CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         CK(cudaEventRecord(ev, s));
         CK(cudaStreamWaitEvent(c->cap_stream, ev, 0));
         cudaEventDestroy(ev);
-        int rc = prepare(c);
+        int rc = c->dirty ? prepare(c) : check_config(c);
         if (rc != HPMC_OK) return rc;
     }
+    if (c->timing) {
+        for (int k = 0; k < n_sweeps; ++k) {
+            int rc = enqueue_sweep_timed(c, s);
+            if (rc != HPMC_OK) return rc;
+        }
+        return HPMC_OK;
+    }
     for (int k = 0; k < n_sweeps; ++k) CK(cudaGraphLaunch(c->exec, s));
+    return HPMC_OK;
+}
+
+int hpmc_set_fp32_margin(hpmc_ctx *c, double margin)
+{
+    if (!c || !(margin >= 0.0) || margin > 1e3) return HPMC_ERR_ARG;
+    c->prm.margin = margin;
+    c->dirty = true;
+    return HPMC_OK;
+}
+
+int hpmc_set_timing(hpmc_ctx *c, int on)
+{
+    if (!c) return HPMC_ERR_ARG;
+    c->timing = on != 0;
+    return HPMC_OK;
+}
+
+int hpmc_get_timing(hpmc_ctx *c, double *ms, uint64_t *launches, int nkinds)
+{
+    if (!c || nkinds < 0) return HPMC_ERR_ARG;
+    DeviceGuard g(c->device);
+    CK(cudaDeviceSynchronize());
+    double acc[2] = {0.0, 0.0};
+    uint64_t cnt[2] = {0, 0};
+    for (size_t k = 0; k < c->tkind.size(); ++k) {
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, c->tev[2 * k], c->tev[2 * k + 1]));
+        acc[c->tkind[k]] += t;
+        cnt[c->tkind[k]] += 1;
+    }
+    for (cudaEvent_t e : c->tev) c->tpool.push_back(e);
+    c->tev.clear();
+    c->tkind.clear();
+    for (int k = 0; k < nkinds && k < 2; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (launches) launches[k] = cnt[k];
+    }
     return HPMC_OK;
 }
 
@@ -553,7 +707,7 @@ int hpmc_set_state(hpmc_ctx *c, const double *pos, const double *quat, int mem, 
     unsigned long long v = sweep;
     CK(cudaMemcpyAsync(c->d_sweep, &v, sizeof v, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
-    c->dirty = true;  // re-validate the new configuration at the next sweep
+    c->state_dirty = true;  // re-validate the new configuration at the next sweep
     return HPMC_OK;
 }
 
@@ -598,7 +752,8 @@ int hpmc_cell_list(int n, double box_l, int n_cell, const double *pos_dev, uint6
             k_cells_count<<<(n + 255) / 256, 256, 0, s>>>(n, box_l, w, n_cell, pos_dev, 3,
                                                           (uint32_t)seed,
                                                           (uint32_t)(seed >> 32) ^ replica,
-                                                          nullptr, sweep, cell_of, count, nullptr);
+                                                          nullptr, sweep, cell_of, count, nullptr,
+                                                          nullptr);
         k_cells_scan<<<1, 1024, 0, s>>>(ncell, count, cell_start_dev);
         if (n > 0) {
             k_cells_scatter<<<(n + 255) / 256, 256, 0, s>>>(n, cell_of, count, cell_idx_dev);
@@ -618,6 +773,8 @@ void hpmc_destroy(hpmc_ctx *c)
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();
     free_graph(c);
+    for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->tpool) cudaEventDestroy(e);
     cudaFree(c->d_pos);
     cudaFree(c->d_quat);
     cudaFree(c->d_stage);
@@ -626,7 +783,8 @@ void hpmc_destroy(hpmc_ctx *c)
     cudaFree(c->d_count);
     cudaFree(c->d_cell_of);
     cudaFree(c->d_sched);
-    cudaFree(c->d_F);
+    cudaFree(c->d_T);
+    cudaFree(c->d_rel);
     cudaFree(c->d_sweep);
     cudaFree(c->d_counters);
     cudaFree(c->d_err);

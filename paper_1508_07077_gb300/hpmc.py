@@ -23,7 +23,8 @@ HPMC_FP64, HPMC_FP32_RECHECK = 0, 1
 HPMC_HOST, HPMC_DEVICE = 0, 1
 
 EXPORTS = ("hpmc_init", "hpmc_set_shape", "hpmc_set_depletant", "hpmc_set_moves",
-           "hpmc_set_cells", "hpmc_set_launch", "hpmc_sweep", "hpmc_get_state",
+           "hpmc_set_cells", "hpmc_set_launch", "hpmc_set_fp32_margin", "hpmc_set_timing",
+           "hpmc_get_timing", "hpmc_sweep", "hpmc_get_state",
            "hpmc_set_state", "hpmc_reset_counters", "hpmc_sync", "hpmc_cell_list",
            "hpmc_strerror", "hpmc_destroy")
 
@@ -65,6 +66,10 @@ def load(path: str = LIB_PATH):
     L.hpmc_set_moves.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.hpmc_set_cells.argtypes = [vp, ip]
     L.hpmc_set_launch.argtypes = [vp, ip]
+    L.hpmc_set_fp32_margin.argtypes = [vp, ctypes.c_double]
+    L.hpmc_set_timing.argtypes = [vp, ip]
+    L.hpmc_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_uint64), ip]
     L.hpmc_sweep.argtypes = [vp, ip, vp]
     L.hpmc_get_state.argtypes = [vp, vp, vp, ip, ctypes.POINTER(ctypes.c_uint64),
                                  ctypes.POINTER(hpmc_counters), vp]
@@ -150,6 +155,22 @@ def hpmc_set_cells(ctx, n_cell):
 
 def hpmc_set_launch(ctx, warps_per_colloid):
     _check(load().hpmc_set_launch(ctx, int(warps_per_colloid)), "hpmc_set_launch")
+
+
+def hpmc_set_fp32_margin(ctx, margin):
+    _check(load().hpmc_set_fp32_margin(ctx, float(margin)), "hpmc_set_fp32_margin")
+
+
+def hpmc_set_timing(ctx, on):
+    _check(load().hpmc_set_timing(ctx, int(bool(on))), "hpmc_set_timing")
+
+
+def hpmc_get_timing(ctx):
+    """(ms, launches) per kind: 0 = cell list, 1 = colour-phase kernel."""
+    ms = (ctypes.c_double * 2)()
+    n = (ctypes.c_uint64 * 2)()
+    _check(load().hpmc_get_timing(ctx, ms, n, 2), "hpmc_get_timing")
+    return [float(x) for x in ms], [int(x) for x in n]
 
 
 def hpmc_sweep(ctx, n_sweeps=1, stream=None):

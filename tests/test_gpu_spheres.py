@@ -24,10 +24,15 @@ def lib():
     return hpmc
 
 
+PRECISIONS = [0, 1]   # HPMC_FP64, HPMC_FP32_RECHECK
+
+
 def _compare(oracle, lib, s, sweeps, *, n_trial=0, d_max=0.05, warps=2, n_cell=0,
-             seed=1, precision=0, sweep0=0):
+             seed=1, precision=0, sweep0=0, margin=0.0):
     smp = lib.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, n_trial=n_trial, d_max=d_max,
                       seed=seed, warps=warps, n_cell=n_cell, precision=precision)
+    if margin:
+        lib.hpmc_set_fp32_margin(smp.ctx, margin)
     if sweep0:
         lib.hpmc_set_state(smp.ctx, s.pos, None, sweep0)
     smp.sweep(sweeps)
@@ -67,50 +72,87 @@ def test_cell_list_empty_and_single(oracle, lib):
     assert int(start.cpu().numpy().max()) == 0
 
 
-def test_spheres_256_plain_100_sweeps(oracle, lib):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_spheres_256_plain_100_sweeps(oracle, lib, precision):
     """The 256-sphere system (phi .2, q .2, eta .2), max displacement 0.1, all
     100 sweeps, n_trial = 0: bit-identical trajectory."""
-    cnt = _compare(oracle, lib, W.spheres_256(), 100, d_max=0.1)
+    cnt = _compare(oracle, lib, W.spheres_256(), 100, d_max=0.1, precision=precision)
     assert cnt["reject_depletant"] > 0 and cnt["accept"] > 0
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("n_trial", [1, 4])
-def test_spheres_256_configurational_bias(oracle, lib, n_trial):
-    cnt = _compare(oracle, lib, W.spheres_256(), 25, n_trial=n_trial, d_max=0.08)
+def test_spheres_256_configurational_bias(oracle, lib, n_trial, precision):
+    cnt = _compare(oracle, lib, W.spheres_256(), 25, n_trial=n_trial, d_max=0.08,
+                   precision=precision)
     assert cnt["reject_cb"] > 0 and cnt["reject_depletant"] == 0
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("warps", [1, 3, 8])
-def test_launch_shape_does_not_change_results(oracle, lib, warps):
-    _compare(oracle, lib, W.spheres_256(), 10, warps=warps, n_trial=2)
+def test_launch_shape_does_not_change_results(oracle, lib, warps, precision):
+    _compare(oracle, lib, W.spheres_256(), 10, warps=warps, n_trial=2, precision=precision)
 
 
-def test_tiny_box_two_cells(oracle, lib):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_tiny_box_two_cells(oracle, lib, precision):
     """n_c = 2: the 27-cell stencil collapses to 8 distinct cells."""
     pos = W.tiny_spheres(8, 2.6)
     s = W.System("tiny", W.SPHERE, 8, 2.6, 0.2, 30.0, pos, None)
-    _compare(oracle, lib, s, 40, d_max=0.08)
-    _compare(oracle, lib, s, 20, d_max=0.08, n_trial=3)
+    _compare(oracle, lib, s, 40, d_max=0.08, precision=precision)
+    _compare(oracle, lib, s, 20, d_max=0.08, n_trial=3, precision=precision)
 
 
-def test_explicit_cell_count_and_resume_index(oracle, lib):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_explicit_cell_count_and_resume_index(oracle, lib, precision):
     s = W.spheres_256()
-    _compare(oracle, lib, s, 12, n_cell=4, d_max=0.1)
-    _compare(oracle, lib, s, 12, d_max=0.1, sweep0=5000)
+    _compare(oracle, lib, s, 12, n_cell=4, d_max=0.1, precision=precision)
+    _compare(oracle, lib, s, 12, d_max=0.1, sweep0=5000, precision=precision)
 
 
-def test_zero_fugacity_and_zero_step(oracle, lib):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_zero_fugacity_and_zero_step(oracle, lib, precision):
     s = W.spheres_256()
     s0 = W.System("hs", W.SPHERE, s.n, s.L, s.q, 0.0, s.pos, None)
-    _compare(oracle, lib, s0, 30, d_max=0.1)
-    cnt = _compare(oracle, lib, s, 3, d_max=0.0)
+    _compare(oracle, lib, s0, 30, d_max=0.1, precision=precision)
+    cnt = _compare(oracle, lib, s, 3, d_max=0.0, precision=precision)
     assert cnt["reject_cell"] == 0
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("eta", [0.1, 0.4])
-def test_spheres_16384_first_sweeps(oracle, lib, eta):
+def test_spheres_16384_first_sweeps(oracle, lib, eta, precision):
     """Full-size 16384-sphere system (phi .3, q .15): first sweeps bit-exact."""
-    _compare(oracle, lib, W.spheres_16384(eta), 3, d_max=0.05)
+    _compare(oracle, lib, W.spheres_16384(eta), 3, d_max=0.05, precision=precision)
+
+
+@pytest.mark.parametrize("n_trial", [0, 3])
+def test_fp32_recheck_path_is_exact(oracle, lib, n_trial):
+    """With a margin of 1 nearly every FP32 decision is re-taken in FP64; the
+    trajectory must not change, and the recheck counter shows the path ran."""
+    cnt = _compare(oracle, lib, W.spheres_256(), 8, d_max=0.08, n_trial=n_trial,
+                   precision=1, margin=1.0)
+    assert cnt["rechecks"] > 10 * cnt["dep_evaluated"] // 20
+
+
+def test_fp32_margin_below_bound_rejected(lib):
+    s = W.spheres_256()
+    smp = lib.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, precision=1)
+    lib.hpmc_set_fp32_margin(smp.ctx, 1e-9)
+    with pytest.raises(lib.HPMCError):
+        smp.sweep(1)
+    smp.close()
+
+
+def test_timing_mode_counts_launches(lib):
+    s = W.spheres_256()
+    smp = lib.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, precision=1)
+    smp.sweep(1)
+    lib.hpmc_set_timing(smp.ctx, True)
+    smp.sweep(3)
+    ms, n = lib.hpmc_get_timing(smp.ctx)
+    smp.close()
+    assert n == [3, 24] and ms[0] > 0 and ms[1] > 0
 
 
 def test_resume_and_device_io(oracle, lib):
