@@ -21,7 +21,8 @@ COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-shared",
                  "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "-I", INCLUDE]
 
 TARGETS = {
-    "libhpmc_dep.so": (["hpmc_dep.cu"], ["hpmc_kernels.cuh"]),
+    "libhpmc_dep.so": (["hpmc_dep.cu"], ["hpmc_common.cuh", "hpmc_cells.cuh", "hpmc_misc.cuh",
+                                       "hpmc_sphere_fp64.cuh", "hpmc_sphere_fp32.cuh"]),
     "libhpmc_peaks.so": (["pipe_peaks.cu"], []),
 }
 

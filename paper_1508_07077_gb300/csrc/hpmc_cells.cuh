@@ -1,0 +1,120 @@
+// Checkerboard cell lists (Sec. III.E), two layouts.
+//
+// * Binned (the sweep's own): one kernel per sweep computes the grid shift
+//   and colour order, bins every colloid into fixed-capacity cell slots with
+//   one atomic each, and writes the colloid's FP32 offset from its cell
+//   origin.  The order inside a bin is arbitrary; the CTA that moves a cell's
+//   colloids restores ascending index order itself.
+// * CSR (the standalone hpmc_cell_list): count -> exclusive scan -> scatter ->
+//   per-cell sort, giving cell_start[ncell + 1] and cell_idx[n] in ascending
+//   index order within each cell.
+#pragma once
+
+#include "hpmc_common.cuh"
+
+namespace hpmc {
+
+// One thread per colloid.  Block 0 thread 0 also writes the sweep's schedule.
+__global__ void k_cells_bin(const __grid_constant__ SimParams P)
+{
+    const uint32_t sweep = (uint32_t)(*P.sweep);
+    double sigma[3];
+    schedule_shift(P.key0, P.key1, sweep, P.w, sigma);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Sched s;
+        s.sigma[0] = sigma[0];
+        s.sigma[1] = sigma[1];
+        s.sigma[2] = sigma[2];
+        schedule_perm(P.key0, P.key1, sweep, s.perm);
+        s.sweep = sweep;
+        *P.sched = s;
+    }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const double4 p = P.pos[i];
+    const int nc = P.nc;
+    const int cx = cell_coord(p.x, sigma[0], P.L, P.w, nc);
+    const int cy = cell_coord(p.y, sigma[1], P.L, P.w, nc);
+    const int cz = cell_coord(p.z, sigma[2], P.L, P.w, nc);
+    const int c = cx + nc * (cy + nc * cz);
+    const int slot = atomicAdd(P.count[sweep & 1u] + c, 1);
+    if (slot < P.cap) P.bins[(size_t)c * P.cap + slot] = i;
+    else atomicCAS(P.err, kErrNone, kErrCellCap);
+    P.rel[i] = make_float4(cell_rel(p.x, sigma[0], P.L, P.w, cx), cell_rel(p.y, sigma[1], P.L, P.w, cy),
+                           cell_rel(p.z, sigma[2], P.L, P.w, cz), 0.0f);
+}
+
+// --- CSR layout ------------------------------------------------------------
+
+// pos is read with element stride `stride` doubles.
+__global__ void k_csr_count(int n, double L, double w, int nc, const double *pos, int stride,
+                            uint32_t k0, uint32_t k1, uint32_t sweep, int *cell_of, int *count)
+{
+    double sigma[3];
+    schedule_shift(k0, k1, sweep, w, sigma);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *p = pos + (size_t)i * stride;
+    const int cx = cell_coord(p[0], sigma[0], L, w, nc);
+    const int cy = cell_coord(p[1], sigma[1], L, w, nc);
+    const int cz = cell_coord(p[2], sigma[2], L, w, nc);
+    const int c = cx + nc * (cy + nc * cz);
+    cell_of[i] = c;
+    atomicAdd(count + c, 1);
+}
+
+// Single-block exclusive scan of the cell populations into cell_start; the
+// count array is overwritten with the scatter cursors (= cell_start).
+__global__ void __launch_bounds__(1024) k_csr_scan(int ncell, int *count, int *cell_start)
+{
+    __shared__ int s_part[1024];
+    const int tid = threadIdx.x;
+    const int per = (ncell + blockDim.x - 1) / blockDim.x;
+    const int lo = min(tid * per, ncell);
+    const int hi = min(lo + per, ncell);
+    int sum = 0;
+    for (int c = lo; c < hi; ++c) sum += count[c];
+    s_part[tid] = sum;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        const int v = tid >= off ? s_part[tid - off] : 0;
+        __syncthreads();
+        s_part[tid] += v;
+        __syncthreads();
+    }
+    int run = s_part[tid] - sum;
+    for (int c = lo; c < hi; ++c) {
+        const int k = count[c];
+        cell_start[c] = run;
+        count[c] = run;
+        run += k;
+    }
+    if (tid == (int)blockDim.x - 1) cell_start[ncell] = s_part[tid];
+}
+
+__global__ void k_csr_scatter(int n, const int *cell_of, int *cursor, int *cell_idx)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int slot = atomicAdd(cursor + cell_of[i], 1);
+    cell_idx[slot] = i;
+}
+
+// Within each cell, ascending colloid index.
+__global__ void k_csr_sort(int ncell, const int *cell_start, int *cell_idx)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const int lo = cell_start[c], hi = cell_start[c + 1];
+    for (int a = lo + 1; a < hi; ++a) {
+        const int v = cell_idx[a];
+        int b = a - 1;
+        while (b >= lo && cell_idx[b] > v) {
+            cell_idx[b + 1] = cell_idx[b];
+            --b;
+        }
+        cell_idx[b + 1] = v;
+    }
+}
+
+}  // namespace hpmc

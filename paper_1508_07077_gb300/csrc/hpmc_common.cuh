@@ -1,0 +1,277 @@
+// Common device code of the implicit-depletant HPMC library (sm_103a).
+//
+// Method: Glaser, Karas & Glotzer, arXiv:1508.07077.
+//   Sec. III.E  checkerboard of active cells, random grid shift and colour order
+//   Sec. III.B  trial move, Poisson number of depletants, reject on overlap
+//   Sec. III.C  depletants sampled in the circumsphere of the NEW pose; those
+//               overlapping the old configuration are ignored
+//   Sec. III.D  configurational-bias reinsertion, Eq. (12)
+//   App. A      the depletants of one move are processed by cooperating threads
+//
+// Every FP64 expression on a decision path is written in the operation order
+// of the library's specification and compiled with -fmad=false, so decisions
+// and positions are bit-identical to any other faithful implementation.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hpmc {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kMaxCand = 256;        // colloids in a 27-cell neighbourhood (capacity)
+constexpr int kMaxThreads = 256;     // 8 warps per colloid at most
+constexpr int kMaxCellCap = 64;      // colloids per cell bin (capacity)
+constexpr int kCounterSlots = 128;   // counters are spread over slots to avoid hot atomics
+constexpr int kNumCounters = 16;
+
+enum Counter {
+    kMoves = 0, kAccept, kRejCell, kRejOverlap, kRejDep, kRejCb, kDepDrawn,
+    kTranslate, kDepEval, kDepBlocking, kCbFwdOk, kCbRevOk, kCapHits, kRechecks
+};
+
+enum DevError { kErrNone = 0, kErrCandCap = 1, kErrCellCap = 2 };
+
+enum Purpose : uint32_t {
+    kPSched = 0, kPMove = 1, kPRot = 2, kPPoisson = 3, kPDep = 4,
+    kPCbFwd = 5, kPCbRev = 6, kPAccept = 7
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw(uint32_t k0, uint32_t k1, uint32_t sweep,
+                                      uint32_t stream, uint32_t purpose,
+                                      uint32_t sub, uint32_t t)
+{
+    return philox4x32_10(make_uint4(sweep, stream, (purpose << 24) | (sub & 0xFFFFFFu), t),
+                         k0, k1);
+}
+
+// word -> real maps (exact in FP64)
+__device__ __forceinline__ double u01(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
+__device__ __forceinline__ double s11(uint32_t w) { return ((double)w + 0.5) * 0x1p-31 - 1.0; }
+__device__ __forceinline__ double u53(uint32_t a, uint32_t b)
+{
+    return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6)) * 0x1p-53;
+}
+
+// ---------------------------------------------------------------------------
+// Parameters shared by the kernels of one sweep.
+// ---------------------------------------------------------------------------
+struct Sched {
+    double sigma[3];
+    int perm[8];
+    uint32_t sweep;   // sweep index these kernels run
+};
+
+struct SimParams {
+    int n, nc, half_nc, n_stencil, cap;
+    double L, half_L, w;
+    int shape, n_trial, has_dep, nF;
+    double R_s, R_s2;      // sampling sphere radius (R_circ + q/2) and its square
+    double R_dep2;         // sphere-depletant contact distance squared
+    double contact2;       // sphere-sphere contact distance squared
+    double nb_cut2;        // neighbours farther than this cannot meet a depletant
+    double d_max, alpha, p_translate;
+    int move_mode;         // 0 translate only, 1 rotate only, 2 both
+    uint32_t key0, key1;
+    // FP32 form: thresholds rounded to float, and the certified margins
+    float w32, L32, half_L32, R_s32, T_s32, T_dep32, T_contact32, nb_cut2_32, d_max32;
+    float m_r2;            // bound on |r2_fp32 - r2_fp64| (+ threshold rounding), doubled
+    float m_cell;          // bound on the error of a cell-relative coordinate
+    double4 *pos;
+    double4 *quat;
+    float4 *rel;           // FP32 position relative to the origin of its cell (this sweep)
+    int *count[2];         // per-cell populations, double-buffered by sweep parity
+    int *bins;             // [ncell][cap] colloid indices (unordered within a cell)
+    const unsigned long long *T;   // Poisson CDF table as integers ceil(F[k] 2^53)
+    Sched *sched;
+    unsigned long long *sweep;     // next sweep index
+    unsigned long long *counters;
+    int *err;
+};
+
+// Sec. III.E: cell coordinate of x under grid shift sigma.
+__device__ __forceinline__ int cell_coord(double x, double sigma, double L, double w, int nc)
+{
+    double s = x - sigma;
+    if (s < 0.0) s = s + L;
+    int c = (int)(s / w);
+    if (c >= nc) c = nc - 1;
+    if (c < 0) c = 0;
+    return c;
+}
+
+// Offset of x from the origin of its cell c (FP32 working copy only).
+__device__ __forceinline__ float cell_rel(double x, double sigma, double L, double w, int c)
+{
+    double s = x - sigma;
+    if (s < 0.0) s = s + L;
+    return (float)(s - (double)c * w);
+}
+
+__device__ __forceinline__ double min_image(double d, double L, double half_L)
+{
+    if (d > half_L) d = d - L;
+    else if (d < -half_L) d = d + L;
+    return d;
+}
+
+__device__ __forceinline__ double norm2(double a, double b, double c)
+{
+    return (a * a + b * b) + c * c;
+}
+
+__device__ __forceinline__ double wrap_box(double x, double L)
+{
+    if (x < 0.0) x = x + L;
+    if (x >= L) x = x - L;
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// Sweep schedule (Sec. III.E): grid shift and colour order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void schedule_shift(uint32_t k0, uint32_t k1, uint32_t sweep,
+                                               double w, double sigma[3])
+{
+    const uint4 a = draw(k0, k1, sweep, 0xFFFFFFFFu, kPSched, 0, 0);
+    sigma[0] = w * u01(a.x);
+    sigma[1] = w * u01(a.y);
+    sigma[2] = w * u01(a.z);
+}
+
+__device__ __forceinline__ void schedule_perm(uint32_t k0, uint32_t k1, uint32_t sweep,
+                                              int perm[8])
+{
+    const uint4 b = draw(k0, k1, sweep, 0xFFFFFFFFu, kPSched, 1, 0);
+    const uint4 c = draw(k0, k1, sweep, 0xFFFFFFFFu, kPSched, 2, 0);
+    const uint32_t words[8] = {b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+    for (int i = 0; i < 8; ++i) perm[i] = i;
+    for (int i = 7; i >= 1; --i) {
+        const int j = (int)(((unsigned long long)words[7 - i] * (unsigned long long)(i + 1)) >> 32);
+        const int t = perm[i];
+        perm[i] = perm[j];
+        perm[j] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Poisson depletant count (Sec. III.B step 2): N_p = #{k : F[k] <= u} with
+// u = m 2^-53 the 53-bit uniform.  F[k] <= m 2^-53  <=>  m >= ceil(F[k] 2^53),
+// so the table is held as those integers and compared exactly in integer
+// arithmetic.  One warp cooperates (3 levels of 32-way ballots, nF <= 32768).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long u53_int(uint32_t a, uint32_t b)
+{
+    return ((unsigned long long)(a >> 5) << 26) | (unsigned long long)(b >> 6);
+}
+
+__device__ __forceinline__ int poisson_count(const unsigned long long *T, int nF,
+                                             unsigned long long m, int lane)
+{
+    const int i1 = (lane + 1) * 1024 - 1;
+    const bool l1 = i1 < nF && T[i1] <= m;
+    const int b1 = __popc(__ballot_sync(kFull, l1));
+    const int i2 = b1 * 1024 + (lane + 1) * 32 - 1;
+    const bool l2 = i2 < nF && T[i2] <= m;
+    const int b2 = __popc(__ballot_sync(kFull, l2));
+    const int i3 = b1 * 1024 + b2 * 32 + lane;
+    const bool l3 = i3 < nF && T[i3] <= m;
+    const int b3 = __popc(__ballot_sync(kFull, l3));
+    return b1 * 1024 + b2 * 32 + b3;
+}
+
+// ---------------------------------------------------------------------------
+// Per-CTA set-up of a colour phase: which cell this CTA owns, its members in
+// ascending index (the order moves are made in), and the zeroing of the
+// other count buffer for the next sweep.
+// ---------------------------------------------------------------------------
+struct CellTask {
+    int cx, cy, cz, cell, n_own;
+    int *count;        // this sweep's populations
+};
+
+__device__ __forceinline__ CellTask cell_task(const SimParams &P, const Sched &S, int phase)
+{
+    CellTask t;
+    const int colour = P.sched->perm[phase];
+    const int h = P.half_nc, nc = P.nc;
+    const int a = blockIdx.x;
+    t.cx = 2 * (a % h) + (colour & 1);
+    t.cy = 2 * ((a / h) % h) + ((colour >> 1) & 1);
+    t.cz = 2 * (a / (h * h)) + ((colour >> 2) & 1);
+    t.cell = t.cx + nc * (t.cy + nc * t.cz);
+    t.count = P.count[S.sweep & 1u];
+    t.n_own = t.count[t.cell];
+    return t;
+}
+
+// Every cell is owned by exactly one CTA of one phase per sweep: that CTA
+// zeroes the cell in the other buffer, which the next sweep fills.
+__device__ __forceinline__ void clear_next(const SimParams &P, const Sched &S, int cell)
+{
+    if (threadIdx.x == 0) P.count[(S.sweep + 1u) & 1u][cell] = 0;
+}
+
+// Sort the own cell's members into s_own[0..n) ascending (n <= kMaxCellCap).
+__device__ __forceinline__ void own_members_sorted(const SimParams &P, int cell, int n, int *s_tmp,
+                                                   int *s_own)
+{
+    const int tid = threadIdx.x;
+    for (int t = tid; t < n; t += blockDim.x) s_tmp[t] = P.bins[(size_t)cell * P.cap + t];
+    __syncthreads();
+    for (int t = tid; t < n; t += blockDim.x) {
+        const int v = s_tmp[t];
+        int r = 0;
+        for (int u = 0; u < n; ++u) r += s_tmp[u] < v ? 1 : 0;
+        s_own[r] = v;
+    }
+    __syncthreads();
+}
+
+// Neighbour cell (index and geometric offset in cells) number `t` of the
+// deduplicated 27-cell stencil of (cx, cy, cz).
+__device__ __forceinline__ int stencil_cell(const SimParams &P, int t, int cx, int cy, int cz,
+                                            int &dx, int &dy, int &dz)
+{
+    const int ns = P.n_stencil, nc = P.nc;
+    const int ox = t % ns, oy = (t / ns) % ns, oz = t / (ns * ns);
+    int nx, ny, nz;
+    if (nc == 2) {
+        nx = ox; ny = oy; nz = oz;
+        dx = ox - cx; dy = oy - cy; dz = oz - cz;
+    } else {
+        nx = (cx + ox - 1 + nc) % nc;
+        ny = (cy + oy - 1 + nc) % nc;
+        nz = (cz + oz - 1 + nc) % nc;
+        dx = ox - 1; dy = oy - 1; dz = oz - 1;
+    }
+    return nx + nc * (ny + nc * nz);
+}
+
+__device__ __forceinline__ void flush_counters(const SimParams &P, const unsigned long long *c)
+{
+    unsigned long long *cnt = P.counters + (size_t)(blockIdx.x % kCounterSlots) * kNumCounters;
+#pragma unroll
+    for (int k = 0; k < kNumCounters; ++k)
+        if (c[k]) atomicAdd(cnt + k, c[k]);
+}
+
+}  // namespace hpmc

@@ -14,7 +14,11 @@
 #include <cuda_runtime.h>
 
 #include "../../include/hpmc_dep.h"
-#include "hpmc_kernels.cuh"
+#include "hpmc_cells.cuh"
+#include "hpmc_common.cuh"
+#include "hpmc_misc.cuh"
+#include "hpmc_sphere_fp32.cuh"
+#include "hpmc_sphere_fp64.cuh"
 
 using namespace hpmc;
 
@@ -55,7 +59,8 @@ struct hpmc_ctx {
     double4 *d_pos = nullptr, *d_quat = nullptr;
     float4 *d_rel = nullptr;
     double *d_stage = nullptr;  // n x 4 doubles: layout conversion for device callers
-    int *d_cell_start = nullptr, *d_cell_idx = nullptr, *d_count = nullptr, *d_cell_of = nullptr;
+    int *d_count = nullptr;   // 2 x ncell populations (double-buffered by sweep parity)
+    int *d_bins = nullptr;    // ncell x cap colloid indices
     int ncell_alloc = -1;
     Sched *d_sched = nullptr;
     unsigned long long *d_T = nullptr;
@@ -163,8 +168,10 @@ SimParams make_params(hpmc_ctx *c)
     P.key1 = (uint32_t)(c->seed >> 32) ^ c->replica;
     P.pos = c->d_pos;
     P.quat = c->d_quat;
-    P.cell_start = c->d_cell_start;
-    P.cell_idx = c->d_cell_idx;
+    P.cap = kMaxCellCap;
+    P.count[0] = c->d_count;
+    P.count[1] = c->d_count ? c->d_count + (size_t)c->nc * c->nc * c->nc : nullptr;
+    P.bins = c->d_bins;
     P.T = c->d_T;
     P.rel = c->d_rel;
     // FP32 form: thresholds in float and the certified margin.  Every vector a
@@ -199,38 +206,36 @@ SimParams make_params(hpmc_ctx *c)
     return P;
 }
 
-// Enqueue the cell list of the sweep whose index is in *d_sweep.
+// Enqueue the binned cell list (and schedule) of the sweep whose index is in
+// *d_sweep.  Its count buffer was zeroed by the previous sweep's phase kernels
+// (or by check_config).
 int enqueue_cells(hpmc_ctx *c, cudaStream_t s)
 {
-    const int ncell = c->nc * c->nc * c->nc;
-    CK(cudaMemsetAsync(c->d_count, 0, sizeof(int) * (size_t)ncell, s));
-    const int nb = (c->n + 255) / 256;
-    k_cells_count<<<nb, 256, 0, s>>>(c->n, c->L, c->w, c->nc, (const double *)c->d_pos, 4,
-                                     (uint32_t)c->seed, (uint32_t)(c->seed >> 32) ^ c->replica,
-                                     c->d_sweep, 0ull, c->d_cell_of, c->d_count, c->d_sched,
-                                     c->d_rel);
-    k_cells_scan<<<1, 1024, 0, s>>>(ncell, c->d_count, c->d_cell_start);
-    k_cells_scatter<<<nb, 256, 0, s>>>(c->n, c->d_cell_of, c->d_count, c->d_cell_idx);
-    k_cells_sort<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, c->d_cell_start, c->d_cell_idx);
+    SimParams P = make_params(c);
+    k_cells_bin<<<(c->n + 255) / 256, 256, 0, s>>>(P);
     CK(cudaGetLastError());
     return HPMC_OK;
 }
 
+void launch_phase(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
+{
+    const int h = c->nc / 2;
+    const int n_active = h * h * h;
+    const int threads = 32 * c->prm.warps;
+    if (c->precision == HPMC_FP32_RECHECK)
+        k_phase_sphere_fp32<<<n_active, threads, 0, s>>>(P, phase);
+    else
+        k_phase_sphere_fp64<<<n_active, threads, 0, s>>>(P, phase);
+}
+
+// One sweep: binned cell list, then the 8 colour phases (phase 7 advances
+// the sweep counter).
 int enqueue_sweep(hpmc_ctx *c, cudaStream_t s)
 {
     int rc = enqueue_cells(c, s);
     if (rc != HPMC_OK) return rc;
     SimParams P = make_params(c);
-    const int h = c->nc / 2;
-    const int n_active = h * h * h;
-    const int threads = 32 * c->prm.warps;
-    for (int phase = 0; phase < 8; ++phase) {
-        if (c->precision == HPMC_FP32_RECHECK)
-            k_phase_sphere_fp32<<<n_active, threads, 0, s>>>(P, phase);
-        else
-            k_phase_sphere_fp64<<<n_active, threads, 0, s>>>(P, phase);
-    }
-    k_sweep_end<<<1, 1, 0, s>>>(c->d_sweep);
+    for (int phase = 0; phase < 8; ++phase) launch_phase(c, P, phase, s);
     CK(cudaGetLastError());
     return HPMC_OK;
 }
@@ -260,22 +265,15 @@ int enqueue_sweep_timed(hpmc_ctx *c, cudaStream_t s)
     c->tev.push_back(b);
     c->tkind.push_back(0);
     SimParams P = make_params(c);
-    const int h = c->nc / 2;
-    const int n_active = h * h * h;
-    const int threads = 32 * c->prm.warps;
     for (int phase = 0; phase < 8; ++phase) {
         cudaEvent_t x = pool_event(c), y = pool_event(c);
         CK(cudaEventRecord(x, s));
-        if (c->precision == HPMC_FP32_RECHECK)
-            k_phase_sphere_fp32<<<n_active, threads, 0, s>>>(P, phase);
-        else
-            k_phase_sphere_fp64<<<n_active, threads, 0, s>>>(P, phase);
+        launch_phase(c, P, phase, s);
         CK(cudaEventRecord(y, s));
         c->tev.push_back(x);
         c->tev.push_back(y);
         c->tkind.push_back(1);
     }
-    k_sweep_end<<<1, 1, 0, s>>>(c->d_sweep);
     CK(cudaGetLastError());
     return HPMC_OK;
 }
@@ -292,17 +290,24 @@ void free_graph(hpmc_ctx *c)
 // [0, L) and no overlapping colloids.  Synchronous.
 int check_config(hpmc_ctx *c)
 {
+    const size_t cbytes = sizeof(int) * 2 * (size_t)c->nc * c->nc * c->nc;
     CK(cudaStreamSynchronize(c->cap_stream));
+    CK(cudaMemsetAsync(c->d_count, 0, cbytes, c->cap_stream));
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->cap_stream));
     int rc = enqueue_cells(c, c->cap_stream);
     if (rc != HPMC_OK) return rc;
     CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->cap_stream));
     SimParams P = make_params(c);
     k_check_spheres<<<(c->n + 255) / 256, 256, 0, c->cap_stream>>>(P, c->d_flag);
     CK(cudaGetLastError());
-    int flag = 0;
+    int flag = 0, err = 0;
     CK(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->cap_stream));
+    CK(cudaMemcpyAsync(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->cap_stream));
+    // the sweeps start from zeroed populations
+    CK(cudaMemsetAsync(c->d_count, 0, cbytes, c->cap_stream));
     CK(cudaStreamSynchronize(c->cap_stream));
     if (flag & 2) return HPMC_ERR_ARG;
+    if (err == kErrCellCap) return HPMC_ERR_CAP;
     if (flag & 1) return HPMC_ERR_OVERLAP;
     c->state_dirty = false;
     return HPMC_OK;
@@ -331,6 +336,11 @@ int prepare(hpmc_ctx *c)
     const double w = c->L / (double)nc;
     if (w < w_min) return HPMC_ERR_ARG;
     if (!(p.d_max >= 0.0) || p.d_max >= w) return HPMC_ERR_ARG;
+    // a cell bin holds at most (w + 2 R_circ)^3 * 0.7405 / v colloids of volume v
+    // (densest packing); spheres only for now
+    const double v_shape = (kPi / 6.0) * p.sp[0] * p.sp[0] * p.sp[0];
+    const double ext = w + 2.0 * c->R_circ;
+    if (ext * ext * ext * 0.7405 / v_shape >= (double)kMaxCellCap) return HPMC_ERR_CAP;
     c->nc = nc;
     c->w = w;
     if (p.margin > 0.0) {
@@ -355,12 +365,13 @@ int prepare(hpmc_ctx *c)
     DeviceGuard g(c->device);
     const int ncell = nc * nc * nc;
     if (ncell != c->ncell_alloc) {
-        cudaFree(c->d_cell_start);
         cudaFree(c->d_count);
-        c->d_cell_start = nullptr;
+        cudaFree(c->d_bins);
         c->d_count = nullptr;
-        CK(cudaMalloc(&c->d_cell_start, sizeof(int) * (size_t)(ncell + 1)));
-        CK(cudaMalloc(&c->d_count, sizeof(int) * (size_t)ncell));
+        c->d_bins = nullptr;
+        c->ncell_alloc = -1;
+        CK(cudaMalloc(&c->d_count, sizeof(int) * 2 * (size_t)ncell));
+        CK(cudaMalloc(&c->d_bins, sizeof(int) * (size_t)ncell * kMaxCellCap));
         c->ncell_alloc = ncell;
     }
     cudaFree(c->d_T);
@@ -469,8 +480,6 @@ int hpmc_init(hpmc_ctx **out, int n, double box_l, const double *pos, const doub
     CKI(cudaMalloc(&c->d_quat, sizeof(double4) * (size_t)n));
     CKI(cudaMalloc(&c->d_rel, sizeof(float4) * (size_t)n));
     CKI(cudaMalloc(&c->d_stage, sizeof(double) * 4 * (size_t)n));
-    CKI(cudaMalloc(&c->d_cell_idx, sizeof(int) * (size_t)n));
-    CKI(cudaMalloc(&c->d_cell_of, sizeof(int) * (size_t)n));
     CKI(cudaMalloc(&c->d_sched, sizeof(Sched)));
     CKI(cudaMalloc(&c->d_sweep, sizeof(unsigned long long)));
     CKI(cudaMalloc(&c->d_counters, sizeof(unsigned long long) * kCounterSlots * kNumCounters));
@@ -748,16 +757,14 @@ int hpmc_cell_list(int n, double box_l, int n_cell, const double *pos_dev, uint6
     int rc = HPMC_OK;
     e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncell, s);
     if (e == cudaSuccess) {
+        const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32) ^ replica;
         if (n > 0)
-            k_cells_count<<<(n + 255) / 256, 256, 0, s>>>(n, box_l, w, n_cell, pos_dev, 3,
-                                                          (uint32_t)seed,
-                                                          (uint32_t)(seed >> 32) ^ replica,
-                                                          nullptr, sweep, cell_of, count, nullptr,
-                                                          nullptr);
-        k_cells_scan<<<1, 1024, 0, s>>>(ncell, count, cell_start_dev);
+            k_csr_count<<<(n + 255) / 256, 256, 0, s>>>(n, box_l, w, n_cell, pos_dev, 3, k0, k1,
+                                                        (uint32_t)sweep, cell_of, count);
+        k_csr_scan<<<1, 1024, 0, s>>>(ncell, count, cell_start_dev);
         if (n > 0) {
-            k_cells_scatter<<<(n + 255) / 256, 256, 0, s>>>(n, cell_of, count, cell_idx_dev);
-            k_cells_sort<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, cell_start_dev, cell_idx_dev);
+            k_csr_scatter<<<(n + 255) / 256, 256, 0, s>>>(n, cell_of, count, cell_idx_dev);
+            k_csr_sort<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, cell_start_dev, cell_idx_dev);
         }
         e = cudaGetLastError();
     }
@@ -778,10 +785,8 @@ void hpmc_destroy(hpmc_ctx *c)
     cudaFree(c->d_pos);
     cudaFree(c->d_quat);
     cudaFree(c->d_stage);
-    cudaFree(c->d_cell_start);
-    cudaFree(c->d_cell_idx);
     cudaFree(c->d_count);
-    cudaFree(c->d_cell_of);
+    cudaFree(c->d_bins);
     cudaFree(c->d_sched);
     cudaFree(c->d_T);
     cudaFree(c->d_rel);

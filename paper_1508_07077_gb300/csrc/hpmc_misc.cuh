@@ -1,0 +1,72 @@
+// Configuration check and layout conversion kernels.
+#pragma once
+
+#include "hpmc_common.cuh"
+
+namespace hpmc {
+
+// One thread per colloid, over the 27 cells of the binned list of the
+// current sweep index: sets bit 1 of *flag if a coordinate is outside [0, L),
+// bit 0 if two spheres overlap.
+__global__ void k_check_spheres(const __grid_constant__ SimParams P, int *flag)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const double4 pi = P.pos[i];
+    if (!(pi.x >= 0.0 && pi.x < P.L && pi.y >= 0.0 && pi.y < P.L && pi.z >= 0.0 && pi.z < P.L)) {
+        atomicOr(flag, 2);
+        return;
+    }
+    const Sched *S = P.sched;
+    const int *count = P.count[S->sweep & 1u];
+    const int cx = cell_coord(pi.x, S->sigma[0], P.L, P.w, P.nc);
+    const int cy = cell_coord(pi.y, S->sigma[1], P.L, P.w, P.nc);
+    const int cz = cell_coord(pi.z, S->sigma[2], P.L, P.w, P.nc);
+    const int ns = P.n_stencil;
+    for (int t = 0; t < ns * ns * ns; ++t) {
+        int dx, dy, dz;
+        const int c = stencil_cell(P, t, cx, cy, cz, dx, dy, dz);
+        const int m = min(count[c], P.cap);
+        for (int s = 0; s < m; ++s) {
+            const int j = P.bins[(size_t)c * P.cap + s];
+            if (j == i) continue;
+            const double4 pj = P.pos[j];
+            const double r2 = norm2(min_image(pj.x - pi.x, P.L, P.half_L),
+                                    min_image(pj.y - pi.y, P.L, P.half_L),
+                                    min_image(pj.z - pi.z, P.L, P.half_L));
+            if (r2 < P.contact2) atomicOr(flag, 1);
+        }
+    }
+}
+
+// Layout conversion between caller arrays (n x 3, n x 4) and device storage.
+__global__ void k_unpack(int n, const double *pos3, const double *quat4, double4 *pos,
+                         double4 *quat)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (pos3) pos[i] = make_double4(pos3[3 * i], pos3[3 * i + 1], pos3[3 * i + 2], 0.0);
+    if (quat4 && quat)
+        quat[i] = make_double4(quat4[4 * i], quat4[4 * i + 1], quat4[4 * i + 2], quat4[4 * i + 3]);
+}
+
+__global__ void k_pack(int n, const double4 *pos, const double4 *quat, double *pos3, double *quat4)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (pos3) {
+        const double4 p = pos[i];
+        pos3[3 * i] = p.x;
+        pos3[3 * i + 1] = p.y;
+        pos3[3 * i + 2] = p.z;
+    }
+    if (quat4 && quat) {
+        const double4 q = quat[i];
+        quat4[4 * i] = q.x;
+        quat4[4 * i + 1] = q.y;
+        quat4[4 * i + 2] = q.z;
+        quat4[4 * i + 3] = q.w;
+    }
+}
+
+}  // namespace hpmc
