@@ -63,9 +63,14 @@ __device__ __forceinline__ uint4 draw(uint32_t k0, uint32_t k1, uint32_t sweep,
                          k0, k1);
 }
 
-// word -> real maps (exact in FP64)
+// word -> real maps, exact in FP64: u01(w) = (w + 1/2) 2^-32 and
+// s11(w) = (w + 1/2) 2^-31 - 1 = v 2^-31 + 2^-32 with v = w - 2^31 (the fma
+// form: every intermediate is exact, so the value is the specification's).
 __device__ __forceinline__ double u01(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
-__device__ __forceinline__ double s11(uint32_t w) { return ((double)w + 0.5) * 0x1p-31 - 1.0; }
+__device__ __forceinline__ double s11(uint32_t w)
+{
+    return __fma_rn((double)(int)(w ^ 0x80000000u), 0x1p-31, 0x1p-32);
+}
 __device__ __forceinline__ double u53(uint32_t a, uint32_t b)
 {
     return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6)) * 0x1p-53;

@@ -176,15 +176,16 @@ SimParams make_params(hpmc_ctx *c)
     P.rel = c->d_rel;
     // FP32 form: thresholds in float and the certified margin.  Every vector a
     // test forms is a difference of cell-relative coordinates; each component
-    // carries at most E = 21 u max(w, 1) of FP32 error (rounding of the
-    // cell-relative copies, of the displacement, of the depletant coordinate
-    // and of the differences).  For |v| near a threshold radius R the squared
+    // carries at most E = 32 u max(w, 1) of FP32 error (rounding of the
+    // cell-relative copies, including one FP32 step for a colloid already moved
+    // this sweep, of the displacement, of the depletant coordinate and of the
+    // differences).  For |v| near a threshold radius R the squared
     // length then errs by at most 2 sqrt(3) R E + 3 E^2 + 3 u R^2, plus u R^2
     // for rounding the threshold itself; the margin is twice that, and at
     // least 1e-5.
     const double u = 0x1p-24;
     const double Wc = c->w > 1.0 ? c->w : 1.0;
-    const double E = 21.0 * u * Wc;
+    const double E = 32.0 * u * Wc;
     const double Rmax = std::sqrt(std::fmax(P.R_s2, P.contact2));
     const double bound = 2.0 * std::sqrt(3.0) * Rmax * E + 3.0 * E * E + 4.0 * u * Rmax * Rmax + 1e-12;
     P.m_r2 = (float)std::fmax(1e-5, 2.0 * bound);

@@ -33,102 +33,114 @@ __device__ __forceinline__ int tri(float r2, float T, float m)
 }
 
 // --- exact FP64 re-takes, as the specification states them -----------------
+//
+// They run rarely and out of line (behind warp votes), and recompute what
+// they need: the move words are re-drawn and FP64 positions re-read.  Moves
+// accepted by this CTA are committed to FP64 only when the CTA finishes, so a
+// colloid of the list acc[0..nacc) is at its moved position.
+
+// Exact FP64 position of colloid j after its move of this sweep.
+__device__ __forceinline__ double4 moved64(const SimParams &P, uint32_t sweep, int j)
+{
+    const uint4 wm = draw(P.key0, P.key1, sweep, (uint32_t)j, kPMove, 0, 0);
+    const double4 p = P.pos[j];
+    return make_double4(wrap_box(p.x + P.d_max * s11(wm.x), P.L),
+                        wrap_box(p.y + P.d_max * s11(wm.y), P.L),
+                        wrap_box(p.z + P.d_max * s11(wm.z), P.L), 0.0);
+}
+
+__device__ __forceinline__ double4 pos_now(const SimParams &P, uint32_t sweep, int j,
+                                           const int *acc, int nacc)
+{
+    for (int a = 0; a < nacc; ++a)
+        if (acc[a] == j) return moved64(P, sweep, j);
+    return P.pos[j];
+}
 
 struct Move64 {
     double x0, x1, x2;  // new position, wrapped into [0, L)
     double o0, o1, o2;  // old position relative to the new one (minimum image)
 };
 
-__device__ __forceinline__ Move64 move64(const SimParams &P, int i, uint4 wm)
+__device__ __forceinline__ Move64 move64(const SimParams &P, uint32_t sweep, int i)
 {
     const double4 pi = P.pos[i];
+    const double4 x = moved64(P, sweep, i);
     Move64 m;
-    m.x0 = wrap_box(pi.x + P.d_max * s11(wm.x), P.L);
-    m.x1 = wrap_box(pi.y + P.d_max * s11(wm.y), P.L);
-    m.x2 = wrap_box(pi.z + P.d_max * s11(wm.z), P.L);
+    m.x0 = x.x;
+    m.x1 = x.y;
+    m.x2 = x.z;
     m.o0 = min_image(pi.x - m.x0, P.L, P.half_L);
     m.o1 = min_image(pi.y - m.x1, P.L, P.half_L);
     m.o2 = min_image(pi.z - m.x2, P.L, P.half_L);
     return m;
 }
 
-__device__ __forceinline__ bool exact_cell_exit(const SimParams &P, int i, uint4 wm, int cx, int cy,
-                                             int cz)
+__device__ __forceinline__ void center64(const SimParams &P, const Move64 &m, double4 pj,
+                                         double &c0, double &c1, double &c2)
 {
-    const Move64 m = move64(P, i, wm);
+    c0 = min_image(pj.x - m.x0, P.L, P.half_L);
+    c1 = min_image(pj.y - m.x1, P.L, P.half_L);
+    c2 = min_image(pj.z - m.x2, P.L, P.half_L);
+}
+
+__device__ __noinline__ bool exact_cell_exit(const SimParams &P, uint32_t sweep, int i, int cx,
+                                             int cy, int cz)
+{
+    const double4 x = moved64(P, sweep, i);
     const Sched *S = P.sched;
-    return cell_coord(m.x0, S->sigma[0], P.L, P.w, P.nc) != cx ||
-           cell_coord(m.x1, S->sigma[1], P.L, P.w, P.nc) != cy ||
-           cell_coord(m.x2, S->sigma[2], P.L, P.w, P.nc) != cz;
+    return cell_coord(x.x, S->sigma[0], P.L, P.w, P.nc) != cx ||
+           cell_coord(x.y, S->sigma[1], P.L, P.w, P.nc) != cy ||
+           cell_coord(x.z, S->sigma[2], P.L, P.w, P.nc) != cz;
 }
 
 // colloid i at its new position overlaps colloid j
-__device__ __forceinline__ bool exact_pair(const SimParams &P, int i, uint4 wm, int j)
+__device__ __noinline__ bool exact_pair(const SimParams &P, uint32_t sweep, int i, int j,
+                                        const int *acc, int nacc)
 {
-    const Move64 m = move64(P, i, wm);
-    const double4 pj = P.pos[j];
-    return norm2(min_image(pj.x - m.x0, P.L, P.half_L), min_image(pj.y - m.x1, P.L, P.half_L),
-                 min_image(pj.z - m.x2, P.L, P.half_L)) < P.contact2;
+    const Move64 m = move64(P, sweep, i);
+    double c0, c1, c2;
+    center64(P, m, pos_now(P, sweep, j, acc, nacc), c0, c1, c2);
+    return norm2(c0, c1, c2) < P.contact2;
 }
 
-__device__ __forceinline__ bool exact_ball(const SimParams &P, uint4 w)
+__device__ __noinline__ bool exact_ball(const SimParams &P, uint4 w)
 {
     const double e0 = P.R_s * s11(w.x), e1 = P.R_s * s11(w.y), e2 = P.R_s * s11(w.z);
     return norm2(e0, e1, e2) < P.R_s2;
 }
 
-// point e (sampled around the new reference point) vs the old pose
-__device__ __forceinline__ bool exact_dep_old(const SimParams &P, uint4 w, int i, uint4 wm)
+// Exact test of a depletant point against one colloid.
+//   what 0: point e (around the new reference point) vs the old pose
+//   what 1: forward CB trial y = o + e (around the old reference point) vs the new pose
+//   what 2: point e vs neighbour j
+//   what 3: forward CB trial y = o + e vs neighbour j
+__device__ __noinline__ bool exact_dep(const SimParams &P, uint32_t sweep, int i, uint4 w, int what,
+                                       int j, const int *acc, int nacc)
 {
-    const Move64 m = move64(P, i, wm);
+    const Move64 m = move64(P, sweep, i);
     const double e0 = P.R_s * s11(w.x), e1 = P.R_s * s11(w.y), e2 = P.R_s * s11(w.z);
-    return SphereFP64::dep(P, e0 - m.o0, e1 - m.o1, e2 - m.o2);
-}
-
-// forward CB trial y = o + e (sampled around the old reference point) vs the new pose
-__device__ __forceinline__ bool exact_fwd_new(const SimParams &P, uint4 w, int i, uint4 wm)
-{
-    const Move64 m = move64(P, i, wm);
-    const double e0 = P.R_s * s11(w.x), e1 = P.R_s * s11(w.y), e2 = P.R_s * s11(w.z);
-    const double y0 = m.o0 + e0, y1 = m.o1 + e1, y2 = m.o2 + e2;
-    return SphereFP64::dep(P, y0, y1, y2);
-}
-
-// kind 0: point e vs neighbour j; kind 1: forward trial y = o + e vs neighbour j
-__device__ __forceinline__ bool exact_dep_nb(const SimParams &P, uint4 w, int kind, int i, uint4 wm,
-                                          int j)
-{
-    const Move64 m = move64(P, i, wm);
-    const double4 pj = P.pos[j];
-    const double d0 = min_image(pj.x - m.x0, P.L, P.half_L);
-    const double d1 = min_image(pj.y - m.x1, P.L, P.half_L);
-    const double d2 = min_image(pj.z - m.x2, P.L, P.half_L);
-    const double e0 = P.R_s * s11(w.x), e1 = P.R_s * s11(w.y), e2 = P.R_s * s11(w.z);
-    if (kind == 0) return SphereFP64::dep(P, e0 - d0, e1 - d1, e2 - d2);
-    const double y0 = m.o0 + e0, y1 = m.o1 + e1, y2 = m.o2 + e2;
-    return SphereFP64::dep(P, y0 - d0, y1 - d1, y2 - d2);
-}
-
-// a8: commit the accepted move in FP64; returns the new FP32 cell offset (index in .w)
-__device__ __forceinline__ float4 commit_move(const SimParams &P, int i, uint4 wm, int cx, int cy,
-                                           int cz)
-{
-    const Move64 m = move64(P, i, wm);
-    const Sched *S = P.sched;
-    P.pos[i] = make_double4(m.x0, m.x1, m.x2, 0.0);
-    const float4 r = make_float4(cell_rel(m.x0, S->sigma[0], P.L, P.w, cx),
-                                 cell_rel(m.x1, S->sigma[1], P.L, P.w, cy),
-                                 cell_rel(m.x2, S->sigma[2], P.L, P.w, cz), __int_as_float(i));
-    P.rel[i] = make_float4(r.x, r.y, r.z, 0.0f);
-    return r;
+    double v0 = e0, v1 = e1, v2 = e2;
+    if (what == 1 || what == 3) {
+        v0 = m.o0 + e0;
+        v1 = m.o1 + e1;
+        v2 = m.o2 + e2;
+    }
+    if (what == 0) return SphereFP64::dep(P, v0 - m.o0, v1 - m.o1, v2 - m.o2);
+    if (what == 1) return SphereFP64::dep(P, v0, v1, v2);
+    double c0, c1, c2;
+    center64(P, m, pos_now(P, sweep, j, acc, nacc), c0, c1, c2);
+    return SphereFP64::dep(P, v0 - c0, v1 - c1, v2 - c2);
 }
 
 // --- FP32 tests with exact fallback -----------------------------------------
 
 // Is v (FP32, relative to the new reference point) free of every neighbour?
+// kind 2: v is a point e; kind 3: v is a forward trial o + e.
 __device__ __forceinline__ bool free_nb32(const SimParams &P, float v0, float v1, float v2,
-                                          const float4 *nb, int nnb, uint4 w, int kind, int i,
-                                          uint4 wm, uint32_t &rck)
+                                          const float4 *nb, int nnb, uint32_t sweep, int i,
+                                          uint4 w, int kind, const int *acc, int nacc,
+                                          uint32_t &rck)
 {
     for (int a = 0; a < nnb; ++a) {
         const float4 d = nb[a];
@@ -136,7 +148,7 @@ __device__ __forceinline__ bool free_nb32(const SimParams &P, float v0, float v1
         if (t == 1) return false;
         if (t == -1) {
             ++rck;
-            if (exact_dep_nb(P, w, kind, i, wm, __float_as_int(d.w))) return false;
+            if (exact_dep(P, sweep, i, w, kind, __float_as_int(d.w), acc, nacc)) return false;
         }
     }
     return true;
@@ -171,12 +183,13 @@ struct CbResult32 {
 
 // CB factor of one blocking depletant (Sec. III.D, Eq. 12), FP32 form.  For
 // spheres "overlaps the pose the ball is centred on" is the ball test itself.
-__device__ __forceinline__ CbResult32 cb_factor_fp32(const SimParams &P, uint32_t sweep, uint32_t tag,
-                                                  uint32_t k, float o0, float o1, float o2, int i,
-                                                  uint4 wm, const float4 *nb, int nnb, float r_hi,
-                                                  float r_lo)
+__device__ __noinline__ CbResult32 cb_factor_fp32(const SimParams &P, uint32_t sweep, int i,
+                                                  uint32_t k, float o0, float o1, float o2,
+                                                  const float4 *nb, int nnb, const int *acc,
+                                                  int nacc, float r_hi, float r_lo)
 {
     CbResult32 r = {0.0, 0u, 0u, 0u, 0u};
+    const uint32_t tag = (uint32_t)i;
     const int n_fwd = P.n_trial, n_rev = P.n_trial - 1;
     int nf = 0, nr = 0, found = 0;
     uint32_t t = 0;
@@ -189,10 +202,10 @@ __device__ __forceinline__ CbResult32 cb_factor_fp32(const SimParams &P, uint32_
         int tn = tri(norm2f(y0, y1, y2), P.T_dep32, P.m_r2);  // overlaps the new pose?
         if (tn == -1) {
             ++r.rck;
-            tn = exact_fwd_new(P, w, i, wm) ? 1 : 0;
+            tn = exact_dep(P, sweep, i, w, 1, 0, acc, nacc) ? 1 : 0;
         }
         if (tn) continue;
-        if (!free_nb32(P, y0, y1, y2, nb, nnb, w, 1, i, wm, r.rck)) continue;
+        if (!free_nb32(P, y0, y1, y2, nb, nnb, sweep, i, w, 3, acc, nacc, r.rck)) continue;
         ++nf;
     }
     if (found < n_fwd) ++r.caps;
@@ -204,10 +217,10 @@ __device__ __forceinline__ CbResult32 cb_factor_fp32(const SimParams &P, uint32_
         int to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), P.T_dep32, P.m_r2);  // old pose?
         if (to == -1) {
             ++r.rck;
-            to = exact_dep_old(P, w, i, wm) ? 1 : 0;
+            to = exact_dep(P, sweep, i, w, 0, 0, acc, nacc) ? 1 : 0;
         }
         if (to) continue;
-        if (!free_nb32(P, e0, e1, e2, nb, nnb, w, 0, i, wm, r.rck)) continue;
+        if (!free_nb32(P, e0, e1, e2, nb, nnb, sweep, i, w, 2, acc, nacc, r.rck)) continue;
         ++nr;
     }
     if (found < n_rev) ++r.caps;
@@ -217,16 +230,28 @@ __device__ __forceinline__ CbResult32 cb_factor_fp32(const SimParams &P, uint32_
     return r;
 }
 
-__global__ void __launch_bounds__(kMaxThreads, 3)
+// Classify one depletant point e (FP32 first, exact where needed): blocking
+// iff it is not in the old pose's excluded volume nor any neighbour's (it is in
+// the new pose's, being inside the ball).  Returns 1 blocking, 0 not.
+__device__ __noinline__ int exact_classify(const SimParams &P, uint32_t sweep, int i, uint4 w,
+                                           const float4 *nb, int nnb, const int *acc, int nacc)
+{
+    if (exact_dep(P, sweep, i, w, 0, 0, acc, nacc)) return 0;
+    for (int a = 0; a < nnb; ++a)
+        if (exact_dep(P, sweep, i, w, 2, __float_as_int(nb[a].w), acc, nacc)) return 0;
+    return 1;
+}
+
+__global__ void __launch_bounds__(kMaxThreads, 2)
     k_phase_sphere_fp32(const __grid_constant__ SimParams P, int phase)
 {
-    __shared__ int s_own[kMaxCellCap], s_tmp[kMaxCellCap];
+    __shared__ int s_own[kMaxCellCap], s_tmp[kMaxCellCap], s_accl[kMaxCellCap];
     __shared__ float4 s_cpos[kMaxCand];  // candidates relative to this cell's origin; index in .w
     __shared__ float4 s_nb[kMaxCand];    // neighbours relative to the new position; index in .w
     __shared__ double s_f[kMaxThreads];
     __shared__ int s_k[kMaxThreads];
     __shared__ int s_warp[kMaxThreads / 32];
-    __shared__ int s_ncand, s_nnb, s_flag, s_acc, s_kmin, s_self;
+    __shared__ int s_ncand, s_nnb, s_flag, s_acc, s_kmin, s_self, s_nacc;
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
@@ -241,7 +266,10 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
     const int cx = T.cx, cy = T.cy, cz = T.cz;
 
     // candidates of the 27-cell stencil, relative to this cell's origin
-    if (tid == 0) s_ncand = 0;
+    if (tid == 0) {
+        s_ncand = 0;
+        s_nacc = 0;
+    }
     __syncthreads();
     if (tid < P.n_stencil * P.n_stencil * P.n_stencil) {
         int dx, dy, dz;
@@ -273,14 +301,17 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
     for (int q = 0; q < n_own; ++q) {
         const int i = s_own[q];
         const uint32_t tag = (uint32_t)i;
+        const int nacc = s_nacc;
         ++c_moves;
-        const uint4 wm = draw(P.key0, P.key1, sweep, tag, kPMove, 0, 0);
+        float rn0, rn1, rn2;
         const float4 ri = P.rel[i];
-
-        // a3: proposal in cell-relative FP32; cell-exit check with margin
-        const float rn0 = ri.x + scaled_s11f(wm.x, dm_hi, dm_lo);
-        const float rn1 = ri.y + scaled_s11f(wm.y, dm_hi, dm_lo);
-        const float rn2 = ri.z + scaled_s11f(wm.z, dm_hi, dm_lo);
+        {
+            const uint4 wm = draw(P.key0, P.key1, sweep, tag, kPMove, 0, 0);
+            rn0 = ri.x + scaled_s11f(wm.x, dm_hi, dm_lo);
+            rn1 = ri.y + scaled_s11f(wm.y, dm_hi, dm_lo);
+            rn2 = ri.z + scaled_s11f(wm.z, dm_hi, dm_lo);
+        }
+        // a3: cell-exit check with margin (exact when within it)
         const float mc = P.m_cell, wc = P.w32;
         const bool out = rn0 < -mc || rn0 > wc + mc || rn1 < -mc || rn1 > wc + mc ||
                          rn2 < -mc || rn2 > wc + mc;
@@ -288,7 +319,7 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
                           rn2 <= mc || rn2 >= wc - mc;
         bool exits = out;
         if (!out && edge) {
-            exits = exact_cell_exit(P, i, wm, cx, cy, cz);
+            exits = exact_cell_exit(P, sweep, i, cx, cy, cz);
             if (tid == 0) ++c_rck;
         }
         if (exits) {
@@ -304,27 +335,38 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
         }
         __syncthreads();
         int ov = 0;
-        for (int j = tid; j < M; j += nthr) {
-            const float4 cp = s_cpos[j];
-            const int pj = __float_as_int(cp.w);
-            if (pj == i) {
-                s_self = j;
-                continue;
+        for (int j0 = 0; j0 < M; j0 += nthr) {
+            const int j = j0 + tid;
+            int t = 0, pj = -1;
+            float d0 = 0.f, d1 = 0.f, d2 = 0.f, r2 = 1e30f;
+            if (j < M) {
+                const float4 cp = s_cpos[j];
+                pj = __float_as_int(cp.w);
+                if (pj == i) {
+                    s_self = j;
+                    pj = -1;
+                } else {
+                    d0 = cp.x - rn0;
+                    d1 = cp.y - rn1;
+                    d2 = cp.z - rn2;
+                    if (d0 > P.half_L32) d0 -= P.L32; else if (d0 < -P.half_L32) d0 += P.L32;
+                    if (d1 > P.half_L32) d1 -= P.L32; else if (d1 < -P.half_L32) d1 += P.L32;
+                    if (d2 > P.half_L32) d2 -= P.L32; else if (d2 < -P.half_L32) d2 += P.L32;
+                    r2 = norm2f(d0, d1, d2);
+                    t = tri(r2, P.T_contact32, P.m_r2);
+                }
             }
-            float d0 = cp.x - rn0, d1 = cp.y - rn1, d2 = cp.z - rn2;
-            if (d0 > P.half_L32) d0 -= P.L32; else if (d0 < -P.half_L32) d0 += P.L32;
-            if (d1 > P.half_L32) d1 -= P.L32; else if (d1 < -P.half_L32) d1 += P.L32;
-            if (d2 > P.half_L32) d2 -= P.L32; else if (d2 < -P.half_L32) d2 += P.L32;
-            const float r2 = norm2f(d0, d1, d2);
-            int t = tri(r2, P.T_contact32, P.m_r2);
-            if (t == -1) {
-                ++c_rck;
-                t = exact_pair(P, i, wm, pj) ? 1 : 0;
+            const bool unsure = t == -1;
+            if (__any_sync(kFull, unsure)) {
+                if (unsure) {
+                    ++c_rck;
+                    t = exact_pair(P, sweep, i, pj, s_accl, nacc) ? 1 : 0;
+                }
             }
             if (t == 1) ov = 1;
-            if (r2 < P.nb_cut2_32) {
+            if (pj >= 0 && r2 < P.nb_cut2_32) {
                 const int slot = atomicAdd(&s_nnb, 1);
-                s_nb[slot] = make_float4(d0, d1, d2, cp.w);
+                s_nb[slot] = make_float4(d0, d1, d2, __int_as_float(pj));
             }
         }
         if (__syncthreads_or(ov)) {
@@ -350,19 +392,24 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
                 const uint32_t t = t0 + (uint32_t)tid;
                 uint4 w = make_uint4(0, 0, 0, 0);
                 float e0 = 0.f, e1 = 0.f, e2 = 0.f;
-                bool inside = false;
+                int in = 0;
                 if (t < t_max) {
                     w = draw(P.key0, P.key1, sweep, tag, kPDep, 0, t);
                     e0 = scaled_s11f(w.x, r_hi, r_lo);
                     e1 = scaled_s11f(w.y, r_hi, r_lo);
                     e2 = scaled_s11f(w.z, r_hi, r_lo);
-                    int in = tri(norm2f(e0, e1, e2), P.T_s32, P.m_r2);
-                    if (in == -1) {
-                        ++c_rck;
-                        in = exact_ball(P, w) ? 1 : 0;
-                    }
-                    inside = in != 0;
+                    in = tri(norm2f(e0, e1, e2), P.T_s32, P.m_r2);
                 }
+                {
+                    const bool unsure = in == -1;
+                    if (__any_sync(kFull, unsure)) {
+                        if (unsure) {
+                            ++c_rck;
+                            in = exact_ball(P, w) ? 1 : 0;
+                        }
+                    }
+                }
+                const bool inside = in == 1;
                 const unsigned bal = __ballot_sync(kFull, inside);
                 int base = 0, total = __popc(bal);
                 if (nwarps > 1) {
@@ -376,17 +423,36 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
                     }
                 }
                 const int k = k0 + base + __popc(bal & ((1u << lane) - 1u));
-                bool blocking = false;
+                // inside the ball = overlaps the new pose (spheres).  Blocking iff it
+                // overlaps neither the old pose nor a neighbour: 1 yes, 0 no, -1 unsure
+                int cls = 0;
                 if (inside && k < n_p) {
-                    // inside the ball = overlaps the new pose (spheres); ignored if it
-                    // overlaps the old configuration
-                    int to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), P.T_dep32, P.m_r2);
-                    if (to == -1) {
-                        ++c_rck;
-                        to = exact_dep_old(P, w, i, wm) ? 1 : 0;
+                    const int to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), P.T_dep32, P.m_r2);
+                    if (to != 1) {
+                        bool unsure = to == -1, hit = false;
+                        for (int a = 0; a < nnb; ++a) {
+                            const float4 d = s_nb[a];
+                            const int tn = tri(norm2f(e0 - d.x, e1 - d.y, e2 - d.z), P.T_dep32,
+                                               P.m_r2);
+                            if (tn == 1) {
+                                hit = true;
+                                break;
+                            }
+                            unsure = unsure || tn == -1;
+                        }
+                        cls = hit ? 0 : (unsure ? -1 : 1);
                     }
-                    if (!to) blocking = free_nb32(P, e0, e1, e2, s_nb, nnb, w, 0, i, wm, c_rck);
                 }
+                {
+                    const bool unsure = cls == -1;
+                    if (__any_sync(kFull, unsure)) {
+                        if (unsure) {
+                            ++c_rck;
+                            cls = exact_classify(P, sweep, i, w, s_nb, nnb, s_accl, nacc);
+                        }
+                    }
+                }
+                const bool blocking = cls == 1;
                 if (P.n_trial == 0) {
                     if (blocking) atomicMin(&s_kmin, k);
                     if (__syncthreads_or(blocking)) {
@@ -399,8 +465,8 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
                 } else {
                     double f = -1.0;
                     if (blocking) {
-                        const CbResult32 r = cb_factor_fp32(P, sweep, tag, (uint32_t)k, o0, o1, o2,
-                                                            i, wm, s_nb, nnb, r_hi, r_lo);
+                        const CbResult32 r = cb_factor_fp32(P, sweep, i, (uint32_t)k, o0, o1, o2,
+                                                            s_nb, nnb, s_accl, nacc, r_hi, r_lo);
                         f = r.f;
                         c_fwd += r.fwd_ok;
                         c_rev += r.rev_ok;
@@ -454,12 +520,26 @@ __global__ void __launch_bounds__(kMaxThreads, 3)
                 accept = s_acc != 0;
             }
         }
-        // a8: commit in FP64; refresh the FP32 working copies
+        // a8: accepted: the FP32 working copies move now, the FP64 position
+        // when this CTA finishes
         if (accept) {
             ++c_acc;
-            if (tid == 0) s_cpos[s_self] = commit_move(P, i, wm, cx, cy, cz);
+            if (tid == 0) {
+                const float4 rnew = make_float4(rn0, rn1, rn2, __int_as_float(i));
+                s_cpos[s_self] = rnew;
+                P.rel[i] = make_float4(rn0, rn1, rn2, 0.0f);
+                s_accl[s_nacc] = i;
+                s_nacc = nacc + 1;
+            }
         }
         __syncthreads();
+    }
+
+    // deferred FP64 commit of the accepted moves, one colloid per lane
+    const int nacc = s_nacc;
+    for (int a = tid; a < nacc; a += nthr) {
+        const int j = s_accl[a];
+        P.pos[j] = moved64(P, sweep, j);
     }
 
     unsigned long long cnt[kNumCounters] = {0};
