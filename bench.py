@@ -212,16 +212,33 @@ def run_ours(args, ws, rank, local):
     for s in systems:
         eta = round(s.extra["eta_r"], 1)
         smp = hpmc.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=D_MAX_TUNED[eta], seed=1,
-                           replica=rank, precision=prec, warps=args.warps, device=local)
+                           replica=rank, precision=prec, warps=args.warps, ilp=args.ilp,
+                           device=local)
         dmax[eta] = tune(smp, hpmc, D_MAX_TUNED[eta]) if not args.no_tune else D_MAX_TUNED[eta]
         smps.append(smp)
     torch.cuda.synchronize()
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    # the four state points are independent systems: each runs on its own
+    # stream, forked from and joined back into the timing stream
+    side = [torch.cuda.Stream() for _ in smps]
+    fork = torch.cuda.Event()
+    joins = [torch.cuda.Event() for _ in smps]
 
-    def step():
+    def step_concurrent():
+        fork.record(stream)
+        for smp, st, ev in zip(smps, side, joins):
+            st.wait_event(fork)
+            smp.sweep(1, st)
+            ev.record(st)
+        for ev in joins:
+            stream.wait_event(ev)
+
+    def step_sequential():
         for smp in smps:
             smp.sweep(1, stream)
+
+    step = step_sequential if args.sequential else step_concurrent
 
     for _ in range(args.warmup):
         step()
@@ -245,6 +262,17 @@ def run_ours(args, ws, rank, local):
         dist.barrier()
     ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     counters = [hpmc.hpmc_get_state(smp.ctx)[1] for smp in smps]
+    # the same systems one at a time (context for the concurrent number)
+    seq_steps = min(args.steps, 50)
+    sa = [torch.cuda.Event(enable_timing=True) for _ in range(seq_steps)]
+    sb = [torch.cuda.Event(enable_timing=True) for _ in range(seq_steps)]
+    for k in range(seq_steps):
+        flush.zero_()
+        sa[k].record(stream)
+        step_sequential()
+        sb[k].record(stream)
+    torch.cuda.synchronize()
+    seq_ms = sum(a.elapsed_time(b) for a, b in zip(sa, sb))
     moves = sum(c["moves"] for c in counters)
     drawn = sum(c["dep_drawn"] for c in counters)
     evaluated = sum(c["dep_evaluated"] for c in counters)
@@ -258,7 +286,7 @@ def run_ours(args, ws, rank, local):
     timing_steps = min(args.steps, 50)
     for k in range(timing_steps):
         flush.zero_()
-        step()
+        step_sequential()
     kern_ms = [0.0, 0.0]
     kern_n = [0, 0]
     for smp in smps:
@@ -310,9 +338,12 @@ def run_ours(args, ws, rank, local):
             "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "form": "FP32+FP64 recheck" if prec == 1 else "FP64",
                        "n_trial": 0, "step": "1 sweep of each of 4 systems (65536 moves)",
+                       "schedule": "4 systems one at a time" if args.sequential
+                                   else "4 systems concurrently (one stream each)",
                        "d_max": {str(k): round(v, 5) for k, v in dmax.items()},
                        "l2": "flushed between steps (256 MB write)",
-                       "warps_per_colloid": args.warps},
+                       "warps_per_colloid": args.warps, "attempts_per_thread": args.ilp},
+            "one_at_a_time_moves_per_s": ws * seq_steps * len(smps) * N / (seq_ms * 1e-3),
             "insertions_drawn_per_s": ws * drawn / (ms * 1e-3),
             "insertions_evaluated_per_s": ws * evaluated / (ms * 1e-3),
             "acceptance": accept / max(1, moves),
@@ -356,7 +387,10 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
     ap.add_argument("--warps", type=int, default=1)
+    ap.add_argument("--ilp", type=int, default=2)
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--sequential", action="store_true",
+                    help="sweep the four systems one after another on one stream")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sweeps", type=int, default=25)
     args = ap.parse_args()

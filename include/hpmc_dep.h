@@ -113,9 +113,11 @@ int hpmc_set_moves(hpmc_ctx *ctx, double d_max, double a_max, double p_translate
  * largest valid count.  Part of the trajectory's definition (Sec. III.E). */
 int hpmc_set_cells(hpmc_ctx *ctx, int n_cell);
 
-/* Launch shape: warps cooperating on one moved colloid's depletants (1..8).
- * A performance knob only: results are identical for every value. */
-int hpmc_set_launch(hpmc_ctx *ctx, int warps_per_colloid);
+/* Launch shape: warps cooperating on one moved colloid's depletants (1..8,
+ * default 1) and depletant attempts each thread carries per pass (1 or 2,
+ * default 2; FP32 form).  Performance knobs only: results are identical for
+ * every value. */
+int hpmc_set_launch(hpmc_ctx *ctx, int warps_per_colloid, int attempts_per_thread);
 
 /* FP32 form only: margin on squared distances inside which an FP32 decision
  * is re-taken in FP64.  0 selects the derived certified bound (default);

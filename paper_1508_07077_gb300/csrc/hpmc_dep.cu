@@ -35,7 +35,8 @@ struct Params {
     int n_trial = 0;
     double d_max = 0.1, a_max = 0.0, p_translate = 1.0;
     int nc_req = 0;
-    int warps = 2;
+    int warps = 1;
+    int ilp = 2;
     double margin = 0.0;
 };
 
@@ -223,9 +224,10 @@ void launch_phase(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
     const int h = c->nc / 2;
     const int n_active = h * h * h;
     const int threads = 32 * c->prm.warps;
-    if (c->precision == HPMC_FP32_RECHECK)
-        k_phase_sphere_fp32<<<n_active, threads, 0, s>>>(P, phase);
-    else
+    if (c->precision == HPMC_FP32_RECHECK) {
+        if (c->prm.ilp == 2) k_phase_sphere_fp32<2><<<n_active, threads, 0, s>>>(P, phase);
+        else k_phase_sphere_fp32<1><<<n_active, threads, 0, s>>>(P, phase);
+    } else
         k_phase_sphere_fp64<<<n_active, threads, 0, s>>>(P, phase);
 }
 
@@ -565,10 +567,12 @@ int hpmc_set_cells(hpmc_ctx *c, int n_cell)
     return HPMC_OK;
 }
 
-int hpmc_set_launch(hpmc_ctx *c, int warps_per_colloid)
+int hpmc_set_launch(hpmc_ctx *c, int warps_per_colloid, int attempts_per_thread)
 {
     if (!c || warps_per_colloid < 1 || warps_per_colloid > kMaxThreads / 32) return HPMC_ERR_ARG;
+    if (attempts_per_thread < 1 || attempts_per_thread > 2) return HPMC_ERR_ARG;
     c->prm.warps = warps_per_colloid;
+    c->prm.ilp = attempts_per_thread;
     c->dirty = true;
     return HPMC_OK;
 }

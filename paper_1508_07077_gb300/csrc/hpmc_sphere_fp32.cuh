@@ -242,15 +242,18 @@ __device__ __noinline__ int exact_classify(const SimParams &P, uint32_t sweep, i
     return 1;
 }
 
+// ILP: attempts each thread carries per pass (independent Philox chains);
+// the pass covers ILP * blockDim attempts of the stream, in order.
+template <int ILP>
 __global__ void __launch_bounds__(kMaxThreads, 2)
     k_phase_sphere_fp32(const __grid_constant__ SimParams P, int phase)
 {
     __shared__ int s_own[kMaxCellCap], s_tmp[kMaxCellCap], s_accl[kMaxCellCap];
     __shared__ float4 s_cpos[kMaxCand];  // candidates relative to this cell's origin; index in .w
     __shared__ float4 s_nb[kMaxCand];    // neighbours relative to the new position; index in .w
-    __shared__ double s_f[kMaxThreads];
-    __shared__ int s_k[kMaxThreads];
-    __shared__ int s_warp[kMaxThreads / 32];
+    __shared__ double s_f[ILP * kMaxThreads];
+    __shared__ int s_k[ILP * kMaxThreads];
+    __shared__ int s_warp[ILP][kMaxThreads / 32];
     __shared__ int s_ncand, s_nnb, s_flag, s_acc, s_kmin, s_self, s_nacc;
 
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -382,80 +385,115 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
             const int n_p = poisson_count(P.T, P.nF, u53_int(wp.x, wp.y), lane);
             c_drawn += (unsigned long long)n_p;
 
-            // a6: attempt stream, nthr attempts per pass
+            // a6: attempt stream, ILP * nthr attempts per pass
             const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
+            const uint32_t per_pass = (uint32_t)(ILP * nthr);
             uint32_t t0 = 0;
             int k0 = 0, nblock = 0;
             double W = 1.0;
             bool rejected = false;
             while (k0 < n_p && t0 < t_max) {
-                const uint32_t t = t0 + (uint32_t)tid;
-                uint4 w = make_uint4(0, 0, 0, 0);
-                float e0 = 0.f, e1 = 0.f, e2 = 0.f;
-                int in = 0;
-                if (t < t_max) {
-                    w = draw(P.key0, P.key1, sweep, tag, kPDep, 0, t);
-                    e0 = scaled_s11f(w.x, r_hi, r_lo);
-                    e1 = scaled_s11f(w.y, r_hi, r_lo);
-                    e2 = scaled_s11f(w.z, r_hi, r_lo);
-                    in = tri(norm2f(e0, e1, e2), P.T_s32, P.m_r2);
+                uint4 w[ILP];
+                float e0[ILP], e1[ILP], e2[ILP];
+                int in[ILP];
+#pragma unroll
+                for (int a = 0; a < ILP; ++a) {
+                    const uint32_t t = t0 + (uint32_t)(a * nthr + tid);
+                    w[a] = make_uint4(0, 0, 0, 0);
+                    e0[a] = e1[a] = e2[a] = 0.f;
+                    in[a] = 0;
+                    if (t < t_max) {
+                        w[a] = draw(P.key0, P.key1, sweep, tag, kPDep, 0, t);
+                        e0[a] = scaled_s11f(w[a].x, r_hi, r_lo);
+                        e1[a] = scaled_s11f(w[a].y, r_hi, r_lo);
+                        e2[a] = scaled_s11f(w[a].z, r_hi, r_lo);
+                        in[a] = tri(norm2f(e0[a], e1[a], e2[a]), P.T_s32, P.m_r2);
+                    }
                 }
-                {
-                    const bool unsure = in == -1;
+#pragma unroll
+                for (int a = 0; a < ILP; ++a) {
+                    const bool unsure = in[a] == -1;
                     if (__any_sync(kFull, unsure)) {
                         if (unsure) {
                             ++c_rck;
-                            in = exact_ball(P, w) ? 1 : 0;
+                            in[a] = exact_ball(P, w[a]) ? 1 : 0;
                         }
                     }
                 }
-                const bool inside = in == 1;
-                const unsigned bal = __ballot_sync(kFull, inside);
-                int base = 0, total = __popc(bal);
+                // depletant index of each inside attempt: prefix over the pass
+                int k[ILP], total = 0;
+                unsigned bal[ILP];
+#pragma unroll
+                for (int a = 0; a < ILP; ++a) bal[a] = __ballot_sync(kFull, in[a] == 1);
                 if (nwarps > 1) {
-                    if (lane == 0) s_warp[warp] = total;
+                    if (lane == 0) {
+#pragma unroll
+                        for (int a = 0; a < ILP; ++a) s_warp[a][warp] = __popc(bal[a]);
+                    }
                     __syncthreads();
-                    total = 0;
-                    for (int u = 0; u < nwarps; ++u) {
-                        const int c = s_warp[u];
-                        base += u < warp ? c : 0;
-                        total += c;
+#pragma unroll
+                    for (int a = 0; a < ILP; ++a) {
+                        int base = 0, tot = 0;
+                        for (int u = 0; u < nwarps; ++u) {
+                            const int c = s_warp[a][u];
+                            base += u < warp ? c : 0;
+                            tot += c;
+                        }
+                        k[a] = k0 + total + base + __popc(bal[a] & ((1u << lane) - 1u));
+                        total += tot;
+                    }
+                } else {
+#pragma unroll
+                    for (int a = 0; a < ILP; ++a) {
+                        k[a] = k0 + total + __popc(bal[a] & ((1u << lane) - 1u));
+                        total += __popc(bal[a]);
                     }
                 }
-                const int k = k0 + base + __popc(bal & ((1u << lane) - 1u));
                 // inside the ball = overlaps the new pose (spheres).  Blocking iff it
                 // overlaps neither the old pose nor a neighbour: 1 yes, 0 no, -1 unsure
-                int cls = 0;
-                if (inside && k < n_p) {
-                    const int to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), P.T_dep32, P.m_r2);
-                    if (to != 1) {
-                        bool unsure = to == -1, hit = false;
-                        for (int a = 0; a < nnb; ++a) {
-                            const float4 d = s_nb[a];
-                            const int tn = tri(norm2f(e0 - d.x, e1 - d.y, e2 - d.z), P.T_dep32,
-                                               P.m_r2);
-                            if (tn == 1) {
-                                hit = true;
-                                break;
+                int cls[ILP];
+#pragma unroll
+                for (int a = 0; a < ILP; ++a) {
+                    cls[a] = 0;
+                    if (in[a] == 1 && k[a] < n_p) {
+                        const int to = tri(norm2f(e0[a] - o0, e1[a] - o1, e2[a] - o2), P.T_dep32,
+                                           P.m_r2);
+                        if (to != 1) {
+                            bool unsure = to == -1, hit = false;
+                            for (int b = 0; b < nnb; ++b) {
+                                const float4 d = s_nb[b];
+                                const int tn = tri(norm2f(e0[a] - d.x, e1[a] - d.y, e2[a] - d.z),
+                                                   P.T_dep32, P.m_r2);
+                                if (tn == 1) {
+                                    hit = true;
+                                    break;
+                                }
+                                unsure = unsure || tn == -1;
                             }
-                            unsure = unsure || tn == -1;
+                            cls[a] = hit ? 0 : (unsure ? -1 : 1);
                         }
-                        cls = hit ? 0 : (unsure ? -1 : 1);
                     }
                 }
-                {
-                    const bool unsure = cls == -1;
+#pragma unroll
+                for (int a = 0; a < ILP; ++a) {
+                    const bool unsure = cls[a] == -1;
                     if (__any_sync(kFull, unsure)) {
                         if (unsure) {
                             ++c_rck;
-                            cls = exact_classify(P, sweep, i, w, s_nb, nnb, s_accl, nacc);
+                            cls[a] = exact_classify(P, sweep, i, w[a], s_nb, nnb, s_accl, nacc);
                         }
                     }
                 }
-                const bool blocking = cls == 1;
                 if (P.n_trial == 0) {
-                    if (blocking) atomicMin(&s_kmin, k);
-                    if (__syncthreads_or(blocking)) {
+                    bool any = false;
+#pragma unroll
+                    for (int a = 0; a < ILP; ++a) {
+                        if (cls[a] == 1) {
+                            atomicMin(&s_kmin, k[a]);
+                            any = true;
+                        }
+                    }
+                    if (__syncthreads_or(any)) {
                         ++c_block;
                         c_eval += (uint32_t)(s_kmin - k0 + 1);
                         rejected = true;
@@ -463,22 +501,27 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
                     }
                     c_eval += (uint32_t)min(total, n_p - k0);
                 } else {
-                    double f = -1.0;
-                    if (blocking) {
-                        const CbResult32 r = cb_factor_fp32(P, sweep, i, (uint32_t)k, o0, o1, o2,
-                                                            s_nb, nnb, s_accl, nacc, r_hi, r_lo);
-                        f = r.f;
-                        c_fwd += r.fwd_ok;
-                        c_rev += r.rev_ok;
-                        c_cap += r.caps;
-                        c_rck += r.rck;
+#pragma unroll
+                    for (int a = 0; a < ILP; ++a) {
+                        double f = -1.0;
+                        if (cls[a] == 1) {
+                            const CbResult32 r = cb_factor_fp32(P, sweep, i, (uint32_t)k[a], o0, o1,
+                                                                o2, s_nb, nnb, s_accl, nacc, r_hi,
+                                                                r_lo);
+                            f = r.f;
+                            c_fwd += r.fwd_ok;
+                            c_rev += r.rev_ok;
+                            c_cap += r.caps;
+                            c_rck += r.rck;
+                        }
+                        s_f[a * nthr + tid] = f;
+                        s_k[a * nthr + tid] = k[a];
                     }
-                    s_f[tid] = f;
-                    s_k[tid] = k;
                     __syncthreads();
                     if (tid == 0) {
+                        // slots in attempt order = ascending depletant index
                         int zero = 0;
-                        for (int u = 0; u < nthr; ++u) {
+                        for (int u = 0; u < ILP * nthr; ++u) {
                             const double fu = s_f[u];
                             if (fu < 0.0) continue;
                             ++nblock;
@@ -500,7 +543,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
                     }
                 }
                 k0 += total;
-                t0 += (uint32_t)nthr;
+                t0 += per_pass;
             }
             if (!rejected && k0 < n_p && tid == 0) ++c_cap;
             if (rejected) {

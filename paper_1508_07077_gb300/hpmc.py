@@ -65,7 +65,7 @@ def load(path: str = LIB_PATH):
     L.hpmc_set_depletant.argtypes = [vp, ctypes.c_double, ctypes.c_double, ip]
     L.hpmc_set_moves.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.hpmc_set_cells.argtypes = [vp, ip]
-    L.hpmc_set_launch.argtypes = [vp, ip]
+    L.hpmc_set_launch.argtypes = [vp, ip, ip]
     L.hpmc_set_fp32_margin.argtypes = [vp, ctypes.c_double]
     L.hpmc_set_timing.argtypes = [vp, ip]
     L.hpmc_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
@@ -153,8 +153,9 @@ def hpmc_set_cells(ctx, n_cell):
     _check(load().hpmc_set_cells(ctx, int(n_cell)), "hpmc_set_cells")
 
 
-def hpmc_set_launch(ctx, warps_per_colloid):
-    _check(load().hpmc_set_launch(ctx, int(warps_per_colloid)), "hpmc_set_launch")
+def hpmc_set_launch(ctx, warps_per_colloid, attempts_per_thread=2):
+    _check(load().hpmc_set_launch(ctx, int(warps_per_colloid), int(attempts_per_thread)),
+           "hpmc_set_launch")
 
 
 def hpmc_set_fp32_margin(ctx, margin):
@@ -228,7 +229,7 @@ class Sampler:
 
     def __init__(self, pos, box_l, *, quat=None, shape=HPMC_SPHERE, shape_params=(1.0,),
                  q=0.0, n_r=0.0, n_trial=0, d_max=0.1, a_max=0.0, p_translate=1.0,
-                 seed=1, replica=0, precision=HPMC_FP64, n_cell=0, warps=2, device=0):
+                 seed=1, replica=0, precision=HPMC_FP64, n_cell=0, warps=1, ilp=2, device=0):
         pos = np.ascontiguousarray(pos, dtype=np.float64) if isinstance(pos, np.ndarray) else pos
         if isinstance(quat, np.ndarray):
             quat = np.ascontiguousarray(quat, dtype=np.float64)
@@ -240,7 +241,7 @@ class Sampler:
             hpmc_set_depletant(self.ctx, q, n_r, n_trial)
             hpmc_set_moves(self.ctx, d_max, a_max, p_translate)
             hpmc_set_cells(self.ctx, n_cell)
-            hpmc_set_launch(self.ctx, warps)
+            hpmc_set_launch(self.ctx, warps, ilp)
         except Exception:
             self.close()
             raise

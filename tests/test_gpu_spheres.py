@@ -27,10 +27,10 @@ def lib():
 PRECISIONS = [0, 1]   # HPMC_FP64, HPMC_FP32_RECHECK
 
 
-def _compare(oracle, lib, s, sweeps, *, n_trial=0, d_max=0.05, warps=2, n_cell=0,
+def _compare(oracle, lib, s, sweeps, *, n_trial=0, d_max=0.05, warps=1, ilp=2, n_cell=0,
              seed=1, precision=0, sweep0=0, margin=0.0):
     smp = lib.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, n_trial=n_trial, d_max=d_max,
-                      seed=seed, warps=warps, n_cell=n_cell, precision=precision)
+                      seed=seed, warps=warps, ilp=ilp, n_cell=n_cell, precision=precision)
     if margin:
         lib.hpmc_set_fp32_margin(smp.ctx, margin)
     if sweep0:
@@ -89,9 +89,11 @@ def test_spheres_256_configurational_bias(oracle, lib, n_trial, precision):
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
-@pytest.mark.parametrize("warps", [1, 3, 8])
-def test_launch_shape_does_not_change_results(oracle, lib, warps, precision):
-    _compare(oracle, lib, W.spheres_256(), 10, warps=warps, n_trial=2, precision=precision)
+@pytest.mark.parametrize("warps,ilp", [(1, 1), (1, 2), (3, 2), (8, 1), (8, 2)])
+def test_launch_shape_does_not_change_results(oracle, lib, warps, ilp, precision):
+    for n_trial in (0, 2):
+        _compare(oracle, lib, W.spheres_256(), 10, warps=warps, ilp=ilp, n_trial=n_trial,
+                 precision=precision)
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
