@@ -387,7 +387,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
     ap.add_argument("--warps", type=int, default=1)
-    ap.add_argument("--ilp", type=int, default=2)
+    ap.add_argument("--ilp", type=int, default=1)
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--sequential", action="store_true",
                     help="sweep the four systems one after another on one stream")

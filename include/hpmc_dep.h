@@ -115,7 +115,7 @@ int hpmc_set_cells(hpmc_ctx *ctx, int n_cell);
 
 /* Launch shape: warps cooperating on one moved colloid's depletants (1..8,
  * default 1) and depletant attempts each thread carries per pass (1 or 2,
- * default 2; FP32 form).  Performance knobs only: results are identical for
+ * default 1; FP32 form).  Performance knobs only: results are identical for
  * every value. */
 int hpmc_set_launch(hpmc_ctx *ctx, int warps_per_colloid, int attempts_per_thread);
 

@@ -36,7 +36,7 @@ struct Params {
     double d_max = 0.1, a_max = 0.0, p_translate = 1.0;
     int nc_req = 0;
     int warps = 1;
-    int ilp = 2;
+    int ilp = 1;
     double margin = 0.0;
 };
 

@@ -153,7 +153,7 @@ def hpmc_set_cells(ctx, n_cell):
     _check(load().hpmc_set_cells(ctx, int(n_cell)), "hpmc_set_cells")
 
 
-def hpmc_set_launch(ctx, warps_per_colloid, attempts_per_thread=2):
+def hpmc_set_launch(ctx, warps_per_colloid, attempts_per_thread=1):
     _check(load().hpmc_set_launch(ctx, int(warps_per_colloid), int(attempts_per_thread)),
            "hpmc_set_launch")
 
@@ -229,7 +229,7 @@ class Sampler:
 
     def __init__(self, pos, box_l, *, quat=None, shape=HPMC_SPHERE, shape_params=(1.0,),
                  q=0.0, n_r=0.0, n_trial=0, d_max=0.1, a_max=0.0, p_translate=1.0,
-                 seed=1, replica=0, precision=HPMC_FP64, n_cell=0, warps=1, ilp=2, device=0):
+                 seed=1, replica=0, precision=HPMC_FP64, n_cell=0, warps=1, ilp=1, device=0):
         pos = np.ascontiguousarray(pos, dtype=np.float64) if isinstance(pos, np.ndarray) else pos
         if isinstance(quat, np.ndarray):
             quat = np.ascontiguousarray(quat, dtype=np.float64)

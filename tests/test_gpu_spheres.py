@@ -27,7 +27,7 @@ def lib():
 PRECISIONS = [0, 1]   # HPMC_FP64, HPMC_FP32_RECHECK
 
 
-def _compare(oracle, lib, s, sweeps, *, n_trial=0, d_max=0.05, warps=1, ilp=2, n_cell=0,
+def _compare(oracle, lib, s, sweeps, *, n_trial=0, d_max=0.05, warps=1, ilp=1, n_cell=0,
              seed=1, precision=0, sweep0=0, margin=0.0):
     smp = lib.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, n_trial=n_trial, d_max=d_max,
                       seed=seed, warps=warps, ilp=ilp, n_cell=n_cell, precision=precision)
