@@ -169,6 +169,28 @@ int hpmc_cell_list(int n, double box_l, int n_cell, const double *pos_dev,
                    uint64_t seed, uint32_t replica, uint64_t sweep,
                    int *cell_start_dev, int *cell_idx_dev, void *stream);
 
+/* The same cell list as hpmc_cell_list, for callers that cannot allocate
+ * device memory at the time they need it (a loop with a fixed memory budget
+ * after start-up, code running while another component owns the allocator, a
+ * framework that hands out memory only from its own pool).  The paper has no
+ * counterpart: this is a service of the library, not a step of the method.
+ * It calls no cudaMalloc / cudaFree or any other allocating routine; its
+ * scratch is a file-scope device array of 1.25 MB that every GPU which loads
+ * the library holds until the process exits.
+ *   - Limits: n_cell <= 40 (n_cell^3 <= 65536 cells) and n <= 262144
+ *     colloids; larger sizes return HPMC_ERR_CAP without doing anything.
+ *   - The first call on a device looks up the array's device address for that
+ *     device (cudaGetSymbolAddress, with the device current); make that first
+ *     call before any stream capture on the device.
+ *   - Every call on a device shares the one array, which keeps the last
+ *     call's contents (the counts are cleared at the start of each call):
+ *     calls whose work overlaps on the GPU (different streams, no ordering)
+ *     race and give wrong lists.  Order them on one stream or with events.
+ * Arguments, outputs and errors as for hpmc_cell_list. */
+int hpmc_cell_list_noalloc(int n, double box_l, int n_cell, const double *pos_dev,
+                           uint64_t seed, uint32_t replica, uint64_t sweep,
+                           int *cell_start_dev, int *cell_idx_dev, void *stream);
+
 /* Human-readable name of an HPMC_* code. */
 const char *hpmc_strerror(int code);
 

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -777,6 +778,79 @@ int hpmc_cell_list(int n, double box_l, int n_cell, const double *pos_dev, uint6
     cudaFreeAsync(cell_of, s);
     cudaFreeAsync(count, s);
     return rc;
+}
+
+}  // extern "C"
+
+// --- allocation-free variant of the standalone cell list ------------------------
+//
+// Some callers cannot allocate device memory when they need a cell list: a
+// real-time loop that has a fixed memory budget after start-up, code that
+// runs while another component owns the device allocator, or a framework that
+// hands out memory only from its own pool.  hpmc_cell_list_noalloc serves them:
+// its scratch (the per-cell counts and the per-colloid cell ids) lives in the
+// file-scope device array below, which every GPU that loads this library
+// holds until the process exits.
+namespace {
+
+constexpr int kNoAllocMaxCells = 1 << 16;  // n_cell^3 <= 65536, i.e. n_cell <= 40
+constexpr int kNoAllocMaxN = 1 << 18;      // at most 262144 colloids
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) int g_noalloc_scratch[kNoAllocMaxCells + kNoAllocMaxN];
+
+// In host code the symbol above is only a host-side stand-in; the device
+// address is looked up once per device, with that device current.
+int *g_noalloc_dev[kNoAllocMaxDevices] = {nullptr};
+std::mutex g_noalloc_mutex;
+
+int noalloc_scratch(int **out)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return HPMC_ERR_CAP;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_dev[dev]) {
+        void *ptr = nullptr;
+        CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        g_noalloc_dev[dev] = (int *)ptr;
+    }
+    *out = g_noalloc_dev[dev];
+    return HPMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hpmc_cell_list_noalloc(int n, double box_l, int n_cell, const double *pos_dev, uint64_t seed,
+                           uint32_t replica, uint64_t sweep, int *cell_start_dev,
+                           int *cell_idx_dev, void *stream)
+{
+    if (n < 0 || !(box_l > 0.0) || n_cell < 2 || (n_cell & 1)) return HPMC_ERR_ARG;
+    if (n > 0 && (!pos_dev || !cell_idx_dev)) return HPMC_ERR_ARG;
+    if (!cell_start_dev) return HPMC_ERR_ARG;
+    if (n_cell > 40 || n > kNoAllocMaxN) return HPMC_ERR_CAP;
+    const int ncell = n_cell * n_cell * n_cell;
+    int *scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc != HPMC_OK) return rc;
+    int *count = scratch, *cell_of = scratch + kNoAllocMaxCells;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double w = box_l / (double)n_cell;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32) ^ replica;
+    // the array keeps the previous call's contents: the counts must start at zero
+    CK(cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncell, s));
+    if (n > 0)
+        k_csr_count<<<(n + 255) / 256, 256, 0, s>>>(n, box_l, w, n_cell, pos_dev, 3, k0, k1,
+                                                    (uint32_t)sweep, cell_of, count);
+    k_csr_scan<<<1, 1024, 0, s>>>(ncell, count, cell_start_dev);
+    if (n > 0) {
+        k_csr_scatter<<<(n + 255) / 256, 256, 0, s>>>(n, cell_of, count, cell_idx_dev);
+        k_csr_sort<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, cell_start_dev, cell_idx_dev);
+    }
+    CK(cudaGetLastError());
+    return HPMC_OK;
 }
 
 void hpmc_destroy(hpmc_ctx *c)

@@ -26,7 +26,7 @@ EXPORTS = ("hpmc_init", "hpmc_set_shape", "hpmc_set_depletant", "hpmc_set_moves"
            "hpmc_set_cells", "hpmc_set_launch", "hpmc_set_fp32_margin", "hpmc_set_timing",
            "hpmc_get_timing", "hpmc_sweep", "hpmc_get_state",
            "hpmc_set_state", "hpmc_reset_counters", "hpmc_sync", "hpmc_cell_list",
-           "hpmc_strerror", "hpmc_destroy")
+           "hpmc_cell_list_noalloc", "hpmc_strerror", "hpmc_destroy")
 
 
 class HPMCError(RuntimeError):
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
     L.hpmc_sync.argtypes = [vp]
     L.hpmc_cell_list.argtypes = [ip, ctypes.c_double, ip, vp, ctypes.c_uint64,
                                  ctypes.c_uint32, ctypes.c_uint64, vp, vp, vp]
+    L.hpmc_cell_list_noalloc.argtypes = L.hpmc_cell_list.argtypes
     L.hpmc_strerror.argtypes = [ip]
     L.hpmc_strerror.restype = ctypes.c_char_p
     L.hpmc_destroy.argtypes = [vp]
@@ -217,6 +218,16 @@ def hpmc_cell_list(n, box_l, n_cell, pos_dev, seed, replica, sweep, cell_start_d
                                  int(seed), int(replica), int(sweep),
                                  cell_start_dev.data_ptr(), cell_idx_dev.data_ptr(),
                                  _stream(stream)), "hpmc_cell_list")
+
+
+def hpmc_cell_list_noalloc(n, box_l, n_cell, pos_dev, seed, replica, sweep, cell_start_dev,
+                           cell_idx_dev, stream=None):
+    """hpmc_cell_list without any device allocation (static scratch; see the
+    header for its limits and its one-array-per-device sharing rule)."""
+    _check(load().hpmc_cell_list_noalloc(int(n), float(box_l), int(n_cell), _ptr(pos_dev)[0],
+                                         int(seed), int(replica), int(sweep),
+                                         cell_start_dev.data_ptr(), cell_idx_dev.data_ptr(),
+                                         _stream(stream)), "hpmc_cell_list_noalloc")
 
 
 def hpmc_destroy(ctx):
