@@ -128,9 +128,10 @@ int hpmc_set_fp32_margin(hpmc_ctx *ctx, double margin);
 /* Per-kernel timing.  While on, hpmc_sweep launches its kernels one by one
  * (no graph) with CUDA events around the cell-list kernels and around every
  * colour-phase kernel.  hpmc_get_timing synchronises and returns the summed
- * milliseconds and launch counts for kinds 0 = cell list (memset + 4 kernels,
- * one bracket), 1 = colour-phase kernel, then clears them.  ms/launches may
- * be NULL; nkinds is the length of both arrays (up to 2 are filled). */
+ * milliseconds and launch counts for kinds 0 = cell list and schedule,
+ * 1 = colour-phase kernel, 2 = depletant lens kernel (FP32 form), then clears
+ * them.  ms/launches may be NULL; nkinds is the length of both arrays (up to 3
+ * are filled). */
 int hpmc_set_timing(hpmc_ctx *ctx, int on);
 int hpmc_get_timing(hpmc_ctx *ctx, double *ms, uint64_t *launches, int nkinds);
 

@@ -106,6 +106,13 @@ struct SimParams {
     int *count[2];         // per-cell populations, double-buffered by sweep parity
     int *bins;             // [ncell][cap] colloid indices (unordered within a cell)
     const unsigned long long *T;   // Poisson CDF table as integers ceil(F[k] 2^53)
+    // per-colloid depletant "lens" lists of this sweep (FP32 form):
+    // lens[i][0..n) = (e, (t << 16) | k) of the depletants that overlap the new
+    // pose and not the old one, in depletant order; lens_hdr[i] = (N_p,
+    // depletants obtained from the stream, n or -1 if the list overflowed, 0)
+    float4 *lens;
+    int4 *lens_hdr;
+    int lens_cap;
     Sched *sched;
     unsigned long long *sweep;     // next sweep index
     unsigned long long *counters;

@@ -27,6 +27,7 @@ namespace {
 
 constexpr double kPi = 3.141592653589793;
 constexpr int kTableCap = 32768;
+constexpr int kLensCap = 64;   // lens points kept per move (longer lists take the full path)
 
 struct Params {
     int shape = HPMC_SPHERE;
@@ -64,6 +65,8 @@ struct hpmc_ctx {
     int *d_count = nullptr;   // 2 x ncell populations (double-buffered by sweep parity)
     int *d_bins = nullptr;    // ncell x cap colloid indices
     int ncell_alloc = -1;
+    float4 *d_lens = nullptr; // n x lens_cap depletant lens points (FP32 form)
+    int4 *d_lens_hdr = nullptr;
     Sched *d_sched = nullptr;
     unsigned long long *d_T = nullptr;
     unsigned long long *d_sweep = nullptr, *d_counters = nullptr;
@@ -175,6 +178,9 @@ SimParams make_params(hpmc_ctx *c)
     P.count[1] = c->d_count ? c->d_count + (size_t)c->nc * c->nc * c->nc : nullptr;
     P.bins = c->d_bins;
     P.T = c->d_T;
+    P.lens = c->d_lens;
+    P.lens_hdr = c->d_lens_hdr;
+    P.lens_cap = kLensCap;
     P.rel = c->d_rel;
     // FP32 form: thresholds in float and the certified margin.  Every vector a
     // test forms is a difference of cell-relative coordinates; each component
@@ -234,11 +240,18 @@ void launch_phase(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
 
 // One sweep: binned cell list, then the 8 colour phases (phase 7 advances
 // the sweep counter).
+void launch_lens(hpmc_ctx *c, const SimParams &P, cudaStream_t s)
+{
+    if (c->precision == HPMC_FP32_RECHECK && P.has_dep)
+        k_lens_sphere_fp32<<<(c->n + 3) / 4, 128, 0, s>>>(P);
+}
+
 int enqueue_sweep(hpmc_ctx *c, cudaStream_t s)
 {
     int rc = enqueue_cells(c, s);
     if (rc != HPMC_OK) return rc;
     SimParams P = make_params(c);
+    launch_lens(c, P, s);
     for (int phase = 0; phase < 8; ++phase) launch_phase(c, P, phase, s);
     CK(cudaGetLastError());
     return HPMC_OK;
@@ -269,6 +282,15 @@ int enqueue_sweep_timed(hpmc_ctx *c, cudaStream_t s)
     c->tev.push_back(b);
     c->tkind.push_back(0);
     SimParams P = make_params(c);
+    if (c->precision == HPMC_FP32_RECHECK && P.has_dep) {
+        cudaEvent_t x = pool_event(c), y = pool_event(c);
+        CK(cudaEventRecord(x, s));
+        launch_lens(c, P, s);
+        CK(cudaEventRecord(y, s));
+        c->tev.push_back(x);
+        c->tev.push_back(y);
+        c->tkind.push_back(2);
+    }
     for (int phase = 0; phase < 8; ++phase) {
         cudaEvent_t x = pool_event(c), y = pool_event(c);
         CK(cudaEventRecord(x, s));
@@ -365,6 +387,8 @@ int prepare(hpmc_ctx *c)
         if (rc != HPMC_OK) return rc;
     }
     c->nF = (int)F.size();
+    // lens points pack the attempt index t < 64 (N_p + 1) into 16 bits
+    if (c->precision == HPMC_FP32_RECHECK && c->nF > 1023) return HPMC_ERR_CAP;
 
     DeviceGuard g(c->device);
     const int ncell = nc * nc * nc;
@@ -377,6 +401,10 @@ int prepare(hpmc_ctx *c)
         CK(cudaMalloc(&c->d_count, sizeof(int) * 2 * (size_t)ncell));
         CK(cudaMalloc(&c->d_bins, sizeof(int) * (size_t)ncell * kMaxCellCap));
         c->ncell_alloc = ncell;
+    }
+    if (c->precision == HPMC_FP32_RECHECK && !c->d_lens) {
+        CK(cudaMalloc(&c->d_lens, sizeof(float4) * (size_t)c->n * kLensCap));
+        CK(cudaMalloc(&c->d_lens_hdr, sizeof(int4) * (size_t)c->n));
     }
     cudaFree(c->d_T);
     c->d_T = nullptr;
@@ -624,8 +652,8 @@ int hpmc_get_timing(hpmc_ctx *c, double *ms, uint64_t *launches, int nkinds)
     if (!c || nkinds < 0) return HPMC_ERR_ARG;
     DeviceGuard g(c->device);
     CK(cudaDeviceSynchronize());
-    double acc[2] = {0.0, 0.0};
-    uint64_t cnt[2] = {0, 0};
+    double acc[3] = {0.0, 0.0, 0.0};
+    uint64_t cnt[3] = {0, 0, 0};
     for (size_t k = 0; k < c->tkind.size(); ++k) {
         float t = 0.0f;
         CK(cudaEventElapsedTime(&t, c->tev[2 * k], c->tev[2 * k + 1]));
@@ -635,7 +663,7 @@ int hpmc_get_timing(hpmc_ctx *c, double *ms, uint64_t *launches, int nkinds)
     for (cudaEvent_t e : c->tev) c->tpool.push_back(e);
     c->tev.clear();
     c->tkind.clear();
-    for (int k = 0; k < nkinds && k < 2; ++k) {
+    for (int k = 0; k < nkinds && k < 3; ++k) {
         if (ms) ms[k] = acc[k];
         if (launches) launches[k] = cnt[k];
     }
@@ -868,6 +896,8 @@ void hpmc_destroy(hpmc_ctx *c)
     cudaFree(c->d_bins);
     cudaFree(c->d_sched);
     cudaFree(c->d_T);
+    cudaFree(c->d_lens);
+    cudaFree(c->d_lens_hdr);
     cudaFree(c->d_rel);
     cudaFree(c->d_sweep);
     cudaFree(c->d_counters);

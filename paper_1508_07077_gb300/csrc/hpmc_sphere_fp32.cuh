@@ -133,6 +133,16 @@ __device__ __noinline__ bool exact_dep(const SimParams &P, uint32_t sweep, int i
     return SphereFP64::dep(P, v0 - c0, v1 - c1, v2 - c2);
 }
 
+// A lens point (attempt t of the depletant stream) free of every neighbour?
+__device__ __noinline__ bool exact_free_nb(const SimParams &P, uint32_t sweep, int i, uint32_t t,
+                                           const float4 *nb, int nnb, const int *acc, int nacc)
+{
+    const uint4 w = draw(P.key0, P.key1, sweep, (uint32_t)i, kPDep, 0, t);
+    for (int a = 0; a < nnb; ++a)
+        if (exact_dep(P, sweep, i, w, 2, __float_as_int(nb[a].w), acc, nacc)) return false;
+    return true;
+}
+
 // --- FP32 tests with exact fallback -----------------------------------------
 
 // Is v (FP32, relative to the new reference point) free of every neighbour?
@@ -240,6 +250,87 @@ __device__ __noinline__ int exact_classify(const SimParams &P, uint32_t sweep, i
     for (int a = 0; a < nnb; ++a)
         if (exact_dep(P, sweep, i, w, 2, __float_as_int(nb[a].w), acc, nacc)) return 0;
     return 1;
+}
+
+// ---------------------------------------------------------------------------
+// Depletant lens lists (Sec. III.B-C), one warp per colloid, all colloids of
+// the sweep at once.  Everything about a move's depletants that does not
+// involve other colloids is fixed by the move's own random streams: the
+// proposal, N_p, the points of the attempt stream, "inside the new pose's
+// circumsphere" (= overlaps the new pose, for spheres) and "overlaps the old
+// pose".  Only the points left after those tests, the lens of the move, can
+// block it, and only they need the neighbours, which the colour phases test
+// in order.  Moves that certainly leave their cell draw nothing.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant__ SimParams P)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= P.n) return;
+    const uint32_t sweep = P.sched->sweep;
+    const uint32_t tag = (uint32_t)i;
+    const float dm_hi = P.d_max32 * 0x1p-31f, dm_lo = P.d_max32 * 0x1p-32f;
+    const float r_hi = P.R_s32 * 0x1p-31f, r_lo = P.R_s32 * 0x1p-32f;
+    const uint4 wm = draw(P.key0, P.key1, sweep, tag, kPMove, 0, 0);
+    const float D0 = scaled_s11f(wm.x, dm_hi, dm_lo);
+    const float D1 = scaled_s11f(wm.y, dm_hi, dm_lo);
+    const float D2 = scaled_s11f(wm.z, dm_hi, dm_lo);
+    {
+        // the same FP32 expression the colour phase uses for the cell-exit test
+        const float4 ri = P.rel[i];
+        const float rn0 = ri.x + D0, rn1 = ri.y + D1, rn2 = ri.z + D2;
+        const float mc = P.m_cell, wc = P.w32;
+        if (rn0 < -mc || rn0 > wc + mc || rn1 < -mc || rn1 > wc + mc || rn2 < -mc ||
+            rn2 > wc + mc) {
+            if (lane == 0) P.lens_hdr[i] = make_int4(0, 0, 0, 0);
+            return;
+        }
+    }
+    const float o0 = -D0, o1 = -D1, o2 = -D2;
+    const uint4 wp = draw(P.key0, P.key1, sweep, tag, kPPoisson, 0, 0);
+    const int n_p = poisson_count(P.T, P.nF, u53_int(wp.x, wp.y), lane);
+    const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
+    float4 *out = P.lens + (size_t)i * P.lens_cap;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t t0 = 0;
+    int k0 = 0, m = 0;
+    while (k0 < n_p && t0 < t_max) {
+        const uint32_t t = t0 + (uint32_t)lane;
+        uint4 w = make_uint4(0, 0, 0, 0);
+        float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+        int in = 0;
+        if (t < t_max) {
+            w = draw(P.key0, P.key1, sweep, tag, kPDep, 0, t);
+            e0 = scaled_s11f(w.x, r_hi, r_lo);
+            e1 = scaled_s11f(w.y, r_hi, r_lo);
+            e2 = scaled_s11f(w.z, r_hi, r_lo);
+            in = tri(norm2f(e0, e1, e2), P.T_s32, P.m_r2);
+        }
+        {
+            const bool unsure = in == -1;
+            if (__any_sync(kFull, unsure))
+                if (unsure) in = exact_ball(P, w) ? 1 : 0;
+        }
+        const unsigned bal = __ballot_sync(kFull, in == 1);
+        const int k = k0 + __popc(bal & lt);
+        const bool dep = in == 1 && k < n_p;
+        int to = 1;  // overlaps the old pose: 1 yes, 0 no, -1 within the margin
+        if (dep) to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), P.T_dep32, P.m_r2);
+        {
+            const bool unsure = to == -1;
+            if (__any_sync(kFull, unsure))
+                if (unsure) to = exact_dep(P, sweep, i, w, 0, 0, nullptr, 0) ? 1 : 0;
+        }
+        const bool lens = dep && to == 0;
+        const unsigned lb = __ballot_sync(kFull, lens);
+        const int slot = m + __popc(lb & lt);
+        if (lens && slot < P.lens_cap)
+            out[slot] = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
+        m += __popc(lb);
+        k0 += __popc(bal);
+        t0 += 32u;
+    }
+    if (lane == 0) P.lens_hdr[i] = make_int4(n_p, min(k0, n_p), m <= P.lens_cap ? m : -1, 0);
 }
 
 // ILP: attempts each thread carries per pass (independent Philox chains);
@@ -380,18 +471,108 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
 
         bool accept = true;
         if (P.has_dep) {
-            // a5: Poisson count (integer table, exact)
-            const uint4 wp = draw(P.key0, P.key1, sweep, tag, kPPoisson, 0, 0);
-            const int n_p = poisson_count(P.T, P.nF, u53_int(wp.x, wp.y), lane);
+            // a5: N_p and the lens points come from the lens kernel
+            const int4 hd = P.lens_hdr[i];
+            const int n_p = hd.x;
             c_drawn += (unsigned long long)n_p;
-
-            // a6: attempt stream, ILP * nthr attempts per pass
+            int nblock = 0;
+            double W = 1.0;
+            bool rejected = false;
+            if (hd.z >= 0) {
+                // a6: the lens points in depletant order; one free of every neighbour
+                // blocks the move
+                const int n_lens = hd.z;
+                const float4 *lens = P.lens + (size_t)i * P.lens_cap;
+                for (int m0 = 0; m0 < n_lens; m0 += nthr) {
+                    const int m = m0 + tid;
+                    int cls = 0, kk = 0x7FFFFFFF;
+                    uint32_t tt = 0;
+                    if (m < n_lens) {
+                        const float4 Lm = lens[m];
+                        const uint32_t tk = (uint32_t)__float_as_int(Lm.w);
+                        kk = (int)(tk & 0xFFFFu);
+                        tt = tk >> 16;
+                        bool unsure = false, hit = false;
+                        for (int b = 0; b < nnb; ++b) {
+                            const float4 d = s_nb[b];
+                            const int tn = tri(norm2f(Lm.x - d.x, Lm.y - d.y, Lm.z - d.z),
+                                               P.T_dep32, P.m_r2);
+                            if (tn == 1) {
+                                hit = true;
+                                break;
+                            }
+                            unsure = unsure || tn == -1;
+                        }
+                        cls = hit ? 0 : (unsure ? -1 : 1);
+                    }
+                    {
+                        const bool unsure = cls == -1;
+                        if (__any_sync(kFull, unsure)) {
+                            if (unsure) {
+                                ++c_rck;
+                                cls = exact_free_nb(P, sweep, i, tt, s_nb, nnb, s_accl, nacc) ? 1
+                                                                                              : 0;
+                            }
+                        }
+                    }
+                    const bool blocking = cls == 1;
+                    if (P.n_trial == 0) {
+                        if (blocking) atomicMin(&s_kmin, kk);
+                        if (__syncthreads_or(blocking)) {
+                            ++c_block;
+                            c_eval += (uint32_t)(s_kmin + 1);
+                            rejected = true;
+                            break;
+                        }
+                    } else {
+                        double f = -1.0;
+                        if (blocking) {
+                            const CbResult32 r = cb_factor_fp32(P, sweep, i, (uint32_t)kk, o0, o1,
+                                                                o2, s_nb, nnb, s_accl, nacc, r_hi,
+                                                                r_lo);
+                            f = r.f;
+                            c_fwd += r.fwd_ok;
+                            c_rev += r.rev_ok;
+                            c_cap += r.caps;
+                            c_rck += r.rck;
+                        }
+                        s_f[tid] = f;
+                        s_k[tid] = kk;
+                        __syncthreads();
+                        if (tid == 0) {
+                            int zero = 0;
+                            for (int u = 0; u < nthr; ++u) {
+                                const double fu = s_f[u];
+                                if (fu < 0.0) continue;
+                                ++nblock;
+                                ++c_block;
+                                if (fu == 0.0) {
+                                    zero = 1;
+                                    c_eval += (uint32_t)(s_k[u] + 1);
+                                    break;
+                                }
+                                W = W * fu;
+                            }
+                            s_flag = zero;
+                        }
+                        __syncthreads();
+                        if (s_flag) {
+                            rejected = true;
+                            break;
+                        }
+                    }
+                }
+                if (!rejected) {
+                    c_eval += (uint32_t)hd.y;
+                    if (hd.y < n_p && tid == 0) ++c_cap;
+                }
+            } else {
+            // a6 (lens list overflowed): the whole attempt stream, ILP * nthr
+            // attempts per pass
             const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
             const uint32_t per_pass = (uint32_t)(ILP * nthr);
             uint32_t t0 = 0;
-            int k0 = 0, nblock = 0;
-            double W = 1.0;
-            bool rejected = false;
+            int k0 = 0;
             while (k0 < n_p && t0 < t_max) {
                 uint4 w[ILP];
                 float e0[ILP], e1[ILP], e2[ILP];
@@ -546,6 +727,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
                 t0 += per_pass;
             }
             if (!rejected && k0 < n_p && tid == 0) ++c_cap;
+            }
             if (rejected) {
                 accept = false;
                 if (P.n_trial == 0) ++c_dep;

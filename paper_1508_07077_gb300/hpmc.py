@@ -168,10 +168,11 @@ def hpmc_set_timing(ctx, on):
 
 
 def hpmc_get_timing(ctx):
-    """(ms, launches) per kind: 0 = cell list, 1 = colour-phase kernel."""
-    ms = (ctypes.c_double * 2)()
-    n = (ctypes.c_uint64 * 2)()
-    _check(load().hpmc_get_timing(ctx, ms, n, 2), "hpmc_get_timing")
+    """(ms, launches) per kind: 0 = cell list, 1 = colour-phase kernel,
+    2 = depletant lens kernel."""
+    ms = (ctypes.c_double * 3)()
+    n = (ctypes.c_uint64 * 3)()
+    _check(load().hpmc_get_timing(ctx, ms, n, 3), "hpmc_get_timing")
     return [float(x) for x in ms], [int(x) for x in n]
 
 

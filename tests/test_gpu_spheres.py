@@ -154,7 +154,7 @@ def test_timing_mode_counts_launches(lib):
     smp.sweep(3)
     ms, n = lib.hpmc_get_timing(smp.ctx)
     smp.close()
-    assert n == [3, 24] and ms[0] > 0 and ms[1] > 0
+    assert n == [3, 24, 3] and ms[0] > 0 and ms[1] > 0 and ms[2] > 0
 
 
 def test_resume_and_device_io(oracle, lib):
