@@ -44,11 +44,15 @@ D_MAX_TUNED = {0.1: 0.0160, 0.2: 0.0080, 0.3: 0.0053, 0.4: 0.0040}
 ACC_TARGET = 0.30
 
 # Algorithmic ALU lane-operations (roofline):
-#  per evaluated depletant: 6/pi attempts x (Philox4x32-10: 40, point in the
-#  cube + ball test: 11) + old-pose test (8)
+#  lens kernel, per depletant drawn: 6/pi attempts x (Philox4x32-10: 40,
+#  point in the cube + ball test: 11) + old-pose test (8); per move: move and
+#  Poisson Philox (2 x 40), proposal and cell check (20), Poisson search (12)
 OPS_PER_DEP = 6.0 / math.pi * (40.0 + 11.0) + 8.0
-#  per trial move: move + Poisson Philox (2 x 40), proposal and cell check
-#  (20), Poisson search (12), ~25 neighbour candidates x 8
+OPS_PER_MOVE_LENS = 2 * 40.0 + 20.0 + 12.0
+#  colour-phase kernel, per move: proposal and cell check (20), ~25 neighbour
+#  candidates x 8 (overlap test)
+OPS_PER_MOVE_PHASE = 20.0 + 25 * 8.0
+#  FP64 plain form (one kernel): everything above per evaluated depletant
 OPS_PER_MOVE = 2 * 40.0 + 20.0 + 12.0 + 25 * 8.0
 ISSUE_LANES_PER_SM = 128        # 4 SM sub-partitions x 32 lanes, one instruction / clock
 BYTES_PER_MOVE = 2 * 32 + 16 + 2 * 4   # pos (double4) read + cell-local copy + cell list ids
@@ -287,8 +291,8 @@ def run_ours(args, ws, rank, local):
     for k in range(timing_steps):
         flush.zero_()
         step_sequential()
-    kern_ms = [0.0, 0.0]
-    kern_n = [0, 0]
+    kern_ms = [0.0, 0.0, 0.0]
+    kern_n = [0, 0, 0]
     for smp in smps:
         t, n = hpmc.hpmc_get_timing(smp.ctx)
         hpmc.hpmc_set_timing(smp.ctx, False)
@@ -297,6 +301,7 @@ def run_ours(args, ws, rank, local):
     tc = [hpmc.hpmc_get_state(smp.ctx)[1] for smp in smps]
     t_moves = sum(c["moves"] for c in tc)
     t_eval = sum(c["dep_evaluated"] for c in tc)
+    t_drawn = sum(c["dep_drawn"] for c in tc)
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     host_pos = [torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy() for _ in smps]
@@ -324,10 +329,21 @@ def run_ours(args, ws, rank, local):
         clocks = clk.summary()
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         phase_launch_ms = kern_ms[1] / max(1, kern_n[1])
-        ops_per_launch = (OPS_PER_DEP * t_eval + OPS_PER_MOVE * t_moves) / max(1, kern_n[1])
-        achieved = ops_per_launch / (phase_launch_ms * 1e-3) / 1e12
+        lens_launch_ms = kern_ms[2] / max(1, kern_n[2])
         f_peak = 2070.0e6
         peak = sms * ISSUE_LANES_PER_SM * f_peak / 1e12
+        if kern_n[2]:
+            # FP32 form: lens kernel (the depletant work) and colour phases
+            lens_ops = (OPS_PER_DEP * t_drawn + OPS_PER_MOVE_LENS * t_moves) / kern_n[2]
+            phase_ops = OPS_PER_MOVE_PHASE * t_moves / max(1, kern_n[1])
+            cand = {"k_lens_sphere_fp32": (kern_ms[2], lens_ops / (lens_launch_ms * 1e-3) / 1e12),
+                    "k_phase_sphere_fp32": (kern_ms[1],
+                                            phase_ops / (phase_launch_ms * 1e-3) / 1e12)}
+        else:
+            ops = (OPS_PER_DEP * t_eval + OPS_PER_MOVE * t_moves) / max(1, kern_n[1])
+            cand = {"k_phase_sphere_fp64": (kern_ms[1], ops / (phase_launch_ms * 1e-3) / 1e12)}
+        dominant = max(cand, key=lambda k: cand[k][0])
+        achieved = cand[dominant][1]
         bytes_per_launch = BYTES_PER_MOVE * t_moves / max(1, kern_n[1])
         value = ws * moves / (ms * 1e-3)
         e2e_moves = ws * e2e_steps * len(smps) * N
@@ -348,13 +364,16 @@ def run_ours(args, ws, rank, local):
             "insertions_evaluated_per_s": ws * evaluated / (ms * 1e-3),
             "acceptance": accept / max(1, moves),
             "fp64_rechecks_per_move": rechecks / max(1, moves),
-            "gpu_launches": args.steps * len(smps) * (1 + 4 + 8 + 1),
+            "gpu_launches": args.steps * len(smps) * (1 + (1 if prec == 1 else 0) + 8),
             "kernels": {"phase_ms_per_launch": phase_launch_ms,
+                        "lens_ms_per_launch": lens_launch_ms,
                         "cells_ms_per_sweep": kern_ms[0] / max(1, kern_n[0]),
-                        "phase_share": kern_ms[1] / max(1e-9, sum(kern_ms))},
+                        "share": {"cells": kern_ms[0] / max(1e-9, sum(kern_ms)),
+                                  "phase": kern_ms[1] / max(1e-9, sum(kern_ms)),
+                                  "lens": kern_ms[2] / max(1e-9, sum(kern_ms))},
+                        "achieved_tops": {k: v[1] for k, v in cand.items()}},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_phase_sphere_%s" % ("fp32" if prec == 1 else "fp64"),
+                         "frac": achieved / peak, "traffic": None, "kernel": dominant,
                          "peak_basis": "%d SMs x 128 lanes x 2070 MHz (issue rate)" % sms,
                          "hbm_achieved_gbs": bytes_per_launch / (phase_launch_ms * 1e-3) / 1e9},
             "clocks": clocks,

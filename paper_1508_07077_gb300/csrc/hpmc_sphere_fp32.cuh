@@ -286,6 +286,7 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
             return;
         }
     }
+    uint32_t rck = 0;
     const float o0 = -D0, o1 = -D1, o2 = -D2;
     const uint4 wp = draw(P.key0, P.key1, sweep, tag, kPPoisson, 0, 0);
     const int n_p = poisson_count(P.T, P.nF, u53_int(wp.x, wp.y), lane);
@@ -308,8 +309,12 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
         }
         {
             const bool unsure = in == -1;
-            if (__any_sync(kFull, unsure))
-                if (unsure) in = exact_ball(P, w) ? 1 : 0;
+            if (__any_sync(kFull, unsure)) {
+                if (unsure) {
+                    ++rck;
+                    in = exact_ball(P, w) ? 1 : 0;
+                }
+            }
         }
         const unsigned bal = __ballot_sync(kFull, in == 1);
         const int k = k0 + __popc(bal & lt);
@@ -318,8 +323,12 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
         if (dep) to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), P.T_dep32, P.m_r2);
         {
             const bool unsure = to == -1;
-            if (__any_sync(kFull, unsure))
-                if (unsure) to = exact_dep(P, sweep, i, w, 0, 0, nullptr, 0) ? 1 : 0;
+            if (__any_sync(kFull, unsure)) {
+                if (unsure) {
+                    ++rck;
+                    to = exact_dep(P, sweep, i, w, 0, 0, nullptr, 0) ? 1 : 0;
+                }
+            }
         }
         const bool lens = dep && to == 0;
         const unsigned lb = __ballot_sync(kFull, lens);
@@ -331,6 +340,10 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
         t0 += 32u;
     }
     if (lane == 0) P.lens_hdr[i] = make_int4(n_p, min(k0, n_p), m <= P.lens_cap ? m : -1, 0);
+    rck = __reduce_add_sync(kFull, rck);
+    if (lane == 0 && rck)
+        atomicAdd(P.counters + (size_t)(i % kCounterSlots) * kNumCounters + kRechecks,
+                  (unsigned long long)rck);
 }
 
 // ILP: attempts each thread carries per pass (independent Philox chains);
