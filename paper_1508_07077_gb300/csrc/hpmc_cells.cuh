@@ -1,10 +1,10 @@
 // Checkerboard cell lists (Sec. III.E), two layouts.
 //
 // * Binned (the sweep's own): one kernel per sweep computes the grid shift
-//   and colour order, bins every colloid into fixed-capacity cell slots with
-//   one atomic each, and writes the colloid's FP32 offset from its cell
-//   origin.  The order inside a bin is arbitrary; the CTA that moves a cell's
-//   colloids restores ascending index order itself.
+//   and colour order and bins every colloid into fixed-capacity cell slots
+//   with one atomic each; a slot holds the colloid's FP32 offset from its cell
+//   origin and its index.  The order inside a bin is arbitrary; the CTA that
+//   moves a cell's colloids restores ascending index order itself.
 // * CSR (the standalone hpmc_cell_list): count -> exclusive scan -> scatter ->
 //   per-cell sort, giving cell_start[ncell + 1] and cell_idx[n] in ascending
 //   index order within each cell.
@@ -37,11 +37,13 @@ __global__ void k_cells_bin(const __grid_constant__ SimParams P)
     const int cy = cell_coord(p.y, sigma[1], P.L, P.w, nc);
     const int cz = cell_coord(p.z, sigma[2], P.L, P.w, nc);
     const int c = cx + nc * (cy + nc * cz);
+    const float4 r = make_float4(cell_rel(p.x, sigma[0], P.L, P.w, cx),
+                                 cell_rel(p.y, sigma[1], P.L, P.w, cy),
+                                 cell_rel(p.z, sigma[2], P.L, P.w, cz), __int_as_float(i));
     const int slot = atomicAdd(P.count[sweep & 1u] + c, 1);
-    if (slot < P.cap) P.bins[(size_t)c * P.cap + slot] = i;
+    if (slot < P.cap) P.bins[(size_t)c * P.cap + slot] = r;
     else atomicCAS(P.err, kErrNone, kErrCellCap);
-    P.rel[i] = make_float4(cell_rel(p.x, sigma[0], P.L, P.w, cx), cell_rel(p.y, sigma[1], P.L, P.w, cy),
-                           cell_rel(p.z, sigma[2], P.L, P.w, cz), 0.0f);
+    P.rel[i] = r;
 }
 
 // --- CSR layout ------------------------------------------------------------

@@ -104,7 +104,8 @@ struct SimParams {
     double4 *quat;
     float4 *rel;           // FP32 position relative to the origin of its cell (this sweep)
     int *count[2];         // per-cell populations, double-buffered by sweep parity
-    int *bins;             // [ncell][cap] colloid indices (unordered within a cell)
+    float4 *bins;          // [ncell][cap] (FP32 offset from the cell origin, index bits in .w),
+                           // unordered within a cell
     const unsigned long long *T;   // Poisson CDF table as integers ceil(F[k] 2^53)
     // per-colloid depletant "lens" lists of this sweep (FP32 form):
     // lens[i][0..n) = (e, (t << 16) | k) of the depletants that overlap the new
@@ -247,7 +248,8 @@ __device__ __forceinline__ void own_members_sorted(const SimParams &P, int cell,
                                                    int *s_own)
 {
     const int tid = threadIdx.x;
-    for (int t = tid; t < n; t += blockDim.x) s_tmp[t] = P.bins[(size_t)cell * P.cap + t];
+    for (int t = tid; t < n; t += blockDim.x)
+        s_tmp[t] = __float_as_int(P.bins[(size_t)cell * P.cap + t].w);
     __syncthreads();
     for (int t = tid; t < n; t += blockDim.x) {
         const int v = s_tmp[t];

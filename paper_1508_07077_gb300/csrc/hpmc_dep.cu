@@ -63,7 +63,7 @@ struct hpmc_ctx {
     float4 *d_rel = nullptr;
     double *d_stage = nullptr;  // n x 4 doubles: layout conversion for device callers
     int *d_count = nullptr;   // 2 x ncell populations (double-buffered by sweep parity)
-    int *d_bins = nullptr;    // ncell x cap colloid indices
+    float4 *d_bins = nullptr; // ncell x cap (cell offset, index)
     int ncell_alloc = -1;
     float4 *d_lens = nullptr; // n x lens_cap depletant lens points (FP32 form)
     int4 *d_lens_hdr = nullptr;
@@ -231,10 +231,10 @@ void launch_phase(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
     const int h = c->nc / 2;
     const int n_active = h * h * h;
     const int threads = 32 * c->prm.warps;
-    if (c->precision == HPMC_FP32_RECHECK) {
-        if (c->prm.ilp == 2) k_phase_sphere_fp32<2><<<n_active, threads, 0, s>>>(P, phase);
-        else k_phase_sphere_fp32<1><<<n_active, threads, 0, s>>>(P, phase);
-    } else
+    if (c->precision == HPMC_FP32_RECHECK)
+        k_phase_sphere_fp32<<<n_active, threads, (size_t)threads * (sizeof(double) + sizeof(int)),
+                              s>>>(P, phase);
+    else
         k_phase_sphere_fp64<<<n_active, threads, 0, s>>>(P, phase);
 }
 
@@ -399,7 +399,7 @@ int prepare(hpmc_ctx *c)
         c->d_bins = nullptr;
         c->ncell_alloc = -1;
         CK(cudaMalloc(&c->d_count, sizeof(int) * 2 * (size_t)ncell));
-        CK(cudaMalloc(&c->d_bins, sizeof(int) * (size_t)ncell * kMaxCellCap));
+        CK(cudaMalloc(&c->d_bins, sizeof(float4) * (size_t)ncell * kMaxCellCap));
         c->ncell_alloc = ncell;
     }
     if (c->precision == HPMC_FP32_RECHECK && !c->d_lens) {

@@ -28,7 +28,7 @@ __global__ void k_check_spheres(const __grid_constant__ SimParams P, int *flag)
         const int c = stencil_cell(P, t, cx, cy, cz, dx, dy, dz);
         const int m = min(count[c], P.cap);
         for (int s = 0; s < m; ++s) {
-            const int j = P.bins[(size_t)c * P.cap + s];
+            const int j = __float_as_int(P.bins[(size_t)c * P.cap + s].w);
             if (j == i) continue;
             const double4 pj = P.pos[j];
             const double r2 = norm2(min_image(pj.x - pi.x, P.L, P.half_L),

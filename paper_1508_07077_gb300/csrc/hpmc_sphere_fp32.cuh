@@ -14,11 +14,13 @@
 
 namespace hpmc {
 
-// R * s11(w) in FP32: s11(w) = v 2^-31 + 2^-32 with v = (int)(w ^ 2^31); one
-// rounding of v, one of the fma (r_hi = R 2^-31, r_lo = R 2^-32).
-__device__ __forceinline__ float scaled_s11f(uint32_t w, float r_hi, float r_lo)
+// R * s11(w) in FP32 without an integer-to-float conversion: the float with
+// exponent of 2 and the top 23 bits of w as mantissa lies in [2, 4), so
+// f - 3 = -1 + (w >> 9) 2^-22 exactly, within 2^-22 below s11(w); one more
+// rounding for the product.  |result - R s11(w)| <= 6 u R (u = 2^-24).
+__device__ __forceinline__ float coord32(uint32_t w, float R)
 {
-    return __fmaf_rn((float)(int)(w ^ 0x80000000u), r_hi, r_lo);
+    return (__int_as_float(0x40000000u | (w >> 9)) - 3.0f) * R;
 }
 
 __device__ __forceinline__ float norm2f(float a, float b, float c)
@@ -167,15 +169,15 @@ __device__ __forceinline__ bool free_nb32(const SimParams &P, float v0, float v1
 // Next point of an attempt stream inside the sampling ball.
 __device__ __forceinline__ bool next_in_ball32(const SimParams &P, uint32_t sweep, uint32_t tag,
                                                uint32_t purpose, uint32_t sub, uint32_t &t,
-                                               uint32_t t_max, float r_hi, float r_lo, uint4 &w,
-                                               float &e0, float &e1, float &e2, uint32_t &rck)
+                                               uint32_t t_max, uint4 &w, float &e0, float &e1,
+                                               float &e2, uint32_t &rck)
 {
     while (t < t_max) {
         w = draw(P.key0, P.key1, sweep, tag, purpose, sub, t);
         ++t;
-        e0 = scaled_s11f(w.x, r_hi, r_lo);
-        e1 = scaled_s11f(w.y, r_hi, r_lo);
-        e2 = scaled_s11f(w.z, r_hi, r_lo);
+        e0 = coord32(w.x, P.R_s32);
+        e1 = coord32(w.y, P.R_s32);
+        e2 = coord32(w.z, P.R_s32);
         int in = tri(norm2f(e0, e1, e2), P.T_s32, P.m_r2);
         if (in == -1) {
             ++rck;
@@ -196,7 +198,7 @@ struct CbResult32 {
 __device__ __noinline__ CbResult32 cb_factor_fp32(const SimParams &P, uint32_t sweep, int i,
                                                   uint32_t k, float o0, float o1, float o2,
                                                   const float4 *nb, int nnb, const int *acc,
-                                                  int nacc, float r_hi, float r_lo)
+                                                  int nacc)
 {
     CbResult32 r = {0.0, 0u, 0u, 0u, 0u};
     const uint32_t tag = (uint32_t)i;
@@ -206,7 +208,7 @@ __device__ __noinline__ CbResult32 cb_factor_fp32(const SimParams &P, uint32_t s
     uint4 w;
     float e0, e1, e2;
     while (found < n_fwd && next_in_ball32(P, sweep, tag, kPCbFwd, k, t, 64u * (uint32_t)(n_fwd + 1),
-                                           r_hi, r_lo, w, e0, e1, e2, r.rck)) {
+                                           w, e0, e1, e2, r.rck)) {
         ++found;
         const float y0 = o0 + e0, y1 = o1 + e1, y2 = o2 + e2;
         int tn = tri(norm2f(y0, y1, y2), P.T_dep32, P.m_r2);  // overlaps the new pose?
@@ -222,7 +224,7 @@ __device__ __noinline__ CbResult32 cb_factor_fp32(const SimParams &P, uint32_t s
     t = 0;
     found = 0;
     while (found < n_rev && next_in_ball32(P, sweep, tag, kPCbRev, k, t, 64u * (uint32_t)(n_rev + 1),
-                                           r_hi, r_lo, w, e0, e1, e2, r.rck)) {
+                                           w, e0, e1, e2, r.rck)) {
         ++found;
         int to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), P.T_dep32, P.m_r2);  // old pose?
         if (to == -1) {
@@ -240,9 +242,8 @@ __device__ __noinline__ CbResult32 cb_factor_fp32(const SimParams &P, uint32_t s
     return r;
 }
 
-// Classify one depletant point e (FP32 first, exact where needed): blocking
-// iff it is not in the old pose's excluded volume nor any neighbour's (it is in
-// the new pose's, being inside the ball).  Returns 1 blocking, 0 not.
+// Classify one depletant point exactly: blocking iff it overlaps neither the
+// old pose nor a neighbour (it overlaps the new pose, being inside the ball).
 __device__ __noinline__ int exact_classify(const SimParams &P, uint32_t sweep, int i, uint4 w,
                                            const float4 *nb, int nnb, const int *acc, int nacc)
 {
@@ -250,6 +251,135 @@ __device__ __noinline__ int exact_classify(const SimParams &P, uint32_t sweep, i
     for (int a = 0; a < nnb; ++a)
         if (exact_dep(P, sweep, i, w, 2, __float_as_int(nb[a].w), acc, nacc)) return 0;
     return 1;
+}
+
+// Shared scratch of the per-move depletant evaluation; f and k point into the
+// dynamic shared memory (blockDim doubles, then blockDim ints).
+struct DepShared {
+    double *f;
+    int *k;
+    int warp[kMaxThreads / 32];
+    int kmin, flag;
+};
+
+// Outcome of one move's depletants (values valid in thread 0 for W and the
+// counters marked "thread 0"; rejected is block-uniform).
+struct DepOutcome {
+    double W;
+    int rejected, nblock;
+    uint32_t eval, block, cap, rck, fwd, rev;  // eval, block: thread 0
+};
+
+// CB bookkeeping of one pass: slots in ascending depletant index, product in
+// order, stop at a zero factor.  Called by every thread.
+__device__ __forceinline__ bool cb_pass(DepShared &sh, int tid, int nslots, double f, int k,
+                                       DepOutcome &o, int eval_if_full)
+{
+    sh.f[tid] = f;
+    sh.k[tid] = k;
+    __syncthreads();
+    if (tid == 0) {
+        int zero = 0;
+        for (int u = 0; u < nslots; ++u) {
+            const double fu = sh.f[u];
+            if (fu < 0.0) continue;
+            ++o.nblock;
+            ++o.block;
+            if (fu == 0.0) {
+                zero = 1;
+                o.eval += (uint32_t)(sh.k[u] + 1);
+                break;
+            }
+            o.W = o.W * fu;
+        }
+        if (!zero && eval_if_full >= 0) o.eval += (uint32_t)eval_if_full;
+        sh.flag = zero;
+    }
+    __syncthreads();
+    return sh.flag != 0;
+}
+
+// A lens list that overflowed: the whole attempt stream of colloid i, one
+// attempt per thread per pass (rare; out of line).
+__device__ __noinline__ DepOutcome full_stream_fp32(const SimParams &P, uint32_t sweep, int i,
+                                                    int n_p, float o0, float o1, float o2,
+                                                    const float4 *nb, int nnb, const int *acc,
+                                                    int nacc, DepShared &sh)
+{
+    DepOutcome o = {1.0, 0, 0, 0u, 0u, 0u, 0u, 0u, 0u};
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+    const uint32_t tag = (uint32_t)i;
+    const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
+    uint32_t t0 = 0;
+    int k0 = 0;
+    if (tid == 0) sh.kmin = 0x7FFFFFFF;
+    __syncthreads();
+    while (k0 < n_p && t0 < t_max) {
+        const uint32_t t = t0 + (uint32_t)tid;
+        uint4 w = make_uint4(0, 0, 0, 0);
+        float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+        int in = 0;
+        if (t < t_max) {
+            w = draw(P.key0, P.key1, sweep, tag, kPDep, 0, t);
+            e0 = coord32(w.x, P.R_s32);
+            e1 = coord32(w.y, P.R_s32);
+            e2 = coord32(w.z, P.R_s32);
+            in = tri(norm2f(e0, e1, e2), P.T_s32, P.m_r2);
+            if (in == -1) {
+                ++o.rck;
+                in = exact_ball(P, w) ? 1 : 0;
+            }
+        }
+        const unsigned bal = __ballot_sync(kFull, in == 1);
+        if (lane == 0) sh.warp[warp] = __popc(bal);
+        __syncthreads();
+        int base = 0, total = 0;
+        for (int u = 0; u < nwarps; ++u) {
+            const int c = sh.warp[u];
+            base += u < warp ? c : 0;
+            total += c;
+        }
+        const int k = k0 + base + __popc(bal & ((1u << lane) - 1u));
+        bool blocking = false;
+        if (in == 1 && k < n_p) {
+            int to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), P.T_dep32, P.m_r2);
+            if (to == -1) {
+                ++o.rck;
+                to = exact_dep(P, sweep, i, w, 0, 0, acc, nacc) ? 1 : 0;
+            }
+            if (!to) blocking = free_nb32(P, e0, e1, e2, nb, nnb, sweep, i, w, 2, acc, nacc, o.rck);
+        }
+        if (P.n_trial == 0) {
+            if (blocking) atomicMin(&sh.kmin, k);
+            if (__syncthreads_or(blocking)) {
+                o.block += 1;
+                o.eval += (uint32_t)(sh.kmin + 1);
+                o.rejected = 1;
+                return o;
+            }
+        } else {
+            double f = -1.0;
+            if (blocking) {
+                const CbResult32 r = cb_factor_fp32(P, sweep, i, (uint32_t)k, o0, o1, o2, nb, nnb,
+                                                    acc, nacc);
+                f = r.f;
+                o.fwd += r.fwd_ok;
+                o.rev += r.rev_ok;
+                o.cap += r.caps;
+                o.rck += r.rck;
+            }
+            if (cb_pass(sh, tid, nthr, f, k, o, -1)) {
+                o.rejected = 1;
+                return o;
+            }
+        }
+        k0 += total;
+        t0 += (uint32_t)nthr;
+    }
+    o.eval += (uint32_t)min(k0, n_p);
+    if (k0 < n_p && tid == 0) ++o.cap;
+    return o;
 }
 
 // ---------------------------------------------------------------------------
@@ -269,12 +399,10 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
     if (i >= P.n) return;
     const uint32_t sweep = P.sched->sweep;
     const uint32_t tag = (uint32_t)i;
-    const float dm_hi = P.d_max32 * 0x1p-31f, dm_lo = P.d_max32 * 0x1p-32f;
-    const float r_hi = P.R_s32 * 0x1p-31f, r_lo = P.R_s32 * 0x1p-32f;
     const uint4 wm = draw(P.key0, P.key1, sweep, tag, kPMove, 0, 0);
-    const float D0 = scaled_s11f(wm.x, dm_hi, dm_lo);
-    const float D1 = scaled_s11f(wm.y, dm_hi, dm_lo);
-    const float D2 = scaled_s11f(wm.z, dm_hi, dm_lo);
+    const float D0 = coord32(wm.x, P.d_max32);
+    const float D1 = coord32(wm.y, P.d_max32);
+    const float D2 = coord32(wm.z, P.d_max32);
     {
         // the same FP32 expression the colour phase uses for the cell-exit test
         const float4 ri = P.rel[i];
@@ -302,9 +430,9 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
         int in = 0;
         if (t < t_max) {
             w = draw(P.key0, P.key1, sweep, tag, kPDep, 0, t);
-            e0 = scaled_s11f(w.x, r_hi, r_lo);
-            e1 = scaled_s11f(w.y, r_hi, r_lo);
-            e2 = scaled_s11f(w.z, r_hi, r_lo);
+            e0 = coord32(w.x, P.R_s32);
+            e1 = coord32(w.y, P.R_s32);
+            e2 = coord32(w.z, P.R_s32);
             in = tri(norm2f(e0, e1, e2), P.T_s32, P.m_r2);
         }
         {
@@ -346,22 +474,32 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
                   (unsigned long long)rck);
 }
 
-// ILP: attempts each thread carries per pass (independent Philox chains);
-// the pass covers ILP * blockDim attempts of the stream, in order.
-template <int ILP>
+constexpr int kMaxLensCTA = 256;   // lens points of one cell staged in shared memory
+
+// ---------------------------------------------------------------------------
+// One colour phase (FP32 form): a CTA per active cell.  The CTA stages its
+// 27-cell neighbourhood, the cell's colloids (ascending index) and their lens
+// points in shared memory, then moves the colloids one after another.
+// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kMaxThreads, 2)
     k_phase_sphere_fp32(const __grid_constant__ SimParams P, int phase)
 {
-    __shared__ int s_own[kMaxCellCap], s_tmp[kMaxCellCap], s_accl[kMaxCellCap];
     __shared__ float4 s_cpos[kMaxCand];  // candidates relative to this cell's origin; index in .w
     __shared__ float4 s_nb[kMaxCand];    // neighbours relative to the new position; index in .w
-    __shared__ double s_f[ILP * kMaxThreads];
-    __shared__ int s_k[ILP * kMaxThreads];
-    __shared__ int s_warp[ILP][kMaxThreads / 32];
-    __shared__ int s_ncand, s_nnb, s_flag, s_acc, s_kmin, s_self, s_nacc;
+    __shared__ float4 s_lens[kMaxLensCTA];
+    __shared__ int4 s_hdr[kMaxCellCap];
+    __shared__ int s_tmp_i[kMaxCellCap], s_tmp_slot[kMaxCellCap];
+    __shared__ int s_own[kMaxCellCap], s_own_slot[kMaxCellCap], s_own_bin[kMaxCellCap];
+    __shared__ int s_loff[kMaxCellCap], s_accl[kMaxCellCap];
+    __shared__ DepShared sh;
+    __shared__ int s_ncand, s_nnb, s_acc, s_nacc;
+    extern __shared__ double s_dyn[];
 
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+    if (tid == 0) {
+        sh.f = s_dyn;
+        sh.k = (int *)(s_dyn + nthr);
+    }
     const Sched S = *P.sched;
     if (phase == 7 && blockIdx.x == 0 && tid == 0) atomicAdd(P.sweep, 1ull);
     const uint32_t sweep = S.sweep;
@@ -369,10 +507,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
     clear_next(P, S, T.cell);
     const int n_own = min(T.n_own, P.cap);
     if (n_own == 0) return;
-    own_members_sorted(P, T.cell, n_own, s_tmp, s_own);
     const int cx = T.cx, cy = T.cy, cz = T.cz;
 
-    // candidates of the 27-cell stencil, relative to this cell's origin
+    // neighbourhood: every colloid of the (deduplicated) 27-cell stencil,
+    // relative to this cell's origin; the cell's own members noted on the way
     if (tid == 0) {
         s_ncand = 0;
         s_nacc = 0;
@@ -382,13 +520,16 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
         int dx, dy, dz;
         const int c = stencil_cell(P, tid, cx, cy, cz, dx, dy, dz);
         const float fx = (float)dx * P.w32, fy = (float)dy * P.w32, fz = (float)dz * P.w32;
-        const int m = min(T.count[c], P.cap);
+        const int m = c == T.cell ? n_own : min(T.count[c], P.cap);
+        const float4 *bin = P.bins + (size_t)c * P.cap;
         for (int s = 0; s < m; ++s) {
-            const int j = P.bins[(size_t)c * P.cap + s];
-            const float4 r = P.rel[j];
+            const float4 e = bin[s];
             const int slot = atomicAdd(&s_ncand, 1);
-            if (slot < kMaxCand)
-                s_cpos[slot] = make_float4(fx + r.x, fy + r.y, fz + r.z, __int_as_float(j));
+            if (slot < kMaxCand) s_cpos[slot] = make_float4(fx + e.x, fy + e.y, fz + e.z, e.w);
+            if (c == T.cell) {
+                s_tmp_i[s] = __float_as_int(e.w);
+                s_tmp_slot[s] = slot;
+            }
         }
     }
     __syncthreads();
@@ -397,10 +538,42 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
         if (tid == 0) atomicCAS(P.err, kErrNone, kErrCandCap);
         return;
     }
-    const float r_hi = P.R_s32 * 0x1p-31f, r_lo = P.R_s32 * 0x1p-32f;
-    const float dm_hi = P.d_max32 * 0x1p-31f, dm_lo = P.d_max32 * 0x1p-32f;
+    // the cell's colloids in ascending index (the order they move in)
+    for (int q = tid; q < n_own; q += nthr) {
+        const int v = s_tmp_i[q];
+        int r = 0;
+        for (int u = 0; u < n_own; ++u) r += s_tmp_i[u] < v ? 1 : 0;
+        s_own[r] = v;
+        s_own_slot[r] = s_tmp_slot[q];
+        s_own_bin[r] = q;
+    }
+    __syncthreads();
+    // their depletant headers and lens points
+    if (P.has_dep) {
+        for (int q = tid; q < n_own; q += nthr) s_hdr[q] = P.lens_hdr[s_own[q]];
+        __syncthreads();
+        if (tid == 0) {
+            int off = 0;
+            for (int q = 0; q < n_own; ++q) {
+                const int n = s_hdr[q].z;
+                if (n > 0 && off + n <= kMaxLensCTA) {
+                    s_loff[q] = off;
+                    off += n;
+                } else {
+                    s_loff[q] = -1;
+                }
+            }
+        }
+        __syncthreads();
+        for (int q = 0; q < n_own; ++q) {
+            const int n = s_hdr[q].z, o = s_loff[q];
+            if (o < 0) continue;
+            const float4 *src = P.lens + (size_t)s_own[q] * P.lens_cap;
+            for (int m = tid; m < n; m += nthr) s_lens[o + m] = src[m];
+        }
+        __syncthreads();
+    }
 
-    // uniform counters (taken by thread 0) and per-thread ones
     uint32_t c_moves = 0, c_acc = 0, c_cell = 0, c_ov = 0, c_dep = 0, c_cb = 0, c_eval = 0,
              c_block = 0, c_fwd = 0, c_rev = 0, c_cap = 0, c_rck = 0;
     unsigned long long c_drawn = 0;
@@ -410,13 +583,13 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
         const uint32_t tag = (uint32_t)i;
         const int nacc = s_nacc;
         ++c_moves;
+        const float4 ri = s_cpos[s_own_slot[q]];
         float rn0, rn1, rn2;
-        const float4 ri = P.rel[i];
         {
             const uint4 wm = draw(P.key0, P.key1, sweep, tag, kPMove, 0, 0);
-            rn0 = ri.x + scaled_s11f(wm.x, dm_hi, dm_lo);
-            rn1 = ri.y + scaled_s11f(wm.y, dm_hi, dm_lo);
-            rn2 = ri.z + scaled_s11f(wm.z, dm_hi, dm_lo);
+            rn0 = ri.x + coord32(wm.x, P.d_max32);
+            rn1 = ri.y + coord32(wm.y, P.d_max32);
+            rn2 = ri.z + coord32(wm.z, P.d_max32);
         }
         // a3: cell-exit check with margin (exact when within it)
         const float mc = P.m_cell, wc = P.w32;
@@ -438,7 +611,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
         // a4: colloid overlap at the new pose; neighbours in range
         if (tid == 0) {
             s_nnb = 0;
-            s_kmin = 0x7FFFFFFF;
+            sh.kmin = 0x7FFFFFFF;
         }
         __syncthreads();
         int ov = 0;
@@ -450,7 +623,6 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
                 const float4 cp = s_cpos[j];
                 pj = __float_as_int(cp.w);
                 if (pj == i) {
-                    s_self = j;
                     pj = -1;
                 } else {
                     d0 = cp.x - rn0;
@@ -485,17 +657,16 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
         bool accept = true;
         if (P.has_dep) {
             // a5: N_p and the lens points come from the lens kernel
-            const int4 hd = P.lens_hdr[i];
+            const int4 hd = s_hdr[q];
             const int n_p = hd.x;
             c_drawn += (unsigned long long)n_p;
-            int nblock = 0;
-            double W = 1.0;
-            bool rejected = false;
+            DepOutcome o = {1.0, 0, 0, 0u, 0u, 0u, 0u, 0u, 0u};
             if (hd.z >= 0) {
-                // a6: the lens points in depletant order; one free of every neighbour
-                // blocks the move
+                // a6: the lens points in depletant order; one free of every
+                // neighbour blocks the move (or enters the CB weight)
                 const int n_lens = hd.z;
-                const float4 *lens = P.lens + (size_t)i * P.lens_cap;
+                const float4 *lens = s_loff[q] >= 0 ? s_lens + s_loff[q]
+                                                    : P.lens + (size_t)i * P.lens_cap;
                 for (int m0 = 0; m0 < n_lens; m0 += nthr) {
                     const int m = m0 + tid;
                     int cls = 0, kk = 0x7FFFFFFF;
@@ -522,7 +693,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
                         const bool unsure = cls == -1;
                         if (__any_sync(kFull, unsure)) {
                             if (unsure) {
-                                ++c_rck;
+                                ++o.rck;
                                 cls = exact_free_nb(P, sweep, i, tt, s_nb, nnb, s_accl, nacc) ? 1
                                                                                               : 0;
                             }
@@ -530,224 +701,50 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
                     }
                     const bool blocking = cls == 1;
                     if (P.n_trial == 0) {
-                        if (blocking) atomicMin(&s_kmin, kk);
+                        if (blocking) atomicMin(&sh.kmin, kk);
                         if (__syncthreads_or(blocking)) {
-                            ++c_block;
-                            c_eval += (uint32_t)(s_kmin + 1);
-                            rejected = true;
+                            o.block += 1;
+                            o.eval += (uint32_t)(sh.kmin + 1);
+                            o.rejected = 1;
                             break;
                         }
                     } else {
                         double f = -1.0;
                         if (blocking) {
                             const CbResult32 r = cb_factor_fp32(P, sweep, i, (uint32_t)kk, o0, o1,
-                                                                o2, s_nb, nnb, s_accl, nacc, r_hi,
-                                                                r_lo);
+                                                                o2, s_nb, nnb, s_accl, nacc);
                             f = r.f;
-                            c_fwd += r.fwd_ok;
-                            c_rev += r.rev_ok;
-                            c_cap += r.caps;
-                            c_rck += r.rck;
+                            o.fwd += r.fwd_ok;
+                            o.rev += r.rev_ok;
+                            o.cap += r.caps;
+                            o.rck += r.rck;
                         }
-                        s_f[tid] = f;
-                        s_k[tid] = kk;
-                        __syncthreads();
-                        if (tid == 0) {
-                            int zero = 0;
-                            for (int u = 0; u < nthr; ++u) {
-                                const double fu = s_f[u];
-                                if (fu < 0.0) continue;
-                                ++nblock;
-                                ++c_block;
-                                if (fu == 0.0) {
-                                    zero = 1;
-                                    c_eval += (uint32_t)(s_k[u] + 1);
-                                    break;
-                                }
-                                W = W * fu;
-                            }
-                            s_flag = zero;
-                        }
-                        __syncthreads();
-                        if (s_flag) {
-                            rejected = true;
+                        if (cb_pass(sh, tid, nthr, f, kk, o, -1)) {
+                            o.rejected = 1;
                             break;
                         }
                     }
                 }
-                if (!rejected) {
-                    c_eval += (uint32_t)hd.y;
-                    if (hd.y < n_p && tid == 0) ++c_cap;
+                if (!o.rejected) {
+                    o.eval += (uint32_t)hd.y;
+                    if (hd.y < n_p && tid == 0) ++o.cap;
                 }
             } else {
-            // a6 (lens list overflowed): the whole attempt stream, ILP * nthr
-            // attempts per pass
-            const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
-            const uint32_t per_pass = (uint32_t)(ILP * nthr);
-            uint32_t t0 = 0;
-            int k0 = 0;
-            while (k0 < n_p && t0 < t_max) {
-                uint4 w[ILP];
-                float e0[ILP], e1[ILP], e2[ILP];
-                int in[ILP];
-#pragma unroll
-                for (int a = 0; a < ILP; ++a) {
-                    const uint32_t t = t0 + (uint32_t)(a * nthr + tid);
-                    w[a] = make_uint4(0, 0, 0, 0);
-                    e0[a] = e1[a] = e2[a] = 0.f;
-                    in[a] = 0;
-                    if (t < t_max) {
-                        w[a] = draw(P.key0, P.key1, sweep, tag, kPDep, 0, t);
-                        e0[a] = scaled_s11f(w[a].x, r_hi, r_lo);
-                        e1[a] = scaled_s11f(w[a].y, r_hi, r_lo);
-                        e2[a] = scaled_s11f(w[a].z, r_hi, r_lo);
-                        in[a] = tri(norm2f(e0[a], e1[a], e2[a]), P.T_s32, P.m_r2);
-                    }
-                }
-#pragma unroll
-                for (int a = 0; a < ILP; ++a) {
-                    const bool unsure = in[a] == -1;
-                    if (__any_sync(kFull, unsure)) {
-                        if (unsure) {
-                            ++c_rck;
-                            in[a] = exact_ball(P, w[a]) ? 1 : 0;
-                        }
-                    }
-                }
-                // depletant index of each inside attempt: prefix over the pass
-                int k[ILP], total = 0;
-                unsigned bal[ILP];
-#pragma unroll
-                for (int a = 0; a < ILP; ++a) bal[a] = __ballot_sync(kFull, in[a] == 1);
-                if (nwarps > 1) {
-                    if (lane == 0) {
-#pragma unroll
-                        for (int a = 0; a < ILP; ++a) s_warp[a][warp] = __popc(bal[a]);
-                    }
-                    __syncthreads();
-#pragma unroll
-                    for (int a = 0; a < ILP; ++a) {
-                        int base = 0, tot = 0;
-                        for (int u = 0; u < nwarps; ++u) {
-                            const int c = s_warp[a][u];
-                            base += u < warp ? c : 0;
-                            tot += c;
-                        }
-                        k[a] = k0 + total + base + __popc(bal[a] & ((1u << lane) - 1u));
-                        total += tot;
-                    }
-                } else {
-#pragma unroll
-                    for (int a = 0; a < ILP; ++a) {
-                        k[a] = k0 + total + __popc(bal[a] & ((1u << lane) - 1u));
-                        total += __popc(bal[a]);
-                    }
-                }
-                // inside the ball = overlaps the new pose (spheres).  Blocking iff it
-                // overlaps neither the old pose nor a neighbour: 1 yes, 0 no, -1 unsure
-                int cls[ILP];
-#pragma unroll
-                for (int a = 0; a < ILP; ++a) {
-                    cls[a] = 0;
-                    if (in[a] == 1 && k[a] < n_p) {
-                        const int to = tri(norm2f(e0[a] - o0, e1[a] - o1, e2[a] - o2), P.T_dep32,
-                                           P.m_r2);
-                        if (to != 1) {
-                            bool unsure = to == -1, hit = false;
-                            for (int b = 0; b < nnb; ++b) {
-                                const float4 d = s_nb[b];
-                                const int tn = tri(norm2f(e0[a] - d.x, e1[a] - d.y, e2[a] - d.z),
-                                                   P.T_dep32, P.m_r2);
-                                if (tn == 1) {
-                                    hit = true;
-                                    break;
-                                }
-                                unsure = unsure || tn == -1;
-                            }
-                            cls[a] = hit ? 0 : (unsure ? -1 : 1);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int a = 0; a < ILP; ++a) {
-                    const bool unsure = cls[a] == -1;
-                    if (__any_sync(kFull, unsure)) {
-                        if (unsure) {
-                            ++c_rck;
-                            cls[a] = exact_classify(P, sweep, i, w[a], s_nb, nnb, s_accl, nacc);
-                        }
-                    }
-                }
-                if (P.n_trial == 0) {
-                    bool any = false;
-#pragma unroll
-                    for (int a = 0; a < ILP; ++a) {
-                        if (cls[a] == 1) {
-                            atomicMin(&s_kmin, k[a]);
-                            any = true;
-                        }
-                    }
-                    if (__syncthreads_or(any)) {
-                        ++c_block;
-                        c_eval += (uint32_t)(s_kmin - k0 + 1);
-                        rejected = true;
-                        break;
-                    }
-                    c_eval += (uint32_t)min(total, n_p - k0);
-                } else {
-#pragma unroll
-                    for (int a = 0; a < ILP; ++a) {
-                        double f = -1.0;
-                        if (cls[a] == 1) {
-                            const CbResult32 r = cb_factor_fp32(P, sweep, i, (uint32_t)k[a], o0, o1,
-                                                                o2, s_nb, nnb, s_accl, nacc, r_hi,
-                                                                r_lo);
-                            f = r.f;
-                            c_fwd += r.fwd_ok;
-                            c_rev += r.rev_ok;
-                            c_cap += r.caps;
-                            c_rck += r.rck;
-                        }
-                        s_f[a * nthr + tid] = f;
-                        s_k[a * nthr + tid] = k[a];
-                    }
-                    __syncthreads();
-                    if (tid == 0) {
-                        // slots in attempt order = ascending depletant index
-                        int zero = 0;
-                        for (int u = 0; u < ILP * nthr; ++u) {
-                            const double fu = s_f[u];
-                            if (fu < 0.0) continue;
-                            ++nblock;
-                            ++c_block;
-                            if (fu == 0.0) {
-                                zero = 1;
-                                c_eval += (uint32_t)(s_k[u] - k0 + 1);
-                                break;
-                            }
-                            W = W * fu;
-                        }
-                        if (!zero) c_eval += (uint32_t)min(total, n_p - k0);
-                        s_flag = zero;
-                    }
-                    __syncthreads();
-                    if (s_flag) {
-                        rejected = true;
-                        break;
-                    }
-                }
-                k0 += total;
-                t0 += per_pass;
+                o = full_stream_fp32(P, sweep, i, n_p, o0, o1, o2, s_nb, nnb, s_accl, nacc, sh);
             }
-            if (!rejected && k0 < n_p && tid == 0) ++c_cap;
-            }
-            if (rejected) {
+            c_eval += o.eval;
+            c_block += o.block;
+            c_cap += o.cap;
+            c_rck += o.rck;
+            c_fwd += o.fwd;
+            c_rev += o.rev;
+            if (o.rejected) {
                 accept = false;
                 if (P.n_trial == 0) ++c_dep;
                 else ++c_cb;
-            } else if (P.n_trial > 0 && tid == 0 && nblock > 0) {
+            } else if (P.n_trial > 0 && tid == 0 && o.nblock > 0) {
                 const uint4 wa = draw(P.key0, P.key1, sweep, tag, kPAccept, 0, 0);
-                if (!(u53(wa.x, wa.y) < W)) {
+                if (!(u53(wa.x, wa.y) < o.W)) {
                     accept = false;
                     ++c_cb;
                 }
@@ -758,15 +755,16 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
                 accept = s_acc != 0;
             }
         }
-        // a8: accepted: the FP32 working copies move now, the FP64 position
-        // when this CTA finishes
+        // a8: accepted: the FP32 working copies move now (shared neighbourhood
+        // and the cell bin later phases stage from), the FP64 position when
+        // this CTA finishes
         if (accept) {
             ++c_acc;
             if (tid == 0) {
                 const float4 rnew = make_float4(rn0, rn1, rn2, __int_as_float(i));
-                s_cpos[s_self] = rnew;
-                P.rel[i] = make_float4(rn0, rn1, rn2, 0.0f);
-                s_accl[s_nacc] = i;
+                s_cpos[s_own_slot[q]] = rnew;
+                P.bins[(size_t)T.cell * P.cap + s_own_bin[q]] = rnew;
+                s_accl[nacc] = i;
                 s_nacc = nacc + 1;
             }
         }

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kMaxThreads)
         const int m = min(T.count[c], P.cap);
         for (int s = 0; s < m; ++s) {
             const int slot = atomicAdd(&s_ncand, 1);
-            if (slot < kMaxCand) s_cand[slot] = P.bins[(size_t)c * P.cap + s];
+            if (slot < kMaxCand) s_cand[slot] = __float_as_int(P.bins[(size_t)c * P.cap + s].w);
         }
     }
     __syncthreads();
