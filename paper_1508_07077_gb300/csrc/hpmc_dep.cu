@@ -27,7 +27,7 @@ namespace {
 
 constexpr double kPi = 3.141592653589793;
 constexpr int kTableCap = 32768;
-constexpr int kLensCap = 64;   // lens points kept per move (longer lists take the full path)
+
 
 struct Params {
     int shape = HPMC_SPHERE;
@@ -67,6 +67,7 @@ struct hpmc_ctx {
     int ncell_alloc = -1;
     float4 *d_lens = nullptr; // n x lens_cap depletant lens points (FP32 form)
     int4 *d_lens_hdr = nullptr;
+    int lens_cap = 0;
     Sched *d_sched = nullptr;
     unsigned long long *d_T = nullptr;
     unsigned long long *d_sweep = nullptr, *d_counters = nullptr;
@@ -180,7 +181,7 @@ SimParams make_params(hpmc_ctx *c)
     P.T = c->d_T;
     P.lens = c->d_lens;
     P.lens_hdr = c->d_lens_hdr;
-    P.lens_cap = kLensCap;
+    P.lens_cap = c->lens_cap;
     P.rel = c->d_rel;
     // FP32 form: thresholds in float and the certified margin.  Every vector a
     // test forms is a difference of cell-relative coordinates; each component
@@ -231,10 +232,11 @@ void launch_phase(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
     const int h = c->nc / 2;
     const int n_active = h * h * h;
     const int threads = 32 * c->prm.warps;
-    if (c->precision == HPMC_FP32_RECHECK)
-        k_phase_sphere_fp32<<<n_active, threads, (size_t)threads * (sizeof(double) + sizeof(int)),
-                              s>>>(P, phase);
-    else
+    const size_t dyn = (size_t)threads * (sizeof(double) + sizeof(int));
+    if (c->precision == HPMC_FP32_RECHECK) {
+        if (P.n_trial > 0) k_phase_sphere_fp32<true><<<n_active, threads, dyn, s>>>(P, phase);
+        else k_phase_sphere_fp32<false><<<n_active, threads, dyn, s>>>(P, phase);
+    } else
         k_phase_sphere_fp64<<<n_active, threads, 0, s>>>(P, phase);
 }
 
@@ -402,9 +404,16 @@ int prepare(hpmc_ctx *c)
         CK(cudaMalloc(&c->d_bins, sizeof(float4) * (size_t)ncell * kMaxCellCap));
         c->ncell_alloc = ncell;
     }
-    if (c->precision == HPMC_FP32_RECHECK && !c->d_lens) {
-        CK(cudaMalloc(&c->d_lens, sizeof(float4) * (size_t)c->n * kLensCap));
-        CK(cudaMalloc(&c->d_lens_hdr, sizeof(int4) * (size_t)c->n));
+    // lens lists hold at most N_p <= nF points each: capacity nF, no overflow
+    if (c->precision == HPMC_FP32_RECHECK && c->nF > 0 && c->nF > c->lens_cap) {
+        const double bytes = (double)sizeof(float4) * (double)c->n * (double)c->nF;
+        if (bytes > 64.0 * (1ull << 30)) return HPMC_ERR_CAP;
+        cudaFree(c->d_lens);
+        c->d_lens = nullptr;
+        c->lens_cap = 0;
+        CK(cudaMalloc(&c->d_lens, sizeof(float4) * (size_t)c->n * (size_t)c->nF));
+        if (!c->d_lens_hdr) CK(cudaMalloc(&c->d_lens_hdr, sizeof(int4) * (size_t)c->n));
+        c->lens_cap = c->nF;
     }
     cudaFree(c->d_T);
     c->d_T = nullptr;

@@ -299,89 +299,6 @@ __device__ __forceinline__ bool cb_pass(DepShared &sh, int tid, int nslots, doub
     return sh.flag != 0;
 }
 
-// A lens list that overflowed: the whole attempt stream of colloid i, one
-// attempt per thread per pass (rare; out of line).
-__device__ __noinline__ DepOutcome full_stream_fp32(const SimParams &P, uint32_t sweep, int i,
-                                                    int n_p, float o0, float o1, float o2,
-                                                    const float4 *nb, int nnb, const int *acc,
-                                                    int nacc, DepShared &sh)
-{
-    DepOutcome o = {1.0, 0, 0, 0u, 0u, 0u, 0u, 0u, 0u};
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
-    const uint32_t tag = (uint32_t)i;
-    const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
-    uint32_t t0 = 0;
-    int k0 = 0;
-    if (tid == 0) sh.kmin = 0x7FFFFFFF;
-    __syncthreads();
-    while (k0 < n_p && t0 < t_max) {
-        const uint32_t t = t0 + (uint32_t)tid;
-        uint4 w = make_uint4(0, 0, 0, 0);
-        float e0 = 0.f, e1 = 0.f, e2 = 0.f;
-        int in = 0;
-        if (t < t_max) {
-            w = draw(P.key0, P.key1, sweep, tag, kPDep, 0, t);
-            e0 = coord32(w.x, P.R_s32);
-            e1 = coord32(w.y, P.R_s32);
-            e2 = coord32(w.z, P.R_s32);
-            in = tri(norm2f(e0, e1, e2), P.T_s32, P.m_r2);
-            if (in == -1) {
-                ++o.rck;
-                in = exact_ball(P, w) ? 1 : 0;
-            }
-        }
-        const unsigned bal = __ballot_sync(kFull, in == 1);
-        if (lane == 0) sh.warp[warp] = __popc(bal);
-        __syncthreads();
-        int base = 0, total = 0;
-        for (int u = 0; u < nwarps; ++u) {
-            const int c = sh.warp[u];
-            base += u < warp ? c : 0;
-            total += c;
-        }
-        const int k = k0 + base + __popc(bal & ((1u << lane) - 1u));
-        bool blocking = false;
-        if (in == 1 && k < n_p) {
-            int to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), P.T_dep32, P.m_r2);
-            if (to == -1) {
-                ++o.rck;
-                to = exact_dep(P, sweep, i, w, 0, 0, acc, nacc) ? 1 : 0;
-            }
-            if (!to) blocking = free_nb32(P, e0, e1, e2, nb, nnb, sweep, i, w, 2, acc, nacc, o.rck);
-        }
-        if (P.n_trial == 0) {
-            if (blocking) atomicMin(&sh.kmin, k);
-            if (__syncthreads_or(blocking)) {
-                o.block += 1;
-                o.eval += (uint32_t)(sh.kmin + 1);
-                o.rejected = 1;
-                return o;
-            }
-        } else {
-            double f = -1.0;
-            if (blocking) {
-                const CbResult32 r = cb_factor_fp32(P, sweep, i, (uint32_t)k, o0, o1, o2, nb, nnb,
-                                                    acc, nacc);
-                f = r.f;
-                o.fwd += r.fwd_ok;
-                o.rev += r.rev_ok;
-                o.cap += r.caps;
-                o.rck += r.rck;
-            }
-            if (cb_pass(sh, tid, nthr, f, k, o, -1)) {
-                o.rejected = 1;
-                return o;
-            }
-        }
-        k0 += total;
-        t0 += (uint32_t)nthr;
-    }
-    o.eval += (uint32_t)min(k0, n_p);
-    if (k0 < n_p && tid == 0) ++o.cap;
-    return o;
-}
-
 // ---------------------------------------------------------------------------
 // Depletant lens lists (Sec. III.B-C), one warp per colloid, all colloids of
 // the sweep at once.  Everything about a move's depletants that does not
@@ -390,7 +307,9 @@ __device__ __noinline__ DepOutcome full_stream_fp32(const SimParams &P, uint32_t
 // circumsphere" (= overlaps the new pose, for spheres) and "overlaps the old
 // pose".  Only the points left after those tests, the lens of the move, can
 // block it, and only they need the neighbours, which the colour phases test
-// in order.  Moves that certainly leave their cell draw nothing.
+// in order.  Moves that certainly leave their cell draw nothing.  A list
+// holds at most N_p <= (Poisson table length) points, the capacity it is
+// allocated with, so it cannot overflow.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant__ SimParams P)
 {
@@ -467,7 +386,10 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
         k0 += __popc(bal);
         t0 += 32u;
     }
-    if (lane == 0) P.lens_hdr[i] = make_int4(n_p, min(k0, n_p), m <= P.lens_cap ? m : -1, 0);
+    if (lane == 0) {
+        P.lens_hdr[i] = make_int4(n_p, min(k0, n_p), min(m, P.lens_cap), 0);
+        if (m > P.lens_cap) atomicCAS(P.err, kErrNone, kErrCandCap);
+    }
     rck = __reduce_add_sync(kFull, rck);
     if (lane == 0 && rck)
         atomicAdd(P.counters + (size_t)(i % kCounterSlots) * kNumCounters + kRechecks,
@@ -475,17 +397,20 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
 }
 
 constexpr int kMaxLensCTA = 256;   // lens points of one cell staged in shared memory
+constexpr int kMaxNb = 128;        // neighbours within reach of a depletant (hard spheres: <= ~36)
 
 // ---------------------------------------------------------------------------
 // One colour phase (FP32 form): a CTA per active cell.  The CTA stages its
 // 27-cell neighbourhood, the cell's colloids (ascending index) and their lens
-// points in shared memory, then moves the colloids one after another.
+// points in shared memory, then moves the colloids one after another.  CB:
+// configurational bias on (n_trial > 0) or off.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kMaxThreads, 2)
+template <bool CB>
+__global__ void __launch_bounds__(kMaxThreads)
     k_phase_sphere_fp32(const __grid_constant__ SimParams P, int phase)
 {
     __shared__ float4 s_cpos[kMaxCand];  // candidates relative to this cell's origin; index in .w
-    __shared__ float4 s_nb[kMaxCand];    // neighbours relative to the new position; index in .w
+    __shared__ float4 s_nb[kMaxNb];      // neighbours relative to the new position; index in .w
     __shared__ float4 s_lens[kMaxLensCTA];
     __shared__ int4 s_hdr[kMaxCellCap];
     __shared__ int s_tmp_i[kMaxCellCap], s_tmp_slot[kMaxCellCap];
@@ -645,7 +570,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
             if (t == 1) ov = 1;
             if (pj >= 0 && r2 < P.nb_cut2_32) {
                 const int slot = atomicAdd(&s_nnb, 1);
-                s_nb[slot] = make_float4(d0, d1, d2, __int_as_float(pj));
+                if (slot < kMaxNb) s_nb[slot] = make_float4(d0, d1, d2, __int_as_float(pj));
             }
         }
         if (__syncthreads_or(ov)) {
@@ -653,6 +578,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
             continue;
         }
         const int nnb = s_nnb;
+        if (nnb > kMaxNb) {
+            if (tid == 0) atomicCAS(P.err, kErrNone, kErrCandCap);
+            return;
+        }
 
         bool accept = true;
         if (P.has_dep) {
@@ -661,7 +590,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
             const int n_p = hd.x;
             c_drawn += (unsigned long long)n_p;
             DepOutcome o = {1.0, 0, 0, 0u, 0u, 0u, 0u, 0u, 0u};
-            if (hd.z >= 0) {
+            {
                 // a6: the lens points in depletant order; one free of every
                 // neighbour blocks the move (or enters the CB weight)
                 const int n_lens = hd.z;
@@ -700,7 +629,7 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
                         }
                     }
                     const bool blocking = cls == 1;
-                    if (P.n_trial == 0) {
+                    if (!CB) {
                         if (blocking) atomicMin(&sh.kmin, kk);
                         if (__syncthreads_or(blocking)) {
                             o.block += 1;
@@ -729,8 +658,6 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
                     o.eval += (uint32_t)hd.y;
                     if (hd.y < n_p && tid == 0) ++o.cap;
                 }
-            } else {
-                o = full_stream_fp32(P, sweep, i, n_p, o0, o1, o2, s_nb, nnb, s_accl, nacc, sh);
             }
             c_eval += o.eval;
             c_block += o.block;
@@ -740,16 +667,16 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
             c_rev += o.rev;
             if (o.rejected) {
                 accept = false;
-                if (P.n_trial == 0) ++c_dep;
+                if (!CB) ++c_dep;
                 else ++c_cb;
-            } else if (P.n_trial > 0 && tid == 0 && o.nblock > 0) {
+            } else if (CB && tid == 0 && o.nblock > 0) {
                 const uint4 wa = draw(P.key0, P.key1, sweep, tag, kPAccept, 0, 0);
                 if (!(u53(wa.x, wa.y) < o.W)) {
                     accept = false;
                     ++c_cb;
                 }
             }
-            if (P.n_trial > 0) {
+            if (CB) {
                 if (tid == 0) s_acc = accept ? 1 : 0;
                 __syncthreads();
                 accept = s_acc != 0;
