@@ -113,6 +113,7 @@ struct SimParams {
     // depletants obtained from the stream, n or -1 if the list overflowed, 0)
     float4 *lens;
     int4 *lens_hdr;
+    float4 *lens_move;     // the move's FP32 displacement (the phase kernels reuse it)
     int lens_cap;
     Sched *sched;
     unsigned long long *sweep;     // next sweep index

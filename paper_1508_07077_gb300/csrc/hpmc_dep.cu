@@ -67,6 +67,7 @@ struct hpmc_ctx {
     int ncell_alloc = -1;
     float4 *d_lens = nullptr; // n x lens_cap depletant lens points (FP32 form)
     int4 *d_lens_hdr = nullptr;
+    float4 *d_lens_move = nullptr;
     int lens_cap = 0;
     Sched *d_sched = nullptr;
     unsigned long long *d_T = nullptr;
@@ -181,6 +182,7 @@ SimParams make_params(hpmc_ctx *c)
     P.T = c->d_T;
     P.lens = c->d_lens;
     P.lens_hdr = c->d_lens_hdr;
+    P.lens_move = c->d_lens_move;
     P.lens_cap = c->lens_cap;
     P.rel = c->d_rel;
     // FP32 form: thresholds in float and the certified margin.  Every vector a
@@ -234,8 +236,14 @@ void launch_phase(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
     const int threads = 32 * c->prm.warps;
     const size_t dyn = (size_t)threads * (sizeof(double) + sizeof(int));
     if (c->precision == HPMC_FP32_RECHECK) {
-        if (P.n_trial > 0) k_phase_sphere_fp32<true><<<n_active, threads, dyn, s>>>(P, phase);
-        else k_phase_sphere_fp32<false><<<n_active, threads, dyn, s>>>(P, phase);
+        const bool warp = threads == 32;
+        if (P.n_trial > 0) {
+            if (warp) k_phase_sphere_fp32<true, true><<<n_active, threads, dyn, s>>>(P, phase);
+            else k_phase_sphere_fp32<true, false><<<n_active, threads, dyn, s>>>(P, phase);
+        } else {
+            if (warp) k_phase_sphere_fp32<false, true><<<n_active, threads, dyn, s>>>(P, phase);
+            else k_phase_sphere_fp32<false, false><<<n_active, threads, dyn, s>>>(P, phase);
+        }
     } else
         k_phase_sphere_fp64<<<n_active, threads, 0, s>>>(P, phase);
 }
@@ -244,8 +252,7 @@ void launch_phase(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
 // the sweep counter).
 void launch_lens(hpmc_ctx *c, const SimParams &P, cudaStream_t s)
 {
-    if (c->precision == HPMC_FP32_RECHECK && P.has_dep)
-        k_lens_sphere_fp32<<<(c->n + 3) / 4, 128, 0, s>>>(P);
+    if (c->precision == HPMC_FP32_RECHECK) k_lens_sphere_fp32<<<(c->n + 3) / 4, 128, 0, s>>>(P);
 }
 
 int enqueue_sweep(hpmc_ctx *c, cudaStream_t s)
@@ -284,7 +291,7 @@ int enqueue_sweep_timed(hpmc_ctx *c, cudaStream_t s)
     c->tev.push_back(b);
     c->tkind.push_back(0);
     SimParams P = make_params(c);
-    if (c->precision == HPMC_FP32_RECHECK && P.has_dep) {
+    if (c->precision == HPMC_FP32_RECHECK) {
         cudaEvent_t x = pool_event(c), y = pool_event(c);
         CK(cudaEventRecord(x, s));
         launch_lens(c, P, s);
@@ -405,15 +412,18 @@ int prepare(hpmc_ctx *c)
         c->ncell_alloc = ncell;
     }
     // lens lists hold at most N_p <= nF points each: capacity nF, no overflow
-    if (c->precision == HPMC_FP32_RECHECK && c->nF > 0 && c->nF > c->lens_cap) {
-        const double bytes = (double)sizeof(float4) * (double)c->n * (double)c->nF;
-        if (bytes > 64.0 * (1ull << 30)) return HPMC_ERR_CAP;
-        cudaFree(c->d_lens);
-        c->d_lens = nullptr;
-        c->lens_cap = 0;
-        CK(cudaMalloc(&c->d_lens, sizeof(float4) * (size_t)c->n * (size_t)c->nF));
+    if (c->precision == HPMC_FP32_RECHECK) {
         if (!c->d_lens_hdr) CK(cudaMalloc(&c->d_lens_hdr, sizeof(int4) * (size_t)c->n));
-        c->lens_cap = c->nF;
+        if (!c->d_lens_move) CK(cudaMalloc(&c->d_lens_move, sizeof(float4) * (size_t)c->n));
+        if (c->nF > c->lens_cap) {
+            const double bytes = (double)sizeof(float4) * (double)c->n * (double)c->nF;
+            if (bytes > 64.0 * (1ull << 30)) return HPMC_ERR_CAP;
+            cudaFree(c->d_lens);
+            c->d_lens = nullptr;
+            c->lens_cap = 0;
+            CK(cudaMalloc(&c->d_lens, sizeof(float4) * (size_t)c->n * (size_t)c->nF));
+            c->lens_cap = c->nF;
+        }
     }
     cudaFree(c->d_T);
     c->d_T = nullptr;
@@ -907,6 +917,7 @@ void hpmc_destroy(hpmc_ctx *c)
     cudaFree(c->d_T);
     cudaFree(c->d_lens);
     cudaFree(c->d_lens_hdr);
+    cudaFree(c->d_lens_move);
     cudaFree(c->d_rel);
     cudaFree(c->d_sweep);
     cudaFree(c->d_counters);

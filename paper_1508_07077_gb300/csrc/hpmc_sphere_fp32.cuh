@@ -322,6 +322,8 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
     const float D0 = coord32(wm.x, P.d_max32);
     const float D1 = coord32(wm.y, P.d_max32);
     const float D2 = coord32(wm.z, P.d_max32);
+    if (lane == 0) P.lens_move[i] = make_float4(D0, D1, D2, 0.0f);
+    if (!P.has_dep) return;
     {
         // the same FP32 expression the colour phase uses for the cell-exit test
         const float4 ri = P.rel[i];
@@ -399,13 +401,29 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
 constexpr int kMaxLensCTA = 256;   // lens points of one cell staged in shared memory
 constexpr int kMaxNb = 128;        // neighbours within reach of a depletant (hard spheres: <= ~36)
 
+// CTA-wide barrier / OR, reduced to warp operations when the CTA is one warp.
+template <bool WARP>
+__device__ __forceinline__ void cta_sync()
+{
+    if (WARP) __syncwarp();
+    else __syncthreads();
+}
+
+template <bool WARP>
+__device__ __forceinline__ bool cta_any(bool p)
+{
+    if (WARP) return __any_sync(kFull, p);
+    return __syncthreads_or(p) != 0;
+}
+
 // ---------------------------------------------------------------------------
 // One colour phase (FP32 form): a CTA per active cell.  The CTA stages its
-// 27-cell neighbourhood, the cell's colloids (ascending index) and their lens
-// points in shared memory, then moves the colloids one after another.  CB:
-// configurational bias on (n_trial > 0) or off.
+// 27-cell neighbourhood, the cell's colloids (ascending index), their
+// displacements and their lens points in shared memory, then moves the
+// colloids one after another.  CB: configurational bias on (n_trial > 0) or
+// off.  WARP: the CTA is a single warp (barriers become warp operations).
 // ---------------------------------------------------------------------------
-template <bool CB>
+template <bool CB, bool WARP>
 __global__ void __launch_bounds__(kMaxThreads)
     k_phase_sphere_fp32(const __grid_constant__ SimParams P, int phase)
 {
@@ -413,6 +431,7 @@ __global__ void __launch_bounds__(kMaxThreads)
     __shared__ float4 s_nb[kMaxNb];      // neighbours relative to the new position; index in .w
     __shared__ float4 s_lens[kMaxLensCTA];
     __shared__ int4 s_hdr[kMaxCellCap];
+    __shared__ float4 s_mv[kMaxCellCap];
     __shared__ int s_tmp_i[kMaxCellCap], s_tmp_slot[kMaxCellCap];
     __shared__ int s_own[kMaxCellCap], s_own_slot[kMaxCellCap], s_own_bin[kMaxCellCap];
     __shared__ int s_loff[kMaxCellCap], s_accl[kMaxCellCap];
@@ -420,7 +439,9 @@ __global__ void __launch_bounds__(kMaxThreads)
     __shared__ int s_ncand, s_nnb, s_acc, s_nacc;
     extern __shared__ double s_dyn[];
 
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = threadIdx.x, nthr = WARP ? 32 : (int)blockDim.x;
+    const int lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u;
     if (tid == 0) {
         sh.f = s_dyn;
         sh.k = (int *)(s_dyn + nthr);
@@ -440,7 +461,7 @@ __global__ void __launch_bounds__(kMaxThreads)
         s_ncand = 0;
         s_nacc = 0;
     }
-    __syncthreads();
+    cta_sync<WARP>();
     if (tid < P.n_stencil * P.n_stencil * P.n_stencil) {
         int dx, dy, dz;
         const int c = stencil_cell(P, tid, cx, cy, cz, dx, dy, dz);
@@ -457,13 +478,14 @@ __global__ void __launch_bounds__(kMaxThreads)
             }
         }
     }
-    __syncthreads();
+    cta_sync<WARP>();
     const int M = s_ncand;
     if (M > kMaxCand) {
         if (tid == 0) atomicCAS(P.err, kErrNone, kErrCandCap);
         return;
     }
-    // the cell's colloids in ascending index (the order they move in)
+    // the cell's colloids in ascending index (the order they move in), their
+    // displacements and depletant headers
     for (int q = tid; q < n_own; q += nthr) {
         const int v = s_tmp_i[q];
         int r = 0;
@@ -471,12 +493,12 @@ __global__ void __launch_bounds__(kMaxThreads)
         s_own[r] = v;
         s_own_slot[r] = s_tmp_slot[q];
         s_own_bin[r] = q;
+        s_mv[r] = P.lens_move[v];
+        if (P.has_dep) s_hdr[r] = P.lens_hdr[v];
     }
-    __syncthreads();
-    // their depletant headers and lens points
+    cta_sync<WARP>();
+    // and their lens points
     if (P.has_dep) {
-        for (int q = tid; q < n_own; q += nthr) s_hdr[q] = P.lens_hdr[s_own[q]];
-        __syncthreads();
         if (tid == 0) {
             int off = 0;
             for (int q = 0; q < n_own; ++q) {
@@ -489,33 +511,26 @@ __global__ void __launch_bounds__(kMaxThreads)
                 }
             }
         }
-        __syncthreads();
+        cta_sync<WARP>();
         for (int q = 0; q < n_own; ++q) {
             const int n = s_hdr[q].z, o = s_loff[q];
             if (o < 0) continue;
             const float4 *src = P.lens + (size_t)s_own[q] * P.lens_cap;
             for (int m = tid; m < n; m += nthr) s_lens[o + m] = src[m];
         }
-        __syncthreads();
+        cta_sync<WARP>();
     }
 
-    uint32_t c_moves = 0, c_acc = 0, c_cell = 0, c_ov = 0, c_dep = 0, c_cb = 0, c_eval = 0,
-             c_block = 0, c_fwd = 0, c_rev = 0, c_cap = 0, c_rck = 0;
+    uint32_t c_acc = 0, c_cell = 0, c_ov = 0, c_dep = 0, c_cb = 0, c_eval = 0, c_block = 0,
+             c_fwd = 0, c_rev = 0, c_cap = 0, c_rck = 0;
     unsigned long long c_drawn = 0;
 
     for (int q = 0; q < n_own; ++q) {
         const int i = s_own[q];
-        const uint32_t tag = (uint32_t)i;
         const int nacc = s_nacc;
-        ++c_moves;
         const float4 ri = s_cpos[s_own_slot[q]];
-        float rn0, rn1, rn2;
-        {
-            const uint4 wm = draw(P.key0, P.key1, sweep, tag, kPMove, 0, 0);
-            rn0 = ri.x + coord32(wm.x, P.d_max32);
-            rn1 = ri.y + coord32(wm.y, P.d_max32);
-            rn2 = ri.z + coord32(wm.z, P.d_max32);
-        }
+        const float4 mv = s_mv[q];
+        const float rn0 = ri.x + mv.x, rn1 = ri.y + mv.y, rn2 = ri.z + mv.z;
         // a3: cell-exit check with margin (exact when within it)
         const float mc = P.m_cell, wc = P.w32;
         const bool out = rn0 < -mc || rn0 > wc + mc || rn1 < -mc || rn1 > wc + mc ||
@@ -534,12 +549,11 @@ __global__ void __launch_bounds__(kMaxThreads)
         const float o0 = ri.x - rn0, o1 = ri.y - rn1, o2 = ri.z - rn2;
 
         // a4: colloid overlap at the new pose; neighbours in range
-        if (tid == 0) {
-            s_nnb = 0;
-            sh.kmin = 0x7FFFFFFF;
+        if (!WARP) {
+            if (tid == 0) s_nnb = 0;
+            __syncthreads();
         }
-        __syncthreads();
-        int ov = 0;
+        int ov = 0, nnb = 0;
         for (int j0 = 0; j0 < M; j0 += nthr) {
             const int j = j0 + tid;
             int t = 0, pj = -1;
@@ -568,16 +582,22 @@ __global__ void __launch_bounds__(kMaxThreads)
                 }
             }
             if (t == 1) ov = 1;
-            if (pj >= 0 && r2 < P.nb_cut2_32) {
+            const bool take = pj >= 0 && r2 < P.nb_cut2_32;
+            if (WARP) {
+                const unsigned b = __ballot_sync(kFull, take);
+                const int slot = nnb + __popc(b & lt);
+                if (take && slot < kMaxNb) s_nb[slot] = make_float4(d0, d1, d2, __int_as_float(pj));
+                nnb += __popc(b);
+            } else if (take) {
                 const int slot = atomicAdd(&s_nnb, 1);
                 if (slot < kMaxNb) s_nb[slot] = make_float4(d0, d1, d2, __int_as_float(pj));
             }
         }
-        if (__syncthreads_or(ov)) {
+        if (cta_any<WARP>(ov)) {
             ++c_ov;
             continue;
         }
-        const int nnb = s_nnb;
+        if (!WARP) nnb = s_nnb;
         if (nnb > kMaxNb) {
             if (tid == 0) atomicCAS(P.err, kErrNone, kErrCandCap);
             return;
@@ -590,74 +610,84 @@ __global__ void __launch_bounds__(kMaxThreads)
             const int n_p = hd.x;
             c_drawn += (unsigned long long)n_p;
             DepOutcome o = {1.0, 0, 0, 0u, 0u, 0u, 0u, 0u, 0u};
-            {
-                // a6: the lens points in depletant order; one free of every
-                // neighbour blocks the move (or enters the CB weight)
-                const int n_lens = hd.z;
-                const float4 *lens = s_loff[q] >= 0 ? s_lens + s_loff[q]
-                                                    : P.lens + (size_t)i * P.lens_cap;
-                for (int m0 = 0; m0 < n_lens; m0 += nthr) {
-                    const int m = m0 + tid;
-                    int cls = 0, kk = 0x7FFFFFFF;
-                    uint32_t tt = 0;
-                    if (m < n_lens) {
-                        const float4 Lm = lens[m];
-                        const uint32_t tk = (uint32_t)__float_as_int(Lm.w);
-                        kk = (int)(tk & 0xFFFFu);
-                        tt = tk >> 16;
-                        bool unsure = false, hit = false;
-                        for (int b = 0; b < nnb; ++b) {
-                            const float4 d = s_nb[b];
-                            const int tn = tri(norm2f(Lm.x - d.x, Lm.y - d.y, Lm.z - d.z),
-                                               P.T_dep32, P.m_r2);
-                            if (tn == 1) {
-                                hit = true;
-                                break;
-                            }
-                            unsure = unsure || tn == -1;
-                        }
-                        cls = hit ? 0 : (unsure ? -1 : 1);
-                    }
-                    {
-                        const bool unsure = cls == -1;
-                        if (__any_sync(kFull, unsure)) {
-                            if (unsure) {
-                                ++o.rck;
-                                cls = exact_free_nb(P, sweep, i, tt, s_nb, nnb, s_accl, nacc) ? 1
-                                                                                              : 0;
-                            }
-                        }
-                    }
-                    const bool blocking = cls == 1;
-                    if (!CB) {
-                        if (blocking) atomicMin(&sh.kmin, kk);
-                        if (__syncthreads_or(blocking)) {
-                            o.block += 1;
-                            o.eval += (uint32_t)(sh.kmin + 1);
-                            o.rejected = 1;
+            // a6: the lens points in depletant order; one free of every
+            // neighbour blocks the move (or enters the CB weight)
+            const int n_lens = hd.z;
+            const float4 *lens = s_loff[q] >= 0 ? s_lens + s_loff[q]
+                                                : P.lens + (size_t)i * P.lens_cap;
+            if (!CB && !WARP) {
+                if (tid == 0) sh.kmin = 0x7FFFFFFF;
+                __syncthreads();
+            }
+            for (int m0 = 0; m0 < n_lens; m0 += nthr) {
+                const int m = m0 + tid;
+                int cls = 0, kk = 0x7FFFFFFF;
+                uint32_t tt = 0;
+                if (m < n_lens) {
+                    const float4 Lm = lens[m];
+                    const uint32_t tk = (uint32_t)__float_as_int(Lm.w);
+                    kk = (int)(tk & 0xFFFFu);
+                    tt = tk >> 16;
+                    bool unsure = false, hit = false;
+                    for (int b = 0; b < nnb; ++b) {
+                        const float4 d = s_nb[b];
+                        const int tn = tri(norm2f(Lm.x - d.x, Lm.y - d.y, Lm.z - d.z),
+                                           P.T_dep32, P.m_r2);
+                        if (tn == 1) {
+                            hit = true;
                             break;
                         }
+                        unsure = unsure || tn == -1;
+                    }
+                    cls = hit ? 0 : (unsure ? -1 : 1);
+                }
+                {
+                    const bool unsure = cls == -1;
+                    if (__any_sync(kFull, unsure)) {
+                        if (unsure) {
+                            ++o.rck;
+                            cls = exact_free_nb(P, sweep, i, tt, s_nb, nnb, s_accl, nacc) ? 1 : 0;
+                        }
+                    }
+                }
+                const bool blocking = cls == 1;
+                if (!CB) {
+                    int kmin;
+                    bool any;
+                    if (WARP) {
+                        kmin = __reduce_min_sync(kFull, blocking ? kk : 0x7FFFFFFF);
+                        any = kmin != 0x7FFFFFFF;
                     } else {
-                        double f = -1.0;
-                        if (blocking) {
-                            const CbResult32 r = cb_factor_fp32(P, sweep, i, (uint32_t)kk, o0, o1,
-                                                                o2, s_nb, nnb, s_accl, nacc);
-                            f = r.f;
-                            o.fwd += r.fwd_ok;
-                            o.rev += r.rev_ok;
-                            o.cap += r.caps;
-                            o.rck += r.rck;
-                        }
-                        if (cb_pass(sh, tid, nthr, f, kk, o, -1)) {
-                            o.rejected = 1;
-                            break;
-                        }
+                        if (blocking) atomicMin(&sh.kmin, kk);
+                        any = __syncthreads_or(blocking) != 0;
+                        kmin = sh.kmin;
+                    }
+                    if (any) {
+                        o.block += 1;
+                        o.eval += (uint32_t)(kmin + 1);
+                        o.rejected = 1;
+                        break;
+                    }
+                } else {
+                    double f = -1.0;
+                    if (blocking) {
+                        const CbResult32 r = cb_factor_fp32(P, sweep, i, (uint32_t)kk, o0, o1, o2,
+                                                            s_nb, nnb, s_accl, nacc);
+                        f = r.f;
+                        o.fwd += r.fwd_ok;
+                        o.rev += r.rev_ok;
+                        o.cap += r.caps;
+                        o.rck += r.rck;
+                    }
+                    if (cb_pass(sh, tid, nthr, f, kk, o, -1)) {
+                        o.rejected = 1;
+                        break;
                     }
                 }
-                if (!o.rejected) {
-                    o.eval += (uint32_t)hd.y;
-                    if (hd.y < n_p && tid == 0) ++o.cap;
-                }
+            }
+            if (!o.rejected) {
+                o.eval += (uint32_t)hd.y;
+                if (hd.y < n_p && tid == 0) ++o.cap;
             }
             c_eval += o.eval;
             c_block += o.block;
@@ -670,16 +700,20 @@ __global__ void __launch_bounds__(kMaxThreads)
                 if (!CB) ++c_dep;
                 else ++c_cb;
             } else if (CB && tid == 0 && o.nblock > 0) {
-                const uint4 wa = draw(P.key0, P.key1, sweep, tag, kPAccept, 0, 0);
+                const uint4 wa = draw(P.key0, P.key1, sweep, (uint32_t)i, kPAccept, 0, 0);
                 if (!(u53(wa.x, wa.y) < o.W)) {
                     accept = false;
                     ++c_cb;
                 }
             }
             if (CB) {
-                if (tid == 0) s_acc = accept ? 1 : 0;
-                __syncthreads();
-                accept = s_acc != 0;
+                if (WARP) {
+                    accept = __shfl_sync(kFull, accept ? 1 : 0, 0) != 0;
+                } else {
+                    if (tid == 0) s_acc = accept ? 1 : 0;
+                    __syncthreads();
+                    accept = s_acc != 0;
+                }
             }
         }
         // a8: accepted: the FP32 working copies move now (shared neighbourhood
@@ -695,7 +729,7 @@ __global__ void __launch_bounds__(kMaxThreads)
                 s_nacc = nacc + 1;
             }
         }
-        __syncthreads();
+        cta_sync<WARP>();
     }
 
     // deferred FP64 commit of the accepted moves, one colloid per lane
@@ -707,8 +741,8 @@ __global__ void __launch_bounds__(kMaxThreads)
 
     unsigned long long cnt[kNumCounters] = {0};
     if (tid == 0) {
-        cnt[kMoves] = c_moves;
-        cnt[kTranslate] = c_moves;
+        cnt[kMoves] = (unsigned long long)n_own;
+        cnt[kTranslate] = (unsigned long long)n_own;
         cnt[kAccept] = c_acc;
         cnt[kRejCell] = c_cell;
         cnt[kRejOverlap] = c_ov;
