@@ -9,7 +9,8 @@ reservoir packing fraction eta_r in {0.1, 0.2, 0.3, 0.4} (four independent
 systems), translation step tuned (untimed) to ~30% acceptance, n_trial = 0,
 FP32 + certified-margin form (``--precision fp64`` for the plain FP64 form).
 One step = one checkerboard sweep of each of the four systems (4 x 16384
-trial moves).  Synthetic, seeded inputs (fcc start, melted during tuning).
+trial moves), run as one batch of four independent replicas.  Synthetic,
+seeded inputs (fcc start, melted during tuning).
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on
 the launching stream, with a 256 MB buffer written between steps to flush L2
@@ -181,17 +182,21 @@ def run_reference(args, ws, rank):
     print(json.dumps(line))
 
 
-def tune(smp, hpmc, d0, rounds=12, sweeps=15):
-    """Untimed: melt the lattice start and tune d_max to ~30% acceptance."""
-    d = d0
+def tune_batch(ctx, hpmc, d0, ns, rounds=12, sweeps=15):
+    """Untimed: melt the lattice starts and tune each replica's d_max to ~30%
+    acceptance (per-replica counters)."""
+    d = list(d0)
     for _ in range(rounds):
-        hpmc.hpmc_set_moves(smp.ctx, d, 0.0, 1.0)
-        hpmc.hpmc_reset_counters(smp.ctx)
-        smp.sweep(sweeps)
-        _, cnt = hpmc.hpmc_get_state(smp.ctx)
-        acc = cnt["accept"] / max(1, cnt["moves"])
-        d = d * min(2.0, max(0.5, (acc + 0.02) / (ACC_TARGET + 0.02)))
-    hpmc.hpmc_set_moves(smp.ctx, d, 0.0, 1.0)
+        for r, dr in enumerate(d):
+            hpmc.hpmc_set_replica_moves(ctx, r, dr, 0.0, 1.0)
+        hpmc.hpmc_reset_counters(ctx)
+        hpmc.hpmc_sweep(ctx, sweeps)
+        for r, n in enumerate(ns):
+            _, _, cnt = hpmc.hpmc_get_replica(ctx, r, n)
+            acc = cnt["accept"] / max(1, cnt["moves"])
+            d[r] = d[r] * min(2.0, max(0.5, (acc + 0.02) / (ACC_TARGET + 0.02)))
+    for r, dr in enumerate(d):
+        hpmc.hpmc_set_replica_moves(ctx, r, dr, 0.0, 1.0)
     return d
 
 
@@ -211,43 +216,29 @@ def run_ours(args, ws, rank, local):
     prec = hpmc.HPMC_FP32_RECHECK if args.precision == "fp32" else hpmc.HPMC_FP64
     stream = torch.cuda.current_stream()
 
+    # the four state points as one batch (independent replicas, one set of
+    # launches per sweep); this rank's replicas are keyed by its rank
     systems = [W.spheres_16384(eta, seed=1) for eta in ETAS]
-    smps, dmax = [], {}
-    for s in systems:
-        eta = round(s.extra["eta_r"], 1)
-        smp = hpmc.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=D_MAX_TUNED[eta], seed=1,
-                           replica=rank, precision=prec, warps=args.warps, ilp=args.ilp,
-                           device=local)
-        dmax[eta] = tune(smp, hpmc, D_MAX_TUNED[eta]) if not args.no_tune else D_MAX_TUNED[eta]
-        smps.append(smp)
+    etas = [round(s.extra["eta_r"], 1) for s in systems]
+    descs = [{"n": s.n, "box_l": s.L, "pos": s.pos, "q": s.q, "n_r": s.n_r, "n_trial": 0,
+              "d_max": D_MAX_TUNED[e], "replica": rank * len(systems) + k}
+             for k, (s, e) in enumerate(zip(systems, etas))]
+    ctx = hpmc.hpmc_init_batch(descs, seed=1, precision=prec, device=local)
+    hpmc.hpmc_set_launch(ctx, args.warps, args.ilp)
+    ns = [s.n for s in systems]
+    d0 = [D_MAX_TUNED[e] for e in etas]
+    dtuned = d0 if args.no_tune else tune_batch(ctx, hpmc, d0, ns)
+    dmax = dict(zip(etas, dtuned))
     torch.cuda.synchronize()
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    # the four state points are independent systems: each runs on its own
-    # stream, forked from and joined back into the timing stream
-    side = [torch.cuda.Stream() for _ in smps]
-    fork = torch.cuda.Event()
-    joins = [torch.cuda.Event() for _ in smps]
 
-    def step_concurrent():
-        fork.record(stream)
-        for smp, st, ev in zip(smps, side, joins):
-            st.wait_event(fork)
-            smp.sweep(1, st)
-            ev.record(st)
-        for ev in joins:
-            stream.wait_event(ev)
-
-    def step_sequential():
-        for smp in smps:
-            smp.sweep(1, stream)
-
-    step = step_sequential if args.sequential else step_concurrent
+    def step():
+        hpmc.hpmc_sweep(ctx, 1, stream)
 
     for _ in range(args.warmup):
         step()
-    for smp in smps:
-        hpmc.hpmc_reset_counters(smp.ctx)
+    hpmc.hpmc_reset_counters(ctx)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -265,57 +256,60 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         dist.barrier()
     ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
-    counters = [hpmc.hpmc_get_state(smp.ctx)[1] for smp in smps]
-    # the same systems one at a time (context for the concurrent number)
+    _, cnt = hpmc.hpmc_get_state(ctx)
+    moves, drawn, evaluated = cnt["moves"], cnt["dep_drawn"], cnt["dep_evaluated"]
+    rechecks, accept = cnt["rechecks"], cnt["accept"]
+
+    # per-kernel durations (events around each launch, kernels launched one by one)
+    hpmc.hpmc_reset_counters(ctx)
+    hpmc.hpmc_set_timing(ctx, True)
+    timing_steps = min(args.steps, 50)
+    for k in range(timing_steps):
+        flush.zero_()
+        step()
+    kern_ms, kern_n = hpmc.hpmc_get_timing(ctx)
+    hpmc.hpmc_set_timing(ctx, False)
+    _, tc = hpmc.hpmc_get_state(ctx)
+    t_moves, t_eval, t_drawn = tc["moves"], tc["dep_evaluated"], tc["dep_drawn"]
+
+    # the same four systems one at a time (separate contexts, one stream)
+    allpos = np.empty((sum(ns), 3))
+    sweep_now, _ = hpmc.hpmc_get_state(ctx, allpos)
+    singles = []
+    off = 0
+    for k, s in enumerate(systems):
+        smp = hpmc.Sampler(allpos[off:off + s.n].copy(), s.L, q=s.q, n_r=s.n_r,
+                           d_max=dtuned[k], seed=1, replica=descs[k]["replica"],
+                           precision=prec, warps=args.warps, ilp=args.ilp, device=local)
+        hpmc.hpmc_set_state(smp.ctx, allpos[off:off + s.n].copy(), None, sweep_now)
+        smp.sweep(1)
+        singles.append(smp)
+        off += s.n
+    torch.cuda.synchronize()
     seq_steps = min(args.steps, 50)
     sa = [torch.cuda.Event(enable_timing=True) for _ in range(seq_steps)]
     sb = [torch.cuda.Event(enable_timing=True) for _ in range(seq_steps)]
     for k in range(seq_steps):
         flush.zero_()
         sa[k].record(stream)
-        step_sequential()
+        for smp in singles:
+            smp.sweep(1, stream)
         sb[k].record(stream)
     torch.cuda.synchronize()
     seq_ms = sum(a.elapsed_time(b) for a, b in zip(sa, sb))
-    moves = sum(c["moves"] for c in counters)
-    drawn = sum(c["dep_drawn"] for c in counters)
-    evaluated = sum(c["dep_evaluated"] for c in counters)
-    rechecks = sum(c["rechecks"] for c in counters)
-    accept = sum(c["accept"] for c in counters)
-
-    # per-kernel durations (events around each launch, kernels launched one by one)
-    for smp in smps:
-        hpmc.hpmc_reset_counters(smp.ctx)
-        hpmc.hpmc_set_timing(smp.ctx, True)
-    timing_steps = min(args.steps, 50)
-    for k in range(timing_steps):
-        flush.zero_()
-        step_sequential()
-    kern_ms = [0.0, 0.0, 0.0]
-    kern_n = [0, 0, 0]
-    for smp in smps:
-        t, n = hpmc.hpmc_get_timing(smp.ctx)
-        hpmc.hpmc_set_timing(smp.ctx, False)
-        kern_ms = [a + b for a, b in zip(kern_ms, t)]
-        kern_n = [a + b for a, b in zip(kern_n, n)]
-    tc = [hpmc.hpmc_get_state(smp.ctx)[1] for smp in smps]
-    t_moves = sum(c["moves"] for c in tc)
-    t_eval = sum(c["dep_evaluated"] for c in tc)
-    t_drawn = sum(c["dep_drawn"] for c in tc)
+    for smp in singles:
+        smp.close()
 
     # end to end through the C ABI with host buffers (pinned), copies timed
-    host_pos = [torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy() for _ in smps]
-    for smp, hp in zip(smps, host_pos):
-        hpmc.hpmc_get_state(smp.ctx, hp)
-    sweeps_now = [hpmc.hpmc_get_state(smp.ctx)[0] for smp in smps]
+    host_pos = torch.empty((sum(ns), 3), dtype=torch.float64).pin_memory().numpy()
+    sweep_now, _ = hpmc.hpmc_get_state(ctx, host_pos)
     torch.cuda.synchronize()
-    e2e_steps = max(3, args.steps // 2)
+    e2e_steps = max(3, min(args.steps, 50) // 2)
     t0 = time.perf_counter()
     for k in range(e2e_steps):
-        for j, (smp, hp) in enumerate(zip(smps, host_pos)):
-            hpmc.hpmc_set_state(smp.ctx, hp, None, sweeps_now[j] + k, stream)
-            smp.sweep(1, stream)
-            hpmc.hpmc_get_state(smp.ctx, hp, None, stream)
+        hpmc.hpmc_set_state(ctx, host_pos, None, sweep_now + k, stream)
+        hpmc.hpmc_sweep(ctx, 1, stream)
+        hpmc.hpmc_get_state(ctx, host_pos, None, stream)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
 
@@ -333,7 +327,6 @@ def run_ours(args, ws, rank, local):
         f_peak = 2070.0e6
         peak = sms * ISSUE_LANES_PER_SM * f_peak / 1e12
         if kern_n[2]:
-            # FP32 form: lens kernel (the depletant work) and colour phases
             lens_ops = (OPS_PER_DEP * t_drawn + OPS_PER_MOVE_LENS * t_moves) / kern_n[2]
             phase_ops = OPS_PER_MOVE_PHASE * t_moves / max(1, kern_n[1])
             cand = {"k_lens_sphere_fp32": (kern_ms[2], lens_ops / (lens_launch_ms * 1e-3) / 1e12),
@@ -346,7 +339,7 @@ def run_ours(args, ws, rank, local):
         achieved = cand[dominant][1]
         bytes_per_launch = BYTES_PER_MOVE * t_moves / max(1, kern_n[1])
         value = ws * moves / (ms * 1e-3)
-        e2e_moves = ws * e2e_steps * len(smps) * N
+        e2e_moves = ws * e2e_steps * sum(ns)
         line = {
             "metric": "colloid trial moves/s", "value": value, "unit": "moves/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -354,17 +347,16 @@ def run_ours(args, ws, rank, local):
             "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "form": "FP32+FP64 recheck" if prec == 1 else "FP64",
                        "n_trial": 0, "step": "1 sweep of each of 4 systems (65536 moves)",
-                       "schedule": "4 systems one at a time" if args.sequential
-                                   else "4 systems concurrently (one stream each)",
+                       "schedule": "4 systems as one batch (one set of launches per sweep)",
                        "d_max": {str(k): round(v, 5) for k, v in dmax.items()},
                        "l2": "flushed between steps (256 MB write)",
                        "warps_per_colloid": args.warps, "attempts_per_thread": args.ilp},
-            "one_at_a_time_moves_per_s": ws * seq_steps * len(smps) * N / (seq_ms * 1e-3),
+            "one_at_a_time_moves_per_s": ws * seq_steps * sum(ns) / (seq_ms * 1e-3),
             "insertions_drawn_per_s": ws * drawn / (ms * 1e-3),
             "insertions_evaluated_per_s": ws * evaluated / (ms * 1e-3),
             "acceptance": accept / max(1, moves),
             "fp64_rechecks_per_move": rechecks / max(1, moves),
-            "gpu_launches": args.steps * len(smps) * (1 + (1 if prec == 1 else 0) + 8),
+            "gpu_launches": args.steps * (1 + (1 if prec == 1 else 0) + 8),
             "kernels": {"phase_ms_per_launch": phase_launch_ms,
                         "lens_ms_per_launch": lens_launch_ms,
                         "cells_ms_per_sweep": kern_ms[0] / max(1, kern_n[0]),
@@ -378,8 +370,8 @@ def run_ours(args, ws, rank, local):
                          "hbm_achieved_gbs": bytes_per_launch / (phase_launch_ms * 1e-3) / 1e9},
             "clocks": clocks,
             "e2e": {"value": e2e_moves / e2e_s, "unit": "moves/s",
-                    "h2d_bytes_per_step": len(smps) * N * 3 * 8,
-                    "d2h_bytes_per_step": len(smps) * (N * 3 * 8 + 8 * 16)},
+                    "h2d_bytes_per_step": sum(ns) * 3 * 8,
+                    "d2h_bytes_per_step": sum(ns) * 3 * 8 + 8 * 16},
         }
         if not args.no_cpu_baseline:
             # the oracle on the host on a bounded sample of the same workload
@@ -392,8 +384,7 @@ def run_ours(args, ws, rank, local):
                           "(%d moves, %.1f s)" % (args.cpu_sweeps, nm, dt),
                 "insertions_evaluated_per_s": ev}
         print(json.dumps(line))
-    for smp in smps:
-        smp.close()
+    hpmc.hpmc_destroy(ctx)
     if ws > 1:
         dist.destroy_process_group()
 
@@ -408,8 +399,6 @@ def main():
     ap.add_argument("--warps", type=int, default=1)
     ap.add_argument("--ilp", type=int, default=1)
     ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--sequential", action="store_true",
-                    help="sweep the four systems one after another on one stream")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sweeps", type=int, default=25)
     args = ap.parse_args()

@@ -92,6 +92,42 @@ int hpmc_init(hpmc_ctx **out, int n, double box_l, const double *pos,
               const double *quat, int mem, uint64_t seed, uint32_t replica,
               int precision, int device);
 
+/* One replica of a batch: an independent system with its own state point.
+ * Pointers are host memory, read during hpmc_init_batch only. */
+typedef struct hpmc_replica_desc {
+    int n;                  /* colloids */
+    double box_l;           /* cubic box side */
+    const double *pos;      /* n x 3, each coordinate in [0, box_l) */
+    const double *quat;     /* n x 4 unit quaternions, or NULL = identity */
+    double q, n_r;          /* depletant diameter and fugacity z_p */
+    int n_trial;            /* configurational-bias reinsertions (0 = none) */
+    double d_max, a_max, p_translate;  /* trial moves, as hpmc_set_moves */
+    uint32_t replica;       /* key word of this replica's random streams */
+    int n_cell;             /* checkerboard cells per side (even), 0 = largest valid */
+} hpmc_replica_desc;
+
+/* A batch of n_rep independent replica systems in one context, all of the
+ * same shape (params as hpmc_set_shape), keyed by (seed, desc[r].replica).
+ * Every hpmc_sweep advances all replicas by one sweep in one set of kernel
+ * launches covering the whole batch; a replica's trajectory is identical to
+ * that of the same system alone in its own context.  Positions of the batch
+ * (hpmc_get_state / hpmc_set_state) are the replicas' arrays one after the
+ * other in replica order; counters from hpmc_get_state are summed over
+ * replicas.  The parameter setters below apply to every replica. */
+int hpmc_init_batch(hpmc_ctx **out, int n_rep, const hpmc_replica_desc *desc, int shape,
+                    const double *shape_params, int nparams, uint64_t seed, int precision,
+                    int device);
+
+/* Replica r of a batch: positions (n x 3), orientations (n x 4) and its own
+ * counters, each optional (NULL), into host memory.  Synchronises. */
+int hpmc_get_replica(hpmc_ctx *ctx, int r, double *pos, double *quat,
+                     hpmc_counters *counters);
+
+/* Trial-move parameters of replica r only (e.g. a step size tuned per
+ * replica); as hpmc_set_moves otherwise. */
+int hpmc_set_replica_moves(hpmc_ctx *ctx, int r, double d_max, double a_max,
+                           double p_translate);
+
 /* Colloid shape (Sec. II; hemisphere Sec. V.A; discoid = oblate spheroid
  * a = b, c < a, Sec. V.B).  params/nparams as listed at HPMC_SPHERE etc. */
 int hpmc_set_shape(hpmc_ctx *ctx, int kind, const double *params, int nparams);

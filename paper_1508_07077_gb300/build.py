@@ -18,7 +18,8 @@ LIBDIR = os.path.join(HERE, "_lib")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-shared",
-                 "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "-I", INCLUDE]
+                 "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "-I", INCLUDE,
+                 "-diag-suppress", "1444"]
 
 TARGETS = {
     "libhpmc_dep.so": (["hpmc_dep.cu"], ["hpmc_common.cuh", "hpmc_cells.cuh", "hpmc_misc.cuh",

@@ -14,36 +14,39 @@
 
 namespace hpmc {
 
-// One thread per colloid.  Block 0 thread 0 also writes the sweep's schedule.
+// One thread per colloid of the batch.  The first colloid of each replica
+// also writes that replica's schedule.
 __global__ void k_cells_bin(const __grid_constant__ SimParams P)
 {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= P.n_total) return;
+    const int r = P.rep_of[g];
+    const Rep &R = P.reps[r];
     const uint32_t sweep = (uint32_t)(*P.sweep);
     double sigma[3];
-    schedule_shift(P.key0, P.key1, sweep, P.w, sigma);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    schedule_shift(R.key0, R.key1, sweep, R.w, sigma);
+    if (g == R.off) {
         Sched s;
         s.sigma[0] = sigma[0];
         s.sigma[1] = sigma[1];
         s.sigma[2] = sigma[2];
-        schedule_perm(P.key0, P.key1, sweep, s.perm);
+        schedule_perm(R.key0, R.key1, sweep, s.perm);
         s.sweep = sweep;
-        *P.sched = s;
+        P.sched[r] = s;
     }
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
-    const double4 p = P.pos[i];
-    const int nc = P.nc;
-    const int cx = cell_coord(p.x, sigma[0], P.L, P.w, nc);
-    const int cy = cell_coord(p.y, sigma[1], P.L, P.w, nc);
-    const int cz = cell_coord(p.z, sigma[2], P.L, P.w, nc);
-    const int c = cx + nc * (cy + nc * cz);
-    const float4 r = make_float4(cell_rel(p.x, sigma[0], P.L, P.w, cx),
-                                 cell_rel(p.y, sigma[1], P.L, P.w, cy),
-                                 cell_rel(p.z, sigma[2], P.L, P.w, cz), __int_as_float(i));
+    const double4 p = P.pos[g];
+    const int nc = R.nc;
+    const int cx = cell_coord(p.x, sigma[0], R.L, R.w, nc);
+    const int cy = cell_coord(p.y, sigma[1], R.L, R.w, nc);
+    const int cz = cell_coord(p.z, sigma[2], R.L, R.w, nc);
+    const int c = R.cell_off + cx + nc * (cy + nc * cz);
+    const float4 rl = make_float4(cell_rel(p.x, sigma[0], R.L, R.w, cx),
+                                  cell_rel(p.y, sigma[1], R.L, R.w, cy),
+                                  cell_rel(p.z, sigma[2], R.L, R.w, cz), __int_as_float(g));
     const int slot = atomicAdd(P.count[sweep & 1u] + c, 1);
-    if (slot < P.cap) P.bins[(size_t)c * P.cap + slot] = r;
+    if (slot < P.cap) P.bins[(size_t)c * P.cap + slot] = rl;
     else atomicCAS(P.err, kErrNone, kErrCellCap);
-    P.rel[i] = r;
+    P.rel[g] = rl;
 }
 
 // --- CSR layout ------------------------------------------------------------

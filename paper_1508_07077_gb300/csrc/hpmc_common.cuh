@@ -22,7 +22,7 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kMaxCand = 256;        // colloids in a 27-cell neighbourhood (capacity)
 constexpr int kMaxThreads = 256;     // 8 warps per colloid at most
 constexpr int kMaxCellCap = 64;      // colloids per cell bin (capacity)
-constexpr int kCounterSlots = 128;   // counters are spread over slots to avoid hot atomics
+constexpr int kRepSlots = 16;        // per replica, counters are spread over slots (fewer hot atomics)
 constexpr int kNumCounters = 16;
 
 enum Counter {
@@ -77,7 +77,8 @@ __device__ __forceinline__ double u53(uint32_t a, uint32_t b)
 }
 
 // ---------------------------------------------------------------------------
-// Parameters shared by the kernels of one sweep.
+// Parameters.  A context is a batch of independent replica systems (one for a
+// single system); every kernel covers all replicas of the batch in one launch.
 // ---------------------------------------------------------------------------
 struct Sched {
     double sigma[3];
@@ -85,39 +86,51 @@ struct Sched {
     uint32_t sweep;   // sweep index these kernels run
 };
 
-struct SimParams {
-    int n, nc, half_nc, n_stencil, cap;
+// One replica: its system, its parameters and where its data sit in the
+// batch-wide arrays.  Colloid arrays are indexed by the global colloid index
+// g = off + i (i the colloid's index inside its replica, also its RNG stream).
+struct Rep {
+    int n, off;            // colloids, first global colloid index
+    int nc, half_nc, n_stencil;
+    int cell_off;          // first global cell index
+    int cta_off;           // first CTA of this replica in a colour-phase grid
+    int nF, t_off;         // Poisson table length and offset in the batch table
+    int has_dep, n_trial;
+    uint32_t key0, key1;
     double L, half_L, w;
-    int shape, n_trial, has_dep, nF;
     double R_s, R_s2;      // sampling sphere radius (R_circ + q/2) and its square
     double R_dep2;         // sphere-depletant contact distance squared
     double contact2;       // sphere-sphere contact distance squared
     double nb_cut2;        // neighbours farther than this cannot meet a depletant
-    double d_max, alpha, p_translate;
-    int move_mode;         // 0 translate only, 1 rotate only, 2 both
-    uint32_t key0, key1;
+    double d_max;
     // FP32 form: thresholds rounded to float, and the certified margins
     float w32, L32, half_L32, R_s32, T_s32, T_dep32, T_contact32, nb_cut2_32, d_max32;
     float m_r2;            // bound on |r2_fp32 - r2_fp64| (+ threshold rounding), doubled
     float m_cell;          // bound on the error of a cell-relative coordinate
+};
+
+struct SimParams {
+    int n_rep, n_total, cap, lens_cap;
+    const Rep *reps;
+    const int *rep_of;     // global colloid index -> replica
+    const int *cta_rep;    // CTA of a colour-phase grid -> replica
     double4 *pos;
     double4 *quat;
     float4 *rel;           // FP32 position relative to the origin of its cell (this sweep)
     int *count[2];         // per-cell populations, double-buffered by sweep parity
-    float4 *bins;          // [ncell][cap] (FP32 offset from the cell origin, index bits in .w),
-                           // unordered within a cell
-    const unsigned long long *T;   // Poisson CDF table as integers ceil(F[k] 2^53)
+    float4 *bins;          // [cell][cap] (FP32 offset from the cell origin, global index bits
+                           // in .w), unordered within a cell
+    const unsigned long long *T;   // Poisson CDF tables as integers ceil(F[k] 2^53)
     // per-colloid depletant "lens" lists of this sweep (FP32 form):
-    // lens[i][0..n) = (e, (t << 16) | k) of the depletants that overlap the new
-    // pose and not the old one, in depletant order; lens_hdr[i] = (N_p,
-    // depletants obtained from the stream, n or -1 if the list overflowed, 0)
+    // lens[g][0..n) = (e, (t << 16) | k) of the depletants that overlap the new
+    // pose and not the old one, in depletant order; lens_hdr[g] = (N_p,
+    // depletants obtained from the stream, n, 0)
     float4 *lens;
     int4 *lens_hdr;
     float4 *lens_move;     // the move's FP32 displacement (the phase kernels reuse it)
-    int lens_cap;
-    Sched *sched;
-    unsigned long long *sweep;     // next sweep index
-    unsigned long long *counters;
+    Sched *sched;          // per replica
+    unsigned long long *sweep;     // next sweep index (all replicas)
+    unsigned long long *counters;  // [n_rep][kRepSlots][kNumCounters]
     int *err;
 };
 
@@ -213,35 +226,38 @@ __device__ __forceinline__ int poisson_count(const unsigned long long *T, int nF
 }
 
 // ---------------------------------------------------------------------------
-// Per-CTA set-up of a colour phase: which cell this CTA owns, its members in
-// ascending index (the order moves are made in), and the zeroing of the
-// other count buffer for the next sweep.
+// Per-CTA set-up of a colour phase: which replica and cell this CTA owns, and
+// the zeroing of the other count buffer for the next sweep.
 // ---------------------------------------------------------------------------
 struct CellTask {
-    int cx, cy, cz, cell, n_own;
-    int *count;        // this sweep's populations
+    int r;                 // replica
+    int cx, cy, cz;        // cell coordinates inside the replica
+    int cell;              // global cell index
+    int n_own;
+    int *count;            // this sweep's populations (global cell index)
 };
 
-__device__ __forceinline__ CellTask cell_task(const SimParams &P, const Sched &S, int phase)
+__device__ __forceinline__ CellTask cell_task(const SimParams &P, const Rep &R, int r, int phase)
 {
     CellTask t;
-    const int colour = P.sched->perm[phase];
-    const int h = P.half_nc, nc = P.nc;
-    const int a = blockIdx.x;
+    t.r = r;
+    const int colour = P.sched[r].perm[phase];
+    const int h = R.half_nc, nc = R.nc;
+    const int a = blockIdx.x - R.cta_off;
     t.cx = 2 * (a % h) + (colour & 1);
     t.cy = 2 * ((a / h) % h) + ((colour >> 1) & 1);
     t.cz = 2 * (a / (h * h)) + ((colour >> 2) & 1);
-    t.cell = t.cx + nc * (t.cy + nc * t.cz);
-    t.count = P.count[S.sweep & 1u];
+    t.cell = R.cell_off + t.cx + nc * (t.cy + nc * t.cz);
+    t.count = P.count[P.sched[r].sweep & 1u];
     t.n_own = t.count[t.cell];
     return t;
 }
 
 // Every cell is owned by exactly one CTA of one phase per sweep: that CTA
 // zeroes the cell in the other buffer, which the next sweep fills.
-__device__ __forceinline__ void clear_next(const SimParams &P, const Sched &S, int cell)
+__device__ __forceinline__ void clear_next(const SimParams &P, uint32_t sweep, int cell)
 {
-    if (threadIdx.x == 0) P.count[(S.sweep + 1u) & 1u][cell] = 0;
+    if (threadIdx.x == 0) P.count[(sweep + 1u) & 1u][cell] = 0;
 }
 
 // Sort the own cell's members into s_own[0..n) ascending (n <= kMaxCellCap).
@@ -261,12 +277,12 @@ __device__ __forceinline__ void own_members_sorted(const SimParams &P, int cell,
     __syncthreads();
 }
 
-// Neighbour cell (index and geometric offset in cells) number `t` of the
-// deduplicated 27-cell stencil of (cx, cy, cz).
-__device__ __forceinline__ int stencil_cell(const SimParams &P, int t, int cx, int cy, int cz,
-                                            int &dx, int &dy, int &dz)
+// Neighbour cell (global index, and geometric offset in cells) number `t` of
+// the deduplicated 27-cell stencil of (cx, cy, cz).
+__device__ __forceinline__ int stencil_cell(const Rep &R, int t, int cx, int cy, int cz, int &dx,
+                                            int &dy, int &dz)
 {
-    const int ns = P.n_stencil, nc = P.nc;
+    const int ns = R.n_stencil, nc = R.nc;
     const int ox = t % ns, oy = (t / ns) % ns, oz = t / (ns * ns);
     int nx, ny, nz;
     if (nc == 2) {
@@ -278,15 +294,24 @@ __device__ __forceinline__ int stencil_cell(const SimParams &P, int t, int cx, i
         nz = (cz + oz - 1 + nc) % nc;
         dx = ox - 1; dy = oy - 1; dz = oz - 1;
     }
-    return nx + nc * (ny + nc * nz);
+    return R.cell_off + nx + nc * (ny + nc * nz);
 }
 
-__device__ __forceinline__ void flush_counters(const SimParams &P, const unsigned long long *c)
+__device__ __forceinline__ void flush_counters(const SimParams &P, int r,
+                                               const unsigned long long *c)
 {
-    unsigned long long *cnt = P.counters + (size_t)(blockIdx.x % kCounterSlots) * kNumCounters;
+    unsigned long long *cnt =
+        P.counters + ((size_t)r * kRepSlots + (blockIdx.x % kRepSlots)) * kNumCounters;
 #pragma unroll
     for (int k = 0; k < kNumCounters; ++k)
         if (c[k]) atomicAdd(cnt + k, c[k]);
+}
+
+__device__ __forceinline__ void count_one(const SimParams &P, int r, int k,
+                                          unsigned long long v)
+{
+    atomicAdd(P.counters + ((size_t)r * kRepSlots + (blockIdx.x % kRepSlots)) * kNumCounters + k,
+              v);
 }
 
 }  // namespace hpmc

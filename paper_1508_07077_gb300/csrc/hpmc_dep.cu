@@ -1,9 +1,9 @@
 // C ABI of the GB300 implicit-depletant HPMC library (see include/hpmc_dep.h).
 //
-// Host side: parameter validation, the Poisson table (Sec. III.B step 2), the
-// checkerboard geometry (Sec. III.E), device buffers, and one CUDA graph per
-// sweep (cell list, 8 colour phases, sweep counter).  All per-step arithmetic
-// runs in the kernels of hpmc_kernels.cuh.
+// Host side: parameter validation, the Poisson tables (Sec. III.B step 2), the
+// checkerboard geometry of every replica (Sec. III.E), device buffers, and one
+// CUDA graph per sweep of the whole batch (cell lists, depletant lens lists,
+// 8 colour phases).  All per-step arithmetic runs in the kernels.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -28,47 +28,53 @@ namespace {
 constexpr double kPi = 3.141592653589793;
 constexpr int kTableCap = 32768;
 
-
+// parameters shared by every replica of a context
 struct Params {
     int shape = HPMC_SPHERE;
     double sp[4] = {1.0, 0.0, 0.0, 0.0};
     int nsp = 1;
-    double q = 0.0, n_r = 0.0;
-    int n_trial = 0;
-    double d_max = 0.1, a_max = 0.0, p_translate = 1.0;
-    int nc_req = 0;
     int warps = 1;
     int ilp = 1;
     double margin = 0.0;
+};
+
+// one replica as the caller described it
+struct RepHost {
+    int n = 0;
+    double L = 0.0;
+    double q = 0.0, n_r = 0.0;
+    int n_trial = 0;
+    double d_max = 0.1, a_max = 0.0, p_translate = 1.0;
+    uint32_t replica = 0;
+    int nc_req = 0;
 };
 
 }  // namespace
 
 struct hpmc_ctx {
     int device = 0;
-    int n = 0;
-    double L = 0.0;
     uint64_t seed = 0;
-    uint32_t replica = 0;
     int precision = HPMC_FP64;
     Params prm;
-
-    // derived
-    int nc = 0;
-    double w = 0.0, R_circ = 0.5, R_s = 0.5, lambda = 0.0;
-    int nF = 0;
+    std::vector<RepHost> reps;
+    std::vector<Rep> rdev;        // derived per-replica records (host copy)
+    int n_total = 0, n_cells = 0, n_cta = 0, nF_max = 0;
 
     // device buffers
     double4 *d_pos = nullptr, *d_quat = nullptr;
     float4 *d_rel = nullptr;
-    double *d_stage = nullptr;  // n x 4 doubles: layout conversion for device callers
-    int *d_count = nullptr;   // 2 x ncell populations (double-buffered by sweep parity)
-    float4 *d_bins = nullptr; // ncell x cap (cell offset, index)
-    int ncell_alloc = -1;
-    float4 *d_lens = nullptr; // n x lens_cap depletant lens points (FP32 form)
+    double *d_stage = nullptr;    // n_total x 4 doubles: layout conversion
+    int *d_count = nullptr;       // 2 x n_cells populations (double-buffered by sweep parity)
+    float4 *d_bins = nullptr;     // n_cells x cap (cell offset, global index)
+    int cells_alloc = -1;
+    float4 *d_lens = nullptr;     // n_total x lens_cap depletant lens points (FP32 form)
     int4 *d_lens_hdr = nullptr;
     float4 *d_lens_move = nullptr;
     int lens_cap = 0;
+    Rep *d_reps = nullptr;
+    int *d_rep_of = nullptr;
+    int *d_cta_rep = nullptr;
+    int cta_alloc = -1;
     Sched *d_sched = nullptr;
     unsigned long long *d_T = nullptr;
     unsigned long long *d_sweep = nullptr, *d_counters = nullptr;
@@ -144,73 +150,111 @@ int build_table(double lambda, std::vector<double> &F)
     return HPMC_OK;
 }
 
+// Derive one replica's device record.  Returns HPMC_OK or an error.
+int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> &F)
+{
+    const Params &p = c->prm;
+    std::memset(&R, 0, sizeof R);
+    const double R_circ = circum_radius(p);
+    if (!(R_circ > 0.0)) return HPMC_ERR_ARG;
+    if (!(h.q >= 0.0) || !(h.n_r >= 0.0) || h.n_trial < 0 || h.n_trial > 100000) return HPMC_ERR_ARG;
+    const double R_s = R_circ + 0.5 * h.q;
+    const double v0 = ((4.0 / 3.0) * kPi) * ((R_s * R_s) * R_s);
+    const double lambda = h.n_r > 0.0 ? h.n_r * v0 : 0.0;
+    const double w_min = 2.0 * R_circ + h.q;
+    int nc = h.nc_req;
+    if (nc == 0) {
+        nc = (int)(h.L / w_min);
+        if (nc & 1) nc -= 1;
+    }
+    if (nc < 2 || (nc & 1)) return HPMC_ERR_ARG;
+    if (nc > 1024) return HPMC_ERR_CAP;
+    const double w = h.L / (double)nc;
+    if (w < w_min) return HPMC_ERR_ARG;
+    if (!(h.d_max >= 0.0) || h.d_max >= w) return HPMC_ERR_ARG;
+    // a cell bin holds at most (w + 2 R_circ)^3 * 0.7405 / v colloids of volume v
+    // (densest packing); spheres only for now
+    const double v_shape = (kPi / 6.0) * p.sp[0] * p.sp[0] * p.sp[0];
+    const double ext = w + 2.0 * R_circ;
+    if (ext * ext * ext * 0.7405 / v_shape >= (double)kMaxCellCap) return HPMC_ERR_CAP;
+    F.clear();
+    if (lambda > 0.0) {
+        int rc = build_table(lambda, F);
+        if (rc != HPMC_OK) return rc;
+        // lens points pack the attempt index t < 64 (N_p + 1) into 16 bits
+        if (c->precision == HPMC_FP32_RECHECK && F.size() > 1023) return HPMC_ERR_CAP;
+    }
+    R.n = h.n;
+    R.nc = nc;
+    R.half_nc = nc / 2;
+    R.n_stencil = nc == 2 ? 2 : 3;
+    R.nF = (int)F.size();
+    R.has_dep = lambda > 0.0 ? 1 : 0;
+    R.n_trial = h.n_trial;
+    R.key0 = (uint32_t)c->seed;
+    R.key1 = (uint32_t)(c->seed >> 32) ^ h.replica;
+    R.L = h.L;
+    R.half_L = 0.5 * h.L;
+    R.w = w;
+    R.R_s = R_s;
+    R.R_s2 = R_s * R_s;
+    const double Rd = 0.5 * p.sp[0] + 0.5 * h.q;
+    R.R_dep2 = Rd * Rd;
+    R.contact2 = p.sp[0] * p.sp[0];
+    const double cut = 2.0 * R_s + 0.01;
+    R.nb_cut2 = cut * cut;
+    R.d_max = h.d_max;
+    // FP32 form: thresholds in float and the certified margin.  Every vector a
+    // test forms is a difference of cell-relative coordinates; each component
+    // carries at most E = 40 u max(w, 1) of FP32 error (rounding of the
+    // cell-relative copies, including one FP32 step for a colloid already moved
+    // this sweep, of the displacement, of the bit-built depletant coordinate
+    // (<= 6 u R) and of the differences).  For |v| near a threshold radius R the
+    // squared length then errs by at most 2 sqrt(3) R E + 3 E^2 + 3 u R^2, plus
+    // u R^2 for rounding the threshold itself; the margin is twice that, and at
+    // least 1e-5.
+    const double u = 0x1p-24;
+    const double Wc = w > 1.0 ? w : 1.0;
+    const double E = 40.0 * u * Wc;
+    const double Rmax = std::sqrt(std::fmax(R.R_s2, R.contact2));
+    const double bound = 2.0 * std::sqrt(3.0) * Rmax * E + 3.0 * E * E + 4.0 * u * Rmax * Rmax + 1e-12;
+    const double m_r2 = std::fmax(1e-5, 2.0 * bound);
+    if (p.margin > 0.0 && p.margin < m_r2) return HPMC_ERR_ARG;
+    R.m_r2 = (float)(p.margin > 0.0 ? p.margin : m_r2);
+    R.m_cell = (float)(1e-5 * Wc);
+    R.w32 = (float)w;
+    R.L32 = (float)h.L;
+    R.half_L32 = (float)(0.5 * h.L);
+    R.R_s32 = (float)R_s;
+    R.T_s32 = (float)R.R_s2;
+    R.T_dep32 = (float)R.R_dep2;
+    R.T_contact32 = (float)R.contact2;
+    R.nb_cut2_32 = (float)R.nb_cut2;
+    R.d_max32 = (float)h.d_max;
+    return HPMC_OK;
+}
+
 SimParams make_params(hpmc_ctx *c)
 {
     SimParams P;
     std::memset(&P, 0, sizeof P);
-    const Params &p = c->prm;
-    P.n = c->n;
-    P.nc = c->nc;
-    P.half_nc = c->nc / 2;
-    P.n_stencil = c->nc == 2 ? 2 : 3;
-    P.L = c->L;
-    P.half_L = 0.5 * c->L;
-    P.w = c->w;
-    P.shape = p.shape;
-    P.n_trial = p.n_trial;
-    P.has_dep = c->lambda > 0.0 ? 1 : 0;
-    P.nF = c->nF;
-    P.R_s = c->R_s;
-    P.R_s2 = c->R_s * c->R_s;
-    const double Rd = 0.5 * p.sp[0] + 0.5 * p.q;
-    P.R_dep2 = Rd * Rd;
-    P.contact2 = p.sp[0] * p.sp[0];
-    const double cut = 2.0 * c->R_s + 0.01;
-    P.nb_cut2 = cut * cut;
-    P.d_max = p.d_max;
-    P.alpha = std::tan(0.5 * p.a_max);
-    P.p_translate = p.p_translate;
-    P.move_mode = 0;
-    P.key0 = (uint32_t)c->seed;
-    P.key1 = (uint32_t)(c->seed >> 32) ^ c->replica;
+    P.n_rep = (int)c->reps.size();
+    P.n_total = c->n_total;
+    P.cap = kMaxCellCap;
+    P.lens_cap = c->lens_cap;
+    P.reps = c->d_reps;
+    P.rep_of = c->d_rep_of;
+    P.cta_rep = c->d_cta_rep;
     P.pos = c->d_pos;
     P.quat = c->d_quat;
-    P.cap = kMaxCellCap;
+    P.rel = c->d_rel;
     P.count[0] = c->d_count;
-    P.count[1] = c->d_count ? c->d_count + (size_t)c->nc * c->nc * c->nc : nullptr;
+    P.count[1] = c->d_count ? c->d_count + c->n_cells : nullptr;
     P.bins = c->d_bins;
     P.T = c->d_T;
     P.lens = c->d_lens;
     P.lens_hdr = c->d_lens_hdr;
     P.lens_move = c->d_lens_move;
-    P.lens_cap = c->lens_cap;
-    P.rel = c->d_rel;
-    // FP32 form: thresholds in float and the certified margin.  Every vector a
-    // test forms is a difference of cell-relative coordinates; each component
-    // carries at most E = 32 u max(w, 1) of FP32 error (rounding of the
-    // cell-relative copies, including one FP32 step for a colloid already moved
-    // this sweep, of the displacement, of the depletant coordinate and of the
-    // differences).  For |v| near a threshold radius R the squared
-    // length then errs by at most 2 sqrt(3) R E + 3 E^2 + 3 u R^2, plus u R^2
-    // for rounding the threshold itself; the margin is twice that, and at
-    // least 1e-5.
-    const double u = 0x1p-24;
-    const double Wc = c->w > 1.0 ? c->w : 1.0;
-    const double E = 32.0 * u * Wc;
-    const double Rmax = std::sqrt(std::fmax(P.R_s2, P.contact2));
-    const double bound = 2.0 * std::sqrt(3.0) * Rmax * E + 3.0 * E * E + 4.0 * u * Rmax * Rmax + 1e-12;
-    P.m_r2 = (float)std::fmax(1e-5, 2.0 * bound);
-    if (p.margin > 0.0) P.m_r2 = (float)p.margin;
-    P.m_cell = (float)(1e-5 * Wc);
-    P.w32 = (float)c->w;
-    P.L32 = (float)c->L;
-    P.half_L32 = (float)(0.5 * c->L);
-    P.R_s32 = (float)c->R_s;
-    P.T_s32 = (float)P.R_s2;
-    P.T_dep32 = (float)P.R_dep2;
-    P.T_contact32 = (float)P.contact2;
-    P.nb_cut2_32 = (float)P.nb_cut2;
-    P.d_max32 = (float)p.d_max;
     P.sched = c->d_sched;
     P.sweep = c->d_sweep;
     P.counters = c->d_counters;
@@ -218,43 +262,45 @@ SimParams make_params(hpmc_ctx *c)
     return P;
 }
 
-// Enqueue the binned cell list (and schedule) of the sweep whose index is in
-// *d_sweep.  Its count buffer was zeroed by the previous sweep's phase kernels
-// (or by check_config).
+// Enqueue the binned cell lists (and schedules) of the sweep whose index is
+// in *d_sweep.  Their count buffer was zeroed by the previous sweep's phase
+// kernels (or by check_config).
 int enqueue_cells(hpmc_ctx *c, cudaStream_t s)
 {
     SimParams P = make_params(c);
-    k_cells_bin<<<(c->n + 255) / 256, 256, 0, s>>>(P);
+    k_cells_bin<<<(c->n_total + 255) / 256, 256, 0, s>>>(P);
     CK(cudaGetLastError());
     return HPMC_OK;
 }
 
 void launch_phase(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
 {
-    const int h = c->nc / 2;
-    const int n_active = h * h * h;
     const int threads = 32 * c->prm.warps;
     const size_t dyn = (size_t)threads * (sizeof(double) + sizeof(int));
+    bool cb = false;
+    for (const RepHost &h : c->reps) cb = cb || h.n_trial > 0;
     if (c->precision == HPMC_FP32_RECHECK) {
         const bool warp = threads == 32;
-        if (P.n_trial > 0) {
-            if (warp) k_phase_sphere_fp32<true, true><<<n_active, threads, dyn, s>>>(P, phase);
-            else k_phase_sphere_fp32<true, false><<<n_active, threads, dyn, s>>>(P, phase);
+        if (cb) {
+            if (warp) k_phase_sphere_fp32<true, true><<<c->n_cta, threads, dyn, s>>>(P, phase);
+            else k_phase_sphere_fp32<true, false><<<c->n_cta, threads, dyn, s>>>(P, phase);
         } else {
-            if (warp) k_phase_sphere_fp32<false, true><<<n_active, threads, dyn, s>>>(P, phase);
-            else k_phase_sphere_fp32<false, false><<<n_active, threads, dyn, s>>>(P, phase);
+            if (warp) k_phase_sphere_fp32<false, true><<<c->n_cta, threads, dyn, s>>>(P, phase);
+            else k_phase_sphere_fp32<false, false><<<c->n_cta, threads, dyn, s>>>(P, phase);
         }
-    } else
-        k_phase_sphere_fp64<<<n_active, threads, 0, s>>>(P, phase);
+    } else {
+        k_phase_sphere_fp64<<<c->n_cta, threads, 0, s>>>(P, phase);
+    }
 }
 
-// One sweep: binned cell list, then the 8 colour phases (phase 7 advances
-// the sweep counter).
 void launch_lens(hpmc_ctx *c, const SimParams &P, cudaStream_t s)
 {
-    if (c->precision == HPMC_FP32_RECHECK) k_lens_sphere_fp32<<<(c->n + 3) / 4, 128, 0, s>>>(P);
+    if (c->precision == HPMC_FP32_RECHECK)
+        k_lens_sphere_fp32<<<(c->n_total + 3) / 4, 128, 0, s>>>(P);
 }
 
+// One sweep of every replica: binned cell lists, depletant lens lists (FP32
+// form), then the 8 colour phases (phase 7 advances the sweep counter).
 int enqueue_sweep(hpmc_ctx *c, cudaStream_t s)
 {
     int rc = enqueue_cells(c, s);
@@ -278,8 +324,8 @@ cudaEvent_t pool_event(hpmc_ctx *c)
     return e;
 }
 
-// One sweep launched kernel by kernel with events around the cell list and
-// around each colour-phase kernel.
+// One sweep launched kernel by kernel with events around the cell lists, the
+// lens kernel and each colour-phase kernel.
 int enqueue_sweep_timed(hpmc_ctx *c, cudaStream_t s)
 {
     cudaEvent_t a = pool_event(c), b = pool_event(c);
@@ -321,11 +367,11 @@ void free_graph(hpmc_ctx *c)
     c->graph = nullptr;
 }
 
-// Configuration check on a cell list of the current sweep index: positions in
-// [0, L) and no overlapping colloids.  Synchronous.
+// Configuration check on cell lists of the current sweep index: positions in
+// [0, L) and no overlapping colloids, in every replica.  Synchronous.
 int check_config(hpmc_ctx *c)
 {
-    const size_t cbytes = sizeof(int) * 2 * (size_t)c->nc * c->nc * c->nc;
+    const size_t cbytes = sizeof(int) * 2 * (size_t)c->n_cells;
     CK(cudaStreamSynchronize(c->cap_stream));
     CK(cudaMemsetAsync(c->d_count, 0, cbytes, c->cap_stream));
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->cap_stream));
@@ -333,7 +379,7 @@ int check_config(hpmc_ctx *c)
     if (rc != HPMC_OK) return rc;
     CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->cap_stream));
     SimParams P = make_params(c);
-    k_check_spheres<<<(c->n + 255) / 256, 256, 0, c->cap_stream>>>(P, c->d_flag);
+    k_check_spheres<<<(c->n_total + 255) / 256, 256, 0, c->cap_stream>>>(P, c->d_flag);
     CK(cudaGetLastError());
     int flag = 0, err = 0;
     CK(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->cap_stream));
@@ -348,94 +394,85 @@ int check_config(hpmc_ctx *c)
     return HPMC_OK;
 }
 
-// Validate parameters, derive geometry, upload the table, check the
-// configuration, record the sweep graph.
+// Validate parameters, derive every replica, upload tables and maps, check
+// the configuration, record the sweep graph.
 int prepare(hpmc_ctx *c)
 {
     const Params &p = c->prm;
     if (p.shape != HPMC_SPHERE) return HPMC_ERR_ARG;  // other shapes: later forms
-    c->R_circ = circum_radius(p);
-    if (!(c->R_circ > 0.0)) return HPMC_ERR_ARG;
-    if (!(p.q >= 0.0) || !(p.n_r >= 0.0) || p.n_trial < 0 || p.n_trial > 100000) return HPMC_ERR_ARG;
-    c->R_s = c->R_circ + 0.5 * p.q;
-    const double v0 = ((4.0 / 3.0) * kPi) * ((c->R_s * c->R_s) * c->R_s);
-    c->lambda = p.n_r > 0.0 ? p.n_r * v0 : 0.0;
-    const double w_min = 2.0 * c->R_circ + p.q;
-    int nc = p.nc_req;
-    if (nc == 0) {
-        nc = (int)(c->L / w_min);
-        if (nc & 1) nc -= 1;
-    }
-    if (nc < 2 || (nc & 1)) return HPMC_ERR_ARG;
-    if (nc > 1024) return HPMC_ERR_CAP;
-    const double w = c->L / (double)nc;
-    if (w < w_min) return HPMC_ERR_ARG;
-    if (!(p.d_max >= 0.0) || p.d_max >= w) return HPMC_ERR_ARG;
-    // a cell bin holds at most (w + 2 R_circ)^3 * 0.7405 / v colloids of volume v
-    // (densest packing); spheres only for now
-    const double v_shape = (kPi / 6.0) * p.sp[0] * p.sp[0] * p.sp[0];
-    const double ext = w + 2.0 * c->R_circ;
-    if (ext * ext * ext * 0.7405 / v_shape >= (double)kMaxCellCap) return HPMC_ERR_CAP;
-    c->nc = nc;
-    c->w = w;
-    if (p.margin > 0.0) {
-        Params def = p;
-        def.margin = 0.0;
-        hpmc_ctx probe = {};
-        probe.prm = def;
-        probe.w = w;
-        probe.R_s = c->R_s;
-        probe.nc = nc;
-        probe.L = c->L;
-        if ((float)p.margin < make_params(&probe).m_r2) return HPMC_ERR_ARG;
-    }
-
+    const int n_rep = (int)c->reps.size();
+    std::vector<Rep> rd((size_t)n_rep);
+    std::vector<unsigned long long> T;
+    std::vector<int> rep_of, cta_rep;
+    rep_of.reserve((size_t)c->n_total);
+    int off = 0, cell_off = 0, cta_off = 0, nF_max = 0;
     std::vector<double> F;
-    if (c->lambda > 0.0) {
-        int rc = build_table(c->lambda, F);
+    for (int r = 0; r < n_rep; ++r) {
+        int rc = derive_rep(c, c->reps[(size_t)r], rd[(size_t)r], F);
         if (rc != HPMC_OK) return rc;
+        Rep &R = rd[(size_t)r];
+        R.off = off;
+        R.cell_off = cell_off;
+        R.cta_off = cta_off;
+        R.t_off = (int)T.size();
+        // F[k] <= m 2^-53  <=>  m >= ceil(F[k] 2^53): exact integer form of the table
+        for (double f : F) T.push_back((unsigned long long)std::ceil(std::ldexp(f, 53)));
+        for (int i = 0; i < R.n; ++i) rep_of.push_back(r);
+        const int h = R.half_nc;
+        for (int a = 0; a < h * h * h; ++a) cta_rep.push_back(r);
+        off += R.n;
+        cell_off += R.nc * R.nc * R.nc;
+        cta_off += h * h * h;
+        if (R.nF > nF_max) nF_max = R.nF;
     }
-    c->nF = (int)F.size();
-    // lens points pack the attempt index t < 64 (N_p + 1) into 16 bits
-    if (c->precision == HPMC_FP32_RECHECK && c->nF > 1023) return HPMC_ERR_CAP;
-
     DeviceGuard g(c->device);
-    const int ncell = nc * nc * nc;
-    if (ncell != c->ncell_alloc) {
+    if (cell_off != c->cells_alloc) {
         cudaFree(c->d_count);
         cudaFree(c->d_bins);
         c->d_count = nullptr;
         c->d_bins = nullptr;
-        c->ncell_alloc = -1;
-        CK(cudaMalloc(&c->d_count, sizeof(int) * 2 * (size_t)ncell));
-        CK(cudaMalloc(&c->d_bins, sizeof(float4) * (size_t)ncell * kMaxCellCap));
-        c->ncell_alloc = ncell;
+        c->cells_alloc = -1;
+        CK(cudaMalloc(&c->d_count, sizeof(int) * 2 * (size_t)cell_off));
+        CK(cudaMalloc(&c->d_bins, sizeof(float4) * (size_t)cell_off * kMaxCellCap));
+        c->cells_alloc = cell_off;
     }
-    // lens lists hold at most N_p <= nF points each: capacity nF, no overflow
+    if (cta_off != c->cta_alloc) {
+        cudaFree(c->d_cta_rep);
+        c->d_cta_rep = nullptr;
+        c->cta_alloc = -1;
+        CK(cudaMalloc(&c->d_cta_rep, sizeof(int) * (size_t)cta_off));
+        c->cta_alloc = cta_off;
+    }
+    CK(cudaMemcpy(c->d_cta_rep, cta_rep.data(), sizeof(int) * (size_t)cta_off,
+                  cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_rep_of, rep_of.data(), sizeof(int) * (size_t)c->n_total,
+                  cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_reps, rd.data(), sizeof(Rep) * (size_t)n_rep, cudaMemcpyHostToDevice));
+    cudaFree(c->d_T);
+    c->d_T = nullptr;
+    if (!T.empty()) {
+        CK(cudaMalloc(&c->d_T, sizeof(unsigned long long) * T.size()));
+        CK(cudaMemcpy(c->d_T, T.data(), sizeof(unsigned long long) * T.size(),
+                      cudaMemcpyHostToDevice));
+    }
+    // lens lists hold at most N_p <= nF points each: capacity nF_max, no overflow
     if (c->precision == HPMC_FP32_RECHECK) {
-        if (!c->d_lens_hdr) CK(cudaMalloc(&c->d_lens_hdr, sizeof(int4) * (size_t)c->n));
-        if (!c->d_lens_move) CK(cudaMalloc(&c->d_lens_move, sizeof(float4) * (size_t)c->n));
-        if (c->nF > c->lens_cap) {
-            const double bytes = (double)sizeof(float4) * (double)c->n * (double)c->nF;
+        if (!c->d_lens_hdr) CK(cudaMalloc(&c->d_lens_hdr, sizeof(int4) * (size_t)c->n_total));
+        if (!c->d_lens_move) CK(cudaMalloc(&c->d_lens_move, sizeof(float4) * (size_t)c->n_total));
+        if (nF_max > c->lens_cap) {
+            const double bytes = (double)sizeof(float4) * (double)c->n_total * (double)nF_max;
             if (bytes > 64.0 * (1ull << 30)) return HPMC_ERR_CAP;
             cudaFree(c->d_lens);
             c->d_lens = nullptr;
             c->lens_cap = 0;
-            CK(cudaMalloc(&c->d_lens, sizeof(float4) * (size_t)c->n * (size_t)c->nF));
-            c->lens_cap = c->nF;
+            CK(cudaMalloc(&c->d_lens, sizeof(float4) * (size_t)c->n_total * (size_t)nF_max));
+            c->lens_cap = nF_max;
         }
     }
-    cudaFree(c->d_T);
-    c->d_T = nullptr;
-    if (c->nF > 0) {
-        // F[k] <= m 2^-53  <=>  m >= ceil(F[k] 2^53): exact integer form of the table
-        std::vector<unsigned long long> T((size_t)c->nF);
-        for (int k = 0; k < c->nF; ++k)
-            T[(size_t)k] = (unsigned long long)std::ceil(std::ldexp(F[(size_t)k], 53));
-        CK(cudaMalloc(&c->d_T, sizeof(unsigned long long) * (size_t)c->nF));
-        CK(cudaMemcpy(c->d_T, T.data(), sizeof(unsigned long long) * (size_t)c->nF,
-                      cudaMemcpyHostToDevice));
-    }
+    c->rdev = rd;
+    c->n_cells = cell_off;
+    c->n_cta = cta_off;
+    c->nF_max = nF_max;
 
     int rc = check_config(c);
     if (rc != HPMC_OK) return rc;
@@ -458,7 +495,7 @@ int prepare(hpmc_ctx *c)
 
 int copy_in(hpmc_ctx *c, const double *pos, const double *quat, int mem, cudaStream_t s)
 {
-    const int n = c->n;
+    const int n = c->n_total;
     const int nb = (n + 255) / 256;
     if (mem == HPMC_DEVICE) {
         k_unpack<<<nb, 256, 0, s>>>(n, pos, quat, c->d_pos, quat ? c->d_quat : nullptr);
@@ -478,6 +515,111 @@ int copy_in(hpmc_ctx *c, const double *pos, const double *quat, int mem, cudaStr
         k_unpack<<<nb, 256, 0, s>>>(n, nullptr, c->d_stage, nullptr, c->d_quat);
         CK(cudaGetLastError());
     }
+    return HPMC_OK;
+}
+
+// Allocate the per-colloid and per-replica buffers of a new context.
+int alloc_ctx(hpmc_ctx *c)
+{
+    const int n = c->n_total, n_rep = (int)c->reps.size();
+    CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    CK(cudaMalloc(&c->d_pos, sizeof(double4) * (size_t)n));
+    CK(cudaMalloc(&c->d_quat, sizeof(double4) * (size_t)n));
+    CK(cudaMalloc(&c->d_rel, sizeof(float4) * (size_t)n));
+    CK(cudaMalloc(&c->d_stage, sizeof(double) * 4 * (size_t)n));
+    CK(cudaMalloc(&c->d_rep_of, sizeof(int) * (size_t)n));
+    CK(cudaMalloc(&c->d_reps, sizeof(Rep) * (size_t)n_rep));
+    CK(cudaMalloc(&c->d_sched, sizeof(Sched) * (size_t)n_rep));
+    CK(cudaMalloc(&c->d_sweep, sizeof(unsigned long long)));
+    CK(cudaMalloc(&c->d_counters,
+                  sizeof(unsigned long long) * (size_t)n_rep * kRepSlots * kNumCounters));
+    CK(cudaMalloc(&c->d_err, sizeof(int)));
+    CK(cudaMalloc(&c->d_flag, sizeof(int)));
+    CK(cudaMemsetAsync(c->d_sweep, 0, sizeof(unsigned long long), c->cap_stream));
+    CK(cudaMemsetAsync(c->d_counters, 0,
+                       sizeof(unsigned long long) * (size_t)n_rep * kRepSlots * kNumCounters,
+                       c->cap_stream));
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->cap_stream));
+    // identity orientations unless given
+    std::vector<double> ident(4 * (size_t)n, 0.0);
+    for (int i = 0; i < n; ++i) ident[4 * (size_t)i] = 1.0;
+    CK(cudaMemcpy(c->d_stage, ident.data(), sizeof(double) * 4 * (size_t)n,
+                  cudaMemcpyHostToDevice));
+    k_unpack<<<(n + 255) / 256, 256, 0, c->cap_stream>>>(n, nullptr, c->d_stage, nullptr,
+                                                         c->d_quat);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->cap_stream));
+    return HPMC_OK;
+}
+
+void sum_counters(const unsigned long long *h, int r0, int r1, hpmc_counters *out)
+{
+    uint64_t tot[kNumCounters] = {0};
+    for (int r = r0; r < r1; ++r)
+        for (int slot = 0; slot < kRepSlots; ++slot)
+            for (int k = 0; k < kNumCounters; ++k)
+                tot[k] += h[((size_t)r * kRepSlots + slot) * kNumCounters + k];
+    std::memset(out, 0, sizeof *out);
+    out->moves = tot[kMoves];
+    out->accept = tot[kAccept];
+    out->reject_cell = tot[kRejCell];
+    out->reject_overlap = tot[kRejOverlap];
+    out->reject_depletant = tot[kRejDep];
+    out->reject_cb = tot[kRejCb];
+    out->dep_drawn = tot[kDepDrawn];
+    out->translate = tot[kTranslate];
+    out->dep_evaluated = tot[kDepEval];
+    out->dep_blocking = tot[kDepBlocking];
+    out->cb_fwd_ok = tot[kCbFwdOk];
+    out->cb_rev_ok = tot[kCbRevOk];
+    out->cap_hits = tot[kCapHits];
+    out->rechecks = tot[kRechecks];
+}
+
+int read_counters(hpmc_ctx *c, std::vector<unsigned long long> &h, cudaStream_t s)
+{
+    h.resize((size_t)c->reps.size() * kRepSlots * kNumCounters);
+    CK(cudaMemcpyAsync(h.data(), c->d_counters, sizeof(unsigned long long) * h.size(),
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return HPMC_OK;
+}
+
+int read_err(hpmc_ctx *c, cudaStream_t s)
+{
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return e ? HPMC_ERR_DEVICE : HPMC_OK;
+}
+
+int create_ctx(hpmc_ctx **out, const std::vector<RepHost> &reps, uint64_t seed, int precision,
+               int device)
+{
+    *out = nullptr;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return HPMC_ERR_ARG;
+    hpmc_ctx *c = new (std::nothrow) hpmc_ctx();
+    if (!c) return HPMC_ERR_ARG;
+    c->device = device;
+    c->seed = seed;
+    c->precision = precision;
+    c->reps = reps;
+    long long tot = 0;
+    for (const RepHost &h : reps) tot += h.n;
+    if (tot > (1ll << 30)) {
+        delete c;
+        return HPMC_ERR_CAP;
+    }
+    c->n_total = (int)tot;
+    DeviceGuard g(device);
+    int rc = alloc_ctx(c);
+    if (rc != HPMC_OK) {
+        hpmc_destroy(c);
+        return rc;
+    }
+    *out = c;
     return HPMC_OK;
 }
 
@@ -508,58 +650,86 @@ int hpmc_init(hpmc_ctx **out, int n, double box_l, const double *pos, const doub
     if (n < 1 || !(box_l > 0.0) || !std::isfinite(box_l) || !pos) return HPMC_ERR_ARG;
     if (mem != HPMC_HOST && mem != HPMC_DEVICE) return HPMC_ERR_ARG;
     if (precision != HPMC_FP64 && precision != HPMC_FP32_RECHECK) return HPMC_ERR_ARG;
-    int ndev = 0;
-    CK(cudaGetDeviceCount(&ndev));
-    if (device < 0 || device >= ndev) return HPMC_ERR_ARG;
-    hpmc_ctx *c = new (std::nothrow) hpmc_ctx();
-    if (!c) return HPMC_ERR_ARG;
-    c->device = device;
-    c->n = n;
-    c->L = box_l;
-    c->seed = seed;
-    c->replica = replica;
-    c->precision = precision;
+    RepHost h;
+    h.n = n;
+    h.L = box_l;
+    h.replica = replica;
+    hpmc_ctx *c = nullptr;
+    int rc = create_ctx(&c, std::vector<RepHost>(1, h), seed, precision, device);
+    if (rc != HPMC_OK) return rc;
     DeviceGuard g(device);
-    int rc = HPMC_OK;
-#define CKI(call)                                  \
-    do {                                           \
-        rc = cuda_fail((call), #call);             \
-        if (rc != HPMC_OK) goto fail;              \
-    } while (0)
-    CKI(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-    CKI(cudaMalloc(&c->d_pos, sizeof(double4) * (size_t)n));
-    CKI(cudaMalloc(&c->d_quat, sizeof(double4) * (size_t)n));
-    CKI(cudaMalloc(&c->d_rel, sizeof(float4) * (size_t)n));
-    CKI(cudaMalloc(&c->d_stage, sizeof(double) * 4 * (size_t)n));
-    CKI(cudaMalloc(&c->d_sched, sizeof(Sched)));
-    CKI(cudaMalloc(&c->d_sweep, sizeof(unsigned long long)));
-    CKI(cudaMalloc(&c->d_counters, sizeof(unsigned long long) * kCounterSlots * kNumCounters));
-    CKI(cudaMalloc(&c->d_err, sizeof(int)));
-    CKI(cudaMalloc(&c->d_flag, sizeof(int)));
-    CKI(cudaMemsetAsync(c->d_sweep, 0, sizeof(unsigned long long), c->cap_stream));
-    CKI(cudaMemsetAsync(c->d_counters, 0,
-                        sizeof(unsigned long long) * kCounterSlots * kNumCounters, c->cap_stream));
-    CKI(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->cap_stream));
-    {
-        // identity orientations unless given
-        std::vector<double> ident(4 * (size_t)n, 0.0);
-        for (int i = 0; i < n; ++i) ident[4 * (size_t)i] = 1.0;
-        CKI(cudaMemcpy(c->d_stage, ident.data(), sizeof(double) * 4 * (size_t)n,
-                       cudaMemcpyHostToDevice));
-        k_unpack<<<(n + 255) / 256, 256, 0, c->cap_stream>>>(n, nullptr, c->d_stage, nullptr,
-                                                             c->d_quat);
-        CKI(cudaGetLastError());
-        CKI(cudaStreamSynchronize(c->cap_stream));
-    }
     rc = copy_in(c, pos, quat, mem, c->cap_stream);
-    if (rc != HPMC_OK) goto fail;
-    CKI(cudaStreamSynchronize(c->cap_stream));
-#undef CKI
+    if (rc == HPMC_OK) rc = cuda_fail(cudaStreamSynchronize(c->cap_stream), "sync");
+    if (rc != HPMC_OK) {
+        hpmc_destroy(c);
+        return rc;
+    }
     *out = c;
     return HPMC_OK;
-fail:
-    hpmc_destroy(c);
-    return rc;
+}
+
+int hpmc_init_batch(hpmc_ctx **out, int n_rep, const hpmc_replica_desc *desc, int shape,
+                    const double *shape_params, int nparams, uint64_t seed, int precision,
+                    int device)
+{
+    if (!out) return HPMC_ERR_ARG;
+    *out = nullptr;
+    if (n_rep < 1 || !desc) return HPMC_ERR_ARG;
+    if (precision != HPMC_FP64 && precision != HPMC_FP32_RECHECK) return HPMC_ERR_ARG;
+    std::vector<RepHost> reps((size_t)n_rep);
+    for (int r = 0; r < n_rep; ++r) {
+        const hpmc_replica_desc &d = desc[r];
+        if (d.n < 1 || !(d.box_l > 0.0) || !std::isfinite(d.box_l) || !d.pos) return HPMC_ERR_ARG;
+        if (!(d.q >= 0.0) || !(d.n_r >= 0.0) || !std::isfinite(d.n_r) || d.n_trial < 0)
+            return HPMC_ERR_ARG;
+        if (!(d.d_max >= 0.0) || !(d.a_max >= 0.0) || !(d.p_translate >= 0.0) ||
+            d.p_translate > 1.0 || d.n_cell < 0 || (d.n_cell & 1))
+            return HPMC_ERR_ARG;
+        RepHost &h = reps[(size_t)r];
+        h.n = d.n;
+        h.L = d.box_l;
+        h.q = d.q;
+        h.n_r = d.n_r;
+        h.n_trial = d.n_trial;
+        h.d_max = d.d_max;
+        h.a_max = d.a_max;
+        h.p_translate = d.p_translate;
+        h.replica = d.replica;
+        h.nc_req = d.n_cell;
+    }
+    hpmc_ctx *c = nullptr;
+    int rc = create_ctx(&c, reps, seed, precision, device);
+    if (rc != HPMC_OK) return rc;
+    if (shape_params) rc = hpmc_set_shape(c, shape, shape_params, nparams);
+    DeviceGuard g(device);
+    // replica positions, one after another
+    std::vector<double> pos(3 * (size_t)c->n_total), quat;
+    bool any_quat = false;
+    for (int r = 0; r < n_rep; ++r) any_quat = any_quat || desc[r].quat;
+    if (any_quat) quat.assign(4 * (size_t)c->n_total, 0.0);
+    size_t o = 0;
+    for (int r = 0; r < n_rep && rc == HPMC_OK; ++r) {
+        std::memcpy(pos.data() + 3 * o, desc[r].pos, sizeof(double) * 3 * (size_t)desc[r].n);
+        if (any_quat) {
+            for (int i = 0; i < desc[r].n; ++i) {
+                if (desc[r].quat)
+                    std::memcpy(quat.data() + 4 * (o + i), desc[r].quat + 4 * (size_t)i,
+                                sizeof(double) * 4);
+                else
+                    quat[4 * (o + i)] = 1.0;
+            }
+        }
+        o += (size_t)desc[r].n;
+    }
+    if (rc == HPMC_OK)
+        rc = copy_in(c, pos.data(), any_quat ? quat.data() : nullptr, HPMC_HOST, c->cap_stream);
+    if (rc == HPMC_OK) rc = cuda_fail(cudaStreamSynchronize(c->cap_stream), "sync");
+    if (rc != HPMC_OK) {
+        hpmc_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return HPMC_OK;
 }
 
 int hpmc_set_shape(hpmc_ctx *c, int kind, const double *params, int nparams)
@@ -588,9 +758,11 @@ int hpmc_set_depletant(hpmc_ctx *c, double q, double n_r, int n_trial)
 {
     if (!c || !(q >= 0.0) || !(n_r >= 0.0) || !std::isfinite(n_r) || n_trial < 0)
         return HPMC_ERR_ARG;
-    c->prm.q = q;
-    c->prm.n_r = n_r;
-    c->prm.n_trial = n_trial;
+    for (RepHost &h : c->reps) {
+        h.q = q;
+        h.n_r = n_r;
+        h.n_trial = n_trial;
+    }
     c->dirty = true;
     return HPMC_OK;
 }
@@ -600,9 +772,24 @@ int hpmc_set_moves(hpmc_ctx *c, double d_max, double a_max, double p_translate)
     if (!c || !(d_max >= 0.0) || !(a_max >= 0.0) || a_max > 3.0 || !(p_translate >= 0.0) ||
         p_translate > 1.0)
         return HPMC_ERR_ARG;
-    c->prm.d_max = d_max;
-    c->prm.a_max = a_max;
-    c->prm.p_translate = p_translate;
+    for (RepHost &h : c->reps) {
+        h.d_max = d_max;
+        h.a_max = a_max;
+        h.p_translate = p_translate;
+    }
+    c->dirty = true;
+    return HPMC_OK;
+}
+
+int hpmc_set_replica_moves(hpmc_ctx *c, int r, double d_max, double a_max, double p_translate)
+{
+    if (!c || r < 0 || r >= (int)c->reps.size() || !(d_max >= 0.0) || !(a_max >= 0.0) ||
+        a_max > 3.0 || !(p_translate >= 0.0) || p_translate > 1.0)
+        return HPMC_ERR_ARG;
+    RepHost &h = c->reps[(size_t)r];
+    h.d_max = d_max;
+    h.a_max = a_max;
+    h.p_translate = p_translate;
     c->dirty = true;
     return HPMC_OK;
 }
@@ -610,7 +797,7 @@ int hpmc_set_moves(hpmc_ctx *c, double d_max, double a_max, double p_translate)
 int hpmc_set_cells(hpmc_ctx *c, int n_cell)
 {
     if (!c || n_cell < 0 || (n_cell & 1) || n_cell == 1) return HPMC_ERR_ARG;
-    c->prm.nc_req = n_cell;
+    for (RepHost &h : c->reps) h.nc_req = n_cell;
     c->dirty = true;
     return HPMC_OK;
 }
@@ -689,21 +876,13 @@ int hpmc_get_timing(hpmc_ctx *c, double *ms, uint64_t *launches, int nkinds)
     return HPMC_OK;
 }
 
-static int read_err(hpmc_ctx *c, cudaStream_t s)
-{
-    int e = 0;
-    CK(cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    return e ? HPMC_ERR_DEVICE : HPMC_OK;
-}
-
 int hpmc_get_state(hpmc_ctx *c, double *pos, double *quat, int mem, uint64_t *sweep,
                    hpmc_counters *counters, void *stream)
 {
     if (!c || (mem != HPMC_HOST && mem != HPMC_DEVICE)) return HPMC_ERR_ARG;
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
-    const int n = c->n, nb = (n + 255) / 256;
+    const int n = c->n_total, nb = (n + 255) / 256;
     if (mem == HPMC_DEVICE) {
         if (pos || quat) {
             k_pack<<<nb, 256, 0, s>>>(n, c->d_pos, c->d_quat, pos, quat);
@@ -732,28 +911,42 @@ int hpmc_get_state(hpmc_ctx *c, double *pos, double *quat, int mem, uint64_t *sw
         *sweep = v;
     }
     if (counters) {
-        std::vector<unsigned long long> h((size_t)kCounterSlots * kNumCounters);
-        CK(cudaMemcpyAsync(h.data(), c->d_counters, sizeof(unsigned long long) * h.size(),
+        std::vector<unsigned long long> h;
+        int rc = read_counters(c, h, s);
+        if (rc != HPMC_OK) return rc;
+        sum_counters(h.data(), 0, (int)c->reps.size(), counters);
+    }
+    return read_err(c, s);
+}
+
+int hpmc_get_replica(hpmc_ctx *c, int r, double *pos, double *quat, hpmc_counters *counters)
+{
+    if (!c || r < 0 || r >= (int)c->reps.size()) return HPMC_ERR_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t s = c->cap_stream;
+    CK(cudaDeviceSynchronize());
+    size_t off = 0;
+    for (int k = 0; k < r; ++k) off += (size_t)c->reps[(size_t)k].n;
+    const int n = c->reps[(size_t)r].n;
+    const int nb = (n + 255) / 256;
+    if (pos) {
+        k_pack<<<nb, 256, 0, s>>>(n, c->d_pos + off, nullptr, c->d_stage, nullptr);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(pos, c->d_stage, sizeof(double) * 3 * (size_t)n,
                            cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        uint64_t tot[kNumCounters] = {0};
-        for (int slot = 0; slot < kCounterSlots; ++slot)
-            for (int k = 0; k < kNumCounters; ++k) tot[k] += h[(size_t)slot * kNumCounters + k];
-        std::memset(counters, 0, sizeof *counters);
-        counters->moves = tot[kMoves];
-        counters->accept = tot[kAccept];
-        counters->reject_cell = tot[kRejCell];
-        counters->reject_overlap = tot[kRejOverlap];
-        counters->reject_depletant = tot[kRejDep];
-        counters->reject_cb = tot[kRejCb];
-        counters->dep_drawn = tot[kDepDrawn];
-        counters->translate = tot[kTranslate];
-        counters->dep_evaluated = tot[kDepEval];
-        counters->dep_blocking = tot[kDepBlocking];
-        counters->cb_fwd_ok = tot[kCbFwdOk];
-        counters->cb_rev_ok = tot[kCbRevOk];
-        counters->cap_hits = tot[kCapHits];
-        counters->rechecks = tot[kRechecks];
+    }
+    if (quat) {
+        k_pack<<<nb, 256, 0, s>>>(n, nullptr, c->d_quat + off, nullptr, c->d_stage + 3 * (size_t)n);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(quat, c->d_stage + 3 * (size_t)n, sizeof(double) * 4 * (size_t)n,
+                           cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    if (counters) {
+        std::vector<unsigned long long> h;
+        int rc = read_counters(c, h, s);
+        if (rc != HPMC_OK) return rc;
+        sum_counters(h.data(), r, r + 1, counters);
     }
     return read_err(c, s);
 }
@@ -778,7 +971,8 @@ int hpmc_reset_counters(hpmc_ctx *c)
     if (!c) return HPMC_ERR_ARG;
     DeviceGuard g(c->device);
     CK(cudaDeviceSynchronize());
-    CK(cudaMemset(c->d_counters, 0, sizeof(unsigned long long) * kCounterSlots * kNumCounters));
+    CK(cudaMemset(c->d_counters, 0,
+                  sizeof(unsigned long long) * c->reps.size() * kRepSlots * kNumCounters));
     return HPMC_OK;
 }
 
@@ -910,15 +1104,18 @@ void hpmc_destroy(hpmc_ctx *c)
     for (cudaEvent_t e : c->tpool) cudaEventDestroy(e);
     cudaFree(c->d_pos);
     cudaFree(c->d_quat);
+    cudaFree(c->d_rel);
     cudaFree(c->d_stage);
     cudaFree(c->d_count);
     cudaFree(c->d_bins);
-    cudaFree(c->d_sched);
-    cudaFree(c->d_T);
     cudaFree(c->d_lens);
     cudaFree(c->d_lens_hdr);
     cudaFree(c->d_lens_move);
-    cudaFree(c->d_rel);
+    cudaFree(c->d_reps);
+    cudaFree(c->d_rep_of);
+    cudaFree(c->d_cta_rep);
+    cudaFree(c->d_sched);
+    cudaFree(c->d_T);
     cudaFree(c->d_sweep);
     cudaFree(c->d_counters);
     cudaFree(c->d_err);

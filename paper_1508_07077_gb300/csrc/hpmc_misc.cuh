@@ -5,36 +5,38 @@
 
 namespace hpmc {
 
-// One thread per colloid, over the 27 cells of the binned list of the
-// current sweep index: sets bit 1 of *flag if a coordinate is outside [0, L),
-// bit 0 if two spheres overlap.
+// One thread per colloid of the batch, over the 27 cells of the binned list
+// of the current sweep index: sets bit 1 of *flag if a coordinate is outside
+// [0, L), bit 0 if two spheres overlap.
 __global__ void k_check_spheres(const __grid_constant__ SimParams P, int *flag)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
-    const double4 pi = P.pos[i];
-    if (!(pi.x >= 0.0 && pi.x < P.L && pi.y >= 0.0 && pi.y < P.L && pi.z >= 0.0 && pi.z < P.L)) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= P.n_total) return;
+    const int r = P.rep_of[g];
+    const Rep &R = P.reps[r];
+    const double4 pi = P.pos[g];
+    if (!(pi.x >= 0.0 && pi.x < R.L && pi.y >= 0.0 && pi.y < R.L && pi.z >= 0.0 && pi.z < R.L)) {
         atomicOr(flag, 2);
         return;
     }
-    const Sched *S = P.sched;
-    const int *count = P.count[S->sweep & 1u];
-    const int cx = cell_coord(pi.x, S->sigma[0], P.L, P.w, P.nc);
-    const int cy = cell_coord(pi.y, S->sigma[1], P.L, P.w, P.nc);
-    const int cz = cell_coord(pi.z, S->sigma[2], P.L, P.w, P.nc);
-    const int ns = P.n_stencil;
+    const Sched &S = P.sched[r];
+    const int *count = P.count[S.sweep & 1u];
+    const int cx = cell_coord(pi.x, S.sigma[0], R.L, R.w, R.nc);
+    const int cy = cell_coord(pi.y, S.sigma[1], R.L, R.w, R.nc);
+    const int cz = cell_coord(pi.z, S.sigma[2], R.L, R.w, R.nc);
+    const int ns = R.n_stencil;
     for (int t = 0; t < ns * ns * ns; ++t) {
         int dx, dy, dz;
-        const int c = stencil_cell(P, t, cx, cy, cz, dx, dy, dz);
+        const int c = stencil_cell(R, t, cx, cy, cz, dx, dy, dz);
         const int m = min(count[c], P.cap);
         for (int s = 0; s < m; ++s) {
             const int j = __float_as_int(P.bins[(size_t)c * P.cap + s].w);
-            if (j == i) continue;
+            if (j == g) continue;
             const double4 pj = P.pos[j];
-            const double r2 = norm2(min_image(pj.x - pi.x, P.L, P.half_L),
-                                    min_image(pj.y - pi.y, P.L, P.half_L),
-                                    min_image(pj.z - pi.z, P.L, P.half_L));
-            if (r2 < P.contact2) atomicOr(flag, 1);
+            const double r2 = norm2(min_image(pj.x - pi.x, R.L, R.half_L),
+                                    min_image(pj.y - pi.y, R.L, R.half_L),
+                                    min_image(pj.z - pi.z, R.L, R.half_L));
+            if (r2 < R.contact2) atomicOr(flag, 1);
         }
     }
 }

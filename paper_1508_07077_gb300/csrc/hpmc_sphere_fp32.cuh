@@ -42,20 +42,20 @@ __device__ __forceinline__ int tri(float r2, float T, float m)
 // colloid of the list acc[0..nacc) is at its moved position.
 
 // Exact FP64 position of colloid j after its move of this sweep.
-__device__ __forceinline__ double4 moved64(const SimParams &P, uint32_t sweep, int j)
+__device__ __forceinline__ double4 moved64(const SimParams &P, const Rep &R, uint32_t sweep, int j)
 {
-    const uint4 wm = draw(P.key0, P.key1, sweep, (uint32_t)j, kPMove, 0, 0);
+    const uint4 wm = draw(R.key0, R.key1, sweep, (uint32_t)(j - R.off), kPMove, 0, 0);
     const double4 p = P.pos[j];
-    return make_double4(wrap_box(p.x + P.d_max * s11(wm.x), P.L),
-                        wrap_box(p.y + P.d_max * s11(wm.y), P.L),
-                        wrap_box(p.z + P.d_max * s11(wm.z), P.L), 0.0);
+    return make_double4(wrap_box(p.x + R.d_max * s11(wm.x), R.L),
+                        wrap_box(p.y + R.d_max * s11(wm.y), R.L),
+                        wrap_box(p.z + R.d_max * s11(wm.z), R.L), 0.0);
 }
 
-__device__ __forceinline__ double4 pos_now(const SimParams &P, uint32_t sweep, int j,
+__device__ __forceinline__ double4 pos_now(const SimParams &P, const Rep &R, uint32_t sweep, int j,
                                            const int *acc, int nacc)
 {
     for (int a = 0; a < nacc; ++a)
-        if (acc[a] == j) return moved64(P, sweep, j);
+        if (acc[a] == j) return moved64(P, R, sweep, j);
     return P.pos[j];
 }
 
@@ -64,52 +64,51 @@ struct Move64 {
     double o0, o1, o2;  // old position relative to the new one (minimum image)
 };
 
-__device__ __forceinline__ Move64 move64(const SimParams &P, uint32_t sweep, int i)
+__device__ __forceinline__ Move64 move64(const SimParams &P, const Rep &R, uint32_t sweep, int i)
 {
     const double4 pi = P.pos[i];
-    const double4 x = moved64(P, sweep, i);
+    const double4 x = moved64(P, R, sweep, i);
     Move64 m;
     m.x0 = x.x;
     m.x1 = x.y;
     m.x2 = x.z;
-    m.o0 = min_image(pi.x - m.x0, P.L, P.half_L);
-    m.o1 = min_image(pi.y - m.x1, P.L, P.half_L);
-    m.o2 = min_image(pi.z - m.x2, P.L, P.half_L);
+    m.o0 = min_image(pi.x - m.x0, R.L, R.half_L);
+    m.o1 = min_image(pi.y - m.x1, R.L, R.half_L);
+    m.o2 = min_image(pi.z - m.x2, R.L, R.half_L);
     return m;
 }
 
-__device__ __forceinline__ void center64(const SimParams &P, const Move64 &m, double4 pj,
+__device__ __forceinline__ void center64(const SimParams &P, const Rep &R, const Move64 &m, double4 pj,
                                          double &c0, double &c1, double &c2)
 {
-    c0 = min_image(pj.x - m.x0, P.L, P.half_L);
-    c1 = min_image(pj.y - m.x1, P.L, P.half_L);
-    c2 = min_image(pj.z - m.x2, P.L, P.half_L);
+    c0 = min_image(pj.x - m.x0, R.L, R.half_L);
+    c1 = min_image(pj.y - m.x1, R.L, R.half_L);
+    c2 = min_image(pj.z - m.x2, R.L, R.half_L);
 }
 
-__device__ __noinline__ bool exact_cell_exit(const SimParams &P, uint32_t sweep, int i, int cx,
-                                             int cy, int cz)
+__device__ __noinline__ bool exact_cell_exit(const SimParams &P, const Rep &R, const Sched *S,
+                                             uint32_t sweep, int i, int cx, int cy, int cz)
 {
-    const double4 x = moved64(P, sweep, i);
-    const Sched *S = P.sched;
-    return cell_coord(x.x, S->sigma[0], P.L, P.w, P.nc) != cx ||
-           cell_coord(x.y, S->sigma[1], P.L, P.w, P.nc) != cy ||
-           cell_coord(x.z, S->sigma[2], P.L, P.w, P.nc) != cz;
+    const double4 x = moved64(P, R, sweep, i);
+    return cell_coord(x.x, S->sigma[0], R.L, R.w, R.nc) != cx ||
+           cell_coord(x.y, S->sigma[1], R.L, R.w, R.nc) != cy ||
+           cell_coord(x.z, S->sigma[2], R.L, R.w, R.nc) != cz;
 }
 
 // colloid i at its new position overlaps colloid j
-__device__ __noinline__ bool exact_pair(const SimParams &P, uint32_t sweep, int i, int j,
+__device__ __noinline__ bool exact_pair(const SimParams &P, const Rep &R, uint32_t sweep, int i, int j,
                                         const int *acc, int nacc)
 {
-    const Move64 m = move64(P, sweep, i);
+    const Move64 m = move64(P, R, sweep, i);
     double c0, c1, c2;
-    center64(P, m, pos_now(P, sweep, j, acc, nacc), c0, c1, c2);
-    return norm2(c0, c1, c2) < P.contact2;
+    center64(P, R, m, pos_now(P, R, sweep, j, acc, nacc), c0, c1, c2);
+    return norm2(c0, c1, c2) < R.contact2;
 }
 
-__device__ __noinline__ bool exact_ball(const SimParams &P, uint4 w)
+__device__ __noinline__ bool exact_ball(const SimParams &P, const Rep &R, uint4 w)
 {
-    const double e0 = P.R_s * s11(w.x), e1 = P.R_s * s11(w.y), e2 = P.R_s * s11(w.z);
-    return norm2(e0, e1, e2) < P.R_s2;
+    const double e0 = R.R_s * s11(w.x), e1 = R.R_s * s11(w.y), e2 = R.R_s * s11(w.z);
+    return norm2(e0, e1, e2) < R.R_s2;
 }
 
 // Exact test of a depletant point against one colloid.
@@ -117,31 +116,31 @@ __device__ __noinline__ bool exact_ball(const SimParams &P, uint4 w)
 //   what 1: forward CB trial y = o + e (around the old reference point) vs the new pose
 //   what 2: point e vs neighbour j
 //   what 3: forward CB trial y = o + e vs neighbour j
-__device__ __noinline__ bool exact_dep(const SimParams &P, uint32_t sweep, int i, uint4 w, int what,
+__device__ __noinline__ bool exact_dep(const SimParams &P, const Rep &R, uint32_t sweep, int i, uint4 w, int what,
                                        int j, const int *acc, int nacc)
 {
-    const Move64 m = move64(P, sweep, i);
-    const double e0 = P.R_s * s11(w.x), e1 = P.R_s * s11(w.y), e2 = P.R_s * s11(w.z);
+    const Move64 m = move64(P, R, sweep, i);
+    const double e0 = R.R_s * s11(w.x), e1 = R.R_s * s11(w.y), e2 = R.R_s * s11(w.z);
     double v0 = e0, v1 = e1, v2 = e2;
     if (what == 1 || what == 3) {
         v0 = m.o0 + e0;
         v1 = m.o1 + e1;
         v2 = m.o2 + e2;
     }
-    if (what == 0) return SphereFP64::dep(P, v0 - m.o0, v1 - m.o1, v2 - m.o2);
-    if (what == 1) return SphereFP64::dep(P, v0, v1, v2);
+    if (what == 0) return SphereFP64::dep(R, v0 - m.o0, v1 - m.o1, v2 - m.o2);
+    if (what == 1) return SphereFP64::dep(R, v0, v1, v2);
     double c0, c1, c2;
-    center64(P, m, pos_now(P, sweep, j, acc, nacc), c0, c1, c2);
-    return SphereFP64::dep(P, v0 - c0, v1 - c1, v2 - c2);
+    center64(P, R, m, pos_now(P, R, sweep, j, acc, nacc), c0, c1, c2);
+    return SphereFP64::dep(R, v0 - c0, v1 - c1, v2 - c2);
 }
 
 // A lens point (attempt t of the depletant stream) free of every neighbour?
-__device__ __noinline__ bool exact_free_nb(const SimParams &P, uint32_t sweep, int i, uint32_t t,
+__device__ __noinline__ bool exact_free_nb(const SimParams &P, const Rep &R, uint32_t sweep, int i, uint32_t t,
                                            const float4 *nb, int nnb, const int *acc, int nacc)
 {
-    const uint4 w = draw(P.key0, P.key1, sweep, (uint32_t)i, kPDep, 0, t);
+    const uint4 w = draw(R.key0, R.key1, sweep, (uint32_t)(i - R.off), kPDep, 0, t);
     for (int a = 0; a < nnb; ++a)
-        if (exact_dep(P, sweep, i, w, 2, __float_as_int(nb[a].w), acc, nacc)) return false;
+        if (exact_dep(P, R, sweep, i, w, 2, __float_as_int(nb[a].w), acc, nacc)) return false;
     return true;
 }
 
@@ -149,39 +148,39 @@ __device__ __noinline__ bool exact_free_nb(const SimParams &P, uint32_t sweep, i
 
 // Is v (FP32, relative to the new reference point) free of every neighbour?
 // kind 2: v is a point e; kind 3: v is a forward trial o + e.
-__device__ __forceinline__ bool free_nb32(const SimParams &P, float v0, float v1, float v2,
+__device__ __forceinline__ bool free_nb32(const SimParams &P, const Rep &R, float v0, float v1, float v2,
                                           const float4 *nb, int nnb, uint32_t sweep, int i,
                                           uint4 w, int kind, const int *acc, int nacc,
                                           uint32_t &rck)
 {
     for (int a = 0; a < nnb; ++a) {
         const float4 d = nb[a];
-        const int t = tri(norm2f(v0 - d.x, v1 - d.y, v2 - d.z), P.T_dep32, P.m_r2);
+        const int t = tri(norm2f(v0 - d.x, v1 - d.y, v2 - d.z), R.T_dep32, R.m_r2);
         if (t == 1) return false;
         if (t == -1) {
             ++rck;
-            if (exact_dep(P, sweep, i, w, kind, __float_as_int(d.w), acc, nacc)) return false;
+            if (exact_dep(P, R, sweep, i, w, kind, __float_as_int(d.w), acc, nacc)) return false;
         }
     }
     return true;
 }
 
 // Next point of an attempt stream inside the sampling ball.
-__device__ __forceinline__ bool next_in_ball32(const SimParams &P, uint32_t sweep, uint32_t tag,
+__device__ __forceinline__ bool next_in_ball32(const SimParams &P, const Rep &R, uint32_t sweep, uint32_t tag,
                                                uint32_t purpose, uint32_t sub, uint32_t &t,
                                                uint32_t t_max, uint4 &w, float &e0, float &e1,
                                                float &e2, uint32_t &rck)
 {
     while (t < t_max) {
-        w = draw(P.key0, P.key1, sweep, tag, purpose, sub, t);
+        w = draw(R.key0, R.key1, sweep, tag, purpose, sub, t);
         ++t;
-        e0 = coord32(w.x, P.R_s32);
-        e1 = coord32(w.y, P.R_s32);
-        e2 = coord32(w.z, P.R_s32);
-        int in = tri(norm2f(e0, e1, e2), P.T_s32, P.m_r2);
+        e0 = coord32(w.x, R.R_s32);
+        e1 = coord32(w.y, R.R_s32);
+        e2 = coord32(w.z, R.R_s32);
+        int in = tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
         if (in == -1) {
             ++rck;
-            in = exact_ball(P, w) ? 1 : 0;
+            in = exact_ball(P, R, w) ? 1 : 0;
         }
         if (in) return true;
     }
@@ -195,44 +194,44 @@ struct CbResult32 {
 
 // CB factor of one blocking depletant (Sec. III.D, Eq. 12), FP32 form.  For
 // spheres "overlaps the pose the ball is centred on" is the ball test itself.
-__device__ __noinline__ CbResult32 cb_factor_fp32(const SimParams &P, uint32_t sweep, int i,
+__device__ __noinline__ CbResult32 cb_factor_fp32(const SimParams &P, const Rep &R, uint32_t sweep, int i,
                                                   uint32_t k, float o0, float o1, float o2,
                                                   const float4 *nb, int nnb, const int *acc,
                                                   int nacc)
 {
     CbResult32 r = {0.0, 0u, 0u, 0u, 0u};
-    const uint32_t tag = (uint32_t)i;
-    const int n_fwd = P.n_trial, n_rev = P.n_trial - 1;
+    const uint32_t tag = (uint32_t)(i - R.off);
+    const int n_fwd = R.n_trial, n_rev = R.n_trial - 1;
     int nf = 0, nr = 0, found = 0;
     uint32_t t = 0;
     uint4 w;
     float e0, e1, e2;
-    while (found < n_fwd && next_in_ball32(P, sweep, tag, kPCbFwd, k, t, 64u * (uint32_t)(n_fwd + 1),
+    while (found < n_fwd && next_in_ball32(P, R, sweep, tag, kPCbFwd, k, t, 64u * (uint32_t)(n_fwd + 1),
                                            w, e0, e1, e2, r.rck)) {
         ++found;
         const float y0 = o0 + e0, y1 = o1 + e1, y2 = o2 + e2;
-        int tn = tri(norm2f(y0, y1, y2), P.T_dep32, P.m_r2);  // overlaps the new pose?
+        int tn = tri(norm2f(y0, y1, y2), R.T_dep32, R.m_r2);  // overlaps the new pose?
         if (tn == -1) {
             ++r.rck;
-            tn = exact_dep(P, sweep, i, w, 1, 0, acc, nacc) ? 1 : 0;
+            tn = exact_dep(P, R, sweep, i, w, 1, 0, acc, nacc) ? 1 : 0;
         }
         if (tn) continue;
-        if (!free_nb32(P, y0, y1, y2, nb, nnb, sweep, i, w, 3, acc, nacc, r.rck)) continue;
+        if (!free_nb32(P, R, y0, y1, y2, nb, nnb, sweep, i, w, 3, acc, nacc, r.rck)) continue;
         ++nf;
     }
     if (found < n_fwd) ++r.caps;
     t = 0;
     found = 0;
-    while (found < n_rev && next_in_ball32(P, sweep, tag, kPCbRev, k, t, 64u * (uint32_t)(n_rev + 1),
+    while (found < n_rev && next_in_ball32(P, R, sweep, tag, kPCbRev, k, t, 64u * (uint32_t)(n_rev + 1),
                                            w, e0, e1, e2, r.rck)) {
         ++found;
-        int to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), P.T_dep32, P.m_r2);  // old pose?
+        int to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), R.T_dep32, R.m_r2);  // old pose?
         if (to == -1) {
             ++r.rck;
-            to = exact_dep(P, sweep, i, w, 0, 0, acc, nacc) ? 1 : 0;
+            to = exact_dep(P, R, sweep, i, w, 0, 0, acc, nacc) ? 1 : 0;
         }
         if (to) continue;
-        if (!free_nb32(P, e0, e1, e2, nb, nnb, sweep, i, w, 2, acc, nacc, r.rck)) continue;
+        if (!free_nb32(P, R, e0, e1, e2, nb, nnb, sweep, i, w, 2, acc, nacc, r.rck)) continue;
         ++nr;
     }
     if (found < n_rev) ++r.caps;
@@ -244,12 +243,12 @@ __device__ __noinline__ CbResult32 cb_factor_fp32(const SimParams &P, uint32_t s
 
 // Classify one depletant point exactly: blocking iff it overlaps neither the
 // old pose nor a neighbour (it overlaps the new pose, being inside the ball).
-__device__ __noinline__ int exact_classify(const SimParams &P, uint32_t sweep, int i, uint4 w,
+__device__ __noinline__ int exact_classify(const SimParams &P, const Rep &R, uint32_t sweep, int i, uint4 w,
                                            const float4 *nb, int nnb, const int *acc, int nacc)
 {
-    if (exact_dep(P, sweep, i, w, 0, 0, acc, nacc)) return 0;
+    if (exact_dep(P, R, sweep, i, w, 0, 0, acc, nacc)) return 0;
     for (int a = 0; a < nnb; ++a)
-        if (exact_dep(P, sweep, i, w, 2, __float_as_int(nb[a].w), acc, nacc)) return 0;
+        if (exact_dep(P, R, sweep, i, w, 2, __float_as_int(nb[a].w), acc, nacc)) return 0;
     return 1;
 }
 
@@ -314,21 +313,24 @@ __device__ __forceinline__ bool cb_pass(DepShared &sh, int tid, int nslots, doub
 __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant__ SimParams P)
 {
     const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= P.n) return;
-    const uint32_t sweep = P.sched->sweep;
-    const uint32_t tag = (uint32_t)i;
-    const uint4 wm = draw(P.key0, P.key1, sweep, tag, kPMove, 0, 0);
-    const float D0 = coord32(wm.x, P.d_max32);
-    const float D1 = coord32(wm.y, P.d_max32);
-    const float D2 = coord32(wm.z, P.d_max32);
+    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= P.n_total) return;
+    const int r = P.rep_of[g];
+    const Rep &R = P.reps[r];
+    const int i = g;   // global colloid index (the helpers take global indices)
+    const uint32_t sweep = P.sched[r].sweep;
+    const uint32_t tag = (uint32_t)(g - R.off);
+    const uint4 wm = draw(R.key0, R.key1, sweep, tag, kPMove, 0, 0);
+    const float D0 = coord32(wm.x, R.d_max32);
+    const float D1 = coord32(wm.y, R.d_max32);
+    const float D2 = coord32(wm.z, R.d_max32);
     if (lane == 0) P.lens_move[i] = make_float4(D0, D1, D2, 0.0f);
-    if (!P.has_dep) return;
+    if (!R.has_dep) return;
     {
         // the same FP32 expression the colour phase uses for the cell-exit test
         const float4 ri = P.rel[i];
         const float rn0 = ri.x + D0, rn1 = ri.y + D1, rn2 = ri.z + D2;
-        const float mc = P.m_cell, wc = P.w32;
+        const float mc = R.m_cell, wc = R.w32;
         if (rn0 < -mc || rn0 > wc + mc || rn1 < -mc || rn1 > wc + mc || rn2 < -mc ||
             rn2 > wc + mc) {
             if (lane == 0) P.lens_hdr[i] = make_int4(0, 0, 0, 0);
@@ -337,10 +339,10 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
     }
     uint32_t rck = 0;
     const float o0 = -D0, o1 = -D1, o2 = -D2;
-    const uint4 wp = draw(P.key0, P.key1, sweep, tag, kPPoisson, 0, 0);
-    const int n_p = poisson_count(P.T, P.nF, u53_int(wp.x, wp.y), lane);
+    const uint4 wp = draw(R.key0, R.key1, sweep, tag, kPPoisson, 0, 0);
+    const int n_p = poisson_count(P.T + R.t_off, R.nF, u53_int(wp.x, wp.y), lane);
     const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
-    float4 *out = P.lens + (size_t)i * P.lens_cap;
+    float4 *out = P.lens + (size_t)g * P.lens_cap;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t t0 = 0;
     int k0 = 0, m = 0;
@@ -350,18 +352,18 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
         float e0 = 0.f, e1 = 0.f, e2 = 0.f;
         int in = 0;
         if (t < t_max) {
-            w = draw(P.key0, P.key1, sweep, tag, kPDep, 0, t);
-            e0 = coord32(w.x, P.R_s32);
-            e1 = coord32(w.y, P.R_s32);
-            e2 = coord32(w.z, P.R_s32);
-            in = tri(norm2f(e0, e1, e2), P.T_s32, P.m_r2);
+            w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, t);
+            e0 = coord32(w.x, R.R_s32);
+            e1 = coord32(w.y, R.R_s32);
+            e2 = coord32(w.z, R.R_s32);
+            in = tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
         }
         {
             const bool unsure = in == -1;
             if (__any_sync(kFull, unsure)) {
                 if (unsure) {
                     ++rck;
-                    in = exact_ball(P, w) ? 1 : 0;
+                    in = exact_ball(P, R, w) ? 1 : 0;
                 }
             }
         }
@@ -369,13 +371,13 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
         const int k = k0 + __popc(bal & lt);
         const bool dep = in == 1 && k < n_p;
         int to = 1;  // overlaps the old pose: 1 yes, 0 no, -1 within the margin
-        if (dep) to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), P.T_dep32, P.m_r2);
+        if (dep) to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), R.T_dep32, R.m_r2);
         {
             const bool unsure = to == -1;
             if (__any_sync(kFull, unsure)) {
                 if (unsure) {
                     ++rck;
-                    to = exact_dep(P, sweep, i, w, 0, 0, nullptr, 0) ? 1 : 0;
+                    to = exact_dep(P, R, sweep, i, w, 0, 0, nullptr, 0) ? 1 : 0;
                 }
             }
         }
@@ -393,9 +395,7 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
         if (m > P.lens_cap) atomicCAS(P.err, kErrNone, kErrCandCap);
     }
     rck = __reduce_add_sync(kFull, rck);
-    if (lane == 0 && rck)
-        atomicAdd(P.counters + (size_t)(i % kCounterSlots) * kNumCounters + kRechecks,
-                  (unsigned long long)rck);
+    if (lane == 0 && rck) count_one(P, r, kRechecks, (unsigned long long)rck);
 }
 
 constexpr int kMaxLensCTA = 256;   // lens points of one cell staged in shared memory
@@ -446,11 +446,13 @@ __global__ void __launch_bounds__(kMaxThreads)
         sh.f = s_dyn;
         sh.k = (int *)(s_dyn + nthr);
     }
-    const Sched S = *P.sched;
+    const int r = P.cta_rep[blockIdx.x];
+    const Rep &R = P.reps[r];
+    const Sched *S = P.sched + r;
     if (phase == 7 && blockIdx.x == 0 && tid == 0) atomicAdd(P.sweep, 1ull);
-    const uint32_t sweep = S.sweep;
-    const CellTask T = cell_task(P, S, phase);
-    clear_next(P, S, T.cell);
+    const uint32_t sweep = S->sweep;
+    const CellTask T = cell_task(P, R, r, phase);
+    clear_next(P, sweep, T.cell);
     const int n_own = min(T.n_own, P.cap);
     if (n_own == 0) return;
     const int cx = T.cx, cy = T.cy, cz = T.cz;
@@ -462,10 +464,10 @@ __global__ void __launch_bounds__(kMaxThreads)
         s_nacc = 0;
     }
     cta_sync<WARP>();
-    if (tid < P.n_stencil * P.n_stencil * P.n_stencil) {
+    if (tid < R.n_stencil * R.n_stencil * R.n_stencil) {
         int dx, dy, dz;
-        const int c = stencil_cell(P, tid, cx, cy, cz, dx, dy, dz);
-        const float fx = (float)dx * P.w32, fy = (float)dy * P.w32, fz = (float)dz * P.w32;
+        const int c = stencil_cell(R, tid, cx, cy, cz, dx, dy, dz);
+        const float fx = (float)dx * R.w32, fy = (float)dy * R.w32, fz = (float)dz * R.w32;
         const int m = c == T.cell ? n_own : min(T.count[c], P.cap);
         const float4 *bin = P.bins + (size_t)c * P.cap;
         for (int s = 0; s < m; ++s) {
@@ -488,17 +490,17 @@ __global__ void __launch_bounds__(kMaxThreads)
     // displacements and depletant headers
     for (int q = tid; q < n_own; q += nthr) {
         const int v = s_tmp_i[q];
-        int r = 0;
-        for (int u = 0; u < n_own; ++u) r += s_tmp_i[u] < v ? 1 : 0;
-        s_own[r] = v;
-        s_own_slot[r] = s_tmp_slot[q];
-        s_own_bin[r] = q;
-        s_mv[r] = P.lens_move[v];
-        if (P.has_dep) s_hdr[r] = P.lens_hdr[v];
+        int rk = 0;
+        for (int u = 0; u < n_own; ++u) rk += s_tmp_i[u] < v ? 1 : 0;
+        s_own[rk] = v;
+        s_own_slot[rk] = s_tmp_slot[q];
+        s_own_bin[rk] = q;
+        s_mv[rk] = P.lens_move[v];
+        if (R.has_dep) s_hdr[rk] = P.lens_hdr[v];
     }
     cta_sync<WARP>();
     // and their lens points
-    if (P.has_dep) {
+    if (R.has_dep) {
         if (tid == 0) {
             int off = 0;
             for (int q = 0; q < n_own; ++q) {
@@ -532,14 +534,14 @@ __global__ void __launch_bounds__(kMaxThreads)
         const float4 mv = s_mv[q];
         const float rn0 = ri.x + mv.x, rn1 = ri.y + mv.y, rn2 = ri.z + mv.z;
         // a3: cell-exit check with margin (exact when within it)
-        const float mc = P.m_cell, wc = P.w32;
+        const float mc = R.m_cell, wc = R.w32;
         const bool out = rn0 < -mc || rn0 > wc + mc || rn1 < -mc || rn1 > wc + mc ||
                          rn2 < -mc || rn2 > wc + mc;
         const bool edge = rn0 <= mc || rn0 >= wc - mc || rn1 <= mc || rn1 >= wc - mc ||
                           rn2 <= mc || rn2 >= wc - mc;
         bool exits = out;
         if (!out && edge) {
-            exits = exact_cell_exit(P, sweep, i, cx, cy, cz);
+            exits = exact_cell_exit(P, R, S, sweep, i, cx, cy, cz);
             if (tid == 0) ++c_rck;
         }
         if (exits) {
@@ -567,22 +569,22 @@ __global__ void __launch_bounds__(kMaxThreads)
                     d0 = cp.x - rn0;
                     d1 = cp.y - rn1;
                     d2 = cp.z - rn2;
-                    if (d0 > P.half_L32) d0 -= P.L32; else if (d0 < -P.half_L32) d0 += P.L32;
-                    if (d1 > P.half_L32) d1 -= P.L32; else if (d1 < -P.half_L32) d1 += P.L32;
-                    if (d2 > P.half_L32) d2 -= P.L32; else if (d2 < -P.half_L32) d2 += P.L32;
+                    if (d0 > R.half_L32) d0 -= R.L32; else if (d0 < -R.half_L32) d0 += R.L32;
+                    if (d1 > R.half_L32) d1 -= R.L32; else if (d1 < -R.half_L32) d1 += R.L32;
+                    if (d2 > R.half_L32) d2 -= R.L32; else if (d2 < -R.half_L32) d2 += R.L32;
                     r2 = norm2f(d0, d1, d2);
-                    t = tri(r2, P.T_contact32, P.m_r2);
+                    t = tri(r2, R.T_contact32, R.m_r2);
                 }
             }
             const bool unsure = t == -1;
             if (__any_sync(kFull, unsure)) {
                 if (unsure) {
                     ++c_rck;
-                    t = exact_pair(P, sweep, i, pj, s_accl, nacc) ? 1 : 0;
+                    t = exact_pair(P, R, sweep, i, pj, s_accl, nacc) ? 1 : 0;
                 }
             }
             if (t == 1) ov = 1;
-            const bool take = pj >= 0 && r2 < P.nb_cut2_32;
+            const bool take = pj >= 0 && r2 < R.nb_cut2_32;
             if (WARP) {
                 const unsigned b = __ballot_sync(kFull, take);
                 const int slot = nnb + __popc(b & lt);
@@ -604,7 +606,7 @@ __global__ void __launch_bounds__(kMaxThreads)
         }
 
         bool accept = true;
-        if (P.has_dep) {
+        if (R.has_dep) {
             // a5: N_p and the lens points come from the lens kernel
             const int4 hd = s_hdr[q];
             const int n_p = hd.x;
@@ -632,7 +634,7 @@ __global__ void __launch_bounds__(kMaxThreads)
                     for (int b = 0; b < nnb; ++b) {
                         const float4 d = s_nb[b];
                         const int tn = tri(norm2f(Lm.x - d.x, Lm.y - d.y, Lm.z - d.z),
-                                           P.T_dep32, P.m_r2);
+                                           R.T_dep32, R.m_r2);
                         if (tn == 1) {
                             hit = true;
                             break;
@@ -646,7 +648,7 @@ __global__ void __launch_bounds__(kMaxThreads)
                     if (__any_sync(kFull, unsure)) {
                         if (unsure) {
                             ++o.rck;
-                            cls = exact_free_nb(P, sweep, i, tt, s_nb, nnb, s_accl, nacc) ? 1 : 0;
+                            cls = exact_free_nb(P, R, sweep, i, tt, s_nb, nnb, s_accl, nacc) ? 1 : 0;
                         }
                     }
                 }
@@ -671,7 +673,7 @@ __global__ void __launch_bounds__(kMaxThreads)
                 } else {
                     double f = -1.0;
                     if (blocking) {
-                        const CbResult32 r = cb_factor_fp32(P, sweep, i, (uint32_t)kk, o0, o1, o2,
+                        const CbResult32 r = cb_factor_fp32(P, R, sweep, i, (uint32_t)kk, o0, o1, o2,
                                                             s_nb, nnb, s_accl, nacc);
                         f = r.f;
                         o.fwd += r.fwd_ok;
@@ -700,7 +702,7 @@ __global__ void __launch_bounds__(kMaxThreads)
                 if (!CB) ++c_dep;
                 else ++c_cb;
             } else if (CB && tid == 0 && o.nblock > 0) {
-                const uint4 wa = draw(P.key0, P.key1, sweep, (uint32_t)i, kPAccept, 0, 0);
+                const uint4 wa = draw(R.key0, R.key1, sweep, (uint32_t)(i - R.off), kPAccept, 0, 0);
                 if (!(u53(wa.x, wa.y) < o.W)) {
                     accept = false;
                     ++c_cb;
@@ -736,7 +738,7 @@ __global__ void __launch_bounds__(kMaxThreads)
     const int nacc = s_nacc;
     for (int a = tid; a < nacc; a += nthr) {
         const int j = s_accl[a];
-        P.pos[j] = moved64(P, sweep, j);
+        P.pos[j] = moved64(P, R, sweep, j);
     }
 
     unsigned long long cnt[kNumCounters] = {0};
@@ -756,7 +758,7 @@ __global__ void __launch_bounds__(kMaxThreads)
     cnt[kCbRevOk] = c_rev;
     cnt[kCapHits] = c_cap;
     cnt[kRechecks] = c_rck;
-    flush_counters(P, cnt);
+    flush_counters(P, r, cnt);
 }
 
 }  // namespace hpmc

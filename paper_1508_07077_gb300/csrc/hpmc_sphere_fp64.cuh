@@ -8,20 +8,20 @@ namespace hpmc {
 
 struct SphereFP64 {
     // depletant at v (relative to the colloid centre) overlaps the colloid
-    static __device__ __forceinline__ bool dep(const SimParams &P, double v0, double v1, double v2)
+    static __device__ __forceinline__ bool dep(const Rep &R, double v0, double v1, double v2)
     {
-        return norm2(v0, v1, v2) < P.R_dep2;
+        return norm2(v0, v1, v2) < R.R_dep2;
     }
 };
 
 // Is the point y (relative to the new reference point) free of every
 // neighbour in the shared list?
-__device__ __forceinline__ bool free_of_nb_fp64(const SimParams &P, double y0, double y1,
-                                                double y2, const double4 *nb, int nnb)
+__device__ __forceinline__ bool free_of_nb_fp64(const Rep &R, double y0, double y1, double y2,
+                                                const double4 *nb, int nnb)
 {
     for (int a = 0; a < nnb; ++a) {
         const double4 d = nb[a];
-        if (SphereFP64::dep(P, y0 - d.x, y1 - d.y, y2 - d.z)) return false;
+        if (SphereFP64::dep(R, y0 - d.x, y1 - d.y, y2 - d.z)) return false;
     }
     return true;
 }
@@ -34,24 +34,24 @@ struct CbResult {
 // Configurational-bias factor of blocking depletant k (Sec. III.D, Eq. 12):
 // f = N'_insert / (N_insert + 1); n_trial forward trials in the old
 // circumsphere, n_trial - 1 reverse trials in the new one.
-__device__ __noinline__ CbResult cb_factor_fp64(const SimParams &P, uint32_t sweep, uint32_t tag,
+__device__ __noinline__ CbResult cb_factor_fp64(const Rep &R, uint32_t sweep, uint32_t tag,
                                                 uint32_t k, double o0, double o1, double o2,
                                                 const double4 *nb, int nnb)
 {
     CbResult r = {0.0, 0u, 0u, 0u};
-    const int n_fwd = P.n_trial, n_rev = P.n_trial - 1;
+    const int n_fwd = R.n_trial, n_rev = R.n_trial - 1;
     int nf = 0, nr = 0, found = 0;
     uint32_t t = 0, t_max = 64u * (uint32_t)(n_fwd + 1);
     while (found < n_fwd && t < t_max) {
-        const uint4 w = draw(P.key0, P.key1, sweep, tag, kPCbFwd, k, t);
+        const uint4 w = draw(R.key0, R.key1, sweep, tag, kPCbFwd, k, t);
         ++t;
-        const double e0 = P.R_s * s11(w.x), e1 = P.R_s * s11(w.y), e2 = P.R_s * s11(w.z);
-        if (!(norm2(e0, e1, e2) < P.R_s2)) continue;
+        const double e0 = R.R_s * s11(w.x), e1 = R.R_s * s11(w.y), e2 = R.R_s * s11(w.z);
+        if (!(norm2(e0, e1, e2) < R.R_s2)) continue;
         ++found;
         const double y0 = o0 + e0, y1 = o1 + e1, y2 = o2 + e2;
-        if (!SphereFP64::dep(P, e0, e1, e2)) continue;      // must overlap the old pose
-        if (SphereFP64::dep(P, y0, y1, y2)) continue;       // must not overlap the new pose
-        if (!free_of_nb_fp64(P, y0, y1, y2, nb, nnb)) continue;
+        if (!SphereFP64::dep(R, e0, e1, e2)) continue;      // must overlap the old pose
+        if (SphereFP64::dep(R, y0, y1, y2)) continue;       // must not overlap the new pose
+        if (!free_of_nb_fp64(R, y0, y1, y2, nb, nnb)) continue;
         ++nf;
     }
     if (found < n_fwd) ++r.caps;
@@ -59,14 +59,14 @@ __device__ __noinline__ CbResult cb_factor_fp64(const SimParams &P, uint32_t swe
     t_max = 64u * (uint32_t)(n_rev + 1);
     found = 0;
     while (found < n_rev && t < t_max) {
-        const uint4 w = draw(P.key0, P.key1, sweep, tag, kPCbRev, k, t);
+        const uint4 w = draw(R.key0, R.key1, sweep, tag, kPCbRev, k, t);
         ++t;
-        const double e0 = P.R_s * s11(w.x), e1 = P.R_s * s11(w.y), e2 = P.R_s * s11(w.z);
-        if (!(norm2(e0, e1, e2) < P.R_s2)) continue;
+        const double e0 = R.R_s * s11(w.x), e1 = R.R_s * s11(w.y), e2 = R.R_s * s11(w.z);
+        if (!(norm2(e0, e1, e2) < R.R_s2)) continue;
         ++found;
-        if (!SphereFP64::dep(P, e0, e1, e2)) continue;                  // overlaps the new pose
-        if (SphereFP64::dep(P, e0 - o0, e1 - o1, e2 - o2)) continue;   // not the old pose
-        if (!free_of_nb_fp64(P, e0, e1, e2, nb, nnb)) continue;
+        if (!SphereFP64::dep(R, e0, e1, e2)) continue;                  // overlaps the new pose
+        if (SphereFP64::dep(R, e0 - o0, e1 - o1, e2 - o2)) continue;   // not the old pose
+        if (!free_of_nb_fp64(R, e0, e1, e2, nb, nnb)) continue;
         ++nr;
     }
     if (found < n_rev) ++r.caps;
@@ -92,22 +92,25 @@ __global__ void __launch_bounds__(kMaxThreads)
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
-    const Sched S = *P.sched;
+    const int r = P.cta_rep[blockIdx.x];
+    const Rep &R = P.reps[r];
+    const Sched &S = P.sched[r];
     if (phase == 7 && blockIdx.x == 0 && tid == 0) atomicAdd(P.sweep, 1ull);
     const uint32_t sweep = S.sweep;
-    const CellTask T = cell_task(P, S, phase);
-    clear_next(P, S, T.cell);
+    const CellTask T = cell_task(P, R, r, phase);
+    clear_next(P, sweep, T.cell);
     const int n_own = min(T.n_own, P.cap);
     if (n_own == 0) return;
     own_members_sorted(P, T.cell, n_own, s_tmp, s_own);
-    const int cx = T.cx, cy = T.cy, cz = T.cz, nc = P.nc;
+    const int cx = T.cx, cy = T.cy, cz = T.cz, nc = R.nc;
+    const unsigned long long *Tab = P.T + R.t_off;
 
     // candidate neighbours: every colloid of the (deduplicated) 27-cell stencil
     if (tid == 0) s_ncand = 0;
     __syncthreads();
-    if (tid < P.n_stencil * P.n_stencil * P.n_stencil) {
+    if (tid < R.n_stencil * R.n_stencil * R.n_stencil) {
         int dx, dy, dz;
-        const int c = stencil_cell(P, tid, cx, cy, cz, dx, dy, dz);
+        const int c = stencil_cell(R, tid, cx, cy, cz, dx, dy, dz);
         const int m = min(T.count[c], P.cap);
         for (int s = 0; s < m; ++s) {
             const int slot = atomicAdd(&s_ncand, 1);
@@ -125,25 +128,25 @@ __global__ void __launch_bounds__(kMaxThreads)
 
     for (int q = 0; q < n_own; ++q) {
         const int i = s_own[q];
-        const uint32_t tag = (uint32_t)i;
+        const uint32_t tag = (uint32_t)(i - R.off);
         const double4 pi = P.pos[i];
         cnt[kMoves]++;
         cnt[kTranslate]++;
 
         // a3: translation proposal, wrap, cell-exit check
-        const uint4 wm = draw(P.key0, P.key1, sweep, tag, kPMove, 0, 0);
-        const double xn0 = wrap_box(pi.x + P.d_max * s11(wm.x), P.L);
-        const double xn1 = wrap_box(pi.y + P.d_max * s11(wm.y), P.L);
-        const double xn2 = wrap_box(pi.z + P.d_max * s11(wm.z), P.L);
-        if (cell_coord(xn0, S.sigma[0], P.L, P.w, nc) != cx ||
-            cell_coord(xn1, S.sigma[1], P.L, P.w, nc) != cy ||
-            cell_coord(xn2, S.sigma[2], P.L, P.w, nc) != cz) {
+        const uint4 wm = draw(R.key0, R.key1, sweep, tag, kPMove, 0, 0);
+        const double xn0 = wrap_box(pi.x + R.d_max * s11(wm.x), R.L);
+        const double xn1 = wrap_box(pi.y + R.d_max * s11(wm.y), R.L);
+        const double xn2 = wrap_box(pi.z + R.d_max * s11(wm.z), R.L);
+        if (cell_coord(xn0, S.sigma[0], R.L, R.w, nc) != cx ||
+            cell_coord(xn1, S.sigma[1], R.L, R.w, nc) != cy ||
+            cell_coord(xn2, S.sigma[2], R.L, R.w, nc) != cz) {
             cnt[kRejCell]++;
             continue;
         }
-        const double o0 = min_image(pi.x - xn0, P.L, P.half_L);
-        const double o1 = min_image(pi.y - xn1, P.L, P.half_L);
-        const double o2 = min_image(pi.z - xn2, P.L, P.half_L);
+        const double o0 = min_image(pi.x - xn0, R.L, R.half_L);
+        const double o1 = min_image(pi.y - xn1, R.L, R.half_L);
+        const double o2 = min_image(pi.z - xn2, R.L, R.half_L);
 
         // a4: colloid overlap at the new pose; collect neighbours in range
         if (tid == 0) {
@@ -156,12 +159,12 @@ __global__ void __launch_bounds__(kMaxThreads)
             const int pj = s_cand[j];
             if (pj == i) continue;
             const double4 xj = P.pos[pj];
-            const double d0 = min_image(xj.x - xn0, P.L, P.half_L);
-            const double d1 = min_image(xj.y - xn1, P.L, P.half_L);
-            const double d2 = min_image(xj.z - xn2, P.L, P.half_L);
+            const double d0 = min_image(xj.x - xn0, R.L, R.half_L);
+            const double d1 = min_image(xj.y - xn1, R.L, R.half_L);
+            const double d2 = min_image(xj.z - xn2, R.L, R.half_L);
             const double r2 = norm2(d0, d1, d2);
-            if (r2 < P.contact2) ov = 1;
-            if (r2 < P.nb_cut2) {
+            if (r2 < R.contact2) ov = 1;
+            if (r2 < R.nb_cut2) {
                 const int slot = atomicAdd(&s_nnb, 1);
                 s_nb[slot] = make_double4(d0, d1, d2, 0.0);
             }
@@ -173,10 +176,10 @@ __global__ void __launch_bounds__(kMaxThreads)
         const int nnb = s_nnb;
 
         bool accept = true;
-        if (P.has_dep) {
+        if (R.has_dep) {
             // a5: Poisson count
-            const uint4 wp = draw(P.key0, P.key1, sweep, tag, kPPoisson, 0, 0);
-            const int n_p = poisson_count(P.T, P.nF, u53_int(wp.x, wp.y), lane);
+            const uint4 wp = draw(R.key0, R.key1, sweep, tag, kPPoisson, 0, 0);
+            const int n_p = poisson_count(Tab, R.nF, u53_int(wp.x, wp.y), lane);
             cnt[kDepDrawn] += (unsigned long long)n_p;
 
             // a6: depletants along the attempt stream, nthr attempts per pass
@@ -190,11 +193,11 @@ __global__ void __launch_bounds__(kMaxThreads)
                 double e0 = 0.0, e1 = 0.0, e2 = 0.0;
                 bool inside = false;
                 if (t < t_max) {
-                    const uint4 w = draw(P.key0, P.key1, sweep, tag, kPDep, 0, t);
-                    e0 = P.R_s * s11(w.x);
-                    e1 = P.R_s * s11(w.y);
-                    e2 = P.R_s * s11(w.z);
-                    inside = norm2(e0, e1, e2) < P.R_s2;
+                    const uint4 w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, t);
+                    e0 = R.R_s * s11(w.x);
+                    e1 = R.R_s * s11(w.y);
+                    e2 = R.R_s * s11(w.z);
+                    inside = norm2(e0, e1, e2) < R.R_s2;
                 }
                 const unsigned bal = __ballot_sync(kFull, inside);
                 if (lane == 0) s_warp[warp] = __popc(bal);
@@ -210,13 +213,13 @@ __global__ void __launch_bounds__(kMaxThreads)
                 if (inside && k < n_p) {
                     // irrelevant unless it overlaps the new pose; ignored if it
                     // overlaps the old configuration
-                    if (SphereFP64::dep(P, e0, e1, e2) &&
-                        !SphereFP64::dep(P, e0 - o0, e1 - o1, e2 - o2) &&
-                        free_of_nb_fp64(P, e0, e1, e2, s_nb, nnb))
+                    if (SphereFP64::dep(R, e0, e1, e2) &&
+                        !SphereFP64::dep(R, e0 - o0, e1 - o1, e2 - o2) &&
+                        free_of_nb_fp64(R, e0, e1, e2, s_nb, nnb))
                         blocking = true;
                 }
                 // depletants classified up to an early exit (same count as a serial loop)
-                if (P.n_trial == 0) {
+                if (R.n_trial == 0) {
                     if (blocking) atomicMin(&s_kmin, k);
                     if (__syncthreads_or(blocking)) {
                         cnt[kDepBlocking] += 1;
@@ -229,12 +232,12 @@ __global__ void __launch_bounds__(kMaxThreads)
                     // a7: CB factors of this pass, multiplied in ascending k
                     double f = -1.0;
                     if (blocking) {
-                        const CbResult r = cb_factor_fp64(P, sweep, tag, (uint32_t)k, o0, o1, o2,
+                        const CbResult cr = cb_factor_fp64(R, sweep, tag, (uint32_t)k, o0, o1, o2,
                                                           s_nb, nnb);
-                        f = r.f;
-                        cnt[kCbFwdOk] += r.fwd_ok;
-                        cnt[kCbRevOk] += r.rev_ok;
-                        cnt[kCapHits] += r.caps;
+                        f = cr.f;
+                        cnt[kCbFwdOk] += cr.fwd_ok;
+                        cnt[kCbRevOk] += cr.rev_ok;
+                        cnt[kCapHits] += cr.caps;
                     }
                     s_f[tid] = f;
                     s_k[tid] = k;
@@ -268,16 +271,16 @@ __global__ void __launch_bounds__(kMaxThreads)
             if (!rejected && k0 < n_p && tid == 0) cnt[kCapHits]++;
             if (rejected) {
                 accept = false;
-                if (P.n_trial == 0) cnt[kRejDep]++;
+                if (R.n_trial == 0) cnt[kRejDep]++;
                 else cnt[kRejCb]++;
-            } else if (P.n_trial > 0 && tid == 0 && nblock > 0) {
-                const uint4 wa = draw(P.key0, P.key1, sweep, tag, kPAccept, 0, 0);
+            } else if (R.n_trial > 0 && tid == 0 && nblock > 0) {
+                const uint4 wa = draw(R.key0, R.key1, sweep, tag, kPAccept, 0, 0);
                 if (!(u53(wa.x, wa.y) < W)) {
                     accept = false;
                     cnt[kRejCb]++;
                 }
             }
-            if (P.n_trial > 0) {
+            if (R.n_trial > 0) {
                 if (tid == 0) s_acc = accept ? 1 : 0;
                 __syncthreads();
                 accept = s_acc != 0;
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(kMaxThreads)
         for (int k = 0; k < kNumCounters; ++k)
             if (k != kCbFwdOk && k != kCbRevOk && k != kCapHits) cnt[k] = 0;
     }
-    flush_counters(P, cnt);
+    flush_counters(P, r, cnt);
 }
 
 }  // namespace hpmc

@@ -22,7 +22,8 @@ HPMC_SPHERE, HPMC_HEMISPHERE, HPMC_SPHEROID = 0, 1, 2
 HPMC_FP64, HPMC_FP32_RECHECK = 0, 1
 HPMC_HOST, HPMC_DEVICE = 0, 1
 
-EXPORTS = ("hpmc_init", "hpmc_set_shape", "hpmc_set_depletant", "hpmc_set_moves",
+EXPORTS = ("hpmc_init", "hpmc_init_batch", "hpmc_get_replica", "hpmc_set_replica_moves",
+           "hpmc_set_shape", "hpmc_set_depletant", "hpmc_set_moves",
            "hpmc_set_cells", "hpmc_set_launch", "hpmc_set_fp32_margin", "hpmc_set_timing",
            "hpmc_get_timing", "hpmc_sweep", "hpmc_get_state",
            "hpmc_set_state", "hpmc_reset_counters", "hpmc_sync", "hpmc_cell_list",
@@ -33,6 +34,15 @@ class HPMCError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
         super().__init__("%s: %s (%d)" % (where, strerror(code), code))
+
+
+class hpmc_replica_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("box_l", ctypes.c_double),
+                ("pos", ctypes.c_void_p), ("quat", ctypes.c_void_p),
+                ("q", ctypes.c_double), ("n_r", ctypes.c_double), ("n_trial", ctypes.c_int),
+                ("d_max", ctypes.c_double), ("a_max", ctypes.c_double),
+                ("p_translate", ctypes.c_double), ("replica", ctypes.c_uint32),
+                ("n_cell", ctypes.c_int)]
 
 
 class hpmc_counters(ctypes.Structure):
@@ -61,6 +71,11 @@ def load(path: str = LIB_PATH):
     vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
     L.hpmc_init.argtypes = [ctypes.POINTER(vp), ip, ctypes.c_double, vp, vp, ip,
                             ctypes.c_uint64, ctypes.c_uint32, ip, ip]
+    L.hpmc_init_batch.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(hpmc_replica_desc), ip,
+                                  dp, ip, ctypes.c_uint64, ip, ip]
+    L.hpmc_get_replica.argtypes = [vp, ip, vp, vp, ctypes.POINTER(hpmc_counters)]
+    L.hpmc_set_replica_moves.argtypes = [vp, ip, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double]
     L.hpmc_set_shape.argtypes = [vp, ip, dp, ip]
     L.hpmc_set_depletant.argtypes = [vp, ctypes.c_double, ctypes.c_double, ip]
     L.hpmc_set_moves.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -132,6 +147,49 @@ def hpmc_init(n, box_l, pos, quat=None, seed=1, replica=0, precision=HPMC_FP64, 
                             int(seed), int(replica), int(precision), int(device)),
            "hpmc_init")
     return ctx
+
+
+def hpmc_init_batch(replicas, shape=HPMC_SPHERE, shape_params=(1.0,), seed=1,
+                    precision=HPMC_FP64, device=0):
+    """replicas: list of dicts with keys n, box_l, pos (n x 3 float64), quat
+    (optional), q, n_r, n_trial, d_max, a_max, p_translate, replica, n_cell."""
+    arr = (hpmc_replica_desc * len(replicas))()
+    keep = []
+    for k, r in enumerate(replicas):
+        pos = np.ascontiguousarray(r["pos"], dtype=np.float64)
+        keep.append(pos)
+        quat = r.get("quat")
+        if quat is not None:
+            quat = np.ascontiguousarray(quat, dtype=np.float64)
+            keep.append(quat)
+        arr[k] = hpmc_replica_desc(
+            int(r["n"]), float(r["box_l"]), pos.ctypes.data,
+            quat.ctypes.data if quat is not None else None, float(r.get("q", 0.0)),
+            float(r.get("n_r", 0.0)), int(r.get("n_trial", 0)), float(r.get("d_max", 0.1)),
+            float(r.get("a_max", 0.0)), float(r.get("p_translate", 1.0)),
+            int(r.get("replica", k)), int(r.get("n_cell", 0)))
+    sp = np.ascontiguousarray(shape_params, dtype=np.float64)
+    ctx = ctypes.c_void_p()
+    _check(load().hpmc_init_batch(ctypes.byref(ctx), len(replicas), arr, int(shape),
+                                  sp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(sp),
+                                  int(seed), int(precision), int(device)), "hpmc_init_batch")
+    return ctx
+
+
+def hpmc_get_replica(ctx, r, n, with_quat=False):
+    """(pos, quat or None, counters dict) of replica r (n colloids)."""
+    pos = np.empty((n, 3))
+    quat = np.empty((n, 4)) if with_quat else None
+    cnt = hpmc_counters()
+    _check(load().hpmc_get_replica(ctx, int(r), pos.ctypes.data,
+                                   quat.ctypes.data if quat is not None else None,
+                                   ctypes.byref(cnt)), "hpmc_get_replica")
+    return pos, quat, cnt.as_dict()
+
+
+def hpmc_set_replica_moves(ctx, r, d_max, a_max=0.0, p_translate=1.0):
+    _check(load().hpmc_set_replica_moves(ctx, int(r), float(d_max), float(a_max),
+                                         float(p_translate)), "hpmc_set_replica_moves")
 
 
 def hpmc_set_shape(ctx, kind, params):
