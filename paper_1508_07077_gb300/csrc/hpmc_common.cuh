@@ -21,7 +21,7 @@ namespace hpmc {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kMaxCand = 256;        // colloids in a 27-cell neighbourhood (capacity)
 constexpr int kMaxThreads = 256;     // 8 warps per colloid at most
-constexpr int kMaxCellCap = 64;      // colloids per cell bin (capacity)
+constexpr int kMaxCellCap = 32;      // colloids per cell bin (capacity; checked from the packing bound)
 constexpr int kRepSlots = 16;        // per replica, counters are spread over slots (fewer hot atomics)
 constexpr int kNumCounters = 16;
 

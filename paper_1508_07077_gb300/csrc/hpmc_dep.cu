@@ -177,6 +177,10 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
     const double v_shape = (kPi / 6.0) * p.sp[0] * p.sp[0] * p.sp[0];
     const double ext = w + 2.0 * R_circ;
     if (ext * ext * ext * 0.7405 / v_shape >= (double)kMaxCellCap) return HPMC_ERR_CAP;
+    // the neighbourhood of a depletant (a ball of radius 2 R_s + 0.01 around the
+    // moved colloid) holds at most the FP32 kernel's kMaxNb colloids
+    const double nb_ext = 2.0 * R_s + 0.01 + R_circ;
+    if (nb_ext * nb_ext * nb_ext * (4.0 / 3.0 * kPi) * 0.7405 / v_shape >= 64.0) return HPMC_ERR_CAP;
     F.clear();
     if (lambda > 0.0) {
         int rc = build_table(lambda, F);

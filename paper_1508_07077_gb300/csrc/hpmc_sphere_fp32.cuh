@@ -398,8 +398,9 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
     if (lane == 0 && rck) count_one(P, r, kRechecks, (unsigned long long)rck);
 }
 
-constexpr int kMaxLensCTA = 256;   // lens points of one cell staged in shared memory
-constexpr int kMaxNb = 128;        // neighbours within reach of a depletant (hard spheres: <= ~36)
+constexpr int kMaxLensCTA = 128;   // lens points of one cell staged in shared memory (more: read
+                                   // from global memory)
+constexpr int kMaxNb = 64;         // neighbours within reach of a depletant (hard spheres: <= ~27)
 
 // CTA-wide barrier / OR, reduced to warp operations when the CTA is one warp.
 template <bool WARP>
@@ -424,7 +425,7 @@ __device__ __forceinline__ bool cta_any(bool p)
 // off.  WARP: the CTA is a single warp (barriers become warp operations).
 // ---------------------------------------------------------------------------
 template <bool CB, bool WARP>
-__global__ void __launch_bounds__(kMaxThreads)
+__global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 24) : 1)
     k_phase_sphere_fp32(const __grid_constant__ SimParams P, int phase)
 {
     __shared__ float4 s_cpos[kMaxCand];  // candidates relative to this cell's origin; index in .w
