@@ -21,7 +21,8 @@ namespace hpmc {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kMaxCand = 256;        // colloids in a 27-cell neighbourhood (capacity)
 constexpr int kMaxThreads = 256;     // 8 warps per colloid at most
-constexpr int kMaxCellCap = 32;      // colloids per cell bin (capacity; checked from the packing bound)
+constexpr int kMaxCellCap = 64;      // colloids per cell bin, largest capacity (checked from the packing bound)
+constexpr int kSmallCellCap = 32;    // capacity of the usual cells (width near d_colloid + d_depletant)
 constexpr int kRepSlots = 16;        // per replica, counters are spread over slots (fewer hot atomics)
 constexpr int kNumCounters = 16;
 
@@ -107,6 +108,7 @@ struct Rep {
     float w32, L32, half_L32, R_s32, T_s32, T_dep32, T_contact32, nb_cut2_32, d_max32;
     float m_r2;            // bound on |r2_fp32 - r2_fp64| (+ threshold rounding), doubled
     float m_cell;          // bound on the error of a cell-relative coordinate
+    double pad_cell_bound; // host: packing bound on a cell's population
 };
 
 struct SimParams {

@@ -59,6 +59,7 @@ struct hpmc_ctx {
     std::vector<RepHost> reps;
     std::vector<Rep> rdev;        // derived per-replica records (host copy)
     int n_total = 0, n_cells = 0, n_cta = 0, nF_max = 0;
+    int cap = kSmallCellCap;      // cell bin capacity of this context
 
     // device buffers
     double4 *d_pos = nullptr, *d_quat = nullptr;
@@ -176,7 +177,9 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
     // (densest packing); spheres only for now
     const double v_shape = (kPi / 6.0) * p.sp[0] * p.sp[0] * p.sp[0];
     const double ext = w + 2.0 * R_circ;
-    if (ext * ext * ext * 0.7405 / v_shape >= (double)kMaxCellCap) return HPMC_ERR_CAP;
+    const double cell_bound = ext * ext * ext * 0.7405 / v_shape;
+    if (cell_bound >= (double)kMaxCellCap) return HPMC_ERR_CAP;
+    R.pad_cell_bound = cell_bound;
     // the neighbourhood of a depletant (a ball of radius 2 R_s + 0.01 around the
     // moved colloid) holds at most the FP32 kernel's kMaxNb colloids
     const double nb_ext = 2.0 * R_s + 0.01 + R_circ;
@@ -244,7 +247,7 @@ SimParams make_params(hpmc_ctx *c)
     std::memset(&P, 0, sizeof P);
     P.n_rep = (int)c->reps.size();
     P.n_total = c->n_total;
-    P.cap = kMaxCellCap;
+    P.cap = c->cap;
     P.lens_cap = c->lens_cap;
     P.reps = c->d_reps;
     P.rep_of = c->d_rep_of;
@@ -277,7 +280,8 @@ int enqueue_cells(hpmc_ctx *c, cudaStream_t s)
     return HPMC_OK;
 }
 
-void launch_phase(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
+template <int CAP>
+void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
 {
     const int threads = 32 * c->prm.warps;
     const size_t dyn = (size_t)threads * (sizeof(double) + sizeof(int));
@@ -286,15 +290,21 @@ void launch_phase(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
     if (c->precision == HPMC_FP32_RECHECK) {
         const bool warp = threads == 32;
         if (cb) {
-            if (warp) k_phase_sphere_fp32<true, true><<<c->n_cta, threads, dyn, s>>>(P, phase);
-            else k_phase_sphere_fp32<true, false><<<c->n_cta, threads, dyn, s>>>(P, phase);
+            if (warp) k_phase_sphere_fp32<true, true, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
+            else k_phase_sphere_fp32<true, false, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
         } else {
-            if (warp) k_phase_sphere_fp32<false, true><<<c->n_cta, threads, dyn, s>>>(P, phase);
-            else k_phase_sphere_fp32<false, false><<<c->n_cta, threads, dyn, s>>>(P, phase);
+            if (warp) k_phase_sphere_fp32<false, true, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
+            else k_phase_sphere_fp32<false, false, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
         }
     } else {
-        k_phase_sphere_fp64<<<c->n_cta, threads, 0, s>>>(P, phase);
+        k_phase_sphere_fp64<CAP><<<c->n_cta, threads, 0, s>>>(P, phase);
     }
+}
+
+void launch_phase(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
+{
+    if (c->cap == kSmallCellCap) launch_phase_cap<kSmallCellCap>(c, P, phase, s);
+    else launch_phase_cap<kMaxCellCap>(c, P, phase, s);
 }
 
 void launch_lens(hpmc_ctx *c, const SimParams &P, cudaStream_t s)
@@ -429,7 +439,12 @@ int prepare(hpmc_ctx *c)
         cta_off += h * h * h;
         if (R.nF > nF_max) nF_max = R.nF;
     }
+    int cap = kSmallCellCap;
+    for (const Rep &R : rd)
+        if (R.pad_cell_bound >= (double)kSmallCellCap) cap = kMaxCellCap;
     DeviceGuard g(c->device);
+    if (cap != c->cap) c->cells_alloc = -2;  // force re-allocation of the bins
+    c->cap = cap;
     if (cell_off != c->cells_alloc) {
         cudaFree(c->d_count);
         cudaFree(c->d_bins);
@@ -437,7 +452,7 @@ int prepare(hpmc_ctx *c)
         c->d_bins = nullptr;
         c->cells_alloc = -1;
         CK(cudaMalloc(&c->d_count, sizeof(int) * 2 * (size_t)cell_off));
-        CK(cudaMalloc(&c->d_bins, sizeof(float4) * (size_t)cell_off * kMaxCellCap));
+        CK(cudaMalloc(&c->d_bins, sizeof(float4) * (size_t)cell_off * cap));
         c->cells_alloc = cell_off;
     }
     if (cta_off != c->cta_alloc) {

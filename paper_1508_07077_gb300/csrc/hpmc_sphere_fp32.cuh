@@ -423,19 +423,20 @@ __device__ __forceinline__ bool cta_any(bool p)
 // displacements and their lens points in shared memory, then moves the
 // colloids one after another.  CB: configurational bias on (n_trial > 0) or
 // off.  WARP: the CTA is a single warp (barriers become warp operations).
+// CAP: capacity of a cell bin (the cell list's stride).
 // ---------------------------------------------------------------------------
-template <bool CB, bool WARP>
+template <bool CB, bool WARP, int CAP>
 __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 24) : 1)
     k_phase_sphere_fp32(const __grid_constant__ SimParams P, int phase)
 {
     __shared__ float4 s_cpos[kMaxCand];  // candidates relative to this cell's origin; index in .w
     __shared__ float4 s_nb[kMaxNb];      // neighbours relative to the new position; index in .w
     __shared__ float4 s_lens[kMaxLensCTA];
-    __shared__ int4 s_hdr[kMaxCellCap];
-    __shared__ float4 s_mv[kMaxCellCap];
-    __shared__ int s_tmp_i[kMaxCellCap], s_tmp_slot[kMaxCellCap];
-    __shared__ int s_own[kMaxCellCap], s_own_slot[kMaxCellCap], s_own_bin[kMaxCellCap];
-    __shared__ int s_loff[kMaxCellCap], s_accl[kMaxCellCap];
+    __shared__ int4 s_hdr[CAP];
+    __shared__ float4 s_mv[CAP];
+    __shared__ int s_tmp_i[CAP], s_tmp_slot[CAP];
+    __shared__ int s_own[CAP], s_own_slot[CAP], s_own_bin[CAP];
+    __shared__ int s_loff[CAP], s_accl[CAP];
     __shared__ DepShared sh;
     __shared__ int s_ncand, s_nnb, s_acc, s_nacc;
     extern __shared__ double s_dyn[];

@@ -79,10 +79,11 @@ __device__ __noinline__ CbResult cb_factor_fp64(const Rep &R, uint32_t sweep, ui
 // One colour phase: a CTA per active cell, blockDim = 32 * warps_per_colloid.
 // The cell's colloids move one after another in ascending index; the
 // depletants of each move are spread over the CTA's threads (App. A).
+template <int CAP>
 __global__ void __launch_bounds__(kMaxThreads)
     k_phase_sphere_fp64(const __grid_constant__ SimParams P, int phase)
 {
-    __shared__ int s_own[kMaxCellCap], s_tmp[kMaxCellCap];
+    __shared__ int s_own[CAP], s_tmp[CAP];
     __shared__ int s_cand[kMaxCand];
     __shared__ double4 s_nb[kMaxCand];
     __shared__ double s_f[kMaxThreads];
