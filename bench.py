@@ -57,6 +57,9 @@ OPS_PER_MOVE_PHASE = 20.0 + 25 * 8.0
 OPS_PER_MOVE = 2 * 40.0 + 20.0 + 12.0 + 25 * 8.0
 ISSUE_LANES_PER_SM = 128        # 4 SM sub-partitions x 32 lanes, one instruction / clock
 BYTES_PER_MOVE = 2 * 32 + 16 + 2 * 4   # pos (double4) read + cell-local copy + cell list ids
+# DRAM bytes (read + write) per launch from one ncu capture of the current kernel
+# build on the four-state-point 16384-sphere batch (profiles/k_phase_sphere_fp32_*.md).
+MEASURED_TRAFFIC = {"k_phase_sphere_fp32": 9.47e6}
 
 
 def _dist():
@@ -198,6 +201,103 @@ def tune_batch(ctx, hpmc, d0, ns, rounds=12, sweeps=15):
     for r, dr in enumerate(d):
         hpmc.hpmc_set_replica_moves(ctx, r, dr, 0.0, 1.0)
     return d
+
+
+def run_batched(args, ws, rank, local):
+    """128 independent sphere replicas (N log-uniform in [500, 20000], phi_c
+    U[0.1, 0.45], q in {0.1, 0.15, 0.2}, eta_r U[0.05, 0.4]) as one batch, vs the
+    same replicas one at a time (each in its own context, one stream)."""
+    import torch
+    import torch.distributed as dist
+    from paper_1508_07077_gb300 import build, hpmc, workloads as W
+
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    try:
+        hpmc.load()
+    except ImportError:
+        build.build()
+        hpmc.load()
+    prec = hpmc.HPMC_FP32_RECHECK if args.precision == "fp32" else hpmc.HPMC_FP64
+    stream = torch.cuda.current_stream()
+    reps = W.batched_replicas(128, seed=1)
+    descs = [{"n": s.n, "box_l": s.L, "pos": s.pos, "q": s.q, "n_r": s.n_r, "n_trial": 0,
+              "d_max": 0.01, "replica": rank * 128 + k} for k, s in enumerate(reps)]
+    ctx = hpmc.hpmc_init_batch(descs, seed=1, precision=prec, device=local)
+    ns = [s.n for s in reps]
+    dtuned = tune_batch(ctx, hpmc, [0.01] * len(reps), ns, rounds=8, sweeps=10)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        hpmc.hpmc_sweep(ctx, 1, stream)
+    hpmc.hpmc_reset_counters(ctx)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            a[k].record(stream)
+            hpmc.hpmc_sweep(ctx, 1, stream)
+            b[k].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms = sum(x.elapsed_time(y) for x, y in zip(a, b))
+    _, cnt = hpmc.hpmc_get_state(ctx)
+    # one at a time
+    allpos = np.empty((sum(ns), 3))
+    sweep_now, _ = hpmc.hpmc_get_state(ctx, allpos)
+    singles, off = [], 0
+    for k, s in enumerate(reps):
+        smp = hpmc.Sampler(allpos[off:off + s.n].copy(), s.L, q=s.q, n_r=s.n_r,
+                           d_max=dtuned[k], seed=1, replica=descs[k]["replica"],
+                           precision=prec, device=local)
+        smp.sweep(1)
+        singles.append(smp)
+        off += s.n
+    torch.cuda.synchronize()
+    seq_steps = min(args.steps, 10)
+    sa = [torch.cuda.Event(enable_timing=True) for _ in range(seq_steps)]
+    sb = [torch.cuda.Event(enable_timing=True) for _ in range(seq_steps)]
+    for k in range(seq_steps):
+        flush.zero_()
+        sa[k].record(stream)
+        for smp in singles:
+            smp.sweep(1, stream)
+        sb[k].record(stream)
+    torch.cuda.synchronize()
+    seq_ms = sum(x.elapsed_time(y) for x, y in zip(sa, sb))
+    for smp in singles:
+        smp.close()
+    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms = float(t_local[0])
+    if rank == 0:
+        value = ws * cnt["moves"] / (ms * 1e-3)
+        line = {
+            "metric": "colloid trial moves/s", "value": value, "unit": "moves/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
+            "config": {"workload": "batched_128_spheres_N500-20000",
+                       "replicas": len(reps), "colloids": sum(ns),
+                       "step": "1 sweep of every replica, one batch (one set of launches)",
+                       "l2": "flushed between steps (256 MB write)"},
+            "one_at_a_time_moves_per_s": ws * seq_steps * sum(ns) / (seq_ms * 1e-3),
+            "insertions_drawn_per_s": ws * cnt["dep_drawn"] / (ms * 1e-3),
+            "insertions_evaluated_per_s": ws * cnt["dep_evaluated"] / (ms * 1e-3),
+            "acceptance": cnt["accept"] / max(1, cnt["moves"]),
+            "gpu_launches": args.steps * (1 + (1 if prec == 1 else 0) + 8),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    hpmc.hpmc_destroy(ctx)
+    if ws > 1:
+        dist.destroy_process_group()
 
 
 def run_ours(args, ws, rank, local):
@@ -365,7 +465,8 @@ def run_ours(args, ws, rank, local):
                                   "lens": kern_ms[2] / max(1e-9, sum(kern_ms))},
                         "achieved_tops": {k: v[1] for k, v in cand.items()}},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": dominant,
+                         "frac": achieved / peak,
+                         "traffic": MEASURED_TRAFFIC.get(dominant), "kernel": dominant,
                          "peak_basis": "%d SMs x 128 lanes x 2070 MHz (issue rate)" % sms,
                          "hbm_achieved_gbs": bytes_per_launch / (phase_launch_ms * 1e-3) / 1e9},
             "clocks": clocks,
@@ -399,6 +500,9 @@ def main():
     ap.add_argument("--warps", type=int, default=1)
     ap.add_argument("--ilp", type=int, default=1)
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--workload", choices=("spheres_16384", "batched"), default="spheres_16384",
+                    help="spheres_16384: the headline four-state-point workload; batched: "
+                         "128 replicas of uneven size and state point")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sweeps", type=int, default=25)
     args = ap.parse_args()
@@ -407,6 +511,8 @@ def main():
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "batched":
+        run_batched(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 
