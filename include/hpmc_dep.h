@@ -59,9 +59,11 @@ extern "C" {
 typedef struct hpmc_ctx hpmc_ctx;
 
 /* Event counters, accumulated since creation or hpmc_reset_counters().
- * The first eight are a pure function of the trajectory and are identical
- * on every correct implementation of the method; the rest depend on the
- * evaluation order (early exit) or on the precision form. */
+ * The first nine are a pure function of the trajectory and are identical
+ * on every correct implementation of the method (dep_evaluated is defined in
+ * depletant order, so it does not depend on which lane finds a blocking
+ * depletant first); the rest depend on the evaluation order of the CB trials
+ * or on the precision form. */
 typedef struct hpmc_counters {
     uint64_t moves;            /* trial moves proposed */
     uint64_t accept;           /* accepted */
@@ -71,7 +73,8 @@ typedef struct hpmc_counters {
     uint64_t reject_cb;        /* n_trial > 0: CB weight W = 0 or u >= W */
     uint64_t dep_drawn;        /* sum of Poisson counts N_p over moves that drew them */
     uint64_t translate;        /* translation (not rotation) proposals */
-    uint64_t dep_evaluated;    /* depletants classified before an early exit */
+    uint64_t dep_evaluated;    /* depletants up to and including the first blocking
+                                  one (all N_p when none blocks; n_trial = 0) */
     uint64_t dep_blocking;     /* blocking depletants found */
     uint64_t cb_fwd_ok;        /* successful forward CB reinsertions */
     uint64_t cb_rev_ok;        /* successful reverse CB reinsertions */
