@@ -29,11 +29,18 @@
  * written in the exact operation order that specification fixes, and must be
  * compiled with -ffp-contract=off (no fused multiply-add).
  *
+ *   - Sec. V: anisotropic colloids (hemispheres, discoids = oblate spheroids)
+ *     with quaternion rotation moves; overlap of two convex colloids by
+ *     Minkowski portal refinement on their support functions.
+ *
  * Parity pins (tests/test_oracle_*.py): Poisson moments and pmf (chi^2),
  * Philox uniformity, brute-force neighbour enumeration, the two-colloid
  * Asakura-Oosawa distribution (detailed balance, Eqs. 5-11 and 12), the
  * hard-sphere Carnahan-Starling contact value at z_p = 0, and the exact
- * free-volume fraction of a single colloid.
+ * free-volume fraction of a single colloid; for the anisotropic shapes,
+ * point and pair tests against a general constrained minimiser and against
+ * touching distances on symmetry axes, the Steiner excluded volume, the
+ * rotation-proposal distribution and detailed balance of rotation moves.
  */
 #include <math.h>
 #include <stdint.h>
@@ -147,37 +154,350 @@ int oracle_poisson_sample(const double *F, int n, double u)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Shapes.  Only spheres here: colloid of diameter d, depletant diameter q.  */
+/* Shapes (Secs. IV-V): the colloid is a sphere of diameter d, a hemisphere  */
+/* of diameter d (Sec. V.A) or an oblate spheroid with semi-axes a = b, c    */
+/* (the discoid of Sec. V.B).  Depletants are penetrable spheres of diameter */
+/* q that interact with colloids only (Sec. II).                             */
 /* ------------------------------------------------------------------------ */
 
 enum { SHAPE_SPHERE = 0, SHAPE_HEMISPHERE = 1, SHAPE_SPHEROID = 2 };
 
 typedef struct {
     int kind;
-    double d;       /* sphere diameter */
+    double d;       /* sphere / hemisphere diameter */
+    double a, c;    /* spheroid semi-axes (body x = y, body z) */
     double R_circ;  /* circumsphere radius about the reference point */
 } oshape;
 
-/* Does a depletant (penetrable sphere of diameter q) at v, given relative to
- * the colloid's reference point, overlap the colloid?  Strict inequality:
- * touching is not an overlap. */
-static int dep_overlap(const oshape *sh, double q, const double v[3],
-                       const double quat[4])
+/* Reference point and body frame.  Sphere and spheroid: the centre.  Hemisphere:
+ * the centre of the flat face, the face in the body plane z = 0 and the dome
+ * on the side z >= 0.  An orientation is a unit quaternion (s, x, y, z); it
+ * maps body-frame vectors to the lab frame. */
+
+/* body -> lab: b + s t + u x t with t = 2 u x b, u = (x, y, z). */
+static void rot_to_lab(const double q[4], const double b[3], double v[3])
 {
-    (void)quat;
-    double R = 0.5 * sh->d + 0.5 * q;
-    double r2 = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2];
-    return r2 < R * R;
+    double s = q[0], ux = q[1], uy = q[2], uz = q[3];
+    double tx = 2.0 * (uy * b[2] - uz * b[1]);
+    double ty = 2.0 * (uz * b[0] - ux * b[2]);
+    double tz = 2.0 * (ux * b[1] - uy * b[0]);
+    v[0] = (b[0] + s * tx) + (uy * tz - uz * ty);
+    v[1] = (b[1] + s * ty) + (uz * tx - ux * tz);
+    v[2] = (b[2] + s * tz) + (ux * ty - uy * tx);
+}
+
+/* lab -> body (rotation by the conjugate): v - s t + u x t, t = 2 u x v. */
+static void rot_to_body(const double q[4], const double v[3], double b[3])
+{
+    double s = q[0], ux = q[1], uy = q[2], uz = q[3];
+    double tx = 2.0 * (uy * v[2] - uz * v[1]);
+    double ty = 2.0 * (uz * v[0] - ux * v[2]);
+    double tz = 2.0 * (ux * v[1] - uy * v[0]);
+    b[0] = (v[0] - s * tx) + (uy * tz - uz * ty);
+    b[1] = (v[1] - s * ty) + (uz * tx - ux * tz);
+    b[2] = (v[2] - s * tz) + (ux * ty - uy * tx);
+}
+
+static const double QUAT_ID[4] = {1.0, 0.0, 0.0, 0.0};
+
+/* Distance test of a point against the spheroid x^2/a^2 + y^2/a^2 + z^2/c^2
+ * <= 1 (body frame): is dist(p, E) < r?  The closest boundary point of E to
+ * an outside point P = (rho, z) of the meridian plane is
+ * (a^2 rho / (t + a^2), c^2 z / (t + c^2)) where t > 0 is the root of
+ * F(t) = (a rho / (t + a^2))^2 + (c z / (t + c^2))^2 - 1, a convex decreasing
+ * function for t > -min(a^2, c^2); Newton's method from t = 0 (F(0) > 0)
+ * climbs monotonically to the root and stops when a step no longer increases
+ * t.  Before that: inside E => overlap; inside the spheroid with semi-axes
+ * (a + r, c + r), which lies inside E + ball(r), => overlap; outside the
+ * slab |z| < c + r or the cylinder rho < a + r, which contain E + ball(r),
+ * => no overlap. */
+static int spheroid_point_within(double a, double c, double r, const double p[3])
+{
+    double A2 = a * a, C2 = c * c;
+    double rho2 = p[0] * p[0] + p[1] * p[1];
+    double z = fabs(p[2]);
+    double z2 = z * z;
+    if (rho2 / A2 + z2 / C2 <= 1.0) return 1;
+    double ar = a + r, cr = c + r;
+    if (rho2 / (ar * ar) + z2 / (cr * cr) < 1.0) return 1;
+    if (z >= cr) return 0;
+    if (rho2 >= ar * ar) return 0;
+    double rho = sqrt(rho2);
+    double t = 0.0;
+    for (int it = 0; it < 64; ++it) {
+        double d1 = t + A2, d2 = t + C2;
+        double g1 = (a * rho) / d1, g2 = (c * z) / d2;
+        double g11 = g1 * g1, g22 = g2 * g2;
+        double F = (g11 + g22) - 1.0;
+        double D = g11 / d1 + g22 / d2;
+        double tn = t + F / (2.0 * D);
+        if (!(tn > t)) break;
+        t = tn;
+    }
+    double x0 = (A2 * rho) / (t + A2), x1 = (C2 * z) / (t + C2);
+    double e0 = rho - x0, e1 = z - x1;
+    return e0 * e0 + e1 * e1 < r * r;
+}
+
+/* Does a depletant (penetrable sphere of diameter q) at v, given relative to
+ * the colloid's reference point in the lab frame, overlap the colloid of
+ * orientation quat (NULL = identity)?  Strict: touching is not an overlap.
+ * The depletant overlaps iff its centre is closer than r = q/2 to the body. */
+static int dep_overlap(const oshape *sh, double q, const double v[3],
+                       const double *quat)
+{
+    double r2v = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2];
+    if (sh->kind == SHAPE_SPHERE) {
+        double R = 0.5 * sh->d + 0.5 * q;
+        return r2v < R * R;
+    }
+    double r = 0.5 * q;
+    double Rr = sh->R_circ + r;
+    if (!(r2v < Rr * Rr)) return 0;        /* the body lies within R_circ */
+    double p[3];
+    rot_to_body(quat ? quat : QUAT_ID, v, p);
+    if (sh->kind == SHAPE_HEMISPHERE) {
+        double R = 0.5 * sh->d;
+        /* z >= 0: distance max(0, |p| - R), and |p| < R + r holds */
+        if (p[2] >= 0.0) return 1;
+        double rho2 = p[0] * p[0] + p[1] * p[1];
+        /* below the flat face: distance -z */
+        if (rho2 <= R * R) return -p[2] < r;
+        /* below and outside the rim: distance to the rim circle */
+        double dr = sqrt(rho2) - R;
+        return dr * dr + p[2] * p[2] < r * r;
+    }
+    return spheroid_point_within(sh->a, sh->c, r, p);
+}
+
+/* Support point of the body (body frame) in direction n: the point of the
+ * body maximising n . x.  Hemisphere: on the dome R n/|n| when n_z >= 0,
+ * else on the rim R (n_x, n_y, 0)/rho_n (the face centre when rho_n = 0).
+ * Spheroid: (a^2 n_x, a^2 n_y, c^2 n_z) / sqrt(a^2 (n_x^2 + n_y^2) + c^2 n_z^2).
+ * A zero direction gives the reference point. */
+static void support_body(const oshape *sh, const double n[3], double s[3])
+{
+    s[0] = 0.0; s[1] = 0.0; s[2] = 0.0;
+    if (sh->kind == SHAPE_HEMISPHERE) {
+        double R = 0.5 * sh->d;
+        if (n[2] >= 0.0) {
+            double l = sqrt((n[0] * n[0] + n[1] * n[1]) + n[2] * n[2]);
+            if (l > 0.0) {
+                s[0] = (R * n[0]) / l;
+                s[1] = (R * n[1]) / l;
+                s[2] = (R * n[2]) / l;
+            }
+        } else {
+            double rho = sqrt(n[0] * n[0] + n[1] * n[1]);
+            if (rho > 0.0) {
+                s[0] = (R * n[0]) / rho;
+                s[1] = (R * n[1]) / rho;
+            }
+        }
+    } else {
+        double A2 = sh->a * sh->a, C2 = sh->c * sh->c;
+        double h = sqrt(A2 * (n[0] * n[0] + n[1] * n[1]) + C2 * (n[2] * n[2]));
+        if (h > 0.0) {
+            s[0] = (A2 * n[0]) / h;
+            s[1] = (A2 * n[1]) / h;
+            s[2] = (C2 * n[2]) / h;
+        }
+    }
+}
+
+/* One colloid placed in the lab frame: reference point at x, orientation q. */
+typedef struct {
+    const oshape *sh;
+    const double *q;
+    double x[3];
+} obody;
+
+static void support_lab(const obody *B, const double n[3], double out[3])
+{
+    double nb[3], sb[3], sl[3];
+    rot_to_body(B->q, n, nb);
+    support_body(B->sh, nb, sb);
+    rot_to_lab(B->q, sb, sl);
+    out[0] = sl[0] + B->x[0];
+    out[1] = sl[1] + B->x[1];
+    out[2] = sl[2] + B->x[2];
+}
+
+/* A point strictly inside the body: the centre of the hemisphere's inscribed
+ * ball (0, 0, R/2) in body coordinates; the spheroid's centre. */
+static void interior_lab(const obody *B, double out[3])
+{
+    double b[3] = {0.0, 0.0, 0.0}, l[3];
+    if (B->sh->kind == SHAPE_HEMISPHERE) b[2] = 0.25 * B->sh->d;
+    rot_to_lab(B->q, b, l);
+    out[0] = l[0] + B->x[0];
+    out[1] = l[1] + B->x[1];
+    out[2] = l[2] + B->x[2];
+}
+
+static double dot3(const double a[3], const double b[3])
+{
+    return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2];
+}
+
+static void cross3(const double a[3], const double b[3], double o[3])
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static void sub3(const double a[3], const double b[3], double o[3])
+{
+    o[0] = a[0] - b[0];
+    o[1] = a[1] - b[1];
+    o[2] = a[2] - b[2];
+}
+
+static void copy3(double o[3], const double a[3]) { o[0] = a[0]; o[1] = a[1]; o[2] = a[2]; }
+
+/* Support point of the Minkowski difference M = B - A = {b - a}. */
+static void support_diff(const obody *A, const obody *B, const double n[3], double out[3])
+{
+    double m[3] = {-n[0], -n[1], -n[2]}, sa[3], sb[3];
+    support_lab(B, n, sb);
+    support_lab(A, m, sa);
+    sub3(sb, sa, out);
+}
+
+/* Do two convex colloids overlap?  A and B overlap iff the origin lies in
+ * M = B - A.  Minkowski portal refinement (Snethen, "XenoCollide", Game
+ * Programming Gems 7, 2008): from an interior point v0 of M, find a triangle
+ * of support points (the portal) that the ray from v0 through the origin
+ * crosses, then push the portal out along its normal until the origin is
+ * inside the tetrahedron (v0, portal) (overlap), a support plane separates
+ * the origin from M (no overlap), or the portal lies within 1e-12 of the
+ * boundary of M (no overlap: touching or closer than the tolerance). */
+static int mpr_overlap(const obody *A, const obody *B)
+{
+    double cA[3], cB[3], v0[3], v1[3], v2[3], v3[3], v4[3], n[3], e1[3], e2[3], t[3];
+    interior_lab(A, cA);
+    interior_lab(B, cB);
+    sub3(cB, cA, v0);
+    if (v0[0] == 0.0 && v0[1] == 0.0 && v0[2] == 0.0) return 1;
+    n[0] = -v0[0]; n[1] = -v0[1]; n[2] = -v0[2];
+    support_diff(A, B, n, v1);
+    if (dot3(v1, n) <= 0.0) return 0;
+    cross3(v1, v0, n);
+    if (n[0] == 0.0 && n[1] == 0.0 && n[2] == 0.0) return 1;
+    support_diff(A, B, n, v2);
+    if (dot3(v2, n) <= 0.0) return 0;
+    sub3(v1, v0, e1);
+    sub3(v2, v0, e2);
+    cross3(e1, e2, n);
+    if (dot3(n, v0) > 0.0) {
+        copy3(t, v1); copy3(v1, v2); copy3(v2, t);
+        n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2];
+    }
+    /* portal discovery */
+    int found = 0;
+    for (int it = 0; it < 64 && !found; ++it) {
+        support_diff(A, B, n, v3);
+        if (dot3(v3, n) <= 0.0) return 0;
+        cross3(v1, v3, t);
+        if (dot3(t, v0) < 0.0) {
+            copy3(v2, v3);
+            sub3(v1, v0, e1);
+            sub3(v3, v0, e2);
+            cross3(e1, e2, n);
+            continue;
+        }
+        cross3(v3, v2, t);
+        if (dot3(t, v0) < 0.0) {
+            copy3(v1, v3);
+            sub3(v3, v0, e1);
+            sub3(v2, v0, e2);
+            cross3(e1, e2, n);
+            continue;
+        }
+        found = 1;
+    }
+    if (!found) return 0;
+    /* portal refinement */
+    for (int it = 0; it < 64; ++it) {
+        sub3(v2, v1, e1);
+        sub3(v3, v1, e2);
+        cross3(e1, e2, n);
+        if (n[0] == 0.0 && n[1] == 0.0 && n[2] == 0.0) return 1;
+        double nn = sqrt(dot3(n, n));
+        n[0] = n[0] / nn; n[1] = n[1] / nn; n[2] = n[2] / nn;
+        if (dot3(n, v1) >= 0.0) return 1;
+        support_diff(A, B, n, v4);
+        if (dot3(v4, n) <= 0.0) return 0;
+        sub3(v4, v3, t);
+        if (dot3(t, n) <= 1e-12) return 0;
+        cross3(v4, v1, t);
+        if (dot3(t, v0) < 0.0) {
+            cross3(v4, v2, t);
+            if (dot3(t, v0) < 0.0) copy3(v1, v4);
+            else copy3(v3, v4);
+        } else {
+            cross3(v4, v3, t);
+            if (dot3(t, v0) < 0.0) copy3(v2, v4);
+            else copy3(v1, v4);
+        }
+    }
+    return 0;
 }
 
 /* Do two colloids whose reference points are separated by r (from the first
- * to the second) overlap?  U_ij = infinity for overlapping hard colloids. */
-static int pair_overlap(const oshape *sh, const double r[3], const double qa[4],
-                        const double qb[4])
+ * to the second) overlap?  U_ij = infinity for overlapping hard colloids.
+ * Beyond twice the circumsphere radius they cannot (the strict convention
+ * makes touching circumspheres non-overlapping). */
+static int pair_overlap(const oshape *sh, const double r[3], const double *qa,
+                        const double *qb)
 {
-    (void)qa; (void)qb;
     double r2 = (r[0] * r[0] + r[1] * r[1]) + r[2] * r[2];
-    return r2 < sh->d * sh->d;
+    if (sh->kind == SHAPE_SPHERE) return r2 < sh->d * sh->d;
+    double D = 2.0 * sh->R_circ;
+    if (!(r2 < D * D)) return 0;
+    obody A = {sh, qa ? qa : QUAT_ID, {0.0, 0.0, 0.0}};
+    obody B = {sh, qb ? qb : QUAT_ID, {r[0], r[1], r[2]}};
+    return mpr_overlap(&A, &B);
+}
+
+/* Shape parameters: sphere {d}, hemisphere {d}, spheroid {a, c}. */
+static int shape_init(oshape *sh, int kind, const double *params, int nparams)
+{
+    memset(sh, 0, sizeof *sh);
+    sh->kind = kind;
+    if (!params) return -1;
+    if (kind == SHAPE_SPHERE || kind == SHAPE_HEMISPHERE) {
+        if (nparams < 1 || !(params[0] > 0.0)) return -1;
+        sh->d = params[0];
+        sh->R_circ = 0.5 * params[0];
+        return 0;
+    }
+    if (kind == SHAPE_SPHEROID) {
+        if (nparams < 2 || !(params[0] > 0.0) || !(params[1] > 0.0)) return -1;
+        sh->a = params[0];
+        sh->c = params[1];
+        sh->R_circ = params[0] > params[1] ? params[0] : params[1];
+        return 0;
+    }
+    return -1;
+}
+
+/* Exported single tests (used by the pins of the shape primitives). */
+int oracle_dep_overlap(int kind, const double *params, int nparams, double q,
+                       const double *v, const double *quat)
+{
+    oshape sh;
+    if (shape_init(&sh, kind, params, nparams) != 0 || !v) return -1;
+    return dep_overlap(&sh, q, v, quat);
+}
+
+int oracle_pair_overlap(int kind, const double *params, int nparams,
+                        const double *r, const double *qa, const double *qb)
+{
+    oshape sh;
+    if (shape_init(&sh, kind, params, nparams) != 0 || !r) return -1;
+    return pair_overlap(&sh, r, qa, qb);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -483,6 +803,49 @@ static int accept_move(const osim *S, uint32_t sweep, int i, const double xn[3],
     return 1;
 }
 
+/* Rotation proposal (Sec. V: orientational moves of anisotropic colloids).
+ * v uniform in the unit ball from the purpose-2 attempt stream (rejection
+ * from the cube, at most 64 attempts); q' = (q_r q)/|q_r q| with
+ * q_r = (1, alpha v): a rotation about v/|v| by 2 atan(alpha |v|) <= a_max
+ * when alpha = tan(a_max / 2).  The proposal density of q_r equals that of its
+ * inverse (v -> -v), so the move is symmetric.  Returns 0 if the cap is hit. */
+static int propose_rotation(okey key, uint32_t sweep, uint32_t tag, double alpha,
+                            const double qo[4], double qn[4])
+{
+    double v[3];
+    int ok = 0;
+    for (uint32_t t = 0; t < 64u && !ok; ++t) {
+        uint32_t w[4];
+        draw(key, sweep, tag, P_ROT, 0, t, w);
+        v[0] = s11(w[0]);
+        v[1] = s11(w[1]);
+        v[2] = s11(w[2]);
+        ok = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2] < 1.0;
+    }
+    if (!ok) return 0;
+    double s1 = 1.0, x1 = alpha * v[0], y1 = alpha * v[1], z1 = alpha * v[2];
+    double s2 = qo[0], x2 = qo[1], y2 = qo[2], z2 = qo[3];
+    double ms = s1 * s2 - ((x1 * x2 + y1 * y2) + z1 * z2);
+    double mx = (s1 * x2 + s2 * x1) + (y1 * z2 - z1 * y2);
+    double my = (s1 * y2 + s2 * y1) + (z1 * x2 - x1 * z2);
+    double mz = (s1 * z2 + s2 * z1) + (x1 * y2 - y1 * x2);
+    double nrm = sqrt(((ms * ms + mx * mx) + my * my) + mz * mz);
+    qn[0] = ms / nrm;
+    qn[1] = mx / nrm;
+    qn[2] = my / nrm;
+    qn[3] = mz / nrm;
+    return 1;
+}
+
+int oracle_rotation_proposal(uint64_t seed, uint32_t replica, uint32_t sweep,
+                             uint32_t tag, double a_max, const double *q_in,
+                             double *q_out)
+{
+    okey key = {{(uint32_t)seed, (uint32_t)(seed >> 32) ^ replica}};
+    if (!q_in || !q_out || !(a_max > 0.0) || a_max >= 3.0) return -1;
+    return propose_rotation(key, sweep, tag, tan(0.5 * a_max), q_in, q_out);
+}
+
 /* One trial move of colloid i in the active cell ci: proposal, cell check,
  * acceptance, commit. */
 static void trial_move(const osim *S, uint32_t sweep, int i, const int ci[3],
@@ -494,16 +857,16 @@ static void trial_move(const osim *S, uint32_t sweep, int i, const int ci[3],
     uint32_t w[4];
     cnt[C_MOVES]++;
     draw(S->key, sweep, tag, P_MOVE, 0, 0, w);
+    const double *qo = quat ? quat + 4 * i : NULL;
 
     int translate = 1;
-    if (S->sh.kind != SHAPE_SPHERE && S->a_max > 0.0) {
+    if (S->sh.kind != SHAPE_SPHERE && S->a_max > 0.0 && qo) {
         if (S->p_translate <= 0.0) translate = 0;
         else if (S->p_translate < 1.0) translate = u01(w[3]) < S->p_translate;
     }
 
     double xn[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
     double qn[4] = {1.0, 0.0, 0.0, 0.0};
-    const double *qo = quat ? quat + 4 * i : NULL;
     if (qo) { qn[0] = qo[0]; qn[1] = qo[1]; qn[2] = qo[2]; qn[3] = qo[3]; }
     double o[3] = {0.0, 0.0, 0.0};
 
@@ -523,6 +886,9 @@ static void trial_move(const osim *S, uint32_t sweep, int i, const int ci[3],
             }
         }
         for (int d = 0; d < 3; ++d) o[d] = min_image(pos[3 * i + d] - xn[d], S->L);
+    } else if (!propose_rotation(S->key, sweep, tag, S->alpha, qo, qn)) {
+        cnt[C_CAP]++;
+        return;
     }
 
     if (!accept_move(S, sweep, i, xn, qn, o, qo, ci, pos, quat, cell_start,
@@ -558,12 +924,9 @@ static int sim_init(osim *S, int n, double L, int shape,
 {
     memset(S, 0, sizeof *S);
     if (n < 1 || !(L > 0.0) || !shape_params) return -1;
-    if (shape != SHAPE_SPHERE || n_shape_params < 1) return -1;
+    if (shape_init(&S->sh, shape, shape_params, n_shape_params) != 0) return -1;
     S->n = n;
     S->L = L;
-    S->sh.kind = shape;
-    S->sh.d = shape_params[0];
-    S->sh.R_circ = 0.5 * S->sh.d;
     S->q = q;
     S->n_r = n_r;
     S->R_s = S->sh.R_circ + 0.5 * q;
@@ -574,6 +937,9 @@ static int sim_init(osim *S, int n, double L, int shape,
     S->d_max = d_max;
     S->a_max = a_max;
     S->p_translate = p_translate;
+    /* rotation by angle 2 atan(alpha |v|) <= a_max about v/|v|, |v| < 1 */
+    S->alpha = a_max > 0.0 ? tan(0.5 * a_max) : 0.0;
+    if (!(a_max >= 0.0) || a_max >= 3.0) return -1;
     S->key.k[0] = (uint32_t)seed;
     S->key.k[1] = (uint32_t)(seed >> 32) ^ replica;
     S->nc = n_cell > 0 ? n_cell : oracle_auto_cells(L, S->sh.R_circ, q);
@@ -709,8 +1075,8 @@ long oracle_free_volume(int n, double L, int shape, const double *shape_params,
                         double q, const double *pos, const double *quat,
                         uint64_t seed, uint32_t sample, long n_probe)
 {
-    if (shape != SHAPE_SPHERE) return -1;
-    oshape sh = {SHAPE_SPHERE, shape_params[0], 0.5 * shape_params[0]};
+    oshape sh;
+    if (shape_init(&sh, shape, shape_params, shape == SHAPE_SPHEROID ? 2 : 1) != 0) return -1;
     okey key = {{(uint32_t)seed, (uint32_t)(seed >> 32)}};
     long free_count = 0;
     for (long m = 0; m < n_probe; ++m) {

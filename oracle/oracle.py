@@ -104,6 +104,15 @@ def lib():
                 ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, ctypes.c_double,
                 dp, dp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_long]
             L.oracle_free_volume.restype = ctypes.c_long
+            L.oracle_dep_overlap.argtypes = [ctypes.c_int, dp, ctypes.c_int,
+                                             ctypes.c_double, dp, dp]
+            L.oracle_dep_overlap.restype = ctypes.c_int
+            L.oracle_pair_overlap.argtypes = [ctypes.c_int, dp, ctypes.c_int, dp, dp, dp]
+            L.oracle_pair_overlap.restype = ctypes.c_int
+            L.oracle_rotation_proposal.argtypes = [ctypes.c_uint64, ctypes.c_uint32,
+                                                   ctypes.c_uint32, ctypes.c_uint32,
+                                                   ctypes.c_double, dp, dp]
+            L.oracle_rotation_proposal.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -245,3 +254,52 @@ def free_volume(pos, L, q, *, shape=SHAPE_SPHERE, shape_params=(1.0,), quat=None
     if c < 0:
         raise ValueError("oracle_free_volume failed")
     return c / float(n_probe)
+
+
+def _opt(a, n):
+    if a is None:
+        return None
+    return np.ascontiguousarray(a, dtype=np.float64).reshape(n)
+
+
+def dep_overlap(v, q, *, shape=SHAPE_SPHERE, shape_params=(1.0,), quat=None):
+    """Does a depletant of diameter q at v (relative to the colloid's reference
+    point, lab frame) overlap the colloid of orientation quat?"""
+    sp = np.ascontiguousarray(shape_params, dtype=np.float64)
+    vv = _opt(v, 3)
+    qq = _opt(quat, 4)
+    r = lib().oracle_dep_overlap(int(shape), _p(sp, ctypes.c_double), len(sp), float(q),
+                                 _p(vv, ctypes.c_double),
+                                 _p(qq, ctypes.c_double) if qq is not None else None)
+    if r < 0:
+        raise ValueError("oracle_dep_overlap rejected its arguments")
+    return bool(r)
+
+
+def pair_overlap(r, *, shape=SHAPE_SPHERE, shape_params=(1.0,), qa=None, qb=None):
+    """Do two colloids with reference points separated by r (first to second)
+    and orientations qa, qb overlap?"""
+    sp = np.ascontiguousarray(shape_params, dtype=np.float64)
+    rr = _opt(r, 3)
+    a = _opt(qa, 4)
+    b = _opt(qb, 4)
+    res = lib().oracle_pair_overlap(int(shape), _p(sp, ctypes.c_double), len(sp),
+                                    _p(rr, ctypes.c_double),
+                                    _p(a, ctypes.c_double) if a is not None else None,
+                                    _p(b, ctypes.c_double) if b is not None else None)
+    if res < 0:
+        raise ValueError("oracle_pair_overlap rejected its arguments")
+    return bool(res)
+
+
+def rotation_proposal(q, a_max, *, seed=1, replica=0, sweep=0, tag=0):
+    """The rotated orientation proposed for colloid `tag` in `sweep`, or None
+    if the attempt stream hit its cap."""
+    qi = _opt(q, 4)
+    qo = np.zeros(4)
+    rc = lib().oracle_rotation_proposal(int(seed), int(replica), int(sweep), int(tag),
+                                        float(a_max), _p(qi, ctypes.c_double),
+                                        _p(qo, ctypes.c_double))
+    if rc < 0:
+        raise ValueError("oracle_rotation_proposal rejected its arguments")
+    return qo if rc == 1 else None
