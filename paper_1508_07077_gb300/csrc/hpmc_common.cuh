@@ -104,6 +104,12 @@ struct Rep {
     double contact2;       // sphere-sphere contact distance squared
     double nb_cut2;        // neighbours farther than this cannot meet a depletant
     double d_max;
+    // shape (hpmc_shapes.cuh): kind, circumsphere radius about the reference
+    // point, depletant radius q/2, hemisphere radius, spheroid semi-axes
+    int shape, rot_on;     // rot_on: rotation moves enabled (anisotropic, a_max > 0)
+    double R_circ, r_dep, sh_R, sh_a, sh_c;
+    double alpha;          // tan(a_max / 2): rotation proposal scale
+    double p_translate;    // probability of a translation when rotations are on
     // FP32 form: thresholds rounded to float, and the certified margins
     float w32, L32, half_L32, R_s32, T_s32, T_dep32, T_contact32, nb_cut2_32, d_max32;
     float m_r2;            // bound on |r2_fp32 - r2_fp64| (+ threshold rounding), doubled

@@ -20,6 +20,7 @@
 #include "hpmc_misc.cuh"
 #include "hpmc_sphere_fp32.cuh"
 #include "hpmc_sphere_fp64.cuh"
+#include "hpmc_aniso_fp64.cuh"
 
 using namespace hpmc;
 
@@ -173,17 +174,30 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
     const double w = h.L / (double)nc;
     if (w < w_min) return HPMC_ERR_ARG;
     if (!(h.d_max >= 0.0) || h.d_max >= w) return HPMC_ERR_ARG;
-    // a cell bin holds at most (w + 2 R_circ)^3 * 0.7405 / v colloids of volume v
-    // (densest packing); spheres only for now
-    const double v_shape = (kPi / 6.0) * p.sp[0] * p.sp[0] * p.sp[0];
+    // a cell bin holds at most (w + 2 R_circ)^3 * pack / v colloids of volume v:
+    // pack = 0.7405 (densest sphere packing) for spheres, 0.78 for the
+    // anisotropic shapes (above the densest known ellipsoid packing, 0.7707,
+    // and hemispheres, which pair into spheres)
+    double v_shape = (kPi / 6.0) * p.sp[0] * p.sp[0] * p.sp[0];
+    if (p.shape == HPMC_HEMISPHERE) v_shape = 0.5 * v_shape;
+    if (p.shape == HPMC_SPHEROID) v_shape = (4.0 / 3.0 * kPi) * p.sp[0] * p.sp[0] * p.sp[1];
+    const double pack = p.shape == HPMC_SPHERE ? 0.7405 : 0.78;
     const double ext = w + 2.0 * R_circ;
-    const double cell_bound = ext * ext * ext * 0.7405 / v_shape;
+    const double cell_bound = ext * ext * ext * pack / v_shape;
     if (cell_bound >= (double)kMaxCellCap) return HPMC_ERR_CAP;
     R.pad_cell_bound = cell_bound;
-    // the neighbourhood of a depletant (a ball of radius 2 R_s + 0.01 around the
-    // moved colloid) holds at most the FP32 kernel's kMaxNb colloids
-    const double nb_ext = 2.0 * R_s + 0.01 + R_circ;
-    if (nb_ext * nb_ext * nb_ext * (4.0 / 3.0 * kPi) * 0.7405 / v_shape >= 64.0) return HPMC_ERR_CAP;
+    // Neighbours that can meet a depletant: a depletant of the new circumsphere
+    // lies within R_s of the new reference point and meets colloid j only if
+    // |x_j - y| < R_circ + q/2 = R_s, so |d_j| < 2 R_s; the forward CB trials
+    // lie in the OLD circumsphere, centred |o| <= sqrt(3) d_max away, which
+    // widens the range by that much.  0.01 covers the FP32 rounding of |d_j|.
+    const double cut = 2.0 * R_s + (h.n_trial > 0 ? std::sqrt(3.0) * h.d_max : 0.0) + 0.01;
+    // in the FP32 form that neighbourhood must hold at most kMaxNb colloids
+    // (the FP64 forms keep every candidate of the 27 cells, up to kMaxCand)
+    const double nb_ext = cut + R_circ;
+    if (c->precision == HPMC_FP32_RECHECK &&
+        nb_ext * nb_ext * nb_ext * (4.0 / 3.0 * kPi) * pack / v_shape >= 64.0)
+        return HPMC_ERR_CAP;
     F.clear();
     if (lambda > 0.0) {
         int rc = build_table(lambda, F);
@@ -208,9 +222,18 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
     const double Rd = 0.5 * p.sp[0] + 0.5 * h.q;
     R.R_dep2 = Rd * Rd;
     R.contact2 = p.sp[0] * p.sp[0];
-    const double cut = 2.0 * R_s + 0.01;
     R.nb_cut2 = cut * cut;
     R.d_max = h.d_max;
+    R.shape = p.shape;
+    R.R_circ = R_circ;
+    R.r_dep = 0.5 * h.q;
+    R.sh_R = 0.5 * p.sp[0];
+    R.sh_a = p.sp[0];
+    R.sh_c = p.shape == HPMC_SPHEROID ? p.sp[1] : p.sp[0];
+    R.rot_on = (p.shape != HPMC_SPHERE && h.a_max > 0.0) ? 1 : 0;
+    // rotation by 2 atan(alpha |v|) <= a_max, |v| < 1
+    R.alpha = h.a_max > 0.0 ? std::tan(0.5 * h.a_max) : 0.0;
+    R.p_translate = h.p_translate;
     // FP32 form: thresholds in float and the certified margin.  Every vector a
     // test forms is a difference of cell-relative coordinates; each component
     // carries at most E = 40 u max(w, 1) of FP32 error (rounding of the
@@ -296,8 +319,10 @@ void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s
             if (warp) k_phase_sphere_fp32<false, true, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
             else k_phase_sphere_fp32<false, false, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
         }
-    } else {
+    } else if (c->prm.shape == HPMC_SPHERE) {
         k_phase_sphere_fp64<CAP><<<c->n_cta, threads, 0, s>>>(P, phase);
+    } else {
+        k_phase_aniso_fp64<CAP><<<c->n_cta, threads, 0, s>>>(P, phase);
     }
 }
 
@@ -393,7 +418,10 @@ int check_config(hpmc_ctx *c)
     if (rc != HPMC_OK) return rc;
     CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->cap_stream));
     SimParams P = make_params(c);
-    k_check_spheres<<<(c->n_total + 255) / 256, 256, 0, c->cap_stream>>>(P, c->d_flag);
+    if (c->prm.shape == HPMC_SPHERE)
+        k_check_spheres<<<(c->n_total + 255) / 256, 256, 0, c->cap_stream>>>(P, c->d_flag);
+    else
+        k_check_aniso<<<(c->n_total + 127) / 128, 128, 0, c->cap_stream>>>(P, c->d_flag);
     CK(cudaGetLastError());
     int flag = 0, err = 0;
     CK(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->cap_stream));
@@ -413,7 +441,8 @@ int check_config(hpmc_ctx *c)
 int prepare(hpmc_ctx *c)
 {
     const Params &p = c->prm;
-    if (p.shape != HPMC_SPHERE) return HPMC_ERR_ARG;  // other shapes: later forms
+    // anisotropic shapes: plain FP64 form
+    if (p.shape != HPMC_SPHERE && c->precision != HPMC_FP64) return HPMC_ERR_ARG;
     const int n_rep = (int)c->reps.size();
     std::vector<Rep> rd((size_t)n_rep);
     std::vector<unsigned long long> T;
