@@ -175,11 +175,14 @@ def _pair_classify(shape, params, r, qa, qb):
     t0 = min(min(g(in_a(x0)) for g in ga), min(g(in_b(x0)) for g in ga)) - 0.1
     res2 = optimize.minimize(lambda z: -z[3], np.concatenate([x0, [t0]]), constraints=cons,
                              method="SLSQP", options={"ftol": 1e-14, "maxiter": 800})
-    depth = -res2.fun if res2.success else None
-    if sep is not None and sep > 1e-6:
-        return 0
-    if depth is not None and depth > 1e-6:
+    depth = -res2.fun
+    feasible = all(c["fun"](res2.x) >= -1e-12 for c in cons)
+    # a feasible point of depth t > 0 proves an overlap; a separation needs
+    # both programs to agree (each alone only bounds its optimum from one side)
+    if feasible and depth > 1e-6:
         return 1
+    if sep is not None and sep > 1e-6 and depth < -1e-6:
+        return 0
     return None
 
 
@@ -199,6 +202,39 @@ def test_pair_test_equals_convex_programs(oracle, shape, params):
         assert int(got) == want, (r, qa, qb)
         seen[want] += 1
     assert seen[0] > 20 and seen[1] > 20, seen
+
+
+def _qaxis(ax, ang):
+    ax = np.asarray(ax, dtype=float)
+    ax = ax / np.linalg.norm(ax)
+    return np.concatenate([[math.cos(ang / 2)], math.sin(ang / 2) * ax])
+
+
+def _qmul(a, b):
+    s1, v1, s2, v2 = a[0], a[1:], b[0], b[1:]
+    return np.concatenate([[s1 * s2 - v1 @ v2], s1 * v2 + s2 * v1 + np.cross(v1, v2)])
+
+
+def test_pair_test_near_parallel_flat_faces(oracle):
+    """Hemispheres face to face, faces nearly parallel, gaps and overlaps from
+    1e-7 to 1e-2: the flat faces make the difference body partly flat, the
+    hardest case for the portal method."""
+    rng = np.random.default_rng(1)
+    flip = np.array([0.0, 1.0, 0.0, 0.0])
+    seen = {0: 0, 1: 0}
+    for _ in range(200):
+        qa = _qmul(_qaxis(rng.normal(size=3), 10 ** rng.uniform(-6, -1)), flip)
+        qb = _qaxis(rng.normal(size=3), 10 ** rng.uniform(-6, -1))
+        lat = rng.uniform(-0.9, 0.9, 2)
+        r = np.array([lat[0], lat[1], rng.choice([-1, 1]) * 10 ** rng.uniform(-7, -2)])
+        if r @ r >= 1.0:
+            continue
+        want = _pair_classify(HEMI, HEMI_P, r, qa, qb)
+        if want is None:
+            continue
+        assert int(oracle.pair_overlap(r, shape=HEMI, shape_params=HEMI_P, qa=qa, qb=qb)) == want
+        seen[want] += 1
+    assert seen[0] > 10 and seen[1] > 10, seen
 
 
 def test_pair_touching_distances_along_axes(oracle):
