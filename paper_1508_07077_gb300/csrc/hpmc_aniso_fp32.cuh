@@ -1,0 +1,693 @@
+// FP32 form for anisotropic colloids (hemispheres, discoids; Sec. V) with
+// translation and rotation moves.
+//
+// Per sweep: k_propose_aniso computes every colloid's proposed pose exactly
+// (FP64, one thread per colloid, so the FP64 work is spread over all lanes);
+// k_lens_aniso_fp32 builds the depletant lens lists (one warp per colloid);
+// the eight colour phases (k_phase_aniso_fp32) test colloid pairs and lens
+// points against neighbours.  Every test is taken in FP32 with a certified
+// margin (hpmc_shapes32.cuh); a test inside its margin is re-taken with the
+// exact FP64 statement (hpmc_shapes.cuh), so all decisions equal the FP64
+// form's.  Accepted poses are committed from the exact proposals.
+#pragma once
+
+#include "hpmc_common.cuh"
+#include "hpmc_shapes.cuh"
+#include "hpmc_shapes32.cuh"
+#include "hpmc_sphere_fp32.cuh"
+
+namespace hpmc {
+
+// ---------------------------------------------------------------------------
+// Exact proposals: prop_pos[g] = (new position, kind) with kind 1 translation,
+// 0 rotation, -1 rotation attempt stream capped (the move is rejected);
+// prop_quat[g] = new orientation (the old one for a translation).
+// ---------------------------------------------------------------------------
+__global__ void k_propose_aniso(const __grid_constant__ SimParams P)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= P.n_total) return;
+    const int r = P.rep_of[g];
+    const Rep &R = P.reps[r];
+    const uint32_t sweep = P.sched[r].sweep;
+    const uint32_t tag = (uint32_t)(g - R.off);
+    const uint4 wm = draw(R.key0, R.key1, sweep, tag, kPMove, 0, 0);
+    bool translate = true;
+    if (R.rot_on) {
+        if (R.p_translate <= 0.0) translate = false;
+        else if (R.p_translate < 1.0) translate = u01(wm.w) < R.p_translate;
+    }
+    const double4 p = P.pos[g];
+    const double4 qo = P.quat[g];
+    if (translate) {
+        P.prop_pos[g] = make_double4(wrap_box(p.x + R.d_max * s11(wm.x), R.L),
+                                     wrap_box(p.y + R.d_max * s11(wm.y), R.L),
+                                     wrap_box(p.z + R.d_max * s11(wm.z), R.L), 1.0);
+        P.prop_quat[g] = qo;
+        return;
+    }
+    double4 qn = qo;
+    const bool ok = propose_rotation(R, sweep, tag, qo, &qn);
+    P.prop_pos[g] = make_double4(p.x, p.y, p.z, ok ? 0.0 : -1.0);
+    P.prop_quat[g] = qn;
+}
+
+__device__ __forceinline__ float4 quat32(double4 q)
+{
+    return make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
+}
+
+// Exact current pose of colloid j: its proposal if this CTA accepted its
+// move (commits are deferred to the end of the CTA), else the state.
+__device__ __forceinline__ void pose_now(const SimParams &P, int j, const int *acc, int nacc,
+                                         double4 &x, double4 &q)
+{
+    for (int a = 0; a < nacc; ++a)
+        if (acc[a] == j) {
+            x = P.prop_pos[j];
+            q = P.prop_quat[j];
+            return;
+        }
+    x = P.pos[j];
+    q = P.quat[j];
+}
+
+// Exact depletant test.  The point is R_s s11(w) around the new reference
+// point of colloid i (base 0) or around its old one (base 1); it is tested
+// against i's new pose (target 0), i's old pose (target 1) or neighbour j
+// (target 2).
+__device__ __noinline__ bool exact_dep_aniso(const SimParams &P, const Rep &R, int i, uint4 w,
+                                             int base, int target, int j, const int *acc, int nacc)
+{
+    const double4 xn = P.prop_pos[i];
+    const double4 xo = P.pos[i];
+    const Vec3 o = v3(min_image(xo.x - xn.x, R.L, R.half_L), min_image(xo.y - xn.y, R.L, R.half_L),
+                      min_image(xo.z - xn.z, R.L, R.half_L));
+    Vec3 v = v3(R.R_s * s11(w.x), R.R_s * s11(w.y), R.R_s * s11(w.z));
+    if (base == 1) v = v3(o.x + v.x, o.y + v.y, o.z + v.z);
+    if (target == 0) return dep_aniso(R, v, P.prop_quat[i]);
+    if (target == 1) return dep_aniso(R, v3(v.x - o.x, v.y - o.y, v.z - o.z), P.quat[i]);
+    double4 xj, qj;
+    pose_now(P, j, acc, nacc, xj, qj);
+    const Vec3 c = v3(min_image(xj.x - xn.x, R.L, R.half_L), min_image(xj.y - xn.y, R.L, R.half_L),
+                      min_image(xj.z - xn.z, R.L, R.half_L));
+    return dep_aniso(R, v3(v.x - c.x, v.y - c.y, v.z - c.z), qj);
+}
+
+// Exact colloid pair test of i at its proposed pose against j now: FP64
+// certificates along the FP32 direction first, the full FP64 statement if
+// they do not decide.
+__device__ __noinline__ bool exact_pair_aniso(const SimParams &P, const Rep &R, int i, int j,
+                                              const int *acc, int nacc, float3 nf, uint32_t &stage3)
+{
+    const double4 xn = P.prop_pos[i];
+    const double4 qn = P.prop_quat[i];
+    double4 xj, qj;
+    pose_now(P, j, acc, nacc, xj, qj);
+    const Vec3 d = v3(min_image(xj.x - xn.x, R.L, R.half_L), min_image(xj.y - xn.y, R.L, R.half_L),
+                      min_image(xj.z - xn.z, R.L, R.half_L));
+    const int c = pair_cert64(R, qn, qj, d, nf);
+    if (c >= 0) return c == 1;
+    ++stage3;
+    return pair_aniso(R, d, qn, qj);
+}
+
+// ---------------------------------------------------------------------------
+// Depletant lens lists, one warp per colloid (as for spheres, but "overlaps
+// the new pose" is a shape test, not the sampling-ball test).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__ SimParams P)
+{
+    const int lane = threadIdx.x & 31;
+    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= P.n_total) return;
+    const int r = P.rep_of[g];
+    const Rep &R = P.reps[r];
+    const uint32_t sweep = P.sched[r].sweep;
+    const uint32_t tag = (uint32_t)(g - R.off);
+    const double kind = P.prop_pos[g].w;
+    float D0 = 0.0f, D1 = 0.0f, D2 = 0.0f;
+    if (kind > 0.5) {
+        const uint4 wm = draw(R.key0, R.key1, sweep, tag, kPMove, 0, 0);
+        D0 = coord32(wm.x, R.d_max32);
+        D1 = coord32(wm.y, R.d_max32);
+        D2 = coord32(wm.z, R.d_max32);
+    }
+    if (lane == 0) P.lens_move[g] = make_float4(D0, D1, D2, (float)kind);
+    if (!R.has_dep) return;
+    if (kind < -0.5) {
+        if (lane == 0) P.lens_hdr[g] = make_int4(0, 0, 0, 0);
+        return;
+    }
+    if (kind > 0.5) {
+        const float4 ri = P.rel[g];
+        const float rn0 = ri.x + D0, rn1 = ri.y + D1, rn2 = ri.z + D2;
+        const float mc = R.m_cell, wc = R.w32;
+        if (rn0 < -mc || rn0 > wc + mc || rn1 < -mc || rn1 > wc + mc || rn2 < -mc ||
+            rn2 > wc + mc) {
+            if (lane == 0) P.lens_hdr[g] = make_int4(0, 0, 0, 0);
+            return;
+        }
+    }
+    const Frame32 Fn = frame32(quat32(P.prop_quat[g]));
+    const Frame32 Fo = frame32(quat32(P.quat[g]));
+    uint32_t rck = 0;
+    const float o0 = -D0, o1 = -D1, o2 = -D2;
+    const uint4 wp = draw(R.key0, R.key1, sweep, tag, kPPoisson, 0, 0);
+    const int n_p = poisson_count(P.T + R.t_off, R.nF, u53_int(wp.x, wp.y), lane);
+    const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
+    float4 *out = P.lens + (size_t)g * P.lens_cap;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t t0 = 0;
+    int k0 = 0, m = 0;
+    while (k0 < n_p && t0 < t_max) {
+        const uint32_t t = t0 + (uint32_t)lane;
+        uint4 w = make_uint4(0, 0, 0, 0);
+        float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+        int in = 0;
+        if (t < t_max) {
+            w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, t);
+            e0 = coord32(w.x, R.R_s32);
+            e1 = coord32(w.y, R.R_s32);
+            e2 = coord32(w.z, R.R_s32);
+            in = tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
+        }
+        {
+            const bool unsure = in == -1;
+            if (__any_sync(kFull, unsure)) {
+                if (unsure) {
+                    ++rck;
+                    in = exact_ball(P, R, w) ? 1 : 0;
+                }
+            }
+        }
+        const unsigned bal = __ballot_sync(kFull, in == 1);
+        const int k = k0 + __popc(bal & lt);
+        const bool dep = in == 1 && k < n_p;
+        // overlaps the new pose?
+        int tn = 0;
+        if (dep) tn = dep_tri32(R, make_float3(e0, e1, e2), Fn);
+        {
+            const bool unsure = tn == -1;
+            if (__any_sync(kFull, unsure)) {
+                if (unsure) {
+                    ++rck;
+                    tn = exact_dep_aniso(P, R, g, w, 0, 0, 0, nullptr, 0) ? 1 : 0;
+                }
+            }
+        }
+        // and not the old pose?
+        int to = 1;
+        if (tn == 1) to = dep_tri32(R, make_float3(e0 - o0, e1 - o1, e2 - o2), Fo);
+        {
+            const bool unsure = to == -1;
+            if (__any_sync(kFull, unsure)) {
+                if (unsure) {
+                    ++rck;
+                    to = exact_dep_aniso(P, R, g, w, 0, 1, 0, nullptr, 0) ? 1 : 0;
+                }
+            }
+        }
+        const bool lens = tn == 1 && to == 0;
+        const unsigned lb = __ballot_sync(kFull, lens);
+        const int slot = m + __popc(lb & lt);
+        if (lens && slot < P.lens_cap)
+            out[slot] = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
+        m += __popc(lb);
+        k0 += __popc(bal);
+        t0 += 32u;
+    }
+    if (lane == 0) {
+        P.lens_hdr[g] = make_int4(n_p, min(k0, n_p), min(m, P.lens_cap), 0);
+        if (m > P.lens_cap) atomicCAS(P.err, kErrNone, kErrCandCap);
+    }
+    rck = __reduce_add_sync(kFull, rck);
+    if (lane == 0 && rck) count_one(P, r, kRechecks, (unsigned long long)rck);
+}
+
+// ---------------------------------------------------------------------------
+// Neighbour tests of one point and the CB factor, FP32 with exact re-takes.
+// ---------------------------------------------------------------------------
+struct Nb32 {
+    float4 d;       // offset from the moved colloid's new reference point; index in .w
+    Frame32 F;
+};
+
+// Is the point y (relative to the new reference point; drawn around base with
+// word w) free of every neighbour?
+__device__ __forceinline__ bool free_nb_aniso32(const SimParams &P, const Rep &R, float3 y,
+                                                const Nb32 *nb, int nnb, int i, uint4 w, int base,
+                                                const int *acc, int nacc, uint32_t &rck)
+{
+    for (int a = 0; a < nnb; ++a) {
+        const float4 d = nb[a].d;
+        const int t = dep_tri32(R, make_float3(y.x - d.x, y.y - d.y, y.z - d.z), nb[a].F);
+        if (t == 1) return false;
+        if (t == -1) {
+            ++rck;
+            if (exact_dep_aniso(P, R, i, w, base, 2, __float_as_int(d.w), acc, nacc)) return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ int dep_self32(const SimParams &P, const Rep &R, float3 v, const Frame32 &F,
+                                          int i, uint4 w, int base, int target, uint32_t &rck)
+{
+    int t = dep_tri32(R, v, F);
+    if (t == -1) {
+        ++rck;
+        t = exact_dep_aniso(P, R, i, w, base, target, 0, nullptr, 0) ? 1 : 0;
+    }
+    return t;
+}
+
+// CB factor of one blocking depletant (Sec. III.D, Eq. 12), FP32 form.
+__device__ __noinline__ CbResult32 cb_factor_aniso32(const SimParams &P, const Rep &R, uint32_t sweep,
+                                                     int i, uint32_t k, float3 o, const Frame32 &Fn,
+                                                     const Frame32 &Fo, const Nb32 *nb, int nnb,
+                                                     const int *acc, int nacc)
+{
+    CbResult32 r = {0.0, 0u, 0u, 0u, 0u};
+    const uint32_t tag = (uint32_t)(i - R.off);
+    const int n_fwd = R.n_trial, n_rev = R.n_trial - 1;
+    int nf = 0, nr = 0, found = 0;
+    uint32_t t = 0;
+    uint4 w;
+    float e0, e1, e2;
+    while (found < n_fwd && next_in_ball32(P, R, sweep, tag, kPCbFwd, k, t, 64u * (uint32_t)(n_fwd + 1),
+                                           w, e0, e1, e2, r.rck)) {
+        ++found;
+        const float3 e = make_float3(e0, e1, e2);
+        const float3 y = make_float3(o.x + e0, o.y + e1, o.z + e2);
+        if (dep_self32(P, R, e, Fo, i, w, 1, 1, r.rck) == 0) continue;   // must overlap the old pose
+        if (dep_self32(P, R, y, Fn, i, w, 1, 0, r.rck) == 1) continue;   // not the new pose
+        if (!free_nb_aniso32(P, R, y, nb, nnb, i, w, 1, acc, nacc, r.rck)) continue;
+        ++nf;
+    }
+    if (found < n_fwd) ++r.caps;
+    t = 0;
+    found = 0;
+    while (found < n_rev && next_in_ball32(P, R, sweep, tag, kPCbRev, k, t, 64u * (uint32_t)(n_rev + 1),
+                                           w, e0, e1, e2, r.rck)) {
+        ++found;
+        const float3 e = make_float3(e0, e1, e2);
+        if (dep_self32(P, R, e, Fn, i, w, 0, 0, r.rck) == 0) continue;   // overlaps the new pose
+        if (dep_self32(P, R, make_float3(e0 - o.x, e1 - o.y, e2 - o.z), Fo, i, w, 0, 1, r.rck) == 1)
+            continue;                                                    // not the old pose
+        if (!free_nb_aniso32(P, R, e, nb, nnb, i, w, 0, acc, nacc, r.rck)) continue;
+        ++nr;
+    }
+    if (found < n_rev) ++r.caps;
+    r.fwd_ok = (uint32_t)nf;
+    r.rev_ok = (uint32_t)nr;
+    r.f = (double)nf / (double)(nr + 1);
+    return r;
+}
+
+// A lens point free of every neighbour, exactly.
+__device__ __noinline__ bool exact_free_nb_aniso(const SimParams &P, const Rep &R, uint32_t sweep, int i,
+                                                 uint32_t t, const Nb32 *nb, int nnb, const int *acc,
+                                                 int nacc)
+{
+    const uint4 w = draw(R.key0, R.key1, sweep, (uint32_t)(i - R.off), kPDep, 0, t);
+    for (int a = 0; a < nnb; ++a)
+        if (exact_dep_aniso(P, R, i, w, 0, 2, __float_as_int(nb[a].d.w), acc, nacc)) return false;
+    return true;
+}
+
+constexpr int kMaxNbAniso = 128;   // neighbours within reach of a depletant (checked on the host)
+
+// ---------------------------------------------------------------------------
+// One colour phase, FP32 form, anisotropic colloids: as k_phase_sphere_fp32,
+// plus orientations (FP32 copies of the candidates' quaternions in shared
+// memory, frames of the neighbours in range) and rotation moves.
+// ---------------------------------------------------------------------------
+template <bool CB, bool WARP, int CAP>
+__global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
+    k_phase_aniso_fp32(const __grid_constant__ SimParams P, int phase)
+{
+    __shared__ float4 s_cpos[kMaxCand];
+    __shared__ float4 s_cq[kMaxCand];
+    __shared__ Nb32 s_nb[kMaxNbAniso];
+    __shared__ float4 s_lens[kMaxLensCTA];
+    __shared__ int4 s_hdr[CAP];
+    __shared__ float4 s_mv[CAP];
+    __shared__ int s_tmp_i[CAP], s_tmp_slot[CAP];
+    __shared__ int s_own[CAP], s_own_slot[CAP], s_own_bin[CAP];
+    __shared__ int s_loff[CAP], s_accl[CAP];
+    __shared__ DepShared sh;
+    __shared__ int s_ncand, s_nnb, s_acc, s_nacc;
+    extern __shared__ double s_dyn[];
+
+    const int tid = threadIdx.x, nthr = WARP ? 32 : (int)blockDim.x;
+    const int lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    if (tid == 0) {
+        sh.f = s_dyn;
+        sh.k = (int *)(s_dyn + nthr);
+    }
+    const int r = P.cta_rep[blockIdx.x];
+    const Rep &R = P.reps[r];
+    const Sched *S = P.sched + r;
+    if (phase == 7 && blockIdx.x == 0 && tid == 0) atomicAdd(P.sweep, 1ull);
+    const uint32_t sweep = S->sweep;
+    const CellTask T = cell_task(P, R, r, phase);
+    clear_next(P, sweep, T.cell);
+    const int n_own = min(T.n_own, P.cap);
+    if (n_own == 0) return;
+    const int cx = T.cx, cy = T.cy, cz = T.cz;
+
+    if (tid == 0) {
+        s_ncand = 0;
+        s_nacc = 0;
+    }
+    cta_sync<WARP>();
+    if (tid < R.n_stencil * R.n_stencil * R.n_stencil) {
+        int dx, dy, dz;
+        const int c = stencil_cell(R, tid, cx, cy, cz, dx, dy, dz);
+        const float fx = (float)dx * R.w32, fy = (float)dy * R.w32, fz = (float)dz * R.w32;
+        const int m = c == T.cell ? n_own : min(T.count[c], P.cap);
+        const float4 *bin = P.bins + (size_t)c * P.cap;
+        for (int s = 0; s < m; ++s) {
+            const float4 e = bin[s];
+            const int slot = atomicAdd(&s_ncand, 1);
+            if (slot < kMaxCand) {
+                s_cpos[slot] = make_float4(fx + e.x, fy + e.y, fz + e.z, e.w);
+                s_cq[slot] = quat32(P.quat[__float_as_int(e.w)]);
+            }
+            if (c == T.cell) {
+                s_tmp_i[s] = __float_as_int(e.w);
+                s_tmp_slot[s] = slot;
+            }
+        }
+    }
+    cta_sync<WARP>();
+    const int M = s_ncand;
+    if (M > kMaxCand) {
+        if (tid == 0) atomicCAS(P.err, kErrNone, kErrCandCap);
+        return;
+    }
+    for (int q = tid; q < n_own; q += nthr) {
+        const int v = s_tmp_i[q];
+        int rk = 0;
+        for (int u = 0; u < n_own; ++u) rk += s_tmp_i[u] < v ? 1 : 0;
+        s_own[rk] = v;
+        s_own_slot[rk] = s_tmp_slot[q];
+        s_own_bin[rk] = q;
+        s_mv[rk] = P.lens_move[v];
+        if (R.has_dep) s_hdr[rk] = P.lens_hdr[v];
+    }
+    cta_sync<WARP>();
+    if (R.has_dep) {
+        if (tid == 0) {
+            int off = 0;
+            for (int q = 0; q < n_own; ++q) {
+                const int n = s_hdr[q].z;
+                if (n > 0 && off + n <= kMaxLensCTA) {
+                    s_loff[q] = off;
+                    off += n;
+                } else {
+                    s_loff[q] = -1;
+                }
+            }
+        }
+        cta_sync<WARP>();
+        for (int q = 0; q < n_own; ++q) {
+            const int n = s_hdr[q].z, o = s_loff[q];
+            if (o < 0) continue;
+            const float4 *src = P.lens + (size_t)s_own[q] * P.lens_cap;
+            for (int m = tid; m < n; m += nthr) s_lens[o + m] = src[m];
+        }
+        cta_sync<WARP>();
+    }
+
+    uint32_t c_acc = 0, c_cell = 0, c_ov = 0, c_dep = 0, c_cb = 0, c_eval = 0, c_block = 0,
+             c_fwd = 0, c_rev = 0, c_cap = 0, c_rck = 0, c_tr = 0;
+    unsigned long long c_drawn = 0;
+    const float D2c = 2.0f * R.R_circ32;
+
+    for (int q = 0; q < n_own; ++q) {
+        const int i = s_own[q];
+        const int nacc = s_nacc;
+        const float4 ri = s_cpos[s_own_slot[q]];
+        const float4 mv = s_mv[q];
+        const float kind = mv.w;
+        if (kind < -0.5f) {          // rotation attempt stream capped: rejected
+            if (tid == 0) ++c_cap;
+            continue;
+        }
+        const bool translate = kind > 0.5f;
+        if (translate) ++c_tr;
+        const float rn0 = ri.x + mv.x, rn1 = ri.y + mv.y, rn2 = ri.z + mv.z;
+        if (translate) {
+            const float mc = R.m_cell, wc = R.w32;
+            const bool out = rn0 < -mc || rn0 > wc + mc || rn1 < -mc || rn1 > wc + mc ||
+                             rn2 < -mc || rn2 > wc + mc;
+            const bool edge = rn0 <= mc || rn0 >= wc - mc || rn1 <= mc || rn1 >= wc - mc ||
+                              rn2 <= mc || rn2 >= wc - mc;
+            bool exits = out;
+            if (!out && edge) {
+                const double4 x = P.prop_pos[i];
+                exits = cell_coord(x.x, S->sigma[0], R.L, R.w, R.nc) != cx ||
+                        cell_coord(x.y, S->sigma[1], R.L, R.w, R.nc) != cy ||
+                        cell_coord(x.z, S->sigma[2], R.L, R.w, R.nc) != cz;
+                if (tid == 0) ++c_rck;
+            }
+            if (exits) {
+                ++c_cell;
+                continue;
+            }
+        }
+        const float4 qo32 = s_cq[s_own_slot[q]];
+        const float4 qn32 = translate ? qo32 : quat32(P.prop_quat[i]);
+        const Frame32 Fo = frame32(qo32);
+        const Frame32 Fn = translate ? Fo : frame32(qn32);
+        const float3 o = make_float3(ri.x - rn0, ri.y - rn1, ri.z - rn2);
+
+        // a4: colloid overlap at the new pose; neighbours in range
+        if (!WARP) {
+            if (tid == 0) s_nnb = 0;
+            __syncthreads();
+        }
+        int ov = 0, nnb = 0;
+        uint32_t st3 = 0;
+        for (int j0 = 0; j0 < M; j0 += nthr) {
+            const int j = j0 + tid;
+            int t = 0, pj = -1;
+            float d0 = 0.f, d1 = 0.f, d2 = 0.f, r2 = 1e30f;
+            float4 qj = make_float4(1.f, 0.f, 0.f, 0.f);
+            if (j < M) {
+                const float4 cp = s_cpos[j];
+                pj = __float_as_int(cp.w);
+                if (pj == i) {
+                    pj = -1;
+                } else {
+                    d0 = cp.x - rn0;
+                    d1 = cp.y - rn1;
+                    d2 = cp.z - rn2;
+                    if (d0 > R.half_L32) d0 -= R.L32; else if (d0 < -R.half_L32) d0 += R.L32;
+                    if (d1 > R.half_L32) d1 -= R.L32; else if (d1 < -R.half_L32) d1 += R.L32;
+                    if (d2 > R.half_L32) d2 -= R.L32; else if (d2 < -R.half_L32) d2 += R.L32;
+                    r2 = norm2f(d0, d1, d2);
+                    qj = s_cq[j];
+                    const float lim = D2c + R.m_pair;
+                    if (r2 < lim * lim) {
+                        Body32 A, B;
+                        A.F = Fn;
+                        A.x = make_float3(0.f, 0.f, 0.f);
+                        B.F = frame32(qj);
+                        B.x = make_float3(d0, d1, d2);
+                        const PairTri pt = pair_tri32(R, A, B);
+                        t = pt.res;
+                        if (t == -1) {
+                            ++c_rck;
+                            t = exact_pair_aniso(P, R, i, pj, s_accl, nacc, pt.n, st3) ? 1 : 0;
+                        }
+                    }
+                }
+            }
+            if (t == 1) ov = 1;
+            const bool take = pj >= 0 && r2 < R.nb_cut2_32;
+            if (WARP) {
+                const unsigned b = __ballot_sync(kFull, take);
+                const int slot = nnb + __popc(b & lt);
+                if (take && slot < kMaxNbAniso) {
+                    s_nb[slot].d = make_float4(d0, d1, d2, __int_as_float(pj));
+                    s_nb[slot].F = frame32(qj);
+                }
+                nnb += __popc(b);
+            } else if (take) {
+                const int slot = atomicAdd(&s_nnb, 1);
+                if (slot < kMaxNbAniso) {
+                    s_nb[slot].d = make_float4(d0, d1, d2, __int_as_float(pj));
+                    s_nb[slot].F = frame32(qj);
+                }
+            }
+        }
+        c_rck += st3;
+        if (cta_any<WARP>(ov)) {
+            ++c_ov;
+            continue;
+        }
+        if (!WARP) nnb = s_nnb;
+        if (nnb > kMaxNbAniso) {
+            if (tid == 0) atomicCAS(P.err, kErrNone, kErrCandCap);
+            return;
+        }
+        cta_sync<WARP>();
+
+        bool accept = true;
+        if (R.has_dep) {
+            const int4 hd = s_hdr[q];
+            const int n_p = hd.x;
+            c_drawn += (unsigned long long)n_p;
+            DepOutcome od = {1.0, 0, 0, 0u, 0u, 0u, 0u, 0u, 0u};
+            const int n_lens = hd.z;
+            const float4 *lens = s_loff[q] >= 0 ? s_lens + s_loff[q]
+                                                : P.lens + (size_t)i * P.lens_cap;
+            if (!CB && !WARP) {
+                if (tid == 0) sh.kmin = 0x7FFFFFFF;
+                __syncthreads();
+            }
+            for (int m0 = 0; m0 < n_lens; m0 += nthr) {
+                const int m = m0 + tid;
+                int cls = 0, kk = 0x7FFFFFFF;
+                uint32_t tt = 0;
+                if (m < n_lens) {
+                    const float4 Lm = lens[m];
+                    const uint32_t tk = (uint32_t)__float_as_int(Lm.w);
+                    kk = (int)(tk & 0xFFFFu);
+                    tt = tk >> 16;
+                    bool unsure = false, hit = false;
+                    for (int b = 0; b < nnb; ++b) {
+                        const float4 d = s_nb[b].d;
+                        const int tn = dep_tri32(R, make_float3(Lm.x - d.x, Lm.y - d.y, Lm.z - d.z),
+                                                 s_nb[b].F);
+                        if (tn == 1) {
+                            hit = true;
+                            break;
+                        }
+                        unsure = unsure || tn == -1;
+                    }
+                    cls = hit ? 0 : (unsure ? -1 : 1);
+                }
+                {
+                    const bool unsure = cls == -1;
+                    if (__any_sync(kFull, unsure)) {
+                        if (unsure) {
+                            ++od.rck;
+                            cls = exact_free_nb_aniso(P, R, sweep, i, tt, s_nb, nnb, s_accl, nacc) ? 1 : 0;
+                        }
+                    }
+                }
+                const bool blocking = cls == 1;
+                if (!CB) {
+                    int kmin;
+                    bool any;
+                    if (WARP) {
+                        kmin = __reduce_min_sync(kFull, blocking ? kk : 0x7FFFFFFF);
+                        any = kmin != 0x7FFFFFFF;
+                    } else {
+                        if (blocking) atomicMin(&sh.kmin, kk);
+                        any = __syncthreads_or(blocking) != 0;
+                        kmin = sh.kmin;
+                    }
+                    if (any) {
+                        od.block += 1;
+                        od.eval += (uint32_t)(kmin + 1);
+                        od.rejected = 1;
+                        break;
+                    }
+                } else {
+                    double f = -1.0;
+                    if (blocking) {
+                        const CbResult32 cr = cb_factor_aniso32(P, R, sweep, i, (uint32_t)kk, o, Fn, Fo,
+                                                                s_nb, nnb, s_accl, nacc);
+                        f = cr.f;
+                        od.fwd += cr.fwd_ok;
+                        od.rev += cr.rev_ok;
+                        od.cap += cr.caps;
+                        od.rck += cr.rck;
+                    }
+                    if (cb_pass(sh, tid, nthr, f, kk, od, -1)) {
+                        od.rejected = 1;
+                        break;
+                    }
+                }
+            }
+            if (!od.rejected) {
+                od.eval += (uint32_t)hd.y;
+                if (hd.y < n_p && tid == 0) ++od.cap;
+            }
+            c_eval += od.eval;
+            c_block += od.block;
+            c_cap += od.cap;
+            c_rck += od.rck;
+            c_fwd += od.fwd;
+            c_rev += od.rev;
+            if (od.rejected) {
+                accept = false;
+                if (!CB) ++c_dep;
+                else ++c_cb;
+            } else if (CB && tid == 0 && od.nblock > 0) {
+                const uint4 wa = draw(R.key0, R.key1, sweep, (uint32_t)(i - R.off), kPAccept, 0, 0);
+                if (!(u53(wa.x, wa.y) < od.W)) {
+                    accept = false;
+                    ++c_cb;
+                }
+            }
+            if (CB) {
+                if (WARP) {
+                    accept = __shfl_sync(kFull, accept ? 1 : 0, 0) != 0;
+                } else {
+                    if (tid == 0) s_acc = accept ? 1 : 0;
+                    __syncthreads();
+                    accept = s_acc != 0;
+                }
+            }
+        }
+        // a8: the FP32 working copies move now, the exact pose at the CTA's end
+        if (accept) {
+            ++c_acc;
+            if (tid == 0) {
+                const float4 rnew = make_float4(rn0, rn1, rn2, __int_as_float(i));
+                s_cpos[s_own_slot[q]] = rnew;
+                s_cq[s_own_slot[q]] = qn32;
+                if (translate) P.bins[(size_t)T.cell * P.cap + s_own_bin[q]] = rnew;
+                s_accl[nacc] = i;
+                s_nacc = nacc + 1;
+            }
+        }
+        cta_sync<WARP>();
+    }
+
+    const int nacc = s_nacc;
+    for (int a = tid; a < nacc; a += nthr) {
+        const int j = s_accl[a];
+        const double4 x = P.prop_pos[j];
+        P.pos[j] = make_double4(x.x, x.y, x.z, 0.0);
+        P.quat[j] = P.prop_quat[j];
+    }
+
+    unsigned long long cnt[kNumCounters] = {0};
+    if (tid == 0) {
+        cnt[kMoves] = (unsigned long long)n_own;
+        cnt[kTranslate] = c_tr;
+        cnt[kAccept] = c_acc;
+        cnt[kRejCell] = c_cell;
+        cnt[kRejOverlap] = c_ov;
+        cnt[kRejDep] = c_dep;
+        cnt[kRejCb] = c_cb;
+        cnt[kDepDrawn] = c_drawn;
+        cnt[kDepEval] = c_eval;
+        cnt[kDepBlocking] = c_block;
+    }
+    cnt[kCbFwdOk] = c_fwd;
+    cnt[kCbRevOk] = c_rev;
+    cnt[kCapHits] = c_cap;
+    cnt[kRechecks] = c_rck;
+    flush_counters(P, r, cnt);
+}
+
+}  // namespace hpmc

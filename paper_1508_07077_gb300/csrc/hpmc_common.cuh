@@ -114,6 +114,9 @@ struct Rep {
     float w32, L32, half_L32, R_s32, T_s32, T_dep32, T_contact32, nb_cut2_32, d_max32;
     float m_r2;            // bound on |r2_fp32 - r2_fp64| (+ threshold rounding), doubled
     float m_cell;          // bound on the error of a cell-relative coordinate
+    // FP32 form, anisotropic shapes: the shape in float, and the distance
+    // margins of the depletant tests and of the colloid-pair certificates
+    float R_circ32, r_dep32, sh_R32, sh_a32, sh_c32, m_d, m_pair;
     double pad_cell_bound; // host: packing bound on a cell's population
 };
 
@@ -135,7 +138,10 @@ struct SimParams {
     // depletants obtained from the stream, n, 0)
     float4 *lens;
     int4 *lens_hdr;
-    float4 *lens_move;     // the move's FP32 displacement (the phase kernels reuse it)
+    float4 *lens_move;     // the move's FP32 displacement (the phase kernels reuse it); .w the
+                           // move kind for anisotropic shapes (1 translation, 0 rotation, -1 capped)
+    double4 *prop_pos;     // anisotropic FP32 form: exact proposed position (.w = move kind)
+    double4 *prop_quat;    // and orientation
     Sched *sched;          // per replica
     unsigned long long *sweep;     // next sweep index (all replicas)
     unsigned long long *counters;  // [n_rep][kRepSlots][kNumCounters]

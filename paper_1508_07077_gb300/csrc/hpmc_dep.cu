@@ -21,6 +21,7 @@
 #include "hpmc_sphere_fp32.cuh"
 #include "hpmc_sphere_fp64.cuh"
 #include "hpmc_aniso_fp64.cuh"
+#include "hpmc_aniso_fp32.cuh"
 
 using namespace hpmc;
 
@@ -72,6 +73,7 @@ struct hpmc_ctx {
     float4 *d_lens = nullptr;     // n_total x lens_cap depletant lens points (FP32 form)
     int4 *d_lens_hdr = nullptr;
     float4 *d_lens_move = nullptr;
+    double4 *d_prop_pos = nullptr, *d_prop_quat = nullptr;
     int lens_cap = 0;
     Rep *d_reps = nullptr;
     int *d_rep_of = nullptr;
@@ -195,8 +197,9 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
     // in the FP32 form that neighbourhood must hold at most kMaxNb colloids
     // (the FP64 forms keep every candidate of the 27 cells, up to kMaxCand)
     const double nb_ext = cut + R_circ;
+    const double nb_cap = p.shape == HPMC_SPHERE ? 64.0 : 128.0;   // kMaxNb, kMaxNbAniso
     if (c->precision == HPMC_FP32_RECHECK &&
-        nb_ext * nb_ext * nb_ext * (4.0 / 3.0 * kPi) * pack / v_shape >= 64.0)
+        nb_ext * nb_ext * nb_ext * (4.0 / 3.0 * kPi) * pack / v_shape >= nb_cap)
         return HPMC_ERR_CAP;
     F.clear();
     if (lambda > 0.0) {
@@ -261,6 +264,33 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
     R.T_contact32 = (float)R.contact2;
     R.nb_cut2_32 = (float)R.nb_cut2;
     R.d_max32 = (float)h.d_max;
+    // anisotropic FP32 form.  A body-frame point errs by at most
+    // sqrt(3) E (its lab-frame offset) + 64 u |v| (an FP32 frame built from
+    // the FP32 image of the FP64 quaternion rotates v within ~33 u |v|), and
+    // the FP32 distance evaluation adds < 32 u max(1, R_circ); m_d is twice
+    // that.  A pair certificate involves two bodies: offsets 2 sqrt(3) E, the
+    // support value or witness depth 256 u max(1, R_circ), evaluation 64 u.
+    R.R_circ32 = (float)R_circ;
+    R.r_dep32 = (float)R.r_dep;
+    R.sh_R32 = (float)R.sh_R;
+    R.sh_a32 = (float)R.sh_a;
+    R.sh_c32 = (float)R.sh_c;
+    {
+        const double Rc = std::fmax(1.0, R_circ);
+        const double md = 2.0 * (std::sqrt(3.0) * E + 64.0 * u * (R_circ + R.r_dep + 1e-3) + 32.0 * u * Rc);
+        const double mp = 2.0 * (2.0 * std::sqrt(3.0) * E + 256.0 * u * Rc + 64.0 * u);
+        R.m_d = (float)std::fmax(1e-5, md);
+        R.m_pair = (float)std::fmax(1e-5, mp);
+        // the FP32 shortcuts assume the depletant radius is well above the margin
+        if (p.shape != HPMC_SPHERE && c->precision == HPMC_FP32_RECHECK && h.n_r > 0.0 &&
+            !(R.r_dep > 4.0 * R.m_d))
+            return HPMC_ERR_ARG;
+        // a larger margin set by the caller widens every FP32 test's band
+        if (p.margin > 0.0) {
+            R.m_d = (float)std::fmax((double)R.m_d, p.margin);
+            R.m_pair = (float)std::fmax((double)R.m_pair, p.margin);
+        }
+    }
     return HPMC_OK;
 }
 
@@ -285,6 +315,8 @@ SimParams make_params(hpmc_ctx *c)
     P.lens = c->d_lens;
     P.lens_hdr = c->d_lens_hdr;
     P.lens_move = c->d_lens_move;
+    P.prop_pos = c->d_prop_pos;
+    P.prop_quat = c->d_prop_quat;
     P.sched = c->d_sched;
     P.sweep = c->d_sweep;
     P.counters = c->d_counters;
@@ -310,7 +342,16 @@ void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s
     const size_t dyn = (size_t)threads * (sizeof(double) + sizeof(int));
     bool cb = false;
     for (const RepHost &h : c->reps) cb = cb || h.n_trial > 0;
-    if (c->precision == HPMC_FP32_RECHECK) {
+    if (c->precision == HPMC_FP32_RECHECK && c->prm.shape != HPMC_SPHERE) {
+        const bool warp = threads == 32;
+        if (cb) {
+            if (warp) k_phase_aniso_fp32<true, true, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
+            else k_phase_aniso_fp32<true, false, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
+        } else {
+            if (warp) k_phase_aniso_fp32<false, true, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
+            else k_phase_aniso_fp32<false, false, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
+        }
+    } else if (c->precision == HPMC_FP32_RECHECK) {
         const bool warp = threads == 32;
         if (cb) {
             if (warp) k_phase_sphere_fp32<true, true, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
@@ -334,8 +375,13 @@ void launch_phase(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
 
 void launch_lens(hpmc_ctx *c, const SimParams &P, cudaStream_t s)
 {
-    if (c->precision == HPMC_FP32_RECHECK)
+    if (c->precision != HPMC_FP32_RECHECK) return;
+    if (c->prm.shape == HPMC_SPHERE) {
         k_lens_sphere_fp32<<<(c->n_total + 3) / 4, 128, 0, s>>>(P);
+    } else {
+        k_propose_aniso<<<(c->n_total + 127) / 128, 128, 0, s>>>(P);
+        k_lens_aniso_fp32<<<(c->n_total + 3) / 4, 128, 0, s>>>(P);
+    }
 }
 
 // One sweep of every replica: binned cell lists, depletant lens lists (FP32
@@ -441,8 +487,6 @@ int check_config(hpmc_ctx *c)
 int prepare(hpmc_ctx *c)
 {
     const Params &p = c->prm;
-    // anisotropic shapes: plain FP64 form
-    if (p.shape != HPMC_SPHERE && c->precision != HPMC_FP64) return HPMC_ERR_ARG;
     const int n_rep = (int)c->reps.size();
     std::vector<Rep> rd((size_t)n_rep);
     std::vector<unsigned long long> T;
@@ -504,6 +548,10 @@ int prepare(hpmc_ctx *c)
                       cudaMemcpyHostToDevice));
     }
     // lens lists hold at most N_p <= nF points each: capacity nF_max, no overflow
+    if (c->precision == HPMC_FP32_RECHECK && p.shape != HPMC_SPHERE) {
+        if (!c->d_prop_pos) CK(cudaMalloc(&c->d_prop_pos, sizeof(double4) * (size_t)c->n_total));
+        if (!c->d_prop_quat) CK(cudaMalloc(&c->d_prop_quat, sizeof(double4) * (size_t)c->n_total));
+    }
     if (c->precision == HPMC_FP32_RECHECK) {
         if (!c->d_lens_hdr) CK(cudaMalloc(&c->d_lens_hdr, sizeof(int4) * (size_t)c->n_total));
         if (!c->d_lens_move) CK(cudaMalloc(&c->d_lens_move, sizeof(float4) * (size_t)c->n_total));
@@ -1159,6 +1207,8 @@ void hpmc_destroy(hpmc_ctx *c)
     cudaFree(c->d_lens);
     cudaFree(c->d_lens_hdr);
     cudaFree(c->d_lens_move);
+    cudaFree(c->d_prop_pos);
+    cudaFree(c->d_prop_quat);
     cudaFree(c->d_reps);
     cudaFree(c->d_rep_of);
     cudaFree(c->d_cta_rep);

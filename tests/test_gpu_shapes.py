@@ -28,12 +28,17 @@ def lib():
     return hpmc
 
 
+PRECISIONS = [0, 1]   # HPMC_FP64, HPMC_FP32_RECHECK
+
+
 def _compare(oracle, lib, s, sweeps, *, n_trial=0, d_max=0.08, a_max=0.2, p_translate=0.5,
-             warps=1, seed=1, precision=0, n_cell=0, sweep0=0):
+             warps=1, seed=1, precision=0, n_cell=0, sweep0=0, margin=0.0):
     smp = lib.Sampler(s.pos, s.L, quat=s.quat, shape=s.shape, shape_params=s.shape_params,
                       q=s.q, n_r=s.n_r, n_trial=n_trial, d_max=d_max, a_max=a_max,
                       p_translate=p_translate, seed=seed, warps=warps, precision=precision,
                       n_cell=n_cell)
+    if margin:
+        lib.hpmc_set_fp32_margin(smp.ctx, margin)
     if sweep0:
         lib.hpmc_set_state(smp.ctx, s.pos, s.quat, sweep0)
     smp.sweep(sweeps)
@@ -55,43 +60,63 @@ def _small(shape, phi, q, eta, n=256, seed=1):
     return W.make_system("small", shape, n, phi, q, eta, seed=seed)
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("shape,phi,q,eta", SHAPES)
-def test_small_system_many_sweeps(oracle, lib, shape, phi, q, eta):
-    cnt = _compare(oracle, lib, _small(shape, phi, q, eta), 30)
+def test_small_system_many_sweeps(oracle, lib, shape, phi, q, eta, precision):
+    cnt = _compare(oracle, lib, _small(shape, phi, q, eta), 30, precision=precision)
     assert cnt["accept"] > 0 and cnt["reject_overlap"] > 0 and cnt["reject_depletant"] > 0
     assert 0 < cnt["translate"] < cnt["moves"]
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("shape,phi,q,eta", SHAPES)
 @pytest.mark.parametrize("n_trial", [1, 3])
-def test_configurational_bias(oracle, lib, shape, phi, q, eta, n_trial):
-    cnt = _compare(oracle, lib, _small(shape, phi, q, eta, seed=2), 8, n_trial=n_trial)
+def test_configurational_bias(oracle, lib, shape, phi, q, eta, n_trial, precision):
+    cnt = _compare(oracle, lib, _small(shape, phi, q, eta, seed=2), 8, n_trial=n_trial,
+                   precision=precision)
     assert cnt["reject_cb"] > 0
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("shape,phi,q,eta", SHAPES)
 @pytest.mark.parametrize("warps", [2, 8])
-def test_launch_shapes(oracle, lib, shape, phi, q, eta, warps):
-    _compare(oracle, lib, _small(shape, phi, q, eta, seed=3), 5, warps=warps)
-    _compare(oracle, lib, _small(shape, phi, q, eta, seed=3), 3, warps=warps, n_trial=2)
+def test_launch_shapes(oracle, lib, shape, phi, q, eta, warps, precision):
+    s = _small(shape, phi, q, eta, seed=3)
+    _compare(oracle, lib, s, 5, warps=warps, precision=precision)
+    _compare(oracle, lib, s, 3, warps=warps, n_trial=2, precision=precision)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("shape,phi,q,eta", SHAPES)
+def test_move_mixes(oracle, lib, shape, phi, q, eta, precision):
+    s = _small(shape, phi, q, eta, n=108, seed=4)
+    kw = dict(precision=precision)
+    _compare(oracle, lib, s, 6, p_translate=0.0, **kw)                  # rotations only
+    _compare(oracle, lib, s, 6, a_max=0.0, **kw)                        # translations only
+    _compare(oracle, lib, s, 6, a_max=1.5, p_translate=0.3, sweep0=777, **kw)
+    # two cells per side: the deduplicated stencil
+    _compare(oracle, lib, _small(shape, phi, q, eta, n=32, seed=4), 6, n_cell=2, **kw)
 
 
 @pytest.mark.parametrize("shape,phi,q,eta", SHAPES)
-def test_move_mixes(oracle, lib, shape, phi, q, eta):
-    s = _small(shape, phi, q, eta, n=108, seed=4)
-    _compare(oracle, lib, s, 6, p_translate=0.0)                  # rotations only
-    _compare(oracle, lib, s, 6, a_max=0.0)                        # translations only
-    _compare(oracle, lib, s, 6, a_max=1.5, p_translate=0.3, sweep0=777)
-    # two cells per side: the deduplicated stencil
-    _compare(oracle, lib, _small(shape, phi, q, eta, n=32, seed=4), 6, n_cell=2)
+@pytest.mark.parametrize("n_trial", [0, 2])
+def test_fp32_exact_paths(oracle, lib, shape, phi, q, eta, n_trial):
+    """A margin of 1 sends every FP32 depletant test and every pair
+    certificate to the exact FP64 re-take: the trajectory must not change,
+    and the recheck counter shows the exact paths ran."""
+    s = _small(shape, phi, q, eta, n=108, seed=5)
+    cnt = _compare(oracle, lib, s, 3, n_trial=n_trial, precision=1, margin=1.0)
+    assert cnt["rechecks"] > cnt["moves"]
 
 
-def test_full_size_hemispheres(oracle, lib):
-    _compare(oracle, lib, W.hemispheres_32768(), 2, d_max=0.05)
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_full_size_hemispheres(oracle, lib, precision):
+    _compare(oracle, lib, W.hemispheres_32768(), 2, d_max=0.05, precision=precision)
 
 
-def test_full_size_discoids(oracle, lib):
-    _compare(oracle, lib, W.discoids_65536(), 1, d_max=0.05)
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_full_size_discoids(oracle, lib, precision):
+    _compare(oracle, lib, W.discoids_65536(), 1, d_max=0.05, precision=precision)
 
 
 def test_overlapping_start_is_rejected(lib):
