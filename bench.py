@@ -300,6 +300,160 @@ def run_batched(args, ws, rank, local):
         dist.destroy_process_group()
 
 
+# Anisotropic lens kernel, per depletant drawn: the sphere work plus the two
+# body-frame tests (rotation 15 + shape test 15 lane-ops), the old-pose one
+# for the ~55% that overlap the new pose; per move: two frames (2 x 20) more.
+OPS_PER_DEP_ANISO = 6.0 / math.pi * (40.0 + 11.0) + 30.0 + 0.55 * 30.0
+OPS_PER_MOVE_LENS_ANISO = 2 * 40.0 + 20.0 + 12.0 + 40.0
+# Phase kernel, per move: ~25 candidates x 8 (bounding test) and ~4 near
+# candidates through the FP32 portal refinement (~20 steps x 80 lane-ops).
+OPS_PER_MOVE_PHASE_ANISO = 25 * 8.0 + 4 * 20 * 80.0
+
+
+def run_shape(args, ws, rank, local):
+    """One anisotropic system: 32768 hemispheres (phi_c 0.25, q 0.10, eta_r
+    0.30) or 65536 discoids (phi_c 0.30, q 0.10, eta_r 0.25), translation and
+    rotation moves (a_max 0.2 rad, p_translate 0.5), d_max tuned to ~30%
+    acceptance, warps per colloid and cell size from the autotuner."""
+    import torch
+    import torch.distributed as dist
+    from paper_1508_07077_gb300 import build, hpmc, workloads as W
+
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    try:
+        hpmc.load()
+    except ImportError:
+        build.build()
+        hpmc.load()
+    prec = hpmc.HPMC_FP32_RECHECK if args.precision == "fp32" else hpmc.HPMC_FP64
+    sysf = W.hemispheres_32768 if args.workload == "hemispheres" else W.discoids_65536
+    s = sysf(seed=1)
+    stream = torch.cuda.current_stream()
+    smp = hpmc.Sampler(s.pos, s.L, quat=s.quat, shape=s.shape, shape_params=s.shape_params,
+                       q=s.q, n_r=s.n_r, d_max=0.02, a_max=s.a_max, p_translate=s.p_translate,
+                       seed=1, replica=rank, precision=prec, device=local)
+    ctx = smp.ctx
+    d = 0.02
+    for _ in range(10 if not args.no_tune else 0):
+        hpmc.hpmc_set_moves(ctx, d, s.a_max, s.p_translate)
+        hpmc.hpmc_reset_counters(ctx)
+        hpmc.hpmc_sweep(ctx, 10)
+        _, cnt = hpmc.hpmc_get_state(ctx)
+        acc = cnt["accept"] / max(1, cnt["moves"])
+        d = min(0.1, d * min(2.0, max(0.5, (acc + 0.02) / (ACC_TARGET + 0.02))))
+    hpmc.hpmc_set_moves(ctx, d, s.a_max, s.p_translate)
+    nc_auto = int(s.L / (1.0 + s.q)) & ~1
+    cells = (0, nc_auto - 2) if nc_auto > 4 else (0,)
+    warps, ncell, tuned_ms = hpmc.hpmc_autotune(ctx, warps=(1, 2, 4), cells=cells, n_sweeps=3)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        hpmc.hpmc_sweep(ctx, 1, stream)
+    hpmc.hpmc_reset_counters(ctx)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            a[k].record(stream)
+            hpmc.hpmc_sweep(ctx, 1, stream)
+            b[k].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms = sum(x.elapsed_time(y) for x, y in zip(a, b))
+    _, cnt = hpmc.hpmc_get_state(ctx)
+    # per-kernel times (kernels launched one by one, events around each)
+    hpmc.hpmc_set_timing(ctx, 1)
+    hpmc.hpmc_reset_counters(ctx)
+    tsweeps = min(args.steps, 10)
+    hpmc.hpmc_sweep(ctx, tsweeps, stream)
+    kern_ms, kern_n = hpmc.hpmc_get_timing(ctx)
+    _, tc = hpmc.hpmc_get_state(ctx)
+    hpmc.hpmc_set_timing(ctx, 0)
+    # end to end through the C ABI with host buffers
+    host_pos = torch.empty((s.n, 3), dtype=torch.float64).pin_memory().numpy()
+    host_q = torch.empty((s.n, 4), dtype=torch.float64).pin_memory().numpy()
+    sweep_now, _ = hpmc.hpmc_get_state(ctx, host_pos, host_q)
+    e2e_steps = max(3, min(args.steps, 20) // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        hpmc.hpmc_set_state(ctx, host_pos, host_q, sweep_now + k, stream)
+        hpmc.hpmc_sweep(ctx, 1, stream)
+        hpmc.hpmc_get_state(ctx, host_pos, host_q, stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    t_local = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms, e2e_s = float(t_local[0]), float(t_local[1])
+    if rank == 0:
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak = sms * ISSUE_LANES_PER_SM * 2070.0e6 / 1e12
+        cand = {}
+        if kern_n[2]:
+            lens_ops = (OPS_PER_DEP_ANISO * tc["dep_drawn"] + OPS_PER_MOVE_LENS_ANISO * tc["moves"])
+            cand["k_lens_aniso_fp32"] = (kern_ms[2], lens_ops / (kern_ms[2] * 1e-3) / 1e12)
+        ph_ops = OPS_PER_MOVE_PHASE_ANISO * tc["moves"]
+        ph_name = "k_phase_aniso_fp32" if prec == 1 else "k_phase_aniso_fp64"
+        cand[ph_name] = (kern_ms[1], ph_ops / (kern_ms[1] * 1e-3) / 1e12)
+        dominant = max(cand, key=lambda k: cand[k][0])
+        achieved = cand[dominant][1]
+        line = {
+            "metric": "colloid trial moves/s", "value": ws * cnt["moves"] / (ms * 1e-3),
+            "unit": "moves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
+            "config": {"workload": s.name + "_phi%.2f_q%.2f_eta%.2f" % (
+                           s.extra["phi_c"], s.q, s.extra["eta_r"]),
+                       "form": "FP32+FP64 recheck" if prec == 1 else "FP64",
+                       "n_trial": 0, "a_max": s.a_max, "p_translate": s.p_translate,
+                       "d_max": round(d, 5), "step": "1 sweep (%d moves)" % s.n,
+                       "autotuned": {"warps_per_colloid": warps, "n_cell": ncell,
+                                     "ms_per_sweep": tuned_ms},
+                       "l2": "flushed between steps (256 MB write)"},
+            "insertions_drawn_per_s": ws * cnt["dep_drawn"] / (ms * 1e-3),
+            "insertions_evaluated_per_s": ws * cnt["dep_evaluated"] / (ms * 1e-3),
+            "acceptance": cnt["accept"] / max(1, cnt["moves"]),
+            "translate_fraction": cnt["translate"] / max(1, cnt["moves"]),
+            "fp64_rechecks_per_move": cnt["rechecks"] / max(1, cnt["moves"]),
+            "gpu_launches": args.steps * (1 + (2 if prec == 1 else 0) + 8),
+            "kernels": {"phase_ms_per_sweep": kern_ms[1] / tsweeps,
+                        "lens_ms_per_sweep": kern_ms[2] / tsweeps,
+                        "cells_ms_per_sweep": kern_ms[0] / tsweeps,
+                        "achieved_tops": {k: v[1] for k, v in cand.items()}},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": dominant,
+                         "peak_basis": "%d SMs x 128 lanes x 2070 MHz (issue rate)" % sms},
+            "clocks": clk.summary(),
+            "e2e": {"value": ws * e2e_steps * s.n / e2e_s, "unit": "moves/s",
+                    "h2d_bytes_per_step": s.n * 7 * 8, "d2h_bytes_per_step": s.n * 7 * 8 + 128},
+        }
+        if not args.no_cpu_baseline:
+            from oracle import oracle as O
+            O.build()
+            pos, quat, _, _ = smp.state(with_quat=True)
+            t0 = time.perf_counter()
+            _, _, oc, _ = O.run(pos, s.L, shape=s.shape, shape_params=s.shape_params, quat=quat,
+                                q=s.q, n_r=s.n_r, d_max=d, a_max=s.a_max,
+                                p_translate=s.p_translate, seed=1, n_cell=ncell,
+                                n_sweeps=args.cpu_sweeps_shape, sweep0=sweep_now + e2e_steps)
+            dt = time.perf_counter() - t0
+            line["cpu_baseline"] = {"value": oc["moves"] / dt, "unit": "moves/s", "cores": 1,
+                                    "kind": "oracle",
+                                    "sample": "%d sweeps of the system (%d moves, %.1f s)"
+                                              % (args.cpu_sweeps_shape, oc["moves"], dt)}
+        print(json.dumps(line))
+    smp.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import torch.distributed as dist
@@ -500,9 +654,12 @@ def main():
     ap.add_argument("--warps", type=int, default=1)
     ap.add_argument("--ilp", type=int, default=1)
     ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--workload", choices=("spheres_16384", "batched"), default="spheres_16384",
+    ap.add_argument("--workload", choices=("spheres_16384", "batched", "hemispheres", "discoids"),
+                    default="spheres_16384",
                     help="spheres_16384: the headline four-state-point workload; batched: "
-                         "128 replicas of uneven size and state point")
+                         "128 replicas of uneven size and state point; hemispheres / "
+                         "discoids: 32768 hemispheres or 65536 discoids with rotations")
+    ap.add_argument("--cpu-sweeps-shape", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sweeps", type=int, default=25)
     args = ap.parse_args()
@@ -513,6 +670,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.workload == "batched":
         run_batched(args, ws, rank, local)
+    elif args.workload in ("hemispheres", "discoids"):
+        run_shape(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

@@ -152,15 +152,32 @@ int hpmc_set_moves(hpmc_ctx *ctx, double d_max, double a_max, double p_translate
  * largest valid count.  Part of the trajectory's definition (Sec. III.E). */
 int hpmc_set_cells(hpmc_ctx *ctx, int n_cell);
 
-/* Launch shape: warps cooperating on one moved colloid's depletants (1..8,
- * default 1) and depletant attempts each thread carries per pass (1 or 2,
- * default 1; FP32 form).  Performance knobs only: results are identical for
- * every value. */
+/* Launch shape: warps cooperating on one moved colloid's depletants and
+ * colloid tests in the colour-phase kernels (1..8, default 1).
+ * attempts_per_thread (1 or 2) is accepted for interface stability; the
+ * kernels take one depletant attempt per thread per pass for either value.
+ * Performance knobs only: results are identical for every value. */
 int hpmc_set_launch(hpmc_ctx *ctx, int warps_per_colloid, int attempts_per_thread);
+
+/* Autotuner: time every combination of warps_per_colloid in warps[0..nw)
+ * and cells per side in cells[0..nc) (0 = the largest valid count) over
+ * n_sweeps sweeps each (after one untimed sweep), on the context's own
+ * systems, and keep the fastest.  The configuration, sweep index and
+ * counters are restored afterwards, so the trajectory continues as if the
+ * tuning had not run; the chosen cell count is part of the trajectory's
+ * definition from then on (hpmc_set_cells).  A candidate the library rejects
+ * (e.g. a cell width below 2 R_circ + q) is skipped.  Writes the choice to
+ * *best_warps, *best_cells (either may be NULL) and its milliseconds per
+ * sweep to *best_ms (may be NULL).  Synchronous.  HPMC_ERR_ARG if no
+ * candidate is valid. */
+int hpmc_autotune(hpmc_ctx *ctx, const int *warps, int nw, const int *cells, int nc,
+                  int n_sweeps, int *best_warps, int *best_cells, double *best_ms);
 
 /* FP32 form only: margin on squared distances inside which an FP32 decision
  * is re-taken in FP64.  0 selects the derived certified bound (default);
  * a value below that bound is rejected with HPMC_ERR_ARG at the next sweep.
+ * For the anisotropic shapes a value above the derived distance margins of
+ * the depletant tests and of the pair certificates replaces them as well.
  * Larger margins only move more decisions to the exact FP64 path. */
 int hpmc_set_fp32_margin(hpmc_ctx *ctx, double margin);
 

@@ -908,6 +908,102 @@ int hpmc_set_launch(hpmc_ctx *c, int warps_per_colloid, int attempts_per_thread)
     return HPMC_OK;
 }
 
+int hpmc_autotune(hpmc_ctx *c, const int *warps, int nw, const int *cells, int nc, int n_sweeps,
+                  int *best_warps, int *best_cells, double *best_ms)
+{
+    if (!c || !warps || !cells || nw < 1 || nc < 1 || n_sweeps < 1) return HPMC_ERR_ARG;
+    for (int a = 0; a < nw; ++a)
+        if (warps[a] < 1 || warps[a] > kMaxThreads / 32) return HPMC_ERR_ARG;
+    for (int b = 0; b < nc; ++b)
+        if (cells[b] < 0 || (cells[b] & 1) || cells[b] == 1) return HPMC_ERR_ARG;
+    DeviceGuard g(c->device);
+    CK(cudaDeviceSynchronize());
+    const int n = c->n_total;
+    const size_t cnt_bytes = sizeof(unsigned long long) * c->reps.size() * kRepSlots * kNumCounters;
+    // saved state: poses, sweep index, counters, configuration
+    double4 *sp = nullptr, *sq = nullptr;
+    unsigned long long *sc = nullptr, sweep0 = 0;
+    CK(cudaMalloc(&sp, sizeof(double4) * (size_t)n));
+    cudaError_t e = cudaMalloc(&sq, sizeof(double4) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&sc, cnt_bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(sp, c->d_pos, sizeof(double4) * (size_t)n, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(sq, c->d_quat, sizeof(double4) * (size_t)n, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(sc, c->d_counters, cnt_bytes, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(&sweep0, c->d_sweep, sizeof sweep0, cudaMemcpyDeviceToHost);
+    const Params p0 = c->prm;
+    std::vector<int> nc0(c->reps.size());
+    for (size_t r = 0; r < c->reps.size(); ++r) nc0[r] = c->reps[r].nc_req;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    int rc = cuda_fail(e, "autotune setup");
+    double best = 1e300;
+    int bw = -1, bc = -1;
+    auto restore = [&]() -> int {
+        CK(cudaMemcpy(c->d_pos, sp, sizeof(double4) * (size_t)n, cudaMemcpyDeviceToDevice));
+        CK(cudaMemcpy(c->d_quat, sq, sizeof(double4) * (size_t)n, cudaMemcpyDeviceToDevice));
+        CK(cudaMemcpy(c->d_counters, sc, cnt_bytes, cudaMemcpyDeviceToDevice));
+        CK(cudaMemcpy(c->d_sweep, &sweep0, sizeof sweep0, cudaMemcpyHostToDevice));
+        CK(cudaMemset(c->d_err, 0, sizeof(int)));
+        c->state_dirty = true;   // cell populations are rebuilt before the next sweep
+        return HPMC_OK;
+    };
+    for (int b = 0; b < nc && rc == HPMC_OK; ++b) {
+        for (int a = 0; a < nw && rc == HPMC_OK; ++a) {
+            c->prm.warps = warps[a];
+            for (RepHost &h : c->reps) h.nc_req = cells[b];
+            c->dirty = true;
+            const bool timing = c->timing;
+            c->timing = false;
+            int rs = hpmc_sweep(c, 1, c->cap_stream);
+            if (rs == HPMC_OK) {
+                e = cudaEventRecord(t0, c->cap_stream);
+                if (e == cudaSuccess) rs = hpmc_sweep(c, n_sweeps, c->cap_stream);
+                if (e == cudaSuccess && rs == HPMC_OK) e = cudaEventRecord(t1, c->cap_stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                float ms = 0.0f;
+                if (e == cudaSuccess && rs == HPMC_OK) e = cudaEventElapsedTime(&ms, t0, t1);
+                if (e != cudaSuccess) rc = cuda_fail(e, "autotune timing");
+                else if (rs == HPMC_OK && read_err(c, c->cap_stream) == HPMC_OK &&
+                         ms / n_sweeps < best) {
+                    best = ms / n_sweeps;
+                    bw = warps[a];
+                    bc = cells[b];
+                }
+            } else if (rs == HPMC_ERR_CUDA) {
+                rc = rs;
+            }
+            c->timing = timing;
+            if (rc == HPMC_OK) rc = restore();
+        }
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    cudaFree(sp);
+    cudaFree(sq);
+    cudaFree(sc);
+    if (rc != HPMC_OK) {
+        c->prm = p0;
+        for (size_t r = 0; r < c->reps.size(); ++r) c->reps[r].nc_req = nc0[r];
+        c->dirty = true;
+        return rc;
+    }
+    if (bw < 0) {
+        c->prm = p0;
+        for (size_t r = 0; r < c->reps.size(); ++r) c->reps[r].nc_req = nc0[r];
+        c->dirty = true;
+        return HPMC_ERR_ARG;
+    }
+    c->prm = p0;
+    c->prm.warps = bw;
+    for (RepHost &h : c->reps) h.nc_req = bc;
+    c->dirty = true;
+    if (best_warps) *best_warps = bw;
+    if (best_cells) *best_cells = bc;
+    if (best_ms) *best_ms = best;
+    return HPMC_OK;
+}
+
 int hpmc_sweep(hpmc_ctx *c, int n_sweeps, void *stream)
 {
     if (!c || n_sweeps < 0) return HPMC_ERR_ARG;

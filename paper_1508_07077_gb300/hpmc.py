@@ -24,7 +24,8 @@ HPMC_HOST, HPMC_DEVICE = 0, 1
 
 EXPORTS = ("hpmc_init", "hpmc_init_batch", "hpmc_get_replica", "hpmc_set_replica_moves",
            "hpmc_set_shape", "hpmc_set_depletant", "hpmc_set_moves",
-           "hpmc_set_cells", "hpmc_set_launch", "hpmc_set_fp32_margin", "hpmc_set_timing",
+           "hpmc_set_cells", "hpmc_set_launch", "hpmc_autotune", "hpmc_set_fp32_margin",
+           "hpmc_set_timing",
            "hpmc_get_timing", "hpmc_sweep", "hpmc_get_state",
            "hpmc_set_state", "hpmc_reset_counters", "hpmc_sync", "hpmc_cell_list",
            "hpmc_cell_list_noalloc", "hpmc_strerror", "hpmc_destroy")
@@ -81,6 +82,9 @@ def load(path: str = LIB_PATH):
     L.hpmc_set_moves.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.hpmc_set_cells.argtypes = [vp, ip]
     L.hpmc_set_launch.argtypes = [vp, ip, ip]
+    L.hpmc_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ip, ctypes.POINTER(ctypes.c_int),
+                                ip, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_double)]
     L.hpmc_set_fp32_margin.argtypes = [vp, ctypes.c_double]
     L.hpmc_set_timing.argtypes = [vp, ip]
     L.hpmc_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
@@ -210,6 +214,18 @@ def hpmc_set_moves(ctx, d_max, a_max=0.0, p_translate=1.0):
 
 def hpmc_set_cells(ctx, n_cell):
     _check(load().hpmc_set_cells(ctx, int(n_cell)), "hpmc_set_cells")
+
+
+def hpmc_autotune(ctx, warps=(1, 2, 4), cells=(0,), n_sweeps=5):
+    """Time every (warps_per_colloid, cells per side) pair and keep the fastest;
+    the state is restored.  Returns (warps, cells, ms_per_sweep)."""
+    wa = (ctypes.c_int * len(warps))(*[int(w) for w in warps])
+    ca = (ctypes.c_int * len(cells))(*[int(c) for c in cells])
+    bw, bc, bm = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(load().hpmc_autotune(ctx, wa, len(warps), ca, len(cells), int(n_sweeps),
+                                ctypes.byref(bw), ctypes.byref(bc), ctypes.byref(bm)),
+           "hpmc_autotune")
+    return bw.value, bc.value, bm.value
 
 
 def hpmc_set_launch(ctx, warps_per_colloid, attempts_per_thread=1):

@@ -131,3 +131,29 @@ def test_overlapping_start_is_rejected(lib):
     with pytest.raises(lib.HPMCError):
         smp.sweep(1)
     smp.close()
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_autotuner_keeps_the_trajectory(oracle, lib, precision):
+    """Tuning times candidate launch shapes and cell counts on the live system
+    and restores it: the trajectory continues as if nothing ran, with the
+    chosen cell count from then on.  A cell count whose bins would overflow
+    (two cells per side here) is skipped."""
+    s = _small(W.HEMISPHERE, 0.25, 0.1, 0.3, n=256, seed=6)
+    kw = dict(q=s.q, n_r=s.n_r, d_max=0.08, a_max=0.2, p_translate=0.5)
+    smp = lib.Sampler(s.pos, s.L, quat=s.quat, shape=s.shape, shape_params=s.shape_params,
+                      seed=1, precision=precision, **kw)
+    smp.sweep(2)
+    warps, ncell, ms = lib.hpmc_autotune(smp.ctx, warps=(1, 2), cells=(0, 2), n_sweeps=2)
+    assert warps in (1, 2) and ncell == 0 and ms > 0
+    smp.sweep(3)
+    pos, quat, sweep, cnt = smp.state(with_quat=True)
+    smp.close()
+    p1, q1, c1, _ = oracle.run(s.pos, s.L, shape=s.shape, shape_params=s.shape_params,
+                               quat=s.quat, seed=1, n_sweeps=2, **kw)
+    p2, q2, c2, _ = oracle.run(p1, s.L, shape=s.shape, shape_params=s.shape_params, quat=q1,
+                               seed=1, n_sweeps=3, sweep0=2, n_cell=ncell, **kw)
+    assert sweep == 5
+    assert np.array_equal(pos, p2) and np.array_equal(quat, q2)
+    for k in oracle.PARITY_COUNTERS:
+        assert cnt[k] == c1[k] + c2[k], k
