@@ -117,6 +117,9 @@ struct Rep {
     // FP32 form, anisotropic shapes: the shape in float, and the distance
     // margins of the depletant tests and of the colloid-pair certificates
     float R_circ32, r_dep32, sh_R32, sh_a32, sh_c32, m_d, m_pair;
+    // spheroid quick tests: 1/a^2, 1/c^2 of the body, of the inner spheroid
+    // (a + r, c + r) and of the outer spheroid, and the squared thresholds
+    float sp_iA2, sp_iC2, sp_inA, sp_inC, sp_outA, sp_outC, sp_kin2, sp_kout2;
     double pad_cell_bound; // host: packing bound on a cell's population
 };
 

@@ -290,6 +290,26 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
             R.m_d = (float)std::fmax((double)R.m_d, p.margin);
             R.m_pair = (float)std::fmax((double)R.m_pair, p.margin);
         }
+        // spheroid quick tests.  The outer spheroid (A', A', C') contains
+        // E + ball(r) iff sqrt(a^2 x + c^2 z) + r <= sqrt(A'^2 x + C'^2 z) for
+        // x + z = 1 (support functions); with A' = a + r (oblate) this holds iff
+        // C'^2 >= c^2 + r^2 + K, K = max(2 r c, r (a^2 + c^2) / a) (the squared
+        // inequality is linear in x, so its end points decide), and symmetrically
+        // for a prolate spheroid.
+        const double a = R.sh_a, cc = R.sh_c, rr = R.r_dep, md2 = (double)R.m_d;
+        double Ao = a + rr, Co = cc + rr;
+        if (a >= cc) Co = std::sqrt(cc * cc + rr * rr + std::fmax(2.0 * rr * cc, rr * (a * a + cc * cc) / a));
+        else Ao = std::sqrt(a * a + rr * rr + std::fmax(2.0 * rr * a, rr * (a * a + cc * cc) / cc));
+        const double kin = 1.0 - md2 / std::fmin(a + rr, cc + rr);
+        const double kout = 1.0 + md2 / std::fmin(Ao, Co);
+        R.sp_iA2 = (float)(1.0 / (a * a));
+        R.sp_iC2 = (float)(1.0 / (cc * cc));
+        R.sp_inA = (float)(1.0 / ((a + rr) * (a + rr)));
+        R.sp_inC = (float)(1.0 / ((cc + rr) * (cc + rr)));
+        R.sp_outA = (float)(1.0 / (Ao * Ao));
+        R.sp_outC = (float)(1.0 / (Co * Co));
+        R.sp_kin2 = kin > 0.0 ? (float)(kin * kin) : -1.0f;
+        R.sp_kout2 = (float)(kout * kout);
     }
     return HPMC_OK;
 }

@@ -70,25 +70,13 @@ __device__ __forceinline__ int tri_less(float d, float thr, float m)
     return d < thr - m ? 1 : (d > thr + m ? 0 : -1);
 }
 
-// Spheroid (a, a, c), body point p: certified "dist(p, E) < r".  Inside E or
-// inside the (a + r, c + r) spheroid (which lies inside E + ball(r)) with
-// margin: overlap; outside the slab |z| < c + r or the cylinder rho < a + r
-// with margin: none.  Otherwise Newton's method for the meridian foot point
+// Spheroid (a, a, c), body point p, outside the quick tests below: certified
+// "dist(p, E) < r" by Newton's method for the meridian foot point, which
 // gives an ellipse point X (an upper bound |P - X| on the distance) and its
 // normal n (a lower bound n.P - h(n), h the ellipse's support function).
-__device__ __noinline__ int spheroid_tri32(float a, float c, float r, float m, float3 p)
+__device__ __noinline__ int spheroid_newton32(float a, float c, float r, float m, float rho2, float z)
 {
     const float A2 = a * a, C2 = c * c;
-    const float rho2 = p.x * p.x + p.y * p.y;
-    const float z = fabsf(p.z);
-    const float ar = a + r, cr = c + r;
-    // inside E: |p| within E_p of E, distance <= E_p + rounding < r
-    if (rho2 / A2 + z * z / C2 <= 1.0f) return 1;
-    // inside the inner spheroid by at least m in distance: s^2 < (1 - m/cr)^2
-    const float sin2 = rho2 / (ar * ar) + z * z / (cr * cr);
-    const float kin = 1.0f - m / fminf(ar, cr);
-    if (kin > 0.0f && sin2 < kin * kin) return 1;
-    if (z > cr + m || rho2 > (ar + m) * (ar + m)) return 0;
     const float rho = sqrtf(rho2);
     float t = 0.0f;
 #pragma unroll 1
@@ -119,6 +107,25 @@ __device__ __noinline__ int spheroid_tri32(float a, float c, float r, float m, f
     return -1;
 }
 
+// Spheroid quick tests, with s_X^2 = rho^2 / A^2 + z^2 / C^2 for a spheroid X
+// of semi-axes (A, A, C): inside E (s_E <= 1): overlap.  Inside the inner
+// spheroid (a + r, c + r), which lies inside E + ball(r), by more than m
+// (s_in < 1 - m / min semi-axis): overlap.  Outside the outer spheroid
+// (host: the smallest coaxial one containing E + ball(r) with one axis equal
+// to its extent) by more than m (s_out > 1 + m / min semi-axis): none.  A
+// point on the boundary of sX is at least (s - 1) min(A, C) from X, which
+// turns the s thresholds into distances.  The band between inner and outer
+// spheroid (~2% of the sampling ball for the discoid) goes to Newton.
+__device__ __forceinline__ int spheroid_tri32(const Rep &R, float m, float3 p)
+{
+    const float rho2 = p.x * p.x + p.y * p.y;
+    const float z2 = p.z * p.z;
+    if (rho2 * R.sp_iA2 + z2 * R.sp_iC2 <= 1.0f) return 1;
+    if (rho2 * R.sp_inA + z2 * R.sp_inC < R.sp_kin2) return 1;
+    if (rho2 * R.sp_outA + z2 * R.sp_outC > R.sp_kout2) return 0;
+    return spheroid_newton32(R.sh_a32, R.sh_c32, R.r_dep32, m, rho2, fabsf(p.z));
+}
+
 // Depletant at v (lab frame, relative to the colloid's reference point)
 // against an anisotropic colloid with frame F.
 __device__ __forceinline__ int dep_tri32(const Rep &R, float3 v, const Frame32 &F)
@@ -146,7 +153,7 @@ __device__ __forceinline__ int dep_tri32(const Rep &R, float3 v, const Frame32 &
         }
         return tri_less(d, r, m);
     }
-    return spheroid_tri32(R.sh_a32, R.sh_c32, r, m, p);
+    return spheroid_tri32(R, m, p);
 }
 
 // Support point (body frame) in direction n, FP32.
