@@ -63,10 +63,8 @@ MEASURED_TRAFFIC = {"k_phase_sphere_fp32": 9.47e6}
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1508_07077_gb300 import replicas
+    return replicas.world()
 
 
 class ClockSampler:
@@ -209,7 +207,7 @@ def run_batched(args, ws, rank, local):
     same replicas one at a time (each in its own context, one stream)."""
     import torch
     import torch.distributed as dist
-    from paper_1508_07077_gb300 import build, hpmc, workloads as W
+    from paper_1508_07077_gb300 import build, hpmc, replicas as R, workloads as W
 
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -223,7 +221,8 @@ def run_batched(args, ws, rank, local):
     stream = torch.cuda.current_stream()
     reps = W.batched_replicas(128, seed=1)
     descs = [{"n": s.n, "box_l": s.L, "pos": s.pos, "q": s.q, "n_r": s.n_r, "n_trial": 0,
-              "d_max": 0.01, "replica": rank * 128 + k} for k, s in enumerate(reps)]
+              "d_max": 0.01, "replica": R.replica_ids(128, rank)[k]}
+             for k, s in enumerate(reps)]
     ctx = hpmc.hpmc_init_batch(descs, seed=1, precision=prec, device=local)
     ns = [s.n for s in reps]
     dtuned = tune_batch(ctx, hpmc, [0.01] * len(reps), ns, rounds=8, sweeps=10)
@@ -272,12 +271,12 @@ def run_batched(args, ws, rank, local):
     seq_ms = sum(x.elapsed_time(y) for x, y in zip(sa, sb))
     for smp in singles:
         smp.close()
-    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms = float(t_local[0])
+    # whole job: every rank's units over the slowest rank's time
+    ms, seq_ms = R.reduce_max([ms, seq_ms], "cuda")
+    moves_all, drawn_all, eval_all = R.reduce_sum(
+        [cnt["moves"], cnt["dep_drawn"], cnt["dep_evaluated"]], "cuda")
     if rank == 0:
-        value = ws * cnt["moves"] / (ms * 1e-3)
+        value = moves_all / (ms * 1e-3)
         line = {
             "metric": "colloid trial moves/s", "value": value, "unit": "moves/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -288,8 +287,8 @@ def run_batched(args, ws, rank, local):
                        "step": "1 sweep of every replica, one batch (one set of launches)",
                        "l2": "flushed between steps (256 MB write)"},
             "one_at_a_time_moves_per_s": ws * seq_steps * sum(ns) / (seq_ms * 1e-3),
-            "insertions_drawn_per_s": ws * cnt["dep_drawn"] / (ms * 1e-3),
-            "insertions_evaluated_per_s": ws * cnt["dep_evaluated"] / (ms * 1e-3),
+            "insertions_drawn_per_s": drawn_all / (ms * 1e-3),
+            "insertions_evaluated_per_s": eval_all / (ms * 1e-3),
             "acceptance": cnt["accept"] / max(1, cnt["moves"]),
             "gpu_launches": args.steps * (1 + (1 if prec == 1 else 0) + 8),
             "clocks": clk.summary(),
@@ -317,7 +316,7 @@ def run_shape(args, ws, rank, local):
     acceptance, warps per colloid and cell size from the autotuner."""
     import torch
     import torch.distributed as dist
-    from paper_1508_07077_gb300 import build, hpmc, workloads as W
+    from paper_1508_07077_gb300 import build, hpmc, replicas as R, workloads as W
 
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -333,7 +332,8 @@ def run_shape(args, ws, rank, local):
     stream = torch.cuda.current_stream()
     smp = hpmc.Sampler(s.pos, s.L, quat=s.quat, shape=s.shape, shape_params=s.shape_params,
                        q=s.q, n_r=s.n_r, d_max=0.02, a_max=s.a_max, p_translate=s.p_translate,
-                       seed=1, replica=rank, precision=prec, device=local)
+                       seed=1, replica=R.replica_ids(1, rank)[0], precision=prec,
+                       device=local)
     ctx = smp.ctx
     d = 0.02
     for _ in range(10 if not args.no_tune else 0):
@@ -388,10 +388,9 @@ def run_shape(args, ws, rank, local):
         hpmc.hpmc_get_state(ctx, host_pos, host_q, stream)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    t_local = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms, e2e_s = float(t_local[0]), float(t_local[1])
+    ms, e2e_s = R.reduce_max([ms, e2e_s], "cuda")
+    moves_all, drawn_all, eval_all = R.reduce_sum(
+        [cnt["moves"], cnt["dep_drawn"], cnt["dep_evaluated"]], "cuda")
     if rank == 0:
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         peak = sms * ISSUE_LANES_PER_SM * 2070.0e6 / 1e12
@@ -405,7 +404,7 @@ def run_shape(args, ws, rank, local):
         dominant = max(cand, key=lambda k: cand[k][0])
         achieved = cand[dominant][1]
         line = {
-            "metric": "colloid trial moves/s", "value": ws * cnt["moves"] / (ms * 1e-3),
+            "metric": "colloid trial moves/s", "value": moves_all / (ms * 1e-3),
             "unit": "moves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
@@ -417,8 +416,8 @@ def run_shape(args, ws, rank, local):
                        "autotuned": {"warps_per_colloid": warps, "n_cell": ncell,
                                      "ms_per_sweep": tuned_ms},
                        "l2": "flushed between steps (256 MB write)"},
-            "insertions_drawn_per_s": ws * cnt["dep_drawn"] / (ms * 1e-3),
-            "insertions_evaluated_per_s": ws * cnt["dep_evaluated"] / (ms * 1e-3),
+            "insertions_drawn_per_s": drawn_all / (ms * 1e-3),
+            "insertions_evaluated_per_s": eval_all / (ms * 1e-3),
             "acceptance": cnt["accept"] / max(1, cnt["moves"]),
             "translate_fraction": cnt["translate"] / max(1, cnt["moves"]),
             "fp64_rechecks_per_move": cnt["rechecks"] / max(1, cnt["moves"]),
@@ -457,7 +456,7 @@ def run_shape(args, ws, rank, local):
 def run_ours(args, ws, rank, local):
     import torch
     import torch.distributed as dist
-    from paper_1508_07077_gb300 import build, hpmc, workloads as W
+    from paper_1508_07077_gb300 import build, hpmc, replicas as R, workloads as W
 
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -475,7 +474,7 @@ def run_ours(args, ws, rank, local):
     systems = [W.spheres_16384(eta, seed=1) for eta in ETAS]
     etas = [round(s.extra["eta_r"], 1) for s in systems]
     descs = [{"n": s.n, "box_l": s.L, "pos": s.pos, "q": s.q, "n_r": s.n_r, "n_trial": 0,
-              "d_max": D_MAX_TUNED[e], "replica": rank * len(systems) + k}
+              "d_max": D_MAX_TUNED[e], "replica": R.replica_ids(len(systems), rank)[k]}
              for k, (s, e) in enumerate(zip(systems, etas))]
     ctx = hpmc.hpmc_init_batch(descs, seed=1, precision=prec, device=local)
     hpmc.hpmc_set_launch(ctx, args.warps, args.ilp)
@@ -568,10 +567,8 @@ def run_ours(args, ws, rank, local):
     e2e_s = time.perf_counter() - t0
 
     # max over ranks
-    t_local = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms, e2e_s = float(t_local[0]), float(t_local[1])
+    ms, e2e_s, seq_ms = R.reduce_max([ms, e2e_s, seq_ms], "cuda")
+    moves_all, drawn_all, eval_all = R.reduce_sum([moves, drawn, evaluated], "cuda")
 
     if rank == 0:
         clocks = clk.summary()
@@ -592,7 +589,7 @@ def run_ours(args, ws, rank, local):
         dominant = max(cand, key=lambda k: cand[k][0])
         achieved = cand[dominant][1]
         bytes_per_launch = BYTES_PER_MOVE * t_moves / max(1, kern_n[1])
-        value = ws * moves / (ms * 1e-3)
+        value = moves_all / (ms * 1e-3)
         e2e_moves = ws * e2e_steps * sum(ns)
         line = {
             "metric": "colloid trial moves/s", "value": value, "unit": "moves/s",
@@ -606,8 +603,8 @@ def run_ours(args, ws, rank, local):
                        "l2": "flushed between steps (256 MB write)",
                        "warps_per_colloid": args.warps, "attempts_per_thread": args.ilp},
             "one_at_a_time_moves_per_s": ws * seq_steps * sum(ns) / (seq_ms * 1e-3),
-            "insertions_drawn_per_s": ws * drawn / (ms * 1e-3),
-            "insertions_evaluated_per_s": ws * evaluated / (ms * 1e-3),
+            "insertions_drawn_per_s": drawn_all / (ms * 1e-3),
+            "insertions_evaluated_per_s": eval_all / (ms * 1e-3),
             "acceptance": accept / max(1, moves),
             "fp64_rechecks_per_move": rechecks / max(1, moves),
             "gpu_launches": args.steps * (1 + (1 if prec == 1 else 0) + 8),
