@@ -14,11 +14,37 @@
 
 namespace hpmc {
 
+// Cell of colour-phase CTA `a` of replica r in phase `phase`.
+// Entry: (global cell, replica, cx | cy << 10 | cz << 20, nc | (sweep & 1) << 16),
+// everything a phase CTA needs to start loading its stencil.
+__device__ __forceinline__ int4 phase_task(const Rep &R, int r, const int perm[8], int phase, int a,
+                                           uint32_t sweep)
+{
+    const int colour = perm[phase];
+    const int h = R.half_nc, nc = R.nc;
+    const int cx = 2 * (a % h) + (colour & 1);
+    const int cy = 2 * ((a / h) % h) + ((colour >> 1) & 1);
+    const int cz = 2 * (a / (h * h)) + ((colour >> 2) & 1);
+    return make_int4(R.cell_off + cx + nc * (cy + nc * cz), r, cx | (cy << 10) | (cz << 20),
+                     nc | (int)((sweep & 1u) << 16));
+}
+
 // One thread per colloid of the batch.  The first colloid of each replica
-// also writes that replica's schedule.
+// also writes that replica's schedule.  When the task table is allocated,
+// threads also fill it (one entry per phase and CTA), so that the colour
+// phases start from their cell without recomputing the schedule.
 __global__ void k_cells_bin(const __grid_constant__ SimParams P)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P.task && g < 8 * P.n_cta) {
+        const int phase = g / P.n_cta, a = g - phase * P.n_cta;
+        const int r = P.cta_rep[a];
+        const Rep &R = P.reps[r];
+        int perm[8];
+        const uint32_t sw = (uint32_t)(*P.sweep);
+        schedule_perm(R.key0, R.key1, sw, perm);
+        P.task[g] = phase_task(R, r, perm, phase, a - R.cta_off, sw);
+    }
     if (g >= P.n_total) return;
     const int r = P.rep_of[g];
     const Rep &R = P.reps[r];
@@ -46,6 +72,7 @@ __global__ void k_cells_bin(const __grid_constant__ SimParams P)
     const int slot = atomicAdd(P.count[sweep & 1u] + c, 1);
     if (slot < P.cap) P.bins[(size_t)c * P.cap + slot] = rl;
     else atomicCAS(P.err, kErrNone, kErrCellCap);
+    if (P.binpos) P.binpos[g] = slot < P.cap ? c * P.cap + slot : -1;
     P.rel[g] = rl;
 }
 

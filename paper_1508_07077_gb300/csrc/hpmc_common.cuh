@@ -25,6 +25,7 @@ constexpr int kMaxCellCap = 64;      // colloids per cell bin, largest capacity 
 constexpr int kSmallCellCap = 32;    // capacity of the usual cells (width near d_colloid + d_depletant)
 constexpr int kRepSlots = 16;        // per replica, counters are spread over slots (fewer hot atomics)
 constexpr int kNumCounters = 16;
+constexpr int kLensInline = 4;       // lens points kept beside each bin slot (FP32 sphere form)
 
 enum Counter {
     kMoves = 0, kAccept, kRejCell, kRejOverlap, kRejDep, kRejCb, kDepDrawn,
@@ -125,6 +126,7 @@ struct Rep {
 
 struct SimParams {
     int n_rep, n_total, cap, lens_cap;
+    int n_cta;             // CTAs of a colour-phase grid (all replicas)
     const Rep *reps;
     const int *rep_of;     // global colloid index -> replica
     const int *cta_rep;    // CTA of a colour-phase grid -> replica
@@ -145,6 +147,15 @@ struct SimParams {
                            // move kind for anisotropic shapes (1 translation, 0 rotation, -1 capped)
     double4 *prop_pos;     // anisotropic FP32 form: exact proposed position (.w = move kind)
     double4 *prop_quat;    // and orientation
+    // per-sweep tables written by the cell-list kernel for the FP32 sphere
+    // phases: task[phase][cta] = (global cell, replica, cx | cy << 10 | cz << 20);
+    // binpos[g] = cell * cap + slot of colloid g; the lens kernel's header
+    // (N_p, obtained, n_lens) and displacement of each bin slot
+    int4 *task;
+    int *binpos;
+    int4 *hdr_bin;
+    float4 *mv_bin;
+    float4 *lens_bin;      // the first kLensInline lens points of each bin slot
     Sched *sched;          // per replica
     unsigned long long *sweep;     // next sweep index (all replicas)
     unsigned long long *counters;  // [n_rep][kRepSlots][kNumCounters]
@@ -312,6 +323,26 @@ __device__ __forceinline__ int stencil_cell(const Rep &R, int t, int cx, int cy,
         dx = ox - 1; dy = oy - 1; dz = oz - 1;
     }
     return R.cell_off + nx + nc * (ny + nc * nz);
+}
+
+// Stencil cell number t of (cx, cy, cz) from the cell count per side and the
+// replica's first cell only (no Rep access).
+__device__ __forceinline__ int stencil_cell_nc(int nc, int cell_off, int t, int cx, int cy, int cz,
+                                               int &dx, int &dy, int &dz)
+{
+    const int ns = nc == 2 ? 2 : 3;
+    const int ox = t % ns, oy = (t / ns) % ns, oz = t / (ns * ns);
+    int nx, ny, nz;
+    if (nc == 2) {
+        nx = ox; ny = oy; nz = oz;
+        dx = ox - cx; dy = oy - cy; dz = oz - cz;
+    } else {
+        nx = (cx + ox - 1 + nc) % nc;
+        ny = (cy + oy - 1 + nc) % nc;
+        nz = (cz + oz - 1 + nc) % nc;
+        dx = ox - 1; dy = oy - 1; dz = oz - 1;
+    }
+    return cell_off + nx + nc * (ny + nc * nz);
 }
 
 __device__ __forceinline__ void flush_counters(const SimParams &P, int r,

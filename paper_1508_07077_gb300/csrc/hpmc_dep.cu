@@ -75,6 +75,13 @@ struct hpmc_ctx {
     float4 *d_lens_move = nullptr;
     double4 *d_prop_pos = nullptr, *d_prop_quat = nullptr;
     int lens_cap = 0;
+    int4 *d_task = nullptr;       // FP32 sphere form: per-phase cell of every CTA
+    int task_alloc = -1;
+    int *d_binpos = nullptr;      // bin slot of every colloid
+    int4 *d_hdr_bin = nullptr;    // lens header and displacement per bin slot
+    float4 *d_mv_bin = nullptr;
+    float4 *d_lens_bin = nullptr; // first lens points per bin slot
+    long long aux_alloc = -1;
     Rep *d_reps = nullptr;
     int *d_rep_of = nullptr;
     int *d_cta_rep = nullptr;
@@ -337,6 +344,12 @@ SimParams make_params(hpmc_ctx *c)
     P.lens_move = c->d_lens_move;
     P.prop_pos = c->d_prop_pos;
     P.prop_quat = c->d_prop_quat;
+    P.n_cta = c->n_cta;
+    P.task = c->d_task;
+    P.binpos = c->d_binpos;
+    P.hdr_bin = c->d_hdr_bin;
+    P.mv_bin = c->d_mv_bin;
+    P.lens_bin = c->d_lens_bin;
     P.sched = c->d_sched;
     P.sweep = c->d_sweep;
     P.counters = c->d_counters;
@@ -350,7 +363,8 @@ SimParams make_params(hpmc_ctx *c)
 int enqueue_cells(hpmc_ctx *c, cudaStream_t s)
 {
     SimParams P = make_params(c);
-    k_cells_bin<<<(c->n_total + 255) / 256, 256, 0, s>>>(P);
+    const int threads = c->d_task ? std::max(c->n_total, 8 * c->n_cta) : c->n_total;
+    k_cells_bin<<<(threads + 255) / 256, 256, 0, s>>>(P);
     CK(cudaGetLastError());
     return HPMC_OK;
 }
@@ -568,6 +582,35 @@ int prepare(hpmc_ctx *c)
                       cudaMemcpyHostToDevice));
     }
     // lens lists hold at most N_p <= nF points each: capacity nF_max, no overflow
+    if (c->precision == HPMC_FP32_RECHECK && p.shape == HPMC_SPHERE) {
+        // task table, bin positions, per-slot lens headers and displacements
+        if (cta_off != c->task_alloc) {
+            cudaFree(c->d_task);
+            c->d_task = nullptr;
+            c->task_alloc = -1;
+            CK(cudaMalloc(&c->d_task, sizeof(int4) * 8 * (size_t)cta_off));
+            c->task_alloc = cta_off;
+        }
+        if (!c->d_binpos) CK(cudaMalloc(&c->d_binpos, sizeof(int) * (size_t)c->n_total));
+        const long long slots = (long long)cell_off * cap;
+        if (slots != c->aux_alloc) {
+            cudaFree(c->d_hdr_bin);
+            cudaFree(c->d_mv_bin);
+            cudaFree(c->d_lens_bin);
+            c->d_hdr_bin = nullptr;
+            c->d_mv_bin = nullptr;
+            c->d_lens_bin = nullptr;
+            c->aux_alloc = -1;
+            CK(cudaMalloc(&c->d_hdr_bin, sizeof(int4) * (size_t)slots));
+            CK(cudaMalloc(&c->d_mv_bin, sizeof(float4) * (size_t)slots));
+            CK(cudaMalloc(&c->d_lens_bin, sizeof(float4) * kLensInline * (size_t)slots));
+            c->aux_alloc = slots;
+        }
+    } else if (c->d_task) {
+        cudaFree(c->d_task);
+        c->d_task = nullptr;
+        c->task_alloc = -1;
+    }
     if (c->precision == HPMC_FP32_RECHECK && p.shape != HPMC_SPHERE) {
         if (!c->d_prop_pos) CK(cudaMalloc(&c->d_prop_pos, sizeof(double4) * (size_t)c->n_total));
         if (!c->d_prop_quat) CK(cudaMalloc(&c->d_prop_quat, sizeof(double4) * (size_t)c->n_total));
@@ -1325,6 +1368,11 @@ void hpmc_destroy(hpmc_ctx *c)
     cudaFree(c->d_lens_move);
     cudaFree(c->d_prop_pos);
     cudaFree(c->d_prop_quat);
+    cudaFree(c->d_task);
+    cudaFree(c->d_binpos);
+    cudaFree(c->d_hdr_bin);
+    cudaFree(c->d_mv_bin);
+    cudaFree(c->d_lens_bin);
     cudaFree(c->d_reps);
     cudaFree(c->d_rep_of);
     cudaFree(c->d_cta_rep);

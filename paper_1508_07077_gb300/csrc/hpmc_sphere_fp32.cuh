@@ -324,7 +324,10 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
     const float D0 = coord32(wm.x, R.d_max32);
     const float D1 = coord32(wm.y, R.d_max32);
     const float D2 = coord32(wm.z, R.d_max32);
-    if (lane == 0) P.lens_move[i] = make_float4(D0, D1, D2, 0.0f);
+    // header and displacement go to the colloid's bin slot, where the colour
+    // phase reads them together with the cell list
+    const int bp = P.binpos[g];
+    if (lane == 0 && bp >= 0) P.mv_bin[bp] = make_float4(D0, D1, D2, 0.0f);
     if (!R.has_dep) return;
     {
         // the same FP32 expression the colour phase uses for the cell-exit test
@@ -333,7 +336,7 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
         const float mc = R.m_cell, wc = R.w32;
         if (rn0 < -mc || rn0 > wc + mc || rn1 < -mc || rn1 > wc + mc || rn2 < -mc ||
             rn2 > wc + mc) {
-            if (lane == 0) P.lens_hdr[i] = make_int4(0, 0, 0, 0);
+            if (lane == 0 && bp >= 0) P.hdr_bin[bp] = make_int4(0, 0, 0, 0);
             return;
         }
     }
@@ -384,14 +387,17 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
         const bool lens = dep && to == 0;
         const unsigned lb = __ballot_sync(kFull, lens);
         const int slot = m + __popc(lb & lt);
-        if (lens && slot < P.lens_cap)
-            out[slot] = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
+        if (lens && slot < P.lens_cap) {
+            const float4 Lp = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
+            out[slot] = Lp;
+            if (slot < kLensInline && bp >= 0) P.lens_bin[(size_t)bp * kLensInline + slot] = Lp;
+        }
         m += __popc(lb);
         k0 += __popc(bal);
         t0 += 32u;
     }
     if (lane == 0) {
-        P.lens_hdr[i] = make_int4(n_p, min(k0, n_p), min(m, P.lens_cap), 0);
+        if (bp >= 0) P.hdr_bin[bp] = make_int4(n_p, min(k0, n_p), min(m, P.lens_cap), 0);
         if (m > P.lens_cap) atomicCAS(P.err, kErrNone, kErrCandCap);
     }
     rck = __reduce_add_sync(kFull, rck);
@@ -432,8 +438,9 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 24)
     __shared__ float4 s_cpos[kMaxCand];  // candidates relative to this cell's origin; index in .w
     __shared__ float4 s_nb[kMaxNb];      // neighbours relative to the new position; index in .w
     __shared__ float4 s_lens[kMaxLensCTA];
-    __shared__ int4 s_hdr[CAP];
+    __shared__ int4 s_hdr[CAP];                  // own cell, bin order
     __shared__ float4 s_mv[CAP];
+    __shared__ float4 s_lin[2][kLensInline];     // inline lens points of bin slots 0, 1
     __shared__ int s_tmp_i[CAP], s_tmp_slot[CAP];
     __shared__ int s_own[CAP], s_own_slot[CAP], s_own_bin[CAP];
     __shared__ int s_loff[CAP], s_accl[CAP];
@@ -448,48 +455,103 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 24)
         sh.f = s_dyn;
         sh.k = (int *)(s_dyn + nthr);
     }
-    const int r = P.cta_rep[blockIdx.x];
+    // the CTA's cell (task table of this sweep): everything needed to start
+    // loading the stencil without the replica record
+    const int4 tk = P.task[(size_t)phase * P.n_cta + blockIdx.x];
+    const int cell = tk.x, r = tk.y;
+    const int cx = tk.z & 1023, cy = (tk.z >> 10) & 1023, cz = tk.z >> 20;
+    const int nc = tk.w & 0xFFFF, par = tk.w >> 16;
+    const int ns = nc == 2 ? 2 : 3, n_st = ns * ns * ns;
+    const int t_own = ns == 3 ? 13 : cx + 2 * cy + 4 * cz;
+    const int cell_off = cell - (cx + nc * (cy + nc * cz));
+    const int *count = P.count[par];
+    // the replica's FP32 parameters, loaded now so that their latency overlaps
+    // the stencil loads below
     const Rep &R = P.reps[r];
-    const Sched *S = P.sched + r;
+    const float w32 = R.w32, L32 = R.L32, half_L32 = R.half_L32, m_r2 = R.m_r2,
+                m_cell = R.m_cell, nb_cut2 = R.nb_cut2_32, T_dep = R.T_dep32,
+                T_contact = R.T_contact32;
+    const int has_dep = R.has_dep;
     if (phase == 7 && blockIdx.x == 0 && tid == 0) atomicAdd(P.sweep, 1ull);
-    const uint32_t sweep = S->sweep;
-    const CellTask T = cell_task(P, R, r, phase);
-    clear_next(P, sweep, T.cell);
-    const int n_own = min(T.n_own, P.cap);
-    if (n_own == 0) return;
-    const int cx = T.cx, cy = T.cy, cz = T.cz;
+    if (tid == 0) P.count[par ^ 1][cell] = 0;   // this cell's population of the next sweep
 
-    // neighbourhood: every colloid of the (deduplicated) 27-cell stencil,
-    // relative to this cell's origin; the cell's own members noted on the way
-    if (tid == 0) {
-        s_ncand = 0;
-        s_nacc = 0;
-    }
-    cta_sync<WARP>();
-    if (tid < R.n_stencil * R.n_stencil * R.n_stencil) {
-        int dx, dy, dz;
-        const int c = stencil_cell(R, tid, cx, cy, cz, dx, dy, dz);
-        const float fx = (float)dx * R.w32, fy = (float)dy * R.w32, fz = (float)dz * R.w32;
-        const int m = c == T.cell ? n_own : min(T.count[c], P.cap);
-        const float4 *bin = P.bins + (size_t)c * P.cap;
-        for (int s = 0; s < m; ++s) {
-            const float4 e = bin[s];
-            const int slot = atomicAdd(&s_ncand, 1);
-            if (slot < kMaxCand) s_cpos[slot] = make_float4(fx + e.x, fy + e.y, fz + e.z, e.w);
-            if (c == T.cell) {
-                s_tmp_i[s] = __float_as_int(e.w);
-                s_tmp_slot[s] = slot;
+    // one round of loads: every stencil cell's population and first two bin
+    // entries (speculatively: most cells hold at most two colloids), and for
+    // the own cell the displacements, headers and inline lens points of
+    // those two slots
+    int c_nb = 0, m_nb = 0, dx = 0, dy = 0, dz = 0;
+    float4 e_a = make_float4(0.f, 0.f, 0.f, 0.f), e_b = e_a;
+    if (tid < n_st) {
+        c_nb = stencil_cell_nc(nc, cell_off, tid, cx, cy, cz, dx, dy, dz);
+        const size_t b0 = (size_t)c_nb * P.cap;
+        m_nb = count[c_nb];
+        e_a = P.bins[b0];
+        e_b = P.bins[b0 + 1];
+        if (tid == t_own) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                s_mv[s] = P.mv_bin[b0 + s];
+                s_hdr[s] = P.hdr_bin[b0 + s];
+#pragma unroll
+                for (int j = 0; j < kLensInline; ++j)
+                    s_lin[s][j] = P.lens_bin[(b0 + s) * kLensInline + j];
             }
         }
+        m_nb = min(m_nb, P.cap);
     }
-    cta_sync<WARP>();
-    const int M = s_ncand;
+    const Sched *S = P.sched + r;
+    int n_own = 0, M = 0, base = 0;
+    if (tid < 32) {
+        n_own = __shfl_sync(kFull, m_nb, t_own);
+        int incl = m_nb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        base = incl - m_nb;
+        M = __shfl_sync(kFull, incl, 31);
+        if (!WARP && tid == 0) {
+            s_ncand = M;
+            s_nacc = n_own;
+        }
+    }
+    if (!WARP) {
+        __syncthreads();
+        M = s_ncand;
+        n_own = s_nacc;
+        __syncthreads();
+    }
+    if (n_own == 0) return;
     if (M > kMaxCand) {
         if (tid == 0) atomicCAS(P.err, kErrNone, kErrCandCap);
         return;
     }
-    // the cell's colloids in ascending index (the order they move in), their
-    // displacements and depletant headers
+    const uint32_t sweep = S->sweep;
+    if (tid == 0) s_nacc = 0;
+    // candidates relative to this cell's origin (entries beyond the first two
+    // in a second, rarely needed, round)
+    if (tid < n_st) {
+        const float fx = (float)dx * w32, fy = (float)dy * w32, fz = (float)dz * w32;
+        const bool own = tid == t_own;
+        const size_t b0 = (size_t)c_nb * P.cap;
+        for (int s = 0; s < m_nb; ++s) {
+            const float4 e = s == 0 ? e_a : (s == 1 ? e_b : P.bins[b0 + s]);
+            const int slot = base + s;
+            s_cpos[slot] = make_float4(fx + e.x, fy + e.y, fz + e.z, e.w);
+            if (own) {
+                s_tmp_i[s] = __float_as_int(e.w);
+                s_tmp_slot[s] = slot;
+                if (s >= 2) {
+                    s_mv[s] = P.mv_bin[b0 + s];
+                    s_hdr[s] = P.hdr_bin[b0 + s];
+                }
+            }
+        }
+    }
+    cta_sync<WARP>();
+    // the cell's colloids in ascending index (the order they move in), and
+    // where each one's lens points go in shared memory (bin order)
     for (int q = tid; q < n_own; q += nthr) {
         const int v = s_tmp_i[q];
         int rk = 0;
@@ -497,30 +559,35 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 24)
         s_own[rk] = v;
         s_own_slot[rk] = s_tmp_slot[q];
         s_own_bin[rk] = q;
-        s_mv[rk] = P.lens_move[v];
-        if (R.has_dep) s_hdr[rk] = P.lens_hdr[v];
     }
-    cta_sync<WARP>();
-    // and their lens points
-    if (R.has_dep) {
-        if (tid == 0) {
-            int off = 0;
-            for (int q = 0; q < n_own; ++q) {
-                const int n = s_hdr[q].z;
-                if (n > 0 && off + n <= kMaxLensCTA) {
-                    s_loff[q] = off;
-                    off += n;
-                } else {
-                    s_loff[q] = -1;
-                }
+    if (has_dep && tid == 0) {
+        int off = 0;
+        for (int q = 0; q < n_own; ++q) {
+            const int n = s_hdr[q].z;
+            if (n > 0 && off + n <= kMaxLensCTA) {
+                s_loff[q] = off;
+                off += n;
+            } else {
+                s_loff[q] = -1;
             }
         }
-        cta_sync<WARP>();
+    }
+    cta_sync<WARP>();
+    // lens points: the first kLensInline of slots 0 and 1 came with the bin
+    // entries; other short lists are beside their bin slots, long ones in the
+    // lens array
+    if (has_dep) {
         for (int q = 0; q < n_own; ++q) {
             const int n = s_hdr[q].z, o = s_loff[q];
             if (o < 0) continue;
-            const float4 *src = P.lens + (size_t)s_own[q] * P.lens_cap;
-            for (int m = tid; m < n; m += nthr) s_lens[o + m] = src[m];
+            if (n <= kLensInline && q < 2) {
+                if (tid < n) s_lens[o + tid] = s_lin[q][tid];
+            } else if (n <= kLensInline) {
+                if (tid < n) s_lens[o + tid] = P.lens_bin[((size_t)cell * P.cap + q) * kLensInline + tid];
+            } else {
+                const float4 *src = P.lens + (size_t)s_tmp_i[q] * P.lens_cap;
+                for (int m = tid; m < n; m += nthr) s_lens[o + m] = src[m];
+            }
         }
         cta_sync<WARP>();
     }
@@ -533,10 +600,11 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 24)
         const int i = s_own[q];
         const int nacc = s_nacc;
         const float4 ri = s_cpos[s_own_slot[q]];
-        const float4 mv = s_mv[q];
+        const int qb = s_own_bin[q];
+        const float4 mv = s_mv[qb];
         const float rn0 = ri.x + mv.x, rn1 = ri.y + mv.y, rn2 = ri.z + mv.z;
         // a3: cell-exit check with margin (exact when within it)
-        const float mc = R.m_cell, wc = R.w32;
+        const float mc = m_cell, wc = w32;
         const bool out = rn0 < -mc || rn0 > wc + mc || rn1 < -mc || rn1 > wc + mc ||
                          rn2 < -mc || rn2 > wc + mc;
         const bool edge = rn0 <= mc || rn0 >= wc - mc || rn1 <= mc || rn1 >= wc - mc ||
@@ -571,11 +639,11 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 24)
                     d0 = cp.x - rn0;
                     d1 = cp.y - rn1;
                     d2 = cp.z - rn2;
-                    if (d0 > R.half_L32) d0 -= R.L32; else if (d0 < -R.half_L32) d0 += R.L32;
-                    if (d1 > R.half_L32) d1 -= R.L32; else if (d1 < -R.half_L32) d1 += R.L32;
-                    if (d2 > R.half_L32) d2 -= R.L32; else if (d2 < -R.half_L32) d2 += R.L32;
+                    if (d0 > half_L32) d0 -= L32; else if (d0 < -half_L32) d0 += L32;
+                    if (d1 > half_L32) d1 -= L32; else if (d1 < -half_L32) d1 += L32;
+                    if (d2 > half_L32) d2 -= L32; else if (d2 < -half_L32) d2 += L32;
                     r2 = norm2f(d0, d1, d2);
-                    t = tri(r2, R.T_contact32, R.m_r2);
+                    t = tri(r2, T_contact, m_r2);
                 }
             }
             const bool unsure = t == -1;
@@ -586,7 +654,7 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 24)
                 }
             }
             if (t == 1) ov = 1;
-            const bool take = pj >= 0 && r2 < R.nb_cut2_32;
+            const bool take = pj >= 0 && r2 < nb_cut2;
             if (WARP) {
                 const unsigned b = __ballot_sync(kFull, take);
                 const int slot = nnb + __popc(b & lt);
@@ -608,16 +676,16 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 24)
         }
 
         bool accept = true;
-        if (R.has_dep) {
+        if (has_dep) {
             // a5: N_p and the lens points come from the lens kernel
-            const int4 hd = s_hdr[q];
+            const int4 hd = s_hdr[qb];
             const int n_p = hd.x;
             c_drawn += (unsigned long long)n_p;
             DepOutcome o = {1.0, 0, 0, 0u, 0u, 0u, 0u, 0u, 0u};
             // a6: the lens points in depletant order; one free of every
             // neighbour blocks the move (or enters the CB weight)
             const int n_lens = hd.z;
-            const float4 *lens = s_loff[q] >= 0 ? s_lens + s_loff[q]
+            const float4 *lens = s_loff[qb] >= 0 ? s_lens + s_loff[qb]
                                                 : P.lens + (size_t)i * P.lens_cap;
             if (!CB && !WARP) {
                 if (tid == 0) sh.kmin = 0x7FFFFFFF;
@@ -636,7 +704,7 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 24)
                     for (int b = 0; b < nnb; ++b) {
                         const float4 d = s_nb[b];
                         const int tn = tri(norm2f(Lm.x - d.x, Lm.y - d.y, Lm.z - d.z),
-                                           R.T_dep32, R.m_r2);
+                                           T_dep, m_r2);
                         if (tn == 1) {
                             hit = true;
                             break;
@@ -728,7 +796,7 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 24)
             if (tid == 0) {
                 const float4 rnew = make_float4(rn0, rn1, rn2, __int_as_float(i));
                 s_cpos[s_own_slot[q]] = rnew;
-                P.bins[(size_t)T.cell * P.cap + s_own_bin[q]] = rnew;
+                P.bins[(size_t)cell * P.cap + s_own_bin[q]] = rnew;
                 s_accl[nacc] = i;
                 s_nacc = nacc + 1;
             }
