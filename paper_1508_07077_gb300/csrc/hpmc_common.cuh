@@ -23,6 +23,10 @@ constexpr int kMaxCand = 256;        // colloids in a 27-cell neighbourhood (cap
 constexpr int kMaxThreads = 256;     // 8 warps per colloid at most
 constexpr int kMaxCellCap = 64;      // colloids per cell bin, largest capacity (checked from the packing bound)
 constexpr int kSmallCellCap = 32;    // capacity of the usual cells (width near d_colloid + d_depletant)
+constexpr int kTinyCellCap = 16;     // spheres in cells below ~1.24 diameters (packing bound < 16)
+// candidate capacity of a 27-cell neighbourhood in the FP32 sphere phase
+// kernel: smaller for the smallest cells, to keep more CTAs resident
+__host__ __device__ constexpr int cand_cap(int cap) { return cap <= kTinyCellCap ? 192 : kMaxCand; }
 constexpr int kRepSlots = 16;        // per replica, counters are spread over slots (fewer hot atomics)
 constexpr int kNumCounters = 16;
 constexpr int kLensInline = 4;       // lens points kept beside each bin slot (FP32 sphere form)

@@ -377,13 +377,16 @@ void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s
     bool cb = false;
     for (const RepHost &h : c->reps) cb = cb || h.n_trial > 0;
     if (c->precision == HPMC_FP32_RECHECK && c->prm.shape != HPMC_SPHERE) {
-        const bool warp = threads == 32;
-        if (cb) {
-            if (warp) k_phase_aniso_fp32<true, true, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
-            else k_phase_aniso_fp32<true, false, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
-        } else {
-            if (warp) k_phase_aniso_fp32<false, true, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
-            else k_phase_aniso_fp32<false, false, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
+        // the anisotropic shapes' packing bound always selects a capacity >= 32
+        if constexpr (CAP >= kSmallCellCap) {
+            const bool warp = threads == 32;
+            if (cb) {
+                if (warp) k_phase_aniso_fp32<true, true, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
+                else k_phase_aniso_fp32<true, false, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
+            } else {
+                if (warp) k_phase_aniso_fp32<false, true, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
+                else k_phase_aniso_fp32<false, false, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
+            }
         }
     } else if (c->precision == HPMC_FP32_RECHECK) {
         const bool warp = threads == 32;
@@ -397,13 +400,15 @@ void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s
     } else if (c->prm.shape == HPMC_SPHERE) {
         k_phase_sphere_fp64<CAP><<<c->n_cta, threads, 0, s>>>(P, phase);
     } else {
-        k_phase_aniso_fp64<CAP><<<c->n_cta, threads, 0, s>>>(P, phase);
+        if constexpr (CAP >= kSmallCellCap)
+            k_phase_aniso_fp64<CAP><<<c->n_cta, threads, 0, s>>>(P, phase);
     }
 }
 
 void launch_phase(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
 {
-    if (c->cap == kSmallCellCap) launch_phase_cap<kSmallCellCap>(c, P, phase, s);
+    if (c->cap == kTinyCellCap) launch_phase_cap<kTinyCellCap>(c, P, phase, s);
+    else if (c->cap == kSmallCellCap) launch_phase_cap<kSmallCellCap>(c, P, phase, s);
     else launch_phase_cap<kMaxCellCap>(c, P, phase, s);
 }
 
@@ -546,9 +551,10 @@ int prepare(hpmc_ctx *c)
         cta_off += h * h * h;
         if (R.nF > nF_max) nF_max = R.nF;
     }
-    int cap = kSmallCellCap;
-    for (const Rep &R : rd)
-        if (R.pad_cell_bound >= (double)kSmallCellCap) cap = kMaxCellCap;
+    double bound = 0.0;
+    for (const Rep &R : rd) bound = std::fmax(bound, R.pad_cell_bound);
+    int cap = bound < (double)kTinyCellCap && p.shape == HPMC_SPHERE ? kTinyCellCap
+              : (bound < (double)kSmallCellCap ? kSmallCellCap : kMaxCellCap);
     DeviceGuard g(c->device);
     if (cap != c->cap) c->cells_alloc = -2;  // force re-allocation of the bins
     c->cap = cap;

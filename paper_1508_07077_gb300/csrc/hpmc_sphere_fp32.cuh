@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
     if (lane == 0 && rck) count_one(P, r, kRechecks, (unsigned long long)rck);
 }
 
-constexpr int kMaxLensCTA = 128;   // lens points of one cell staged in shared memory (more: read
+constexpr int kMaxLensCTA = 64;    // lens points of one cell staged in shared memory (more: read
                                    // from global memory)
 constexpr int kMaxNb = 64;         // neighbours within reach of a depletant (hard spheres: <= ~27)
 
@@ -432,10 +432,10 @@ __device__ __forceinline__ bool cta_any(bool p)
 // CAP: capacity of a cell bin (the cell list's stride).
 // ---------------------------------------------------------------------------
 template <bool CB, bool WARP, int CAP>
-__global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 24) : 1)
+__global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32) : 1)
     k_phase_sphere_fp32(const __grid_constant__ SimParams P, int phase)
 {
-    __shared__ float4 s_cpos[kMaxCand];  // candidates relative to this cell's origin; index in .w
+    __shared__ float4 s_cpos[cand_cap(CAP)];  // candidates relative to this cell's origin; index in .w
     __shared__ float4 s_nb[kMaxNb];      // neighbours relative to the new position; index in .w
     __shared__ float4 s_lens[kMaxLensCTA];
     __shared__ int4 s_hdr[CAP];                  // own cell, bin order
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 24)
         __syncthreads();
     }
     if (n_own == 0) return;
-    if (M > kMaxCand) {
+    if (M > cand_cap(CAP)) {
         if (tid == 0) atomicCAS(P.err, kErrNone, kErrCandCap);
         return;
     }
