@@ -329,6 +329,13 @@ __device__ __forceinline__ int stencil_cell(const Rep &R, int t, int cx, int cy,
     return R.cell_off + nx + nc * (ny + nc * nz);
 }
 
+// Programmatic dependent launch (a kernel launched with programmatic stream
+// serialization may start before its predecessor finishes): let the next
+// kernel in the stream launch early, and wait for the predecessor's
+// completion (and the visibility of its writes) before touching its results.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Stencil cell number t of (cx, cy, cz) from the cell count per side and the
 // replica's first cell only (no Rep access).
 __device__ __forceinline__ int stencil_cell_nc(int nc, int cell_off, int t, int cx, int cy, int cz,

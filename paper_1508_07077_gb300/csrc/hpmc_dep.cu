@@ -369,6 +369,25 @@ int enqueue_cells(hpmc_ctx *c, cudaStream_t s)
     return HPMC_OK;
 }
 
+// Launch with programmatic stream serialization (the kernel may start while
+// its predecessor in the stream drains; it orders itself with pdl_wait()).
+template <typename K>
+void launch_pdl(K kernel, int grid, int block, size_t dyn, cudaStream_t s, const SimParams &P,
+                int phase)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, P, phase);
+}
+
 template <int CAP>
 void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
 {
@@ -391,11 +410,11 @@ void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s
     } else if (c->precision == HPMC_FP32_RECHECK) {
         const bool warp = threads == 32;
         if (cb) {
-            if (warp) k_phase_sphere_fp32<true, true, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
-            else k_phase_sphere_fp32<true, false, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
+            if (warp) launch_pdl(k_phase_sphere_fp32<true, true, CAP>, c->n_cta, threads, dyn, s, P, phase);
+            else launch_pdl(k_phase_sphere_fp32<true, false, CAP>, c->n_cta, threads, dyn, s, P, phase);
         } else {
-            if (warp) k_phase_sphere_fp32<false, true, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
-            else k_phase_sphere_fp32<false, false, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
+            if (warp) launch_pdl(k_phase_sphere_fp32<false, true, CAP>, c->n_cta, threads, dyn, s, P, phase);
+            else launch_pdl(k_phase_sphere_fp32<false, false, CAP>, c->n_cta, threads, dyn, s, P, phase);
         }
     } else if (c->prm.shape == HPMC_SPHERE) {
         k_phase_sphere_fp64<CAP><<<c->n_cta, threads, 0, s>>>(P, phase);

@@ -455,6 +455,12 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
         sh.f = s_dyn;
         sh.k = (int *)(s_dyn + nthr);
     }
+    // The phases are launched with programmatic dependent launch: the next
+    // phase's CTAs may start while this one drains.  Everything read before
+    // pdl_wait() is fixed for the whole sweep (task table, populations, replica
+    // record, lens headers, displacements and lens points); positions (bins,
+    // FP64 state) are read and written only after it.
+    pdl_trigger();
     // the CTA's cell (task table of this sweep): everything needed to start
     // loading the stencil without the replica record
     const int4 tk = P.task[(size_t)phase * P.n_cta + blockIdx.x];
@@ -475,18 +481,15 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
     if (phase == 7 && blockIdx.x == 0 && tid == 0) atomicAdd(P.sweep, 1ull);
     if (tid == 0) P.count[par ^ 1][cell] = 0;   // this cell's population of the next sweep
 
-    // one round of loads: every stencil cell's population and first two bin
-    // entries (speculatively: most cells hold at most two colloids), and for
-    // the own cell the displacements, headers and inline lens points of
-    // those two slots
+    // one round of loads: every stencil cell's population, and for the own
+    // cell the displacements, headers and inline lens points of its first two
+    // slots (speculatively: most cells hold at most two colloids)
     int c_nb = 0, m_nb = 0, dx = 0, dy = 0, dz = 0;
     float4 e_a = make_float4(0.f, 0.f, 0.f, 0.f), e_b = e_a;
     if (tid < n_st) {
         c_nb = stencil_cell_nc(nc, cell_off, tid, cx, cy, cz, dx, dy, dz);
         const size_t b0 = (size_t)c_nb * P.cap;
         m_nb = count[c_nb];
-        e_a = P.bins[b0];
-        e_b = P.bins[b0 + 1];
         if (tid == t_own) {
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
@@ -528,6 +531,13 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
         return;
     }
     const uint32_t sweep = S->sweep;
+    // the previous phase's moves are visible from here on
+    pdl_wait();
+    if (tid < n_st) {
+        const size_t b0 = (size_t)c_nb * P.cap;
+        e_a = P.bins[b0];
+        e_b = P.bins[b0 + 1];
+    }
     if (tid == 0) s_nacc = 0;
     // candidates relative to this cell's origin (entries beyond the first two
     // in a second, rarely needed, round)
