@@ -35,6 +35,9 @@ __device__ __forceinline__ int4 phase_task(const Rep &R, int r, const int perm[8
 // phases start from their cell without recomputing the schedule.
 __global__ void k_cells_bin(const __grid_constant__ SimParams P)
 {
+    // the lens kernel behind this one may start at once (it waits for this
+    // kernel's results only where it files them)
+    pdl_trigger();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (P.task && g < 8 * P.n_cta) {
         const int phase = g / P.n_cta, a = g - phase * P.n_cta;

@@ -388,6 +388,21 @@ void launch_pdl(K kernel, int grid, int block, size_t dyn, cudaStream_t s, const
     cudaLaunchKernelEx(&cfg, kernel, P, phase);
 }
 
+template <typename K>
+void launch_pdl1(K kernel, int grid, int block, cudaStream_t s, const SimParams &P)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, P);
+}
+
 template <int CAP>
 void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
 {
@@ -435,7 +450,7 @@ void launch_lens(hpmc_ctx *c, const SimParams &P, cudaStream_t s)
 {
     if (c->precision != HPMC_FP32_RECHECK) return;
     if (c->prm.shape == HPMC_SPHERE) {
-        k_lens_sphere_fp32<<<(c->n_total + 3) / 4, 128, 0, s>>>(P);
+        launch_pdl1(k_lens_sphere_fp32, (c->n_total + 3) / 4, 128, s, P);
     } else {
         k_propose_aniso<<<(c->n_total + 127) / 128, 128, 0, s>>>(P);
         k_lens_aniso_fp32<<<(c->n_total + 3) / 4, 128, 0, s>>>(P);

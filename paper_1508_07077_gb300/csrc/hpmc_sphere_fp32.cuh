@@ -315,30 +315,26 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
     const int lane = threadIdx.x & 31;
     const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (g >= P.n_total) return;
+    // Launched with programmatic dependent launch behind the cell-list kernel:
+    // the depletant work below needs nothing that kernel writes (the sweep
+    // index is the counter the previous sweep advanced); only the bin slot
+    // the results are filed under does, and it is read after pdl_wait().
+    // (This kernel does not release its own successor early: the colour
+    // phases read its results before they wait.)
     const int r = P.rep_of[g];
     const Rep &R = P.reps[r];
     const int i = g;   // global colloid index (the helpers take global indices)
-    const uint32_t sweep = P.sched[r].sweep;
+    const uint32_t sweep = (uint32_t)(*P.sweep);
     const uint32_t tag = (uint32_t)(g - R.off);
     const uint4 wm = draw(R.key0, R.key1, sweep, tag, kPMove, 0, 0);
     const float D0 = coord32(wm.x, R.d_max32);
     const float D1 = coord32(wm.y, R.d_max32);
     const float D2 = coord32(wm.z, R.d_max32);
-    // header and displacement go to the colloid's bin slot, where the colour
-    // phase reads them together with the cell list
-    const int bp = P.binpos[g];
-    if (lane == 0 && bp >= 0) P.mv_bin[bp] = make_float4(D0, D1, D2, 0.0f);
-    if (!R.has_dep) return;
-    {
-        // the same FP32 expression the colour phase uses for the cell-exit test
-        const float4 ri = P.rel[i];
-        const float rn0 = ri.x + D0, rn1 = ri.y + D1, rn2 = ri.z + D2;
-        const float mc = R.m_cell, wc = R.w32;
-        if (rn0 < -mc || rn0 > wc + mc || rn1 < -mc || rn1 > wc + mc || rn2 < -mc ||
-            rn2 > wc + mc) {
-            if (lane == 0 && bp >= 0) P.hdr_bin[bp] = make_int4(0, 0, 0, 0);
-            return;
-        }
+    if (!R.has_dep) {
+        pdl_wait();
+        const int bp = P.binpos[g];
+        if (lane == 0 && bp >= 0) P.mv_bin[bp] = make_float4(D0, D1, D2, 0.0f);
+        return;
     }
     uint32_t rck = 0;
     const float o0 = -D0, o1 = -D1, o2 = -D2;
@@ -387,19 +383,25 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
         const bool lens = dep && to == 0;
         const unsigned lb = __ballot_sync(kFull, lens);
         const int slot = m + __popc(lb & lt);
-        if (lens && slot < P.lens_cap) {
-            const float4 Lp = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
-            out[slot] = Lp;
-            if (slot < kLensInline && bp >= 0) P.lens_bin[(size_t)bp * kLensInline + slot] = Lp;
-        }
+        if (lens && slot < P.lens_cap)
+            out[slot] = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
         m += __popc(lb);
         k0 += __popc(bal);
         t0 += 32u;
     }
-    if (lane == 0) {
-        if (bp >= 0) P.hdr_bin[bp] = make_int4(n_p, min(k0, n_p), min(m, P.lens_cap), 0);
-        if (m > P.lens_cap) atomicCAS(P.err, kErrNone, kErrCandCap);
+    // file the header, the displacement and the first lens points under the
+    // colloid's bin slot, where the colour phase reads them with the cell list
+    __syncwarp();
+    pdl_wait();
+    const int bp = P.binpos[g];
+    if (bp >= 0) {
+        if (lane == 0) {
+            P.mv_bin[bp] = make_float4(D0, D1, D2, 0.0f);
+            P.hdr_bin[bp] = make_int4(n_p, min(k0, n_p), min(m, P.lens_cap), 0);
+        }
+        if (lane < min(m, kLensInline)) P.lens_bin[(size_t)bp * kLensInline + lane] = out[lane];
     }
+    if (lane == 0 && m > P.lens_cap) atomicCAS(P.err, kErrNone, kErrCandCap);
     rck = __reduce_add_sync(kFull, rck);
     if (lane == 0 && rck) count_one(P, r, kRechecks, (unsigned long long)rck);
 }
