@@ -39,6 +39,7 @@ __global__ void k_cells_bin(const __grid_constant__ SimParams P)
     // kernel's results only where it files them)
     pdl_trigger();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P.cls_count && g < 32) P.cls_count[g] = 0;
     if (P.task && g < 8 * P.n_cta) {
         const int phase = g / P.n_cta, a = g - phase * P.n_cta;
         const int r = P.cta_rep[a];
@@ -77,6 +78,37 @@ __global__ void k_cells_bin(const __grid_constant__ SimParams P)
     else atomicCAS(P.err, kErrNone, kErrCellCap);
     if (P.binpos) P.binpos[g] = slot < P.cap ? c * P.cap + slot : -1;
     P.rel[g] = rl;
+}
+
+// Order every phase's tasks by the population of their cell, fullest first:
+// a phase lasts as long as its longest sequential chain of moves, so the long
+// chains should start first.  One thread per (phase, CTA) entry; positions
+// inside a class come from warp-aggregated atomics (any order is valid: the
+// cells of one colour are independent).
+__global__ void k_task_order(const __grid_constant__ SimParams P)
+{
+    pdl_trigger();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = t < 8 * P.n_cta;
+    int key = -1;
+    int4 tk = make_int4(0, 0, 0, 0);
+    if (valid) {
+        const int phase = t / P.n_cta;
+        tk = P.task[t];
+        const int n = P.count[tk.w >> 16][tk.x];
+        const int cls = n >= 3 ? 0 : (n == 2 ? 1 : (n == 1 ? 2 : 3));
+        key = phase * 4 + cls;
+    }
+    const unsigned peers = __match_any_sync(kFull, key);
+    const int leader = __ffs(peers) - 1;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (valid && lane == leader) base = atomicAdd(P.cls_count + key, __popc(peers));
+    base = __shfl_sync(kFull, base, leader);
+    if (valid) {
+        const int idx = base + __popc(peers & ((1u << lane) - 1u));
+        P.task_ord[(size_t)key * P.n_cta + idx] = tk;
+    }
 }
 
 // --- CSR layout ------------------------------------------------------------

@@ -156,6 +156,10 @@ struct SimParams {
     // binpos[g] = cell * cap + slot of colloid g; the lens kernel's header
     // (N_p, obtained, n_lens) and displacement of each bin slot
     int4 *task;
+    // the same tasks per phase in four classes of the cell's population
+    // (>= 3, 2, 1, 0: the longest chains first), class sizes in cls_count
+    int4 *task_ord;
+    int *cls_count;        // [8][4]
     int *binpos;
     int4 *hdr_bin;
     float4 *mv_bin;

@@ -76,6 +76,8 @@ struct hpmc_ctx {
     double4 *d_prop_pos = nullptr, *d_prop_quat = nullptr;
     int lens_cap = 0;
     int4 *d_task = nullptr;       // FP32 sphere form: per-phase cell of every CTA
+    int4 *d_task_ord = nullptr;   // and ordered by population class
+    int *d_cls_count = nullptr;
     int task_alloc = -1;
     int *d_binpos = nullptr;      // bin slot of every colloid
     int4 *d_hdr_bin = nullptr;    // lens header and displacement per bin slot
@@ -346,6 +348,8 @@ SimParams make_params(hpmc_ctx *c)
     P.prop_quat = c->d_prop_quat;
     P.n_cta = c->n_cta;
     P.task = c->d_task;
+    P.task_ord = c->d_task_ord;
+    P.cls_count = c->d_cls_count;
     P.binpos = c->d_binpos;
     P.hdr_bin = c->d_hdr_bin;
     P.mv_bin = c->d_mv_bin;
@@ -365,6 +369,7 @@ int enqueue_cells(hpmc_ctx *c, cudaStream_t s)
     SimParams P = make_params(c);
     const int threads = c->d_task ? std::max(c->n_total, 8 * c->n_cta) : c->n_total;
     k_cells_bin<<<(threads + 255) / 256, 256, 0, s>>>(P);
+    if (c->d_task) k_task_order<<<(8 * c->n_cta + 255) / 256, 256, 0, s>>>(P);
     CK(cudaGetLastError());
     return HPMC_OK;
 }
@@ -626,11 +631,15 @@ int prepare(hpmc_ctx *c)
         // task table, bin positions, per-slot lens headers and displacements
         if (cta_off != c->task_alloc) {
             cudaFree(c->d_task);
+            cudaFree(c->d_task_ord);
             c->d_task = nullptr;
+            c->d_task_ord = nullptr;
             c->task_alloc = -1;
             CK(cudaMalloc(&c->d_task, sizeof(int4) * 8 * (size_t)cta_off));
+            CK(cudaMalloc(&c->d_task_ord, sizeof(int4) * 32 * (size_t)cta_off));
             c->task_alloc = cta_off;
         }
+        if (!c->d_cls_count) CK(cudaMalloc(&c->d_cls_count, sizeof(int) * 32));
         if (!c->d_binpos) CK(cudaMalloc(&c->d_binpos, sizeof(int) * (size_t)c->n_total));
         const long long slots = (long long)cell_off * cap;
         if (slots != c->aux_alloc) {
@@ -648,7 +657,11 @@ int prepare(hpmc_ctx *c)
         }
     } else if (c->d_task) {
         cudaFree(c->d_task);
+        cudaFree(c->d_task_ord);
+        cudaFree(c->d_cls_count);
         c->d_task = nullptr;
+        c->d_task_ord = nullptr;
+        c->d_cls_count = nullptr;
         c->task_alloc = -1;
     }
     if (c->precision == HPMC_FP32_RECHECK && p.shape != HPMC_SPHERE) {
@@ -789,6 +802,9 @@ int read_err(hpmc_ctx *c, cudaStream_t s)
     int e = 0;
     CK(cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (e && getenv("HPMC_VERBOSE"))
+        fprintf(stderr, "hpmc: device error %d (%s)\n", e,
+                e == kErrCandCap ? "neighbourhood or lens capacity" : "cell bin capacity");
     return e ? HPMC_ERR_DEVICE : HPMC_OK;
 }
 
@@ -1409,6 +1425,8 @@ void hpmc_destroy(hpmc_ctx *c)
     cudaFree(c->d_prop_pos);
     cudaFree(c->d_prop_quat);
     cudaFree(c->d_task);
+    cudaFree(c->d_task_ord);
+    cudaFree(c->d_cls_count);
     cudaFree(c->d_binpos);
     cudaFree(c->d_hdr_bin);
     cudaFree(c->d_mv_bin);

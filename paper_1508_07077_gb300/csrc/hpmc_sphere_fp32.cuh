@@ -463,12 +463,34 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
     // record, lens headers, displacements and lens points); positions (bins,
     // FP64 state) are read and written only after it.
     pdl_trigger();
-    // the CTA's cell (task table of this sweep): everything needed to start
-    // loading the stencil without the replica record
-    const int4 tk = P.task[(size_t)phase * P.n_cta + blockIdx.x];
+    if (phase == 7 && blockIdx.x == 0 && tid == 0) atomicAdd(P.sweep, 1ull);
+    // the CTA's cell (task table of this sweep, fullest cells first):
+    // everything needed to start loading the stencil without the replica
+    // record
+    int cls = 0, idx = blockIdx.x;
+    {
+        const int4 cc = reinterpret_cast<const int4 *>(P.cls_count)[phase];
+        if (idx >= cc.x) {
+            idx -= cc.x;
+            cls = 1;
+            if (idx >= cc.y) {
+                idx -= cc.y;
+                cls = 2;
+                if (idx >= cc.z) {
+                    idx -= cc.z;
+                    cls = 3;
+                }
+            }
+        }
+    }
+    const int4 tk = P.task_ord[(size_t)(phase * 4 + cls) * P.n_cta + idx];
     const int cell = tk.x, r = tk.y;
     const int cx = tk.z & 1023, cy = (tk.z >> 10) & 1023, cz = tk.z >> 20;
     const int nc = tk.w & 0xFFFF, par = tk.w >> 16;
+    if (cls == 3) {               // an empty cell: only its next-sweep population
+        if (tid == 0) P.count[par ^ 1][cell] = 0;
+        return;
+    }
     const int ns = nc == 2 ? 2 : 3, n_st = ns * ns * ns;
     const int t_own = ns == 3 ? 13 : cx + 2 * cy + 4 * cz;
     const int cell_off = cell - (cx + nc * (cy + nc * cz));
@@ -480,7 +502,6 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
                 m_cell = R.m_cell, nb_cut2 = R.nb_cut2_32, T_dep = R.T_dep32,
                 T_contact = R.T_contact32;
     const int has_dep = R.has_dep;
-    if (phase == 7 && blockIdx.x == 0 && tid == 0) atomicAdd(P.sweep, 1ull);
     if (tid == 0) P.count[par ^ 1][cell] = 0;   // this cell's population of the next sweep
 
     // one round of loads: every stencil cell's population, and for the own
