@@ -61,6 +61,35 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+
+// Philox4x32-10 with the ten round keys of (k0, k1) computed once: the hot
+// depletant loops draw many counters under one key.
+struct RoundKeys {
+    uint32_t a[10], b[10];
+};
+__device__ __forceinline__ RoundKeys round_keys(uint32_t k0, uint32_t k1)
+{
+    RoundKeys K;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        K.a[r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        K.b[r] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    return K;
+}
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const RoundKeys &K)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ K.a[r], lo1, hi0 ^ c.w ^ K.b[r], lo0);
+    }
+    return c;
+}
+
 __device__ __forceinline__ uint4 draw(uint32_t k0, uint32_t k1, uint32_t sweep,
                                       uint32_t stream, uint32_t purpose,
                                       uint32_t sub, uint32_t t)

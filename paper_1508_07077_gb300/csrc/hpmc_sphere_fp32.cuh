@@ -341,6 +341,7 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
     const uint4 wp = draw(R.key0, R.key1, sweep, tag, kPPoisson, 0, 0);
     const int n_p = poisson_count(P.T + R.t_off, R.nF, u53_int(wp.x, wp.y), lane);
     const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
+    const RoundKeys K = round_keys(R.key0, R.key1);
     float4 *out = P.lens + (size_t)g * P.lens_cap;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t t0 = 0;
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant_
         float e0 = 0.f, e1 = 0.f, e2 = 0.f;
         int in = 0;
         if (t < t_max) {
-            w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, t);
+            w = philox_rk(make_uint4(sweep, tag, kPDep << 24, t), K);
             e0 = coord32(w.x, R.R_s32);
             e1 = coord32(w.y, R.R_s32);
             e2 = coord32(w.z, R.R_s32);
