@@ -149,8 +149,16 @@ __global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__
             return;
         }
     }
-    const Frame32 Fn = frame32(quat32(P.prop_quat[g]));
-    const Frame32 Fo = frame32(quat32(P.quat[g]));
+    // the two frames live in shared memory (fewer registers, more resident warps)
+    __shared__ Frame32 s_F[4][2];
+    const int wib = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_F[wib][0] = frame32(quat32(P.prop_quat[g]));
+        s_F[wib][1] = frame32(quat32(P.quat[g]));
+    }
+    __syncwarp();
+    const Frame32 &Fn = s_F[wib][0];
+    const Frame32 &Fo = s_F[wib][1];
     uint32_t rck = 0;
     const float o0 = -D0, o1 = -D1, o2 = -D2;
     const uint4 wp = draw(R.key0, R.key1, sweep, tag, kPPoisson, 0, 0);
