@@ -248,6 +248,16 @@ int hpmc_cell_list_noalloc(int n, double box_l, int n_cell, const double *pos_de
                            uint64_t seed, uint32_t replica, uint64_t sweep,
                            int *cell_start_dev, int *cell_idx_dev, void *stream);
 
+/* Depletant free volume (Sec. IV.A observable): of n_probe points uniform in
+ * replica `replica`'s box, how many overlap none of its colloids as a
+ * depletant of diameter q (at the current positions, FP64 tests).  Probe m
+ * draws Philox4x32-10 under the key (seed_lo, seed_hi) with counter
+ * (sample, m_lo, 8 << 24 | m_hi, 0) and sits at box_l * ((w_d + 1/2) 2^-32);
+ * alpha = n_free / n_probe, and phi_p = alpha * eta_r.  Synchronous.  Uses
+ * stream-ordered scratch on the context's own stream. */
+int hpmc_free_volume(hpmc_ctx *ctx, int replica, double q, uint64_t seed, uint32_t sample,
+                     uint64_t n_probe, uint64_t *n_free);
+
 /* Human-readable name of an HPMC_* code. */
 const char *hpmc_strerror(int code);
 

@@ -25,7 +25,8 @@ TARGETS = {
     "libhpmc_dep.so": (["hpmc_dep.cu"], ["hpmc_common.cuh", "hpmc_cells.cuh", "hpmc_misc.cuh",
                                        "hpmc_sphere_fp64.cuh", "hpmc_sphere_fp32.cuh",
                                        "hpmc_shapes.cuh", "hpmc_aniso_fp64.cuh",
-                                       "hpmc_shapes32.cuh", "hpmc_aniso_fp32.cuh"]),
+                                       "hpmc_shapes32.cuh", "hpmc_aniso_fp32.cuh",
+                                       "hpmc_probe.cuh"]),
     "libhpmc_peaks.so": (["pipe_peaks.cu"], []),
 }
 

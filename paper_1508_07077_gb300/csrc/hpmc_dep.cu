@@ -22,6 +22,7 @@
 #include "hpmc_sphere_fp64.cuh"
 #include "hpmc_aniso_fp64.cuh"
 #include "hpmc_aniso_fp32.cuh"
+#include "hpmc_probe.cuh"
 
 using namespace hpmc;
 
@@ -1330,6 +1331,62 @@ int hpmc_cell_list(int n, double box_l, int n_cell, const double *pos_dev, uint6
     cudaFreeAsync(cell_of, s);
     cudaFreeAsync(count, s);
     return rc;
+}
+
+int hpmc_free_volume(hpmc_ctx *c, int replica, double q, uint64_t seed, uint32_t sample,
+                     uint64_t n_probe, uint64_t *n_free)
+{
+    if (!c || !n_free || replica < 0 || replica >= (int)c->reps.size() || !(q >= 0.0) ||
+        !std::isfinite(q))
+        return HPMC_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (c->dirty || c->state_dirty) {
+        CK(cudaDeviceSynchronize());
+        const int rc = c->dirty ? prepare(c) : check_config(c);
+        if (rc != HPMC_OK) return rc;
+    }
+    Rep R = c->rdev[(size_t)replica];
+    R.r_dep = 0.5 * q;
+    const double Rd = 0.5 * c->prm.sp[0] + 0.5 * q;
+    R.R_dep2 = Rd * Rd;
+    const int n = R.n, nc = R.nc, ncell = nc * nc * nc;
+    const double w = R.L / (double)nc;
+    cudaStream_t s = c->cap_stream;
+    CK(cudaStreamSynchronize(s));
+    int *count = nullptr, *cell_of = nullptr, *start = nullptr, *idx = nullptr;
+    unsigned long long *d_free = nullptr;
+    cudaError_t e = cudaMallocAsync(&count, sizeof(int) * (size_t)ncell, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&cell_of, sizeof(int) * (size_t)n, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&start, sizeof(int) * ((size_t)ncell + 1), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&idx, sizeof(int) * (size_t)n, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_free, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncell, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_free, 0, sizeof(unsigned long long), s);
+    unsigned long long h_free = 0;
+    if (e == cudaSuccess) {
+        const double *pos = reinterpret_cast<const double *>(c->d_pos + R.off);
+        k_csr_count<<<(n + 255) / 256, 256, 0, s>>>(n, R.L, w, nc, pos, 4, R.key0, R.key1, 0u,
+                                                    cell_of, count);
+        k_csr_scan<<<1, 1024, 0, s>>>(ncell, count, start);
+        k_csr_scatter<<<(n + 255) / 256, 256, 0, s>>>(n, cell_of, count, idx);
+        const unsigned long long want = (n_probe + 255) / 256;
+        const int blocks = (int)std::min<unsigned long long>(want > 0 ? want : 1, 152ull * 16);
+        k_free_volume<<<blocks, 256, 0, s>>>(R, nc, R.key0, R.key1, 0u, c->d_pos + R.off,
+                                             c->d_quat + R.off, start, idx, (uint32_t)seed,
+                                             (uint32_t)(seed >> 32), sample, n_probe, d_free);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&h_free, d_free, sizeof h_free, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    cudaFreeAsync(count, s);
+    cudaFreeAsync(cell_of, s);
+    cudaFreeAsync(start, s);
+    cudaFreeAsync(idx, s);
+    cudaFreeAsync(d_free, s);
+    if (e != cudaSuccess) return cuda_fail(e, "hpmc_free_volume");
+    *n_free = h_free;
+    return HPMC_OK;
 }
 
 }  // extern "C"

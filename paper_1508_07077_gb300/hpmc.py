@@ -28,7 +28,7 @@ EXPORTS = ("hpmc_init", "hpmc_init_batch", "hpmc_get_replica", "hpmc_set_replica
            "hpmc_set_timing",
            "hpmc_get_timing", "hpmc_sweep", "hpmc_get_state",
            "hpmc_set_state", "hpmc_reset_counters", "hpmc_sync", "hpmc_cell_list",
-           "hpmc_cell_list_noalloc", "hpmc_strerror", "hpmc_destroy")
+           "hpmc_cell_list_noalloc", "hpmc_free_volume", "hpmc_strerror", "hpmc_destroy")
 
 
 class HPMCError(RuntimeError):
@@ -98,6 +98,8 @@ def load(path: str = LIB_PATH):
     L.hpmc_cell_list.argtypes = [ip, ctypes.c_double, ip, vp, ctypes.c_uint64,
                                  ctypes.c_uint32, ctypes.c_uint64, vp, vp, vp]
     L.hpmc_cell_list_noalloc.argtypes = L.hpmc_cell_list.argtypes
+    L.hpmc_free_volume.argtypes = [vp, ip, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                                   ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
     L.hpmc_strerror.argtypes = [ip]
     L.hpmc_strerror.restype = ctypes.c_char_p
     L.hpmc_destroy.argtypes = [vp]
@@ -226,6 +228,15 @@ def hpmc_autotune(ctx, warps=(1, 2, 4), cells=(0,), n_sweeps=5):
                                 ctypes.byref(bw), ctypes.byref(bc), ctypes.byref(bm)),
            "hpmc_autotune")
     return bw.value, bc.value, bm.value
+
+
+def hpmc_free_volume(ctx, q, *, replica=0, seed=7, sample=0, n_probe=1000000):
+    """(free probes, n_probe): probes of replica `replica` overlapping no colloid
+    as a depletant of diameter q."""
+    out = ctypes.c_uint64(0)
+    _check(load().hpmc_free_volume(ctx, int(replica), float(q), int(seed), int(sample),
+                                   int(n_probe), ctypes.byref(out)), "hpmc_free_volume")
+    return out.value, int(n_probe)
 
 
 def hpmc_set_launch(ctx, warps_per_colloid, attempts_per_thread=1):
