@@ -78,6 +78,14 @@ __global__ void k_cells_bin(const __grid_constant__ SimParams P)
     else atomicCAS(P.err, kErrNone, kErrCellCap);
     if (P.binpos) P.binpos[g] = slot < P.cap ? c * P.cap + slot : -1;
     P.rel[g] = rl;
+    // FP32 sphere form: the exact proposal of this sweep (translation), for
+    // the colour phases' commit and exact re-takes
+    if (P.task) {
+        const uint4 wm = draw(R.key0, R.key1, sweep, (uint32_t)(g - R.off), kPMove, 0, 0);
+        P.prop_pos[g] = make_double4(wrap_box(p.x + R.d_max * s11(wm.x), R.L),
+                                     wrap_box(p.y + R.d_max * s11(wm.y), R.L),
+                                     wrap_box(p.z + R.d_max * s11(wm.z), R.L), 0.0);
+    }
 }
 
 // Order every phase's tasks by the population of their cell, fullest first:

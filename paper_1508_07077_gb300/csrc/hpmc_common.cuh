@@ -178,7 +178,8 @@ struct SimParams {
     int4 *lens_hdr;
     float4 *lens_move;     // the move's FP32 displacement (the phase kernels reuse it); .w the
                            // move kind for anisotropic shapes (1 translation, 0 rotation, -1 capped)
-    double4 *prop_pos;     // anisotropic FP32 form: exact proposed position (.w = move kind)
+    double4 *prop_pos;     // FP32 forms: exact proposed position of this sweep (anisotropic:
+                           // .w = move kind)
     double4 *prop_quat;    // and orientation
     // per-sweep tables written by the cell-list kernel for the FP32 sphere
     // phases: task[phase][cta] = (global cell, replica, cx | cy << 10 | cz << 20);

@@ -665,9 +665,10 @@ int prepare(hpmc_ctx *c)
         c->d_cls_count = nullptr;
         c->task_alloc = -1;
     }
-    if (c->precision == HPMC_FP32_RECHECK && p.shape != HPMC_SPHERE) {
+    if (c->precision == HPMC_FP32_RECHECK) {
         if (!c->d_prop_pos) CK(cudaMalloc(&c->d_prop_pos, sizeof(double4) * (size_t)c->n_total));
-        if (!c->d_prop_quat) CK(cudaMalloc(&c->d_prop_quat, sizeof(double4) * (size_t)c->n_total));
+        if (p.shape != HPMC_SPHERE && !c->d_prop_quat)
+            CK(cudaMalloc(&c->d_prop_quat, sizeof(double4) * (size_t)c->n_total));
     }
     if (c->precision == HPMC_FP32_RECHECK) {
         if (!c->d_lens_hdr) CK(cudaMalloc(&c->d_lens_hdr, sizeof(int4) * (size_t)c->n_total));

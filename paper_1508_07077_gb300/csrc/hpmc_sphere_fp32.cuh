@@ -41,14 +41,15 @@ __device__ __forceinline__ int tri(float r2, float T, float m)
 // accepted by this CTA are committed to FP64 only when the CTA finishes, so a
 // colloid of the list acc[0..nacc) is at its moved position.
 
-// Exact FP64 position of colloid j after its move of this sweep.
+// Exact FP64 position of colloid j after its move of this sweep: computed
+// once per sweep, one thread per colloid, by the cell-list kernel (GB300's
+// FP64 issue is slow, and a single-lane FP64 sequence costs a whole warp's
+// time, so it is kept off the colour phases).
 __device__ __forceinline__ double4 moved64(const SimParams &P, const Rep &R, uint32_t sweep, int j)
 {
-    const uint4 wm = draw(R.key0, R.key1, sweep, (uint32_t)(j - R.off), kPMove, 0, 0);
-    const double4 p = P.pos[j];
-    return make_double4(wrap_box(p.x + R.d_max * s11(wm.x), R.L),
-                        wrap_box(p.y + R.d_max * s11(wm.y), R.L),
-                        wrap_box(p.z + R.d_max * s11(wm.z), R.L), 0.0);
+    (void)R;
+    (void)sweep;
+    return P.prop_pos[j];
 }
 
 __device__ __forceinline__ double4 pos_now(const SimParams &P, const Rep &R, uint32_t sweep, int j,
@@ -842,7 +843,7 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
     const int nacc = s_nacc;
     for (int a = tid; a < nacc; a += nthr) {
         const int j = s_accl[a];
-        P.pos[j] = moved64(P, R, sweep, j);
+        P.pos[j] = P.prop_pos[j];
     }
 
     unsigned long long cnt[kNumCounters] = {0};
