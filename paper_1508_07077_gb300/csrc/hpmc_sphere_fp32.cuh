@@ -311,7 +311,7 @@ __device__ __forceinline__ bool cb_pass(DepShared &sh, int tid, int nslots, doub
 // holds at most N_p <= (Poisson table length) points, the capacity it is
 // allocated with, so it cannot overflow.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_lens_sphere_fp32(const __grid_constant__ SimParams P)
+__global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_constant__ SimParams P)
 {
     const int lane = threadIdx.x & 31;
     const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
