@@ -661,6 +661,8 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
             __syncthreads();
         }
         int ov = 0, nnb = 0;
+        // the neighbour list is needed only if the move has lens points (or CB)
+        const bool need_nb = has_dep && (CB || s_hdr[qb].z > 0);
         for (int j0 = 0; j0 < M; j0 += nthr) {
             const int j = j0 + tid;
             int t = 0, pj = -1;
@@ -671,12 +673,17 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
                 if (pj == i) {
                     pj = -1;
                 } else {
+                    // candidates are relative to this cell's origin: with 4 or
+                    // more cells per side |d| < 2w <= L/2 and the minimum image
+                    // is d itself; only n_c = 2 folds
                     d0 = cp.x - rn0;
                     d1 = cp.y - rn1;
                     d2 = cp.z - rn2;
-                    if (d0 > half_L32) d0 -= L32; else if (d0 < -half_L32) d0 += L32;
-                    if (d1 > half_L32) d1 -= L32; else if (d1 < -half_L32) d1 += L32;
-                    if (d2 > half_L32) d2 -= L32; else if (d2 < -half_L32) d2 += L32;
+                    if (nc == 2) {
+                        if (d0 > half_L32) d0 -= L32; else if (d0 < -half_L32) d0 += L32;
+                        if (d1 > half_L32) d1 -= L32; else if (d1 < -half_L32) d1 += L32;
+                        if (d2 > half_L32) d2 -= L32; else if (d2 < -half_L32) d2 += L32;
+                    }
                     r2 = norm2f(d0, d1, d2);
                     t = tri(r2, T_contact, m_r2);
                 }
@@ -689,6 +696,7 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
                 }
             }
             if (t == 1) ov = 1;
+            if (!need_nb) continue;
             const bool take = pj >= 0 && r2 < nb_cut2;
             if (WARP) {
                 const unsigned b = __ballot_sync(kFull, take);
