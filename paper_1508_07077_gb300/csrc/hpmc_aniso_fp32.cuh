@@ -133,10 +133,13 @@ __global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__
         D1 = coord32(wm.y, R.d_max32);
         D2 = coord32(wm.z, R.d_max32);
     }
-    if (lane == 0) P.lens_move[g] = make_float4(D0, D1, D2, (float)kind);
+    // displacement, move kind, header and the first lens points go to the
+    // colloid's bin slot, where the colour phase reads them
+    const int bp = P.binpos[g];
+    if (lane == 0 && bp >= 0) P.mv_bin[bp] = make_float4(D0, D1, D2, (float)kind);
     if (!R.has_dep) return;
     if (kind < -0.5) {
-        if (lane == 0) P.lens_hdr[g] = make_int4(0, 0, 0, 0);
+        if (lane == 0 && bp >= 0) P.hdr_bin[bp] = make_int4(0, 0, 0, 0);
         return;
     }
     if (kind > 0.5) {
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__
         const float mc = R.m_cell, wc = R.w32;
         if (rn0 < -mc || rn0 > wc + mc || rn1 < -mc || rn1 > wc + mc || rn2 < -mc ||
             rn2 > wc + mc) {
-            if (lane == 0) P.lens_hdr[g] = make_int4(0, 0, 0, 0);
+            if (lane == 0 && bp >= 0) P.hdr_bin[bp] = make_int4(0, 0, 0, 0);
             return;
         }
     }
@@ -225,10 +228,12 @@ __global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__
         k0 += __popc(bal);
         t0 += 32u;
     }
-    if (lane == 0) {
-        P.lens_hdr[g] = make_int4(n_p, min(k0, n_p), min(m, P.lens_cap), 0);
-        if (m > P.lens_cap) atomicCAS(P.err, kErrNone, kErrCandCap);
+    __syncwarp();
+    if (bp >= 0) {
+        if (lane == 0) P.hdr_bin[bp] = make_int4(n_p, min(k0, n_p), min(m, P.lens_cap), 0);
+        if (lane < min(m, kLensInline)) P.lens_bin[(size_t)bp * kLensInline + lane] = out[lane];
     }
+    if (lane == 0 && m > P.lens_cap) atomicCAS(P.err, kErrNone, kErrCandCap);
     rck = __reduce_add_sync(kFull, rck);
     if (lane == 0 && rck) count_one(P, r, kRechecks, (unsigned long long)rck);
 }
@@ -339,8 +344,9 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
     __shared__ float4 s_cq[kMaxCand];
     __shared__ Nb32 s_nb[kMaxNbAniso];
     __shared__ float4 s_lens[kMaxLensCTA];
-    __shared__ int4 s_hdr[CAP];
+    __shared__ int4 s_hdr[CAP];                  // own cell, bin order
     __shared__ float4 s_mv[CAP];
+    __shared__ float4 s_lin[2][kLensInline];     // inline lens points of bin slots 0, 1
     __shared__ int s_tmp_i[CAP], s_tmp_slot[CAP];
     __shared__ int s_own[CAP], s_own_slot[CAP], s_own_bin[CAP];
     __shared__ int s_loff[CAP], s_accl[CAP];
@@ -355,47 +361,119 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
         sh.f = s_dyn;
         sh.k = (int *)(s_dyn + nthr);
     }
-    const int r = P.cta_rep[blockIdx.x];
-    const Rep &R = P.reps[r];
-    const Sched *S = P.sched + r;
+    // Launched with programmatic dependent launch, as the sphere phases: the
+    // task, populations, replica record and the lens kernel's per-slot data
+    // are fixed for the sweep and read before pdl_wait(); positions and
+    // orientations (bins, FP64 state) only after it.
+    pdl_trigger();
     if (phase == 7 && blockIdx.x == 0 && tid == 0) atomicAdd(P.sweep, 1ull);
-    const uint32_t sweep = S->sweep;
-    const CellTask T = cell_task(P, R, r, phase);
-    clear_next(P, sweep, T.cell);
-    const int n_own = min(T.n_own, P.cap);
-    if (n_own == 0) return;
-    const int cx = T.cx, cy = T.cy, cz = T.cz;
-
-    if (tid == 0) {
-        s_ncand = 0;
-        s_nacc = 0;
-    }
-    cta_sync<WARP>();
-    if (tid < R.n_stencil * R.n_stencil * R.n_stencil) {
-        int dx, dy, dz;
-        const int c = stencil_cell(R, tid, cx, cy, cz, dx, dy, dz);
-        const float fx = (float)dx * R.w32, fy = (float)dy * R.w32, fz = (float)dz * R.w32;
-        const int m = c == T.cell ? n_own : min(T.count[c], P.cap);
-        const float4 *bin = P.bins + (size_t)c * P.cap;
-        for (int s = 0; s < m; ++s) {
-            const float4 e = bin[s];
-            const int slot = atomicAdd(&s_ncand, 1);
-            if (slot < kMaxCand) {
-                s_cpos[slot] = make_float4(fx + e.x, fy + e.y, fz + e.z, e.w);
-                s_cq[slot] = quat32(P.quat[__float_as_int(e.w)]);
-            }
-            if (c == T.cell) {
-                s_tmp_i[s] = __float_as_int(e.w);
-                s_tmp_slot[s] = slot;
+    int cls = 0, idx = blockIdx.x;
+    {
+        const int4 cc = reinterpret_cast<const int4 *>(P.cls_count)[phase];
+        if (idx >= cc.x) {
+            idx -= cc.x;
+            cls = 1;
+            if (idx >= cc.y) {
+                idx -= cc.y;
+                cls = 2;
+                if (idx >= cc.z) {
+                    idx -= cc.z;
+                    cls = 3;
+                }
             }
         }
     }
-    cta_sync<WARP>();
-    const int M = s_ncand;
+    const int4 tk = P.task_ord[(size_t)(phase * 4 + cls) * P.n_cta + idx];
+    const int cell = tk.x, r = tk.y;
+    const int cx = tk.z & 1023, cy = (tk.z >> 10) & 1023, cz = tk.z >> 20;
+    const int nc = tk.w & 0xFFFF, par = tk.w >> 16;
+    if (cls == 3) {               // an empty cell: only its next-sweep population
+        if (tid == 0) P.count[par ^ 1][cell] = 0;
+        return;
+    }
+    const int ns = nc == 2 ? 2 : 3, n_st = ns * ns * ns;
+    const int t_own = ns == 3 ? 13 : cx + 2 * cy + 4 * cz;
+    const int cell_off = cell - (cx + nc * (cy + nc * cz));
+    const int *count = P.count[par];
+    const Rep &R = P.reps[r];
+    const float w32 = R.w32, L32 = R.L32, half_L32 = R.half_L32;
+    const int has_dep = R.has_dep;
+    const Sched *S = P.sched + r;
+    if (tid == 0) P.count[par ^ 1][cell] = 0;
+
+    // populations of the stencil; the own cell's lens data (slots 0 and 1)
+    int c_nb = 0, m_nb = 0, dx = 0, dy = 0, dz = 0;
+    if (tid < n_st) {
+        c_nb = stencil_cell_nc(nc, cell_off, tid, cx, cy, cz, dx, dy, dz);
+        const size_t b0 = (size_t)c_nb * P.cap;
+        m_nb = count[c_nb];
+        if (tid == t_own) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                s_mv[s] = P.mv_bin[b0 + s];
+                s_hdr[s] = P.hdr_bin[b0 + s];
+#pragma unroll
+                for (int j = 0; j < kLensInline; ++j)
+                    s_lin[s][j] = P.lens_bin[(b0 + s) * kLensInline + j];
+            }
+        }
+        m_nb = min(m_nb, P.cap);
+    }
+    int n_own = 0, M = 0, base = 0;
+    if (tid < 32) {
+        n_own = __shfl_sync(kFull, m_nb, t_own);
+        int incl = m_nb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        base = incl - m_nb;
+        M = __shfl_sync(kFull, incl, 31);
+        if (!WARP && tid == 0) {
+            s_ncand = M;
+            s_nacc = n_own;
+        }
+    }
+    if (!WARP) {
+        __syncthreads();
+        M = s_ncand;
+        n_own = s_nacc;
+        __syncthreads();
+    }
+    if (n_own == 0) return;
     if (M > kMaxCand) {
         if (tid == 0) atomicCAS(P.err, kErrNone, kErrCandCap);
         return;
     }
+    const uint32_t sweep = S->sweep;
+    if (tid == 0) s_nacc = 0;
+    // the previous phase's moves are visible from here on
+    pdl_wait();
+    // candidates (positions and FP32 orientations) relative to this cell's
+    // origin; the own cell's entries beyond slot 1 with their lens data
+    if (tid < n_st) {
+        const float fx = (float)dx * w32, fy = (float)dy * w32, fz = (float)dz * w32;
+        const bool own = tid == t_own;
+        const size_t b0 = (size_t)c_nb * P.cap;
+        for (int s = 0; s < m_nb; ++s) {
+            const float4 e = P.bins[b0 + s];
+            const int slot = base + s;
+            s_cpos[slot] = make_float4(fx + e.x, fy + e.y, fz + e.z, e.w);
+            s_cq[slot] = P.bin_q[b0 + s];
+            if (own) {
+                s_tmp_i[s] = __float_as_int(e.w);
+                s_tmp_slot[s] = slot;
+                if (s >= 2) {
+                    s_mv[s] = P.mv_bin[b0 + s];
+                    s_hdr[s] = P.hdr_bin[b0 + s];
+                }
+            }
+        }
+    }
+    cta_sync<WARP>();
+    // the cell's colloids in ascending index (the order they move in), and
+    // where each one's lens points go (bin order)
     for (int q = tid; q < n_own; q += nthr) {
         const int v = s_tmp_i[q];
         int rk = 0;
@@ -403,29 +481,32 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
         s_own[rk] = v;
         s_own_slot[rk] = s_tmp_slot[q];
         s_own_bin[rk] = q;
-        s_mv[rk] = P.lens_move[v];
-        if (R.has_dep) s_hdr[rk] = P.lens_hdr[v];
     }
-    cta_sync<WARP>();
-    if (R.has_dep) {
-        if (tid == 0) {
-            int off = 0;
-            for (int q = 0; q < n_own; ++q) {
-                const int n = s_hdr[q].z;
-                if (n > 0 && off + n <= kMaxLensCTA) {
-                    s_loff[q] = off;
-                    off += n;
-                } else {
-                    s_loff[q] = -1;
-                }
+    if (has_dep && tid == 0) {
+        int off = 0;
+        for (int q = 0; q < n_own; ++q) {
+            const int n = s_hdr[q].z;
+            if (n > 0 && off + n <= kMaxLensCTA) {
+                s_loff[q] = off;
+                off += n;
+            } else {
+                s_loff[q] = -1;
             }
         }
-        cta_sync<WARP>();
+    }
+    cta_sync<WARP>();
+    if (has_dep) {
         for (int q = 0; q < n_own; ++q) {
             const int n = s_hdr[q].z, o = s_loff[q];
             if (o < 0) continue;
-            const float4 *src = P.lens + (size_t)s_own[q] * P.lens_cap;
-            for (int m = tid; m < n; m += nthr) s_lens[o + m] = src[m];
+            if (n <= kLensInline && q < 2) {
+                if (tid < n) s_lens[o + tid] = s_lin[q][tid];
+            } else if (n <= kLensInline) {
+                if (tid < n) s_lens[o + tid] = P.lens_bin[((size_t)cell * P.cap + q) * kLensInline + tid];
+            } else {
+                const float4 *src = P.lens + (size_t)s_tmp_i[q] * P.lens_cap;
+                for (int m = tid; m < n; m += nthr) s_lens[o + m] = src[m];
+            }
         }
         cta_sync<WARP>();
     }
@@ -438,8 +519,9 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
     for (int q = 0; q < n_own; ++q) {
         const int i = s_own[q];
         const int nacc = s_nacc;
+        const int qb = s_own_bin[q];
         const float4 ri = s_cpos[s_own_slot[q]];
-        const float4 mv = s_mv[q];
+        const float4 mv = s_mv[qb];
         const float kind = mv.w;
         if (kind < -0.5f) {          // rotation attempt stream capped: rejected
             if (tid == 0) ++c_cap;
@@ -547,13 +629,13 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
 
         bool accept = true;
         if (R.has_dep) {
-            const int4 hd = s_hdr[q];
+            const int4 hd = s_hdr[qb];
             const int n_p = hd.x;
             c_drawn += (unsigned long long)n_p;
             DepOutcome od = {1.0, 0, 0, 0u, 0u, 0u, 0u, 0u, 0u};
             const int n_lens = hd.z;
-            const float4 *lens = s_loff[q] >= 0 ? s_lens + s_loff[q]
-                                                : P.lens + (size_t)i * P.lens_cap;
+            const float4 *lens = s_loff[qb] >= 0 ? s_lens + s_loff[qb]
+                                                 : P.lens + (size_t)i * P.lens_cap;
             if (!CB && !WARP) {
                 if (tid == 0) sh.kmin = 0x7FFFFFFF;
                 __syncthreads();
@@ -662,7 +744,8 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
                 const float4 rnew = make_float4(rn0, rn1, rn2, __int_as_float(i));
                 s_cpos[s_own_slot[q]] = rnew;
                 s_cq[s_own_slot[q]] = qn32;
-                if (translate) P.bins[(size_t)T.cell * P.cap + s_own_bin[q]] = rnew;
+                if (translate) P.bins[(size_t)cell * P.cap + qb] = rnew;
+                else P.bin_q[(size_t)cell * P.cap + qb] = qn32;
                 s_accl[nacc] = i;
                 s_nacc = nacc + 1;
             }

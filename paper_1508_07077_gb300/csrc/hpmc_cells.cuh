@@ -77,10 +77,14 @@ __global__ void k_cells_bin(const __grid_constant__ SimParams P)
     if (slot < P.cap) P.bins[(size_t)c * P.cap + slot] = rl;
     else atomicCAS(P.err, kErrNone, kErrCellCap);
     if (P.binpos) P.binpos[g] = slot < P.cap ? c * P.cap + slot : -1;
+    if (P.bin_q && slot < P.cap) {
+        const double4 q = P.quat[g];
+        P.bin_q[(size_t)c * P.cap + slot] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
+    }
     P.rel[g] = rl;
     // FP32 sphere form: the exact proposal of this sweep (translation), for
     // the colour phases' commit and exact re-takes
-    if (P.task) {
+    if (P.task && R.shape == 0) {
         const uint4 wm = draw(R.key0, R.key1, sweep, (uint32_t)(g - R.off), kPMove, 0, 0);
         P.prop_pos[g] = make_double4(wrap_box(p.x + R.d_max * s11(wm.x), R.L),
                                      wrap_box(p.y + R.d_max * s11(wm.y), R.L),

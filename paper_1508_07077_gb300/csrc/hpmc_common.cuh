@@ -194,6 +194,7 @@ struct SimParams {
     int4 *hdr_bin;
     float4 *mv_bin;
     float4 *lens_bin;      // the first kLensInline lens points of each bin slot
+    float4 *bin_q;         // FP32 orientation of each bin slot (anisotropic FP32 form)
     Sched *sched;          // per replica
     unsigned long long *sweep;     // next sweep index (all replicas)
     unsigned long long *counters;  // [n_rep][kRepSlots][kNumCounters]

@@ -85,6 +85,8 @@ struct hpmc_ctx {
     float4 *d_mv_bin = nullptr;
     float4 *d_lens_bin = nullptr; // first lens points per bin slot
     long long aux_alloc = -1;
+    float4 *d_bin_q = nullptr;    // FP32 orientation per bin slot (anisotropic FP32 form)
+    long long binq_alloc = -1;
     Rep *d_reps = nullptr;
     int *d_rep_of = nullptr;
     int *d_cta_rep = nullptr;
@@ -355,6 +357,7 @@ SimParams make_params(hpmc_ctx *c)
     P.hdr_bin = c->d_hdr_bin;
     P.mv_bin = c->d_mv_bin;
     P.lens_bin = c->d_lens_bin;
+    P.bin_q = c->prm.shape == HPMC_SPHERE ? nullptr : c->d_bin_q;
     P.sched = c->d_sched;
     P.sweep = c->d_sweep;
     P.counters = c->d_counters;
@@ -421,11 +424,11 @@ void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s
         if constexpr (CAP >= kSmallCellCap) {
             const bool warp = threads == 32;
             if (cb) {
-                if (warp) k_phase_aniso_fp32<true, true, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
-                else k_phase_aniso_fp32<true, false, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
+                if (warp) launch_pdl(k_phase_aniso_fp32<true, true, CAP>, c->n_cta, threads, dyn, s, P, phase);
+                else launch_pdl(k_phase_aniso_fp32<true, false, CAP>, c->n_cta, threads, dyn, s, P, phase);
             } else {
-                if (warp) k_phase_aniso_fp32<false, true, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
-                else k_phase_aniso_fp32<false, false, CAP><<<c->n_cta, threads, dyn, s>>>(P, phase);
+                if (warp) launch_pdl(k_phase_aniso_fp32<false, true, CAP>, c->n_cta, threads, dyn, s, P, phase);
+                else launch_pdl(k_phase_aniso_fp32<false, false, CAP>, c->n_cta, threads, dyn, s, P, phase);
             }
         }
     } else if (c->precision == HPMC_FP32_RECHECK) {
@@ -628,7 +631,7 @@ int prepare(hpmc_ctx *c)
                       cudaMemcpyHostToDevice));
     }
     // lens lists hold at most N_p <= nF points each: capacity nF_max, no overflow
-    if (c->precision == HPMC_FP32_RECHECK && p.shape == HPMC_SPHERE) {
+    if (c->precision == HPMC_FP32_RECHECK) {
         // task table, bin positions, per-slot lens headers and displacements
         if (cta_off != c->task_alloc) {
             cudaFree(c->d_task);
@@ -655,6 +658,13 @@ int prepare(hpmc_ctx *c)
             CK(cudaMalloc(&c->d_mv_bin, sizeof(float4) * (size_t)slots));
             CK(cudaMalloc(&c->d_lens_bin, sizeof(float4) * kLensInline * (size_t)slots));
             c->aux_alloc = slots;
+        }
+        if (p.shape != HPMC_SPHERE && slots != c->binq_alloc) {
+            cudaFree(c->d_bin_q);
+            c->d_bin_q = nullptr;
+            c->binq_alloc = -1;
+            CK(cudaMalloc(&c->d_bin_q, sizeof(float4) * (size_t)slots));
+            c->binq_alloc = slots;
         }
     } else if (c->d_task) {
         cudaFree(c->d_task);
@@ -1489,6 +1499,7 @@ void hpmc_destroy(hpmc_ctx *c)
     cudaFree(c->d_hdr_bin);
     cudaFree(c->d_mv_bin);
     cudaFree(c->d_lens_bin);
+    cudaFree(c->d_bin_q);
     cudaFree(c->d_reps);
     cudaFree(c->d_rep_of);
     cudaFree(c->d_cta_rep);
