@@ -79,31 +79,37 @@ __device__ __noinline__ int spheroid_newton32(float a, float c, float r, float m
     const float A2 = a * a, C2 = c * c;
     const float rho = sqrtf(rho2);
     float t = 0.0f;
+    // the certificate holds for any t (X is a point of the ellipse, n its
+    // normal there), so it is tried after a few steps and the iteration stops
+    // as soon as it decides
 #pragma unroll 1
-    for (int it = 0; it < 24; ++it) {
+    for (int it = 1; it <= 24; ++it) {
         const float d1 = t + A2, d2 = t + C2;
         const float g1 = a * rho / d1, g2 = c * z / d2;
         const float F = g1 * g1 + g2 * g2 - 1.0f;
         const float D = g1 * g1 / d1 + g2 * g2 / d2;
         const float tn = t + F / (2.0f * D);
-        if (!(tn > t)) break;
-        t = tn;
+        const bool done = !(tn > t) || it == 24;
+        if (!done) t = tn;
+        if (done || it == 3 || it == 6 || it == 12) {
+            // foot point, projected radially onto the ellipse
+            float x0 = A2 * rho / (t + A2), x1 = C2 * z / (t + C2);
+            const float sc = rsqrtf(x0 * x0 / A2 + x1 * x1 / C2);
+            x0 *= sc;
+            x1 *= sc;
+            const float e0 = rho - x0, e1 = z - x1;
+            const float hi = sqrtf(e0 * e0 + e1 * e1);
+            // outward normal of the ellipse at X
+            float n0 = x0 / A2, n1 = x1 / C2;
+            const float nl = rsqrtf(n0 * n0 + n1 * n1);
+            n0 *= nl;
+            n1 *= nl;
+            const float lo = n0 * rho + n1 * z - sqrtf(A2 * n0 * n0 + C2 * n1 * n1);
+            if (hi < r - m) return 1;
+            if (lo > r + m) return 0;
+            if (done) return -1;
+        }
     }
-    // foot point, projected radially onto the ellipse
-    float x0 = A2 * rho / (t + A2), x1 = C2 * z / (t + C2);
-    const float sc = rsqrtf(x0 * x0 / A2 + x1 * x1 / C2);
-    x0 *= sc;
-    x1 *= sc;
-    const float e0 = rho - x0, e1 = z - x1;
-    const float hi = sqrtf(e0 * e0 + e1 * e1);
-    // outward normal of the ellipse at X
-    float n0 = x0 / A2, n1 = x1 / C2;
-    const float nl = rsqrtf(n0 * n0 + n1 * n1);
-    n0 *= nl;
-    n1 *= nl;
-    const float lo = n0 * rho + n1 * z - sqrtf(A2 * n0 * n0 + C2 * n1 * n1);
-    if (hi < r - m) return 1;
-    if (lo > r + m) return 0;
     return -1;
 }
 
