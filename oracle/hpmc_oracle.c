@@ -29,6 +29,10 @@
  * written in the exact operation order that specification fixes, and must be
  * compiled with -ffp-contract=off (no fused multiply-add).
  *
+ *   - Sec. III.C, closing remark (option v0_mode 1): for sphere translations
+ *     V_0 may be restricted to the shell of the moved colloid's excluded
+ *     volume that can hold points overlapping only the new pose; the shell
+ *     thickness is quantised into 32 levels chosen from the move's words.
  *   - Sec. V: anisotropic colloids (hemispheres, discoids = oblate spheroids)
  *     with quaternion rotation moves; overlap of two convex colloids by
  *     Minkowski portal refinement on their support functions.
@@ -40,7 +44,11 @@
  * free-volume fraction of a single colloid; for the anisotropic shapes,
  * point and pair tests against a general constrained minimiser and against
  * touching distances on symmetry axes, the Steiner excluded volume, the
- * rotation-proposal distribution and detailed balance of rotation moves.
+ * rotation-proposal distribution and detailed balance of rotation moves; for
+ * the shell V_0, lens containment by brute force, the uniformity of the shell
+ * points, the Poisson mean of the shell volume, equality of the acceptance
+ * probability with the circumsphere's, detailed balance and the
+ * Asakura-Oosawa distribution.
  */
 #include <math.h>
 #include <stdint.h>
@@ -599,6 +607,13 @@ typedef struct {
     int brute_force;
     double *F;
     int nF;
+    /* shell-restricted V_0 (v0_mode 1, sphere translations): per level k =
+     * 1..SHELL_LEVELS the inner radius, the thickness and the Poisson table */
+    int v0_mode;
+    double R_s4, dd;
+    double s_rin[32], s_h[32];
+    double *sF[32];
+    int snF[32];
 } osim;
 
 typedef struct {
@@ -674,6 +689,105 @@ static int next_in_ball(const osim *S, uint32_t sweep, uint32_t tag,
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Shell-restricted V_0 (Sec. III.C, the closing remark): for a sphere      */
+/* translated by D, a depletant overlapping the new pose but not the old     */
+/* one lies at distance >= R_s - |D| from the new centre, so the spherical   */
+/* shell R_in <= |e| < R_s with R_in <= R_s - |D| is a valid V_0.  The shell */
+/* is taken from SHELL_LEVELS quantised thicknesses so that each has a       */
+/* precomputed Poisson table.                                                */
+/* ------------------------------------------------------------------------ */
+#define SHELL_LEVELS 32
+
+/* Level of a translation from its move words w[0..2].  D_d = d_max n_d 2^-32
+ * with n_d = 2 w_d + 1 - 2^32 (odd, |n_d| < 2^32); a_d = floor(|n_d| 2^-16)
+ * + 1 exceeds |n_d| 2^-16, so with S = sum a_d^2 the displacement obeys
+ * |D| < d_max sqrt(S) 2^-16.  The level is the smallest k >= 1 with
+ * S <= 3 k^2 2^22, hence |D| < k sqrt(3) d_max / 32 = k dd.  Integer-only. */
+static int shell_level_words(const uint32_t w[3])
+{
+    uint64_t S = 0;
+    for (int d = 0; d < 3; ++d) {
+        int64_t n = 2 * (int64_t)w[d] + 1 - ((int64_t)1 << 32);
+        uint64_t a = ((uint64_t)(n < 0 ? -n : n) >> 16) + 1;
+        S += a * a;
+    }
+    int k = 1;
+    while (k < SHELL_LEVELS && S > (((uint64_t)3 * (uint64_t)k * (uint64_t)k) << 22)) ++k;
+    return k;
+}
+
+int oracle_shell_level(const uint32_t w[3]) { return shell_level_words(w); }
+
+/* Geometry of level k: thickness k dd plus 1e-9 R_s (so that rounding never
+ * leaves a lens point outside), inner radius clamped at 0. */
+static void shell_geometry(double R_s, double dd, int k, double *R_in, double *h)
+{
+    double t = (double)k * dd + 1e-9 * R_s;
+    double r = R_s - t;
+    if (r < 0.0) r = 0.0;
+    *R_in = r;
+    *h = R_s - r;
+}
+
+/* Mean depletant number of a shell: z_p (4 pi / 3) (R_s^3 - R_in^3). */
+double oracle_shell_lambda(double R_s, double R_in, double n_r)
+{
+    double v = ((4.0 / 3.0) * ORACLE_PI) * (((R_s * R_s) * R_s) - ((R_in * R_in) * R_in));
+    return n_r * v;
+}
+
+/* Next point of the depletant attempt stream uniform in the shell of level
+ * lvl.  Attempt t: v_d = s11(w_d) uniform in the cube; r = R_in + h u01(w_3)
+ * uniform in [R_in, R_s); accepted iff |v|^6 R_s^4 < r^4, i.e.
+ * |v|^3 < (r / R_s)^2.  For v in the unit ball |v|^3 is uniform on [0, 1]
+ * and independent of the direction v / |v|, so the accepted r has density
+ * proportional to r^2 on [R_in, R_s) and the direction is uniform: e =
+ * v (r / |v|) is uniform in the shell.  (r < R_s forces |v| < 1.) */
+static int next_in_shell(const osim *S, int lvl, uint32_t sweep, uint32_t tag,
+                         uint32_t *t, uint32_t t_max, double e[3])
+{
+    const double R_in = S->s_rin[lvl - 1], h = S->s_h[lvl - 1];
+    while (*t < t_max) {
+        uint32_t w[4];
+        draw(S->key, sweep, tag, P_DEP, 0, *t, w);
+        *t += 1;
+        double v0 = s11(w[0]), v1 = s11(w[1]), v2 = s11(w[2]);
+        double p2 = (v0 * v0 + v1 * v1) + v2 * v2;
+        double r = R_in + h * u01(w[3]);
+        double r2 = r * r;
+        if (!(((p2 * p2) * p2) * S->R_s4 < r2 * r2)) continue;
+        double sc = r / sqrt(p2);
+        e[0] = v0 * sc;
+        e[1] = v1 * sc;
+        e[2] = v2 * sc;
+        return 1;
+    }
+    return 0;
+}
+
+/* Points of the shell generator for tests: attempts t = 0 .. n_att - 1 of
+ * stream (sweep, tag) at level lvl of a sphere system; writes the accepted
+ * points to e (3 per point) and returns their count. */
+long oracle_shell_points(double R_s, double d_max, int lvl, uint64_t seed,
+                         uint32_t sweep, uint32_t tag, uint32_t n_att, double *e)
+{
+    osim S;
+    memset(&S, 0, sizeof S);
+    if (lvl < 1 || lvl > SHELL_LEVELS || !(R_s > 0.0) || !(d_max >= 0.0)) return -1;
+    S.R_s = R_s;
+    S.R_s2 = R_s * R_s;
+    S.R_s4 = S.R_s2 * S.R_s2;
+    S.dd = (sqrt(3.0) * d_max) / 32.0;
+    S.key.k[0] = (uint32_t)seed;
+    S.key.k[1] = (uint32_t)(seed >> 32);
+    shell_geometry(R_s, S.dd, lvl, &S.s_rin[lvl - 1], &S.s_h[lvl - 1]);
+    uint32_t t = 0;
+    long m = 0;
+    while (next_in_shell(&S, lvl, sweep, tag, &t, n_att, e + 3 * m)) ++m;
+    return m;
+}
+
 /* Is v (relative to the new reference point) free of every other colloid? */
 static int free_of_neighbours(const osim *S, const double v[3], const onb *nb,
                               int m)
@@ -741,7 +855,7 @@ static double cb_factor(const osim *S, uint32_t sweep, uint32_t tag, uint32_t k,
  * Sec. III.B-III.D.  Returns 1 to accept, 0 to reject. */
 static int accept_move(const osim *S, uint32_t sweep, int i, const double xn[3],
                        const double qn[4], const double o[3], const double *qo,
-                       const int ci[3], const double *pos, const double *quat,
+                       int lvl, const int ci[3], const double *pos, const double *quat,
                        const int *cell_start, const int *cell_idx, onb *nb,
                        uint64_t *cnt)
 {
@@ -757,17 +871,21 @@ static int accept_move(const osim *S, uint32_t sweep, int i, const double xn[3],
     }
     if (!(S->lambda > 0.0)) return 1;
 
-    /* N_p ~ Poisson(z_p |V_0|) depletants uniform in V_0 (Sec. III.B step 2). */
+    /* N_p ~ Poisson(z_p |V_0|) depletants uniform in V_0 (Sec. III.B step 2);
+     * V_0 is the circumsphere, or the shell of level lvl > 0 (Sec. III.C). */
     uint32_t wp[4];
     draw(S->key, sweep, tag, P_POISSON, 0, 0, wp);
-    int n_p = poisson_invert(S->F, S->nF, u53(wp[0], wp[1]));
+    int n_p = lvl > 0 ? poisson_invert(S->sF[lvl - 1], S->snF[lvl - 1], u53(wp[0], wp[1]))
+                      : poisson_invert(S->F, S->nF, u53(wp[0], wp[1]));
     cnt[C_DEP_DRAWN] += (uint64_t)n_p;
     uint32_t t = 0, t_max = 64u * (uint32_t)(n_p + 1);
     int n_block = 0;
     double W = 1.0;
     for (int k = 0; k < n_p; ++k) {
         double e[3];
-        if (!next_in_ball(S, sweep, tag, P_DEP, 0, &t, t_max, e)) {
+        int got = lvl > 0 ? next_in_shell(S, lvl, sweep, tag, &t, t_max, e)
+                          : next_in_ball(S, sweep, tag, P_DEP, 0, &t, t_max, e);
+        if (!got) {
             cnt[C_CAP]++;
             break;
         }
@@ -869,6 +987,7 @@ static void trial_move(const osim *S, uint32_t sweep, int i, const int ci[3],
     double qn[4] = {1.0, 0.0, 0.0, 0.0};
     if (qo) { qn[0] = qo[0]; qn[1] = qo[1]; qn[2] = qo[2]; qn[3] = qo[3]; }
     double o[3] = {0.0, 0.0, 0.0};
+    int lvl = 0;
 
     if (translate) {
         cnt[C_TRANSLATE]++;
@@ -886,12 +1005,13 @@ static void trial_move(const osim *S, uint32_t sweep, int i, const int ci[3],
             }
         }
         for (int d = 0; d < 3; ++d) o[d] = min_image(pos[3 * i + d] - xn[d], S->L);
+        if (S->v0_mode == 1) lvl = shell_level_words(w);
     } else if (!propose_rotation(S->key, sweep, tag, S->alpha, qo, qn)) {
         cnt[C_CAP]++;
         return;
     }
 
-    if (!accept_move(S, sweep, i, xn, qn, o, qo, ci, pos, quat, cell_start,
+    if (!accept_move(S, sweep, i, xn, qn, o, qo, lvl, ci, pos, quat, cell_start,
                      cell_idx, nb, cnt))
         return;
 
@@ -914,11 +1034,16 @@ int oracle_auto_cells(double L, double R_circ, double q)
     return nc;
 }
 
-static void sim_free(osim *S) { free(S->F); S->F = NULL; }
+static void sim_free(osim *S)
+{
+    free(S->F);
+    S->F = NULL;
+    for (int k = 0; k < SHELL_LEVELS; ++k) { free(S->sF[k]); S->sF[k] = NULL; }
+}
 
 static int sim_init(osim *S, int n, double L, int shape,
                     const double *shape_params, int n_shape_params, double q,
-                    double n_r, int n_trial, int cb_mode, double d_max,
+                    double n_r, int n_trial, int cb_mode, int v0_mode, double d_max,
                     double a_max, double p_translate, uint64_t seed,
                     uint32_t replica, int n_cell, int brute_force)
 {
@@ -955,6 +1080,26 @@ static int sim_init(osim *S, int n, double L, int shape,
         S->nF = oracle_poisson_table(S->lambda, S->F, cap);
         if (S->nF < 0) { sim_free(S); return -1; }
     }
+    /* shell V_0: spheres only (anisotropic colloids keep the circumsphere) */
+    if ((v0_mode != 0 && v0_mode != 1) || (v0_mode == 1 && shape != SHAPE_SPHERE)) {
+        sim_free(S);
+        return -1;
+    }
+    S->v0_mode = v0_mode;
+    S->R_s4 = S->R_s2 * S->R_s2;
+    S->dd = (sqrt(3.0) * d_max) / 32.0;
+    if (v0_mode == 1) {
+        for (int k = 1; k <= SHELL_LEVELS; ++k) {
+            shell_geometry(S->R_s, S->dd, k, &S->s_rin[k - 1], &S->s_h[k - 1]);
+            if (!(S->lambda > 0.0)) continue;
+            int cap = 8192;
+            S->sF[k - 1] = (double *)malloc(sizeof(double) * (size_t)cap);
+            if (!S->sF[k - 1]) { sim_free(S); return -1; }
+            double lam = oracle_shell_lambda(S->R_s, S->s_rin[k - 1], n_r);
+            S->snF[k - 1] = oracle_poisson_table(lam, S->sF[k - 1], cap);
+            if (S->snF[k - 1] < 0) { sim_free(S); return -1; }
+        }
+    }
     return 0;
 }
 
@@ -966,7 +1111,7 @@ static int sim_init(osim *S, int n, double L, int shape,
  */
 int oracle_run(int n, double L, int shape, const double *shape_params,
                int n_shape_params, double q, double n_r, int n_trial,
-               int cb_mode, double d_max, double a_max, double p_translate,
+               int cb_mode, int v0_mode, double d_max, double a_max, double p_translate,
                uint64_t seed, uint32_t replica, int n_cell, int brute_force,
                double *pos, double *quat, uint64_t sweep0, int n_sweeps,
                uint64_t *counters, int hist_bins, double hist_rmax,
@@ -975,7 +1120,7 @@ int oracle_run(int n, double L, int shape, const double *shape_params,
     osim S;
     if (!pos || !counters || n_sweeps < 0) return -1;
     if (sim_init(&S, n, L, shape, shape_params, n_shape_params, q, n_r, n_trial,
-                 cb_mode, d_max, a_max, p_translate, seed, replica, n_cell,
+                 cb_mode, v0_mode, d_max, a_max, p_translate, seed, replica, n_cell,
                  brute_force) != 0)
         return -1;
     int ncell = S.nc * S.nc * S.nc;
@@ -1037,7 +1182,8 @@ out:
  */
 long oracle_acceptance(int n, double L, int shape, const double *shape_params,
                        int n_shape_params, double q, double n_r, int n_trial,
-                       int cb_mode, uint64_t seed, const double *pos,
+                       int cb_mode, int v0_mode, double d_max, uint64_t seed,
+                       const double *pos,
                        const double *quat, int i, const double *xn_in,
                        const double *qn_in, uint64_t sweep0, long n_rep,
                        uint64_t *counters)
@@ -1045,7 +1191,7 @@ long oracle_acceptance(int n, double L, int shape, const double *shape_params,
     osim S;
     if (!pos || !xn_in || i < 0 || i >= n || n_rep < 0 || !counters) return -1;
     if (sim_init(&S, n, L, shape, shape_params, n_shape_params, q, n_r, n_trial,
-                 cb_mode, 0.0, 0.0, 1.0, seed, 0, 0, 1) != 0)
+                 cb_mode, v0_mode, d_max, 0.0, 1.0, seed, 0, 0, 1) != 0)
         return -1;
     onb *nb = (onb *)malloc(sizeof(onb) * (size_t)n);
     if (!nb) { sim_free(&S); return -1; }
@@ -1057,10 +1203,23 @@ long oracle_acceptance(int n, double L, int shape, const double *shape_params,
     double o[3];
     for (int d = 0; d < 3; ++d) o[d] = min_image(pos[3 * i + d] - xn[d], L);
     int ci[3] = {0, 0, 0};
+    /* shell V_0 for a given displacement: the thinnest level whose shell
+     * holds every point that overlaps the new pose but not the old one */
+    int lvl = 0;
+    if (S.v0_mode == 1) {
+        double dl = sqrt((o[0] * o[0] + o[1] * o[1]) + o[2] * o[2]);
+        lvl = 1;
+        while (lvl < SHELL_LEVELS && S.s_h[lvl - 1] < dl) ++lvl;
+        if (S.s_h[lvl - 1] < dl && S.s_rin[lvl - 1] > 0.0) {
+            free(nb);
+            sim_free(&S);
+            return -1;
+        }
+    }
     long acc = 0;
     for (long r = 0; r < n_rep; ++r)
         acc += accept_move(&S, (uint32_t)(sweep0 + (uint64_t)r), i, xn, qn, o, qo,
-                           ci, pos, quat, NULL, NULL, nb, counters);
+                           lvl, ci, pos, quat, NULL, NULL, nb, counters);
     free(nb);
     sim_free(&S);
     return acc;

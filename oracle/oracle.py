@@ -25,6 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 SHAPE_SPHERE, SHAPE_HEMISPHERE, SHAPE_SPHEROID = 0, 1, 2
+V0_CIRCUMSPHERE, V0_SHELL = 0, 1
 
 # counter slots of oracle_run
 COUNTERS = ("moves", "accept", "reject_cell", "reject_overlap", "reject_depletant",
@@ -87,7 +88,7 @@ def lib():
             L.oracle_run.argtypes = [
                 ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, ctypes.c_int,
                 ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                 ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
                 dp, dp, ctypes.c_uint64, ctypes.c_int, u64p,
                 ctypes.c_int, ctypes.c_double, u64p]
@@ -97,7 +98,7 @@ def lib():
             L.oracle_acceptance.argtypes = [
                 ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, ctypes.c_int,
                 ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                ctypes.c_uint64, dp, dp, ctypes.c_int, dp, dp, ctypes.c_uint64,
+                ctypes.c_int, ctypes.c_double, ctypes.c_uint64, dp, dp, ctypes.c_int, dp, dp, ctypes.c_uint64,
                 ctypes.c_long, u64p]
             L.oracle_acceptance.restype = ctypes.c_long
             L.oracle_free_volume.argtypes = [
@@ -113,6 +114,14 @@ def lib():
                                                    ctypes.c_uint32, ctypes.c_uint32,
                                                    ctypes.c_double, dp, dp]
             L.oracle_rotation_proposal.restype = ctypes.c_int
+            L.oracle_shell_level.argtypes = [u32p]
+            L.oracle_shell_level.restype = ctypes.c_int
+            L.oracle_shell_lambda.argtypes = [ctypes.c_double] * 3
+            L.oracle_shell_lambda.restype = ctypes.c_double
+            L.oracle_shell_points.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                              ctypes.c_uint64, ctypes.c_uint32,
+                                              ctypes.c_uint32, ctypes.c_uint32, dp]
+            L.oracle_shell_points.restype = ctypes.c_long
             _lib = L
     return _lib
 
@@ -163,10 +172,12 @@ def poisson_sample(F, u):
 
 
 def acceptance(pos, L, i, xn, *, shape=SHAPE_SPHERE, shape_params=(1.0,), q=0.0,
-               n_r=0.0, n_trial=0, cb_mode=0, seed=1, quat=None, qn=None,
-               sweep0=0, n_rep=1000):
+               n_r=0.0, n_trial=0, cb_mode=0, v0_mode=0, d_max=0.0, seed=1, quat=None,
+               qn=None, sweep0=0, n_rep=1000):
     """How many of n_rep independent evaluations accept the fixed proposed move
-    of colloid i to position xn (and orientation qn).  Returns (count, counters)."""
+    of colloid i to position xn (and orientation qn).  Returns (count, counters).
+    v0_mode 1 samples depletants in the thinnest shell level (of a system with
+    step size d_max) that holds the move's lens."""
     pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
     sp = np.ascontiguousarray(shape_params, dtype=np.float64)
     x = np.ascontiguousarray(xn, dtype=np.float64)
@@ -175,8 +186,8 @@ def acceptance(pos, L, i, xn, *, shape=SHAPE_SPHERE, shape_params=(1.0,), q=0.0,
     cnt = np.zeros(N_COUNTERS, dtype=np.uint64)
     a = lib().oracle_acceptance(
         pos.shape[0], float(L), int(shape), _p(sp, ctypes.c_double), len(sp),
-        float(q), float(n_r), int(n_trial), int(cb_mode), int(seed),
-        _p(pos, ctypes.c_double),
+        float(q), float(n_r), int(n_trial), int(cb_mode), int(v0_mode), float(d_max),
+        int(seed), _p(pos, ctypes.c_double),
         _p(qa, ctypes.c_double) if qa is not None else None, int(i),
         _p(x, ctypes.c_double), _p(qb, ctypes.c_double) if qb is not None else None,
         int(sweep0), int(n_rep), _p(cnt, ctypes.c_uint64))
@@ -211,7 +222,7 @@ def cell_list(pos, L, nc, seed, replica, sweep):
 
 
 def run(pos, L, *, shape=SHAPE_SPHERE, shape_params=(1.0,), q=0.0, n_r=0.0,
-        n_trial=0, cb_mode=0, d_max=0.1, a_max=0.0, p_translate=1.0, seed=1,
+        n_trial=0, cb_mode=0, v0_mode=0, d_max=0.1, a_max=0.0, p_translate=1.0, seed=1,
         replica=0, n_cell=0, brute_force=False, quat=None, sweep0=0, n_sweeps=1,
         hist_bins=0, hist_rmax=0.0):
     """Run the serial sampler in place on copies of pos/quat.
@@ -227,7 +238,7 @@ def run(pos, L, *, shape=SHAPE_SPHERE, shape_params=(1.0,), q=0.0, n_r=0.0,
     hist = np.zeros(max(hist_bins, 1), dtype=np.uint64) if hist_bins > 0 else None
     rc = lib().oracle_run(
         n, float(L), int(shape), _p(sp, ctypes.c_double), len(sp), float(q),
-        float(n_r), int(n_trial), int(cb_mode), float(d_max), float(a_max),
+        float(n_r), int(n_trial), int(cb_mode), int(v0_mode), float(d_max), float(a_max),
         float(p_translate), int(seed), int(replica), int(n_cell),
         int(bool(brute_force)), _p(pos, ctypes.c_double),
         _p(qa, ctypes.c_double) if qa is not None else None,
@@ -238,6 +249,26 @@ def run(pos, L, *, shape=SHAPE_SPHERE, shape_params=(1.0,), q=0.0, n_r=0.0,
         raise ValueError("oracle_run rejected its arguments (rc=%d)" % rc)
     counters = {name: int(cnt[i]) for i, name in enumerate(COUNTERS)}
     return pos, qa, counters, hist
+
+
+def shell_level(w0, w1, w2):
+    """Shell level (1..32) of a translation drawn from move words w0..w2."""
+    w = np.array([w0, w1, w2], dtype=np.uint32)
+    return lib().oracle_shell_level(_p(w, ctypes.c_uint32))
+
+
+def shell_lambda(R_s, R_in, n_r):
+    return lib().oracle_shell_lambda(float(R_s), float(R_in), float(n_r))
+
+
+def shell_points(R_s, d_max, lvl, n_att, *, seed=1, sweep=0, tag=0):
+    """Points the shell generator accepts among n_att attempts (n x 3)."""
+    e = np.zeros((max(n_att, 1), 3))
+    m = lib().oracle_shell_points(float(R_s), float(d_max), int(lvl), int(seed), int(sweep),
+                                  int(tag), int(n_att), _p(e, ctypes.c_double))
+    if m < 0:
+        raise ValueError("oracle_shell_points rejected its arguments")
+    return e[:m].copy()
 
 
 def free_volume(pos, L, q, *, shape=SHAPE_SPHERE, shape_params=(1.0,), quat=None,
