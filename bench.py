@@ -121,7 +121,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sms)}
 
 
-def cpu_oracle_rate(systems, d_max, sweeps, first_sweep=0):
+def cpu_oracle_rate(systems, d_max, sweeps, first_sweep=0, v0_mode=0):
     """Moves/s and insertions/s of the serial oracle on this host (1 core)."""
     from oracle import oracle as O
     O.build()
@@ -129,7 +129,8 @@ def cpu_oracle_rate(systems, d_max, sweeps, first_sweep=0):
     moves = drawn = evaluated = 0
     for s in systems:
         _, _, c, _ = O.run(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=d_max[s.extra["eta_r"]],
-                           seed=s.seed, replica=s.replica, n_sweeps=sweeps, sweep0=first_sweep)
+                           seed=s.seed, replica=s.replica, n_sweeps=sweeps, sweep0=first_sweep,
+                           v0_mode=v0_mode)
         moves += c["moves"]
         drawn += c["dep_drawn"]
         evaluated += c["dep_evaluated"]
@@ -155,7 +156,8 @@ def run_reference(args, ws, rank):
         eta = s.extra["eta_r"]
         t0 = time.perf_counter()
         p, _, c, _ = O.run(pos[eta], s.L, q=s.q, n_r=s.n_r, d_max=D_MAX_TUNED[eta], seed=1,
-                           n_sweeps=1, sweep0=step // len(systems))
+                           n_sweeps=1, sweep0=step // len(systems),
+                           v0_mode=1 if args.v0 == "shell" else 0)
         dt = time.perf_counter() - t0
         pos[eta] = p
         if step >= args.warmup:
@@ -170,7 +172,7 @@ def run_reference(args, ws, rank):
         "unit": "moves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": "serial CPU oracle",
+        "config": {"workload": WORKLOAD, "form": "serial CPU oracle", "v0": args.v0,
                    "step": "one sweep of one of the four eta_r systems (16384 moves)"},
         "insertions_drawn_per_s": drawn / total,
         "insertions_evaluated_per_s": evaluated / total,
@@ -478,6 +480,8 @@ def run_ours(args, ws, rank, local):
              for k, (s, e) in enumerate(zip(systems, etas))]
     ctx = hpmc.hpmc_init_batch(descs, seed=1, precision=prec, device=local)
     hpmc.hpmc_set_launch(ctx, args.warps, args.ilp)
+    if args.v0 == "shell":
+        hpmc.hpmc_set_v0(ctx, hpmc.HPMC_V0_SHELL)
     ns = [s.n for s in systems]
     d0 = [D_MAX_TUNED[e] for e in etas]
     dtuned = d0 if args.no_tune else tune_batch(ctx, hpmc, d0, ns)
@@ -524,6 +528,45 @@ def run_ours(args, ws, rank, local):
     hpmc.hpmc_set_timing(ctx, False)
     _, tc = hpmc.hpmc_get_state(ctx)
     t_moves, t_eval, t_drawn = tc["moves"], tc["dep_evaluated"], tc["dep_drawn"]
+
+    # the same batch with the shell-restricted V_0 (Sec. III.C remark), same
+    # step sizes: reported beside the headline, which keeps the circumsphere
+    shell = None
+    if args.v0 == "circumsphere" and not args.no_shell:
+        hpmc.hpmc_set_v0(ctx, hpmc.HPMC_V0_SHELL)
+        for _ in range(args.warmup):
+            step()
+        hpmc.hpmc_reset_counters(ctx)
+        torch.cuda.synchronize()
+        sh_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        sh_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            sh_a[k].record(stream)
+            step()
+            sh_b[k].record(stream)
+        torch.cuda.synchronize()
+        sh_ms = sum(a.elapsed_time(b) for a, b in zip(sh_a, sh_b))
+        _, sc = hpmc.hpmc_get_state(ctx)
+        hpmc.hpmc_reset_counters(ctx)
+        hpmc.hpmc_set_timing(ctx, True)
+        for k in range(timing_steps):
+            flush.zero_()
+            step()
+        sk_ms, sk_n = hpmc.hpmc_get_timing(ctx)
+        hpmc.hpmc_set_timing(ctx, False)
+        hpmc.hpmc_set_v0(ctx, hpmc.HPMC_V0_CIRCUMSPHERE)
+        sh_ms = R.reduce_max([sh_ms], "cuda")[0]
+        sh_moves, sh_drawn = R.reduce_sum([sc["moves"], sc["dep_drawn"]], "cuda")
+        shell = {"value": sh_moves / (sh_ms * 1e-3), "unit": "moves/s",
+                 "ms_per_step": sh_ms / args.steps, "steps": args.steps,
+                 "insertions_drawn_per_s": sh_drawn / (sh_ms * 1e-3),
+                 "acceptance": sc["accept"] / max(1, sc["moves"]),
+                 "fp64_rechecks_per_move": sc["rechecks"] / max(1, sc["moves"]),
+                 "lens_ms_per_launch": sk_ms[2] / max(1, sk_n[2]),
+                 "phase_ms_per_launch": sk_ms[1] / max(1, sk_n[1]),
+                 "note": "V_0 = the excluded-volume shell of the move's level; same "
+                         "acceptance probabilities, fewer depletants per move"}
 
     # the same four systems one at a time (separate contexts, one stream)
     allpos = np.empty((sum(ns), 3))
@@ -597,6 +640,7 @@ def run_ours(args, ws, rank, local):
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "form": "FP32+FP64 recheck" if prec == 1 else "FP64",
+                       "v0": args.v0,
                        "n_trial": 0, "step": "1 sweep of each of 4 systems (65536 moves)",
                        "schedule": "4 systems as one batch (one set of launches per sweep)",
                        "d_max": {str(k): round(v, 5) for k, v in dmax.items()},
@@ -625,11 +669,14 @@ def run_ours(args, ws, rank, local):
                     "h2d_bytes_per_step": sum(ns) * 3 * 8,
                     "d2h_bytes_per_step": sum(ns) * 3 * 8 + 8 * 16},
         }
+        if shell is not None:
+            line["shell_v0"] = shell
         if not args.no_cpu_baseline:
             # the oracle on the host on a bounded sample of the same workload
             for s in systems:
                 s.extra["eta_r"] = round(s.extra["eta_r"], 1)
-            mv, dr, ev, dt, nm = cpu_oracle_rate(systems, dmax, args.cpu_sweeps)
+            mv, dr, ev, dt, nm = cpu_oracle_rate(systems, dmax, args.cpu_sweeps,
+                                                 v0_mode=1 if args.v0 == "shell" else 0)
             line["cpu_baseline"] = {
                 "value": mv, "unit": "moves/s", "cores": 1, "kind": "oracle",
                 "sample": "%d sweep(s) of each of the 4 systems from the fcc start "
@@ -656,6 +703,12 @@ def main():
                     help="spheres_16384: the headline four-state-point workload; batched: "
                          "128 replicas of uneven size and state point; hemispheres / "
                          "discoids: 32768 hemispheres or 65536 discoids with rotations")
+    ap.add_argument("--v0", choices=("circumsphere", "shell"), default="circumsphere",
+                    help="depletant region V_0 of the spheres workload: the new pose's "
+                         "circumsphere (the paper's; default, with a shell measurement "
+                         "alongside) or the excluded-volume shell of the move")
+    ap.add_argument("--no-shell", action="store_true",
+                    help="skip the shell-V_0 measurement beside the headline")
     ap.add_argument("--cpu-sweeps-shape", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sweeps", type=int, default=25)

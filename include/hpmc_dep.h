@@ -53,6 +53,9 @@ extern "C" {
 #define HPMC_FP64 0            /* every overlap test in FP64 */
 #define HPMC_FP32_RECHECK 1    /* FP32 tests with a certified margin, FP64 recheck near contact */
 
+#define HPMC_V0_CIRCUMSPHERE 0 /* depletants sampled in the new pose's circumsphere (default) */
+#define HPMC_V0_SHELL 1        /* spheres: in the shell that can hold the move's lens */
+
 #define HPMC_HOST 0
 #define HPMC_DEVICE 1
 
@@ -177,9 +180,28 @@ int hpmc_autotune(hpmc_ctx *ctx, const int *warps, int nw, const int *cells, int
  * is re-taken in FP64.  0 selects the derived certified bound (default);
  * a value below that bound is rejected with HPMC_ERR_ARG at the next sweep.
  * For the anisotropic shapes a value above the derived distance margins of
- * the depletant tests and of the pair certificates replaces them as well.
+ * the depletant tests and of the pair certificates replaces them as well;
+ * with the shell V_0 it also widens the FP32 shell-acceptance band by that
+ * fraction of r^4 (1 sends every shell decision to FP64).
  * Larger margins only move more decisions to the exact FP64 path. */
 int hpmc_set_fp32_margin(hpmc_ctx *ctx, double margin);
+
+/* Depletant sampling region V_0 (Sec. III.C).  HPMC_V0_CIRCUMSPHERE (default):
+ * N_p ~ Poisson(z_p |V_0|) depletants uniform in the circumsphere of
+ * diameter d_colloid + d_depletant around the moved colloid's new pose.
+ * HPMC_V0_SHELL (spheres only; the restriction to the excluded-volume shell
+ * the paper remarks on): a translation by D only needs the shell
+ * R_s - t_k <= |e - x'| < R_s, where t_k = k sqrt(3) d_max / 32 + 1e-9 R_s is
+ * the thickness of level k (1..32), the smallest whose integer rule bounds
+ * |D| from the move's random words; N_p ~ Poisson(z_p |shell_k|).  A shell
+ * point takes attempt t's words: v = (s11(w0), s11(w1), s11(w2)),
+ * r = R_in + t_k u01(w3), accepted iff |v|^6 R_s^4 < r^4, e = v r / |v|.
+ * Acceptance probabilities are those of the circumsphere (the blocking
+ * depletants form the same Poisson process), so the sampled ensemble is the
+ * same; the trajectory and the counters dep_drawn and dep_evaluated are
+ * those of the shell.  HPMC_ERR_ARG for an anisotropic shape or an unknown
+ * mode.  Takes effect at the next sweep. */
+int hpmc_set_v0(hpmc_ctx *ctx, int mode);
 
 /* Per-kernel timing.  While on, hpmc_sweep launches its kernels one by one
  * (no graph) with CUDA events around the cell-list kernels and around every

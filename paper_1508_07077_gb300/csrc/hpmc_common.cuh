@@ -155,7 +155,48 @@ struct Rep {
     // (a + r, c + r) and of the outer spheroid, and the squared thresholds
     float sp_iA2, sp_iC2, sp_inA, sp_inC, sp_outA, sp_outC, sp_kin2, sp_kout2;
     double pad_cell_bound; // host: packing bound on a cell's population
+    // shell-restricted V_0 (spheres, translations): on when v0_shell; level k
+    // (1..kShellLevels) samples R_in <= |e| < R_s with R_in = sh_rin[k-1],
+    // thickness sh_h[k-1]; its Poisson table is the (k-1)-th block of nF
+    // entries at t_off
+    int v0_shell;
+    double dd;             // level thickness step sqrt(3) d_max / 32
+    double R_s4;           // R_s^4
+    float R_s4_32;
+    float shell_band;      // extra relative band of the FP32 shell test (caller's margin)
+    double sh_rin[32], sh_h[32];
+    float sh_rin32[32], sh_h32[32];
 };
+
+constexpr int kShellLevels = 32;
+
+// Shell level of a translation from its move words (integer rule).  The
+// displacement is D_d = d_max n_d 2^-32 with n_d = 2 w_d + 1 - 2^32 (odd,
+// |n_d| < 2^32).  a_d = floor(|n_d| / 2^16) + 1 exceeds |n_d| / 2^16, so with
+// S = a_0^2 + a_1^2 + a_2^2 the move length obeys |D| < d_max sqrt(S) 2^-16;
+// the level is the smallest k >= 1 with S <= 3 k^2 2^22, which makes
+// |D| < k sqrt(3) d_max / 32, the level's thickness.
+__host__ __device__ __forceinline__ int shell_level(uint32_t w0, uint32_t w1, uint32_t w2)
+{
+    const uint32_t w[3] = {w0, w1, w2};
+    unsigned long long S = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        // |n_d| >> 16 without 64-bit signed arithmetic: |2 w + 1 - 2^32| is
+        // 2 (w - 2^31) + 1 for w >= 2^31 and 2 (2^31 - w) - 1 below
+        const unsigned long long n = w[d] >= 0x80000000u
+                                         ? 2ull * (unsigned long long)(w[d] - 0x80000000u) + 1ull
+                                         : 2ull * (unsigned long long)(0x80000000u - w[d]) - 1ull;
+        const unsigned long long a = (n >> 16) + 1ull;
+        S += a * a;
+    }
+    // k = ceil(sqrt(S / (3 2^22))) by a float estimate, fixed up exactly
+    int k = (int)ceilf(sqrtf((float)S * (1.0f / 12582912.0f)));
+    k = k < 1 ? 1 : (k > kShellLevels ? kShellLevels : k);
+    while (k > 1 && S <= ((3ull * (unsigned long long)((k - 1) * (k - 1))) << 22)) --k;
+    while (k < kShellLevels && S > ((3ull * (unsigned long long)(k * k)) << 22)) ++k;
+    return k;
+}
 
 struct SimParams {
     int n_rep, n_total, cap, lens_cap;
@@ -230,6 +271,26 @@ __device__ __forceinline__ double min_image(double d, double L, double half_L)
 __device__ __forceinline__ double norm2(double a, double b, double c)
 {
     return (a * a + b * b) + c * c;
+}
+
+// Attempt w of the shell generator at level lvl, FP64 in the specification's
+// operation order: v_d = s11(w_d) uniform in the cube, r = R_in + h u01(w_3)
+// uniform in [R_in, R_s); accepted iff |v|^6 R_s^4 < r^4 (that is
+// |v|^3 < (r / R_s)^2: for v in the unit ball |v|^3 is uniform and
+// independent of the direction, so the accepted r has density ~ r^2 and e is
+// uniform in the shell); the point is e = v (r / |v|).
+__device__ __forceinline__ bool shell_point64(const Rep &R, int lvl, uint4 w, double &e0, double &e1,
+                                              double &e2)
+{
+    const double v0 = s11(w.x), v1 = s11(w.y), v2 = s11(w.z);
+    const double p2 = (v0 * v0 + v1 * v1) + v2 * v2;
+    const double r = R.sh_rin[lvl - 1] + R.sh_h[lvl - 1] * u01(w.w);
+    const double r2 = r * r;
+    const double sc = r / sqrt(p2);
+    e0 = v0 * sc;
+    e1 = v1 * sc;
+    e2 = v2 * sc;
+    return ((p2 * p2) * p2) * R.R_s4 < r2 * r2;
 }
 
 __device__ __forceinline__ double wrap_box(double x, double L)

@@ -39,6 +39,7 @@ struct Params {
     int warps = 1;
     int ilp = 1;
     double margin = 0.0;
+    int v0_mode = HPMC_V0_CIRCUMSPHERE;
 };
 
 // one replica as the caller described it
@@ -220,11 +221,45 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
         // lens points pack the attempt index t < 64 (N_p + 1) into 16 bits
         if (c->precision == HPMC_FP32_RECHECK && F.size() > 1023) return HPMC_ERR_CAP;
     }
+    // shell-restricted V_0 (Sec. III.C, closing remark; spheres only): level k
+    // samples R_in <= |e| < R_s with thickness k dd + 1e-9 R_s, dd =
+    // sqrt(3) d_max / 32, which exceeds the length of every move of that
+    // level.  One Poisson table per level, each padded to the longest with
+    // entries no 53-bit uniform reaches (2.0), so that level k's table is the
+    // block of nF entries at (k - 1) nF.
+    int shell_stride = 0;
+    if (p.v0_mode == HPMC_V0_SHELL) {
+        if (p.shape != HPMC_SPHERE) return HPMC_ERR_ARG;
+        R.dd = (std::sqrt(3.0) * h.d_max) / 32.0;
+        std::vector<double> Fl[kShellLevels];
+        for (int k = 1; k <= kShellLevels; ++k) {
+            const double t = (double)k * R.dd + 1e-9 * R_s;
+            double rin = R_s - t;
+            if (rin < 0.0) rin = 0.0;
+            R.sh_rin[k - 1] = rin;
+            R.sh_h[k - 1] = R_s - rin;
+            R.sh_rin32[k - 1] = (float)rin;
+            R.sh_h32[k - 1] = (float)R.sh_h[k - 1];
+            if (!(lambda > 0.0)) continue;
+            const double vs = ((4.0 / 3.0) * kPi) * (((R_s * R_s) * R_s) - ((rin * rin) * rin));
+            int rc = build_table(h.n_r * vs, Fl[k - 1]);
+            if (rc != HPMC_OK) return rc;
+            if ((int)Fl[k - 1].size() > shell_stride) shell_stride = (int)Fl[k - 1].size();
+        }
+        if (lambda > 0.0) {
+            F.clear();
+            for (int k = 0; k < kShellLevels; ++k) {
+                F.insert(F.end(), Fl[k].begin(), Fl[k].end());
+                F.resize((size_t)(k + 1) * (size_t)shell_stride, 2.0);
+            }
+            R.v0_shell = 1;
+        }
+    }
     R.n = h.n;
     R.nc = nc;
     R.half_nc = nc / 2;
     R.n_stencil = nc == 2 ? 2 : 3;
-    R.nF = (int)F.size();
+    R.nF = R.v0_shell ? shell_stride : (int)F.size();
     R.has_dep = lambda > 0.0 ? 1 : 0;
     R.n_trial = h.n_trial;
     R.key0 = (uint32_t)c->seed;
@@ -234,6 +269,11 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
     R.w = w;
     R.R_s = R_s;
     R.R_s2 = R_s * R_s;
+    R.R_s4 = R.R_s2 * R.R_s2;
+    R.R_s4_32 = (float)R.R_s4;
+    // a margin set by the caller also widens the shell test's band (a margin
+    // >= 1 sends every shell decision to FP64)
+    R.shell_band = (float)p.margin;
     const double Rd = 0.5 * p.sp[0] + 0.5 * h.q;
     R.R_dep2 = Rd * Rd;
     R.contact2 = p.sp[0] * p.sp[0];
@@ -260,7 +300,9 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
     // least 1e-5.
     const double u = 0x1p-24;
     const double Wc = w > 1.0 ? w : 1.0;
-    const double E = 40.0 * u * Wc;
+    // (a shell point, built from its direction and radius, errs by <= 16 u R_s
+    // per component instead of 6 u R_s)
+    const double E = 40.0 * u * Wc + (R.v0_shell ? 12.0 * u * R_s : 0.0);
     const double Rmax = std::sqrt(std::fmax(R.R_s2, R.contact2));
     const double bound = 2.0 * std::sqrt(3.0) * Rmax * E + 3.0 * E * E + 4.0 * u * Rmax * Rmax + 1e-12;
     const double m_r2 = std::fmax(1e-5, 2.0 * bound);
@@ -459,7 +501,10 @@ void launch_lens(hpmc_ctx *c, const SimParams &P, cudaStream_t s)
 {
     if (c->precision != HPMC_FP32_RECHECK) return;
     if (c->prm.shape == HPMC_SPHERE) {
-        launch_pdl1(k_lens_sphere_fp32, (c->n_total + 3) / 4, 128, s, P);
+        if (c->prm.v0_mode == HPMC_V0_SHELL)
+            launch_pdl1(k_lens_sphere_fp32<true>, (c->n_total + 3) / 4, 128, s, P);
+        else
+            launch_pdl1(k_lens_sphere_fp32<false>, (c->n_total + 3) / 4, 128, s, P);
     } else {
         k_propose_aniso<<<(c->n_total + 127) / 128, 128, 0, s>>>(P);
         k_lens_aniso_fp32<<<(c->n_total + 3) / 4, 128, 0, s>>>(P);
@@ -1165,6 +1210,15 @@ int hpmc_set_fp32_margin(hpmc_ctx *c, double margin)
 {
     if (!c || !(margin >= 0.0) || margin > 1e3) return HPMC_ERR_ARG;
     c->prm.margin = margin;
+    c->dirty = true;
+    return HPMC_OK;
+}
+
+int hpmc_set_v0(hpmc_ctx *c, int mode)
+{
+    if (!c || (mode != HPMC_V0_CIRCUMSPHERE && mode != HPMC_V0_SHELL)) return HPMC_ERR_ARG;
+    if (mode == HPMC_V0_SHELL && c->prm.shape != HPMC_SPHERE) return HPMC_ERR_ARG;
+    c->prm.v0_mode = mode;
     c->dirty = true;
     return HPMC_OK;
 }

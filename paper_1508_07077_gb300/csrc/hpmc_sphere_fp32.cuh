@@ -117,6 +117,8 @@ __device__ __noinline__ bool exact_ball(const SimParams &P, const Rep &R, uint4 
 //   what 1: forward CB trial y = o + e (around the old reference point) vs the new pose
 //   what 2: point e vs neighbour j
 //   what 3: forward CB trial y = o + e vs neighbour j
+// e = R_s (s11(w.x), s11(w.y), s11(w.z)): a circumsphere point (a depletant
+// with the circumsphere V_0, or a CB trial).
 __device__ __noinline__ bool exact_dep(const SimParams &P, const Rep &R, uint32_t sweep, int i, uint4 w, int what,
                                        int j, const int *acc, int nacc)
 {
@@ -135,14 +137,98 @@ __device__ __noinline__ bool exact_dep(const SimParams &P, const Rep &R, uint32_
     return SphereFP64::dep(R, v0 - c0, v1 - c1, v2 - c2);
 }
 
+// Exact FP64 coordinates of attempt w of colloid i's depletant stream with
+// the shell V_0 (a point of the level of i's move).
+__device__ __noinline__ double3 shell_dep_point64(const Rep &R, uint32_t sweep, int i, uint4 w)
+{
+    const uint4 wm = draw(R.key0, R.key1, sweep, (uint32_t)(i - R.off), kPMove, 0, 0);
+    double3 e;
+    (void)shell_point64(R, shell_level(wm.x, wm.y, wm.z), w, e.x, e.y, e.z);
+    return e;
+}
+
+// The same tests for a depletant of the shell V_0 (attempt w of colloid i's
+// stream): what 0: vs the old pose;  what 4: vs the new pose
+__device__ __noinline__ bool exact_dep_shell(const SimParams &P, const Rep &R, uint32_t sweep, int i, uint4 w,
+                                             int what)
+{
+    const double3 e = shell_dep_point64(R, sweep, i, w);
+    if (what == 4) return SphereFP64::dep(R, e.x, e.y, e.z);
+    const Move64 m = move64(P, R, sweep, i);
+    return SphereFP64::dep(R, e.x - m.o0, e.y - m.o1, e.z - m.o2);
+}
+
 // A lens point (attempt t of the depletant stream) free of every neighbour?
 __device__ __noinline__ bool exact_free_nb(const SimParams &P, const Rep &R, uint32_t sweep, int i, uint32_t t,
                                            const float4 *nb, int nnb, const int *acc, int nacc)
 {
     const uint4 w = draw(R.key0, R.key1, sweep, (uint32_t)(i - R.off), kPDep, 0, t);
-    for (int a = 0; a < nnb; ++a)
-        if (exact_dep(P, R, sweep, i, w, 2, __float_as_int(nb[a].w), acc, nacc)) return false;
+    double e0, e1, e2;
+    if (R.v0_shell) {
+        const double3 e = shell_dep_point64(R, sweep, i, w);
+        e0 = e.x;
+        e1 = e.y;
+        e2 = e.z;
+    } else {
+        e0 = R.R_s * s11(w.x);
+        e1 = R.R_s * s11(w.y);
+        e2 = R.R_s * s11(w.z);
+    }
+    const Move64 m = move64(P, R, sweep, i);
+    for (int a = 0; a < nnb; ++a) {
+        double c0, c1, c2;
+        center64(P, R, m, pos_now(P, R, sweep, __float_as_int(nb[a].w), acc, nacc), c0, c1, c2);
+        if (SphereFP64::dep(R, e0 - c0, e1 - c1, e2 - c2)) return false;
+    }
     return true;
+}
+
+// Shell attempt decided in FP64 (the FP32 test was inside its margin):
+// returns acceptance and the point rounded to float.
+__device__ __noinline__ bool exact_shell_pt(const Rep &R, int lvl, uint4 w, float &e0, float &e1, float &e2)
+{
+    double d0, d1, d2;
+    const bool in = shell_point64(R, lvl, w, d0, d1, d2);
+    e0 = (float)d0;
+    e1 = (float)d1;
+    e2 = (float)d2;
+    return in;
+}
+
+// Shell attempt in FP32 (the acceptance |v|^6 R_s^4 < r^4 and the point
+// e = v r / |v|): 1 accepted and e set, 0 rejected, -1 undecided in FP32.
+// Error bounds, u = 2^-24, against the FP64 values the specification
+// defines: v_d = float(w_d - 2^31) 2^-31 errs by <= u |v_d| + 2^-31, so for
+// |v| >= 2^-7 the FP32 |v|^2 errs by <= 12 u |v|^2 (relative); r =
+// fma(h, float(w_3) 2^-32, R_in) errs by <= 5 u R_s.  Then |A32 - A| <=
+// 3 * 12 u A + 5 u A (A = |v|^6 R_s^4, five roundings) and |B32 - B| <=
+// 4 r^3 (5 u R_s) + 3 u B (B = r^4), and the decision is certain when B - A
+// exceeds twice their sum.  The point then errs by <= 16 u R_s per component
+// (direction 2 u r, radius 5 u R_s, |v|^2 in the scale 6 u r, sqrt, division
+// and product 3 u r).  |v| < 2^-7 (probability 2^-21) is left to FP64.
+__device__ __forceinline__ int shell_point32(const Rep &R, float rin, float h, uint4 w, float &e0, float &e1,
+                                             float &e2)
+{
+    constexpr float u = 0x1p-24f;
+    const float v0 = __int2float_rn((int)(w.x ^ 0x80000000u)) * 0x1p-31f;
+    const float v1 = __int2float_rn((int)(w.y ^ 0x80000000u)) * 0x1p-31f;
+    const float v2 = __int2float_rn((int)(w.z ^ 0x80000000u)) * 0x1p-31f;
+    const float p2 = norm2f(v0, v1, v2);
+    const float r = __fmaf_rn(h, __uint2float_rn(w.w) * 0x1p-32f, rin);
+    const float r2 = r * r;
+    const float A = ((p2 * p2) * p2) * R.R_s4_32;
+    const float B = r2 * r2;
+    const float err = 2.0f * ((41.0f * u) * A + (20.0f * u) * R.R_s32 * (r * r2) + (3.0f * u) * B) +
+                      R.shell_band * B;
+    if (p2 < 0x1p-14f) return -1;
+    const float diff = B - A;
+    if (diff < -err) return 0;
+    if (!(diff > err)) return -1;
+    const float sc = __fdiv_rn(r, __fsqrt_rn(p2));
+    e0 = v0 * sc;
+    e1 = v1 * sc;
+    e2 = v2 * sc;
+    return 1;
 }
 
 // --- FP32 tests with exact fallback -----------------------------------------
@@ -311,6 +397,8 @@ __device__ __forceinline__ bool cb_pass(DepShared &sh, int tid, int nslots, doub
 // holds at most N_p <= (Poisson table length) points, the capacity it is
 // allocated with, so it cannot overflow.
 // ---------------------------------------------------------------------------
+// SHELL: V_0 is the shell of the move's level instead of the circumsphere.
+template <bool SHELL>
 __global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_constant__ SimParams P)
 {
     const int lane = threadIdx.x & 31;
@@ -339,8 +427,17 @@ __global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_consta
     }
     uint32_t rck = 0;
     const float o0 = -D0, o1 = -D1, o2 = -D2;
+    const unsigned long long *Tab = P.T + R.t_off;
+    int lvl = 0;
+    float rin32 = 0.0f, h32 = 0.0f;
+    if (SHELL) {
+        lvl = shell_level(wm.x, wm.y, wm.z);
+        Tab += (size_t)(lvl - 1) * (size_t)R.nF;
+        rin32 = R.sh_rin32[lvl - 1];
+        h32 = R.sh_h32[lvl - 1];
+    }
     const uint4 wp = draw(R.key0, R.key1, sweep, tag, kPPoisson, 0, 0);
-    const int n_p = poisson_count(P.T + R.t_off, R.nF, u53_int(wp.x, wp.y), lane);
+    const int n_p = poisson_count(Tab, R.nF, u53_int(wp.x, wp.y), lane);
     const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
     const RoundKeys K = round_keys(R.key0, R.key1);
     float4 *out = P.lens + (size_t)g * P.lens_cap;
@@ -354,23 +451,40 @@ __global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_consta
         int in = 0;
         if (t < t_max) {
             w = philox_rk(make_uint4(sweep, tag, kPDep << 24, t), K);
-            e0 = coord32(w.x, R.R_s32);
-            e1 = coord32(w.y, R.R_s32);
-            e2 = coord32(w.z, R.R_s32);
-            in = tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
+            if (SHELL) {
+                in = shell_point32(R, rin32, h32, w, e0, e1, e2);
+            } else {
+                e0 = coord32(w.x, R.R_s32);
+                e1 = coord32(w.y, R.R_s32);
+                e2 = coord32(w.z, R.R_s32);
+                in = tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
+            }
         }
         {
             const bool unsure = in == -1;
             if (__any_sync(kFull, unsure)) {
                 if (unsure) {
                     ++rck;
-                    in = exact_ball(P, R, w) ? 1 : 0;
+                    if (SHELL) in = exact_shell_pt(R, lvl, w, e0, e1, e2) ? 1 : 0;
+                    else in = exact_ball(P, R, w) ? 1 : 0;
                 }
             }
         }
         const unsigned bal = __ballot_sync(kFull, in == 1);
         const int k = k0 + __popc(bal & lt);
-        const bool dep = in == 1 && k < n_p;
+        bool dep = in == 1 && k < n_p;
+        if (SHELL) {
+            // a shell point overlaps the new pose unless it rounds onto R_s
+            int tn = dep ? tri(norm2f(e0, e1, e2), R.T_dep32, R.m_r2) : 1;
+            const bool unsure = tn == -1;
+            if (__any_sync(kFull, unsure)) {
+                if (unsure) {
+                    ++rck;
+                    tn = exact_dep_shell(P, R, sweep, i, w, 4) ? 1 : 0;
+                }
+            }
+            dep = dep && tn == 1;
+        }
         int to = 1;  // overlaps the old pose: 1 yes, 0 no, -1 within the margin
         if (dep) to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), R.T_dep32, R.m_r2);
         {
@@ -378,7 +492,8 @@ __global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_consta
             if (__any_sync(kFull, unsure)) {
                 if (unsure) {
                     ++rck;
-                    to = exact_dep(P, R, sweep, i, w, 0, 0, nullptr, 0) ? 1 : 0;
+                    to = (SHELL ? exact_dep_shell(P, R, sweep, i, w, 0)
+                                : exact_dep(P, R, sweep, i, w, 0, 0, nullptr, 0)) ? 1 : 0;
                 }
             }
         }

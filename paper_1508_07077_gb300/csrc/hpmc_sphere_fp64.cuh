@@ -179,8 +179,11 @@ __global__ void __launch_bounds__(kMaxThreads)
         bool accept = true;
         if (R.has_dep) {
             // a5: Poisson count
+            // V_0: the circumsphere, or the shell of the move's level
+            const int lvl = R.v0_shell ? shell_level(wm.x, wm.y, wm.z) : 0;
+            const unsigned long long *TabV = lvl > 0 ? Tab + (size_t)(lvl - 1) * R.nF : Tab;
             const uint4 wp = draw(R.key0, R.key1, sweep, tag, kPPoisson, 0, 0);
-            const int n_p = poisson_count(Tab, R.nF, u53_int(wp.x, wp.y), lane);
+            const int n_p = poisson_count(TabV, R.nF, u53_int(wp.x, wp.y), lane);
             cnt[kDepDrawn] += (unsigned long long)n_p;
 
             // a6: depletants along the attempt stream, nthr attempts per pass
@@ -195,10 +198,14 @@ __global__ void __launch_bounds__(kMaxThreads)
                 bool inside = false;
                 if (t < t_max) {
                     const uint4 w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, t);
-                    e0 = R.R_s * s11(w.x);
-                    e1 = R.R_s * s11(w.y);
-                    e2 = R.R_s * s11(w.z);
-                    inside = norm2(e0, e1, e2) < R.R_s2;
+                    if (lvl > 0) {
+                        inside = shell_point64(R, lvl, w, e0, e1, e2);
+                    } else {
+                        e0 = R.R_s * s11(w.x);
+                        e1 = R.R_s * s11(w.y);
+                        e2 = R.R_s * s11(w.z);
+                        inside = norm2(e0, e1, e2) < R.R_s2;
+                    }
                 }
                 const unsigned bal = __ballot_sync(kFull, inside);
                 if (lane == 0) s_warp[warp] = __popc(bal);

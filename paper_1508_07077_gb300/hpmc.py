@@ -21,11 +21,12 @@ HPMC_OK = 0
 HPMC_SPHERE, HPMC_HEMISPHERE, HPMC_SPHEROID = 0, 1, 2
 HPMC_FP64, HPMC_FP32_RECHECK = 0, 1
 HPMC_HOST, HPMC_DEVICE = 0, 1
+HPMC_V0_CIRCUMSPHERE, HPMC_V0_SHELL = 0, 1
 
 EXPORTS = ("hpmc_init", "hpmc_init_batch", "hpmc_get_replica", "hpmc_set_replica_moves",
            "hpmc_set_shape", "hpmc_set_depletant", "hpmc_set_moves",
            "hpmc_set_cells", "hpmc_set_launch", "hpmc_autotune", "hpmc_set_fp32_margin",
-           "hpmc_set_timing",
+           "hpmc_set_v0", "hpmc_set_timing",
            "hpmc_get_timing", "hpmc_sweep", "hpmc_get_state",
            "hpmc_set_state", "hpmc_reset_counters", "hpmc_sync", "hpmc_cell_list",
            "hpmc_cell_list_noalloc", "hpmc_free_volume", "hpmc_strerror", "hpmc_destroy")
@@ -86,6 +87,7 @@ def load(path: str = LIB_PATH):
                                 ip, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_double)]
     L.hpmc_set_fp32_margin.argtypes = [vp, ctypes.c_double]
+    L.hpmc_set_v0.argtypes = [vp, ip]
     L.hpmc_set_timing.argtypes = [vp, ip]
     L.hpmc_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_uint64), ip]
@@ -248,6 +250,10 @@ def hpmc_set_fp32_margin(ctx, margin):
     _check(load().hpmc_set_fp32_margin(ctx, float(margin)), "hpmc_set_fp32_margin")
 
 
+def hpmc_set_v0(ctx, mode):
+    _check(load().hpmc_set_v0(ctx, int(mode)), "hpmc_set_v0")
+
+
 def hpmc_set_timing(ctx, on):
     _check(load().hpmc_set_timing(ctx, int(bool(on))), "hpmc_set_timing")
 
@@ -326,7 +332,8 @@ class Sampler:
 
     def __init__(self, pos, box_l, *, quat=None, shape=HPMC_SPHERE, shape_params=(1.0,),
                  q=0.0, n_r=0.0, n_trial=0, d_max=0.1, a_max=0.0, p_translate=1.0,
-                 seed=1, replica=0, precision=HPMC_FP64, n_cell=0, warps=1, ilp=1, device=0):
+                 seed=1, replica=0, precision=HPMC_FP64, n_cell=0, warps=1, ilp=1, device=0,
+                 v0=HPMC_V0_CIRCUMSPHERE):
         pos = np.ascontiguousarray(pos, dtype=np.float64) if isinstance(pos, np.ndarray) else pos
         if isinstance(quat, np.ndarray):
             quat = np.ascontiguousarray(quat, dtype=np.float64)
@@ -339,6 +346,8 @@ class Sampler:
             hpmc_set_moves(self.ctx, d_max, a_max, p_translate)
             hpmc_set_cells(self.ctx, n_cell)
             hpmc_set_launch(self.ctx, warps, ilp)
+            if v0 != HPMC_V0_CIRCUMSPHERE:
+                hpmc_set_v0(self.ctx, v0)
         except Exception:
             self.close()
             raise

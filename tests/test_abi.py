@@ -54,6 +54,7 @@ def test_host_side_validation_without_gpu(built):
     assert lib.hpmc_init(ctypes.byref(ctx), 0, 5.0, None, None, 0, 1, 0, 0, 0) == -1
     assert lib.hpmc_init(None, 4, 5.0, None, None, 0, 1, 0, 0, 0) == -1
     assert lib.hpmc_set_depletant(None, 0.1, 1.0, 0) == -1
+    assert lib.hpmc_set_v0(None, 1) == -1
     assert lib.hpmc_cell_list(4, 5.0, 3, None, 1, 0, 0, None, None, None) == -1
 
 
