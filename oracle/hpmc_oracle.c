@@ -33,6 +33,8 @@
  *     V_0 may be restricted to the shell of the moved colloid's excluded
  *     volume that can hold points overlapping only the new pose; the shell
  *     thickness is quantised into 32 levels chosen from the move's words.
+ *     Option v0_mode 2: V_0 is the axis-aligned cube around the circumsphere
+ *     (every attempt is a depletant; no rejection).
  *   - Sec. V: anisotropic colloids (hemispheres, discoids = oblate spheroids)
  *     with quaternion rotation moves; overlap of two convex colloids by
  *     Minkowski portal refinement on their support functions.
@@ -766,6 +768,25 @@ static int next_in_shell(const osim *S, int lvl, uint32_t sweep, uint32_t tag,
     return 0;
 }
 
+/* Cube V_0 (v0_mode 2; "any convenient V_0", Sec. III.C): the axis-aligned
+ * cube [-R_s, R_s)^3 around the new reference point contains the new pose's
+ * circumsphere, so every attempt is a depletant: e = R_s (s11(w_0), s11(w_1),
+ * s11(w_2)) at attempt t = its index, and N_p ~ Poisson(z_p (2 R_s)^3). */
+static void cube_point(const osim *S, uint32_t sweep, uint32_t tag, uint32_t t, double e[3])
+{
+    uint32_t w[4];
+    draw(S->key, sweep, tag, P_DEP, 0, t, w);
+    e[0] = S->R_s * s11(w[0]);
+    e[1] = S->R_s * s11(w[1]);
+    e[2] = S->R_s * s11(w[2]);
+}
+
+double oracle_cube_lambda(double R_s, double n_r)
+{
+    double a = 2.0 * R_s;
+    return n_r * ((a * a) * a);
+}
+
 /* Points of the shell generator for tests: attempts t = 0 .. n_att - 1 of
  * stream (sweep, tag) at level lvl of a sphere system; writes the accepted
  * points to e (3 per point) and returns their count. */
@@ -883,8 +904,16 @@ static int accept_move(const osim *S, uint32_t sweep, int i, const double xn[3],
     double W = 1.0;
     for (int k = 0; k < n_p; ++k) {
         double e[3];
-        int got = lvl > 0 ? next_in_shell(S, lvl, sweep, tag, &t, t_max, e)
-                          : next_in_ball(S, sweep, tag, P_DEP, 0, &t, t_max, e);
+        int got;
+        if (S->v0_mode == 2) {
+            cube_point(S, sweep, tag, t, e);
+            t += 1;
+            got = 1;
+        } else if (lvl > 0) {
+            got = next_in_shell(S, lvl, sweep, tag, &t, t_max, e);
+        } else {
+            got = next_in_ball(S, sweep, tag, P_DEP, 0, &t, t_max, e);
+        }
         if (!got) {
             cnt[C_CAP]++;
             break;
@@ -1056,7 +1085,8 @@ static int sim_init(osim *S, int n, double L, int shape,
     S->n_r = n_r;
     S->R_s = S->sh.R_circ + 0.5 * q;
     S->R_s2 = S->R_s * S->R_s;
-    S->lambda = n_r > 0.0 ? oracle_lambda(S->R_s, n_r) : 0.0;
+    S->lambda = n_r > 0.0 ? (v0_mode == 2 ? oracle_cube_lambda(S->R_s, n_r)
+                                          : oracle_lambda(S->R_s, n_r)) : 0.0;
     S->n_trial = n_trial;
     S->cb_mode = cb_mode;
     S->d_max = d_max;
@@ -1081,7 +1111,7 @@ static int sim_init(osim *S, int n, double L, int shape,
         if (S->nF < 0) { sim_free(S); return -1; }
     }
     /* shell V_0: spheres only (anisotropic colloids keep the circumsphere) */
-    if ((v0_mode != 0 && v0_mode != 1) || (v0_mode == 1 && shape != SHAPE_SPHERE)) {
+    if (v0_mode < 0 || v0_mode > 2 || (v0_mode == 1 && shape != SHAPE_SPHERE)) {
         sim_free(S);
         return -1;
     }

@@ -25,7 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 SHAPE_SPHERE, SHAPE_HEMISPHERE, SHAPE_SPHEROID = 0, 1, 2
-V0_CIRCUMSPHERE, V0_SHELL = 0, 1
+V0_CIRCUMSPHERE, V0_SHELL, V0_CUBE = 0, 1, 2
 
 # counter slots of oracle_run
 COUNTERS = ("moves", "accept", "reject_cell", "reject_overlap", "reject_depletant",
@@ -122,6 +122,8 @@ def lib():
                                               ctypes.c_uint64, ctypes.c_uint32,
                                               ctypes.c_uint32, ctypes.c_uint32, dp]
             L.oracle_shell_points.restype = ctypes.c_long
+            L.oracle_cube_lambda.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.oracle_cube_lambda.restype = ctypes.c_double
             _lib = L
     return _lib
 

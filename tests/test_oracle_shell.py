@@ -1,7 +1,12 @@
-"""Pins of the shell-restricted depletant region V_0 (Sec. III.C, closing
-remark): for a translated sphere, depletants may be sampled in the shell of
-the moved colloid's excluded volume that can hold points overlapping the new
-pose but not the old one, instead of in the whole circumsphere.
+"""Pins of the alternative depletant regions V_0 (Sec. III.C: any convenient
+region that contains every point overlapping the new configuration but not
+the old one).
+
+Shell (closing remark of Sec. III.C): for a translated sphere, depletants may
+be sampled in the shell of the moved colloid's excluded volume that can hold
+points overlapping the new pose but not the old one, instead of in the whole
+circumsphere.  Cube: the axis-aligned cube around the circumsphere, sampled
+with no rejection (every attempt is a depletant), for every shape.
 
 What mathematics fixes, and what is checked here:
 * geometry: a point within R_s of the new centre and at least R_s from the
@@ -199,8 +204,89 @@ def test_shell_argument_validation(oracle):
         oracle.run(s, 3.0, shape=oracle.SHAPE_HEMISPHERE, shape_params=(1.0,),
                    quat=np.tile([1.0, 0, 0, 0], (2, 1)), q=0.2, n_r=1.0, v0_mode=1)
     with pytest.raises(ValueError):
-        oracle.run(s, 3.0, q=0.2, n_r=1.0, v0_mode=2)
+        oracle.run(s, 3.0, q=0.2, n_r=1.0, v0_mode=3)
     with pytest.raises(ValueError):   # move longer than the largest level
         oracle.acceptance(s, 3.0, 1, s[1] + 0.2, q=0.2, n_r=1.0, v0_mode=1, d_max=0.05)
     with pytest.raises(ValueError):
         oracle.shell_points(0.6, 0.1, 33, 10)
+
+
+# --------------------------------------------------------------------------
+# cube V_0
+# --------------------------------------------------------------------------
+
+def test_cube_draws_poisson_of_the_cube_volume(oracle):
+    pos, xn = _move(1.05, 1.10)
+    n_rep = 40000
+    _, c = oracle.acceptance(pos, L2, 1, xn, q=Q, n_r=Z_P, v0_mode=2, n_rep=n_rep)
+    lam = Z_P * (2.0 * R_S) ** 3
+    mean = c["dep_drawn"] / n_rep
+    assert abs(mean - lam) < 4.5 * math.sqrt(lam / n_rep), (mean, lam)
+    assert abs(oracle.lib().oracle_cube_lambda(R_S, Z_P) - lam) < 1e-9 * lam
+
+
+@pytest.mark.parametrize("n_trial", [0, 3])
+def test_cube_acceptance_equals_the_circumsphere(oracle, n_trial):
+    pos = np.array([[1.2, 1.2, 1.2], [2.25, 1.2, 1.2], [1.2, 2.27, 1.25],
+                    [0.2, 1.0, 1.3], [1.3, 0.15, 1.9]])
+    xn = pos[0] + np.array([0.04, 0.03, -0.02])
+    n_rep = 60000
+    p = []
+    for mode, sweep0 in ((0, 11), (2, 77777)):
+        a, _ = oracle.acceptance(pos, 3.2, 0, xn, q=Q, n_r=Z_P, n_trial=n_trial, v0_mode=mode,
+                                 n_rep=n_rep, sweep0=sweep0)
+        p.append(a / n_rep)
+    se = math.sqrt(sum(x * (1 - x) for x in p) / n_rep)
+    assert 0.05 < p[0] < 0.95 and abs(p[0] - p[1]) < 4.5 * se, (p, se)
+
+
+def test_cube_acceptance_of_a_rotation_equals_the_circumsphere(oracle):
+    """Anisotropic colloids: a fixed rotation of a hemisphere next to another."""
+    shape, params = oracle.SHAPE_HEMISPHERE, (1.0,)
+    pos = np.array([[1.5, 1.5, 1.5], [1.5, 1.5, 2.55]])
+    quat = np.array([[1.0, 0.0, 0.0, 0.0], [0.0, 1.0, 0.0, 0.0]])
+    th = 0.15
+    qn = np.array([math.cos(th / 2), math.sin(th / 2), 0.0, 0.0])
+    n_rep = 40000
+    p = []
+    for mode, sweep0 in ((0, 5), (2, 99999)):
+        a, _ = oracle.acceptance(pos, 3.5, 0, pos[0], shape=shape, shape_params=params, q=0.1,
+                                 n_r=40.0, v0_mode=mode, quat=quat, qn=qn, n_rep=n_rep,
+                                 sweep0=sweep0)
+        p.append(a / n_rep)
+    se = math.sqrt(sum(x * (1 - x) for x in p) / n_rep)
+    assert 0.05 < p[0] < 0.95 and abs(p[0] - p[1]) < 4.5 * se, (p, se)
+
+
+@pytest.mark.parametrize("n_trial", [0, 3])
+def test_detailed_balance_with_the_cube(oracle, n_trial):
+    pos0, x1 = _move(1.02, 1.09)
+    pos1, x0 = _move(1.09, 1.02)
+    kw = dict(q=Q, n_r=Z_P, n_trial=n_trial, v0_mode=2, n_rep=150000)
+    f, _ = oracle.acceptance(pos0, L2, 1, x1, **kw)
+    b, _ = oracle.acceptance(pos1, L2, 1, x0, sweep0=10 ** 7, **kw)
+    ratio = f / b
+    se = ratio * math.sqrt(1.0 / f + 1.0 / b)
+    expect = math.exp(Z_P * float(lens(1.09) - lens(1.02)))
+    assert abs(ratio - expect) < 4.0 * se, (ratio, expect, se)
+
+
+def test_asakura_oosawa_pair_distribution_with_the_cube(oracle):
+    bins, rmax, lo = 24, 1.2, 20
+    edges = np.linspace(0.0, rmax, bins + 1)
+    expect = []
+    for b in range(lo, bins):
+        r = np.linspace(edges[b], edges[b + 1], 401)
+        expect.append(np.trapezoid(r ** 2 * np.exp(Z_P * lens(r)), r))
+    expect = np.array(expect) / np.sum(expect)
+    a, b = _pair(1.5)
+    hs = []
+    for seed in range(1, 9):
+        _, _, c, h = oracle.run(np.array([a, b]), L2, q=Q, n_r=Z_P, v0_mode=2, d_max=0.03,
+                                seed=seed, n_sweeps=40000, hist_bins=bins, hist_rmax=rmax)
+        h = h[lo:].astype(float)
+        hs.append(h / h.sum())
+        assert c["dep_evaluated"] <= c["dep_drawn"]
+    hs = np.array(hs)
+    m, se = hs.mean(0), hs.std(0, ddof=1) / math.sqrt(len(hs))
+    assert np.all(np.abs((m - expect) / se) < 4.0)
