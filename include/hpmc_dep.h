@@ -55,6 +55,7 @@ extern "C" {
 
 #define HPMC_V0_CIRCUMSPHERE 0 /* depletants sampled in the new pose's circumsphere (default) */
 #define HPMC_V0_SHELL 1        /* spheres: in the shell that can hold the move's lens */
+#define HPMC_V0_CUBE 2         /* in the cube of side 2 R_s around the circumsphere */
 
 #define HPMC_HOST 0
 #define HPMC_DEVICE 1
@@ -199,8 +200,11 @@ int hpmc_set_fp32_margin(hpmc_ctx *ctx, double margin);
  * Acceptance probabilities are those of the circumsphere (the blocking
  * depletants form the same Poisson process), so the sampled ensemble is the
  * same; the trajectory and the counters dep_drawn and dep_evaluated are
- * those of the shell.  HPMC_ERR_ARG for an anisotropic shape or an unknown
- * mode.  Takes effect at the next sweep. */
+ * those of the shell.  HPMC_V0_CUBE (every shape): the axis-aligned cube
+ * [-R_s, R_s)^3 around the new reference point, N_p ~ Poisson(z_p (2 R_s)^3),
+ * depletant k = attempt k (no rejection step); those outside the new pose's
+ * excluded volume are irrelevant.  HPMC_ERR_ARG for the shell with an
+ * anisotropic shape or an unknown mode.  Takes effect at the next sweep. */
 int hpmc_set_v0(hpmc_ctx *ctx, int mode);
 
 /* Per-kernel timing.  While on, hpmc_sweep launches its kernels one by one

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__
             e0 = coord32(w.x, R.R_s32);
             e1 = coord32(w.y, R.R_s32);
             e2 = coord32(w.z, R.R_s32);
-            in = tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
+            in = R.v0_cube ? 1 : tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
         }
         {
             const bool unsure = in == -1;

@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kMaxThreads)
                     e0 = R.R_s * s11(w.x);
                     e1 = R.R_s * s11(w.y);
                     e2 = R.R_s * s11(w.z);
-                    inside = norm2(e0, e1, e2) < R.R_s2;
+                    inside = R.v0_cube || norm2(e0, e1, e2) < R.R_s2;
                 }
                 const unsigned bal = __ballot_sync(kFull, inside);
                 if (lane == 0) s_warp[warp] = __popc(bal);

@@ -160,6 +160,7 @@ struct Rep {
     // thickness sh_h[k-1]; its Poisson table is the (k-1)-th block of nF
     // entries at t_off
     int v0_shell;
+    int v0_cube;           // V_0 is the cube [-R_s, R_s)^3: every attempt is a depletant
     double dd;             // level thickness step sqrt(3) d_max / 32
     double R_s4;           // R_s^4
     float R_s4_32;

@@ -176,7 +176,10 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
     if (!(R_circ > 0.0)) return HPMC_ERR_ARG;
     if (!(h.q >= 0.0) || !(h.n_r >= 0.0) || h.n_trial < 0 || h.n_trial > 100000) return HPMC_ERR_ARG;
     const double R_s = R_circ + 0.5 * h.q;
-    const double v0 = ((4.0 / 3.0) * kPi) * ((R_s * R_s) * R_s);
+    // |V_0|: the circumsphere, or the cube of side 2 R_s around it
+    const double a_cube = 2.0 * R_s;
+    const double v0 = p.v0_mode == HPMC_V0_CUBE ? (a_cube * a_cube) * a_cube
+                                                : ((4.0 / 3.0) * kPi) * ((R_s * R_s) * R_s);
     const double lambda = h.n_r > 0.0 ? h.n_r * v0 : 0.0;
     const double w_min = 2.0 * R_circ + h.q;
     int nc = h.nc_req;
@@ -260,6 +263,7 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
     R.half_nc = nc / 2;
     R.n_stencil = nc == 2 ? 2 : 3;
     R.nF = R.v0_shell ? shell_stride : (int)F.size();
+    R.v0_cube = p.v0_mode == HPMC_V0_CUBE ? 1 : 0;
     R.has_dep = lambda > 0.0 ? 1 : 0;
     R.n_trial = h.n_trial;
     R.key0 = (uint32_t)c->seed;
@@ -502,9 +506,11 @@ void launch_lens(hpmc_ctx *c, const SimParams &P, cudaStream_t s)
     if (c->precision != HPMC_FP32_RECHECK) return;
     if (c->prm.shape == HPMC_SPHERE) {
         if (c->prm.v0_mode == HPMC_V0_SHELL)
-            launch_pdl1(k_lens_sphere_fp32<true>, (c->n_total + 3) / 4, 128, s, P);
+            launch_pdl1(k_lens_shell_fp32, (c->n_total + 127) / 128, 128, s, P);
+        else if (c->prm.v0_mode == HPMC_V0_CUBE)
+            launch_pdl1(k_lens_sphere_fp32<2>, (c->n_total + 3) / 4, 128, s, P);
         else
-            launch_pdl1(k_lens_sphere_fp32<false>, (c->n_total + 3) / 4, 128, s, P);
+            launch_pdl1(k_lens_sphere_fp32<0>, (c->n_total + 3) / 4, 128, s, P);
     } else {
         k_propose_aniso<<<(c->n_total + 127) / 128, 128, 0, s>>>(P);
         k_lens_aniso_fp32<<<(c->n_total + 3) / 4, 128, 0, s>>>(P);
@@ -1216,7 +1222,7 @@ int hpmc_set_fp32_margin(hpmc_ctx *c, double margin)
 
 int hpmc_set_v0(hpmc_ctx *c, int mode)
 {
-    if (!c || (mode != HPMC_V0_CIRCUMSPHERE && mode != HPMC_V0_SHELL)) return HPMC_ERR_ARG;
+    if (!c || mode < HPMC_V0_CIRCUMSPHERE || mode > HPMC_V0_CUBE) return HPMC_ERR_ARG;
     if (mode == HPMC_V0_SHELL && c->prm.shape != HPMC_SPHERE) return HPMC_ERR_ARG;
     c->prm.v0_mode = mode;
     c->dirty = true;

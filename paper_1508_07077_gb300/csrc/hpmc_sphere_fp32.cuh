@@ -397,8 +397,9 @@ __device__ __forceinline__ bool cb_pass(DepShared &sh, int tid, int nslots, doub
 // holds at most N_p <= (Poisson table length) points, the capacity it is
 // allocated with, so it cannot overflow.
 // ---------------------------------------------------------------------------
-// SHELL: V_0 is the shell of the move's level instead of the circumsphere.
-template <bool SHELL>
+// V0: the depletant region; 0 the circumsphere, 2 the cube around it (every
+// attempt a depletant).  (The shell, 1, has its own kernel below.)
+template <int V0>
 __global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_constant__ SimParams P)
 {
     const int lane = threadIdx.x & 31;
@@ -427,17 +428,10 @@ __global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_consta
     }
     uint32_t rck = 0;
     const float o0 = -D0, o1 = -D1, o2 = -D2;
-    const unsigned long long *Tab = P.T + R.t_off;
-    int lvl = 0;
-    float rin32 = 0.0f, h32 = 0.0f;
-    if (SHELL) {
-        lvl = shell_level(wm.x, wm.y, wm.z);
-        Tab += (size_t)(lvl - 1) * (size_t)R.nF;
-        rin32 = R.sh_rin32[lvl - 1];
-        h32 = R.sh_h32[lvl - 1];
-    }
+    static_assert(V0 == 0 || V0 == 2, "circumsphere or cube");
+    constexpr bool CUBE = V0 == 2;
     const uint4 wp = draw(R.key0, R.key1, sweep, tag, kPPoisson, 0, 0);
-    const int n_p = poisson_count(Tab, R.nF, u53_int(wp.x, wp.y), lane);
+    const int n_p = poisson_count(P.T + R.t_off, R.nF, u53_int(wp.x, wp.y), lane);
     const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
     const RoundKeys K = round_keys(R.key0, R.key1);
     float4 *out = P.lens + (size_t)g * P.lens_cap;
@@ -451,36 +445,31 @@ __global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_consta
         int in = 0;
         if (t < t_max) {
             w = philox_rk(make_uint4(sweep, tag, kPDep << 24, t), K);
-            if (SHELL) {
-                in = shell_point32(R, rin32, h32, w, e0, e1, e2);
-            } else {
-                e0 = coord32(w.x, R.R_s32);
-                e1 = coord32(w.y, R.R_s32);
-                e2 = coord32(w.z, R.R_s32);
-                in = tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
-            }
+            e0 = coord32(w.x, R.R_s32);
+            e1 = coord32(w.y, R.R_s32);
+            e2 = coord32(w.z, R.R_s32);
+            in = CUBE ? 1 : tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
         }
         {
             const bool unsure = in == -1;
             if (__any_sync(kFull, unsure)) {
                 if (unsure) {
                     ++rck;
-                    if (SHELL) in = exact_shell_pt(R, lvl, w, e0, e1, e2) ? 1 : 0;
-                    else in = exact_ball(P, R, w) ? 1 : 0;
+                    in = exact_ball(P, R, w) ? 1 : 0;
                 }
             }
         }
         const unsigned bal = __ballot_sync(kFull, in == 1);
         const int k = k0 + __popc(bal & lt);
         bool dep = in == 1 && k < n_p;
-        if (SHELL) {
-            // a shell point overlaps the new pose unless it rounds onto R_s
+        if (CUBE) {
+            // a cube point overlaps the new pose only inside the circumsphere
             int tn = dep ? tri(norm2f(e0, e1, e2), R.T_dep32, R.m_r2) : 1;
             const bool unsure = tn == -1;
             if (__any_sync(kFull, unsure)) {
                 if (unsure) {
                     ++rck;
-                    tn = exact_dep_shell(P, R, sweep, i, w, 4) ? 1 : 0;
+                    tn = exact_ball(P, R, w) ? 1 : 0;
                 }
             }
             dep = dep && tn == 1;
@@ -492,8 +481,7 @@ __global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_consta
             if (__any_sync(kFull, unsure)) {
                 if (unsure) {
                     ++rck;
-                    to = (SHELL ? exact_dep_shell(P, R, sweep, i, w, 0)
-                                : exact_dep(P, R, sweep, i, w, 0, 0, nullptr, 0)) ? 1 : 0;
+                    to = exact_dep(P, R, sweep, i, w, 0, 0, nullptr, 0) ? 1 : 0;
                 }
             }
         }
@@ -521,6 +509,94 @@ __global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_consta
     if (lane == 0 && m > P.lens_cap) atomicCAS(P.err, kErrNone, kErrCandCap);
     rck = __reduce_add_sync(kFull, rck);
     if (lane == 0 && rck) count_one(P, r, kRechecks, (unsigned long long)rck);
+}
+
+// Shell V_0, one thread per colloid.  A shell holds few depletants (the
+// level's thickness is of the order of the step size), so a warp per move
+// would leave most lanes of its one pass idle and repeat the move's draws on
+// every lane; here each thread walks its own attempt stream.  Same output
+// contract as k_lens_sphere_fp32.
+__device__ __forceinline__ int poisson_count1(const unsigned long long *T, int nF, unsigned long long m)
+{
+    int lo = 0, hi = nF;   // the table is non-decreasing: count = first index with T > m
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(T + mid) <= m) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(128, 4) k_lens_shell_fp32(const __grid_constant__ SimParams P)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= P.n_total) {
+        pdl_wait();
+        return;
+    }
+    const int r = P.rep_of[g];
+    const Rep &R = P.reps[r];
+    const int i = g;
+    const uint32_t sweep = (uint32_t)(*P.sweep);
+    const uint32_t tag = (uint32_t)(g - R.off);
+    const uint4 wm = draw(R.key0, R.key1, sweep, tag, kPMove, 0, 0);
+    const float D0 = coord32(wm.x, R.d_max32);
+    const float D1 = coord32(wm.y, R.d_max32);
+    const float D2 = coord32(wm.z, R.d_max32);
+    if (!R.has_dep) {
+        pdl_wait();
+        const int bp = P.binpos[g];
+        if (bp >= 0) P.mv_bin[bp] = make_float4(D0, D1, D2, 0.0f);
+        return;
+    }
+    uint32_t rck = 0;
+    const int lvl = shell_level(wm.x, wm.y, wm.z);
+    const float rin32 = R.sh_rin32[lvl - 1], h32 = R.sh_h32[lvl - 1];
+    const uint4 wp = draw(R.key0, R.key1, sweep, tag, kPPoisson, 0, 0);
+    const int n_p = poisson_count1(P.T + R.t_off + (size_t)(lvl - 1) * (size_t)R.nF, R.nF,
+                                   u53_int(wp.x, wp.y));
+    const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
+    const RoundKeys K = round_keys(R.key0, R.key1);
+    float4 *out = P.lens + (size_t)g * P.lens_cap;
+    int k = 0, m = 0;
+    for (uint32_t t = 0; k < n_p && t < t_max; ++t) {
+        const uint4 w = philox_rk(make_uint4(sweep, tag, kPDep << 24, t), K);
+        float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+        int in = shell_point32(R, rin32, h32, w, e0, e1, e2);
+        if (in == -1) {
+            ++rck;
+            in = exact_shell_pt(R, lvl, w, e0, e1, e2) ? 1 : 0;
+        }
+        if (!in) continue;
+        const int kk = k++;
+        int tn = tri(norm2f(e0, e1, e2), R.T_dep32, R.m_r2);   // overlaps the new pose
+        if (tn == -1) {
+            ++rck;
+            tn = exact_dep_shell(P, R, sweep, i, w, 4) ? 1 : 0;
+        }
+        if (tn != 1) continue;
+        int to = tri(norm2f(e0 + D0, e1 + D1, e2 + D2), R.T_dep32, R.m_r2);   // the old pose
+        if (to == -1) {
+            ++rck;
+            to = exact_dep_shell(P, R, sweep, i, w, 0) ? 1 : 0;
+        }
+        if (to != 0) continue;
+        if (m < P.lens_cap) out[m] = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)kk)));
+        ++m;
+    }
+    pdl_wait();
+    const int bp = P.binpos[g];
+    if (bp >= 0) {
+        P.mv_bin[bp] = make_float4(D0, D1, D2, 0.0f);
+        P.hdr_bin[bp] = make_int4(n_p, min(k, n_p), min(m, P.lens_cap), 0);
+        const int ni = min(m, kLensInline);
+        for (int a = 0; a < ni; ++a) P.lens_bin[(size_t)bp * kLensInline + a] = out[a];
+    }
+    if (m > P.lens_cap) atomicCAS(P.err, kErrNone, kErrCandCap);
+    // recheck count, summed over the lanes of the same replica
+    const unsigned peers = __match_any_sync(__activemask(), r);
+    rck = __reduce_add_sync(peers, rck);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1 && rck) count_one(P, r, kRechecks, (unsigned long long)rck);
 }
 
 constexpr int kMaxLensCTA = 64;    // lens points of one cell staged in shared memory (more: read

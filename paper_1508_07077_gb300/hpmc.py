@@ -21,7 +21,7 @@ HPMC_OK = 0
 HPMC_SPHERE, HPMC_HEMISPHERE, HPMC_SPHEROID = 0, 1, 2
 HPMC_FP64, HPMC_FP32_RECHECK = 0, 1
 HPMC_HOST, HPMC_DEVICE = 0, 1
-HPMC_V0_CIRCUMSPHERE, HPMC_V0_SHELL = 0, 1
+HPMC_V0_CIRCUMSPHERE, HPMC_V0_SHELL, HPMC_V0_CUBE = 0, 1, 2
 
 EXPORTS = ("hpmc_init", "hpmc_init_batch", "hpmc_get_replica", "hpmc_set_replica_moves",
            "hpmc_set_shape", "hpmc_set_depletant", "hpmc_set_moves",

@@ -1,8 +1,10 @@
-"""GPU parity of the shell-restricted depletant region V_0 (spheres,
-translations; Sec. III.C closing remark) against the oracle, through the C ABI.
+"""GPU parity of the alternative depletant regions V_0 (Sec. III.C) against
+the oracle, through the C ABI: the shell-restricted V_0 (spheres,
+translations; the closing remark of Sec. III.C) and the cube around the
+circumsphere (every shape, no rejection step).
 
 Positions and every trajectory counter must be bit-identical to the oracle's
-shell mode: the level rule is integer-only, the shell point is FP64 in the
+mode: the level rule is integer-only, the shell point is FP64 in the
 specification's order, and the FP32 form certifies its shell decisions (or
 re-takes them in FP64)."""
 import numpy as np
@@ -155,5 +157,64 @@ def test_shell_is_for_spheres_only(lib):
     with pytest.raises(lib.HPMCError):
         lib.hpmc_set_v0(smp.ctx, SHELL)
     with pytest.raises(lib.HPMCError):
-        lib.hpmc_set_v0(smp.ctx, 2)
+        lib.hpmc_set_v0(smp.ctx, 3)
+    lib.hpmc_set_v0(smp.ctx, 2)        # the cube is for every shape
     smp.close()
+
+
+# --------------------------------------------------------------------------
+# cube V_0
+# --------------------------------------------------------------------------
+CUBE = 2
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("n_trial", [0, 2])
+def test_cube_spheres(oracle, lib, precision, n_trial):
+    s = W.spheres_256(seed=11)
+    smp = lib.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, n_trial=n_trial, d_max=0.1, seed=3,
+                      precision=precision, v0=CUBE)
+    smp.sweep(12)
+    pos, _, sweep, cnt = smp.state()
+    smp.close()
+    ref, _, rc, _ = oracle.run(s.pos, s.L, q=s.q, n_r=s.n_r, n_trial=n_trial, d_max=0.1,
+                               seed=3, n_sweeps=12, v0_mode=CUBE)
+    for k in oracle.PARITY_COUNTERS:
+        assert cnt[k] == rc[k], (k, cnt[k], rc[k])
+    assert np.array_equal(pos, ref)
+    assert cnt["accept"] > 0 and cnt["reject_depletant" if n_trial == 0 else "reject_cb"] > 0
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("shape,phi,q,eta", [(W.HEMISPHERE, 0.25, 0.10, 0.12),
+                                             (W.SPHEROID, 0.30, 0.10, 0.12)])
+def test_cube_anisotropic_with_rotations(oracle, lib, precision, shape, phi, q, eta):
+    # (the cube holds 1.9x the circumsphere's depletants: eta_r is kept below
+    # the Poisson table's mean limit of 700)
+    s = W.make_system("c", shape, 256, phi, q, eta, seed=12)
+    kw = dict(q=s.q, n_r=s.n_r, d_max=0.08, a_max=0.2, p_translate=0.5)
+    smp = lib.Sampler(s.pos, s.L, quat=s.quat, shape=s.shape, shape_params=s.shape_params,
+                      seed=4, precision=precision, v0=CUBE, **kw)
+    smp.sweep(6)
+    pos, quat, _, cnt = smp.state(with_quat=True)
+    smp.close()
+    ref, refq, rc, _ = oracle.run(s.pos, s.L, shape=s.shape, shape_params=s.shape_params,
+                                  quat=s.quat, seed=4, n_sweeps=6, v0_mode=CUBE, **kw)
+    for k in oracle.PARITY_COUNTERS:
+        assert cnt[k] == rc[k], (k, cnt[k], rc[k])
+    assert np.array_equal(pos, ref) and np.array_equal(quat, refq)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_cube_spheres_16384_first_sweeps(oracle, lib, precision):
+    s = W.spheres_16384(0.2)
+    smp = lib.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=0.1, seed=1, precision=precision,
+                      v0=CUBE)
+    smp.sweep(2)
+    pos, _, _, cnt = smp.state()
+    smp.close()
+    ref, _, rc, _ = oracle.run(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=0.1, seed=1, n_sweeps=2,
+                               v0_mode=CUBE)
+    for k in oracle.PARITY_COUNTERS:
+        assert cnt[k] == rc[k], (k, cnt[k], rc[k])
+    assert np.array_equal(pos, ref)
