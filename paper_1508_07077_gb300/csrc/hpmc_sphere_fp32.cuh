@@ -386,55 +386,43 @@ __device__ __forceinline__ bool cb_pass(DepShared &sh, int tid, int nslots, doub
 }
 
 // ---------------------------------------------------------------------------
-// Depletant lens lists (Sec. III.B-C), one warp per colloid, all colloids of
-// the sweep at once.  Everything about a move's depletants that does not
-// involve other colloids is fixed by the move's own random streams: the
-// proposal, N_p, the points of the attempt stream, "inside the new pose's
-// circumsphere" (= overlaps the new pose, for spheres) and "overlaps the old
-// pose".  Only the points left after those tests, the lens of the move, can
-// block it, and only they need the neighbours, which the colour phases test
-// in order.  Moves that certainly leave their cell draw nothing.  A list
-// holds at most N_p <= (Poisson table length) points, the capacity it is
-// allocated with, so it cannot overflow.
+// Depletant lens lists (Sec. III.B-C).  Everything about a move's depletants
+// that does not involve other colloids is fixed by the move's own random
+// streams: the proposal, N_p, the points of the attempt stream, "inside the
+// new pose's circumsphere" (= overlaps the new pose, for spheres) and
+// "overlaps the old pose".  Only the points left after those tests, the lens
+// of the move, can block it, and only they need the neighbours, which the
+// colour phases test in order.  A list holds at most N_p <= (Poisson table
+// length) points, the capacity it is allocated with, so it cannot overflow.
 // ---------------------------------------------------------------------------
-// V0: the depletant region; 0 the circumsphere, 2 the cube around it (every
-// attempt a depletant).  (The shell, 1, has its own kernel below.)
+// One move's lens list, warp-cooperative (all 32 lanes call it).  V0: the
+// depletant region; 0 the circumsphere, 2 the cube around it (every attempt
+// a depletant).  (The shell, 1, has its own kernel below.)  Writes the FP32
+// displacement to *mv (lane 0), and the lens points, in depletant order, to
+// sdst[slot] for slot < room and to gdst[slot] beyond (gdst is the move's
+// list of capacity lens_cap).  Returns (N_p, depletants obtained from the
+// stream, lens points, FP64 re-takes), the same in every lane.
 template <int V0>
-__global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_constant__ SimParams P)
+__device__ __forceinline__ int4 lens_of_move(const SimParams &P, const Rep &R, int g, uint32_t sweep, float4 *mv,
+                                          float4 *sdst, int room, float4 *gdst)
 {
+    static_assert(V0 == 0 || V0 == 2, "circumsphere or cube");
+    constexpr bool CUBE = V0 == 2;
     const int lane = threadIdx.x & 31;
-    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (g >= P.n_total) return;
-    // Launched with programmatic dependent launch behind the cell-list kernel:
-    // the depletant work below needs nothing that kernel writes (the sweep
-    // index is the counter the previous sweep advanced); only the bin slot
-    // the results are filed under does, and it is read after pdl_wait().
-    // (This kernel does not release its own successor early: the colour
-    // phases read its results before they wait.)
-    const int r = P.rep_of[g];
-    const Rep &R = P.reps[r];
     const int i = g;   // global colloid index (the helpers take global indices)
-    const uint32_t sweep = (uint32_t)(*P.sweep);
     const uint32_t tag = (uint32_t)(g - R.off);
     const uint4 wm = draw(R.key0, R.key1, sweep, tag, kPMove, 0, 0);
     const float D0 = coord32(wm.x, R.d_max32);
     const float D1 = coord32(wm.y, R.d_max32);
     const float D2 = coord32(wm.z, R.d_max32);
-    if (!R.has_dep) {
-        pdl_wait();
-        const int bp = P.binpos[g];
-        if (lane == 0 && bp >= 0) P.mv_bin[bp] = make_float4(D0, D1, D2, 0.0f);
-        return;
-    }
+    if (lane == 0) *mv = make_float4(D0, D1, D2, 0.0f);
+    if (!R.has_dep) return make_int4(0, 0, 0, 0);
     uint32_t rck = 0;
     const float o0 = -D0, o1 = -D1, o2 = -D2;
-    static_assert(V0 == 0 || V0 == 2, "circumsphere or cube");
-    constexpr bool CUBE = V0 == 2;
     const uint4 wp = draw(R.key0, R.key1, sweep, tag, kPPoisson, 0, 0);
     const int n_p = poisson_count(P.T + R.t_off, R.nF, u53_int(wp.x, wp.y), lane);
     const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
     const RoundKeys K = round_keys(R.key0, R.key1);
-    float4 *out = P.lens + (size_t)g * P.lens_cap;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t t0 = 0;
     int k0 = 0, m = 0;
@@ -488,12 +476,41 @@ __global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_consta
         const bool lens = dep && to == 0;
         const unsigned lb = __ballot_sync(kFull, lens);
         const int slot = m + __popc(lb & lt);
-        if (lens && slot < P.lens_cap)
-            out[slot] = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
+        if (lens) {
+            const float4 v = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
+            if (slot < room) sdst[slot] = v;
+            else if (slot < P.lens_cap) gdst[slot] = v;
+        }
         m += __popc(lb);
         k0 += __popc(bal);
         t0 += 32u;
     }
+    if (lane == 0 && m > P.lens_cap) atomicCAS(P.err, kErrNone, kErrCandCap);
+    rck = __reduce_add_sync(kFull, rck);
+    return make_int4(n_p, min(k0, n_p), min(m, P.lens_cap), (int)rck);
+}
+
+// The lens lists of all moves of the sweep, one warp per colloid, filed under
+// the colloids' bin slots (used when the colour phases do not build them
+// themselves).
+template <int V0>
+__global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_constant__ SimParams P)
+{
+    __shared__ float4 s_mv[4];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int g = blockIdx.x * (blockDim.x >> 5) + wl;
+    if (g >= P.n_total) return;
+    // Launched with programmatic dependent launch behind the cell-list kernel:
+    // the depletant work below needs nothing that kernel writes (the sweep
+    // index is the counter the previous sweep advanced); only the bin slot
+    // the results are filed under does, and it is read after pdl_wait().
+    // (This kernel does not release its own successor early: the colour
+    // phases read its results before they wait.)
+    const int r = P.rep_of[g];
+    const Rep &R = P.reps[r];
+    const uint32_t sweep = (uint32_t)(*P.sweep);
+    float4 *out = P.lens + (size_t)g * P.lens_cap;
+    const int4 h = lens_of_move<V0>(P, R, g, sweep, &s_mv[wl], nullptr, 0, out);
     // file the header, the displacement and the first lens points under the
     // colloid's bin slot, where the colour phase reads them with the cell list
     __syncwarp();
@@ -501,14 +518,12 @@ __global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_consta
     const int bp = P.binpos[g];
     if (bp >= 0) {
         if (lane == 0) {
-            P.mv_bin[bp] = make_float4(D0, D1, D2, 0.0f);
-            P.hdr_bin[bp] = make_int4(n_p, min(k0, n_p), min(m, P.lens_cap), 0);
+            P.mv_bin[bp] = s_mv[wl];
+            if (R.has_dep) P.hdr_bin[bp] = make_int4(h.x, h.y, h.z, 0);
         }
-        if (lane < min(m, kLensInline)) P.lens_bin[(size_t)bp * kLensInline + lane] = out[lane];
+        if (lane < min(h.z, kLensInline)) P.lens_bin[(size_t)bp * kLensInline + lane] = out[lane];
     }
-    if (lane == 0 && m > P.lens_cap) atomicCAS(P.err, kErrNone, kErrCandCap);
-    rck = __reduce_add_sync(kFull, rck);
-    if (lane == 0 && rck) count_one(P, r, kRechecks, (unsigned long long)rck);
+    if (lane == 0 && h.w) count_one(P, r, kRechecks, (unsigned long long)h.w);
 }
 
 // Shell V_0, one thread per colloid.  A shell holds few depletants (the
