@@ -59,7 +59,7 @@ ISSUE_LANES_PER_SM = 128        # 4 SM sub-partitions x 32 lanes, one instructio
 BYTES_PER_MOVE = 2 * 32 + 16 + 2 * 4   # pos (double4) read + cell-local copy + cell list ids
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel
 # build on the four-state-point 16384-sphere batch (profiles/k_phase_sphere_fp32_*.md).
-MEASURED_TRAFFIC = {"k_phase_sphere_fp32": 10.19e6, "k_lens_sphere_fp32": 2.52e6}
+MEASURED_TRAFFIC = {"k_phase_sphere_fp32": 10.20e6, "k_lens_sphere_fp32": 2.50e6}
 
 
 def _dist():

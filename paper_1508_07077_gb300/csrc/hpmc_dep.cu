@@ -103,6 +103,10 @@ struct hpmc_ctx {
     std::vector<cudaEvent_t> tpool; // reusable events
 
     cudaStream_t cap_stream = nullptr;
+    // pinned host staging of the small device-to-host reads (sweep index,
+    // error word, check flag, counters), so that a call issues all its copies
+    // and synchronises once
+    unsigned long long *h_pin = nullptr;   // [kPinHead + counters]
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool dirty = true;        // parameters changed: re-derive and re-record the graph
@@ -110,6 +114,15 @@ struct hpmc_ctx {
 };
 
 namespace {
+
+// Pinned staging slots (h_pin): sweep index, error word, check flag, sweep
+// index to upload, then the counters.
+constexpr int kPinSweep = 0, kPinErr = 1, kPinFlag = 2, kPinUp = 3, kPinHead = 4;
+
+size_t counter_words(const hpmc_ctx *c)
+{
+    return (size_t)c->reps.size() * kRepSlots * kNumCounters;
+}
 
 int cuda_fail(cudaError_t e, const char *what)
 {
@@ -597,17 +610,20 @@ int check_config(hpmc_ctx *c)
     if (rc != HPMC_OK) return rc;
     CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->cap_stream));
     SimParams P = make_params(c);
-    if (c->prm.shape == HPMC_SPHERE)
+    if (c->prm.shape == HPMC_SPHERE && c->precision == HPMC_FP32_RECHECK)
+        k_check_spheres32<<<(c->n_total + 255) / 256, 256, 0, c->cap_stream>>>(P, c->d_flag);
+    else if (c->prm.shape == HPMC_SPHERE)
         k_check_spheres<<<(c->n_total + 255) / 256, 256, 0, c->cap_stream>>>(P, c->d_flag);
     else
         k_check_aniso<<<(c->n_total + 127) / 128, 128, 0, c->cap_stream>>>(P, c->d_flag);
     CK(cudaGetLastError());
-    int flag = 0, err = 0;
-    CK(cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->cap_stream));
-    CK(cudaMemcpyAsync(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->cap_stream));
+    CK(cudaMemcpyAsync(c->h_pin + kPinFlag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->cap_stream));
+    CK(cudaMemcpyAsync(c->h_pin + kPinErr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->cap_stream));
     // the sweeps start from zeroed populations
     CK(cudaMemsetAsync(c->d_count, 0, cbytes, c->cap_stream));
     CK(cudaStreamSynchronize(c->cap_stream));
+    const int flag = *reinterpret_cast<const int *>(c->h_pin + kPinFlag);
+    const int err = *reinterpret_cast<const int *>(c->h_pin + kPinErr);
     if (flag & 2) return HPMC_ERR_ARG;
     if (err == kErrCellCap) return HPMC_ERR_CAP;
     if (flag & 1) return HPMC_ERR_OVERLAP;
@@ -798,6 +814,7 @@ int alloc_ctx(hpmc_ctx *c)
 {
     const int n = c->n_total, n_rep = (int)c->reps.size();
     CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    CK(cudaMallocHost(&c->h_pin, sizeof(unsigned long long) * (kPinHead + counter_words(c))));
     CK(cudaMalloc(&c->d_pos, sizeof(double4) * (size_t)n));
     CK(cudaMalloc(&c->d_quat, sizeof(double4) * (size_t)n));
     CK(cudaMalloc(&c->d_rel, sizeof(float4) * (size_t)n));
@@ -851,24 +868,42 @@ void sum_counters(const unsigned long long *h, int r0, int r1, hpmc_counters *ou
     out->rechecks = tot[kRechecks];
 }
 
+// Enqueue the copies of the error word and (optionally) the counters into
+// the pinned staging block; the caller synchronises once.
+int stage_err_counters(hpmc_ctx *c, cudaStream_t s, bool counters)
+{
+    CK(cudaMemcpyAsync(c->h_pin + kPinErr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (counters)
+        CK(cudaMemcpyAsync(c->h_pin + kPinHead, c->d_counters,
+                           sizeof(unsigned long long) * counter_words(c), cudaMemcpyDeviceToHost, s));
+    return HPMC_OK;
+}
+
+int staged_err(const hpmc_ctx *c)
+{
+    const int e = *reinterpret_cast<const int *>(c->h_pin + kPinErr);
+    if (e && getenv("HPMC_VERBOSE"))
+        fprintf(stderr, "hpmc: device error %d (%s)\n", e,
+                e == kErrCandCap ? "neighbourhood or lens capacity" : "cell bin capacity");
+    return e ? HPMC_ERR_DEVICE : HPMC_OK;
+}
+
 int read_counters(hpmc_ctx *c, std::vector<unsigned long long> &h, cudaStream_t s)
 {
-    h.resize((size_t)c->reps.size() * kRepSlots * kNumCounters);
-    CK(cudaMemcpyAsync(h.data(), c->d_counters, sizeof(unsigned long long) * h.size(),
+    h.resize(counter_words(c));
+    CK(cudaMemcpyAsync(c->h_pin + kPinHead, c->d_counters, sizeof(unsigned long long) * h.size(),
                        cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    std::memcpy(h.data(), c->h_pin + kPinHead, sizeof(unsigned long long) * h.size());
     return HPMC_OK;
 }
 
 int read_err(hpmc_ctx *c, cudaStream_t s)
 {
-    int e = 0;
-    CK(cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int rc = stage_err_counters(c, s, false);
+    if (rc != HPMC_OK) return rc;
     CK(cudaStreamSynchronize(s));
-    if (e && getenv("HPMC_VERBOSE"))
-        fprintf(stderr, "hpmc: device error %d (%s)\n", e,
-                e == kErrCandCap ? "neighbourhood or lens capacity" : "cell bin capacity");
-    return e ? HPMC_ERR_DEVICE : HPMC_OK;
+    return staged_err(c);
 }
 
 int create_ctx(hpmc_ctx **out, const std::vector<RepHost> &reps, uint64_t seed, int precision,
@@ -1277,29 +1312,26 @@ int hpmc_get_state(hpmc_ctx *c, double *pos, double *quat, int mem, uint64_t *sw
             CK(cudaGetLastError());
             CK(cudaMemcpyAsync(pos, c->d_stage, sizeof(double) * 3 * (size_t)n,
                                cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
         }
         if (quat) {
+            // (the staging buffer is reused: the position copy must finish first)
+            if (pos) CK(cudaStreamSynchronize(s));
             k_pack<<<nb, 256, 0, s>>>(n, nullptr, c->d_quat, nullptr, c->d_stage);
             CK(cudaGetLastError());
             CK(cudaMemcpyAsync(quat, c->d_stage, sizeof(double) * 4 * (size_t)n,
                                cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
         }
     }
-    if (sweep) {
-        unsigned long long v = 0;
-        CK(cudaMemcpyAsync(&v, c->d_sweep, sizeof v, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        *sweep = v;
-    }
-    if (counters) {
-        std::vector<unsigned long long> h;
-        int rc = read_counters(c, h, s);
-        if (rc != HPMC_OK) return rc;
-        sum_counters(h.data(), 0, (int)c->reps.size(), counters);
-    }
-    return read_err(c, s);
+    // the sweep index, the counters and the error word in the same round trip
+    if (sweep)
+        CK(cudaMemcpyAsync(c->h_pin + kPinSweep, c->d_sweep, sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+    int rc = stage_err_counters(c, s, counters != nullptr);
+    if (rc != HPMC_OK) return rc;
+    CK(cudaStreamSynchronize(s));
+    if (sweep) *sweep = c->h_pin[kPinSweep];
+    if (counters) sum_counters(c->h_pin + kPinHead, 0, (int)c->reps.size(), counters);
+    return staged_err(c);
 }
 
 int hpmc_get_replica(hpmc_ctx *c, int r, double *pos, double *quat, hpmc_counters *counters)
@@ -1342,8 +1374,9 @@ int hpmc_set_state(hpmc_ctx *c, const double *pos, const double *quat, int mem, 
     cudaStream_t s = (cudaStream_t)stream;
     int rc = copy_in(c, pos, quat, mem, s);
     if (rc != HPMC_OK) return rc;
-    unsigned long long v = sweep;
-    CK(cudaMemcpyAsync(c->d_sweep, &v, sizeof v, cudaMemcpyHostToDevice, s));
+    c->h_pin[kPinUp] = sweep;
+    CK(cudaMemcpyAsync(c->d_sweep, c->h_pin + kPinUp, sizeof(unsigned long long),
+                       cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     c->state_dirty = true;  // re-validate the new configuration at the next sweep
     return HPMC_OK;
@@ -1570,6 +1603,7 @@ void hpmc_destroy(hpmc_ctx *c)
     cudaFree(c->d_err);
     cudaFree(c->d_flag);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->h_pin) cudaFreeHost(c->h_pin);
     delete c;
 }
 

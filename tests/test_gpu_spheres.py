@@ -190,3 +190,37 @@ def test_errors_are_reported(lib):
         lib.Sampler(s.pos, s.L, q=s.q, n_r=1e7).sweep(1)  # lambda beyond the table
     with pytest.raises(lib.HPMCError):
         lib.Sampler(s.pos, 1.5, q=s.q, n_r=1.0).sweep(1)  # box smaller than two cells
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_configuration_check_at_contact(oracle, lib, precision):
+    """The start check: a pair closer than contact (by 1e-12) is an overlap,
+    one at contact (by 1e-12) is not; a position outside the box is an
+    argument error.  The FP32 form decides such pairs in FP64."""
+    s = W.spheres_256(seed=8)
+    for gap, code in ((-1e-12, -2), (1e-12, 0)):
+        pos = s.pos.copy()
+        d = np.array([1.0, 1.0, 0.0]) / np.sqrt(2.0)
+        pos[1] = (pos[0] + (1.0 + gap) * d) % s.L
+        # keep the pair clear of every other sphere
+        far = np.linalg.norm(((pos[2:] - pos[0] + s.L / 2) % s.L) - s.L / 2, axis=1)
+        keep = np.concatenate([[True, True], far > 2.2])
+        pos = pos[keep]
+        smp = lib.Sampler(pos, s.L, q=s.q, n_r=s.n_r, precision=precision)
+        if code:
+            with pytest.raises(lib.HPMCError) as e:
+                smp.sweep(1)
+            assert e.value.code == code
+        else:
+            smp.sweep(1)
+            p, _, _, c = smp.state()
+            ref, _, rc, _ = oracle.run(pos, s.L, q=s.q, n_r=s.n_r, n_sweeps=1)
+            assert np.array_equal(p, ref)
+        smp.close()
+    pos = s.pos.copy()
+    pos[3, 1] = s.L
+    smp = lib.Sampler(pos, s.L, q=s.q, n_r=s.n_r, precision=precision)
+    with pytest.raises(lib.HPMCError) as e:
+        smp.sweep(1)
+    assert e.value.code == -1
+    smp.close()
