@@ -35,6 +35,9 @@
  *     thickness is quantised into 32 levels chosen from the move's words.
  *     Option v0_mode 2: V_0 is the axis-aligned cube around the circumsphere
  *     (every attempt is a depletant; no rejection).
+ *   - Sec. IV.B (coexistence): Gibbs-ensemble colloid exchange between two
+ *     boxes with depletants inserted at the new position and reinserted in
+ *     the old box (configurational bias), spheres.
  *   - Sec. V: anisotropic colloids (hemispheres, discoids = oblate spheroids)
  *     with quaternion rotation moves; overlap of two convex colloids by
  *     Minkowski portal refinement on their support functions.
@@ -50,7 +53,9 @@
  * the shell V_0, lens containment by brute force, the uniformity of the shell
  * points, the Poisson mean of the shell volume, equality of the acceptance
  * probability with the circumsphere's, detailed balance and the
- * Asakura-Oosawa distribution.
+ * Asakura-Oosawa distribution; for the Gibbs exchange, detailed balance of
+ * one exchange against the closed form (Gibbs prior times exp(z_p dV_f)),
+ * the binomial box occupancy of an ideal gas, conservation and validity.
  */
 #include <math.h>
 #include <stdint.h>
@@ -1281,4 +1286,229 @@ long oracle_free_volume(int n, double L, int shape, const double *shape_params,
         if (!hit) ++free_count;
     }
     return free_count;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gibbs-ensemble colloid exchange with configurational bias (Sec. IV.B,    */
+/* coexistence of the penetrable-hard-sphere model): two boxes share one    */
+/* depletant reservoir (fugacity z_p); a colloid leaves one box for a       */
+/* uniform random position in the other.  Depletants are inserted at the    */
+/* new position; those that overlap the inserted colloid and no other       */
+/* colloid of that box block the move, or, with n_trial > 0, are reinserted */
+/* in the old box around the removed colloid (the weight of Eq. 12).  The   */
+/* Gibbs factor N_s V_d / ((N_d + 1) V_s) enters by a Metropolis test.      */
+/* Spheres.  Boxes keep their colloids in slots 0..n-1: a removed colloid's */
+/* slot takes the box's last colloid; an inserted one takes slot n.         */
+/* ------------------------------------------------------------------------ */
+
+enum { G_ATTEMPT = 0, G_ACCEPT, G_REJ_EMPTY, G_REJ_RATIO, G_REJ_OVERLAP, G_REJ_DEP,
+       G_REJ_CB, G_DEP_DRAWN, G_N = 8 };
+
+#define GIBBS_STREAM 0xFFFFFFFEu   /* RNG stream word of the exchange moves */
+
+typedef struct {
+    int n;
+    double L;
+    double *pos;
+} obox;
+
+static void gibbs_draw(const osim *S, uint32_t step, uint32_t purpose, uint32_t sub,
+                       uint32_t t, uint32_t w[4])
+{
+    draw(S->key, step, GIBBS_STREAM, purpose, sub, t, w);
+}
+
+/* Is the point x + v of box b free of every colloid of b except slot skip? */
+static int gibbs_free(const osim *S, const obox *b, const double x[3], const double v[3],
+                      int skip)
+{
+    for (int j = 0; j < b->n; ++j) {
+        if (j == skip) continue;
+        double u[3];
+        for (int d = 0; d < 3; ++d) u[d] = v[d] - min_image(b->pos[3 * j + d] - x[d], b->L);
+        if (dep_overlap(&S->sh, S->q, u, NULL)) return 0;
+    }
+    return 1;
+}
+
+/* CB weight of blocking depletant k: forward trials in the old colloid's
+ * circumsphere in the source box (overlapping it, free of the source's
+ * other colloids), reverse trials in the new one in the destination box
+ * (overlapping the inserted colloid, free of the others):
+ * f = N'_insert / (N_insert + 1), with n_trial - 1 reverse trials. */
+static double gibbs_cb(const osim *S, uint32_t step, uint32_t k, const obox *src, int i,
+                       const double xo[3], const obox *dst, const double xn[3], uint64_t *cnt)
+{
+    int n_fwd = S->n_trial, n_rev = S->n_trial - 1, found = 0, nf = 0, nr = 0;
+    uint32_t t = 0, t_max = 64u * (uint32_t)(n_fwd + 1);
+    double e[3];
+    while (found < n_fwd && next_in_ball(S, step, GIBBS_STREAM, P_CB_FWD, k, &t, t_max, e)) {
+        ++found;
+        if (!dep_overlap(&S->sh, S->q, e, NULL)) continue;
+        if (!gibbs_free(S, src, xo, e, i)) continue;
+        ++nf;
+    }
+    if (found < n_fwd) cnt[C_CAP]++;
+    t = 0;
+    t_max = 64u * (uint32_t)(n_rev + 1);
+    found = 0;
+    while (found < n_rev && next_in_ball(S, step, GIBBS_STREAM, P_CB_REV, k, &t, t_max, e)) {
+        ++found;
+        if (!dep_overlap(&S->sh, S->q, e, NULL)) continue;
+        if (!gibbs_free(S, dst, xn, e, -1)) continue;
+        ++nr;
+    }
+    if (found < n_rev) cnt[C_CAP]++;
+    cnt[C_CB_FWD_OK] += (uint64_t)nf;
+    cnt[C_CB_REV_OK] += (uint64_t)nr;
+    return (double)nf / (double)(nr + 1);
+}
+
+/* Acceptance of the exchange of slot i of box src to position xn of box dst
+ * (the Gibbs test, then Sec. III.B-D at the new position). */
+static int gibbs_accept(const osim *S, uint32_t step, obox *src, int i, obox *dst,
+                        const double xn[3], uint64_t *g, uint64_t *cnt)
+{
+    double Vs = (src->L * src->L) * src->L, Vd = (dst->L * dst->L) * dst->L;
+    double G = ((double)src->n * Vd) / ((double)(dst->n + 1) * Vs);
+    uint32_t wa[4];
+    gibbs_draw(S, step, P_ACCEPT, 1, 0, wa);
+    if (!(u53(wa[0], wa[1]) < G)) { g[G_REJ_RATIO]++; return 0; }
+    for (int j = 0; j < dst->n; ++j) {
+        double v[3];
+        for (int d = 0; d < 3; ++d) v[d] = min_image(dst->pos[3 * j + d] - xn[d], dst->L);
+        if ((v[0] * v[0] + v[1] * v[1]) + v[2] * v[2] < S->sh.d * S->sh.d) {
+            g[G_REJ_OVERLAP]++;
+            return 0;
+        }
+    }
+    if (!(S->lambda > 0.0)) return 1;
+    const double *xo = src->pos + 3 * i;
+    uint32_t wp[4];
+    gibbs_draw(S, step, P_POISSON, 0, 0, wp);
+    int n_p = poisson_invert(S->F, S->nF, u53(wp[0], wp[1]));
+    g[G_DEP_DRAWN] += (uint64_t)n_p;
+    cnt[C_DEP_DRAWN] += (uint64_t)n_p;
+    uint32_t t = 0, t_max = 64u * (uint32_t)(n_p + 1);
+    int n_block = 0;
+    double W = 1.0;
+    for (int k = 0; k < n_p; ++k) {
+        double e[3];
+        if (!next_in_ball(S, step, GIBBS_STREAM, P_DEP, 0, &t, t_max, e)) {
+            cnt[C_CAP]++;
+            break;
+        }
+        cnt[C_DEP_EVAL]++;
+        if (!dep_overlap(&S->sh, S->q, e, NULL)) continue;
+        if (!gibbs_free(S, dst, xn, e, -1)) continue;
+        cnt[C_DEP_BLOCKING]++;
+        ++n_block;
+        if (S->n_trial == 0) { g[G_REJ_DEP]++; return 0; }
+        double f = gibbs_cb(S, step, (uint32_t)k, src, i, xo, dst, xn, cnt);
+        if (f == 0.0) { g[G_REJ_CB]++; return 0; }
+        W = W * f;
+    }
+    if (n_block > 0) {
+        uint32_t w2[4];
+        gibbs_draw(S, step, P_ACCEPT, 0, 0, w2);
+        if (!(u53(w2[0], w2[1]) < W)) { g[G_REJ_CB]++; return 0; }
+    }
+    return 1;
+}
+
+/* One exchange attempt at step index `step`: source box from the top bit of
+ * the first word, slot i = floor(w_1 n_src / 2^32), new position
+ * L_dst u01(w) from the second draw. */
+static void gibbs_exchange(const osim *S, uint32_t step, obox box[2], uint64_t *g, uint64_t *cnt)
+{
+    uint32_t w[4], wx[4];
+    g[G_ATTEMPT]++;
+    gibbs_draw(S, step, P_MOVE, 0, 0, w);
+    int s = (int)(w[0] >> 31), dd = 1 - s;
+    obox *src = &box[s], *dst = &box[dd];
+    if (src->n == 0) { g[G_REJ_EMPTY]++; return; }
+    int i = (int)(((uint64_t)w[1] * (uint64_t)src->n) >> 32);
+    gibbs_draw(S, step, P_MOVE, 1, 0, wx);
+    double xn[3] = {dst->L * u01(wx[0]), dst->L * u01(wx[1]), dst->L * u01(wx[2])};
+    if (!gibbs_accept(S, step, src, i, dst, xn, g, cnt)) return;
+    for (int d = 0; d < 3; ++d) dst->pos[3 * dst->n + d] = xn[d];
+    dst->n++;
+    src->n--;
+    for (int d = 0; d < 3; ++d) src->pos[3 * i + d] = src->pos[3 * src->n + d];
+    g[G_ACCEPT]++;
+}
+
+/*
+ * A Gibbs pair of sphere boxes (replicas rep0, rep1 of seed; the exchange
+ * streams use rep0's key): n_cycles of { sweeps_per_cycle checkerboard
+ * sweeps of each box (sweep indices sweep0, sweep0 + 1, ...), then
+ * ex_per_cycle exchange attempts (steps step0, step0 + 1, ...) }.  pos0,
+ * pos1: capacity n[0] + n[1] slots each (3 doubles); n updated.  counters:
+ * 2 x C_N (sweeps and exchange depletant work of each box; the exchange's
+ * depletant counts go to the source box), g: G_N exchange counters.
+ */
+int oracle_gibbs_run(double diameter, double q, double n_r, int n_trial, double d_max0,
+                     double d_max1, uint64_t seed, uint32_t rep0, uint32_t rep1, double L0,
+                     double L1, int *n, double *pos0, double *pos1, uint64_t sweep0,
+                     uint64_t step0, int n_cycles, int sweeps_per_cycle, int ex_per_cycle,
+                     uint64_t *counters, uint64_t *g)
+{
+    if (!n || !pos0 || !pos1 || !counters || !g || n[0] < 0 || n[1] < 0 || n_cycles < 0)
+        return -1;
+    osim S;
+    double sp[1] = {diameter};
+    /* the pair's parameters (table, key) as box 0's; its box length is not used */
+    if (sim_init(&S, 1, L0, SHAPE_SPHERE, sp, 1, q, n_r, n_trial, 0, 0, 0.0, 0.0, 1.0,
+                 seed, rep0, 0, 1) != 0)
+        return -1;
+    obox box[2] = {{n[0], L0, pos0}, {n[1], L1, pos1}};
+    uint64_t sweep = sweep0, step = step0;
+    int rc = 0;
+    for (int cy = 0; cy < n_cycles && rc == 0; ++cy) {
+        for (int b = 0; b < 2 && rc == 0; ++b) {
+            if (box[b].n == 0 || sweeps_per_cycle == 0) continue;
+            rc = oracle_run(box[b].n, box[b].L, SHAPE_SPHERE, sp, 1, q, n_r, n_trial, 0, 0,
+                            b == 0 ? d_max0 : d_max1, 0.0, 1.0, seed, b == 0 ? rep0 : rep1, 0, 0,
+                            box[b].pos, NULL, sweep, sweeps_per_cycle, counters + b * C_N, 0,
+                            0.0, NULL);
+        }
+        sweep += (uint64_t)sweeps_per_cycle;
+        for (int e = 0; e < ex_per_cycle && rc == 0; ++e) {
+            uint32_t w[4];
+            gibbs_draw(&S, (uint32_t)step, P_MOVE, 0, 0, w);
+            int src = (int)(w[0] >> 31);
+            gibbs_exchange(&S, (uint32_t)step, box, g, counters + src * C_N);
+            ++step;
+        }
+    }
+    n[0] = box[0].n;
+    n[1] = box[1].n;
+    sim_free(&S);
+    return rc;
+}
+
+/* Acceptance count of one fixed exchange: slot i of box src (0 or 1) to the
+ * position xn of the other box, over n_rep independent steps step0 ...
+ * (Gibbs test included).  Used to check detailed balance directly. */
+long oracle_gibbs_acceptance(double diameter, double q, double n_r, int n_trial, uint64_t seed,
+                             uint32_t rep0, double L0, double L1, int n0, int n1,
+                             const double *pos0, const double *pos1, int src, int i,
+                             const double *xn, uint64_t step0, long n_rep, uint64_t *g)
+{
+    if (!pos0 || !pos1 || !xn || !g || src < 0 || src > 1 || n_rep < 0) return -1;
+    int ns = src == 0 ? n0 : n1;
+    if (i < 0 || i >= ns) return -1;
+    osim S;
+    double sp[1] = {diameter};
+    if (sim_init(&S, 1, L0, SHAPE_SPHERE, sp, 1, q, n_r, n_trial, 0, 0, 0.0, 0.0, 1.0, seed,
+                 rep0, 0, 1) != 0)
+        return -1;
+    obox box[2] = {{n0, L0, (double *)pos0}, {n1, L1, (double *)pos1}};
+    uint64_t cnt[C_N] = {0};
+    long acc = 0;
+    for (long r = 0; r < n_rep; ++r)
+        acc += gibbs_accept(&S, (uint32_t)(step0 + (uint64_t)r), &box[src], i, &box[1 - src], xn,
+                            g, cnt);
+    sim_free(&S);
+    return acc;
 }

@@ -124,6 +124,20 @@ def lib():
             L.oracle_shell_points.restype = ctypes.c_long
             L.oracle_cube_lambda.argtypes = [ctypes.c_double, ctypes.c_double]
             L.oracle_cube_lambda.restype = ctypes.c_double
+            ip = ctypes.POINTER(ctypes.c_int)
+            L.oracle_gibbs_run.argtypes = [
+                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                ctypes.c_uint32, ctypes.c_double, ctypes.c_double, ip, dp, dp,
+                ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                u64p, u64p]
+            L.oracle_gibbs_run.restype = ctypes.c_int
+            L.oracle_gibbs_acceptance.argtypes = [
+                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
+                ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int, dp,
+                ctypes.c_uint64, ctypes.c_long, u64p]
+            L.oracle_gibbs_acceptance.restype = ctypes.c_long
             _lib = L
     return _lib
 
@@ -271,6 +285,58 @@ def shell_points(R_s, d_max, lvl, n_att, *, seed=1, sweep=0, tag=0):
     if m < 0:
         raise ValueError("oracle_shell_points rejected its arguments")
     return e[:m].copy()
+
+
+GIBBS_COUNTERS = ("attempts", "accept", "reject_empty", "reject_ratio", "reject_overlap",
+                  "reject_depletant", "reject_cb", "dep_drawn")
+
+
+def gibbs_run(pos0, pos1, L0, L1, *, diameter=1.0, q=0.0, n_r=0.0, n_trial=0, d_max=(0.1, 0.1),
+              seed=1, replicas=(0, 1), sweep0=0, step0=0, n_cycles=1, sweeps_per_cycle=1,
+              ex_per_cycle=1):
+    """A Gibbs pair of sphere boxes: cycles of sweeps of both boxes, then
+    exchange attempts.  Returns (pos0, pos1, counters0, counters1, gibbs
+    counters) with the boxes' live colloids."""
+    a = np.ascontiguousarray(pos0, dtype=np.float64).reshape(-1, 3)
+    b = np.ascontiguousarray(pos1, dtype=np.float64).reshape(-1, 3)
+    cap = a.shape[0] + b.shape[0]
+    p0 = np.zeros((cap, 3))
+    p1 = np.zeros((cap, 3))
+    p0[:a.shape[0]] = a
+    p1[:b.shape[0]] = b
+    n = np.array([a.shape[0], b.shape[0]], dtype=np.int32)
+    cnt = np.zeros(2 * N_COUNTERS, dtype=np.uint64)
+    g = np.zeros(len(GIBBS_COUNTERS), dtype=np.uint64)
+    rc = lib().oracle_gibbs_run(
+        float(diameter), float(q), float(n_r), int(n_trial), float(d_max[0]), float(d_max[1]),
+        int(seed), int(replicas[0]), int(replicas[1]), float(L0), float(L1),
+        _p(n, ctypes.c_int), _p(p0, ctypes.c_double), _p(p1, ctypes.c_double), int(sweep0),
+        int(step0), int(n_cycles), int(sweeps_per_cycle), int(ex_per_cycle),
+        _p(cnt, ctypes.c_uint64), _p(g, ctypes.c_uint64))
+    if rc != 0:
+        raise ValueError("oracle_gibbs_run rejected its arguments")
+    c0 = {name: int(cnt[k]) for k, name in enumerate(COUNTERS)}
+    c1 = {name: int(cnt[N_COUNTERS + k]) for k, name in enumerate(COUNTERS)}
+    gc = {name: int(g[k]) for k, name in enumerate(GIBBS_COUNTERS)}
+    return p0[:n[0]].copy(), p1[:n[1]].copy(), c0, c1, gc
+
+
+def gibbs_acceptance(pos0, pos1, L0, L1, src, i, xn, *, diameter=1.0, q=0.0, n_r=0.0,
+                     n_trial=0, seed=1, replica=0, step0=0, n_rep=1000):
+    """How many of n_rep evaluations accept moving slot i of box src to xn
+    in the other box.  Returns (count, gibbs counters)."""
+    a = np.ascontiguousarray(pos0, dtype=np.float64).reshape(-1, 3)
+    b = np.ascontiguousarray(pos1, dtype=np.float64).reshape(-1, 3)
+    x = np.ascontiguousarray(xn, dtype=np.float64)
+    g = np.zeros(len(GIBBS_COUNTERS), dtype=np.uint64)
+    acc = lib().oracle_gibbs_acceptance(
+        float(diameter), float(q), float(n_r), int(n_trial), int(seed), int(replica),
+        float(L0), float(L1), a.shape[0], b.shape[0], _p(a, ctypes.c_double),
+        _p(b, ctypes.c_double), int(src), int(i), _p(x, ctypes.c_double), int(step0),
+        int(n_rep), _p(g, ctypes.c_uint64))
+    if acc < 0:
+        raise ValueError("oracle_gibbs_acceptance rejected its arguments")
+    return int(acc), {name: int(g[k]) for k, name in enumerate(GIBBS_COUNTERS)}
 
 
 def free_volume(pos, L, q, *, shape=SHAPE_SPHERE, shape_params=(1.0,), quat=None,
