@@ -207,6 +207,42 @@ int hpmc_set_fp32_margin(hpmc_ctx *ctx, double margin);
  * anisotropic shape or an unknown mode.  Takes effect at the next sweep. */
 int hpmc_set_v0(hpmc_ctx *ctx, int mode);
 
+/* Colloids in use.  Replica r keeps its colloids in its slots 0..n_live-1
+ * (the RNG stream of a colloid is its slot); slots beyond are not moved,
+ * binned or tested.  hpmc_set_live sets the count of one replica (0..its
+ * number of slots; spheres; re-validated at the next sweep); hpmc_get_live
+ * writes every replica's count to n_live[0..n_rep).  Both synchronise the
+ * device.  Without these calls every slot is in use. */
+int hpmc_set_live(hpmc_ctx *ctx, int replica, int n_live);
+int hpmc_get_live(hpmc_ctx *ctx, int *n_live);
+
+/* Gibbs-ensemble colloid exchange (Sec. IV.B, coexistence; spheres).
+ * Replicas 2p and 2p + 1 are the two boxes of pair p (they must share q,
+ * n_r and n_trial: one depletant reservoir).  Each call makes n_attempts
+ * exchange attempts per pair, one after another, all pairs in parallel
+ * (one CTA per pair), on `stream`.  Attempt s of pair p (s counts the
+ * pair's attempts from 0) draws from box 2p's key with stream word
+ * 0xFFFFFFFE and counter s: purpose 1 sub 0 picks the source box (top bit
+ * of word 0) and its slot floor(w_1 n_src / 2^32); purpose 1 sub 1 the new
+ * position L_dst u01(w_d); purpose 7 sub 1 the Metropolis test
+ * u53 < N_src V_dst / ((N_dst + 1) V_src); then the hard-core test in the
+ * new box and the depletants of Sec. III.B at the new position (purposes
+ * 3, 4), a depletant overlapping the inserted colloid and no other colloid
+ * of its box blocking the move, or with n_trial > 0 entering the weight of
+ * Eq. 12 with forward trials around the old position in the old box and
+ * n_trial - 1 reverse trials around the new one (purposes 5, 6 with the
+ * depletant index as sub; accept with purpose 7 sub 0, u53 < W).  On
+ * acceptance the new box's slot n_dst takes the colloid and the old box's
+ * last colloid moves into the vacated slot.  The exchange's depletant
+ * counters go to the source box's counters.  FP64.  HPMC_ERR_ARG for an
+ * odd replica count, a non-sphere shape or unequal depletant parameters. */
+int hpmc_gibbs_exchange(hpmc_ctx *ctx, int n_attempts, void *stream);
+
+/* Pair p's attempt count and its counters (attempts, accepted, rejected:
+ * empty source box, Gibbs ratio, overlap, depletant, CB; depletants drawn).
+ * Synchronises; HPMC_ERR_DEVICE for a recorded kernel error. */
+int hpmc_get_gibbs(hpmc_ctx *ctx, int pair, uint64_t *step, uint64_t counters[8]);
+
 /* Per-kernel timing.  While on, hpmc_sweep launches its kernels one by one
  * (no graph) with CUDA events around the cell-list kernels and around every
  * colour-phase kernel.  hpmc_get_timing synchronises and returns the summed

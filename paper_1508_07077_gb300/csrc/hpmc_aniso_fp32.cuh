@@ -718,7 +718,9 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
             c_rev += od.rev;
             if (od.rejected) {
                 accept = false;
-                if (!CB) ++c_dep;
+                // (a replica without CB in a batch that has some: its first
+                // blocking depletant rejects the move as a depletant rejection)
+                if (!CB || R.n_trial == 0) ++c_dep;
                 else ++c_cb;
             } else if (CB && tid == 0 && od.nblock > 0) {
                 const uint4 wa = draw(R.key0, R.key1, sweep, (uint32_t)(i - R.off), kPAccept, 0, 0);

@@ -322,6 +322,7 @@ __global__ void k_check_aniso(const __grid_constant__ SimParams P, int *flag)
     if (g >= P.n_total) return;
     const int r = P.rep_of[g];
     const Rep &R = P.reps[r];
+    if (g - R.off >= P.n_live[r]) return;
     const double4 pi = P.pos[g];
     if (!(pi.x >= 0.0 && pi.x < R.L && pi.y >= 0.0 && pi.y < R.L && pi.z >= 0.0 && pi.z < R.L)) {
         atomicOr(flag, 2);

@@ -64,6 +64,10 @@ __global__ void k_cells_bin(const __grid_constant__ SimParams P)
         s.sweep = sweep;
         P.sched[r] = s;
     }
+    if (g - R.off >= P.n_live[r]) {   // a slot not in use (Gibbs pair)
+        if (P.binpos) P.binpos[g] = -1;
+        return;
+    }
     const double4 p = P.pos[g];
     const int nc = R.nc;
     const int cx = cell_coord(p.x, sigma[0], R.L, R.w, nc);

@@ -237,6 +237,12 @@ struct SimParams {
     float4 *mv_bin;
     float4 *lens_bin;      // the first kLensInline lens points of each bin slot
     float4 *bin_q;         // FP32 orientation of each bin slot (anisotropic FP32 form)
+    // colloids in use per replica (slots off .. off + n_live - 1; fewer than
+    // the replica's slots only in Gibbs-ensemble pairs), and per pair of
+    // replicas the exchange step counter and counters
+    int *n_live;
+    unsigned long long *gibbs_step;
+    unsigned long long *gibbs_cnt;
     Sched *sched;          // per replica
     unsigned long long *sweep;     // next sweep index (all replicas)
     unsigned long long *counters;  // [n_rep][kRepSlots][kNumCounters]

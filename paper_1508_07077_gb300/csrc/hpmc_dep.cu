@@ -4,6 +4,7 @@
 // checkerboard geometry of every replica (Sec. III.E), device buffers, and one
 // CUDA graph per sweep of the whole batch (cell lists, depletant lens lists,
 // 8 colour phases).  All per-step arithmetic runs in the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -23,6 +24,7 @@
 #include "hpmc_aniso_fp64.cuh"
 #include "hpmc_aniso_fp32.cuh"
 #include "hpmc_probe.cuh"
+#include "hpmc_gibbs.cuh"
 
 using namespace hpmc;
 
@@ -107,6 +109,9 @@ struct hpmc_ctx {
     // error word, check flag, counters), so that a call issues all its copies
     // and synchronises once
     unsigned long long *h_pin = nullptr;   // [kPinHead + counters]
+    // colloids in use per replica; Gibbs pairs' exchange steps and counters
+    int *d_n_live = nullptr;
+    unsigned long long *d_gibbs_step = nullptr, *d_gibbs_cnt = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool dirty = true;        // parameters changed: re-derive and re-record the graph
@@ -410,6 +415,9 @@ SimParams make_params(hpmc_ctx *c)
     P.prop_quat = c->d_prop_quat;
     P.n_cta = c->n_cta;
     P.task = c->d_task;
+    P.n_live = c->d_n_live;
+    P.gibbs_step = c->d_gibbs_step;
+    P.gibbs_cnt = c->d_gibbs_cnt;
     P.task_ord = c->d_task_ord;
     P.cls_count = c->d_cls_count;
     P.binpos = c->d_binpos;
@@ -815,6 +823,12 @@ int alloc_ctx(hpmc_ctx *c)
     const int n = c->n_total, n_rep = (int)c->reps.size();
     CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     CK(cudaMallocHost(&c->h_pin, sizeof(unsigned long long) * (kPinHead + counter_words(c))));
+    {
+        std::vector<int> live((size_t)n_rep);
+        for (int r = 0; r < n_rep; ++r) live[(size_t)r] = c->reps[(size_t)r].n;
+        CK(cudaMalloc(&c->d_n_live, sizeof(int) * (size_t)n_rep));
+        CK(cudaMemcpy(c->d_n_live, live.data(), sizeof(int) * (size_t)n_rep, cudaMemcpyHostToDevice));
+    }
     CK(cudaMalloc(&c->d_pos, sizeof(double4) * (size_t)n));
     CK(cudaMalloc(&c->d_quat, sizeof(double4) * (size_t)n));
     CK(cudaMalloc(&c->d_rel, sizeof(float4) * (size_t)n));
@@ -1437,6 +1451,78 @@ int hpmc_cell_list(int n, double box_l, int n_cell, const double *pos_dev, uint6
     return rc;
 }
 
+int hpmc_set_live(hpmc_ctx *c, int replica, int n_live)
+{
+    if (!c || replica < 0 || replica >= (int)c->reps.size() || c->prm.shape != HPMC_SPHERE ||
+        n_live < 0 || n_live > c->reps[(size_t)replica].n)
+        return HPMC_ERR_ARG;
+    DeviceGuard g(c->device);
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(c->d_n_live + replica, &n_live, sizeof(int), cudaMemcpyHostToDevice));
+    c->state_dirty = true;   // re-validate the colloids in use at the next sweep
+    return HPMC_OK;
+}
+
+int hpmc_get_live(hpmc_ctx *c, int *n_live)
+{
+    if (!c || !n_live) return HPMC_ERR_ARG;
+    DeviceGuard g(c->device);
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(n_live, c->d_n_live, sizeof(int) * c->reps.size(), cudaMemcpyDeviceToHost));
+    return HPMC_OK;
+}
+
+int hpmc_gibbs_exchange(hpmc_ctx *c, int n_attempts, void *stream)
+{
+    if (!c || n_attempts < 0) return HPMC_ERR_ARG;
+    const int n_rep = (int)c->reps.size();
+    if (c->prm.shape != HPMC_SPHERE || (n_rep & 1)) return HPMC_ERR_ARG;
+    for (int p = 0; p < n_rep / 2; ++p) {
+        const RepHost &a = c->reps[(size_t)(2 * p)], &b = c->reps[(size_t)(2 * p + 1)];
+        if (a.q != b.q || a.n_r != b.n_r || a.n_trial != b.n_trial) return HPMC_ERR_ARG;
+    }
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->dirty || c->state_dirty) {
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, s));
+        CK(cudaStreamWaitEvent(c->cap_stream, ev, 0));
+        cudaEventDestroy(ev);
+        int rc = c->dirty ? prepare(c) : check_config(c);
+        if (rc != HPMC_OK) return rc;
+    }
+    if (!c->d_gibbs_step) {
+        const size_t np = (size_t)(n_rep / 2);
+        CK(cudaMalloc(&c->d_gibbs_step, sizeof(unsigned long long) * np));
+        CK(cudaMalloc(&c->d_gibbs_cnt, sizeof(unsigned long long) * np * kGibbsCounters));
+        CK(cudaMemset(c->d_gibbs_step, 0, sizeof(unsigned long long) * np));
+        CK(cudaMemset(c->d_gibbs_cnt, 0, sizeof(unsigned long long) * np * kGibbsCounters));
+    }
+    if (n_attempts == 0 || n_rep == 0) return HPMC_OK;
+    SimParams P = make_params(c);
+    k_gibbs_exchange<<<n_rep / 2, kMaxThreads, 0, s>>>(P, n_attempts);
+    CK(cudaGetLastError());
+    return HPMC_OK;
+}
+
+int hpmc_get_gibbs(hpmc_ctx *c, int pair, uint64_t *step, uint64_t *counters)
+{
+    if (!c || pair < 0 || pair >= (int)c->reps.size() / 2) return HPMC_ERR_ARG;
+    DeviceGuard g(c->device);
+    CK(cudaDeviceSynchronize());
+    unsigned long long st = 0, cnt[kGibbsCounters] = {0};
+    if (c->d_gibbs_step) {
+        CK(cudaMemcpy(&st, c->d_gibbs_step + pair, sizeof st, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(cnt, c->d_gibbs_cnt + (size_t)pair * kGibbsCounters, sizeof cnt,
+                      cudaMemcpyDeviceToHost));
+    }
+    if (step) *step = st;
+    if (counters)
+        for (int k = 0; k < kGibbsCounters; ++k) counters[k] = cnt[k];
+    return read_err(c, c->cap_stream);
+}
+
 int hpmc_free_volume(hpmc_ctx *c, int replica, double q, uint64_t seed, uint32_t sample,
                      uint64_t n_probe, uint64_t *n_free)
 {
@@ -1453,26 +1539,28 @@ int hpmc_free_volume(hpmc_ctx *c, int replica, double q, uint64_t seed, uint32_t
     R.r_dep = 0.5 * q;
     const double Rd = 0.5 * c->prm.sp[0] + 0.5 * q;
     R.R_dep2 = Rd * Rd;
-    const int n = R.n, nc = R.nc, ncell = nc * nc * nc;
+    const int nc = R.nc, ncell = nc * nc * nc;
     const double w = R.L / (double)nc;
     cudaStream_t s = c->cap_stream;
     CK(cudaStreamSynchronize(s));
+    int n = R.n;   // the colloids in use (slots 0 .. n - 1)
+    CK(cudaMemcpy(&n, c->d_n_live + replica, sizeof(int), cudaMemcpyDeviceToHost));
     int *count = nullptr, *cell_of = nullptr, *start = nullptr, *idx = nullptr;
     unsigned long long *d_free = nullptr;
     cudaError_t e = cudaMallocAsync(&count, sizeof(int) * (size_t)ncell, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&cell_of, sizeof(int) * (size_t)n, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&cell_of, sizeof(int) * (size_t)std::max(n, 1), s);
     if (e == cudaSuccess) e = cudaMallocAsync(&start, sizeof(int) * ((size_t)ncell + 1), s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&idx, sizeof(int) * (size_t)n, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&idx, sizeof(int) * (size_t)std::max(n, 1), s);
     if (e == cudaSuccess) e = cudaMallocAsync(&d_free, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)ncell, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_free, 0, sizeof(unsigned long long), s);
     unsigned long long h_free = 0;
     if (e == cudaSuccess) {
         const double *pos = reinterpret_cast<const double *>(c->d_pos + R.off);
-        k_csr_count<<<(n + 255) / 256, 256, 0, s>>>(n, R.L, w, nc, pos, 4, R.key0, R.key1, 0u,
-                                                    cell_of, count);
+        const int nb = std::max(1, (n + 255) / 256);   // (an empty box still has its probes)
+        k_csr_count<<<nb, 256, 0, s>>>(n, R.L, w, nc, pos, 4, R.key0, R.key1, 0u, cell_of, count);
         k_csr_scan<<<1, 1024, 0, s>>>(ncell, count, start);
-        k_csr_scatter<<<(n + 255) / 256, 256, 0, s>>>(n, cell_of, count, idx);
+        k_csr_scatter<<<nb, 256, 0, s>>>(n, cell_of, count, idx);
         const unsigned long long want = (n_probe + 255) / 256;
         const int blocks = (int)std::min<unsigned long long>(want > 0 ? want : 1, 152ull * 16);
         k_free_volume<<<blocks, 256, 0, s>>>(R, nc, R.key0, R.key1, 0u, c->d_pos + R.off,
@@ -1604,6 +1692,9 @@ void hpmc_destroy(hpmc_ctx *c)
     cudaFree(c->d_flag);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->h_pin) cudaFreeHost(c->h_pin);
+    cudaFree(c->d_n_live);
+    cudaFree(c->d_gibbs_step);
+    cudaFree(c->d_gibbs_cnt);
     delete c;
 }
 

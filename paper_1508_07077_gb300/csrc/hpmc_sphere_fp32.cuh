@@ -508,6 +508,7 @@ __global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_consta
     // phases read its results before they wait.)
     const int r = P.rep_of[g];
     const Rep &R = P.reps[r];
+    if (g - R.off >= P.n_live[r]) return;   // a slot not in use (Gibbs pair)
     const uint32_t sweep = (uint32_t)(*P.sweep);
     float4 *out = P.lens + (size_t)g * P.lens_cap;
     const int4 h = lens_of_move<V0>(P, R, g, sweep, &s_mv[wl], nullptr, 0, out);
@@ -551,6 +552,10 @@ __global__ void __launch_bounds__(128, 4) k_lens_shell_fp32(const __grid_constan
     }
     const int r = P.rep_of[g];
     const Rep &R = P.reps[r];
+    if (g - R.off >= P.n_live[r]) {   // a slot not in use (Gibbs pair)
+        pdl_wait();
+        return;
+    }
     const int i = g;
     const uint32_t sweep = (uint32_t)(*P.sweep);
     const uint32_t tag = (uint32_t)(g - R.off);
@@ -1018,7 +1023,9 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
             c_rev += o.rev;
             if (o.rejected) {
                 accept = false;
-                if (!CB) ++c_dep;
+                // (a replica without CB in a batch that has some: its first
+                // blocking depletant rejects the move as a depletant rejection)
+                if (!CB || R.n_trial == 0) ++c_dep;
                 else ++c_cb;
             } else if (CB && tid == 0 && o.nblock > 0) {
                 const uint4 wa = draw(R.key0, R.key1, sweep, (uint32_t)(i - R.off), kPAccept, 0, 0);
@@ -1091,6 +1098,7 @@ __global__ void k_check_spheres32(const __grid_constant__ SimParams P, int *flag
     if (g >= P.n_total) return;
     const int r = P.rep_of[g];
     const Rep &R = P.reps[r];
+    if (g - R.off >= P.n_live[r]) return;
     const double4 pi = P.pos[g];
     if (!(pi.x >= 0.0 && pi.x < R.L && pi.y >= 0.0 && pi.y < R.L && pi.z >= 0.0 && pi.z < R.L)) {
         atomicOr(flag, 2);

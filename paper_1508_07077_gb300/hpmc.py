@@ -26,7 +26,8 @@ HPMC_V0_CIRCUMSPHERE, HPMC_V0_SHELL, HPMC_V0_CUBE = 0, 1, 2
 EXPORTS = ("hpmc_init", "hpmc_init_batch", "hpmc_get_replica", "hpmc_set_replica_moves",
            "hpmc_set_shape", "hpmc_set_depletant", "hpmc_set_moves",
            "hpmc_set_cells", "hpmc_set_launch", "hpmc_autotune", "hpmc_set_fp32_margin",
-           "hpmc_set_v0", "hpmc_set_timing",
+           "hpmc_set_v0", "hpmc_set_live", "hpmc_get_live", "hpmc_gibbs_exchange",
+           "hpmc_get_gibbs", "hpmc_set_timing",
            "hpmc_get_timing", "hpmc_sweep", "hpmc_get_state",
            "hpmc_set_state", "hpmc_reset_counters", "hpmc_sync", "hpmc_cell_list",
            "hpmc_cell_list_noalloc", "hpmc_free_volume", "hpmc_strerror", "hpmc_destroy")
@@ -88,6 +89,11 @@ def load(path: str = LIB_PATH):
                                 ctypes.POINTER(ctypes.c_double)]
     L.hpmc_set_fp32_margin.argtypes = [vp, ctypes.c_double]
     L.hpmc_set_v0.argtypes = [vp, ip]
+    L.hpmc_set_live.argtypes = [vp, ip, ip]
+    L.hpmc_get_live.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.hpmc_gibbs_exchange.argtypes = [vp, ip, vp]
+    L.hpmc_get_gibbs.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_uint64),
+                                 ctypes.POINTER(ctypes.c_uint64)]
     L.hpmc_set_timing.argtypes = [vp, ip]
     L.hpmc_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_uint64), ip]
@@ -252,6 +258,81 @@ def hpmc_set_fp32_margin(ctx, margin):
 
 def hpmc_set_v0(ctx, mode):
     _check(load().hpmc_set_v0(ctx, int(mode)), "hpmc_set_v0")
+
+
+def hpmc_set_live(ctx, replica, n_live):
+    _check(load().hpmc_set_live(ctx, int(replica), int(n_live)), "hpmc_set_live")
+
+
+def hpmc_get_live(ctx, n_rep):
+    out = (ctypes.c_int * n_rep)()
+    _check(load().hpmc_get_live(ctx, out), "hpmc_get_live")
+    return [int(x) for x in out]
+
+
+def hpmc_gibbs_exchange(ctx, n_attempts, stream=None):
+    _check(load().hpmc_gibbs_exchange(ctx, int(n_attempts), _stream(stream)),
+           "hpmc_gibbs_exchange")
+
+
+GIBBS_COUNTERS = ("attempts", "accept", "reject_empty", "reject_ratio", "reject_overlap",
+                  "reject_depletant", "reject_cb", "dep_drawn")
+
+
+def hpmc_get_gibbs(ctx, pair):
+    """(attempt count, counters dict) of Gibbs pair `pair`."""
+    step = ctypes.c_uint64(0)
+    cnt = (ctypes.c_uint64 * 8)()
+    _check(load().hpmc_get_gibbs(ctx, int(pair), ctypes.byref(step), cnt), "hpmc_get_gibbs")
+    return int(step.value), {k: int(v) for k, v in zip(GIBBS_COUNTERS, cnt)}
+
+
+class GibbsPairs:
+    """Gibbs-ensemble pairs of sphere boxes in one context: pair p is
+    replicas 2p, 2p + 1, each with one slot per colloid of the pair."""
+
+    def __init__(self, pairs, *, diameter=1.0, seed=1, precision=HPMC_FP64, device=0):
+        """pairs: list of ((pos0, L0), (pos1, L1), params) with params a dict
+        of q, n_r, n_trial, d_max (per box: d_max may be a pair)."""
+        reps, self.live = [], []
+        for p, ((a, L0), (b, L1), prm) in enumerate(pairs):
+            a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1, 3)
+            b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1, 3)
+            cap = a.shape[0] + b.shape[0]
+            dm = prm.get("d_max", 0.1)
+            dm = dm if isinstance(dm, (tuple, list)) else (dm, dm)
+            for k, (x, L) in enumerate(((a, L0), (b, L1))):
+                slots = np.zeros((cap, 3))
+                slots[:x.shape[0]] = x
+                reps.append({"n": cap, "box_l": L, "pos": slots, "q": prm.get("q", 0.0),
+                             "n_r": prm.get("n_r", 0.0), "n_trial": prm.get("n_trial", 0),
+                             "d_max": dm[k], "replica": 2 * p + k})
+                self.live.append(x.shape[0])
+        self.reps = reps
+        self.ctx = hpmc_init_batch(reps, shape=HPMC_SPHERE, shape_params=(diameter,), seed=seed,
+                                   precision=precision, device=device)
+        for r, n in enumerate(self.live):
+            hpmc_set_live(self.ctx, r, n)
+
+    def cycle(self, sweeps=1, exchanges=1, stream=None):
+        if sweeps:
+            hpmc_sweep(self.ctx, sweeps, stream)
+        if exchanges:
+            hpmc_gibbs_exchange(self.ctx, exchanges, stream)
+
+    def boxes(self):
+        """[(pos of the colloids in use, counters)] per replica."""
+        live = hpmc_get_live(self.ctx, len(self.reps))
+        out = []
+        for r, rep in enumerate(self.reps):
+            pos, _, cnt = hpmc_get_replica(self.ctx, r, rep["n"])
+            out.append((pos[:live[r]].copy(), cnt))
+        return out
+
+    def close(self):
+        if self.ctx is not None:
+            hpmc_destroy(self.ctx)
+            self.ctx = None
 
 
 def hpmc_set_timing(ctx, on):

@@ -76,3 +76,23 @@ def test_batch_per_replica_moves_and_resume(oracle, lib):
                                   seed=2, replica=r["replica"], n_sweeps=7)
         assert np.array_equal(pos, ref), k
     lib.hpmc_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_mixed_configurational_bias(oracle, lib, precision):
+    """Replicas with and without configurational bias in one batch: the
+    rejections of the n_trial = 0 replicas count as depletant rejections."""
+    reps = _replicas(4, seed=5)
+    for k, r in enumerate(reps):
+        r["n_trial"] = 3 if k % 2 else 0
+    ctx = lib.hpmc_init_batch(reps, seed=9, precision=precision)
+    lib.hpmc_sweep(ctx, 5)
+    for k, r in enumerate(reps):
+        pos, _, cnt = lib.hpmc_get_replica(ctx, k, r["n"])
+        ref, _, rc, _ = oracle.run(r["pos"], r["box_l"], q=r["q"], n_r=r["n_r"],
+                                   n_trial=r["n_trial"], d_max=r["d_max"], seed=9,
+                                   replica=r["replica"], n_sweeps=5)
+        assert np.array_equal(pos, ref), k
+        for name in oracle.PARITY_COUNTERS:
+            assert cnt[name] == rc[name], (k, name, cnt[name], rc[name])
+    lib.hpmc_destroy(ctx)
