@@ -301,6 +301,123 @@ def run_batched(args, ws, rank, local):
         dist.destroy_process_group()
 
 
+# Gibbs exchange kernel, per attempt of a depletant or CB-trial stream:
+# Philox (40) + ball test (11) + ~6 colloids within reach x 8 (point test).
+OPS_PER_GIBBS_TRIAL = 40.0 + 11.0 + 6 * 8.0
+
+
+def run_gibbs(args, ws, rank, local):
+    """Gibbs-ensemble coexistence runs (Sec. IV.B): 152 pairs (one CTA per
+    pair) of two boxes of 512 spheres at phi_c = 0.12, q = 0.8, eta_r from
+    0.80 to 1.00 across the pairs (a scan through coexistence), n_trial =
+    100.  One step = 1 sweep of every box + 100 exchange attempts per pair.
+    (512 per box: with q = 0.8 the cell width must exceed 1.8, and 256
+    spheres would leave cells too wide for the cell-bin capacity.)"""
+    import torch
+    import torch.distributed as dist
+    from paper_1508_07077_gb300 import build, hpmc, replicas as R, workloads as W
+
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    try:
+        hpmc.load()
+    except ImportError:
+        build.build()
+        hpmc.load()
+    prec = hpmc.HPMC_FP32_RECHECK if args.precision == "fp32" else hpmc.HPMC_FP64
+    stream = torch.cuda.current_stream()
+    n_pairs, N, phi, q, n_trial, n_ex = 152, 512, 0.12, 0.8, 100, 100
+    etas = np.linspace(0.80, 1.00, n_pairs)
+    base = rank * 2 * n_pairs
+    boxes = []
+    for p, eta in enumerate(etas):
+        a = W.make_system("gibbs0", W.SPHERE, N, phi, q, float(eta), seed=1, replica=base + 2 * p)
+        b = W.make_system("gibbs1", W.SPHERE, N, phi, q, float(eta), seed=1,
+                          replica=base + 2 * p + 1)
+        boxes.append((a, b))
+    pairs = [((a.pos, a.L), (b.pos, b.L), {"q": q, "n_r": a.n_r, "n_trial": n_trial,
+                                           "d_max": 0.15}) for a, b in boxes]
+    gp = hpmc.GibbsPairs(pairs, seed=1, precision=prec, device=local, replica0=base)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        gp.cycle(1, n_ex, stream)
+    g0 = [hpmc.hpmc_get_gibbs(gp.ctx, p)[1] for p in range(n_pairs)]
+    hpmc.hpmc_reset_counters(gp.ctx)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            hpmc.hpmc_sweep(gp.ctx, 1, stream)
+            ev[k][1].record(stream)
+            hpmc.hpmc_gibbs_exchange(gp.ctx, n_ex, stream)
+            ev[k][2].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    sweep_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
+    ex_ms = sum(e[1].elapsed_time(e[2]) for e in ev)
+    ms = sweep_ms + ex_ms
+    _, cnt = hpmc.hpmc_get_state(gp.ctx)
+    g1 = [hpmc.hpmc_get_gibbs(gp.ctx, p)[1] for p in range(n_pairs)]
+    gd = {k: sum(b[k] - a[k] for a, b in zip(g0, g1)) for k in g1[0]}
+    live = hpmc.hpmc_get_live(gp.ctx, 2 * n_pairs)
+    gp.close()
+    ms, ex_ms = R.reduce_max([ms, ex_ms], "cuda")
+    attempts_all, moves_all, blocking_all = R.reduce_sum(
+        [gd["attempts"], cnt["moves"], cnt["dep_blocking"]], "cuda")
+    if rank == 0:
+        clocks = clk.summary()
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak = sms * ISSUE_LANES_PER_SM * 2070.0e6 / 1e12
+        # exchange kernel: depletant streams and 2 n_trial - 1 CB trials per
+        # blocking depletant, 6/pi attempts per point in the ball
+        trials = 6.0 / math.pi * (gd["dep_drawn"] + blocking_all * (2 * n_trial - 1))
+        achieved = OPS_PER_GIBBS_TRIAL * trials / (ex_ms * 1e-3) / 1e12
+        line = {
+            "metric": "Gibbs exchange attempts/s", "value": attempts_all / (ms * 1e-3),
+            "unit": "attempts/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
+            "config": {"workload": "gibbs_152_pairs_2x512_spheres_phi0.12_q0.8_eta0.8-1.0",
+                       "n_trial": n_trial, "exchanges_per_pair_per_step": n_ex,
+                       "step": "1 sweep of every box + 100 exchange attempts per pair",
+                       "l2": "flushed between steps (256 MB write)"},
+            "colloid_moves_per_s": moves_all / (ms * 1e-3),
+            "exchange_ms_per_step": ex_ms / args.steps,
+            "sweep_ms_per_step": sweep_ms / args.steps,
+            "exchange_acceptance": gd["accept"] / max(1, gd["attempts"]),
+            "exchange_outcomes": gd,
+            "box_populations": {"min": min(live), "max": max(live)},
+            "gpu_launches": args.steps * (1 + (1 if prec == 1 else 0) + 8 + 1),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_gibbs_exchange",
+                         "peak_basis": "%d SMs x 128 lanes x 2070 MHz (issue rate)" % sms},
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            from oracle import oracle as O
+            O.build()
+            a, b = boxes[0]
+            t0 = time.perf_counter()
+            _, _, _, _, g = O.gibbs_run(a.pos, b.pos, a.L, b.L, q=q, n_r=a.n_r, n_trial=n_trial,
+                                        d_max=(0.15, 0.15), seed=1, replicas=(base, base + 1),
+                                        n_cycles=args.cpu_cycles_gibbs, sweeps_per_cycle=1,
+                                        ex_per_cycle=n_ex)
+            dt = time.perf_counter() - t0
+            line["cpu_baseline"] = {
+                "value": g["attempts"] / dt, "unit": "attempts/s", "cores": 1, "kind": "oracle",
+                "sample": "%d steps of pair 0 (eta_r 0.80) from the start (%d attempts, "
+                          "%.1f s)" % (args.cpu_cycles_gibbs, g["attempts"], dt)}
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 # Anisotropic lens kernel, per depletant drawn: the sphere work plus the two
 # body-frame tests (rotation 15 + shape test 15 lane-ops), the old-pose one
 # for the ~55% that overlap the new pose; per move: two frames (2 x 20) more.
@@ -698,11 +815,14 @@ def main():
     ap.add_argument("--warps", type=int, default=1)
     ap.add_argument("--ilp", type=int, default=1)
     ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--workload", choices=("spheres_16384", "batched", "hemispheres", "discoids"),
+    ap.add_argument("--workload", choices=("spheres_16384", "batched", "hemispheres", "discoids",
+                                           "gibbs"),
                     default="spheres_16384",
                     help="spheres_16384: the headline four-state-point workload; batched: "
                          "128 replicas of uneven size and state point; hemispheres / "
-                         "discoids: 32768 hemispheres or 65536 discoids with rotations")
+                         "discoids: 32768 hemispheres or 65536 discoids with rotations; "
+                         "gibbs: 152 Gibbs-ensemble pairs (exchange attempts/s)")
+    ap.add_argument("--cpu-cycles-gibbs", type=int, default=40)
     ap.add_argument("--v0", choices=("circumsphere", "shell"), default="circumsphere",
                     help="depletant region V_0 of the spheres workload: the new pose's "
                          "circumsphere (the paper's; default, with a shell measurement "
@@ -722,6 +842,8 @@ def main():
         run_batched(args, ws, rank, local)
     elif args.workload in ("hemispheres", "discoids"):
         run_shape(args, ws, rank, local)
+    elif args.workload == "gibbs":
+        run_gibbs(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

@@ -155,6 +155,7 @@ struct Rep {
     // (a + r, c + r) and of the outer spheroid, and the squared thresholds
     float sp_iA2, sp_iC2, sp_inA, sp_inC, sp_outA, sp_outC, sp_kin2, sp_kout2;
     double pad_cell_bound; // host: packing bound on a cell's population
+    double pad_nb_bound;   // host: packing bound on the colloids within a depletant's reach
     // shell-restricted V_0 (spheres, translations): on when v0_shell; level k
     // (1..kShellLevels) samples R_in <= |e| < R_s with R_in = sh_rin[k-1],
     // thickness sh_h[k-1]; its Poisson table is the (k-1)-th block of nF

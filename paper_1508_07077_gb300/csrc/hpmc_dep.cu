@@ -228,12 +228,13 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
     // lie in the OLD circumsphere, centred |o| <= sqrt(3) d_max away, which
     // widens the range by that much.  0.01 covers the FP32 rounding of |d_j|.
     const double cut = 2.0 * R_s + (h.n_trial > 0 ? std::sqrt(3.0) * h.d_max : 0.0) + 0.01;
-    // in the FP32 form that neighbourhood must hold at most kMaxNb colloids
-    // (the FP64 forms keep every candidate of the 27 cells, up to kMaxCand)
+    // in the FP32 form that neighbourhood must fit the phase kernel's list:
+    // 128 for the anisotropic shapes (kMaxNbAniso); for spheres 64, or 128 in
+    // the widest cells (max_nb), checked in prepare() once the cell capacity
+    // is known (the FP64 forms keep every candidate of the 27 cells)
     const double nb_ext = cut + R_circ;
-    const double nb_cap = p.shape == HPMC_SPHERE ? 64.0 : 128.0;   // kMaxNb, kMaxNbAniso
-    if (c->precision == HPMC_FP32_RECHECK &&
-        nb_ext * nb_ext * nb_ext * (4.0 / 3.0 * kPi) * pack / v_shape >= nb_cap)
+    R.pad_nb_bound = nb_ext * nb_ext * nb_ext * (4.0 / 3.0 * kPi) * pack / v_shape;
+    if (c->precision == HPMC_FP32_RECHECK && p.shape != HPMC_SPHERE && R.pad_nb_bound >= 128.0)
         return HPMC_ERR_CAP;
     F.clear();
     if (lambda > 0.0) {
@@ -673,6 +674,9 @@ int prepare(hpmc_ctx *c)
     for (const Rep &R : rd) bound = std::fmax(bound, R.pad_cell_bound);
     int cap = bound < (double)kTinyCellCap && p.shape == HPMC_SPHERE ? kTinyCellCap
               : (bound < (double)kSmallCellCap ? kSmallCellCap : kMaxCellCap);
+    if (c->precision == HPMC_FP32_RECHECK && p.shape == HPMC_SPHERE)
+        for (const Rep &R : rd)
+            if (R.pad_nb_bound >= (double)max_nb(cap)) return HPMC_ERR_CAP;
     DeviceGuard g(c->device);
     if (cap != c->cap) c->cells_alloc = -2;  // force re-allocation of the bins
     c->cap = cap;
@@ -1501,7 +1505,8 @@ int hpmc_gibbs_exchange(hpmc_ctx *c, int n_attempts, void *stream)
     }
     if (n_attempts == 0 || n_rep == 0) return HPMC_OK;
     SimParams P = make_params(c);
-    k_gibbs_exchange<<<n_rep / 2, kMaxThreads, 0, s>>>(P, n_attempts);
+    if (c->precision == HPMC_FP32_RECHECK) k_gibbs_exchange<true><<<n_rep / 2, kMaxThreads, 0, s>>>(P, n_attempts);
+    else k_gibbs_exchange<false><<<n_rep / 2, kMaxThreads, 0, s>>>(P, n_attempts);
     CK(cudaGetLastError());
     return HPMC_OK;
 }

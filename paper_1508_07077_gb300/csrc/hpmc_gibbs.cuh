@@ -13,6 +13,7 @@
 
 #include "hpmc_common.cuh"
 #include "hpmc_sphere_fp64.cuh"
+#include "hpmc_sphere_fp32.cuh"
 
 namespace hpmc {
 
@@ -20,62 +21,116 @@ constexpr uint32_t kGibbsStream = 0xFFFFFFFEu;   // RNG stream word of the excha
 constexpr int kGibbsCounters = 8;   // attempts, accept, empty, ratio, overlap, depletant, cb, drawn
 constexpr int kMaxGibbsNb = 192;    // colloids within reach of the new (old) circumsphere
 
-// Configurational-bias weight of blocking depletant k of the exchange: n_trial
-// forward trials in the old circumsphere (overlapping the removed colloid,
-// free of the old box's other colloids nbo), n_trial - 1 reverse trials in the
-// new one (overlapping the inserted colloid, free of the new box's colloids nb).
-__device__ __noinline__ CbResult gibbs_cb(const Rep &R, uint32_t step, uint32_t k, const double4 *nb,
-                                          int nnb, const double4 *nbo, int nnbo)
+// Block-wide count and rank of a predicate over the CTA's threads (in thread
+// order).  s_warp: one int per warp; every thread must call it.
+__device__ __forceinline__ int block_rank(bool p, int *s_warp, int &rank)
 {
-    CbResult r = {0.0, 0u, 0u, 0u};
-    const int n_fwd = R.n_trial, n_rev = R.n_trial - 1;
-    int nf = 0, nr = 0, found = 0;
-    uint32_t t = 0, t_max = 64u * (uint32_t)(n_fwd + 1);
-    while (found < n_fwd && t < t_max) {
-        const uint4 w = draw(R.key0, R.key1, step, kGibbsStream, kPCbFwd, k, t);
-        ++t;
-        const double e0 = R.R_s * s11(w.x), e1 = R.R_s * s11(w.y), e2 = R.R_s * s11(w.z);
-        if (!(norm2(e0, e1, e2) < R.R_s2)) continue;
-        ++found;
-        if (!SphereFP64::dep(R, e0, e1, e2)) continue;
-        if (!free_of_nb_fp64(R, e0, e1, e2, nbo, nnbo)) continue;
-        ++nf;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const unsigned bal = __ballot_sync(kFull, p);
+    __syncthreads();                     // the previous call's counts are consumed
+    if (lane == 0) s_warp[warp] = __popc(bal);
+    __syncthreads();
+    int base = 0, total = 0;
+    for (int u = 0; u < nwarps; ++u) {
+        const int c = s_warp[u];
+        base += u < warp ? c : 0;
+        total += c;
     }
-    if (found < n_fwd) ++r.caps;
-    t = 0;
-    t_max = 64u * (uint32_t)(n_rev + 1);
+    rank = base + __popc(bal & ((1u << lane) - 1u));
+    return total;
+}
+
+// Point e (attempt word w of a depletant or CB stream, FP32 copy e32) free of
+// every colloid of the list (offsets d from the point's centre, FP64 and FP32
+// copies)?  F32: certified FP32 test, FP64 inside the margin.
+template <bool F32>
+__device__ __forceinline__ bool gibbs_free(const Rep &R, uint4 w, float3 e32, const double4 *nb,
+                                           const float4 *nb32, int nnb, uint32_t &rck)
+{
+    for (int a = 0; a < nnb; ++a) {
+        int t;
+        if (F32) {
+            const float4 d = nb32[a];
+            t = tri(norm2f(e32.x - d.x, e32.y - d.y, e32.z - d.z), R.T_dep32, R.m_r2);
+        } else {
+            t = -1;
+        }
+        if (t == -1) {
+            if (F32) ++rck;
+            const double e0 = R.R_s * s11(w.x), e1 = R.R_s * s11(w.y), e2 = R.R_s * s11(w.z);
+            const double4 d = nb[a];
+            t = SphereFP64::dep(R, e0 - d.x, e1 - d.y, e2 - d.z) ? 1 : 0;
+        }
+        if (t == 1) return false;
+    }
+    return true;
+}
+
+// Attempt w inside the circumsphere (the sampling ball)?  Returns the FP32
+// copy of the point in e32.
+template <bool F32>
+__device__ __forceinline__ bool gibbs_ball(const Rep &R, uint4 w, float3 &e32, uint32_t &rck)
+{
+    if (F32) {
+        e32 = make_float3(coord32(w.x, R.R_s32), coord32(w.y, R.R_s32), coord32(w.z, R.R_s32));
+        const int t = tri(norm2f(e32.x, e32.y, e32.z), R.T_s32, R.m_r2);
+        if (t != -1) return t == 1;
+        ++rck;
+    }
+    const double e0 = R.R_s * s11(w.x), e1 = R.R_s * s11(w.y), e2 = R.R_s * s11(w.z);
+    return norm2(e0, e1, e2) < R.R_s2;
+}
+
+// One direction of the CB trials of blocking depletant k, by the whole CTA:
+// the first n_want attempts of stream (purpose, k) inside the ball, each
+// counted when free of the list.  Returns the count; *found the trials
+// obtained (fewer than n_want when the attempt cap is hit).
+template <bool F32>
+__device__ int gibbs_trials(const Rep &R, uint32_t step, uint32_t purpose, uint32_t k, int n_want,
+                            const double4 *nb, const float4 *nb32, int nnb, int *s_warp, int &found,
+                            uint32_t &rck)
+{
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const uint32_t t_max = 64u * (uint32_t)(n_want + 1);
+    int ok_total = 0;
     found = 0;
-    while (found < n_rev && t < t_max) {
-        const uint4 w = draw(R.key0, R.key1, step, kGibbsStream, kPCbRev, k, t);
-        ++t;
-        const double e0 = R.R_s * s11(w.x), e1 = R.R_s * s11(w.y), e2 = R.R_s * s11(w.z);
-        if (!(norm2(e0, e1, e2) < R.R_s2)) continue;
-        ++found;
-        if (!SphereFP64::dep(R, e0, e1, e2)) continue;
-        if (!free_of_nb_fp64(R, e0, e1, e2, nb, nnb)) continue;
-        ++nr;
+    for (uint32_t t0 = 0; found < n_want && t0 < t_max; t0 += (uint32_t)nthr) {
+        const uint32_t t = t0 + (uint32_t)tid;
+        uint4 w = make_uint4(0, 0, 0, 0);
+        float3 e32 = make_float3(0.f, 0.f, 0.f);
+        bool in = false;
+        if (t < t_max) {
+            w = draw(R.key0, R.key1, step, kGibbsStream, purpose, k, t);
+            in = gibbs_ball<F32>(R, w, e32, rck);
+        }
+        int rank;
+        const int n_in = block_rank(in, s_warp, rank);
+        // (for spheres, inside the ball = overlapping the colloid it is centred on)
+        const bool take = in && found + rank < n_want;
+        const bool ok = take && gibbs_free<F32>(R, w, e32, nb, nb32, nnb, rck);
+        int dummy;
+        ok_total += block_rank(ok, s_warp, dummy);
+        found += min(n_in, n_want - found);
     }
-    if (found < n_rev) ++r.caps;
-    r.fwd_ok = (uint32_t)nf;
-    r.rev_ok = (uint32_t)nr;
-    r.f = (double)nf / (double)(nr + 1);
-    return r;
+    return ok_total;
 }
 
 // n_attempts exchanges of every pair, one after another; one CTA per pair.
+// F32: FP32 depletant tests with the certified margin (FP64 inside it).
+template <bool F32>
 __global__ void __launch_bounds__(kMaxThreads) k_gibbs_exchange(const __grid_constant__ SimParams P,
                                                                 int n_attempts)
 {
     __shared__ double4 s_nb[kMaxGibbsNb], s_nbo[kMaxGibbsNb];
-    __shared__ double s_f[kMaxThreads];
-    __shared__ int s_k[kMaxThreads];
+    __shared__ float4 s_nb32[kMaxGibbsNb], s_nbo32[kMaxGibbsNb];
+    __shared__ int s_blk[kMaxThreads];
     __shared__ int s_warp[kMaxThreads / 32];
-    __shared__ int s_n[2], s_src, s_i, s_go, s_nnb, s_nnbo, s_kmin, s_flag;
+    __shared__ int s_n[2], s_src, s_i, s_go, s_nnb, s_nnbo;
     __shared__ double s_x[3], s_xo[3];
     __shared__ unsigned long long s_cnt[2][kNumCounters], s_g[kGibbsCounters];
 
     const int pr = blockIdx.x, tid = threadIdx.x, nthr = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+    const int lane = tid & 31;
     const int r0 = 2 * pr;
     // the pair's depletant parameters, table and key: box 0's (the host
     // requires equal parameters in both boxes)
@@ -86,6 +141,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_gibbs_exchange(const __grid_con
     for (int k = tid; k < 2 * kNumCounters; k += nthr) s_cnt[k / kNumCounters][k % kNumCounters] = 0ull;
     if (tid < kGibbsCounters) s_g[tid] = 0ull;
     const unsigned long long step0 = P.gibbs_step[pr];
+    uint32_t rck = 0;
     __syncthreads();
 
     for (int a = 0; a < n_attempts; ++a) {
@@ -124,7 +180,6 @@ __global__ void __launch_bounds__(kMaxThreads) k_gibbs_exchange(const __grid_con
             s_go = go;
             s_nnb = 0;
             s_nnbo = 0;
-            s_kmin = 0x7FFFFFFF;
         }
         __syncthreads();
         if (!s_go) continue;
@@ -143,7 +198,10 @@ __global__ void __launch_bounds__(kMaxThreads) k_gibbs_exchange(const __grid_con
             if (r2 < R.contact2) ov = 1;
             if (r2 < R.nb_cut2) {
                 const int slot = atomicAdd(&s_nnb, 1);
-                if (slot < kMaxGibbsNb) s_nb[slot] = make_double4(d0, d1, d2, 0.0);
+                if (slot < kMaxGibbsNb) {
+                    s_nb[slot] = make_double4(d0, d1, d2, 0.0);
+                    s_nb32[slot] = make_float4((float)d0, (float)d1, (float)d2, 0.0f);
+                }
             }
         }
         // (CB) the old box's colloids within reach of the old circumsphere
@@ -157,7 +215,10 @@ __global__ void __launch_bounds__(kMaxThreads) k_gibbs_exchange(const __grid_con
                 const double d2 = min_image(pj.z - o2, Rs.L, Rs.half_L);
                 if (norm2(d0, d1, d2) < R.nb_cut2) {
                     const int slot = atomicAdd(&s_nnbo, 1);
-                    if (slot < kMaxGibbsNb) s_nbo[slot] = make_double4(d0, d1, d2, 0.0);
+                    if (slot < kMaxGibbsNb) {
+                        s_nbo[slot] = make_double4(d0, d1, d2, 0.0);
+                        s_nbo32[slot] = make_float4((float)d0, (float)d1, (float)d2, 0.0f);
+                    }
                 }
             }
         }
@@ -181,79 +242,66 @@ __global__ void __launch_bounds__(kMaxThreads) k_gibbs_exchange(const __grid_con
             const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
             uint32_t t0 = 0;
             int k0 = 0;
-            double W = 1.0;
+            double W = 1.0;     // (thread 0)
             int nblock = 0;
             bool rejected = false;
             while (k0 < n_p && t0 < t_max) {
                 const uint32_t t = t0 + (uint32_t)tid;
-                double e0 = 0.0, e1 = 0.0, e2 = 0.0;
+                uint4 w = make_uint4(0, 0, 0, 0);
+                float3 e32 = make_float3(0.f, 0.f, 0.f);
                 bool inside = false;
                 if (t < t_max) {
-                    const uint4 w = draw(R.key0, R.key1, step, kGibbsStream, kPDep, 0, t);
-                    e0 = R.R_s * s11(w.x);
-                    e1 = R.R_s * s11(w.y);
-                    e2 = R.R_s * s11(w.z);
-                    inside = norm2(e0, e1, e2) < R.R_s2;
+                    w = draw(R.key0, R.key1, step, kGibbsStream, kPDep, 0, t);
+                    inside = gibbs_ball<F32>(R, w, e32, rck);
                 }
-                const unsigned bal = __ballot_sync(kFull, inside);
-                if (lane == 0) s_warp[warp] = __popc(bal);
+                int rank;
+                const int total = block_rank(inside, s_warp, rank);
+                const int k = k0 + rank;
+                // blocking: overlaps the inserted colloid (inside, for spheres)
+                // and no other colloid of its box
+                const bool blocking = inside && k < n_p &&
+                                      gibbs_free<F32>(R, w, e32, s_nb, s_nb32, nnb, rck);
+                int brank;
+                const int nblk = block_rank(blocking, s_warp, brank);
+                if (blocking) s_blk[brank] = k;    // ascending k
                 __syncthreads();
-                int base = 0, total = 0;
-                for (int u = 0; u < nwarps; ++u) {
-                    const int c = s_warp[u];
-                    base += u < warp ? c : 0;
-                    total += c;
-                }
-                const int k = k0 + base + __popc(bal & ((1u << lane) - 1u));
-                // blocking: overlaps the inserted colloid and no other colloid of its box
-                const bool blocking = inside && k < n_p && SphereFP64::dep(R, e0, e1, e2) &&
-                                      free_of_nb_fp64(R, e0, e1, e2, s_nb, nnb);
+                int stop = -1;   // index of the depletant that rejects the move
                 if (R.n_trial == 0) {
-                    if (blocking) atomicMin(&s_kmin, k);
-                    if (__syncthreads_or(blocking)) {
-                        if (tid == 0) {
-                            s_cnt[src][kDepBlocking] += 1ull;
-                            s_cnt[src][kDepEval] += (unsigned long long)(s_kmin - k0 + 1);
-                        }
-                        rejected = true;
-                        break;
-                    }
-                    if (tid == 0) s_cnt[src][kDepEval] += (unsigned long long)min(total, n_p - k0);
+                    if (nblk > 0) stop = s_blk[0];
                 } else {
-                    double f = -1.0;
-                    if (blocking) {
-                        const CbResult cr = gibbs_cb(R, step, (uint32_t)k, s_nb, nnb, s_nbo, nnbo);
-                        f = cr.f;
-                        atomicAdd(&s_cnt[src][kCbFwdOk], (unsigned long long)cr.fwd_ok);
-                        atomicAdd(&s_cnt[src][kCbRevOk], (unsigned long long)cr.rev_ok);
-                        if (cr.caps) atomicAdd(&s_cnt[src][kCapHits], (unsigned long long)cr.caps);
-                    }
-                    s_f[tid] = f;
-                    s_k[tid] = k;
-                    __syncthreads();
-                    if (tid == 0) {
-                        int zero = 0;
-                        for (int u = 0; u < nthr; ++u) {
-                            const double fu = s_f[u];
-                            if (fu < 0.0) continue;
-                            ++nblock;
+                    for (int b = 0; b < nblk; ++b) {
+                        const int kb = s_blk[b];
+                        int found_f, found_r;
+                        const int nf = gibbs_trials<F32>(R, step, kPCbFwd, (uint32_t)kb, R.n_trial,
+                                                         s_nbo, s_nbo32, nnbo, s_warp, found_f, rck);
+                        const int nr = gibbs_trials<F32>(R, step, kPCbRev, (uint32_t)kb,
+                                                         R.n_trial - 1, s_nb, s_nb32, nnb, s_warp,
+                                                         found_r, rck);
+                        if (tid == 0) {
+                            s_cnt[src][kCbFwdOk] += (unsigned long long)nf;
+                            s_cnt[src][kCbRevOk] += (unsigned long long)nr;
+                            if (found_f < R.n_trial) s_cnt[src][kCapHits]++;
+                            if (found_r < R.n_trial - 1) s_cnt[src][kCapHits]++;
                             s_cnt[src][kDepBlocking]++;
-                            if (fu == 0.0) {
-                                zero = 1;
-                                s_cnt[src][kDepEval] += (unsigned long long)(s_k[u] - k0 + 1);
-                                break;
-                            }
-                            W = W * fu;
+                            ++nblock;
                         }
-                        if (!zero) s_cnt[src][kDepEval] += (unsigned long long)min(total, n_p - k0);
-                        s_flag = zero;
-                    }
-                    __syncthreads();
-                    if (s_flag) {
-                        rejected = true;
-                        break;
+                        const double f = (double)nf / (double)(nr + 1);
+                        if (f == 0.0) {
+                            stop = kb;
+                            break;
+                        }
+                        if (tid == 0) W = W * f;
                     }
                 }
+                if (stop >= 0) {
+                    if (tid == 0) {
+                        if (R.n_trial == 0) s_cnt[src][kDepBlocking]++;
+                        s_cnt[src][kDepEval] += (unsigned long long)(stop - k0 + 1);
+                    }
+                    rejected = true;
+                    break;
+                }
+                if (tid == 0) s_cnt[src][kDepEval] += (unsigned long long)min(total, n_p - k0);
                 k0 += total;
                 t0 += (uint32_t)nthr;
             }
@@ -290,6 +338,10 @@ __global__ void __launch_bounds__(kMaxThreads) k_gibbs_exchange(const __grid_con
         if (v) atomicAdd(P.counters + (size_t)(r0 + k / kNumCounters) * kRepSlots * kNumCounters +
                              (k % kNumCounters), v);
     }
+    // FP64 re-takes, to box 0's counters
+    rck = __reduce_add_sync(kFull, rck);
+    if (lane == 0 && rck) atomicAdd(P.counters + (size_t)r0 * kRepSlots * kNumCounters + kRechecks,
+                                    (unsigned long long)rck);
 }
 
 }  // namespace hpmc

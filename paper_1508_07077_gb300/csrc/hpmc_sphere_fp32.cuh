@@ -621,7 +621,9 @@ __global__ void __launch_bounds__(128, 4) k_lens_shell_fp32(const __grid_constan
 
 constexpr int kMaxLensCTA = 64;    // lens points of one cell staged in shared memory (more: read
                                    // from global memory)
-constexpr int kMaxNb = 64;         // neighbours within reach of a depletant (hard spheres: <= ~27)
+// neighbours within reach of a depletant, per cell-bin capacity: the widest
+// cells (large depletants) get the larger list
+__host__ __device__ constexpr int max_nb(int cap) { return cap >= kMaxCellCap ? 128 : 64; }
 
 // CTA-wide barrier / OR, reduced to warp operations when the CTA is one warp.
 template <bool WARP>
@@ -651,7 +653,7 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
     k_phase_sphere_fp32(const __grid_constant__ SimParams P, int phase)
 {
     __shared__ float4 s_cpos[cand_cap(CAP)];  // candidates relative to this cell's origin; index in .w
-    __shared__ float4 s_nb[kMaxNb];      // neighbours relative to the new position; index in .w
+    __shared__ float4 s_nb[max_nb(CAP)];      // neighbours relative to the new position; index in .w
     __shared__ float4 s_lens[kMaxLensCTA];
     __shared__ int4 s_hdr[CAP];                  // own cell, bin order
     __shared__ float4 s_mv[CAP];
@@ -912,11 +914,11 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
             if (WARP) {
                 const unsigned b = __ballot_sync(kFull, take);
                 const int slot = nnb + __popc(b & lt);
-                if (take && slot < kMaxNb) s_nb[slot] = make_float4(d0, d1, d2, __int_as_float(pj));
+                if (take && slot < max_nb(CAP)) s_nb[slot] = make_float4(d0, d1, d2, __int_as_float(pj));
                 nnb += __popc(b);
             } else if (take) {
                 const int slot = atomicAdd(&s_nnb, 1);
-                if (slot < kMaxNb) s_nb[slot] = make_float4(d0, d1, d2, __int_as_float(pj));
+                if (slot < max_nb(CAP)) s_nb[slot] = make_float4(d0, d1, d2, __int_as_float(pj));
             }
         }
         if (cta_any<WARP>(ov)) {
@@ -924,7 +926,7 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
             continue;
         }
         if (!WARP) nnb = s_nnb;
-        if (nnb > kMaxNb) {
+        if (nnb > max_nb(CAP)) {
             if (tid == 0) atomicCAS(P.err, kErrNone, kErrCandCap);
             return;
         }

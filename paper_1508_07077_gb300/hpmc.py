@@ -291,9 +291,11 @@ class GibbsPairs:
     """Gibbs-ensemble pairs of sphere boxes in one context: pair p is
     replicas 2p, 2p + 1, each with one slot per colloid of the pair."""
 
-    def __init__(self, pairs, *, diameter=1.0, seed=1, precision=HPMC_FP64, device=0):
+    def __init__(self, pairs, *, diameter=1.0, seed=1, precision=HPMC_FP64, device=0,
+                 replica0=0):
         """pairs: list of ((pos0, L0), (pos1, L1), params) with params a dict
-        of q, n_r, n_trial, d_max (per box: d_max may be a pair)."""
+        of q, n_r, n_trial, d_max (per box: d_max may be a pair).  Box k of
+        pair p is replica replica0 + 2 p + k (its RNG key)."""
         reps, self.live = [], []
         for p, ((a, L0), (b, L1), prm) in enumerate(pairs):
             a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1, 3)
@@ -306,7 +308,7 @@ class GibbsPairs:
                 slots[:x.shape[0]] = x
                 reps.append({"n": cap, "box_l": L, "pos": slots, "q": prm.get("q", 0.0),
                              "n_r": prm.get("n_r", 0.0), "n_trial": prm.get("n_trial", 0),
-                             "d_max": dm[k], "replica": 2 * p + k})
+                             "d_max": dm[k], "replica": replica0 + 2 * p + k})
                 self.live.append(x.shape[0])
         self.reps = reps
         self.ctx = hpmc_init_batch(reps, shape=HPMC_SPHERE, shape_params=(diameter,), seed=seed,
