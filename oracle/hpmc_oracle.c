@@ -38,6 +38,9 @@
  *   - Sec. IV.B (coexistence): Gibbs-ensemble colloid exchange between two
  *     boxes with depletants inserted at the new position and reinserted in
  *     the old box (configurational bias), spheres.
+ *   - Sec. VI (the remark that the scheme generalises to soft interactions,
+ *     option soft_eps > 0): a Hertz colloid-depletant potential; a depletant
+ *     blocks with probability e^(-U_others) max(0, e^(-u_old) - e^(-u_new)).
  *   - Sec. V: anisotropic colloids (hemispheres, discoids = oblate spheroids)
  *     with quaternion rotation moves; overlap of two convex colloids by
  *     Minkowski portal refinement on their support functions.
@@ -55,7 +58,11 @@
  * probability with the circumsphere's, detailed balance and the
  * Asakura-Oosawa distribution; for the Gibbs exchange, detailed balance of
  * one exchange against the closed form (Gibbs prior times exp(z_p dV_f)),
- * the binomial box occupancy of an ideal gas, conservation and validity.
+ * the binomial box occupancy of an ideal gas, conservation and validity;
+ * for the soft interaction, the shared exponential against the library's,
+ * detailed balance against a quadrature of the semigrand weight ratio and
+ * the two-colloid distribution against a quadrature of the effective
+ * attraction.
  */
 #include <math.h>
 #include <stdint.h>
@@ -617,6 +624,7 @@ typedef struct {
     /* shell-restricted V_0 (v0_mode 1, sphere translations): per level k =
      * 1..SHELL_LEVELS the inner radius, the thickness and the Poisson table */
     int v0_mode;
+    double soft_eps;   /* > 0: Hertz colloid-depletant interaction of strength soft_eps kT */
     double R_s4, dd;
     double s_rin[32], s_h[32];
     double *sF[32];
@@ -679,9 +687,69 @@ static int gather_neighbours(const osim *S, int i, const double xn[3],
 /* Next point of an attempt stream, uniform in the ball |e| < R_s (rejection
  * from the cube [-R_s, R_s]^3).  *t is the running attempt index; returns 0
  * once *t reaches t_max. */
-static int next_in_ball(const osim *S, uint32_t sweep, uint32_t tag,
-                        uint32_t purpose, uint32_t sub, uint32_t *t,
-                        uint32_t t_max, double e[3])
+/* ------------------------------------------------------------------------ */
+/* Soft colloid-depletant interaction (Sec. VI: the scheme generalises to    */
+/* soft potentials such as the Hertz potential).  u(r) = eps (1 - r/s)^(5/2) */
+/* for r < s = (d + q)/2, else 0; colloids stay hard among themselves.       */
+/* Reading: a depletant at x blocks the move with probability                */
+/*   b(x) = e^(-U_others(x)) max(0, e^(-u(|x - r_old|)) - e^(-u(|x - r_new|))) */
+/* (U_others: the other colloids' energy, summed in ascending index), which  */
+/* gives P(M->M')/P(M'->M) = exp(z_p Int[e^(-U') - e^(-U)] dx), the         */
+/* semigrand weight ratio; for hard interactions b is the indicator of       */
+/* "overlaps only the new configuration".                                    */
+/* ------------------------------------------------------------------------ */
+
+/* e^(-y), y >= 0: Cody-Waite reduction y = k ln2 + r (ln2 split into a
+ * 29-bit head and a tail), |r| <= ln2/2, then the degree-14 Taylor
+ * polynomial of e^(-r) by Horner (truncation error < 2^-60), times 2^-k. */
+static double exp_neg(double y)
+{
+    if (!(y < 700.0)) return 0.0;
+    const double ln2_hi = 0x1.62e42ff000000p-1, ln2_lo = -0x1.718432a1b0e26p-35;
+    double kd = floor(y * 0x1.71547652b82fep+0 + 0.5);
+    double r = (y - kd * ln2_hi) - kd * ln2_lo;
+    double x = -r;
+    double p = 1.0 / 87178291200.0;
+    p = p * x + 1.0 / 6227020800.0;
+    p = p * x + 1.0 / 479001600.0;
+    p = p * x + 1.0 / 39916800.0;
+    p = p * x + 1.0 / 3628800.0;
+    p = p * x + 1.0 / 362880.0;
+    p = p * x + 1.0 / 40320.0;
+    p = p * x + 1.0 / 5040.0;
+    p = p * x + 1.0 / 720.0;
+    p = p * x + 1.0 / 120.0;
+    p = p * x + 1.0 / 24.0;
+    p = p * x + 1.0 / 6.0;
+    p = p * x + 0.5;
+    p = p * x + 1.0;
+    p = p * x + 1.0;
+    return ldexp(p, -(int)kd);
+}
+
+double oracle_exp_neg(double y) { return exp_neg(y); }
+
+/* Hertz energy (kT) of a depletant at squared distance r2 from a colloid. */
+static double hertz(const osim *S, double r2)
+{
+    if (!(r2 < S->R_s2)) return 0.0;
+    double t = 1.0 - sqrt(r2) / S->R_s;
+    return S->soft_eps * ((t * t) * sqrt(t));
+}
+
+double oracle_hertz(double eps, double sigma, double r2)
+{
+    osim S;
+    memset(&S, 0, sizeof S);
+    S.soft_eps = eps;
+    S.R_s = sigma;
+    S.R_s2 = sigma * sigma;
+    return hertz(&S, r2);
+}
+
+static int next_in_ball_w(const osim *S, uint32_t sweep, uint32_t tag,
+                          uint32_t purpose, uint32_t sub, uint32_t *t,
+                          uint32_t t_max, double e[3], uint32_t *w3)
 {
     while (*t < t_max) {
         uint32_t w[4];
@@ -691,9 +759,19 @@ static int next_in_ball(const osim *S, uint32_t sweep, uint32_t tag,
         e[1] = S->R_s * s11(w[1]);
         e[2] = S->R_s * s11(w[2]);
         double r2 = (e[0] * e[0] + e[1] * e[1]) + e[2] * e[2];
-        if (r2 < S->R_s2) return 1;
+        if (r2 < S->R_s2) {
+            if (w3) *w3 = w[3];
+            return 1;
+        }
     }
     return 0;
+}
+
+static int next_in_ball(const osim *S, uint32_t sweep, uint32_t tag,
+                        uint32_t purpose, uint32_t sub, uint32_t *t,
+                        uint32_t t_max, double e[3])
+{
+    return next_in_ball_w(S, sweep, tag, purpose, sub, t, t_max, e, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -889,6 +967,15 @@ static int accept_move(const osim *S, uint32_t sweep, int i, const double xn[3],
 
     /* Colloid-colloid overlap at the new pose: Delta H_cc = infinity. */
     int m = gather_neighbours(S, i, xn, ci, pos, quat, cell_start, cell_idx, nb);
+    if (S->soft_eps > 0.0) {
+        /* soft interactions sum the neighbours' energies in ascending index */
+        for (int a = 1; a < m; ++a) {
+            onb v = nb[a];
+            int b = a - 1;
+            while (b >= 0 && nb[b].j > v.j) { nb[b + 1] = nb[b]; --b; }
+            nb[b + 1] = v;
+        }
+    }
     for (int a = 0; a < m; ++a) {
         if (pair_overlap(&S->sh, nb[a].d, qn, nb[a].qj)) {
             cnt[C_REJ_OVERLAP]++;
@@ -910,6 +997,7 @@ static int accept_move(const osim *S, uint32_t sweep, int i, const double xn[3],
     for (int k = 0; k < n_p; ++k) {
         double e[3];
         int got;
+        uint32_t w3 = 0;
         if (S->v0_mode == 2) {
             cube_point(S, sweep, tag, t, e);
             t += 1;
@@ -917,19 +1005,35 @@ static int accept_move(const osim *S, uint32_t sweep, int i, const double xn[3],
         } else if (lvl > 0) {
             got = next_in_shell(S, lvl, sweep, tag, &t, t_max, e);
         } else {
-            got = next_in_ball(S, sweep, tag, P_DEP, 0, &t, t_max, e);
+            got = next_in_ball_w(S, sweep, tag, P_DEP, 0, &t, t_max, e, &w3);
         }
         if (!got) {
             cnt[C_CAP]++;
             break;
         }
         cnt[C_DEP_EVAL]++;
-        /* irrelevant unless it overlaps the new pose */
-        if (!dep_overlap(&S->sh, S->q, e, qn)) continue;
-        /* ignored if it overlaps the old configuration */
-        double u[3] = {e[0] - o[0], e[1] - o[1], e[2] - o[2]};
-        if (dep_overlap(&S->sh, S->q, u, qo)) continue;
-        if (!free_of_neighbours(S, e, nb, m)) continue;
+        if (S->soft_eps > 0.0) {
+            /* soft: blocks with probability b(e), decided by the attempt's
+             * fourth word */
+            double u[3] = {e[0] - o[0], e[1] - o[1], e[2] - o[2]};
+            double e_new = exp_neg(hertz(S, (e[0] * e[0] + e[1] * e[1]) + e[2] * e[2]));
+            double e_old = exp_neg(hertz(S, (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2]));
+            if (!(e_old > e_new)) continue;
+            double U = 0.0;
+            for (int a = 0; a < m; ++a) {
+                double v[3] = {e[0] - nb[a].d[0], e[1] - nb[a].d[1], e[2] - nb[a].d[2]};
+                U = U + hertz(S, (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2]);
+            }
+            double b = exp_neg(U) * (e_old - e_new);
+            if (!(u01(w3) < b)) continue;
+        } else {
+            /* irrelevant unless it overlaps the new pose */
+            if (!dep_overlap(&S->sh, S->q, e, qn)) continue;
+            /* ignored if it overlaps the old configuration */
+            double u[3] = {e[0] - o[0], e[1] - o[1], e[2] - o[2]};
+            if (dep_overlap(&S->sh, S->q, u, qo)) continue;
+            if (!free_of_neighbours(S, e, nb, m)) continue;
+        }
         /* overlaps only the new configuration: blocks the move */
         cnt[C_DEP_BLOCKING]++;
         ++n_block;
@@ -1077,8 +1181,8 @@ static void sim_free(osim *S)
 
 static int sim_init(osim *S, int n, double L, int shape,
                     const double *shape_params, int n_shape_params, double q,
-                    double n_r, int n_trial, int cb_mode, int v0_mode, double d_max,
-                    double a_max, double p_translate, uint64_t seed,
+                    double n_r, int n_trial, int cb_mode, int v0_mode, double soft_eps,
+                    double d_max, double a_max, double p_translate, uint64_t seed,
                     uint32_t replica, int n_cell, int brute_force)
 {
     memset(S, 0, sizeof *S);
@@ -1120,6 +1224,14 @@ static int sim_init(osim *S, int n, double L, int shape,
         sim_free(S);
         return -1;
     }
+    /* soft colloid-depletant interaction: spheres, no CB, a V_0 that holds
+     * the new circumsphere (not the shell) */
+    if (!(soft_eps >= 0.0) ||
+        (soft_eps > 0.0 && (shape != SHAPE_SPHERE || n_trial != 0 || v0_mode == 1))) {
+        sim_free(S);
+        return -1;
+    }
+    S->soft_eps = soft_eps;
     S->v0_mode = v0_mode;
     S->R_s4 = S->R_s2 * S->R_s2;
     S->dd = (sqrt(3.0) * d_max) / 32.0;
@@ -1146,8 +1258,8 @@ static int sim_init(osim *S, int n, double L, int shape,
  */
 int oracle_run(int n, double L, int shape, const double *shape_params,
                int n_shape_params, double q, double n_r, int n_trial,
-               int cb_mode, int v0_mode, double d_max, double a_max, double p_translate,
-               uint64_t seed, uint32_t replica, int n_cell, int brute_force,
+               int cb_mode, int v0_mode, double soft_eps, double d_max, double a_max,
+               double p_translate, uint64_t seed, uint32_t replica, int n_cell, int brute_force,
                double *pos, double *quat, uint64_t sweep0, int n_sweeps,
                uint64_t *counters, int hist_bins, double hist_rmax,
                uint64_t *hist)
@@ -1155,7 +1267,7 @@ int oracle_run(int n, double L, int shape, const double *shape_params,
     osim S;
     if (!pos || !counters || n_sweeps < 0) return -1;
     if (sim_init(&S, n, L, shape, shape_params, n_shape_params, q, n_r, n_trial,
-                 cb_mode, v0_mode, d_max, a_max, p_translate, seed, replica, n_cell,
+                 cb_mode, v0_mode, soft_eps, d_max, a_max, p_translate, seed, replica, n_cell,
                  brute_force) != 0)
         return -1;
     int ncell = S.nc * S.nc * S.nc;
@@ -1217,7 +1329,7 @@ out:
  */
 long oracle_acceptance(int n, double L, int shape, const double *shape_params,
                        int n_shape_params, double q, double n_r, int n_trial,
-                       int cb_mode, int v0_mode, double d_max, uint64_t seed,
+                       int cb_mode, int v0_mode, double soft_eps, double d_max, uint64_t seed,
                        const double *pos,
                        const double *quat, int i, const double *xn_in,
                        const double *qn_in, uint64_t sweep0, long n_rep,
@@ -1226,7 +1338,7 @@ long oracle_acceptance(int n, double L, int shape, const double *shape_params,
     osim S;
     if (!pos || !xn_in || i < 0 || i >= n || n_rep < 0 || !counters) return -1;
     if (sim_init(&S, n, L, shape, shape_params, n_shape_params, q, n_r, n_trial,
-                 cb_mode, v0_mode, d_max, 0.0, 1.0, seed, 0, 0, 1) != 0)
+                 cb_mode, v0_mode, soft_eps, d_max, 0.0, 1.0, seed, 0, 0, 1) != 0)
         return -1;
     onb *nb = (onb *)malloc(sizeof(onb) * (size_t)n);
     if (!nb) { sim_free(&S); return -1; }
@@ -1458,7 +1570,7 @@ int oracle_gibbs_run(double diameter, double q, double n_r, int n_trial, double 
     osim S;
     double sp[1] = {diameter};
     /* the pair's parameters (table, key) as box 0's; its box length is not used */
-    if (sim_init(&S, 1, L0, SHAPE_SPHERE, sp, 1, q, n_r, n_trial, 0, 0, 0.0, 0.0, 1.0,
+    if (sim_init(&S, 1, L0, SHAPE_SPHERE, sp, 1, q, n_r, n_trial, 0, 0, 0.0, 0.0, 0.0, 1.0,
                  seed, rep0, 0, 1) != 0)
         return -1;
     obox box[2] = {{n[0], L0, pos0}, {n[1], L1, pos1}};
@@ -1467,7 +1579,7 @@ int oracle_gibbs_run(double diameter, double q, double n_r, int n_trial, double 
     for (int cy = 0; cy < n_cycles && rc == 0; ++cy) {
         for (int b = 0; b < 2 && rc == 0; ++b) {
             if (box[b].n == 0 || sweeps_per_cycle == 0) continue;
-            rc = oracle_run(box[b].n, box[b].L, SHAPE_SPHERE, sp, 1, q, n_r, n_trial, 0, 0,
+            rc = oracle_run(box[b].n, box[b].L, SHAPE_SPHERE, sp, 1, q, n_r, n_trial, 0, 0, 0.0,
                             b == 0 ? d_max0 : d_max1, 0.0, 1.0, seed, b == 0 ? rep0 : rep1, 0, 0,
                             box[b].pos, NULL, sweep, sweeps_per_cycle, counters + b * C_N, 0,
                             0.0, NULL);
@@ -1500,8 +1612,8 @@ long oracle_gibbs_acceptance(double diameter, double q, double n_r, int n_trial,
     if (i < 0 || i >= ns) return -1;
     osim S;
     double sp[1] = {diameter};
-    if (sim_init(&S, 1, L0, SHAPE_SPHERE, sp, 1, q, n_r, n_trial, 0, 0, 0.0, 0.0, 1.0, seed,
-                 rep0, 0, 1) != 0)
+    if (sim_init(&S, 1, L0, SHAPE_SPHERE, sp, 1, q, n_r, n_trial, 0, 0, 0.0, 0.0, 0.0, 1.0,
+                 seed, rep0, 0, 1) != 0)
         return -1;
     obox box[2] = {{n0, L0, (double *)pos0}, {n1, L1, (double *)pos1}};
     uint64_t cnt[C_N] = {0};

@@ -88,7 +88,7 @@ def lib():
             L.oracle_run.argtypes = [
                 ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, ctypes.c_int,
                 ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                 ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
                 dp, dp, ctypes.c_uint64, ctypes.c_int, u64p,
                 ctypes.c_int, ctypes.c_double, u64p]
@@ -98,7 +98,7 @@ def lib():
             L.oracle_acceptance.argtypes = [
                 ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, ctypes.c_int,
                 ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                ctypes.c_int, ctypes.c_double, ctypes.c_uint64, dp, dp, ctypes.c_int, dp, dp, ctypes.c_uint64,
+                ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, dp, dp, ctypes.c_int, dp, dp, ctypes.c_uint64,
                 ctypes.c_long, u64p]
             L.oracle_acceptance.restype = ctypes.c_long
             L.oracle_free_volume.argtypes = [
@@ -138,6 +138,10 @@ def lib():
                 ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int, dp,
                 ctypes.c_uint64, ctypes.c_long, u64p]
             L.oracle_gibbs_acceptance.restype = ctypes.c_long
+            L.oracle_exp_neg.argtypes = [ctypes.c_double]
+            L.oracle_exp_neg.restype = ctypes.c_double
+            L.oracle_hertz.argtypes = [ctypes.c_double] * 3
+            L.oracle_hertz.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -188,8 +192,8 @@ def poisson_sample(F, u):
 
 
 def acceptance(pos, L, i, xn, *, shape=SHAPE_SPHERE, shape_params=(1.0,), q=0.0,
-               n_r=0.0, n_trial=0, cb_mode=0, v0_mode=0, d_max=0.0, seed=1, quat=None,
-               qn=None, sweep0=0, n_rep=1000):
+               n_r=0.0, n_trial=0, cb_mode=0, v0_mode=0, soft_eps=0.0, d_max=0.0, seed=1,
+               quat=None, qn=None, sweep0=0, n_rep=1000):
     """How many of n_rep independent evaluations accept the fixed proposed move
     of colloid i to position xn (and orientation qn).  Returns (count, counters).
     v0_mode 1 samples depletants in the thinnest shell level (of a system with
@@ -202,8 +206,8 @@ def acceptance(pos, L, i, xn, *, shape=SHAPE_SPHERE, shape_params=(1.0,), q=0.0,
     cnt = np.zeros(N_COUNTERS, dtype=np.uint64)
     a = lib().oracle_acceptance(
         pos.shape[0], float(L), int(shape), _p(sp, ctypes.c_double), len(sp),
-        float(q), float(n_r), int(n_trial), int(cb_mode), int(v0_mode), float(d_max),
-        int(seed), _p(pos, ctypes.c_double),
+        float(q), float(n_r), int(n_trial), int(cb_mode), int(v0_mode), float(soft_eps),
+        float(d_max), int(seed), _p(pos, ctypes.c_double),
         _p(qa, ctypes.c_double) if qa is not None else None, int(i),
         _p(x, ctypes.c_double), _p(qb, ctypes.c_double) if qb is not None else None,
         int(sweep0), int(n_rep), _p(cnt, ctypes.c_uint64))
@@ -238,7 +242,7 @@ def cell_list(pos, L, nc, seed, replica, sweep):
 
 
 def run(pos, L, *, shape=SHAPE_SPHERE, shape_params=(1.0,), q=0.0, n_r=0.0,
-        n_trial=0, cb_mode=0, v0_mode=0, d_max=0.1, a_max=0.0, p_translate=1.0, seed=1,
+        n_trial=0, cb_mode=0, v0_mode=0, soft_eps=0.0, d_max=0.1, a_max=0.0, p_translate=1.0, seed=1,
         replica=0, n_cell=0, brute_force=False, quat=None, sweep0=0, n_sweeps=1,
         hist_bins=0, hist_rmax=0.0):
     """Run the serial sampler in place on copies of pos/quat.
@@ -254,7 +258,8 @@ def run(pos, L, *, shape=SHAPE_SPHERE, shape_params=(1.0,), q=0.0, n_r=0.0,
     hist = np.zeros(max(hist_bins, 1), dtype=np.uint64) if hist_bins > 0 else None
     rc = lib().oracle_run(
         n, float(L), int(shape), _p(sp, ctypes.c_double), len(sp), float(q),
-        float(n_r), int(n_trial), int(cb_mode), int(v0_mode), float(d_max), float(a_max),
+        float(n_r), int(n_trial), int(cb_mode), int(v0_mode), float(soft_eps), float(d_max),
+        float(a_max),
         float(p_translate), int(seed), int(replica), int(n_cell),
         int(bool(brute_force)), _p(pos, ctypes.c_double),
         _p(qa, ctypes.c_double) if qa is not None else None,
@@ -265,6 +270,14 @@ def run(pos, L, *, shape=SHAPE_SPHERE, shape_params=(1.0,), q=0.0, n_r=0.0,
         raise ValueError("oracle_run rejected its arguments (rc=%d)" % rc)
     counters = {name: int(cnt[i]) for i, name in enumerate(COUNTERS)}
     return pos, qa, counters, hist
+
+
+def exp_neg(y):
+    return lib().oracle_exp_neg(float(y))
+
+
+def hertz(eps, sigma, r2):
+    return lib().oracle_hertz(float(eps), float(sigma), float(r2))
 
 
 def shell_level(w0, w1, w2):
