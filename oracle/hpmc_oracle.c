@@ -855,13 +855,15 @@ static int next_in_shell(const osim *S, int lvl, uint32_t sweep, uint32_t tag,
  * cube [-R_s, R_s)^3 around the new reference point contains the new pose's
  * circumsphere, so every attempt is a depletant: e = R_s (s11(w_0), s11(w_1),
  * s11(w_2)) at attempt t = its index, and N_p ~ Poisson(z_p (2 R_s)^3). */
-static void cube_point(const osim *S, uint32_t sweep, uint32_t tag, uint32_t t, double e[3])
+static void cube_point(const osim *S, uint32_t sweep, uint32_t tag, uint32_t t, double e[3],
+                       uint32_t *w3)
 {
     uint32_t w[4];
     draw(S->key, sweep, tag, P_DEP, 0, t, w);
     e[0] = S->R_s * s11(w[0]);
     e[1] = S->R_s * s11(w[1]);
     e[2] = S->R_s * s11(w[2]);
+    *w3 = w[3];
 }
 
 double oracle_cube_lambda(double R_s, double n_r)
@@ -999,7 +1001,7 @@ static int accept_move(const osim *S, uint32_t sweep, int i, const double xn[3],
         int got;
         uint32_t w3 = 0;
         if (S->v0_mode == 2) {
-            cube_point(S, sweep, tag, t, e);
+            cube_point(S, sweep, tag, t, e, &w3);
             t += 1;
             got = 1;
         } else if (lvl > 0) {

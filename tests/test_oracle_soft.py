@@ -135,3 +135,19 @@ def test_soft_argument_validation(oracle):
         oracle.run(s, 3.0, q=0.2, n_r=1.0, soft_eps=1.0, v0_mode=1)     # not the shell
     with pytest.raises(ValueError):
         oracle.run(s, 3.0, q=0.2, n_r=1.0, soft_eps=-1.0)
+
+
+def test_soft_with_the_cube_has_the_same_acceptance(oracle):
+    """The cube V_0 holds the new circumsphere, so the soft acceptance
+    probability is the circumsphere's (the blocking uniform is each
+    attempt's fourth word in both)."""
+    a, b0 = _pair(1.05)
+    _, b1 = _pair(1.10)
+    n_rep = 60000
+    p = []
+    for mode, sweep0 in ((0, 1), (2, 5 * 10 ** 6)):
+        f, _ = oracle.acceptance(np.array([a, b0]), L2, 1, b1, q=Q, n_r=10.0, soft_eps=20.0,
+                                 v0_mode=mode, n_rep=n_rep, sweep0=sweep0)
+        p.append(f / n_rep)
+    se = math.sqrt(sum(x * (1 - x) for x in p) / n_rep)
+    assert 0.05 < p[0] < 0.95 and abs(p[0] - p[1]) < 4.5 * se, (p, se)
