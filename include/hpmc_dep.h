@@ -207,6 +207,19 @@ int hpmc_set_fp32_margin(hpmc_ctx *ctx, double margin);
  * anisotropic shape or an unknown mode.  Takes effect at the next sweep. */
 int hpmc_set_v0(hpmc_ctx *ctx, int mode);
 
+/* Soft colloid-depletant interaction (the paper's closing remark that the
+ * scheme generalises to soft potentials such as the Hertz potential).
+ * eps > 0: u(r) = eps (1 - r/s)^(5/2) kT for r < s = (d_colloid +
+ * d_depletant) / 2, else 0, in place of the hard colloid-depletant overlap
+ * (colloids stay hard among themselves).  A depletant at x blocks a move with
+ * probability e^(-U_others(x)) max(0, e^(-u_old(x)) - e^(-u_new(x))), decided
+ * by u01 of the fourth word of its attempt (U_others summed over the other
+ * colloids in ascending index; e^(-y) by Cody-Waite reduction and the
+ * degree-14 Taylor polynomial, the same bits on every side).  Spheres, FP64
+ * form, n_trial = 0 and the circumsphere or cube V_0 (HPMC_ERR_ARG at the
+ * next sweep otherwise).  eps = 0 (default): hard. */
+int hpmc_set_soft(hpmc_ctx *ctx, double eps);
+
 /* Colloids in use.  Replica r keeps its colloids in its slots 0..n_live-1
  * (the RNG stream of a colloid is its slot); slots beyond are not moved,
  * binned or tested.  hpmc_set_live sets the count of one replica (0..its

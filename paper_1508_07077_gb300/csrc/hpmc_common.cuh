@@ -160,6 +160,7 @@ struct Rep {
     // (1..kShellLevels) samples R_in <= |e| < R_s with R_in = sh_rin[k-1],
     // thickness sh_h[k-1]; its Poisson table is the (k-1)-th block of nF
     // entries at t_off
+    double soft_eps;       // > 0: Hertz colloid-depletant interaction (eps in kT), FP64 form
     int v0_shell;
     int v0_cube;           // V_0 is the cube [-R_s, R_s)^3: every attempt is a depletant
     double dd;             // level thickness step sqrt(3) d_max / 32

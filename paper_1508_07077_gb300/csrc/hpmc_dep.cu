@@ -42,6 +42,7 @@ struct Params {
     int ilp = 1;
     double margin = 0.0;
     int v0_mode = HPMC_V0_CIRCUMSPHERE;
+    double soft_eps = 0.0;
 };
 
 // one replica as the caller described it
@@ -282,6 +283,12 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
     R.half_nc = nc / 2;
     R.n_stencil = nc == 2 ? 2 : 3;
     R.nF = R.v0_shell ? shell_stride : (int)F.size();
+    // soft colloid-depletant interaction: spheres, FP64 form, no CB, a V_0
+    // that holds the new circumsphere
+    if (p.soft_eps > 0.0 && (p.shape != HPMC_SPHERE || c->precision != HPMC_FP64 ||
+                             h.n_trial != 0 || p.v0_mode == HPMC_V0_SHELL))
+        return HPMC_ERR_ARG;
+    R.soft_eps = p.soft_eps;
     R.v0_cube = p.v0_mode == HPMC_V0_CUBE ? 1 : 0;
     R.has_dep = lambda > 0.0 ? 1 : 0;
     R.n_trial = h.n_trial;
@@ -1278,6 +1285,14 @@ int hpmc_set_v0(hpmc_ctx *c, int mode)
     if (!c || mode < HPMC_V0_CIRCUMSPHERE || mode > HPMC_V0_CUBE) return HPMC_ERR_ARG;
     if (mode == HPMC_V0_SHELL && c->prm.shape != HPMC_SPHERE) return HPMC_ERR_ARG;
     c->prm.v0_mode = mode;
+    c->dirty = true;
+    return HPMC_OK;
+}
+
+int hpmc_set_soft(hpmc_ctx *c, double eps)
+{
+    if (!c || !(eps >= 0.0) || !std::isfinite(eps) || eps > 1e6) return HPMC_ERR_ARG;
+    c->prm.soft_eps = eps;
     c->dirty = true;
     return HPMC_OK;
 }

@@ -26,6 +26,54 @@ __device__ __forceinline__ bool free_of_nb_fp64(const Rep &R, double y0, double 
     return true;
 }
 
+// --- soft (Hertz) colloid-depletant interaction -----------------------------
+// u(r) = eps (1 - r / s)^(5/2) for r < s = (d + q) / 2.  A depletant blocks a
+// move with probability e^(-U_others) max(0, e^(-u_old) - e^(-u_new)), the
+// neighbours' energies summed in ascending index.
+
+// e^(-y), y >= 0, written out so that every form gives the same bits:
+// y = k ln2 + r with ln2 in a 29-bit head and a tail (Cody and Waite's
+// reduction), |r| <= ln2 / 2, e^(-r) by its Taylor polynomial of degree 14
+// (Horner), then the exact scaling by 2^-k.
+__device__ __forceinline__ double exp_neg_spec(double y)
+{
+    if (!(y < 700.0)) return 0.0;
+    const double kd = floor(y * 0x1.71547652b82fep+0 + 0.5);
+    const double r = (y - kd * 0x1.62e42ff000000p-1) - kd * -0x1.718432a1b0e26p-35;
+    const double x = -r;
+    const double c[15] = {1.0 / 87178291200.0, 1.0 / 6227020800.0, 1.0 / 479001600.0,
+                          1.0 / 39916800.0, 1.0 / 3628800.0, 1.0 / 362880.0, 1.0 / 40320.0,
+                          1.0 / 5040.0, 1.0 / 720.0, 1.0 / 120.0, 1.0 / 24.0, 1.0 / 6.0, 0.5,
+                          1.0, 1.0};
+    double p = c[0];
+#pragma unroll
+    for (int n = 1; n < 15; ++n) p = p * x + c[n];
+    return ldexp(p, -(int)kd);
+}
+
+__device__ __forceinline__ double hertz_spec(const Rep &R, double r2)
+{
+    if (!(r2 < R.R_s2)) return 0.0;
+    const double t = 1.0 - sqrt(r2) / R.R_s;
+    return R.soft_eps * ((t * t) * sqrt(t));
+}
+
+__device__ __noinline__ bool soft_blocks(const Rep &R, uint4 w, double e0, double e1, double e2,
+                                         double o0, double o1, double o2, const double4 *nb, int nnb)
+{
+    const double u0 = e0 - o0, u1 = e1 - o1, u2 = e2 - o2;
+    const double e_new = exp_neg_spec(hertz_spec(R, norm2(e0, e1, e2)));
+    const double e_old = exp_neg_spec(hertz_spec(R, norm2(u0, u1, u2)));
+    if (!(e_old > e_new)) return false;
+    double U = 0.0;
+    for (int a = 0; a < nnb; ++a) {
+        const double4 d = nb[a];
+        U = U + hertz_spec(R, norm2(e0 - d.x, e1 - d.y, e2 - d.z));
+    }
+    const double b = exp_neg_spec(U) * (e_old - e_new);
+    return u01(w.w) < b;
+}
+
 struct CbResult {
     double f;
     uint32_t fwd_ok, rev_ok, caps;
@@ -167,7 +215,7 @@ __global__ void __launch_bounds__(kMaxThreads)
             if (r2 < R.contact2) ov = 1;
             if (r2 < R.nb_cut2) {
                 const int slot = atomicAdd(&s_nnb, 1);
-                s_nb[slot] = make_double4(d0, d1, d2, 0.0);
+                s_nb[slot] = make_double4(d0, d1, d2, (double)pj);
             }
         }
         if (__syncthreads_or(ov)) {
@@ -175,6 +223,20 @@ __global__ void __launch_bounds__(kMaxThreads)
             continue;
         }
         const int nnb = s_nnb;
+        if (R.soft_eps > 0.0) {
+            // soft interactions sum the neighbours' energies in ascending index
+            if (tid == 0)
+                for (int a = 1; a < nnb; ++a) {
+                    const double4 v = s_nb[a];
+                    int b = a - 1;
+                    while (b >= 0 && s_nb[b].w > v.w) {
+                        s_nb[b + 1] = s_nb[b];
+                        --b;
+                    }
+                    s_nb[b + 1] = v;
+                }
+            __syncthreads();
+        }
 
         bool accept = true;
         if (R.has_dep) {
@@ -196,8 +258,9 @@ __global__ void __launch_bounds__(kMaxThreads)
                 const uint32_t t = t0 + (uint32_t)tid;
                 double e0 = 0.0, e1 = 0.0, e2 = 0.0;
                 bool inside = false;
+                uint4 w = make_uint4(0, 0, 0, 0);
                 if (t < t_max) {
-                    const uint4 w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, t);
+                    w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, t);
                     if (lvl > 0) {
                         inside = shell_point64(R, lvl, w, e0, e1, e2);
                     } else {
@@ -219,12 +282,16 @@ __global__ void __launch_bounds__(kMaxThreads)
                 const int k = k0 + base + __popc(bal & ((1u << lane) - 1u));
                 bool blocking = false;
                 if (inside && k < n_p) {
-                    // irrelevant unless it overlaps the new pose; ignored if it
-                    // overlaps the old configuration
-                    if (SphereFP64::dep(R, e0, e1, e2) &&
-                        !SphereFP64::dep(R, e0 - o0, e1 - o1, e2 - o2) &&
-                        free_of_nb_fp64(R, e0, e1, e2, s_nb, nnb))
+                    if (R.soft_eps > 0.0) {
+                        // soft: blocks with probability e^-U_others (e^-u_old - e^-u_new)
+                        blocking = soft_blocks(R, w, e0, e1, e2, o0, o1, o2, s_nb, nnb);
+                    } else if (SphereFP64::dep(R, e0, e1, e2) &&
+                               !SphereFP64::dep(R, e0 - o0, e1 - o1, e2 - o2) &&
+                               free_of_nb_fp64(R, e0, e1, e2, s_nb, nnb)) {
+                        // irrelevant unless it overlaps the new pose; ignored if
+                        // it overlaps the old configuration
                         blocking = true;
+                    }
                 }
                 // depletants classified up to an early exit (same count as a serial loop)
                 if (R.n_trial == 0) {

@@ -26,7 +26,7 @@ HPMC_V0_CIRCUMSPHERE, HPMC_V0_SHELL, HPMC_V0_CUBE = 0, 1, 2
 EXPORTS = ("hpmc_init", "hpmc_init_batch", "hpmc_get_replica", "hpmc_set_replica_moves",
            "hpmc_set_shape", "hpmc_set_depletant", "hpmc_set_moves",
            "hpmc_set_cells", "hpmc_set_launch", "hpmc_autotune", "hpmc_set_fp32_margin",
-           "hpmc_set_v0", "hpmc_set_live", "hpmc_get_live", "hpmc_gibbs_exchange",
+           "hpmc_set_v0", "hpmc_set_soft", "hpmc_set_live", "hpmc_get_live", "hpmc_gibbs_exchange",
            "hpmc_get_gibbs", "hpmc_set_timing",
            "hpmc_get_timing", "hpmc_sweep", "hpmc_get_state",
            "hpmc_set_state", "hpmc_reset_counters", "hpmc_sync", "hpmc_cell_list",
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
                                 ctypes.POINTER(ctypes.c_double)]
     L.hpmc_set_fp32_margin.argtypes = [vp, ctypes.c_double]
     L.hpmc_set_v0.argtypes = [vp, ip]
+    L.hpmc_set_soft.argtypes = [vp, ctypes.c_double]
     L.hpmc_set_live.argtypes = [vp, ip, ip]
     L.hpmc_get_live.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.hpmc_gibbs_exchange.argtypes = [vp, ip, vp]
@@ -260,6 +261,10 @@ def hpmc_set_v0(ctx, mode):
     _check(load().hpmc_set_v0(ctx, int(mode)), "hpmc_set_v0")
 
 
+def hpmc_set_soft(ctx, eps):
+    _check(load().hpmc_set_soft(ctx, float(eps)), "hpmc_set_soft")
+
+
 def hpmc_set_live(ctx, replica, n_live):
     _check(load().hpmc_set_live(ctx, int(replica), int(n_live)), "hpmc_set_live")
 
@@ -416,7 +421,7 @@ class Sampler:
     def __init__(self, pos, box_l, *, quat=None, shape=HPMC_SPHERE, shape_params=(1.0,),
                  q=0.0, n_r=0.0, n_trial=0, d_max=0.1, a_max=0.0, p_translate=1.0,
                  seed=1, replica=0, precision=HPMC_FP64, n_cell=0, warps=1, ilp=1, device=0,
-                 v0=HPMC_V0_CIRCUMSPHERE):
+                 v0=HPMC_V0_CIRCUMSPHERE, soft_eps=0.0):
         pos = np.ascontiguousarray(pos, dtype=np.float64) if isinstance(pos, np.ndarray) else pos
         if isinstance(quat, np.ndarray):
             quat = np.ascontiguousarray(quat, dtype=np.float64)
@@ -431,6 +436,8 @@ class Sampler:
             hpmc_set_launch(self.ctx, warps, ilp)
             if v0 != HPMC_V0_CIRCUMSPHERE:
                 hpmc_set_v0(self.ctx, v0)
+            if soft_eps:
+                hpmc_set_soft(self.ctx, soft_eps)
         except Exception:
             self.close()
             raise
