@@ -147,6 +147,7 @@ struct Rep {
     // FP32 form: thresholds rounded to float, and the certified margins
     float w32, L32, half_L32, R_s32, T_s32, T_dep32, T_contact32, nb_cut2_32, d_max32;
     float m_r2;            // bound on |r2_fp32 - r2_fp64| (+ threshold rounding), doubled
+    float m_box32;         // the same for vectors from FP32 absolute positions (error ~ u L)
     float m_cell;          // bound on the error of a cell-relative coordinate
     // FP32 form, anisotropic shapes: the shape in float, and the distance
     // margins of the depletant tests and of the colloid-pair certificates

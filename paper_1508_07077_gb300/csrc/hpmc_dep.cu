@@ -339,6 +339,14 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
     if (p.margin > 0.0 && p.margin < m_r2) return HPMC_ERR_ARG;
     R.m_r2 = (float)(p.margin > 0.0 ? p.margin : m_r2);
     R.m_cell = (float)(1e-5 * Wc);
+    {
+        // differences of FP32 images of absolute positions in [0, L): each
+        // component errs by <= 4 u max(L, 1) (two roundings of a coordinate,
+        // the difference, the periodic shift)
+        const double EL = 4.0 * u * std::fmax(h.L, 1.0);
+        const double bl = 2.0 * std::sqrt(3.0) * Rmax * EL + 3.0 * EL * EL + 4.0 * u * Rmax * Rmax + 1e-12;
+        R.m_box32 = (float)std::fmax(1e-5, 2.0 * bl);
+    }
     R.w32 = (float)w;
     R.L32 = (float)h.L;
     R.half_L32 = (float)(0.5 * h.L);

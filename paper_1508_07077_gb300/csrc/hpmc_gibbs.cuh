@@ -21,6 +21,13 @@ constexpr uint32_t kGibbsStream = 0xFFFFFFFEu;   // RNG stream word of the excha
 constexpr int kGibbsCounters = 8;   // attempts, accept, empty, ratio, overlap, depletant, cb, drawn
 constexpr int kMaxGibbsNb = 192;    // colloids within reach of the new (old) circumsphere
 
+__device__ __forceinline__ float fmin_image32(float d, float L, float half_L)
+{
+    if (d > half_L) d = d - L;
+    else if (d < -half_L) d = d + L;
+    return d;
+}
+
 // Block-wide count and rank of a predicate over the CTA's threads (in thread
 // order).  s_warp: one int per warp; every thread must call it.
 __device__ __forceinline__ int block_rank(bool p, int *s_warp, int &rank)
@@ -187,10 +194,24 @@ __global__ void __launch_bounds__(kMaxThreads) k_gibbs_exchange(const __grid_con
         const int ns = s_n[src], nd = s_n[dst];
         const Rep &Rd = *RB[dst], &Rs = *RB[src];
         const double x0 = s_x[0], x1 = s_x[1], x2 = s_x[2];
-        // hard core in the new box; its colloids within reach of the new circumsphere
+        // hard core in the new box; its colloids within reach of the new
+        // circumsphere (F32: distances from FP32 images of the positions with
+        // the box margin, FP64 near the contact distance; the list takes a
+        // superset and keeps exact FP64 offsets)
         int ov = 0;
         for (int j = tid; j < nd; j += nthr) {
             const double4 pj = P.pos[Rd.off + j];
+            bool near = true;
+            if (F32) {
+                const float f0 = fmin_image32((float)pj.x - (float)x0, Rd.L32, Rd.half_L32);
+                const float f1 = fmin_image32((float)pj.y - (float)x1, Rd.L32, Rd.half_L32);
+                const float f2 = fmin_image32((float)pj.z - (float)x2, Rd.L32, Rd.half_L32);
+                const float r2f = norm2f(f0, f1, f2);
+                const int t = tri(r2f, R.T_contact32, Rd.m_box32);
+                if (t == 1) ov = 1;
+                near = t == -1 || r2f < R.nb_cut2_32 + Rd.m_box32;
+                if (!near) continue;
+            }
             const double d0 = min_image(pj.x - x0, Rd.L, Rd.half_L);
             const double d1 = min_image(pj.y - x1, Rd.L, Rd.half_L);
             const double d2 = min_image(pj.z - x2, Rd.L, Rd.half_L);
@@ -210,6 +231,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_gibbs_exchange(const __grid_con
             for (int j = tid; j < ns; j += nthr) {
                 if (j == i) continue;
                 const double4 pj = P.pos[Rs.off + j];
+                if (F32) {
+                    const float f0 = fmin_image32((float)pj.x - (float)o0, Rs.L32, Rs.half_L32);
+                    const float f1 = fmin_image32((float)pj.y - (float)o1, Rs.L32, Rs.half_L32);
+                    const float f2 = fmin_image32((float)pj.z - (float)o2, Rs.L32, Rs.half_L32);
+                    if (!(norm2f(f0, f1, f2) < R.nb_cut2_32 + Rs.m_box32)) continue;
+                }
                 const double d0 = min_image(pj.x - o0, Rs.L, Rs.half_L);
                 const double d1 = min_image(pj.y - o1, Rs.L, Rs.half_L);
                 const double d2 = min_image(pj.z - o2, Rs.L, Rs.half_L);
