@@ -58,20 +58,30 @@ __device__ __forceinline__ double hertz_spec(const Rep &R, double r2)
     return R.soft_eps * ((t * t) * sqrt(t));
 }
 
+// Two exits that give the specification's decision without its full cost:
+// a point no nearer the new centre than the old one has u_new <= u_old (the
+// energy is evaluated monotonically in r2), so e_old - e_new is at most a few
+// ulp of rounding and b < 2^-33 <= u01(w); and since e^(-U) <= 1 (U >= 0),
+// b <= e_old - e_new, so u01(w) >= e_old - e_new decides "not blocking"
+// before the neighbours' energies are summed.
 __device__ __noinline__ bool soft_blocks(const Rep &R, uint4 w, double e0, double e1, double e2,
                                          double o0, double o1, double o2, const double4 *nb, int nnb)
 {
     const double u0 = e0 - o0, u1 = e1 - o1, u2 = e2 - o2;
-    const double e_new = exp_neg_spec(hertz_spec(R, norm2(e0, e1, e2)));
-    const double e_old = exp_neg_spec(hertz_spec(R, norm2(u0, u1, u2)));
+    const double r2n = norm2(e0, e1, e2), r2o = norm2(u0, u1, u2);
+    if (!(r2n < r2o)) return false;
+    const double e_new = exp_neg_spec(hertz_spec(R, r2n));
+    const double e_old = exp_neg_spec(hertz_spec(R, r2o));
     if (!(e_old > e_new)) return false;
+    const double v = u01(w.w);
+    if (!(v < e_old - e_new)) return false;
     double U = 0.0;
     for (int a = 0; a < nnb; ++a) {
         const double4 d = nb[a];
         U = U + hertz_spec(R, norm2(e0 - d.x, e1 - d.y, e2 - d.z));
     }
     const double b = exp_neg_spec(U) * (e_old - e_new);
-    return u01(w.w) < b;
+    return v < b;
 }
 
 struct CbResult {
