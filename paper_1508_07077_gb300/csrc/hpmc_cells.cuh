@@ -33,6 +33,28 @@ __device__ __forceinline__ int4 phase_task(const Rep &R, int r, const int perm[8
 // also writes that replica's schedule.  When the task table is allocated,
 // threads also fill it (one entry per phase and CTA), so that the colour
 // phases start from their cell without recomputing the schedule.
+// cell_coord without the FP64 division in all but rare cases: the FP32
+// quotient (s and 1/w rounded to float, one product: relative error < 4u)
+// decides floor(s / w) when it is more than 8u q + 2^-40 away from an
+// integer, since then the exact quotient and its FP64 rounding lie in the
+// same unit interval; otherwise the FP64 quotient decides.  (GB300 issues
+// FP64 at 1/64 of FP32: the division was most of this kernel's time.)
+__device__ __forceinline__ int cell_coord_fast(double x, double sigma, double L, double w, float iw32,
+                                               int nc)
+{
+    double s = x - sigma;
+    if (s < 0.0) s = s + L;
+    const float q = (float)s * iw32;
+    const float fl = floorf(q);
+    const float m = 8.0f * 0x1p-24f * fmaxf(q, 1.0f) + 0x1p-40f;
+    int c;
+    if (q - fl > m && (fl + 1.0f) - q > m) c = (int)fl;
+    else c = (int)(s / w);
+    if (c >= nc) c = nc - 1;
+    if (c < 0) c = 0;
+    return c;
+}
+
 __global__ void k_cells_bin(const __grid_constant__ SimParams P)
 {
     // the lens kernel behind this one may start at once (it waits for this
@@ -70,9 +92,10 @@ __global__ void k_cells_bin(const __grid_constant__ SimParams P)
     }
     const double4 p = P.pos[g];
     const int nc = R.nc;
-    const int cx = cell_coord(p.x, sigma[0], R.L, R.w, nc);
-    const int cy = cell_coord(p.y, sigma[1], R.L, R.w, nc);
-    const int cz = cell_coord(p.z, sigma[2], R.L, R.w, nc);
+    const float iw32 = 1.0f / R.w32;
+    const int cx = cell_coord_fast(p.x, sigma[0], R.L, R.w, iw32, nc);
+    const int cy = cell_coord_fast(p.y, sigma[1], R.L, R.w, iw32, nc);
+    const int cz = cell_coord_fast(p.z, sigma[2], R.L, R.w, iw32, nc);
     const int c = R.cell_off + cx + nc * (cy + nc * cz);
     const float4 rl = make_float4(cell_rel(p.x, sigma[0], R.L, R.w, cx),
                                   cell_rel(p.y, sigma[1], R.L, R.w, cy),
