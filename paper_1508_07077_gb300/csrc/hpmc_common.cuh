@@ -217,12 +217,9 @@ struct SimParams {
     const unsigned long long *T;   // Poisson CDF tables as integers ceil(F[k] 2^53)
     // per-colloid depletant "lens" lists of this sweep (FP32 form):
     // lens[g][0..n) = (e, (t << 16) | k) of the depletants that overlap the new
-    // pose and not the old one, in depletant order; lens_hdr[g] = (N_p,
-    // depletants obtained from the stream, n, 0)
+    // pose and not the old one, in depletant order (their header is filed
+    // per bin slot, hdr_bin below)
     float4 *lens;
-    int4 *lens_hdr;
-    float4 *lens_move;     // the move's FP32 displacement (the phase kernels reuse it); .w the
-                           // move kind for anisotropic shapes (1 translation, 0 rotation, -1 capped)
     double4 *prop_pos;     // FP32 forms: exact proposed position of this sweep (anisotropic:
                            // .w = move kind)
     double4 *prop_quat;    // and orientation

@@ -76,8 +76,6 @@ struct hpmc_ctx {
     float4 *d_bins = nullptr;     // n_cells x cap (cell offset, global index)
     int cells_alloc = -1;
     float4 *d_lens = nullptr;     // n_total x lens_cap depletant lens points (FP32 form)
-    int4 *d_lens_hdr = nullptr;
-    float4 *d_lens_move = nullptr;
     double4 *d_prop_pos = nullptr, *d_prop_quat = nullptr;
     int lens_cap = 0;
     int4 *d_task = nullptr;       // FP32 sphere form: per-phase cell of every CTA
@@ -425,8 +423,6 @@ SimParams make_params(hpmc_ctx *c)
     P.bins = c->d_bins;
     P.T = c->d_T;
     P.lens = c->d_lens;
-    P.lens_hdr = c->d_lens_hdr;
-    P.lens_move = c->d_lens_move;
     P.prop_pos = c->d_prop_pos;
     P.prop_quat = c->d_prop_quat;
     P.n_cta = c->n_cta;
@@ -775,8 +771,6 @@ int prepare(hpmc_ctx *c)
             CK(cudaMalloc(&c->d_prop_quat, sizeof(double4) * (size_t)c->n_total));
     }
     if (c->precision == HPMC_FP32_RECHECK) {
-        if (!c->d_lens_hdr) CK(cudaMalloc(&c->d_lens_hdr, sizeof(int4) * (size_t)c->n_total));
-        if (!c->d_lens_move) CK(cudaMalloc(&c->d_lens_move, sizeof(float4) * (size_t)c->n_total));
         if (nF_max > c->lens_cap) {
             const double bytes = (double)sizeof(float4) * (double)c->n_total * (double)nF_max;
             if (bytes > 64.0 * (1ull << 30)) return HPMC_ERR_CAP;
@@ -1697,8 +1691,6 @@ void hpmc_destroy(hpmc_ctx *c)
     cudaFree(c->d_count);
     cudaFree(c->d_bins);
     cudaFree(c->d_lens);
-    cudaFree(c->d_lens_hdr);
-    cudaFree(c->d_lens_move);
     cudaFree(c->d_prop_pos);
     cudaFree(c->d_prop_quat);
     cudaFree(c->d_task);

@@ -328,17 +328,6 @@ __device__ __noinline__ CbResult32 cb_factor_fp32(const SimParams &P, const Rep 
     return r;
 }
 
-// Classify one depletant point exactly: blocking iff it overlaps neither the
-// old pose nor a neighbour (it overlaps the new pose, being inside the ball).
-__device__ __noinline__ int exact_classify(const SimParams &P, const Rep &R, uint32_t sweep, int i, uint4 w,
-                                           const float4 *nb, int nnb, const int *acc, int nacc)
-{
-    if (exact_dep(P, R, sweep, i, w, 0, 0, acc, nacc)) return 0;
-    for (int a = 0; a < nnb; ++a)
-        if (exact_dep(P, R, sweep, i, w, 2, __float_as_int(nb[a].w), acc, nacc)) return 0;
-    return 1;
-}
-
 // Shared scratch of the per-move depletant evaluation; f and k point into the
 // dynamic shared memory (blockDim doubles, then blockDim ints).
 struct DepShared {
