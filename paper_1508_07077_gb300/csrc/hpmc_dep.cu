@@ -343,7 +343,7 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
         // the difference, the periodic shift)
         const double EL = 4.0 * u * std::fmax(h.L, 1.0);
         const double bl = 2.0 * std::sqrt(3.0) * Rmax * EL + 3.0 * EL * EL + 4.0 * u * Rmax * Rmax + 1e-12;
-        R.m_box32 = (float)std::fmax(1e-5, 2.0 * bl);
+        R.m_box32 = (float)std::fmax(std::fmax(1e-5, 2.0 * bl), p.margin);
     }
     R.w32 = (float)w;
     R.L32 = (float)h.L;

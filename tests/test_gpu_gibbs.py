@@ -30,9 +30,11 @@ def _pair(n0, phi0, n1, phi1, eta, seed):
     return a, b
 
 
-def _compare(oracle, lib, pairs, cycles, sweeps, exchanges, precision, seed=3):
+def _compare(oracle, lib, pairs, cycles, sweeps, exchanges, precision, seed=3, margin=0.0):
     gp = lib.GibbsPairs([((a.pos, a.L), (b.pos, b.L), prm) for a, b, prm in pairs],
                         seed=seed, precision=precision)
+    if margin:
+        lib.hpmc_set_fp32_margin(gp.ctx, margin)
     for _ in range(cycles):
         gp.cycle(sweeps, exchanges)
     boxes = gp.boxes()
@@ -95,3 +97,11 @@ def test_gibbs_argument_errors(lib):
     with pytest.raises(lib.HPMCError):
         lib.hpmc_gibbs_exchange(smp.ctx, 1)       # one replica: no pair
     smp.close()
+
+
+def test_gibbs_fp32_exact_paths(oracle, lib):
+    """A margin of 1 sends every FP32 point test and distance of the exchange
+    (and of the sweeps) to FP64: the trajectory must not change."""
+    a, b = _pair(40, 0.15, 24, 0.06, 0.05, seed=15)
+    prm = {"q": Q, "n_r": a.n_r, "n_trial": 6, "d_max": 0.1}
+    _compare(oracle, lib, [(a, b, prm)], 4, 1, 10, 1, margin=1.0)

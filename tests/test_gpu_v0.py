@@ -218,3 +218,19 @@ def test_cube_spheres_16384_first_sweeps(oracle, lib, precision):
     for k in oracle.PARITY_COUNTERS:
         assert cnt[k] == rc[k], (k, cnt[k], rc[k])
     assert np.array_equal(pos, ref)
+
+
+def test_cube_fp32_exact_paths(oracle, lib):
+    """Margin 1: every FP32 decision of the cube lens kernel goes to FP64."""
+    s = W.spheres_256(seed=13)
+    smp = lib.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=0.1, seed=3, precision=1, v0=CUBE)
+    lib.hpmc_set_fp32_margin(smp.ctx, 1.0)
+    smp.sweep(4)
+    pos, _, _, cnt = smp.state()
+    smp.close()
+    ref, _, rc, _ = oracle.run(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=0.1, seed=3, n_sweeps=4,
+                               v0_mode=CUBE)
+    for k in oracle.PARITY_COUNTERS:
+        assert cnt[k] == rc[k], (k, cnt[k], rc[k])
+    assert np.array_equal(pos, ref)
+    assert cnt["rechecks"] > cnt["dep_evaluated"]
