@@ -121,7 +121,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sms)}
 
 
-def cpu_oracle_rate(systems, d_max, sweeps, first_sweep=0, v0_mode=0):
+def cpu_oracle_rate(systems, d_max, sweeps, first_sweep=0, v0_mode=0, soft_eps=0.0):
     """Moves/s and insertions/s of the serial oracle on this host (1 core)."""
     from oracle import oracle as O
     O.build()
@@ -130,7 +130,7 @@ def cpu_oracle_rate(systems, d_max, sweeps, first_sweep=0, v0_mode=0):
     for s in systems:
         _, _, c, _ = O.run(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=d_max[s.extra["eta_r"]],
                            seed=s.seed, replica=s.replica, n_sweeps=sweeps, sweep0=first_sweep,
-                           v0_mode=v0_mode)
+                           v0_mode=v0_mode, soft_eps=soft_eps)
         moves += c["moves"]
         drawn += c["dep_drawn"]
         evaluated += c["dep_evaluated"]
@@ -599,6 +599,8 @@ def run_ours(args, ws, rank, local):
     hpmc.hpmc_set_launch(ctx, args.warps, args.ilp)
     if args.v0 == "shell":
         hpmc.hpmc_set_v0(ctx, hpmc.HPMC_V0_SHELL)
+    if args.soft > 0.0:
+        hpmc.hpmc_set_soft(ctx, args.soft)
     ns = [s.n for s in systems]
     d0 = [D_MAX_TUNED[e] for e in etas]
     dtuned = d0 if args.no_tune else tune_batch(ctx, hpmc, d0, ns)
@@ -649,7 +651,7 @@ def run_ours(args, ws, rank, local):
     # the same batch with the shell-restricted V_0 (Sec. III.C remark), same
     # step sizes: reported beside the headline, which keeps the circumsphere
     shell = None
-    if args.v0 == "circumsphere" and not args.no_shell:
+    if args.v0 == "circumsphere" and not args.no_shell and args.soft == 0.0:
         hpmc.hpmc_set_v0(ctx, hpmc.HPMC_V0_SHELL)
         for _ in range(args.warmup):
             step()
@@ -693,7 +695,8 @@ def run_ours(args, ws, rank, local):
     for k, s in enumerate(systems):
         smp = hpmc.Sampler(allpos[off:off + s.n].copy(), s.L, q=s.q, n_r=s.n_r,
                            d_max=dtuned[k], seed=1, replica=descs[k]["replica"],
-                           precision=prec, warps=args.warps, ilp=args.ilp, device=local)
+                           precision=prec, warps=args.warps, ilp=args.ilp, device=local,
+                           soft_eps=args.soft)
         hpmc.hpmc_set_state(smp.ctx, allpos[off:off + s.n].copy(), None, sweep_now)
         smp.sweep(1)
         singles.append(smp)
@@ -758,6 +761,7 @@ def run_ours(args, ws, rank, local):
             "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "form": "FP32+FP64 recheck" if prec == 1 else "FP64",
                        "v0": args.v0,
+                       "colloid_depletant": ("Hertz eps=%g kT" % args.soft) if args.soft else "hard",
                        "n_trial": 0, "step": "1 sweep of each of 4 systems (65536 moves)",
                        "schedule": "4 systems as one batch (one set of launches per sweep)",
                        "d_max": {str(k): round(v, 5) for k, v in dmax.items()},
@@ -793,7 +797,8 @@ def run_ours(args, ws, rank, local):
             for s in systems:
                 s.extra["eta_r"] = round(s.extra["eta_r"], 1)
             mv, dr, ev, dt, nm = cpu_oracle_rate(systems, dmax, args.cpu_sweeps,
-                                                 v0_mode=1 if args.v0 == "shell" else 0)
+                                                 v0_mode=1 if args.v0 == "shell" else 0,
+                                                 soft_eps=args.soft)
             line["cpu_baseline"] = {
                 "value": mv, "unit": "moves/s", "cores": 1, "kind": "oracle",
                 "sample": "%d sweep(s) of each of the 4 systems from the fcc start "
@@ -827,6 +832,9 @@ def main():
                     help="depletant region V_0 of the spheres workload: the new pose's "
                          "circumsphere (the paper's; default, with a shell measurement "
                          "alongside) or the excluded-volume shell of the move")
+    ap.add_argument("--soft", type=float, default=0.0,
+                    help="Hertz colloid-depletant interaction of this strength (kT); "
+                         "FP64 form only (use with --precision fp64)")
     ap.add_argument("--no-shell", action="store_true",
                     help="skip the shell-V_0 measurement beside the headline")
     ap.add_argument("--cpu-sweeps-shape", type=int, default=3)
@@ -835,6 +843,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.soft and args.precision != "fp64":
+        ap.error("--soft needs --precision fp64")
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank)
