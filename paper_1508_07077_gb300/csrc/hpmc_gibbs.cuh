@@ -312,12 +312,13 @@ __global__ void __launch_bounds__(kMaxThreads) k_gibbs_exchange(const __grid_con
                             s_cnt[src][kDepBlocking]++;
                             ++nblock;
                         }
-                        const double f = (double)nf / (double)(nr + 1);
-                        if (f == 0.0) {
+                        // f = nf / (nr + 1) is zero iff nf is (the FP64 quotient
+                        // and product only in thread 0)
+                        if (nf == 0) {
                             stop = kb;
                             break;
                         }
-                        if (tid == 0) W = W * f;
+                        if (tid == 0) W = W * ((double)nf / (double)(nr + 1));
                     }
                 }
                 if (stop >= 0) {

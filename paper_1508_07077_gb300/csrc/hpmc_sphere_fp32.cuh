@@ -207,7 +207,7 @@ __device__ __noinline__ bool exact_shell_pt(const Rep &R, int lvl, uint4 w, floa
 // (direction 2 u r, radius 5 u R_s, |v|^2 in the scale 6 u r, sqrt, division
 // and product 3 u r).  |v| < 2^-7 (probability 2^-21) is left to FP64.
 __device__ __forceinline__ int shell_point32(const Rep &R, float rin, float h, uint4 w, float &e0, float &e1,
-                                             float &e2)
+                                             float &e2, float &r_out)
 {
     constexpr float u = 0x1p-24f;
     const float v0 = __int2float_rn((int)(w.x ^ 0x80000000u)) * 0x1p-31f;
@@ -215,6 +215,7 @@ __device__ __forceinline__ int shell_point32(const Rep &R, float rin, float h, u
     const float v2 = __int2float_rn((int)(w.z ^ 0x80000000u)) * 0x1p-31f;
     const float p2 = norm2f(v0, v1, v2);
     const float r = __fmaf_rn(h, __uint2float_rn(w.w) * 0x1p-32f, rin);
+    r_out = r;
     const float r2 = r * r;
     const float A = ((p2 * p2) * p2) * R.R_s4_32;
     const float B = r2 * r2;
@@ -570,15 +571,19 @@ __global__ void __launch_bounds__(128, 4) k_lens_shell_fp32(const __grid_constan
     int k = 0, m = 0;
     for (uint32_t t = 0; k < n_p && t < t_max; ++t) {
         const uint4 w = philox_rk(make_uint4(sweep, tag, kPDep << 24, t), K);
-        float e0 = 0.f, e1 = 0.f, e2 = 0.f;
-        int in = shell_point32(R, rin32, h32, w, e0, e1, e2);
+        float e0 = 0.f, e1 = 0.f, e2 = 0.f, r32 = 0.f;
+        int in = shell_point32(R, rin32, h32, w, e0, e1, e2, r32);
         if (in == -1) {
             ++rck;
             in = exact_shell_pt(R, lvl, w, e0, e1, e2) ? 1 : 0;
+            r32 = R.R_s32;   // (no radius bound from the FP64 path)
         }
         if (!in) continue;
         const int kk = k++;
-        int tn = tri(norm2f(e0, e1, e2), R.T_dep32, R.m_r2);   // overlaps the new pose
+        // overlaps the new pose: certain when the radius is clear of R_s (r32
+        // errs by <= 5u R_s, and |e|^2 in FP64 by a few 2^-53 relative, so
+        // r < R_s (1 - 2^-18) - 5u R_s puts |e|^2 below R_s^2); else tested
+        int tn = r32 < R.R_s32 * (1.0f - 0x1p-18f) ? 1 : tri(norm2f(e0, e1, e2), R.T_dep32, R.m_r2);
         if (tn == -1) {
             ++rck;
             tn = exact_dep_shell(P, R, sweep, i, w, 4) ? 1 : 0;
