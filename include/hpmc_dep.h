@@ -247,8 +247,10 @@ int hpmc_get_live(hpmc_ctx *ctx, int *n_live);
  * depletant index as sub; accept with purpose 7 sub 0, u53 < W).  On
  * acceptance the new box's slot n_dst takes the colloid and the old box's
  * last colloid moves into the vacated slot.  The exchange's depletant
- * counters go to the source box's counters.  FP64.  HPMC_ERR_ARG for an
- * odd replica count, a non-sphere shape or unequal depletant parameters. */
+ * counters go to the source box's counters.  FP64 decisions (the FP32 form
+ * takes its point tests in FP32 with certified margins, FP64 inside them).
+ * HPMC_ERR_ARG for an odd replica count, a non-sphere shape, unequal
+ * depletant parameters, the shell or cube V_0 or a soft interaction. */
 int hpmc_gibbs_exchange(hpmc_ctx *ctx, int n_attempts, void *stream);
 
 /* Pair p's attempt count and its counters (attempts, accepted, rejected:
@@ -280,7 +282,12 @@ int hpmc_get_state(hpmc_ctx *ctx, double *pos, double *quat, int mem,
                    uint64_t *sweep, hpmc_counters *counters, void *stream);
 
 /* Replace positions / orientations (quat may be NULL to keep them) and the
- * sweep index (checkpoint / resume: bit-exact continuation). */
+ * sweep index (checkpoint / resume: bit-exact continuation).  Synchronises
+ * `stream`: the buffers are consumed on return, and the new configuration
+ * is checked in the same round trip (positions in the box, no overlaps; a
+ * failed check is reported by the next hpmc_sweep, as HPMC_ERR_OVERLAP or
+ * HPMC_ERR_ARG).  After a parameter change the check runs at the next sweep
+ * instead. */
 int hpmc_set_state(hpmc_ctx *ctx, const double *pos, const double *quat, int mem,
                    uint64_t sweep, void *stream);
 

@@ -26,7 +26,7 @@ TARGETS = {
                                        "hpmc_sphere_fp64.cuh", "hpmc_sphere_fp32.cuh",
                                        "hpmc_shapes.cuh", "hpmc_aniso_fp64.cuh",
                                        "hpmc_shapes32.cuh", "hpmc_aniso_fp32.cuh",
-                                       "hpmc_probe.cuh"]),
+                                       "hpmc_probe.cuh", "hpmc_gibbs.cuh"]),
     "libhpmc_peaks.so": (["pipe_peaks.cu"], []),
 }
 

@@ -275,7 +275,12 @@ __device__ __forceinline__ int dep_self32(const SimParams &P, const Rep &R, floa
     return t;
 }
 
-// CB factor of one blocking depletant (Sec. III.D, Eq. 12), FP32 form.
+// CB factor of one blocking depletant k (Sec. III.D, Eq. 12), FP32 form,
+// computed by a whole warp (all 32 lanes call it with the same k): the trials
+// of a direction are the first n_fwd (n_rev) attempts of the stream
+// (purpose, k) inside the sampling ball; lanes take consecutive attempts and
+// a ballot ranks the in-ball ones.  Returns the same values in every lane
+// except rck (the lane's own FP64 re-takes).
 __device__ __noinline__ CbResult32 cb_factor_aniso32(const SimParams &P, const Rep &R, uint32_t sweep,
                                                      int i, uint32_t k, float3 o, const Frame32 &Fn,
                                                      const Frame32 &Fo, const Nb32 *nb, int nnb,
@@ -283,38 +288,55 @@ __device__ __noinline__ CbResult32 cb_factor_aniso32(const SimParams &P, const R
 {
     CbResult32 r = {0.0, 0u, 0u, 0u, 0u};
     const uint32_t tag = (uint32_t)(i - R.off);
-    const int n_fwd = R.n_trial, n_rev = R.n_trial - 1;
-    int nf = 0, nr = 0, found = 0;
-    uint32_t t = 0;
-    uint4 w;
-    float e0, e1, e2;
-    while (found < n_fwd && next_in_ball32(P, R, sweep, tag, kPCbFwd, k, t, 64u * (uint32_t)(n_fwd + 1),
-                                           w, e0, e1, e2, r.rck)) {
-        ++found;
-        const float3 e = make_float3(e0, e1, e2);
-        const float3 y = make_float3(o.x + e0, o.y + e1, o.z + e2);
-        if (dep_self32(P, R, e, Fo, i, w, 1, 1, r.rck) == 0) continue;   // must overlap the old pose
-        if (dep_self32(P, R, y, Fn, i, w, 1, 0, r.rck) == 1) continue;   // not the new pose
-        if (!free_nb_aniso32(P, R, y, nb, nnb, i, w, 1, acc, nacc, r.rck)) continue;
-        ++nf;
+    const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+    for (int dir = 0; dir < 2; ++dir) {
+        const bool fwd = dir == 0;
+        const int n_want = fwd ? R.n_trial : R.n_trial - 1;
+        const uint32_t purpose = fwd ? kPCbFwd : kPCbRev;
+        const uint32_t t_max = 64u * (uint32_t)(n_want + 1);
+        int found = 0, ok = 0;
+        for (uint32_t t0 = 0; found < n_want && t0 < t_max; t0 += 32u) {
+            const uint32_t t = t0 + (threadIdx.x & 31);
+            uint4 w = make_uint4(0u, 0u, 0u, 0u);
+            float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+            int in = 0;
+            if (t < t_max) {
+                w = draw(R.key0, R.key1, sweep, tag, purpose, k, t);
+                e0 = coord32(w.x, R.R_s32);
+                e1 = coord32(w.y, R.R_s32);
+                e2 = coord32(w.z, R.R_s32);
+                in = tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
+                if (in == -1) {
+                    ++r.rck;
+                    in = exact_ball(P, R, w) ? 1 : 0;
+                }
+            }
+            const unsigned bal = __ballot_sync(kFull, in != 0);
+            bool good = false;
+            if (in && found + __popc(bal & lt) < n_want) {
+                const float3 e = make_float3(e0, e1, e2);
+                if (fwd) {
+                    // must overlap the old pose and miss the new one
+                    const float3 y = make_float3(o.x + e0, o.y + e1, o.z + e2);
+                    good = dep_self32(P, R, e, Fo, i, w, 1, 1, r.rck) != 0 &&
+                           dep_self32(P, R, y, Fn, i, w, 1, 0, r.rck) != 1 &&
+                           free_nb_aniso32(P, R, y, nb, nnb, i, w, 1, acc, nacc, r.rck);
+                } else {
+                    // must overlap the new pose and miss the old one
+                    good = dep_self32(P, R, e, Fn, i, w, 0, 0, r.rck) != 0 &&
+                           dep_self32(P, R, make_float3(e0 - o.x, e1 - o.y, e2 - o.z), Fo, i, w, 0, 1,
+                                      r.rck) != 1 &&
+                           free_nb_aniso32(P, R, e, nb, nnb, i, w, 0, acc, nacc, r.rck);
+                }
+            }
+            ok += __popc(__ballot_sync(kFull, good));
+            found += min(__popc(bal), n_want - found);
+        }
+        if (found < n_want) ++r.caps;
+        if (fwd) r.fwd_ok = (uint32_t)ok;
+        else r.rev_ok = (uint32_t)ok;
     }
-    if (found < n_fwd) ++r.caps;
-    t = 0;
-    found = 0;
-    while (found < n_rev && next_in_ball32(P, R, sweep, tag, kPCbRev, k, t, 64u * (uint32_t)(n_rev + 1),
-                                           w, e0, e1, e2, r.rck)) {
-        ++found;
-        const float3 e = make_float3(e0, e1, e2);
-        if (dep_self32(P, R, e, Fn, i, w, 0, 0, r.rck) == 0) continue;   // overlaps the new pose
-        if (dep_self32(P, R, make_float3(e0 - o.x, e1 - o.y, e2 - o.z), Fo, i, w, 0, 1, r.rck) == 1)
-            continue;                                                    // not the old pose
-        if (!free_nb_aniso32(P, R, e, nb, nnb, i, w, 0, acc, nacc, r.rck)) continue;
-        ++nr;
-    }
-    if (found < n_rev) ++r.caps;
-    r.fwd_ok = (uint32_t)nf;
-    r.rev_ok = (uint32_t)nr;
-    r.f = (double)nf / (double)(nr + 1);
+    r.f = (double)r.fwd_ok / (double)(r.rev_ok + 1);
     return r;
 }
 
@@ -396,7 +418,7 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
     const int cell_off = cell - (cx + nc * (cy + nc * cz));
     const int *count = P.count[par];
     const Rep &R = P.reps[r];
-    const float w32 = R.w32, L32 = R.L32, half_L32 = R.half_L32;
+    const float w32 = R.w32;
     const int has_dep = R.has_dep;
     const Sched *S = P.sched + r;
     if (tid == 0) P.count[par ^ 1][cell] = 0;
@@ -690,15 +712,25 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
                         break;
                     }
                 } else {
+                    // the factors of the warp's blocking depletants in
+                    // ascending k, each by the whole warp; a zero factor
+                    // rejects the move, so the ones after it are not needed
                     double f = -1.0;
-                    if (blocking) {
-                        const CbResult32 cr = cb_factor_aniso32(P, R, sweep, i, (uint32_t)kk, o, Fn, Fo,
-                                                                s_nb, nnb, s_accl, nacc);
-                        f = cr.f;
-                        od.fwd += cr.fwd_ok;
-                        od.rev += cr.rev_ok;
-                        od.cap += cr.caps;
+                    unsigned bm = __ballot_sync(kFull, blocking);
+                    while (bm) {
+                        const int b = __ffs(bm) - 1;
+                        bm &= bm - 1u;
+                        const uint32_t kb = (uint32_t)__shfl_sync(kFull, kk, b);
+                        const CbResult32 cr = cb_factor_aniso32(P, R, sweep, i, kb, o, Fn, Fo, s_nb, nnb,
+                                                                s_accl, nacc);
                         od.rck += cr.rck;
+                        if (lane == b) {
+                            f = cr.f;
+                            od.fwd += cr.fwd_ok;
+                            od.rev += cr.rev_ok;
+                            od.cap += cr.caps;
+                        }
+                        if (cr.fwd_ok == 0) break;
                     }
                     if (cb_pass(sh, tid, nthr, f, kk, od, -1)) {
                         od.rejected = 1;

@@ -243,6 +243,7 @@ struct SimParams {
     int *n_live;
     unsigned long long *gibbs_step;
     unsigned long long *gibbs_cnt;
+    float4 *pos32;         // FP32 images of the positions, kept by the exchange kernel
     Sched *sched;          // per replica
     unsigned long long *sweep;     // next sweep index (all replicas)
     unsigned long long *counters;  // [n_rep][kRepSlots][kNumCounters]

@@ -111,6 +111,7 @@ struct hpmc_ctx {
     // colloids in use per replica; Gibbs pairs' exchange steps and counters
     int *d_n_live = nullptr;
     unsigned long long *d_gibbs_step = nullptr, *d_gibbs_cnt = nullptr;
+    float4 *d_gibbs_pos32 = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool dirty = true;        // parameters changed: re-derive and re-record the graph
@@ -430,6 +431,7 @@ SimParams make_params(hpmc_ctx *c)
     P.n_live = c->d_n_live;
     P.gibbs_step = c->d_gibbs_step;
     P.gibbs_cnt = c->d_gibbs_cnt;
+    P.pos32 = c->d_gibbs_pos32;
     P.task_ord = c->d_task_ord;
     P.cls_count = c->d_cls_count;
     P.binpos = c->d_binpos;
@@ -619,29 +621,34 @@ void free_graph(hpmc_ctx *c)
 }
 
 // Configuration check on cell lists of the current sweep index: positions in
-// [0, L) and no overlapping colloids, in every replica.  Synchronous.
-int check_config(hpmc_ctx *c)
+// [0, L) and no overlapping colloids, in every replica.  Synchronous: runs
+// on stream s (the context's own stream by default, after its pending work)
+// and waits for it.
+int check_config(hpmc_ctx *c, cudaStream_t s = nullptr, bool own = true)
 {
     const size_t cbytes = sizeof(int) * 2 * (size_t)c->n_cells;
-    CK(cudaStreamSynchronize(c->cap_stream));
-    CK(cudaMemsetAsync(c->d_count, 0, cbytes, c->cap_stream));
-    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->cap_stream));
-    int rc = enqueue_cells(c, c->cap_stream);
+    if (own) {
+        s = c->cap_stream;
+        CK(cudaStreamSynchronize(s));
+    }
+    CK(cudaMemsetAsync(c->d_count, 0, cbytes, s));
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
+    int rc = enqueue_cells(c, s);
     if (rc != HPMC_OK) return rc;
-    CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->cap_stream));
+    CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
     SimParams P = make_params(c);
     if (c->prm.shape == HPMC_SPHERE && c->precision == HPMC_FP32_RECHECK)
-        k_check_spheres32<<<(c->n_total + 255) / 256, 256, 0, c->cap_stream>>>(P, c->d_flag);
+        k_check_spheres32<<<(c->n_total + 255) / 256, 256, 0, s>>>(P, c->d_flag);
     else if (c->prm.shape == HPMC_SPHERE)
-        k_check_spheres<<<(c->n_total + 255) / 256, 256, 0, c->cap_stream>>>(P, c->d_flag);
+        k_check_spheres<<<(c->n_total + 255) / 256, 256, 0, s>>>(P, c->d_flag);
     else
-        k_check_aniso<<<(c->n_total + 127) / 128, 128, 0, c->cap_stream>>>(P, c->d_flag);
+        k_check_aniso<<<(c->n_total + 127) / 128, 128, 0, s>>>(P, c->d_flag);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(c->h_pin + kPinFlag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->cap_stream));
-    CK(cudaMemcpyAsync(c->h_pin + kPinErr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->cap_stream));
+    CK(cudaMemcpyAsync(c->h_pin + kPinFlag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->h_pin + kPinErr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     // the sweeps start from zeroed populations
-    CK(cudaMemsetAsync(c->d_count, 0, cbytes, c->cap_stream));
-    CK(cudaStreamSynchronize(c->cap_stream));
+    CK(cudaMemsetAsync(c->d_count, 0, cbytes, s));
+    CK(cudaStreamSynchronize(s));
     const int flag = *reinterpret_cast<const int *>(c->h_pin + kPinFlag);
     const int err = *reinterpret_cast<const int *>(c->h_pin + kPinErr);
     if (flag & 2) return HPMC_ERR_ARG;
@@ -1412,9 +1419,16 @@ int hpmc_set_state(hpmc_ctx *c, const double *pos, const double *quat, int mem, 
     c->h_pin[kPinUp] = sweep;
     CK(cudaMemcpyAsync(c->d_sweep, c->h_pin + kPinUp, sizeof(unsigned long long),
                        cudaMemcpyHostToDevice, s));
-    CK(cudaStreamSynchronize(s));
-    c->state_dirty = true;  // re-validate the new configuration at the next sweep
-    return HPMC_OK;
+    c->state_dirty = true;  // re-validate the new configuration before the next sweep
+    if (c->dirty) {
+        // (the next sweep prepares the context, the check included)
+        CK(cudaStreamSynchronize(s));
+        return HPMC_OK;
+    }
+    // validate now, in the same host round trip as the upload; a failed check
+    // leaves the state dirty, so the next sweep repeats it and reports it
+    rc = check_config(c, s, false);
+    return rc == HPMC_ERR_CUDA ? rc : HPMC_OK;
 }
 
 int hpmc_reset_counters(hpmc_ctx *c)
@@ -1498,6 +1512,8 @@ int hpmc_gibbs_exchange(hpmc_ctx *c, int n_attempts, void *stream)
     if (!c || n_attempts < 0) return HPMC_ERR_ARG;
     const int n_rep = (int)c->reps.size();
     if (c->prm.shape != HPMC_SPHERE || (n_rep & 1)) return HPMC_ERR_ARG;
+    // (the exchange inserts depletants in the circumsphere, hard interaction)
+    if (c->prm.v0_mode != HPMC_V0_CIRCUMSPHERE || c->prm.soft_eps > 0.0) return HPMC_ERR_ARG;
     for (int p = 0; p < n_rep / 2; ++p) {
         const RepHost &a = c->reps[(size_t)(2 * p)], &b = c->reps[(size_t)(2 * p + 1)];
         if (a.q != b.q || a.n_r != b.n_r || a.n_trial != b.n_trial) return HPMC_ERR_ARG;
@@ -1519,6 +1535,7 @@ int hpmc_gibbs_exchange(hpmc_ctx *c, int n_attempts, void *stream)
         CK(cudaMalloc(&c->d_gibbs_cnt, sizeof(unsigned long long) * np * kGibbsCounters));
         CK(cudaMemset(c->d_gibbs_step, 0, sizeof(unsigned long long) * np));
         CK(cudaMemset(c->d_gibbs_cnt, 0, sizeof(unsigned long long) * np * kGibbsCounters));
+        CK(cudaMalloc(&c->d_gibbs_pos32, sizeof(float4) * (size_t)(c->n_total > 0 ? c->n_total : 1)));
     }
     if (n_attempts == 0 || n_rep == 0) return HPMC_OK;
     SimParams P = make_params(c);
@@ -1715,6 +1732,7 @@ void hpmc_destroy(hpmc_ctx *c)
     cudaFree(c->d_n_live);
     cudaFree(c->d_gibbs_step);
     cudaFree(c->d_gibbs_cnt);
+    cudaFree(c->d_gibbs_pos32);
     delete c;
 }
 

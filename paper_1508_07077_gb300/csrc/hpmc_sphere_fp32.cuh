@@ -280,52 +280,74 @@ struct CbResult32 {
     uint32_t fwd_ok, rev_ok, caps, rck;
 };
 
-// CB factor of one blocking depletant (Sec. III.D, Eq. 12), FP32 form.  For
-// spheres "overlaps the pose the ball is centred on" is the ball test itself.
-__device__ __noinline__ CbResult32 cb_factor_fp32(const SimParams &P, const Rep &R, uint32_t sweep, int i,
-                                                  uint32_t k, float o0, float o1, float o2,
-                                                  const float4 *nb, int nnb, const int *acc,
-                                                  int nacc)
+// CB factor of one blocking depletant k (Sec. III.D, Eq. 12), FP32 form,
+// computed by a whole warp (all 32 lanes call it with the same k).  The
+// trials of a direction are the first n_fwd (n_rev) attempts of the stream
+// (purpose, k) that fall inside the sampling ball: lanes take consecutive
+// attempts, a ballot ranks the in-ball ones, and the lanes holding trials
+// test them.  For spheres "overlaps the pose the ball is centred on" is the
+// ball test itself.  Returns the same values in every lane except rck (the
+// lane's own FP64 re-takes).
+__device__ __noinline__ CbResult32 cb_factor_warp32(const SimParams &P, const Rep &R, uint32_t sweep, int i,
+                                                    uint32_t k, float o0, float o1, float o2,
+                                                    const float4 *nb, int nnb, const int *acc,
+                                                    int nacc)
 {
     CbResult32 r = {0.0, 0u, 0u, 0u, 0u};
     const uint32_t tag = (uint32_t)(i - R.off);
-    const int n_fwd = R.n_trial, n_rev = R.n_trial - 1;
-    int nf = 0, nr = 0, found = 0;
-    uint32_t t = 0;
-    uint4 w;
-    float e0, e1, e2;
-    while (found < n_fwd && next_in_ball32(P, R, sweep, tag, kPCbFwd, k, t, 64u * (uint32_t)(n_fwd + 1),
-                                           w, e0, e1, e2, r.rck)) {
-        ++found;
-        const float y0 = o0 + e0, y1 = o1 + e1, y2 = o2 + e2;
-        int tn = tri(norm2f(y0, y1, y2), R.T_dep32, R.m_r2);  // overlaps the new pose?
-        if (tn == -1) {
-            ++r.rck;
-            tn = exact_dep(P, R, sweep, i, w, 1, 0, acc, nacc) ? 1 : 0;
+    const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+    for (int dir = 0; dir < 2; ++dir) {
+        const bool fwd = dir == 0;
+        const int n_want = fwd ? R.n_trial : R.n_trial - 1;
+        const uint32_t purpose = fwd ? kPCbFwd : kPCbRev;
+        const uint32_t t_max = 64u * (uint32_t)(n_want + 1);
+        int found = 0, ok = 0;
+        for (uint32_t t0 = 0; found < n_want && t0 < t_max; t0 += 32u) {
+            const uint32_t t = t0 + (threadIdx.x & 31);
+            uint4 w = make_uint4(0u, 0u, 0u, 0u);
+            float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+            int in = 0;
+            if (t < t_max) {
+                w = draw(R.key0, R.key1, sweep, tag, purpose, k, t);
+                e0 = coord32(w.x, R.R_s32);
+                e1 = coord32(w.y, R.R_s32);
+                e2 = coord32(w.z, R.R_s32);
+                in = tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
+                if (in == -1) {
+                    ++r.rck;
+                    in = exact_ball(P, R, w) ? 1 : 0;
+                }
+            }
+            const unsigned bal = __ballot_sync(kFull, in != 0);
+            bool good = false;
+            if (in && found + __popc(bal & lt) < n_want) {
+                if (fwd) {
+                    // forward trial around the old pose: must miss the new pose
+                    const float y0 = o0 + e0, y1 = o1 + e1, y2 = o2 + e2;
+                    int tn = tri(norm2f(y0, y1, y2), R.T_dep32, R.m_r2);
+                    if (tn == -1) {
+                        ++r.rck;
+                        tn = exact_dep(P, R, sweep, i, w, 1, 0, acc, nacc) ? 1 : 0;
+                    }
+                    good = !tn && free_nb32(P, R, y0, y1, y2, nb, nnb, sweep, i, w, 3, acc, nacc, r.rck);
+                } else {
+                    // reverse trial around the new pose: must miss the old pose
+                    int to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), R.T_dep32, R.m_r2);
+                    if (to == -1) {
+                        ++r.rck;
+                        to = exact_dep(P, R, sweep, i, w, 0, 0, acc, nacc) ? 1 : 0;
+                    }
+                    good = !to && free_nb32(P, R, e0, e1, e2, nb, nnb, sweep, i, w, 2, acc, nacc, r.rck);
+                }
+            }
+            ok += __popc(__ballot_sync(kFull, good));
+            found += min(__popc(bal), n_want - found);
         }
-        if (tn) continue;
-        if (!free_nb32(P, R, y0, y1, y2, nb, nnb, sweep, i, w, 3, acc, nacc, r.rck)) continue;
-        ++nf;
+        if (found < n_want) ++r.caps;
+        if (fwd) r.fwd_ok = (uint32_t)ok;
+        else r.rev_ok = (uint32_t)ok;
     }
-    if (found < n_fwd) ++r.caps;
-    t = 0;
-    found = 0;
-    while (found < n_rev && next_in_ball32(P, R, sweep, tag, kPCbRev, k, t, 64u * (uint32_t)(n_rev + 1),
-                                           w, e0, e1, e2, r.rck)) {
-        ++found;
-        int to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), R.T_dep32, R.m_r2);  // old pose?
-        if (to == -1) {
-            ++r.rck;
-            to = exact_dep(P, R, sweep, i, w, 0, 0, acc, nacc) ? 1 : 0;
-        }
-        if (to) continue;
-        if (!free_nb32(P, R, e0, e1, e2, nb, nnb, sweep, i, w, 2, acc, nacc, r.rck)) continue;
-        ++nr;
-    }
-    if (found < n_rev) ++r.caps;
-    r.fwd_ok = (uint32_t)nf;
-    r.rev_ok = (uint32_t)nr;
-    r.f = (double)nf / (double)(nr + 1);
+    r.f = (double)r.fwd_ok / (double)(r.rev_ok + 1);
     return r;
 }
 
@@ -991,15 +1013,25 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
                         break;
                     }
                 } else {
+                    // the factors of the warp's blocking depletants in
+                    // ascending k, each by the whole warp; a zero factor
+                    // rejects the move, so the ones after it are not needed
                     double f = -1.0;
-                    if (blocking) {
-                        const CbResult32 r = cb_factor_fp32(P, R, sweep, i, (uint32_t)kk, o0, o1, o2,
-                                                            s_nb, nnb, s_accl, nacc);
-                        f = r.f;
-                        o.fwd += r.fwd_ok;
-                        o.rev += r.rev_ok;
-                        o.cap += r.caps;
+                    unsigned bm = __ballot_sync(kFull, blocking);
+                    while (bm) {
+                        const int b = __ffs(bm) - 1;
+                        bm &= bm - 1u;
+                        const uint32_t kb = (uint32_t)__shfl_sync(kFull, kk, b);
+                        const CbResult32 r = cb_factor_warp32(P, R, sweep, i, kb, o0, o1, o2, s_nb, nnb,
+                                                              s_accl, nacc);
                         o.rck += r.rck;
+                        if (lane == b) {
+                            f = r.f;
+                            o.fwd += r.fwd_ok;
+                            o.rev += r.rev_ok;
+                            o.cap += r.caps;
+                        }
+                        if (r.fwd_ok == 0) break;
                     }
                     if (cb_pass(sh, tid, nthr, f, kk, o, -1)) {
                         o.rejected = 1;

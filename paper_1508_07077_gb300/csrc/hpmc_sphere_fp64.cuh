@@ -91,46 +91,58 @@ struct CbResult {
 
 // Configurational-bias factor of blocking depletant k (Sec. III.D, Eq. 12):
 // f = N'_insert / (N_insert + 1); n_trial forward trials in the old
-// circumsphere, n_trial - 1 reverse trials in the new one.
+// circumsphere, n_trial - 1 reverse trials in the new one.  The trials of a
+// direction are the first n_fwd (n_rev) attempts of the stream (purpose, k)
+// inside the ball.  Computed by a whole warp (all 32 lanes call it with the
+// same k): lanes take consecutive attempts and a ballot ranks the in-ball
+// ones.  Returns the same values in every lane.
 __device__ __noinline__ CbResult cb_factor_fp64(const Rep &R, uint32_t sweep, uint32_t tag,
                                                 uint32_t k, double o0, double o1, double o2,
                                                 const double4 *nb, int nnb)
 {
     CbResult r = {0.0, 0u, 0u, 0u};
-    const int n_fwd = R.n_trial, n_rev = R.n_trial - 1;
-    int nf = 0, nr = 0, found = 0;
-    uint32_t t = 0, t_max = 64u * (uint32_t)(n_fwd + 1);
-    while (found < n_fwd && t < t_max) {
-        const uint4 w = draw(R.key0, R.key1, sweep, tag, kPCbFwd, k, t);
-        ++t;
-        const double e0 = R.R_s * s11(w.x), e1 = R.R_s * s11(w.y), e2 = R.R_s * s11(w.z);
-        if (!(norm2(e0, e1, e2) < R.R_s2)) continue;
-        ++found;
-        const double y0 = o0 + e0, y1 = o1 + e1, y2 = o2 + e2;
-        if (!SphereFP64::dep(R, e0, e1, e2)) continue;      // must overlap the old pose
-        if (SphereFP64::dep(R, y0, y1, y2)) continue;       // must not overlap the new pose
-        if (!free_of_nb_fp64(R, y0, y1, y2, nb, nnb)) continue;
-        ++nf;
+    const uint32_t lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int dir = 0; dir < 2; ++dir) {
+        const bool fwd = dir == 0;
+        const int n_want = fwd ? R.n_trial : R.n_trial - 1;
+        const uint32_t purpose = fwd ? kPCbFwd : kPCbRev;
+        const uint32_t t_max = 64u * (uint32_t)(n_want + 1);
+        int found = 0, ok = 0;
+        for (uint32_t t0 = 0; found < n_want && t0 < t_max; t0 += 32u) {
+            const uint32_t t = t0 + lane;
+            double e0 = 0.0, e1 = 0.0, e2 = 0.0;
+            bool in = false;
+            if (t < t_max) {
+                const uint4 w = draw(R.key0, R.key1, sweep, tag, purpose, k, t);
+                e0 = R.R_s * s11(w.x);
+                e1 = R.R_s * s11(w.y);
+                e2 = R.R_s * s11(w.z);
+                in = norm2(e0, e1, e2) < R.R_s2;
+            }
+            const unsigned bal = __ballot_sync(kFull, in);
+            bool good = false;
+            if (in && found + __popc(bal & lt) < n_want) {
+                if (fwd) {
+                    // must overlap the old pose and miss the new one
+                    const double y0 = o0 + e0, y1 = o1 + e1, y2 = o2 + e2;
+                    good = SphereFP64::dep(R, e0, e1, e2) && !SphereFP64::dep(R, y0, y1, y2) &&
+                           free_of_nb_fp64(R, y0, y1, y2, nb, nnb);
+                } else {
+                    // must overlap the new pose and miss the old one
+                    good = SphereFP64::dep(R, e0, e1, e2) &&
+                           !SphereFP64::dep(R, e0 - o0, e1 - o1, e2 - o2) &&
+                           free_of_nb_fp64(R, e0, e1, e2, nb, nnb);
+                }
+            }
+            ok += __popc(__ballot_sync(kFull, good));
+            found += min(__popc(bal), n_want - found);
+        }
+        if (found < n_want) ++r.caps;
+        if (fwd) r.fwd_ok = (uint32_t)ok;
+        else r.rev_ok = (uint32_t)ok;
     }
-    if (found < n_fwd) ++r.caps;
-    t = 0;
-    t_max = 64u * (uint32_t)(n_rev + 1);
-    found = 0;
-    while (found < n_rev && t < t_max) {
-        const uint4 w = draw(R.key0, R.key1, sweep, tag, kPCbRev, k, t);
-        ++t;
-        const double e0 = R.R_s * s11(w.x), e1 = R.R_s * s11(w.y), e2 = R.R_s * s11(w.z);
-        if (!(norm2(e0, e1, e2) < R.R_s2)) continue;
-        ++found;
-        if (!SphereFP64::dep(R, e0, e1, e2)) continue;                  // overlaps the new pose
-        if (SphereFP64::dep(R, e0 - o0, e1 - o1, e2 - o2)) continue;   // not the old pose
-        if (!free_of_nb_fp64(R, e0, e1, e2, nb, nnb)) continue;
-        ++nr;
-    }
-    if (found < n_rev) ++r.caps;
-    r.fwd_ok = (uint32_t)nf;
-    r.rev_ok = (uint32_t)nr;
-    r.f = (double)nf / (double)(nr + 1);
+    r.f = (double)r.fwd_ok / (double)(r.rev_ok + 1);
     return r;
 }
 
@@ -314,15 +326,24 @@ __global__ void __launch_bounds__(kMaxThreads)
                     }
                     cnt[kDepEval] += (unsigned long long)min(total, n_p - k0);
                 } else {
-                    // a7: CB factors of this pass, multiplied in ascending k
+                    // a7: CB factors of this pass (each warp's blocking
+                    // depletants in ascending k, each by the whole warp; a
+                    // zero factor rejects, so the ones after it are not
+                    // needed), multiplied in ascending k
                     double f = -1.0;
-                    if (blocking) {
-                        const CbResult cr = cb_factor_fp64(R, sweep, tag, (uint32_t)k, o0, o1, o2,
-                                                          s_nb, nnb);
-                        f = cr.f;
-                        cnt[kCbFwdOk] += cr.fwd_ok;
-                        cnt[kCbRevOk] += cr.rev_ok;
-                        cnt[kCapHits] += cr.caps;
+                    unsigned bm = __ballot_sync(kFull, blocking);
+                    while (bm) {
+                        const int b = __ffs(bm) - 1;
+                        bm &= bm - 1u;
+                        const uint32_t kb = (uint32_t)__shfl_sync(kFull, k, b);
+                        const CbResult cr = cb_factor_fp64(R, sweep, tag, kb, o0, o1, o2, s_nb, nnb);
+                        if (lane == b) {
+                            f = cr.f;
+                            cnt[kCbFwdOk] += cr.fwd_ok;
+                            cnt[kCbRevOk] += cr.rev_ok;
+                            cnt[kCapHits] += cr.caps;
+                        }
+                        if (cr.fwd_ok == 0) break;
                     }
                     s_f[tid] = f;
                     s_k[tid] = k;

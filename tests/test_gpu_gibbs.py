@@ -58,7 +58,7 @@ def _compare(oracle, lib, pairs, cycles, sweeps, exchanges, precision, seed=3, m
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("n_trial,eta", [(0, 0.003), (8, 0.05)])
+@pytest.mark.parametrize("n_trial,eta", [(0, 0.003), (8, 0.05), (40, 0.08)])
 def test_gibbs_pair_matches_oracle(oracle, lib, precision, n_trial, eta):
     a, b = _pair(48, 0.15, 24, 0.06, eta, seed=5)
     prm = {"q": Q, "n_r": a.n_r, "n_trial": n_trial, "d_max": 0.1}
@@ -92,6 +92,15 @@ def test_gibbs_argument_errors(lib):
     with pytest.raises(lib.HPMCError):
         lib.hpmc_set_live(gp.ctx, 0, 41)          # beyond the replica's slots
     gp.close()
+    # the exchange inserts its depletants in the circumsphere, hard interaction
+    for setter, value in ((lib.hpmc_set_v0, 1), (lib.hpmc_set_v0, 2), (lib.hpmc_set_soft, 3.0)):
+        gp = lib.GibbsPairs([((a.pos, a.L), (b.pos, b.L), {"q": Q, "n_r": a.n_r})],
+                            precision=0)
+        setter(gp.ctx, value)
+        with pytest.raises(lib.HPMCError) as e:
+            lib.hpmc_gibbs_exchange(gp.ctx, 1)
+        assert e.value.code == -1
+        gp.close()
     s = W.spheres_256()
     smp = lib.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r)
     with pytest.raises(lib.HPMCError):

@@ -79,6 +79,13 @@ def test_configurational_bias(oracle, lib, shape, phi, q, eta, n_trial, precisio
 
 @pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("shape,phi,q,eta", SHAPES)
+def test_many_reinsertion_trials(oracle, lib, shape, phi, q, eta, precision):
+    """n_trial = 24: each CB factor's trial streams span several warp passes."""
+    _compare(oracle, lib, _small(shape, phi, q, eta, seed=4), 4, n_trial=24, precision=precision)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("shape,phi,q,eta", SHAPES)
 @pytest.mark.parametrize("warps", [2, 8])
 def test_launch_shapes(oracle, lib, shape, phi, q, eta, warps, precision):
     s = _small(shape, phi, q, eta, seed=3)

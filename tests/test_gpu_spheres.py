@@ -89,6 +89,16 @@ def test_spheres_256_configurational_bias(oracle, lib, n_trial, precision):
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("warps", [1, 4])
+def test_many_reinsertion_trials(oracle, lib, warps, precision):
+    """n_trial = 40: a warp takes each CB factor's trial streams in several
+    passes of 32 attempts (the first n_trial in-ball attempts by rank)."""
+    cnt = _compare(oracle, lib, W.spheres_256(seed=6), 10, n_trial=40, d_max=0.08, warps=warps,
+                   precision=precision)
+    assert cnt["reject_cb"] > 0 and cnt["accept"] > 0
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("warps,ilp", [(1, 1), (1, 2), (3, 2), (8, 1), (8, 2)])
 def test_launch_shape_does_not_change_results(oracle, lib, warps, ilp, precision):
     for n_trial in (0, 2):
@@ -224,3 +234,31 @@ def test_configuration_check_at_contact(oracle, lib, precision):
         smp.sweep(1)
     assert e.value.code == -1
     smp.close()
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_uploaded_state_is_checked(oracle, lib, precision):
+    """hpmc_set_state checks the uploaded configuration in its own round trip:
+    an overlap (or a position outside the box) is reported by every following
+    sweep until a valid state replaces it; a valid upload continues the
+    oracle's trajectory."""
+    s = W.spheres_256(seed=9)
+    smp = lib.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=0.05, precision=precision)
+    smp.sweep(2)
+    good, _, sweep, _ = smp.state()
+    bad = good.copy()
+    bad[1] = (bad[0] + np.array([0.0, 0.4, 0.0])) % s.L
+    outside = good.copy()
+    outside[5, 2] = s.L
+    for pos, code in ((bad, -2), (outside, -1)):
+        lib.hpmc_set_state(smp.ctx, pos, None, sweep)
+        for _ in range(2):
+            with pytest.raises(lib.HPMCError) as e:
+                smp.sweep(1)
+            assert e.value.code == code
+    lib.hpmc_set_state(smp.ctx, good, None, sweep)
+    smp.sweep(3)
+    p, _, sw, _ = smp.state()
+    smp.close()
+    ref, _, _, _ = oracle.run(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=0.05, n_sweeps=5)
+    assert sw == 5 and np.array_equal(p, ref)
