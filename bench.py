@@ -366,16 +366,27 @@ def run_gibbs(args, ws, rank, local):
     g1 = [hpmc.hpmc_get_gibbs(gp.ctx, p)[1] for p in range(n_pairs)]
     gd = {k: sum(b[k] - a[k] for a, b in zip(g0, g1)) for k in g1[0]}
     live = hpmc.hpmc_get_live(gp.ctx, 2 * n_pairs)
+    # the replica counters hold the sweeps' blocking depletants too: the
+    # exchange's own rate per attempt from two more steps (untimed), the
+    # counters read between the sweep and the exchanges
+    ex_blk = 0
+    for _ in range(2):
+        hpmc.hpmc_sweep(gp.ctx, 1, stream)
+        _, c_a = hpmc.hpmc_get_state(gp.ctx, None, None, stream)
+        hpmc.hpmc_gibbs_exchange(gp.ctx, n_ex, stream)
+        _, c_b = hpmc.hpmc_get_state(gp.ctx, None, None, stream)
+        ex_blk += c_b["dep_blocking"] - c_a["dep_blocking"]
+    blk_per_attempt = ex_blk / (2.0 * n_ex * n_pairs)
     gp.close()
     ms, ex_ms = R.reduce_max([ms, ex_ms], "cuda")
     attempts_all, moves_all, blocking_all = R.reduce_sum(
-        [gd["attempts"], cnt["moves"], cnt["dep_blocking"]], "cuda")
+        [gd["attempts"], cnt["moves"], blk_per_attempt * gd["attempts"]], "cuda")
     if rank == 0:
         clocks = clk.summary()
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         peak = sms * ISSUE_LANES_PER_SM * 2070.0e6 / 1e12
         # exchange kernel: depletant streams and 2 n_trial - 1 CB trials per
-        # blocking depletant, 6/pi attempts per point in the ball
+        # blocking depletant of an exchange, 6/pi attempts per point in the ball
         trials = 6.0 / math.pi * (gd["dep_drawn"] + blocking_all * (2 * n_trial - 1))
         achieved = OPS_PER_GIBBS_TRIAL * trials / (ex_ms * 1e-3) / 1e12
         line = {
@@ -392,6 +403,7 @@ def run_gibbs(args, ws, rank, local):
             "sweep_ms_per_step": sweep_ms / args.steps,
             "exchange_acceptance": gd["accept"] / max(1, gd["attempts"]),
             "exchange_outcomes": gd,
+            "exchange_blocking_per_attempt": blk_per_attempt,
             "box_populations": {"min": min(live), "max": max(live)},
             "gpu_launches": args.steps * (1 + (1 if prec == 1 else 0) + 8 + 1),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",

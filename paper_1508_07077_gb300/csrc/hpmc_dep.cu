@@ -638,7 +638,7 @@ int check_config(hpmc_ctx *c, cudaStream_t s = nullptr, bool own = true)
     CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
     SimParams P = make_params(c);
     if (c->prm.shape == HPMC_SPHERE && c->precision == HPMC_FP32_RECHECK)
-        k_check_spheres32<<<(c->n_total + 255) / 256, 256, 0, s>>>(P, c->d_flag);
+        k_check_spheres32<<<(unsigned)(((size_t)c->n_total * kCheckStencil + 255) / 256), 256, 0, s>>>(P, c->d_flag);
     else if (c->prm.shape == HPMC_SPHERE)
         k_check_spheres<<<(c->n_total + 255) / 256, 256, 0, s>>>(P, c->d_flag);
     else

@@ -1116,57 +1116,60 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
 }
 
 // Configuration check (positions in the box, no overlapping pair), FP32
-// sphere form: distances from the FP32
-// cell-relative copies the cell-list kernel filed in the bins (its bin slot
-// from binpos), decided with the certified margin and re-taken in FP64 (the
-// positions, minimum image) only inside it.
+// sphere form: distances from the FP32 cell-relative copies the cell-list
+// kernel filed in the bins (its bin slot from binpos), decided with the
+// certified margin and re-taken in FP64 (the positions, minimum image) only
+// inside it.  One thread per (colloid, stencil cell): every thread's loads
+// are two dependent rounds (the cell's population, then its entries).
+constexpr int kCheckStencil = 27;
+
 __global__ void k_check_spheres32(const __grid_constant__ SimParams P, int *flag)
 {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t gt = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = (int)(gt / kCheckStencil), t = (int)(gt % kCheckStencil);
     if (g >= P.n_total) return;
     const int r = P.rep_of[g];
     const Rep &R = P.reps[r];
     if (g - R.off >= P.n_live[r]) return;
     const double4 pi = P.pos[g];
     if (!(pi.x >= 0.0 && pi.x < R.L && pi.y >= 0.0 && pi.y < R.L && pi.z >= 0.0 && pi.z < R.L)) {
-        atomicOr(flag, 2);
+        if (t == 0) atomicOr(flag, 2);
         return;
     }
+    const int nc = R.nc;
+    const int ns = nc == 2 ? 2 : 3;
+    if (t >= ns * ns * ns) return;
     const int bp = P.binpos[g];
     if (bp < 0) return;   // a full cell: the cell-list kernel has flagged it
-    const int nc = R.nc;
     const int cl = bp / P.cap - R.cell_off;
     const int cx = cl % nc, cy = (cl / nc) % nc, cz = cl / (nc * nc);
     const float4 ri = P.bins[bp];
     const Sched &S = P.sched[r];
     const int *count = P.count[S.sweep & 1u];
-    const int ns = nc == 2 ? 2 : 3;
     const float w32 = R.w32, L32 = R.L32, half_L32 = R.half_L32;
-    for (int t = 0; t < ns * ns * ns; ++t) {
-        int dx, dy, dz;
-        const int c = stencil_cell_nc(nc, R.cell_off, t, cx, cy, cz, dx, dy, dz);
-        const int m = min(count[c], P.cap);
-        const float fx = (float)dx * w32 - ri.x, fy = (float)dy * w32 - ri.y, fz = (float)dz * w32 - ri.z;
-        for (int s = 0; s < m; ++s) {
-            const float4 e = P.bins[(size_t)c * P.cap + s];
-            const int j = __float_as_int(e.w);
-            if (j == g) continue;
-            float d0 = fx + e.x, d1 = fy + e.y, d2 = fz + e.z;
-            if (nc == 2) {
-                if (d0 > half_L32) d0 -= L32; else if (d0 < -half_L32) d0 += L32;
-                if (d1 > half_L32) d1 -= L32; else if (d1 < -half_L32) d1 += L32;
-                if (d2 > half_L32) d2 -= L32; else if (d2 < -half_L32) d2 += L32;
-            }
-            int o = tri(norm2f(d0, d1, d2), R.T_contact32, R.m_r2);
-            if (o == -1) {
-                const double4 pj = P.pos[j];
-                const double r2 = norm2(min_image(pj.x - pi.x, R.L, R.half_L),
-                                        min_image(pj.y - pi.y, R.L, R.half_L),
-                                        min_image(pj.z - pi.z, R.L, R.half_L));
-                o = r2 < R.contact2 ? 1 : 0;
-            }
-            if (o == 1) atomicOr(flag, 1);
+    int dx, dy, dz;
+    const int c = stencil_cell_nc(nc, R.cell_off, t, cx, cy, cz, dx, dy, dz);
+    const int m = min(count[c], P.cap);
+    const float fx = (float)dx * w32 - ri.x, fy = (float)dy * w32 - ri.y, fz = (float)dz * w32 - ri.z;
+    for (int s = 0; s < m; ++s) {
+        const float4 e = P.bins[(size_t)c * P.cap + s];
+        const int j = __float_as_int(e.w);
+        if (j == g) continue;
+        float d0 = fx + e.x, d1 = fy + e.y, d2 = fz + e.z;
+        if (nc == 2) {
+            if (d0 > half_L32) d0 -= L32; else if (d0 < -half_L32) d0 += L32;
+            if (d1 > half_L32) d1 -= L32; else if (d1 < -half_L32) d1 += L32;
+            if (d2 > half_L32) d2 -= L32; else if (d2 < -half_L32) d2 += L32;
         }
+        int o = tri(norm2f(d0, d1, d2), R.T_contact32, R.m_r2);
+        if (o == -1) {
+            const double4 pj = P.pos[j];
+            const double r2 = norm2(min_image(pj.x - pi.x, R.L, R.half_L),
+                                    min_image(pj.y - pi.y, R.L, R.half_L),
+                                    min_image(pj.z - pi.z, R.L, R.half_L));
+            o = r2 < R.contact2 ? 1 : 0;
+        }
+        if (o == 1) atomicOr(flag, 1);
     }
 }
 
