@@ -497,9 +497,11 @@ template <int CAP>
 void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
 {
     const int threads = 32 * c->prm.warps;
-    const size_t dyn = (size_t)threads * (sizeof(double) + sizeof(int));
     bool cb = false;
     for (const RepHost &h : c->reps) cb = cb || h.n_trial > 0;
+    // the CB pass's per-thread factor and index slots; none without CB (the
+    // one-warp CTA of the 16-slot bins then fits 32 per SM)
+    const size_t dyn = cb ? (size_t)threads * (sizeof(double) + sizeof(int)) : 0;
     if (c->precision == HPMC_FP32_RECHECK && c->prm.shape != HPMC_SPHERE) {
         // the anisotropic shapes' packing bound always selects a capacity >= 32
         if constexpr (CAP >= kSmallCellCap) {
