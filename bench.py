@@ -366,6 +366,21 @@ def run_gibbs(args, ws, rank, local):
     g1 = [hpmc.hpmc_get_gibbs(gp.ctx, p)[1] for p in range(n_pairs)]
     gd = {k: sum(b[k] - a[k] for a, b in zip(g0, g1)) for k in g1[0]}
     live = hpmc.hpmc_get_live(gp.ctx, 2 * n_pairs)
+    # end to end through the C ABI with host buffers (pinned), copies timed:
+    # every box's slots uploaded (and checked), one sweep and the exchanges,
+    # the slots and counters read back
+    n_slots = sum(rep["n"] for rep in gp.reps)
+    host_pos = torch.empty((n_slots, 3), dtype=torch.float64).pin_memory().numpy()
+    sweep_now, _ = hpmc.hpmc_get_state(gp.ctx, host_pos)
+    e2e_steps = max(3, min(args.steps, 20) // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        hpmc.hpmc_set_state(gp.ctx, host_pos, None, sweep_now + k, stream)
+        gp.cycle(1, n_ex, stream)
+        hpmc.hpmc_get_state(gp.ctx, host_pos, None, stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
     # the replica counters hold the sweeps' blocking depletants too: the
     # exchange's own rate per attempt from two more steps (untimed), the
     # counters read between the sweep and the exchanges
@@ -378,7 +393,7 @@ def run_gibbs(args, ws, rank, local):
         ex_blk += c_b["dep_blocking"] - c_a["dep_blocking"]
     blk_per_attempt = ex_blk / (2.0 * n_ex * n_pairs)
     gp.close()
-    ms, ex_ms = R.reduce_max([ms, ex_ms], "cuda")
+    ms, ex_ms, e2e_s = R.reduce_max([ms, ex_ms, e2e_s], "cuda")
     attempts_all, moves_all, blocking_all = R.reduce_sum(
         [gd["attempts"], cnt["moves"], blk_per_attempt * gd["attempts"]], "cuda")
     if rank == 0:
@@ -404,6 +419,9 @@ def run_gibbs(args, ws, rank, local):
             "exchange_acceptance": gd["accept"] / max(1, gd["attempts"]),
             "exchange_outcomes": gd,
             "exchange_blocking_per_attempt": blk_per_attempt,
+            "e2e": {"value": ws * e2e_steps * n_ex * n_pairs / e2e_s, "unit": "attempts/s",
+                    "h2d_bytes_per_step": int(host_pos.nbytes),
+                    "d2h_bytes_per_step": int(host_pos.nbytes)},
             "box_populations": {"min": min(live), "max": max(live)},
             "gpu_launches": args.steps * (1 + (1 if prec == 1 else 0) + 8 + 1),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
