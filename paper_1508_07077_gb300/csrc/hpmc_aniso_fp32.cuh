@@ -715,7 +715,8 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
                     // the factors of the warp's blocking depletants in
                     // ascending k, each by the whole warp; a zero factor
                     // rejects the move, so the ones after it are not needed
-                    double f = -1.0;
+                    double f = 0.0;
+                    bool has = false, zero = false;
                     unsigned bm = __ballot_sync(kFull, blocking);
                     while (bm) {
                         const int b = __ffs(bm) - 1;
@@ -726,13 +727,15 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
                         od.rck += cr.rck;
                         if (lane == b) {
                             f = cr.f;
+                            has = true;
+                            zero = cr.fwd_ok == 0;
                             od.fwd += cr.fwd_ok;
                             od.rev += cr.rev_ok;
                             od.cap += cr.caps;
                         }
                         if (cr.fwd_ok == 0) break;
                     }
-                    if (cb_pass(sh, tid, nthr, f, kk, od, -1)) {
+                    if (cb_pass(sh, tid, nthr, has, f, zero, kk, od, -1)) {
                         od.rejected = 1;
                         break;
                     }

@@ -437,6 +437,30 @@ __device__ __forceinline__ int stencil_cell(const Rep &R, int t, int cx, int cy,
 // serialization may start before its predecessor finishes): let the next
 // kernel in the stream launch early, and wait for the predecessor's
 // completion (and the visibility of its writes) before touching its results.
+// (one thread) The factors of a CB pass in ascending slot order, i.e.
+// ascending depletant index: bit l of masks[w] marks slot 32 w + l as holding
+// a factor; kc[slot] is its depletant index k (factor f[slot], nonzero) or
+// -1 - k (a zero factor).  Multiplies the nonzero factors into W up to the
+// first zero one and returns that one's k, else -1; *n_fact counts the
+// factors walked (the zero one included).  Slots are skipped and zeros found
+// by integer tests: a thread's FP64 work is one product per factor.
+__device__ __forceinline__ int cb_walk(const unsigned *masks, int nwarps, const int *kc, const double *f,
+                                       double &W, int &n_fact)
+{
+    for (int w = 0; w < nwarps; ++w) {
+        unsigned m = masks[w];
+        while (m) {
+            const int u = (w << 5) + __ffs(m) - 1;
+            m &= m - 1u;
+            ++n_fact;
+            const int c = kc[u];
+            if (c < 0) return -1 - c;
+            W = W * f[u];
+        }
+    }
+    return -1;
+}
+
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 

@@ -357,6 +357,7 @@ struct DepShared {
     double *f;
     int *k;
     int warp[kMaxThreads / 32];
+    unsigned mask[kMaxThreads / 32];
     int kmin, flag;
 };
 
@@ -369,29 +370,26 @@ struct DepOutcome {
 };
 
 // CB bookkeeping of one pass: slots in ascending depletant index, product in
-// order, stop at a zero factor.  Called by every thread.
-__device__ __forceinline__ bool cb_pass(DepShared &sh, int tid, int nslots, double f, int k,
-                                       DepOutcome &o, int eval_if_full)
+// order, stop at a zero factor.  Called by every thread; has: the thread's
+// slot holds a factor f (zero: f is 0) of depletant k.
+__device__ __forceinline__ bool cb_pass(DepShared &sh, int tid, int nslots, bool has, double f,
+                                        bool zero, int k, DepOutcome &o, int eval_if_full)
 {
-    sh.f[tid] = f;
-    sh.k[tid] = k;
+    const unsigned bal = __ballot_sync(kFull, has);
+    if ((tid & 31) == 0) sh.mask[tid >> 5] = bal;
+    if (has) {
+        sh.f[tid] = f;
+        sh.k[tid] = zero ? -1 - k : k;
+    }
     __syncthreads();
     if (tid == 0) {
-        int zero = 0;
-        for (int u = 0; u < nslots; ++u) {
-            const double fu = sh.f[u];
-            if (fu < 0.0) continue;
-            ++o.nblock;
-            ++o.block;
-            if (fu == 0.0) {
-                zero = 1;
-                o.eval += (uint32_t)(sh.k[u] + 1);
-                break;
-            }
-            o.W = o.W * fu;
-        }
-        if (!zero && eval_if_full >= 0) o.eval += (uint32_t)eval_if_full;
-        sh.flag = zero;
+        int n_fact = 0;
+        const int kz = cb_walk(sh.mask, (nslots + 31) >> 5, sh.k, sh.f, o.W, n_fact);
+        o.nblock += n_fact;
+        o.block += (uint32_t)n_fact;
+        if (kz >= 0) o.eval += (uint32_t)(kz + 1);
+        else if (eval_if_full >= 0) o.eval += (uint32_t)eval_if_full;
+        sh.flag = kz >= 0 ? 1 : 0;
     }
     __syncthreads();
     return sh.flag != 0;
@@ -1016,7 +1014,8 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
                     // the factors of the warp's blocking depletants in
                     // ascending k, each by the whole warp; a zero factor
                     // rejects the move, so the ones after it are not needed
-                    double f = -1.0;
+                    double f = 0.0;
+                    bool has = false, zero = false;
                     unsigned bm = __ballot_sync(kFull, blocking);
                     while (bm) {
                         const int b = __ffs(bm) - 1;
@@ -1027,13 +1026,15 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
                         o.rck += r.rck;
                         if (lane == b) {
                             f = r.f;
+                            has = true;
+                            zero = r.fwd_ok == 0;
                             o.fwd += r.fwd_ok;
                             o.rev += r.rev_ok;
                             o.cap += r.caps;
                         }
                         if (r.fwd_ok == 0) break;
                     }
-                    if (cb_pass(sh, tid, nthr, f, kk, o, -1)) {
+                    if (cb_pass(sh, tid, nthr, has, f, zero, kk, o, -1)) {
                         o.rejected = 1;
                         break;
                     }

@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(kMaxThreads)
     __shared__ double s_f[kMaxThreads];
     __shared__ int s_k[kMaxThreads];
     __shared__ int s_warp[kMaxThreads / 32];
+    __shared__ unsigned s_mask[kMaxThreads / 32];
     __shared__ int s_ncand, s_nnb, s_flag, s_acc, s_kmin;
 
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -330,7 +331,8 @@ __global__ void __launch_bounds__(kMaxThreads)
                     // depletants in ascending k, each by the whole warp; a
                     // zero factor rejects, so the ones after it are not
                     // needed), multiplied in ascending k
-                    double f = -1.0;
+                    double f = 0.0;
+                    bool has = false, zero = false;
                     unsigned bm = __ballot_sync(kFull, blocking);
                     while (bm) {
                         const int b = __ffs(bm) - 1;
@@ -339,31 +341,31 @@ __global__ void __launch_bounds__(kMaxThreads)
                         const CbResult cr = cb_factor_fp64(R, sweep, tag, kb, o0, o1, o2, s_nb, nnb);
                         if (lane == b) {
                             f = cr.f;
+                            has = true;
+                            zero = cr.fwd_ok == 0;
                             cnt[kCbFwdOk] += cr.fwd_ok;
                             cnt[kCbRevOk] += cr.rev_ok;
                             cnt[kCapHits] += cr.caps;
                         }
                         if (cr.fwd_ok == 0) break;
                     }
-                    s_f[tid] = f;
-                    s_k[tid] = k;
+                    // slots holding a factor, by warp ballots; zero factors
+                    // as -1 - k (integer tests only in the walk)
+                    const unsigned hb = __ballot_sync(kFull, has);
+                    if (lane == 0) s_mask[warp] = hb;
+                    if (has) {
+                        s_f[tid] = f;
+                        s_k[tid] = zero ? -1 - k : k;
+                    }
                     __syncthreads();
                     if (tid == 0) {
-                        int zero = 0;
-                        for (int u = 0; u < nthr; ++u) {
-                            const double fu = s_f[u];
-                            if (fu < 0.0) continue;
-                            ++nblock;
-                            cnt[kDepBlocking]++;
-                            if (fu == 0.0) {
-                                zero = 1;
-                                cnt[kDepEval] += (unsigned long long)(s_k[u] - k0 + 1);
-                                break;
-                            }
-                            W = W * fu;
-                        }
-                        if (!zero) cnt[kDepEval] += (unsigned long long)min(total, n_p - k0);
-                        s_flag = zero;
+                        int n_fact = 0;
+                        const int kz = cb_walk(s_mask, nwarps, s_k, s_f, W, n_fact);
+                        nblock += n_fact;
+                        cnt[kDepBlocking] += (unsigned long long)n_fact;
+                        if (kz >= 0) cnt[kDepEval] += (unsigned long long)(kz - k0 + 1);
+                        else cnt[kDepEval] += (unsigned long long)min(total, n_p - k0);
+                        s_flag = kz >= 0 ? 1 : 0;
                     }
                     __syncthreads();
                     if (s_flag) {
