@@ -750,7 +750,7 @@ def run_ours(args, ws, rank, local):
     host_pos = torch.empty((sum(ns), 3), dtype=torch.float64).pin_memory().numpy()
     sweep_now, _ = hpmc.hpmc_get_state(ctx, host_pos)
     torch.cuda.synchronize()
-    e2e_steps = max(3, min(args.steps, 50) // 2)
+    e2e_steps = max(3, min(args.steps, 200) // 2)
     t0 = time.perf_counter()
     for k in range(e2e_steps):
         hpmc.hpmc_set_state(ctx, host_pos, None, sweep_now + k, stream)
