@@ -340,6 +340,12 @@ int hpmc_cell_list_noalloc(int n, double box_l, int n_cell, const double *pos_de
 int hpmc_free_volume(hpmc_ctx *ctx, int replica, double q, uint64_t seed, uint32_t sample,
                      uint64_t n_probe, uint64_t *n_free);
 
+/* Colloid slots of the context (*n_total: the rows of the pos / quat
+ * buffers of hpmc_get_state and hpmc_set_state) and replicas (*n_rep); either
+ * pointer may be NULL.  A pinned host buffer is read or written in place by
+ * the device (no staging copy), so it must hold that many rows. */
+int hpmc_get_size(hpmc_ctx *ctx, int *n_total, int *n_rep);
+
 /* Human-readable name of an HPMC_* code. */
 const char *hpmc_strerror(int code);
 

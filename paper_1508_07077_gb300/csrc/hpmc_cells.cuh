@@ -55,14 +55,16 @@ __device__ __forceinline__ int cell_coord_fast(double x, double sigma, double L,
     return c;
 }
 
-__global__ void k_cells_bin(const __grid_constant__ SimParams P)
+// full = 0: the bins, populations and schedules only (a configuration
+// check), without the phase task table and the exact proposals.
+__global__ void k_cells_bin(const __grid_constant__ SimParams P, int full)
 {
     // the lens kernel behind this one may start at once (it waits for this
     // kernel's results only where it files them)
     pdl_trigger();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (P.cls_count && g < 32) P.cls_count[g] = 0;
-    if (P.task && g < 8 * P.n_cta) {
+    if (full && P.task && g < 8 * P.n_cta) {
         const int phase = g / P.n_cta, a = g - phase * P.n_cta;
         const int r = P.cta_rep[a];
         const Rep &R = P.reps[r];
@@ -111,7 +113,7 @@ __global__ void k_cells_bin(const __grid_constant__ SimParams P)
     P.rel[g] = rl;
     // FP32 sphere form: the exact proposal of this sweep (translation), for
     // the colour phases' commit and exact re-takes
-    if (P.task && R.shape == 0) {
+    if (full && P.task && R.shape == 0) {
         const uint4 wm = draw(R.key0, R.key1, sweep, (uint32_t)(g - R.off), kPMove, 0, 0);
         P.prop_pos[g] = make_double4(wrap_box(p.x + R.d_max * s11(wm.x), R.L),
                                      wrap_box(p.y + R.d_max * s11(wm.y), R.L),

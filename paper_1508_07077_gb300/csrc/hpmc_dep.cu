@@ -114,6 +114,7 @@ struct hpmc_ctx {
     float4 *d_gibbs_pos32 = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t check_exec = nullptr;   // the configuration check of an upload
     bool dirty = true;        // parameters changed: re-derive and re-record the graph
     bool state_dirty = true;  // configuration replaced: re-check overlaps only
 };
@@ -449,12 +450,14 @@ SimParams make_params(hpmc_ctx *c)
 // Enqueue the binned cell lists (and schedules) of the sweep whose index is
 // in *d_sweep.  Their count buffer was zeroed by the previous sweep's phase
 // kernels (or by check_config).
-int enqueue_cells(hpmc_ctx *c, cudaStream_t s)
+// tasks = false: bins for a configuration check only (no phase task table,
+// no proposals)
+int enqueue_cells(hpmc_ctx *c, cudaStream_t s, bool tasks = true)
 {
     SimParams P = make_params(c);
-    const int threads = c->d_task ? std::max(c->n_total, 8 * c->n_cta) : c->n_total;
-    k_cells_bin<<<(threads + 255) / 256, 256, 0, s>>>(P);
-    if (c->d_task) k_task_order<<<(8 * c->n_cta + 255) / 256, 256, 0, s>>>(P);
+    const int threads = (c->d_task && tasks) ? std::max(c->n_total, 8 * c->n_cta) : c->n_total;
+    k_cells_bin<<<(threads + 255) / 256, 256, 0, s>>>(P, tasks ? 1 : 0);
+    if (c->d_task && tasks) k_task_order<<<(8 * c->n_cta + 255) / 256, 256, 0, s>>>(P);
     CK(cudaGetLastError());
     return HPMC_OK;
 }
@@ -617,25 +620,24 @@ int enqueue_sweep_timed(hpmc_ctx *c, cudaStream_t s)
 void free_graph(hpmc_ctx *c)
 {
     if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->check_exec) cudaGraphExecDestroy(c->check_exec);
+    c->check_exec = nullptr;
     if (c->graph) cudaGraphDestroy(c->graph);
     c->exec = nullptr;
     c->graph = nullptr;
 }
 
 // Configuration check on cell lists of the current sweep index: positions in
-// [0, L) and no overlapping colloids, in every replica.  Synchronous: runs
-// on stream s (the context's own stream by default, after its pending work)
-// and waits for it.
-int check_config(hpmc_ctx *c, cudaStream_t s = nullptr, bool own = true)
+// [0, L) and no overlapping colloids, in every replica.  enqueue_check puts
+// the device work on stream s (bins of the current sweep, the check kernel,
+// the flags to pinned host memory, zeroed populations); check_result reads
+// the flags once s has been synchronised.
+int enqueue_check(hpmc_ctx *c, cudaStream_t s)
 {
     const size_t cbytes = sizeof(int) * 2 * (size_t)c->n_cells;
-    if (own) {
-        s = c->cap_stream;
-        CK(cudaStreamSynchronize(s));
-    }
     CK(cudaMemsetAsync(c->d_count, 0, cbytes, s));
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
-    int rc = enqueue_cells(c, s);
+    int rc = enqueue_cells(c, s, false);   // (the phase task order is not needed)
     if (rc != HPMC_OK) return rc;
     CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
     SimParams P = make_params(c);
@@ -650,7 +652,11 @@ int check_config(hpmc_ctx *c, cudaStream_t s = nullptr, bool own = true)
     CK(cudaMemcpyAsync(c->h_pin + kPinErr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     // the sweeps start from zeroed populations
     CK(cudaMemsetAsync(c->d_count, 0, cbytes, s));
-    CK(cudaStreamSynchronize(s));
+    return HPMC_OK;
+}
+
+int check_result(hpmc_ctx *c)
+{
     const int flag = *reinterpret_cast<const int *>(c->h_pin + kPinFlag);
     const int err = *reinterpret_cast<const int *>(c->h_pin + kPinErr);
     if (flag & 2) return HPMC_ERR_ARG;
@@ -658,6 +664,25 @@ int check_config(hpmc_ctx *c, cudaStream_t s = nullptr, bool own = true)
     if (flag & 1) return HPMC_ERR_OVERLAP;
     c->state_dirty = false;
     return HPMC_OK;
+}
+
+// Synchronous check: on the context's own stream after its pending work, or
+// (own = false) on stream s, which the caller has ordered; the recorded
+// check graph when one exists.
+int check_config(hpmc_ctx *c, cudaStream_t s = nullptr, bool own = true)
+{
+    if (own) {
+        s = c->cap_stream;
+        CK(cudaStreamSynchronize(s));
+    }
+    if (c->check_exec) {
+        CK(cudaGraphLaunch(c->check_exec, s));
+    } else {
+        int rc = enqueue_check(c, s);
+        if (rc != HPMC_OK) return rc;
+    }
+    CK(cudaStreamSynchronize(s));
+    return check_result(c);
 }
 
 // Validate parameters, derive every replica, upload tables and maps, check
@@ -795,10 +820,12 @@ int prepare(hpmc_ctx *c)
     c->n_cta = cta_off;
     c->nF_max = nF_max;
 
+    // (the graphs of the previous parameters go first: the check must not
+    // launch a stale one)
+    free_graph(c);
     int rc = check_config(c);
     if (rc != HPMC_OK) return rc;
 
-    free_graph(c);
     CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     rc = enqueue_sweep(c, c->cap_stream);
     cudaGraph_t graph = nullptr;
@@ -810,8 +837,35 @@ int prepare(hpmc_ctx *c)
     CK(e);
     c->graph = graph;
     CK(cudaGraphInstantiate(&c->exec, c->graph, 0));
+    // the check an upload runs, as one graph launch
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue_check(c, c->cap_stream);
+    cudaGraph_t cg = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &cg);
+    if (rc != HPMC_OK) {
+        if (cg) cudaGraphDestroy(cg);
+        return rc;
+    }
+    CK(e);
+    e = cudaGraphInstantiate(&c->check_exec, cg, 0);
+    cudaGraphDestroy(cg);
+    CK(e);
     c->dirty = false;
     return HPMC_OK;
+}
+
+// Device address of a host buffer the GPU reaches directly (page-locked and
+// mapped, as every pinned allocation is under unified addressing), else
+// null: such buffers are read and written in place by the layout kernels,
+// with no staging copy.
+const double *mapped_host(const double *p)
+{
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // (an unregistered pointer is not an error here)
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? static_cast<const double *>(a.devicePointer) : nullptr;
 }
 
 int copy_in(hpmc_ctx *c, const double *pos, const double *quat, int mem, cudaStream_t s)
@@ -825,15 +879,23 @@ int copy_in(hpmc_ctx *c, const double *pos, const double *quat, int mem, cudaStr
     }
     if (mem != HPMC_HOST) return HPMC_ERR_ARG;
     if (pos) {
-        CK(cudaMemcpyAsync(c->d_stage, pos, sizeof(double) * 3 * (size_t)n,
-                           cudaMemcpyHostToDevice, s));
-        k_unpack<<<nb, 256, 0, s>>>(n, c->d_stage, nullptr, c->d_pos, nullptr);
+        const double *src = mapped_host(pos);
+        if (!src) {
+            CK(cudaMemcpyAsync(c->d_stage, pos, sizeof(double) * 3 * (size_t)n,
+                               cudaMemcpyHostToDevice, s));
+            src = c->d_stage;
+        }
+        k_unpack<<<nb, 256, 0, s>>>(n, src, nullptr, c->d_pos, nullptr);
         CK(cudaGetLastError());
     }
     if (quat) {
-        CK(cudaMemcpyAsync(c->d_stage, quat, sizeof(double) * 4 * (size_t)n,
-                           cudaMemcpyHostToDevice, s));
-        k_unpack<<<nb, 256, 0, s>>>(n, nullptr, c->d_stage, nullptr, c->d_quat);
+        const double *src = mapped_host(quat);
+        if (!src) {
+            CK(cudaMemcpyAsync(c->d_stage, quat, sizeof(double) * 4 * (size_t)n,
+                               cudaMemcpyHostToDevice, s));
+            src = c->d_stage;
+        }
+        k_unpack<<<nb, 256, 0, s>>>(n, nullptr, src, nullptr, c->d_quat);
         CK(cudaGetLastError());
     }
     return HPMC_OK;
@@ -1351,19 +1413,33 @@ int hpmc_get_state(hpmc_ctx *c, double *pos, double *quat, int mem, uint64_t *sw
             CK(cudaGetLastError());
         }
     } else {
+        bool staged = false;
         if (pos) {
-            k_pack<<<nb, 256, 0, s>>>(n, c->d_pos, nullptr, c->d_stage, nullptr);
-            CK(cudaGetLastError());
-            CK(cudaMemcpyAsync(pos, c->d_stage, sizeof(double) * 3 * (size_t)n,
-                               cudaMemcpyDeviceToHost, s));
+            double *dst = const_cast<double *>(mapped_host(pos));
+            if (dst) {
+                k_pack<<<nb, 256, 0, s>>>(n, c->d_pos, nullptr, dst, nullptr);
+                CK(cudaGetLastError());
+            } else {
+                k_pack<<<nb, 256, 0, s>>>(n, c->d_pos, nullptr, c->d_stage, nullptr);
+                CK(cudaGetLastError());
+                CK(cudaMemcpyAsync(pos, c->d_stage, sizeof(double) * 3 * (size_t)n,
+                                   cudaMemcpyDeviceToHost, s));
+                staged = true;
+            }
         }
         if (quat) {
-            // (the staging buffer is reused: the position copy must finish first)
-            if (pos) CK(cudaStreamSynchronize(s));
-            k_pack<<<nb, 256, 0, s>>>(n, nullptr, c->d_quat, nullptr, c->d_stage);
-            CK(cudaGetLastError());
-            CK(cudaMemcpyAsync(quat, c->d_stage, sizeof(double) * 4 * (size_t)n,
-                               cudaMemcpyDeviceToHost, s));
+            double *dst = const_cast<double *>(mapped_host(quat));
+            if (dst) {
+                k_pack<<<nb, 256, 0, s>>>(n, nullptr, c->d_quat, nullptr, dst);
+                CK(cudaGetLastError());
+            } else {
+                // (the staging buffer is reused: the position copy must finish first)
+                if (staged) CK(cudaStreamSynchronize(s));
+                k_pack<<<nb, 256, 0, s>>>(n, nullptr, c->d_quat, nullptr, c->d_stage);
+                CK(cudaGetLastError());
+                CK(cudaMemcpyAsync(quat, c->d_stage, sizeof(double) * 4 * (size_t)n,
+                                   cudaMemcpyDeviceToHost, s));
+            }
         }
     }
     // the sweep index, the counters and the error word in the same round trip
@@ -1431,6 +1507,14 @@ int hpmc_set_state(hpmc_ctx *c, const double *pos, const double *quat, int mem, 
     // leaves the state dirty, so the next sweep repeats it and reports it
     rc = check_config(c, s, false);
     return rc == HPMC_ERR_CUDA ? rc : HPMC_OK;
+}
+
+int hpmc_get_size(hpmc_ctx *c, int *n_total, int *n_rep)
+{
+    if (!c) return HPMC_ERR_ARG;
+    if (n_total) *n_total = c->n_total;
+    if (n_rep) *n_rep = (int)c->reps.size();
+    return HPMC_OK;
 }
 
 int hpmc_reset_counters(hpmc_ctx *c)

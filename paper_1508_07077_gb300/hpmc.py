@@ -30,7 +30,8 @@ EXPORTS = ("hpmc_init", "hpmc_init_batch", "hpmc_get_replica", "hpmc_set_replica
            "hpmc_get_gibbs", "hpmc_set_timing",
            "hpmc_get_timing", "hpmc_sweep", "hpmc_get_state",
            "hpmc_set_state", "hpmc_reset_counters", "hpmc_sync", "hpmc_cell_list",
-           "hpmc_cell_list_noalloc", "hpmc_free_volume", "hpmc_strerror", "hpmc_destroy")
+           "hpmc_cell_list_noalloc", "hpmc_free_volume", "hpmc_get_size", "hpmc_strerror",
+           "hpmc_destroy")
 
 
 class HPMCError(RuntimeError):
@@ -109,6 +110,7 @@ def load(path: str = LIB_PATH):
     L.hpmc_cell_list_noalloc.argtypes = L.hpmc_cell_list.argtypes
     L.hpmc_free_volume.argtypes = [vp, ip, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
                                    ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
+    L.hpmc_get_size.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.hpmc_strerror.argtypes = [ip]
     L.hpmc_strerror.restype = ctypes.c_char_p
     L.hpmc_destroy.argtypes = [vp]
@@ -130,7 +132,7 @@ def _check(rc: int, where: str) -> None:
 
 
 def _ptr(buf):
-    """(address, mem kind) of a numpy array (host) or torch tensor / raw int."""
+    """(address, mem kind) of a numpy array (host) or a torch tensor."""
     if buf is None:
         return None, HPMC_HOST
     if isinstance(buf, np.ndarray):
@@ -138,8 +140,8 @@ def _ptr(buf):
             raise ValueError("host arrays must be C-contiguous float64")
         return buf.ctypes.data, HPMC_HOST
     if hasattr(buf, "data_ptr"):
-        if not buf.is_contiguous():
-            raise ValueError("tensors must be contiguous")
+        if not buf.is_contiguous() or str(buf.dtype) != "torch.float64":
+            raise ValueError("tensors must be contiguous float64")
         return buf.data_ptr(), (HPMC_DEVICE if buf.is_cuda else HPMC_HOST)
     raise TypeError("unsupported buffer type %r" % type(buf))
 
@@ -359,9 +361,29 @@ def hpmc_sweep(ctx, n_sweeps=1, stream=None):
     _check(load().hpmc_sweep(ctx, int(n_sweeps), _stream(stream)), "hpmc_sweep")
 
 
+def hpmc_get_size(ctx):
+    """(colloid slots, replicas) of a context."""
+    n, r = ctypes.c_int(), ctypes.c_int()
+    _check(load().hpmc_get_size(ctx, ctypes.byref(n), ctypes.byref(r)), "hpmc_get_size")
+    return int(n.value), int(r.value)
+
+
+def _check_rows(ctx, buf, width, what):
+    """A state buffer must hold exactly one row of `width` per colloid slot
+    (the device reads and writes pinned and device buffers in place)."""
+    if buf is None:
+        return
+    n = hpmc_get_size(ctx)[0]
+    size = buf.size if isinstance(buf, np.ndarray) else buf.numel()
+    if size != n * width:
+        raise ValueError("%s must hold %d x %d values, got %d" % (what, n, width, size))
+
+
 def hpmc_get_state(ctx, pos=None, quat=None, stream=None):
     """Fill pos (n x 3) / quat (n x 4) buffers (numpy or CUDA tensors, same
     memory); returns (sweep, counters dict)."""
+    _check_rows(ctx, pos, 3, "pos")
+    _check_rows(ctx, quat, 4, "quat")
     p, mem = _ptr(pos)
     q, mem_q = _ptr(quat)
     if pos is not None and quat is not None and mem != mem_q:
@@ -376,6 +398,8 @@ def hpmc_get_state(ctx, pos=None, quat=None, stream=None):
 
 
 def hpmc_set_state(ctx, pos=None, quat=None, sweep=0, stream=None):
+    _check_rows(ctx, pos, 3, "pos")
+    _check_rows(ctx, quat, 4, "quat")
     p, mem = _ptr(pos)
     q, mem_q = _ptr(quat)
     if pos is None:

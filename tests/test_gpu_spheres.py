@@ -262,3 +262,28 @@ def test_uploaded_state_is_checked(oracle, lib, precision):
     smp.close()
     ref, _, _, _ = oracle.run(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=0.05, n_sweeps=5)
     assert sw == 5 and np.array_equal(p, ref)
+
+
+def test_pinned_host_buffers_in_place(oracle, lib):
+    """Pinned host buffers are read and written by the device in place (no
+    staging copy): the same state and trajectory as through pageable ones;
+    a buffer of the wrong length is refused before any device access."""
+    s = W.spheres_256(seed=10)
+    smp = lib.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=0.05)
+    smp.sweep(2)
+    pageable = np.empty((s.n, 3))
+    pinned = torch.empty((s.n, 3), dtype=torch.float64).pin_memory().numpy()
+    sweep, _ = lib.hpmc_get_state(smp.ctx, pageable)
+    lib.hpmc_get_state(smp.ctx, pinned)
+    assert np.array_equal(pageable, pinned)
+    lib.hpmc_set_state(smp.ctx, pinned, None, sweep)
+    smp.sweep(3)
+    p, _, sw, _ = smp.state()
+    for bad in (np.zeros((s.n - 1, 3)), torch.zeros((s.n + 1, 3), dtype=torch.float64).pin_memory()):
+        with pytest.raises(ValueError):
+            lib.hpmc_set_state(smp.ctx, bad, None, sweep)
+        with pytest.raises(ValueError):
+            lib.hpmc_get_state(smp.ctx, bad)
+    smp.close()
+    ref, _, _, _ = oracle.run(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=0.05, n_sweeps=5)
+    assert sw == 5 and np.array_equal(p, ref)
