@@ -863,8 +863,8 @@ def main():
                          "circumsphere (the paper's; default, with a shell measurement "
                          "alongside) or the excluded-volume shell of the move")
     ap.add_argument("--soft", type=float, default=0.0,
-                    help="Hertz colloid-depletant interaction of this strength (kT); "
-                         "FP64 form only (use with --precision fp64)")
+                    help="Hertz colloid-depletant interaction of this strength (kT), "
+                         "in either form")
     ap.add_argument("--no-shell", action="store_true",
                     help="skip the shell-V_0 measurement beside the headline")
     ap.add_argument("--cpu-sweeps-shape", type=int, default=3)
@@ -873,8 +873,6 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.soft and args.precision != "fp64":
-        ap.error("--soft needs --precision fp64")
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank)

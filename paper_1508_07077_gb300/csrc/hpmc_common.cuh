@@ -161,7 +161,12 @@ struct Rep {
     // (1..kShellLevels) samples R_in <= |e| < R_s with R_in = sh_rin[k-1],
     // thickness sh_h[k-1]; its Poisson table is the (k-1)-th block of nF
     // entries at t_off
-    double soft_eps;       // > 0: Hertz colloid-depletant interaction (eps in kT), FP64 form
+    double soft_eps;       // > 0: Hertz colloid-depletant interaction (eps in kT)
+    // FP32 form of the soft interaction: each depletant's two early exits
+    // (r_new >= r_old; u01(w_3) >= e^-u_old - e^-u_new) taken in FP32 when
+    // clear of the bands, the full FP64 statement otherwise
+    int soft32;
+    float soft_eps32, soft_inv_s32, soft_r2band, soft_vband;
     int v0_shell;
     int v0_cube;           // V_0 is the cube [-R_s, R_s)^3: every attempt is a depletant
     double dd;             // level thickness step sqrt(3) d_max / 32
@@ -437,6 +442,28 @@ __device__ __forceinline__ int stencil_cell(const Rep &R, int t, int cx, int cy,
 // serialization may start before its predecessor finishes): let the next
 // kernel in the stream launch early, and wait for the predecessor's
 // completion (and the visibility of its writes) before touching its results.
+// --- FP32 helpers of the certified forms ---------------------------------
+
+// R * s11(w) in FP32 without an integer-to-float conversion: the float with
+// exponent of 2 and the top 23 bits of w as mantissa lies in [2, 4), so
+// f - 3 = -1 + (w >> 9) 2^-22 exactly, within 2^-22 below s11(w); one more
+// rounding for the product.  |result - R s11(w)| <= 6 u R (u = 2^-24).
+__device__ __forceinline__ float coord32(uint32_t w, float R)
+{
+    return (__int_as_float(0x40000000u | (w >> 9)) - 3.0f) * R;
+}
+
+__device__ __forceinline__ float norm2f(float a, float b, float c)
+{
+    return __fmaf_rn(a, a, __fmaf_rn(b, b, c * c));
+}
+
+// 1: r2 < T certainly, 0: r2 >= T certainly, -1: inside the margin
+__device__ __forceinline__ int tri(float r2, float T, float m)
+{
+    return r2 < T - m ? 1 : (r2 > T + m ? 0 : -1);
+}
+
 // (one thread) The factors of a CB pass in ascending slot order, i.e.
 // ascending depletant index: bit l of masks[w] marks slot 32 w + l as holding
 // a factor; kc[slot] is its depletant index k (factor f[slot], nonzero) or

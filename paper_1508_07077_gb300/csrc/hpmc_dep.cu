@@ -283,12 +283,40 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
     R.half_nc = nc / 2;
     R.n_stencil = nc == 2 ? 2 : 3;
     R.nF = R.v0_shell ? shell_stride : (int)F.size();
-    // soft colloid-depletant interaction: spheres, FP64 form, no CB, a V_0
-    // that holds the new circumsphere
-    if (p.soft_eps > 0.0 && (p.shape != HPMC_SPHERE || c->precision != HPMC_FP64 ||
-                             h.n_trial != 0 || p.v0_mode == HPMC_V0_SHELL))
+    // soft colloid-depletant interaction: spheres, no CB, a V_0 that holds
+    // the new circumsphere
+    if (p.soft_eps > 0.0 && (p.shape != HPMC_SPHERE || h.n_trial != 0 || p.v0_mode == HPMC_V0_SHELL))
         return HPMC_ERR_ARG;
     R.soft_eps = p.soft_eps;
+    R.soft32 = (p.soft_eps > 0.0 && c->precision == HPMC_FP32_RECHECK) ? 1 : 0;
+    if (R.soft32) {
+        // FP32 bands (u = 2^-24).  A point's FP32 coordinates err by <= 6u R_s
+        // each and the displacement's FP32 image by u |o|; a difference adds
+        // u (R_s + |o|).  Vectors therefore err by Ev <= sqrt(3) (6u R_s +
+        // 2u (R_s + |o|)), and a squared length r^2 <= Rm^2 (Rm = R_s + |o|)
+        // by 2 Rm Ev + Ev^2 + 3u Rm^2; r_new >= r_old is certain when
+        // r2n32 - r2o32 exceeds twice that plus the subtraction's u Rm^2.
+        // A length errs by dr <= Ev + 4u Rm (the norm is 1-Lipschitz), so
+        // t = 1 - r / s by dt <= dr / s + 4u and u(r) = eps t^(5/2) by
+        // du <= eps (5/2 dt + 6u); expf errs by <= 2 ulp (CUDA's bound) and
+        // e^-u is 1-Lipschitz for u >= 0, so each e^-u by <= 2^-22 + du, the
+        // difference of two by twice that plus u, and u01(w) in FP32 by
+        // u + 2^-33: u01 >= e_old - e_new is certain beyond their sum.  The
+        // FP64 statements' own rounding is below 1e-12 eps.  A margin set by
+        // the caller widens both bands (1 sends every point to FP64).
+        const double u = 0x1p-24;
+        const double om = std::sqrt(3.0) * h.d_max, Rm = R_s + om;
+        const double Ev = std::sqrt(3.0) * (6.0 * u * R_s + 2.0 * u * Rm);
+        const double r2err = 2.0 * Rm * Ev + Ev * Ev + 3.0 * u * Rm * Rm;
+        const double dt = (Ev + 4.0 * u * Rm) / R_s + 4.0 * u;
+        const double du = p.soft_eps * (2.5 * dt + 6.0 * u) + 1e-12 * p.soft_eps;
+        const double eE = 0x1p-22 + du + 1e-12;
+        const double extra = p.margin > 0.0 ? p.margin : 0.0;
+        R.soft_eps32 = (float)p.soft_eps;
+        R.soft_inv_s32 = (float)(1.0 / R_s);
+        R.soft_r2band = (float)(2.0 * (2.0 * r2err + u * Rm * Rm) + extra);
+        R.soft_vband = (float)(2.0 * (2.0 * eE + u + u + 0x1p-33) + extra);
+    }
     R.v0_cube = p.v0_mode == HPMC_V0_CUBE ? 1 : 0;
     R.has_dep = lambda > 0.0 ? 1 : 0;
     R.n_trial = h.n_trial;
@@ -496,6 +524,13 @@ void launch_pdl1(K kernel, int grid, int block, cudaStream_t s, const SimParams 
     cudaLaunchKernelEx(&cfg, kernel, P);
 }
 
+// The FP32 form of the soft interaction runs the one-kernel phases (no lens
+// lists: a soft depletant's fate depends on the neighbours' energies).
+bool soft32_form(const hpmc_ctx *c)
+{
+    return c->precision == HPMC_FP32_RECHECK && c->prm.soft_eps > 0.0;
+}
+
 template <int CAP>
 void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
 {
@@ -517,7 +552,7 @@ void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s
                 else launch_pdl(k_phase_aniso_fp32<false, false, CAP>, c->n_cta, threads, dyn, s, P, phase);
             }
         }
-    } else if (c->precision == HPMC_FP32_RECHECK) {
+    } else if (c->precision == HPMC_FP32_RECHECK && !soft32_form(c)) {
         const bool warp = threads == 32;
         if (cb) {
             if (warp) launch_pdl(k_phase_sphere_fp32<true, true, CAP>, c->n_cta, threads, dyn, s, P, phase);
@@ -543,7 +578,7 @@ void launch_phase(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
 
 void launch_lens(hpmc_ctx *c, const SimParams &P, cudaStream_t s)
 {
-    if (c->precision != HPMC_FP32_RECHECK) return;
+    if (c->precision != HPMC_FP32_RECHECK || soft32_form(c)) return;
     if (c->prm.shape == HPMC_SPHERE) {
         if (c->prm.v0_mode == HPMC_V0_SHELL)
             launch_pdl1(k_lens_shell_fp32, (c->n_total + 127) / 128, 128, s, P);

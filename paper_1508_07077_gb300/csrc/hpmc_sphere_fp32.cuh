@@ -14,26 +14,6 @@
 
 namespace hpmc {
 
-// R * s11(w) in FP32 without an integer-to-float conversion: the float with
-// exponent of 2 and the top 23 bits of w as mantissa lies in [2, 4), so
-// f - 3 = -1 + (w >> 9) 2^-22 exactly, within 2^-22 below s11(w); one more
-// rounding for the product.  |result - R s11(w)| <= 6 u R (u = 2^-24).
-__device__ __forceinline__ float coord32(uint32_t w, float R)
-{
-    return (__int_as_float(0x40000000u | (w >> 9)) - 3.0f) * R;
-}
-
-__device__ __forceinline__ float norm2f(float a, float b, float c)
-{
-    return __fmaf_rn(a, a, __fmaf_rn(b, b, c * c));
-}
-
-// 1: r2 < T certainly, 0: r2 >= T certainly, -1: inside the margin
-__device__ __forceinline__ int tri(float r2, float T, float m)
-{
-    return r2 < T - m ? 1 : (r2 > T + m ? 0 : -1);
-}
-
 // --- exact FP64 re-takes, as the specification states them -----------------
 //
 // They run rarely and out of line (behind warp votes), and recompute what
