@@ -167,6 +167,9 @@ struct Rep {
     // clear of the bands, the full FP64 statement otherwise
     int soft32;
     float soft_eps32, soft_inv_s32, soft_r2band, soft_vband;
+    // and the colour phases' blocking test: band soft_bband + U-dependent
+    // terms (soft_du_nb per neighbour in range, relative u per term of U)
+    float soft_du_nb, soft_bband;
     int v0_shell;
     int v0_cube;           // V_0 is the cube [-R_s, R_s)^3: every attempt is a depletant
     double dd;             // level thickness step sqrt(3) d_max / 32

@@ -306,7 +306,8 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
         // the caller widens both bands (1 sends every point to FP64).
         const double u = 0x1p-24;
         const double om = std::sqrt(3.0) * h.d_max, Rm = R_s + om;
-        const double Ev = std::sqrt(3.0) * (6.0 * u * R_s + 2.0 * u * Rm);
+        // (the displacement's FP32 image is bit-built: <= 6u d_max more)
+        const double Ev = std::sqrt(3.0) * (6.0 * u * R_s + 7.0 * u * h.d_max + 2.0 * u * Rm);
         const double r2err = 2.0 * Rm * Ev + Ev * Ev + 3.0 * u * Rm * Rm;
         const double dt = (Ev + 4.0 * u * Rm) / R_s + 4.0 * u;
         const double du = p.soft_eps * (2.5 * dt + 6.0 * u) + 1e-12 * p.soft_eps;
@@ -316,6 +317,17 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
         R.soft_inv_s32 = (float)(1.0 / R_s);
         R.soft_r2band = (float)(2.0 * (2.0 * r2err + u * Rm * Rm) + extra);
         R.soft_vband = (float)(2.0 * (2.0 * eE + u + u + 0x1p-33) + extra);
+        // the colour phases' test u01 < e^-U (e^-u_old - e^-u_new): a
+        // neighbour's offset from the point errs by <= sqrt(3) (E + 6u R_s)
+        // (E: the cell-relative budget of the certified form), so its energy
+        // by du_nb = eps (2.5 dt_nb + 6u); U (n terms in range) by n du_nb plus
+        // n u U for the sum, e^-U by 2^-22 plus that; the product with the
+        // difference d (its bound above) adds u.  The band is twice the sum
+        // (n counted per point), plus the caller's margin.
+        const double Enb = std::sqrt(3.0) * (40.0 * u * (w > 1.0 ? w : 1.0) + 6.0 * u * R_s);
+        const double dt_nb = (Enb + 4.0 * u * 2.0 * R_s) / R_s + 4.0 * u;
+        R.soft_du_nb = (float)(2.0 * (p.soft_eps * (2.5 * dt_nb + 6.0 * u) + 1e-12 * p.soft_eps));
+        R.soft_bband = (float)(2.0 * (2.0 * eE + 0x1p-22 + 3.0 * u + 0x1p-33) + extra);
     }
     R.v0_cube = p.v0_mode == HPMC_V0_CUBE ? 1 : 0;
     R.has_dep = lambda > 0.0 ? 1 : 0;
@@ -524,13 +536,6 @@ void launch_pdl1(K kernel, int grid, int block, cudaStream_t s, const SimParams 
     cudaLaunchKernelEx(&cfg, kernel, P);
 }
 
-// The FP32 form of the soft interaction runs the one-kernel phases (no lens
-// lists: a soft depletant's fate depends on the neighbours' energies).
-bool soft32_form(const hpmc_ctx *c)
-{
-    return c->precision == HPMC_FP32_RECHECK && c->prm.soft_eps > 0.0;
-}
-
 template <int CAP>
 void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
 {
@@ -552,11 +557,14 @@ void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s
                 else launch_pdl(k_phase_aniso_fp32<false, false, CAP>, c->n_cta, threads, dyn, s, P, phase);
             }
         }
-    } else if (c->precision == HPMC_FP32_RECHECK && !soft32_form(c)) {
+    } else if (c->precision == HPMC_FP32_RECHECK) {
         const bool warp = threads == 32;
         if (cb) {
             if (warp) launch_pdl(k_phase_sphere_fp32<true, true, CAP>, c->n_cta, threads, dyn, s, P, phase);
             else launch_pdl(k_phase_sphere_fp32<true, false, CAP>, c->n_cta, threads, dyn, s, P, phase);
+        } else if (c->prm.soft_eps > 0.0) {
+            if (warp) launch_pdl(k_phase_sphere_fp32<false, true, CAP, true>, c->n_cta, threads, dyn, s, P, phase);
+            else launch_pdl(k_phase_sphere_fp32<false, false, CAP, true>, c->n_cta, threads, dyn, s, P, phase);
         } else {
             if (warp) launch_pdl(k_phase_sphere_fp32<false, true, CAP>, c->n_cta, threads, dyn, s, P, phase);
             else launch_pdl(k_phase_sphere_fp32<false, false, CAP>, c->n_cta, threads, dyn, s, P, phase);
@@ -578,10 +586,14 @@ void launch_phase(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
 
 void launch_lens(hpmc_ctx *c, const SimParams &P, cudaStream_t s)
 {
-    if (c->precision != HPMC_FP32_RECHECK || soft32_form(c)) return;
+    if (c->precision != HPMC_FP32_RECHECK) return;
     if (c->prm.shape == HPMC_SPHERE) {
         if (c->prm.v0_mode == HPMC_V0_SHELL)
             launch_pdl1(k_lens_shell_fp32, (c->n_total + 127) / 128, 128, s, P);
+        else if (c->prm.soft_eps > 0.0 && c->prm.v0_mode == HPMC_V0_CUBE)
+            launch_pdl1(k_lens_sphere_fp32<2, true>, (c->n_total + 3) / 4, 128, s, P);
+        else if (c->prm.soft_eps > 0.0)
+            launch_pdl1(k_lens_sphere_fp32<0, true>, (c->n_total + 3) / 4, 128, s, P);
         else if (c->prm.v0_mode == HPMC_V0_CUBE)
             launch_pdl1(k_lens_sphere_fp32<2>, (c->n_total + 3) / 4, 128, s, P);
         else

@@ -163,6 +163,92 @@ __device__ __noinline__ bool exact_free_nb(const SimParams &P, const Rep &R, uin
     return true;
 }
 
+// Soft interaction, FP32 form.  hertz32: u(r) = eps (1 - r/s)^(5/2) from r^2
+// in FP32.  soft_may_block32: false when the point (FP32 image e,
+// displacement image o = old - new, attempt word w) certainly does not
+// block, by either of the FP64 statement's early exits (r_new >= r_old;
+// u01(w_3) >= e^-u_old - e^-u_new) taken outside the bands derived with the
+// Rep; true when it may (the lens keeps it).
+__device__ __forceinline__ float hertz32(const Rep &R, float r2)
+{
+    const float t = 1.0f - __fsqrt_rn(r2) * R.soft_inv_s32;
+    return t > 0.0f ? R.soft_eps32 * ((t * t) * __fsqrt_rn(t)) : 0.0f;
+}
+
+__device__ __forceinline__ bool soft_may_block32(const Rep &R, uint32_t w3, float e0, float e1, float e2,
+                                                 float o0, float o1, float o2)
+{
+    const float r2n = norm2f(e0, e1, e2);
+    const float r2o = norm2f(e0 - o0, e1 - o1, e2 - o2);
+    if (r2n - r2o > R.soft_r2band) return false;
+    const float d = expf(-hertz32(R, r2o)) - expf(-hertz32(R, r2n));
+    const float v = __uint2float_rn(w3) * 0x1p-32f;
+    return !(v - d > R.soft_vband);
+}
+
+// Soft interaction: the FP64 statement for lens point t of colloid i's
+// move (the FP32 test was inside its band): the early exits, then the other
+// colloids' energies at the point summed in ascending index (nb: the
+// neighbours within reach, any order; those out of range add 0), then
+// u01(w_3) < e^-U (e^-u_old - e^-u_new).
+__device__ __noinline__ bool exact_soft_nb(const SimParams &P, const Rep &R, uint32_t sweep, int i, uint32_t t,
+                                           const float4 *nb, int nnb, const int *acc, int nacc)
+{
+    const uint4 w = draw(R.key0, R.key1, sweep, (uint32_t)(i - R.off), kPDep, 0, t);
+    const double e0 = R.R_s * s11(w.x), e1 = R.R_s * s11(w.y), e2 = R.R_s * s11(w.z);
+    const Move64 m = move64(P, R, sweep, i);
+    const double u0 = e0 - m.o0, u1 = e1 - m.o1, u2 = e2 - m.o2;
+    const double r2n = norm2(e0, e1, e2), r2o = norm2(u0, u1, u2);
+    if (!(r2n < r2o)) return false;
+    const double e_new = exp_neg_spec(hertz_spec(R, r2n));
+    const double e_old = exp_neg_spec(hertz_spec(R, r2o));
+    if (!(e_old > e_new)) return false;
+    const double v = u01(w.w);
+    if (!(v < e_old - e_new)) return false;
+    double U = 0.0;
+    int last = -1;
+    for (int a = 0; a < nnb; ++a) {
+        int j = 0x7FFFFFFF;   // the next index in ascending order
+        for (int b = 0; b < nnb; ++b) {
+            const int jb = __float_as_int(nb[b].w);
+            if (jb > last && jb < j) j = jb;
+        }
+        last = j;
+        double c0, c1, c2;
+        center64(P, R, m, pos_now(P, R, sweep, j, acc, nacc), c0, c1, c2);
+        U = U + hertz_spec(R, norm2(e0 - c0, e1 - c1, e2 - c2));
+    }
+    return v < exp_neg_spec(U) * (e_old - e_new);
+}
+
+// Soft interaction in FP32: does lens point t (FP32 point e relative to the
+// new position, displacement image o = old - new) block?  1 certainly, 0
+// certainly not, -1 inside the band (the FP64 statement decides).  nb: the
+// neighbours' FP32 offsets from the new position.
+__device__ __forceinline__ int soft_cls32(const Rep &R, uint32_t sweep, uint32_t tag, uint32_t t, float e0,
+                                          float e1, float e2, float o0, float o1, float o2,
+                                          const float4 *nb, int nnb)
+{
+    float U = 0.0f;
+    int n_in = 0;
+    const float reach = R.T_s32 * 1.001f;
+    for (int b = 0; b < nnb; ++b) {
+        const float4 d = nb[b];
+        const float r2 = norm2f(e0 - d.x, e1 - d.y, e2 - d.z);
+        if (r2 < reach) {
+            ++n_in;
+            U += hertz32(R, r2);
+        }
+    }
+    const float dd = expf(-hertz32(R, norm2f(e0 - o0, e1 - o1, e2 - o2))) -
+                     expf(-hertz32(R, norm2f(e0, e1, e2)));
+    const uint4 w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, t);
+    const float v = __uint2float_rn(w.w) * 0x1p-32f;
+    const float b = expf(-U) * dd;
+    const float band = R.soft_bband + 2.0f * (float)n_in * (R.soft_du_nb + 0x1p-24f * U);
+    return v < b - band ? 1 : (v > b + band ? 0 : -1);
+}
+
 // Shell attempt decided in FP64 (the FP32 test was inside its margin):
 // returns acceptance and the point rounded to float.
 __device__ __noinline__ bool exact_shell_pt(const Rep &R, int lvl, uint4 w, float &e0, float &e1, float &e2)
@@ -391,8 +477,10 @@ __device__ __forceinline__ bool cb_pass(DepShared &sh, int tid, int nslots, bool
 // displacement to *mv (lane 0), and the lens points, in depletant order, to
 // sdst[slot] for slot < room and to gdst[slot] beyond (gdst is the move's
 // list of capacity lens_cap).  Returns (N_p, depletants obtained from the
-// stream, lens points, FP64 re-takes), the same in every lane.
-template <int V0>
+// stream, lens points, FP64 re-takes), the same in every lane.  SOFT: the
+// soft interaction keeps the points neither of whose early exits is certain
+// in FP32 (instead of those outside the old pose).
+template <int V0, bool SOFT>
 __device__ __forceinline__ int4 lens_of_move(const SimParams &P, const Rep &R, int g, uint32_t sweep, float4 *mv,
                                           float4 *sdst, int room, float4 *gdst)
 {
@@ -452,18 +540,25 @@ __device__ __forceinline__ int4 lens_of_move(const SimParams &P, const Rep &R, i
             }
             dep = dep && tn == 1;
         }
-        int to = 1;  // overlaps the old pose: 1 yes, 0 no, -1 within the margin
-        if (dep) to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), R.T_dep32, R.m_r2);
-        {
-            const bool unsure = to == -1;
-            if (__any_sync(kFull, unsure)) {
-                if (unsure) {
-                    ++rck;
-                    to = exact_dep(P, R, sweep, i, w, 0, 0, nullptr, 0) ? 1 : 0;
+        bool lens;
+        if (SOFT) {
+            // soft: the points that may block (neither early exit of the
+            // FP64 statement certain in FP32); the phases decide them
+            lens = dep && soft_may_block32(R, w.w, e0, e1, e2, o0, o1, o2);
+        } else {
+            int to = 1;  // overlaps the old pose: 1 yes, 0 no, -1 within the margin
+            if (dep) to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), R.T_dep32, R.m_r2);
+            {
+                const bool unsure = to == -1;
+                if (__any_sync(kFull, unsure)) {
+                    if (unsure) {
+                        ++rck;
+                        to = exact_dep(P, R, sweep, i, w, 0, 0, nullptr, 0) ? 1 : 0;
+                    }
                 }
             }
+            lens = dep && to == 0;
         }
-        const bool lens = dep && to == 0;
         const unsigned lb = __ballot_sync(kFull, lens);
         const int slot = m + __popc(lb & lt);
         if (lens) {
@@ -483,7 +578,7 @@ __device__ __forceinline__ int4 lens_of_move(const SimParams &P, const Rep &R, i
 // The lens lists of all moves of the sweep, one warp per colloid, filed under
 // the colloids' bin slots (used when the colour phases do not build them
 // themselves).
-template <int V0>
+template <int V0, bool SOFT = false>
 __global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_constant__ SimParams P)
 {
     __shared__ float4 s_mv[4];
@@ -501,7 +596,7 @@ __global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_consta
     if (g - R.off >= P.n_live[r]) return;   // a slot not in use (Gibbs pair)
     const uint32_t sweep = (uint32_t)(*P.sweep);
     float4 *out = P.lens + (size_t)g * P.lens_cap;
-    const int4 h = lens_of_move<V0>(P, R, g, sweep, &s_mv[wl], nullptr, 0, out);
+    const int4 h = lens_of_move<V0, SOFT>(P, R, g, sweep, &s_mv[wl], nullptr, 0, out);
     // file the header, the displacement and the first lens points under the
     // colloid's bin slot, where the colour phase reads them with the cell list
     __syncwarp();
@@ -642,7 +737,7 @@ __device__ __forceinline__ bool cta_any(bool p)
 // off.  WARP: the CTA is a single warp (barriers become warp operations).
 // CAP: capacity of a cell bin (the cell list's stride).
 // ---------------------------------------------------------------------------
-template <bool CB, bool WARP, int CAP>
+template <bool CB, bool WARP, int CAP, bool SOFT = false>
 __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32) : 1)
     k_phase_sphere_fp32(const __grid_constant__ SimParams P, int phase)
 {
@@ -945,7 +1040,14 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
                 const int m = m0 + tid;
                 int cls = 0, kk = 0x7FFFFFFF;
                 uint32_t tt = 0;
-                if (m < n_lens) {
+                if (SOFT && m < n_lens) {
+                    const float4 Lm = lens[m];
+                    const uint32_t tk = (uint32_t)__float_as_int(Lm.w);
+                    kk = (int)(tk & 0xFFFFu);
+                    tt = tk >> 16;
+                    cls = soft_cls32(R, sweep, (uint32_t)(i - R.off), tt, Lm.x, Lm.y, Lm.z, -mv.x, -mv.y,
+                                     -mv.z, s_nb, nnb);
+                } else if (!SOFT && m < n_lens) {
                     const float4 Lm = lens[m];
                     const uint32_t tk = (uint32_t)__float_as_int(Lm.w);
                     kk = (int)(tk & 0xFFFFu);
@@ -968,7 +1070,9 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32)
                     if (__any_sync(kFull, unsure)) {
                         if (unsure) {
                             ++o.rck;
-                            cls = exact_free_nb(P, R, sweep, i, tt, s_nb, nnb, s_accl, nacc) ? 1 : 0;
+                            cls = (SOFT ? exact_soft_nb(P, R, sweep, i, tt, s_nb, nnb, s_accl, nacc)
+                                        : exact_free_nb(P, R, sweep, i, tt, s_nb, nnb, s_accl, nacc))
+                                      ? 1 : 0;
                         }
                     }
                 }

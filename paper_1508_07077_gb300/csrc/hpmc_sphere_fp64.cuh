@@ -84,28 +84,6 @@ __device__ __noinline__ bool soft_blocks(const Rep &R, uint4 w, double e0, doubl
     return v < b;
 }
 
-// FP32 form of the soft interaction: false when the point (FP32 image e,
-// displacement image o, attempt word w) certainly does not block, by either
-// of the FP64 statement's early exits (r_new >= r_old; u01(w_3) >= e^-u_old -
-// e^-u_new), decided outside the bands derived with the Rep; true when the
-// FP64 statement must decide.
-__device__ __forceinline__ float hertz32(const Rep &R, float r2)
-{
-    const float t = 1.0f - __fsqrt_rn(r2) * R.soft_inv_s32;
-    return t > 0.0f ? R.soft_eps32 * ((t * t) * __fsqrt_rn(t)) : 0.0f;
-}
-
-__device__ __forceinline__ bool soft_may_block32(const Rep &R, uint32_t w3, float e0, float e1, float e2,
-                                                 float o0, float o1, float o2)
-{
-    const float r2n = norm2f(e0, e1, e2);
-    const float r2o = norm2f(e0 - o0, e1 - o1, e2 - o2);
-    if (r2n - r2o > R.soft_r2band) return false;
-    const float d = expf(-hertz32(R, r2o)) - expf(-hertz32(R, r2n));
-    const float v = __uint2float_rn(w3) * 0x1p-32f;
-    return !(v - d > R.soft_vband);
-}
-
 struct CbResult {
     double f;
     uint32_t fwd_ok, rev_ok, caps;
@@ -302,28 +280,12 @@ __global__ void __launch_bounds__(kMaxThreads)
             while (k0 < n_p && t0 < t_max) {
                 const uint32_t t = t0 + (uint32_t)tid;
                 double e0 = 0.0, e1 = 0.0, e2 = 0.0;
-                float f0 = 0.f, f1 = 0.f, f2 = 0.f;
                 bool inside = false;
                 uint4 w = make_uint4(0, 0, 0, 0);
                 if (t < t_max) {
                     w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, t);
                     if (lvl > 0) {
                         inside = shell_point64(R, lvl, w, e0, e1, e2);
-                    } else if (R.soft32) {
-                        // FP32 image of the point and its ball test (FP64
-                        // coordinates only where the FP64 statement runs)
-                        f0 = coord32(w.x, R.R_s32);
-                        f1 = coord32(w.y, R.R_s32);
-                        f2 = coord32(w.z, R.R_s32);
-                        int in = R.v0_cube ? 1 : tri(norm2f(f0, f1, f2), R.T_s32, R.m_r2);
-                        if (in == -1) {
-                            ++cnt[kRechecks];
-                            e0 = R.R_s * s11(w.x);
-                            e1 = R.R_s * s11(w.y);
-                            e2 = R.R_s * s11(w.z);
-                            in = norm2(e0, e1, e2) < R.R_s2 ? 1 : 0;
-                        }
-                        inside = in != 0;
                     } else {
                         e0 = R.R_s * s11(w.x);
                         e1 = R.R_s * s11(w.y);
@@ -345,15 +307,7 @@ __global__ void __launch_bounds__(kMaxThreads)
                 if (inside && k < n_p) {
                     if (R.soft_eps > 0.0) {
                         // soft: blocks with probability e^-U_others (e^-u_old - e^-u_new)
-                        if (!R.soft32) {
-                            blocking = soft_blocks(R, w, e0, e1, e2, o0, o1, o2, s_nb, nnb);
-                        } else if (soft_may_block32(R, w.w, f0, f1, f2, (float)o0, (float)o1, (float)o2)) {
-                            ++cnt[kRechecks];   // the FP64 statement decides
-                            e0 = R.R_s * s11(w.x);
-                            e1 = R.R_s * s11(w.y);
-                            e2 = R.R_s * s11(w.z);
-                            blocking = soft_blocks(R, w, e0, e1, e2, o0, o1, o2, s_nb, nnb);
-                        }
+                        blocking = soft_blocks(R, w, e0, e1, e2, o0, o1, o2, s_nb, nnb);
                     } else if (SphereFP64::dep(R, e0, e1, e2) &&
                                !SphereFP64::dep(R, e0 - o0, e1 - o1, e2 - o2) &&
                                free_of_nb_fp64(R, e0, e1, e2, s_nb, nnb)) {
@@ -448,12 +402,11 @@ __global__ void __launch_bounds__(kMaxThreads)
         __syncthreads();
     }
 
-    // thread 0 holds the CTA's move counters; every thread its own CB, cap and
-    // FP64 re-take counts
+    // thread 0 holds the CTA's move counters; every thread its own CB/cap counts
     if (tid != 0) {
 #pragma unroll
         for (int k = 0; k < kNumCounters; ++k)
-            if (k != kCbFwdOk && k != kCbRevOk && k != kCapHits && k != kRechecks) cnt[k] = 0;
+            if (k != kCbFwdOk && k != kCbRevOk && k != kCapHits) cnt[k] = 0;
     }
     flush_counters(P, r, cnt);
 }
