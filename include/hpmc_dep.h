@@ -218,8 +218,9 @@ int hpmc_set_v0(hpmc_ctx *ctx, int mode);
  * degree-14 Taylor polynomial, the same bits on every side).  Spheres,
  * n_trial = 0 and the circumsphere or cube V_0 (HPMC_ERR_ARG at the next
  * sweep otherwise); both forms (HPMC_FP32_RECHECK takes each depletant's two
- * early exits, r_new >= r_old and u01 >= e^(-u_old) - e^(-u_new), in FP32
- * outside certified bands and the rest in FP64).  eps = 0 (default): hard. */
+ * early exits, r_new >= r_old and u01 >= e^(-u_old) - e^(-u_new), and its
+ * blocking test in FP32 outside certified bands, the FP64 statement inside
+ * them: the same decisions).  eps = 0 (default): hard. */
 int hpmc_set_soft(hpmc_ctx *ctx, double eps);
 
 /* Colloids in use.  Replica r keeps its colloids in its slots 0..n_live-1

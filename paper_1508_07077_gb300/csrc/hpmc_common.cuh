@@ -163,8 +163,9 @@ struct Rep {
     // entries at t_off
     double soft_eps;       // > 0: Hertz colloid-depletant interaction (eps in kT)
     // FP32 form of the soft interaction: each depletant's two early exits
-    // (r_new >= r_old; u01(w_3) >= e^-u_old - e^-u_new) taken in FP32 when
-    // clear of the bands, the full FP64 statement otherwise
+    // (r_new >= r_old; u01(w_3) >= e^-u_old - e^-u_new, in the lens kernel)
+    // and its blocking test (in the phases) taken in FP32 when clear of the
+    // bands, the full FP64 statement otherwise
     int soft32;
     float soft_eps32, soft_inv_s32, soft_r2band, soft_vband;
     // and the colour phases' blocking test: band soft_bband + U-dependent
