@@ -738,7 +738,7 @@ __device__ __forceinline__ bool cta_any(bool p)
 // CAP: capacity of a cell bin (the cell list's stride).
 // ---------------------------------------------------------------------------
 template <bool CB, bool WARP, int CAP, bool SOFT = false>
-__global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? (CB ? 16 : 32) : 1)
+__global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? ((CB || SOFT) ? 16 : 32) : 1)
     k_phase_sphere_fp32(const __grid_constant__ SimParams P, int phase)
 {
     __shared__ float4 s_cpos[cand_cap(CAP)];  // candidates relative to this cell's origin; index in .w
