@@ -58,8 +58,10 @@ OPS_PER_MOVE = 2 * 40.0 + 20.0 + 12.0 + 25 * 8.0
 ISSUE_LANES_PER_SM = 128        # 4 SM sub-partitions x 32 lanes, one instruction / clock
 BYTES_PER_MOVE = 2 * 32 + 16 + 2 * 4   # pos (double4) read + cell-local copy + cell list ids
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel
-# build on the four-state-point 16384-sphere batch (profiles/k_phase_sphere_fp32_*.md).
-MEASURED_TRAFFIC = {"k_phase_sphere_fp32": 10.20e6, "k_lens_sphere_fp32": 2.50e6}
+# build on the four-state-point 16384-sphere batch, in the timed steps' conditions
+# (ncu --cache-control none; the mean over the 8 phases of a sweep that starts
+# after the 256 MB L2 flush; profiles/k_phase_sphere_fp32_*.md).
+MEASURED_TRAFFIC = {"k_phase_sphere_fp32": 5.44e6, "k_lens_sphere_fp32": 11.88e6}
 
 
 def _dist():
@@ -869,7 +871,7 @@ def main():
                     help="skip the shell-V_0 measurement beside the headline")
     ap.add_argument("--cpu-sweeps-shape", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sweeps", type=int, default=25)
+    ap.add_argument("--cpu-sweeps", type=int, default=40)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
