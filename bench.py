@@ -250,6 +250,18 @@ def run_batched(args, ws, rank, local):
         dist.barrier()
     ms = sum(x.elapsed_time(y) for x, y in zip(a, b))
     _, cnt = hpmc.hpmc_get_state(ctx)
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    host_pos = torch.empty((sum(ns), 3), dtype=torch.float64).pin_memory().numpy()
+    sweep_e, _ = hpmc.hpmc_get_state(ctx, host_pos)
+    e2e_steps = max(3, min(args.steps, 50) // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        hpmc.hpmc_set_state(ctx, host_pos, None, sweep_e + k, stream)
+        hpmc.hpmc_sweep(ctx, 1, stream)
+        hpmc.hpmc_get_state(ctx, host_pos, None, stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
     # one at a time
     allpos = np.empty((sum(ns), 3))
     sweep_now, _ = hpmc.hpmc_get_state(ctx, allpos)
@@ -276,7 +288,7 @@ def run_batched(args, ws, rank, local):
     for smp in singles:
         smp.close()
     # whole job: every rank's units over the slowest rank's time
-    ms, seq_ms = R.reduce_max([ms, seq_ms], "cuda")
+    ms, seq_ms, e2e_s = R.reduce_max([ms, seq_ms, e2e_s], "cuda")
     moves_all, drawn_all, eval_all = R.reduce_sum(
         [cnt["moves"], cnt["dep_drawn"], cnt["dep_evaluated"]], "cuda")
     if rank == 0:
@@ -291,6 +303,9 @@ def run_batched(args, ws, rank, local):
                        "step": "1 sweep of every replica, one batch (one set of launches)",
                        "l2": "flushed between steps (256 MB write)"},
             "one_at_a_time_moves_per_s": ws * seq_steps * sum(ns) / (seq_ms * 1e-3),
+            "e2e": {"value": ws * e2e_steps * sum(ns) / e2e_s, "unit": "moves/s",
+                    "h2d_bytes_per_step": int(host_pos.nbytes),
+                    "d2h_bytes_per_step": int(host_pos.nbytes)},
             "insertions_drawn_per_s": drawn_all / (ms * 1e-3),
             "insertions_evaluated_per_s": eval_all / (ms * 1e-3),
             "acceptance": cnt["accept"] / max(1, cnt["moves"]),
