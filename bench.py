@@ -356,6 +356,8 @@ def run_gibbs(args, ws, rank, local):
     pairs = [((a.pos, a.L), (b.pos, b.L), {"q": q, "n_r": a.n_r, "n_trial": n_trial,
                                            "d_max": 0.15}) for a, b in boxes]
     gp = hpmc.GibbsPairs(pairs, seed=1, precision=prec, device=local, replica0=base)
+    if args.warps != 1:
+        hpmc.hpmc_set_launch(gp.ctx, args.warps, 1)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         gp.cycle(1, n_ex, stream)
