@@ -320,10 +320,15 @@ int hpmc_cell_list(int n, double box_l, int n_cell, const double *pos_dev,
  * scratch is a file-scope device array of 1.25 MB that every GPU which loads
  * the library holds until the process exits.
  *   - Limits: n_cell <= 40 (n_cell^3 <= 65536 cells) and n <= 262144
- *     colloids; larger sizes return HPMC_ERR_CAP without doing anything.
+ *     colloids; n_cell in 41..1024 or a larger n returns HPMC_ERR_CAP without
+ *     doing anything (n_cell > 1024, odd or < 2 is HPMC_ERR_ARG, as for
+ *     hpmc_cell_list).
  *   - The first call on a device looks up the array's device address for that
- *     device (cudaGetSymbolAddress, with the device current); make that first
- *     call before any stream capture on the device.
+ *     device (cudaGetSymbolAddress, with the device current) and keeps it for
+ *     the life of the process; make that first call before any stream capture
+ *     on the device.  cudaDeviceReset on that device invalidates the kept
+ *     address (the module is reloaded at another address): do not call this
+ *     entry point on a device after resetting it.
  *   - Every call on a device shares the one array, which keeps the last
  *     call's contents (the counts are cleared at the start of each call):
  *     calls whose work overlaps on the GPU (different streams, no ordering)
@@ -342,6 +347,19 @@ int hpmc_cell_list_noalloc(int n, double box_l, int n_cell, const double *pos_de
  * stream-ordered scratch on the context's own stream. */
 int hpmc_free_volume(hpmc_ctx *ctx, int replica, double q, uint64_t seed, uint32_t sample,
                      uint64_t n_probe, uint64_t *n_free);
+
+/* The library's own device Philox4x32-10 (Salmon, Moraes, Dror & Shaw,
+ * SC'11: the counter-based generator every random stream of the method draws
+ * from, the reading of the paper's unspecified random numbers) applied to n
+ * (counter, key) pairs, so that the device generator can be checked against
+ * the published known-answer vectors.  ctr_dev: n x 4 words, key_dev: n x 2
+ * words (k0, k1), out_dev: n x 4 words, all device memory owned by the
+ * caller.  variant 0: the rounds with the key bumped by the Weyl constants
+ * each round; 1: the same with the ten round keys precomputed (the form the
+ * depletant loops use).  Enqueued on `stream`; HPMC_ERR_ARG for n < 0, an
+ * unknown variant or a NULL buffer with n > 0. */
+int hpmc_philox(int n, const uint32_t *ctr_dev, const uint32_t *key_dev, uint32_t *out_dev,
+                int variant, void *stream);
 
 /* Colloid slots of the context (*n_total: the rows of the pos / quat
  * buffers of hpmc_get_state and hpmc_set_state) and replicas (*n_rep); either

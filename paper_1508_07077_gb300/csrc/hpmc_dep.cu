@@ -1619,6 +1619,17 @@ int hpmc_cell_list(int n, double box_l, int n_cell, const double *pos_dev, uint6
     return rc;
 }
 
+int hpmc_philox(int n, const uint32_t *ctr_dev, const uint32_t *key_dev, uint32_t *out_dev,
+                int variant, void *stream)
+{
+    if (n < 0 || (variant != 0 && variant != 1)) return HPMC_ERR_ARG;
+    if (n == 0) return HPMC_OK;
+    if (!ctr_dev || !key_dev || !out_dev) return HPMC_ERR_ARG;
+    k_philox<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(n, ctr_dev, key_dev, out_dev, variant);
+    CK(cudaGetLastError());
+    return HPMC_OK;
+}
+
 int hpmc_set_live(hpmc_ctx *c, int replica, int n_live)
 {
     if (!c || replica < 0 || replica >= (int)c->reps.size() || c->prm.shape != HPMC_SPHERE ||
@@ -1800,7 +1811,9 @@ int hpmc_cell_list_noalloc(int n, double box_l, int n_cell, const double *pos_de
                            uint32_t replica, uint64_t sweep, int *cell_start_dev,
                            int *cell_idx_dev, void *stream)
 {
-    if (n < 0 || !(box_l > 0.0) || n_cell < 2 || (n_cell & 1)) return HPMC_ERR_ARG;
+    // the same argument rules as hpmc_cell_list (n_cell > 1024 is invalid
+    // there too), then this entry point's own capacity
+    if (n < 0 || !(box_l > 0.0) || n_cell < 2 || (n_cell & 1) || n_cell > 1024) return HPMC_ERR_ARG;
     if (n > 0 && (!pos_dev || !cell_idx_dev)) return HPMC_ERR_ARG;
     if (!cell_start_dev) return HPMC_ERR_ARG;
     if (n_cell > 40 || n > kNoAllocMaxN) return HPMC_ERR_CAP;

@@ -72,4 +72,20 @@ __global__ void k_pack(int n, const double4 *pos, const double4 *quat, double *p
     }
 }
 
+// The device generator on n (counter, key) pairs, for known-answer tests:
+// variant 0 is philox4x32_10 (key bumped every round), 1 is philox_rk with the
+// ten round keys precomputed (the form the depletant loops use).
+__global__ void k_philox(int n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, int variant)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+    const uint32_t k0 = key[2 * i], k1 = key[2 * i + 1];
+    const uint4 w = variant == 0 ? philox4x32_10(c, k0, k1) : philox_rk(c, round_keys(k0, k1));
+    out[4 * i] = w.x;
+    out[4 * i + 1] = w.y;
+    out[4 * i + 2] = w.z;
+    out[4 * i + 3] = w.w;
+}
+
 }  // namespace hpmc

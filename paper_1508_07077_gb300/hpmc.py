@@ -30,7 +30,7 @@ EXPORTS = ("hpmc_init", "hpmc_init_batch", "hpmc_get_replica", "hpmc_set_replica
            "hpmc_get_gibbs", "hpmc_set_timing",
            "hpmc_get_timing", "hpmc_sweep", "hpmc_get_state",
            "hpmc_set_state", "hpmc_reset_counters", "hpmc_sync", "hpmc_cell_list",
-           "hpmc_cell_list_noalloc", "hpmc_free_volume", "hpmc_get_size", "hpmc_strerror",
+           "hpmc_cell_list_noalloc", "hpmc_philox", "hpmc_free_volume", "hpmc_get_size", "hpmc_strerror",
            "hpmc_destroy")
 
 
@@ -108,6 +108,7 @@ def load(path: str = LIB_PATH):
     L.hpmc_cell_list.argtypes = [ip, ctypes.c_double, ip, vp, ctypes.c_uint64,
                                  ctypes.c_uint32, ctypes.c_uint64, vp, vp, vp]
     L.hpmc_cell_list_noalloc.argtypes = L.hpmc_cell_list.argtypes
+    L.hpmc_philox.argtypes = [ip, vp, vp, vp, ip, vp]
     L.hpmc_free_volume.argtypes = [vp, ip, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
                                    ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
     L.hpmc_get_size.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
@@ -432,6 +433,20 @@ def hpmc_cell_list_noalloc(n, box_l, n_cell, pos_dev, seed, replica, sweep, cell
                                          int(seed), int(replica), int(sweep),
                                          cell_start_dev.data_ptr(), cell_idx_dev.data_ptr(),
                                          _stream(stream)), "hpmc_cell_list_noalloc")
+
+
+def hpmc_philox(ctr_dev, key_dev, out_dev, variant=0, stream=None):
+    """Device Philox4x32-10 of n counters (n x 4 int32 CUDA tensor) under n
+    keys (n x 2) into out_dev (n x 4); words are the tensors' bit patterns."""
+    n = int(ctr_dev.shape[0])
+    if tuple(ctr_dev.shape) != (n, 4) or tuple(key_dev.shape) != (n, 2) or \
+            tuple(out_dev.shape) != (n, 4):
+        raise ValueError("ctr, key, out must be n x 4, n x 2, n x 4")
+    for t in (ctr_dev, key_dev, out_dev):
+        if not t.is_cuda or not t.is_contiguous() or t.element_size() != 4:
+            raise ValueError("buffers must be contiguous 32-bit CUDA tensors")
+    _check(load().hpmc_philox(n, ctr_dev.data_ptr(), key_dev.data_ptr(), out_dev.data_ptr(),
+                              int(variant), _stream(stream)), "hpmc_philox")
 
 
 def hpmc_destroy(ctx):

@@ -72,3 +72,24 @@ def test_word_to_real_maps(oracle):
     assert oracle.u53(2 ** 32 - 1, 2 ** 32 - 1) == 1.0 - 2.0 ** -53
     assert oracle.u53(2 ** 5, 0) == 2.0 ** -27      # lowest kept bit of word 0
     assert oracle.u53(0, 2 ** 6) == 2.0 ** -53      # lowest kept bit of word 1
+
+
+def _kat():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "philox4x32_10_kat.json")
+    with open(path) as f:
+        vecs = json.load(f)["vectors"]
+    return [([int(x, 16) for x in v["ctr"]], [int(x, 16) for x in v["key"]],
+             [int(x, 16) for x in v["out"]]) for v in vecs]
+
+
+def test_known_answer_vectors(oracle):
+    """The published Philox4x32-10 known-answer vectors (zero, all-ones and
+    pi-digit counter/key): a wrong round count, multiplier, key schedule or
+    output permutation fails at least one of them."""
+    kat = _kat()
+    assert len(kat) == 3
+    for ctr, key, out in kat:
+        assert [int(x) for x in oracle.philox(ctr, key)] == out, (ctr, key)
