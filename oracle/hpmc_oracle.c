@@ -24,6 +24,14 @@
  *     reinserted (configurational bias) and the move is accepted with the
  *     product of per-depletant weights.
  *
+ * Threads (oracle_run_threads, n_threads > 1; OpenMP, -fopenmp): Sec. III.E
+ * makes the active cells of one colour independent (a colloid moves only
+ * inside its cell and interacts only with its 26 neighbour cells, none of
+ * which is active at the same time), so their trial moves may run in any
+ * order.  The cells of a colour phase are then handed out to threads; each
+ * thread keeps its own counters, summed at the end of the phase.  Positions
+ * and counters are identical to the serial run for every thread count.
+ *
  * Readings where the paper is silent (RNG, op order, sampling details) are the
  * ones listed in the design notes; every floating-point expression below is
  * written in the exact operation order that specification fixes, and must be
@@ -68,6 +76,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------------ */
 /* Counter-based RNG: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11).    */
@@ -1256,18 +1267,22 @@ static int sim_init(osim *S, int n, double L, int shape,
  * Run n_sweeps sweeps starting at sweep index sweep0, in place on pos (n x 3)
  * and quat (n x 4 or NULL).  counters: C_N uint64 accumulated.  If hist is
  * non-NULL, after every sweep all pair distances r < hist_rmax are binned into
- * hist[hist_bins] (minimum image).  Returns 0 or a negative error.
+ * hist[hist_bins] (minimum image).  n_threads > 1 moves the active cells of a
+ * colour on that many threads (identical results).  Returns 0 or a negative
+ * error.  oracle_run is the serial form.
  */
-int oracle_run(int n, double L, int shape, const double *shape_params,
-               int n_shape_params, double q, double n_r, int n_trial,
-               int cb_mode, int v0_mode, double soft_eps, double d_max, double a_max,
-               double p_translate, uint64_t seed, uint32_t replica, int n_cell, int brute_force,
-               double *pos, double *quat, uint64_t sweep0, int n_sweeps,
-               uint64_t *counters, int hist_bins, double hist_rmax,
-               uint64_t *hist)
+int oracle_run_threads(int n, double L, int shape, const double *shape_params,
+                       int n_shape_params, double q, double n_r, int n_trial,
+                       int cb_mode, int v0_mode, double soft_eps, double d_max, double a_max,
+                       double p_translate, uint64_t seed, uint32_t replica, int n_cell,
+                       int brute_force, double *pos, double *quat, uint64_t sweep0,
+                       int n_sweeps, uint64_t *counters, int hist_bins, double hist_rmax,
+                       uint64_t *hist, int n_threads)
 {
     osim S;
-    if (!pos || !counters || n_sweeps < 0) return -1;
+    if (!pos || !counters || n_sweeps < 0 || n_threads < 1) return -1;
+    /* brute-force neighbours read every colloid: only the serial order */
+    if (brute_force) n_threads = 1;
     if (sim_init(&S, n, L, shape, shape_params, n_shape_params, q, n_r, n_trial,
                  cb_mode, v0_mode, soft_eps, d_max, a_max, p_translate, seed, replica, n_cell,
                  brute_force) != 0)
@@ -1275,7 +1290,8 @@ int oracle_run(int n, double L, int shape, const double *shape_params,
     int ncell = S.nc * S.nc * S.nc;
     int *cell_start = (int *)malloc(sizeof(int) * (size_t)(ncell + 1));
     int *cell_idx = (int *)malloc(sizeof(int) * (size_t)n);
-    onb *nb = (onb *)malloc(sizeof(onb) * (size_t)n);
+    /* one neighbour buffer per thread */
+    onb *nb = (onb *)malloc(sizeof(onb) * (size_t)n * (size_t)n_threads);
     int rc = 0;
     if (!cell_start || !cell_idx || !nb) { rc = -1; goto out; }
 
@@ -1288,14 +1304,40 @@ int oracle_run(int n, double L, int shape, const double *shape_params,
                              cell_idx) != 0) { rc = -1; goto out; }
         for (int p = 0; p < 8; ++p) {
             int colour = perm[p];
-            for (int c = 0; c < ncell; ++c) {
-                int cx = c % S.nc, cy = (c / S.nc) % S.nc, cz = c / (S.nc * S.nc);
-                int col = (cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2);
-                if (col != colour) continue;
-                int ci[3] = {cx, cy, cz};
-                for (int s = cell_start[c]; s < cell_start[c + 1]; ++s)
-                    trial_move(&S, sweep, cell_idx[s], ci, sigma, pos, quat,
-                               cell_start, cell_idx, nb, counters);
+            if (n_threads == 1) {
+                for (int c = 0; c < ncell; ++c) {
+                    int cx = c % S.nc, cy = (c / S.nc) % S.nc, cz = c / (S.nc * S.nc);
+                    int col = (cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2);
+                    if (col != colour) continue;
+                    int ci[3] = {cx, cy, cz};
+                    for (int s = cell_start[c]; s < cell_start[c + 1]; ++s)
+                        trial_move(&S, sweep, cell_idx[s], ci, sigma, pos, quat,
+                                   cell_start, cell_idx, nb, counters);
+                }
+                continue;
+            }
+            /* the active cells of this colour over the threads (Sec. III.E) */
+#pragma omp parallel num_threads(n_threads)
+            {
+                int th = 0;
+#ifdef _OPENMP
+                th = omp_get_thread_num();
+#endif
+                onb *nbt = nb + (size_t)th * (size_t)n;
+                uint64_t ct[C_N];
+                memset(ct, 0, sizeof ct);
+#pragma omp for schedule(dynamic, 8)
+                for (int c = 0; c < ncell; ++c) {
+                    int cx = c % S.nc, cy = (c / S.nc) % S.nc, cz = c / (S.nc * S.nc);
+                    int col = (cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2);
+                    if (col != colour) continue;
+                    int ci[3] = {cx, cy, cz};
+                    for (int s = cell_start[c]; s < cell_start[c + 1]; ++s)
+                        trial_move(&S, sweep, cell_idx[s], ci, sigma, pos, quat,
+                                   cell_start, cell_idx, nbt, ct);
+                }
+#pragma omp critical
+                for (int k = 0; k < C_N; ++k) counters[k] += ct[k];
             }
         }
         if (hist && hist_bins > 0) {
@@ -1321,6 +1363,20 @@ out:
     free(cell_idx);
     free(nb);
     return rc;
+}
+
+int oracle_run(int n, double L, int shape, const double *shape_params,
+               int n_shape_params, double q, double n_r, int n_trial,
+               int cb_mode, int v0_mode, double soft_eps, double d_max, double a_max,
+               double p_translate, uint64_t seed, uint32_t replica, int n_cell, int brute_force,
+               double *pos, double *quat, uint64_t sweep0, int n_sweeps,
+               uint64_t *counters, int hist_bins, double hist_rmax,
+               uint64_t *hist)
+{
+    return oracle_run_threads(n, L, shape, shape_params, n_shape_params, q, n_r, n_trial,
+                              cb_mode, v0_mode, soft_eps, d_max, a_max, p_translate, seed,
+                              replica, n_cell, brute_force, pos, quat, sweep0, n_sweeps,
+                              counters, hist_bins, hist_rmax, hist, 1);
 }
 
 /*

@@ -47,7 +47,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
            "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
@@ -93,6 +93,8 @@ def lib():
                 dp, dp, ctypes.c_uint64, ctypes.c_int, u64p,
                 ctypes.c_int, ctypes.c_double, u64p]
             L.oracle_run.restype = ctypes.c_int
+            L.oracle_run_threads.argtypes = L.oracle_run.argtypes + [ctypes.c_int]
+            L.oracle_run_threads.restype = ctypes.c_int
             L.oracle_poisson_sample.argtypes = [dp, ctypes.c_int, ctypes.c_double]
             L.oracle_poisson_sample.restype = ctypes.c_int
             L.oracle_acceptance.argtypes = [
@@ -244,8 +246,9 @@ def cell_list(pos, L, nc, seed, replica, sweep):
 def run(pos, L, *, shape=SHAPE_SPHERE, shape_params=(1.0,), q=0.0, n_r=0.0,
         n_trial=0, cb_mode=0, v0_mode=0, soft_eps=0.0, d_max=0.1, a_max=0.0, p_translate=1.0, seed=1,
         replica=0, n_cell=0, brute_force=False, quat=None, sweep0=0, n_sweeps=1,
-        hist_bins=0, hist_rmax=0.0):
-    """Run the serial sampler in place on copies of pos/quat.
+        hist_bins=0, hist_rmax=0.0, threads=1):
+    """Run the sampler in place on copies of pos/quat (threads > 1: the active
+    cells of each colour phase on that many threads, identical results).
 
     Returns (pos, quat, counters dict, hist or None)."""
     pos = np.array(pos, dtype=np.float64, order="C").reshape(-1, 3)
@@ -256,7 +259,7 @@ def run(pos, L, *, shape=SHAPE_SPHERE, shape_params=(1.0,), q=0.0, n_r=0.0,
     sp = np.ascontiguousarray(shape_params, dtype=np.float64)
     cnt = np.zeros(N_COUNTERS, dtype=np.uint64)
     hist = np.zeros(max(hist_bins, 1), dtype=np.uint64) if hist_bins > 0 else None
-    rc = lib().oracle_run(
+    rc = lib().oracle_run_threads(
         n, float(L), int(shape), _p(sp, ctypes.c_double), len(sp), float(q),
         float(n_r), int(n_trial), int(cb_mode), int(v0_mode), float(soft_eps), float(d_max),
         float(a_max),
@@ -265,7 +268,7 @@ def run(pos, L, *, shape=SHAPE_SPHERE, shape_params=(1.0,), q=0.0, n_r=0.0,
         _p(qa, ctypes.c_double) if qa is not None else None,
         int(sweep0), int(n_sweeps), _p(cnt, ctypes.c_uint64),
         int(hist_bins), float(hist_rmax),
-        _p(hist, ctypes.c_uint64) if hist is not None else None)
+        _p(hist, ctypes.c_uint64) if hist is not None else None, int(threads))
     if rc != 0:
         raise ValueError("oracle_run rejected its arguments (rc=%d)" % rc)
     counters = {name: int(cnt[i]) for i, name in enumerate(COUNTERS)}
