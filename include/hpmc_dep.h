@@ -60,6 +60,9 @@ extern "C" {
 #define HPMC_HOST 0
 #define HPMC_DEVICE 1
 
+#define HPMC_PHASES_LAUNCHES 0    /* colour phases: one kernel launch per phase (default) */
+#define HPMC_PHASES_PERSISTENT 1  /* colour phases: one persistent launch per sweep */
+
 typedef struct hpmc_ctx hpmc_ctx;
 
 /* Event counters, accumulated since creation or hpmc_reset_counters().
@@ -157,11 +160,36 @@ int hpmc_set_moves(hpmc_ctx *ctx, double d_max, double a_max, double p_translate
 int hpmc_set_cells(hpmc_ctx *ctx, int n_cell);
 
 /* Launch shape: warps cooperating on one moved colloid's depletants and
- * colloid tests in the colour-phase kernels (1..8, default 1).
- * attempts_per_thread (1 or 2) is accepted for interface stability; the
- * kernels take one depletant attempt per thread per pass for either value.
- * Performance knobs only: results are identical for every value. */
-int hpmc_set_launch(hpmc_ctx *ctx, int warps_per_colloid, int attempts_per_thread);
+ * colloid tests in the colour-phase kernels (1..8, default 1), and the
+ * schedule of the eight colour phases of a sweep (Sec. III.E):
+ * HPMC_PHASES_LAUNCHES (default) runs one kernel launch per phase, each waiting
+ * for the previous one (programmatic dependent launch lets a phase's
+ * set-up overlap the previous one's tail); HPMC_PHASES_PERSISTENT runs all
+ * eight in one
+ * persistent launch whose one-warp CTAs take the non-empty active cells in
+ * phase order from a ticket counter, each cell waiting only until the
+ * non-empty cells of its 27-cell neighbourhood that belong to earlier phases
+ * of the sweep are done (per-cell readiness counters; every wait is bounded,
+ * see hpmc_set_wait_limit).  The persistent schedule applies to the
+ * HPMC_FP32_RECHECK form of spheres with one warp per colloid; other
+ * combinations use the launches.  Performance knobs only: results are
+ * identical for every value.  HPMC_ERR_ARG for an unknown schedule. */
+int hpmc_set_launch(hpmc_ctx *ctx, int warps_per_colloid, int phase_schedule);
+
+/* Bound of every device-side wait of the persistent colour phases, in
+ * seconds of GPU global time (default 1; 1e-6 .. 60).  A wait that runs out
+ * records HPMC_ERR_TIMEOUT (reported by the next synchronising call, as
+ * hpmc_sync or hpmc_get_state) and its cell is left unmoved for that sweep;
+ * the kernel still finishes, and the context stays usable (hpmc_set_state
+ * clears the error).  Takes effect at the next sweep. */
+int hpmc_set_wait_limit(hpmc_ctx *ctx, double seconds);
+
+/* Testing aid for the bounded waits: the persistent colour phases never
+ * publish global cell `cell` as done (-1, the default: none), so the waits of
+ * its neighbours in later phases run out.  Host-side fault injection only;
+ * the device is never made to fault or hang.  Takes effect at the next sweep.
+ * HPMC_ERR_ARG for cell < -1. */
+int hpmc_debug_withhold_cell(hpmc_ctx *ctx, int cell);
 
 /* Autotuner: time every combination of warps_per_colloid in warps[0..nw)
  * and cells per side in cells[0..nc) (0 = the largest valid count) over
@@ -347,6 +375,13 @@ int hpmc_cell_list_noalloc(int n, double box_l, int n_cell, const double *pos_de
  * stream-ordered scratch on the context's own stream. */
 int hpmc_free_volume(hpmc_ctx *ctx, int replica, double q, uint64_t seed, uint32_t sample,
                      uint64_t n_probe, uint64_t *n_free);
+
+/* The architecture the library's kernels were compiled for, as the CUDA
+ * runtime reports it for the current device (cudaFuncGetAttributes of one of
+ * them): *binary_version (103 for sm_103a) and *ptx_version (0 when the
+ * library carries no PTX); either pointer may be NULL, not both.  A library
+ * service, not a step of the method. */
+int hpmc_kernel_arch(int *binary_version, int *ptx_version);
 
 /* The library's own device Philox4x32-10 (Salmon, Moraes, Dror & Shaw,
  * SC'11: the counter-based generator every random stream of the method draws

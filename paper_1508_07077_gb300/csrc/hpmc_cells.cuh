@@ -64,6 +64,12 @@ __global__ void k_cells_bin(const __grid_constant__ SimParams P, int full)
     pdl_trigger();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (P.cls_count && g < 32) P.cls_count[g] = 0;
+    // persistent colour phases: a new epoch for the cells' readiness counters
+    // and a fresh ticket counter for the sweep that follows
+    if (g == 0 && P.epoch) {
+        atomicAdd(P.epoch, 1u);
+        *P.ticket = 0;
+    }
     if (full && P.task && g < 8 * P.n_cta) {
         const int phase = g / P.n_cta, a = g - phase * P.n_cta;
         const int r = P.cta_rep[a];
@@ -86,6 +92,8 @@ __global__ void k_cells_bin(const __grid_constant__ SimParams P, int full)
         s.sigma[2] = sigma[2];
         schedule_perm(R.key0, R.key1, sweep, s.perm);
         s.sweep = sweep;
+        s.phase_of = 0u;
+        for (int ph = 0; ph < 8; ++ph) s.phase_of |= (uint32_t)ph << (4 * s.perm[ph]);
         P.sched[r] = s;
     }
     if (g - R.off >= P.n_live[r]) {   // a slot not in use (Gibbs pair)
@@ -99,6 +107,7 @@ __global__ void k_cells_bin(const __grid_constant__ SimParams P, int full)
     const int cy = cell_coord_fast(p.y, sigma[1], R.L, R.w, iw32, nc);
     const int cz = cell_coord_fast(p.z, sigma[2], R.L, R.w, iw32, nc);
     const int c = R.cell_off + cx + nc * (cy + nc * cz);
+    if (HPMC_CHECK_FAILS(P, c >= R.cell_off && c < R.cell_off + nc * nc * nc, 10)) return;
     const float4 rl = make_float4(cell_rel(p.x, sigma[0], R.L, R.w, cx),
                                   cell_rel(p.y, sigma[1], R.L, R.w, cy),
                                   cell_rel(p.z, sigma[2], R.L, R.w, cz), __int_as_float(g));
@@ -122,8 +131,8 @@ __global__ void k_cells_bin(const __grid_constant__ SimParams P, int full)
 }
 
 // Order every phase's tasks by the population of their cell, fullest first:
-// a phase lasts as long as its longest sequential chain of moves, so the long
-// chains should start first.  One thread per (phase, CTA) entry; positions
+// a phase launch lasts as long as its longest sequential chain of moves, so
+// the long chains should start first.  One thread per (phase, CTA) entry; positions
 // inside a class come from warp-aggregated atomics (any order is valid: the
 // cells of one colour are independent).
 __global__ void k_task_order(const __grid_constant__ SimParams P)
@@ -137,7 +146,13 @@ __global__ void k_task_order(const __grid_constant__ SimParams P)
         const int phase = t / P.n_cta;
         tk = P.task[t];
         const int n = P.count[tk.w >> 16][tk.x];
-        const int cls = n >= 3 ? 0 : (n == 2 ? 1 : (n == 1 ? 2 : 3));
+        // persistent colour phases: one class of non-empty cells, kept close
+        // to the table's spatial order (blocks run in roughly increasing
+        // order), so that a cell's neighbours of the previous phase sit about
+        // one phase's worth of tickets earlier and are done by the time it is
+        // taken
+        const int cls = P.persistent ? (n > 0 ? 0 : 3)
+                                     : (n >= 3 ? 0 : (n == 2 ? 1 : (n == 1 ? 2 : 3)));
         key = phase * 4 + cls;
     }
     const unsigned peers = __match_any_sync(kFull, key);

@@ -36,7 +36,20 @@ enum Counter {
     kTranslate, kDepEval, kDepBlocking, kCbFwdOk, kCbRevOk, kCapHits, kRechecks
 };
 
-enum DevError { kErrNone = 0, kErrCandCap = 1, kErrCellCap = 2 };
+enum DevError { kErrNone = 0, kErrCandCap = 1, kErrCellCap = 2, kErrTimeout = 3, kErrCheck = 4 };
+
+// Checked build (-DHPMC_CHECKED): the FP32 sphere path bounds-checks its
+// cell, bin, neighbour, shared-memory and colloid indices and the
+// checkerboard invariant (Sec. III.E: a move reads only colloids of its own
+// cell and of cells that are not active in the same phase).  A failed check
+// records kErrCheck, with the check's number in the second error word, and
+// the access is skipped; nothing traps.  In the regular build every check
+// compiles away.
+#ifdef HPMC_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
 
 enum Purpose : uint32_t {
     kPSched = 0, kPMove = 1, kPRot = 2, kPPoisson = 3, kPDep = 4,
@@ -119,6 +132,7 @@ struct Sched {
     double sigma[3];
     int perm[8];
     uint32_t sweep;   // sweep index these kernels run
+    uint32_t phase_of;  // phase of each colour c in bits 4c..4c+3 (the inverse of perm)
 };
 
 // One replica: its system, its parameters and where its data sit in the
@@ -257,7 +271,77 @@ struct SimParams {
     unsigned long long *sweep;     // next sweep index (all replicas)
     unsigned long long *counters;  // [n_rep][kRepSlots][kNumCounters]
     int *err;
+    // persistent colour phases (FP32 sphere form): readiness counter of every
+    // cell (the epoch of the sweep in which it was last done), the epoch
+    // (advanced by the cell-list kernel before every sweep), the ticket
+    // counter of the work items (reset with it), the bound of every wait in
+    // nanoseconds of global time, and a cell whose readiness is never
+    // published (-1: none; set only to test the bounded waits)
+    int n_cells;
+    uint32_t *done;
+    uint32_t *epoch;
+    int *ticket;
+    int ticket_chunk;      // work items a CTA takes per ticket atomic
+    int persistent;        // the colour phases run as one persistent launch
+    unsigned long long wait_ns;
+    int withhold;
 };
+
+// True (and the error recorded) when a check of the checked build fails.
+__device__ __noinline__ bool check_failed(int *err, int id)
+{
+    atomicCAS(err, kErrNone, kErrCheck);
+    atomicCAS(err + 1, 0, id);
+    return true;
+}
+#define HPMC_CHECK_FAILS(P, cond, id) (kChecked && !(cond) && check_failed((P).err, (id)))
+
+// --- bounded device-side waits ----------------------------------------------
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait until *flag has reached target (compared modulo 2^32, so epochs may
+// wrap), at most limit_ns of global time and a matching number of polls;
+// false if the wait ran out.  Polls back off with __nanosleep after the
+// first 64.
+__device__ __noinline__ bool wait_ready_slow(const uint32_t *flag, uint32_t target,
+                                             unsigned long long limit_ns)
+{
+    const unsigned long long t0 = globaltimer_ns();
+    const unsigned long long max_polls = limit_ns / 32ull + 1024ull;
+    for (unsigned long long it = 0; it < max_polls; ++it) {
+        // the usual wait is about one cell's work: poll at L2 latency first,
+        // then back off
+        if (it >= 64) __nanosleep(it < 256 ? 64 : 512);
+        if ((int)(ld_acquire_u32(flag) - target) >= 0) return true;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool wait_ready(const uint32_t *flag, uint32_t target,
+                                           unsigned long long limit_ns)
+{
+    if ((int)(ld_acquire_u32(flag) - target) >= 0) return true;
+    return wait_ready_slow(flag, target, limit_ns);
+}
 
 // Sec. III.E: cell coordinate of x under grid shift sigma.
 __device__ __forceinline__ int cell_coord(double x, double sigma, double L, double w, int nc)

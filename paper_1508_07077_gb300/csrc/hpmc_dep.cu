@@ -14,6 +14,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/hpmc_dep.h"
 #include "hpmc_cells.cuh"
@@ -39,7 +40,7 @@ struct Params {
     double sp[4] = {1.0, 0.0, 0.0, 0.0};
     int nsp = 1;
     int warps = 1;
-    int ilp = 1;
+    int schedule = HPMC_PHASES_LAUNCHES;  // colour phases: 8 launches or one persistent kernel
     double margin = 0.0;
     int v0_mode = HPMC_V0_CIRCUMSPHERE;
     double soft_eps = 0.0;
@@ -97,6 +98,13 @@ struct hpmc_ctx {
     unsigned long long *d_T = nullptr;
     unsigned long long *d_sweep = nullptr, *d_counters = nullptr;
     int *d_err = nullptr, *d_flag = nullptr;
+    // persistent colour phases: per-cell readiness counters, epoch, ticket
+    uint32_t *d_done = nullptr, *d_epoch = nullptr;
+    int *d_ticket = nullptr;
+    int done_alloc = -1;
+    double wait_s = 1.0;      // bound of every device-side wait
+    int withhold = -1;        // test only: a cell whose readiness is never published
+    int ticket_chunk = 1;     // persistent colour phases: work items per ticket atomic
 
     bool timing = false;
     std::vector<cudaEvent_t> tev;   // pairs (start, stop)
@@ -446,6 +454,14 @@ int derive_rep(const hpmc_ctx *c, const RepHost &h, Rep &R, std::vector<double> 
     return HPMC_OK;
 }
 
+// The persistent colour-phase kernel runs the FP32 sphere form's sweeps with
+// one-warp CTAs (warps per colloid = 1) when the schedule selects it.
+bool use_persistent(const hpmc_ctx *c)
+{
+    return c->prm.schedule == HPMC_PHASES_PERSISTENT && c->precision == HPMC_FP32_RECHECK &&
+           c->prm.shape == HPMC_SPHERE && c->prm.warps == 1 && c->d_done != nullptr;
+}
+
 SimParams make_params(hpmc_ctx *c)
 {
     SimParams P;
@@ -484,8 +500,18 @@ SimParams make_params(hpmc_ctx *c)
     P.sweep = c->d_sweep;
     P.counters = c->d_counters;
     P.err = c->d_err;
+    P.n_cells = c->n_cells;
+    P.done = c->d_done;
+    P.epoch = c->d_epoch;
+    P.ticket = c->d_ticket;
+    P.wait_ns = (unsigned long long)(c->wait_s * 1e9);
+    P.ticket_chunk = c->ticket_chunk;
+    P.persistent = use_persistent(c) ? 1 : 0;
+    P.withhold = c->withhold;
     return P;
 }
+
+
 
 // Enqueue the binned cell lists (and schedules) of the sweep whose index is
 // in *d_sweep.  Their count buffer was zeroed by the previous sweep's phase
@@ -577,6 +603,47 @@ void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s
     }
 }
 
+// One launch for all eight colour phases: as many one-warp CTAs as fit on
+// the GPU at once (any count is correct; more would only wait for a slot).
+template <typename K>
+void launch_persistent(K kernel, size_t dyn, cudaStream_t s, const SimParams &P)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32, dyn);
+    const int grid = std::max(1, sms * std::max(1, per_sm));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(32u);
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, P);
+}
+
+template <int CAP>
+void launch_sweep_cap(hpmc_ctx *c, const SimParams &P, cudaStream_t s)
+{
+    bool cb = false;
+    for (const RepHost &h : c->reps) cb = cb || h.n_trial > 0;
+    const size_t dyn = cb ? (size_t)32 * (sizeof(double) + sizeof(int)) : 0;
+    if (cb) launch_persistent(k_sweep_sphere_fp32<true, CAP>, dyn, s, P);
+    else if (c->prm.soft_eps > 0.0) launch_persistent(k_sweep_sphere_fp32<false, CAP, true>, dyn, s, P);
+    else launch_persistent(k_sweep_sphere_fp32<false, CAP>, dyn, s, P);
+}
+
+void launch_sweep_phases(hpmc_ctx *c, const SimParams &P, cudaStream_t s)
+{
+    if (c->cap == kTinyCellCap) launch_sweep_cap<kTinyCellCap>(c, P, s);
+    else if (c->cap == kSmallCellCap) launch_sweep_cap<kSmallCellCap>(c, P, s);
+    else launch_sweep_cap<kMaxCellCap>(c, P, s);
+}
+
 void launch_phase(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
 {
     if (c->cap == kTinyCellCap) launch_phase_cap<kTinyCellCap>(c, P, phase, s);
@@ -612,7 +679,9 @@ int enqueue_sweep(hpmc_ctx *c, cudaStream_t s)
     if (rc != HPMC_OK) return rc;
     SimParams P = make_params(c);
     launch_lens(c, P, s);
-    for (int phase = 0; phase < 8; ++phase) launch_phase(c, P, phase, s);
+    if (use_persistent(c)) launch_sweep_phases(c, P, s);
+    else
+        for (int phase = 0; phase < 8; ++phase) launch_phase(c, P, phase, s);
     CK(cudaGetLastError());
     return HPMC_OK;
 }
@@ -635,7 +704,9 @@ int enqueue_sweep_timed(hpmc_ctx *c, cudaStream_t s)
 {
     cudaEvent_t a = pool_event(c), b = pool_event(c);
     CK(cudaEventRecord(a, s));
+    nvtxRangePushA("cell lists");
     int rc = enqueue_cells(c, s);
+    nvtxRangePop();
     if (rc != HPMC_OK) return rc;
     CK(cudaEventRecord(b, s));
     c->tev.push_back(a);
@@ -645,20 +716,39 @@ int enqueue_sweep_timed(hpmc_ctx *c, cudaStream_t s)
     if (c->precision == HPMC_FP32_RECHECK) {
         cudaEvent_t x = pool_event(c), y = pool_event(c);
         CK(cudaEventRecord(x, s));
+        nvtxRangePushA("depletant lens lists");
         launch_lens(c, P, s);
+        nvtxRangePop();
         CK(cudaEventRecord(y, s));
         c->tev.push_back(x);
         c->tev.push_back(y);
         c->tkind.push_back(2);
     }
-    for (int phase = 0; phase < 8; ++phase) {
+    if (use_persistent(c)) {
         cudaEvent_t x = pool_event(c), y = pool_event(c);
         CK(cudaEventRecord(x, s));
-        launch_phase(c, P, phase, s);
+        nvtxRangePushA("colour phases 0-7 (persistent)");
+        launch_sweep_phases(c, P, s);
+        nvtxRangePop();
         CK(cudaEventRecord(y, s));
         c->tev.push_back(x);
         c->tev.push_back(y);
         c->tkind.push_back(1);
+    } else {
+        for (int phase = 0; phase < 8; ++phase) {
+            static const char *names[8] = {"colour phase 0", "colour phase 1", "colour phase 2",
+                                           "colour phase 3", "colour phase 4", "colour phase 5",
+                                           "colour phase 6", "colour phase 7"};
+            cudaEvent_t x = pool_event(c), y = pool_event(c);
+            CK(cudaEventRecord(x, s));
+            nvtxRangePushA(names[phase]);
+            launch_phase(c, P, phase, s);
+            nvtxRangePop();
+            CK(cudaEventRecord(y, s));
+            c->tev.push_back(x);
+            c->tev.push_back(y);
+            c->tkind.push_back(1);
+        }
     }
     CK(cudaGetLastError());
     return HPMC_OK;
@@ -683,7 +773,7 @@ int enqueue_check(hpmc_ctx *c, cudaStream_t s)
 {
     const size_t cbytes = sizeof(int) * 2 * (size_t)c->n_cells;
     CK(cudaMemsetAsync(c->d_count, 0, cbytes, s));
-    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int), s));
     int rc = enqueue_cells(c, s, false);   // (the phase task order is not needed)
     if (rc != HPMC_OK) return rc;
     CK(cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
@@ -696,7 +786,7 @@ int enqueue_check(hpmc_ctx *c, cudaStream_t s)
         k_check_aniso<<<(c->n_total + 127) / 128, 128, 0, s>>>(P, c->d_flag);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->h_pin + kPinFlag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(c->h_pin + kPinErr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->h_pin + kPinErr, c->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     // the sweeps start from zeroed populations
     CK(cudaMemsetAsync(c->d_count, 0, cbytes, s));
     return HPMC_OK;
@@ -815,6 +905,22 @@ int prepare(hpmc_ctx *c)
             c->task_alloc = cta_off;
         }
         if (!c->d_cls_count) CK(cudaMalloc(&c->d_cls_count, sizeof(int) * 32));
+        // readiness counters of the persistent colour phases (zero: done in
+        // no sweep yet; the epoch only grows)
+        if (cell_off != c->done_alloc) {
+            cudaFree(c->d_done);
+            c->d_done = nullptr;
+            c->done_alloc = -1;
+            CK(cudaMalloc(&c->d_done, sizeof(uint32_t) * (size_t)cell_off));
+            CK(cudaMemset(c->d_done, 0, sizeof(uint32_t) * (size_t)cell_off));
+            c->done_alloc = cell_off;
+        }
+        if (!c->d_epoch) {
+            CK(cudaMalloc(&c->d_epoch, sizeof(uint32_t)));
+            CK(cudaMemset(c->d_epoch, 0, sizeof(uint32_t)));
+            CK(cudaMalloc(&c->d_ticket, sizeof(int)));
+            CK(cudaMemset(c->d_ticket, 0, sizeof(int)));
+        }
         if (!c->d_binpos) CK(cudaMalloc(&c->d_binpos, sizeof(int) * (size_t)c->n_total));
         const long long slots = (long long)cell_off * cap;
         if (slots != c->aux_alloc) {
@@ -970,13 +1076,13 @@ int alloc_ctx(hpmc_ctx *c)
     CK(cudaMalloc(&c->d_sweep, sizeof(unsigned long long)));
     CK(cudaMalloc(&c->d_counters,
                   sizeof(unsigned long long) * (size_t)n_rep * kRepSlots * kNumCounters));
-    CK(cudaMalloc(&c->d_err, sizeof(int)));
+    CK(cudaMalloc(&c->d_err, 2 * sizeof(int)));   // error code, check id
     CK(cudaMalloc(&c->d_flag, sizeof(int)));
     CK(cudaMemsetAsync(c->d_sweep, 0, sizeof(unsigned long long), c->cap_stream));
     CK(cudaMemsetAsync(c->d_counters, 0,
                        sizeof(unsigned long long) * (size_t)n_rep * kRepSlots * kNumCounters,
                        c->cap_stream));
-    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->cap_stream));
+    CK(cudaMemsetAsync(c->d_err, 0, 2 * sizeof(int), c->cap_stream));
     // identity orientations unless given
     std::vector<double> ident(4 * (size_t)n, 0.0);
     for (int i = 0; i < n; ++i) ident[4 * (size_t)i] = 1.0;
@@ -1017,7 +1123,7 @@ void sum_counters(const unsigned long long *h, int r0, int r1, hpmc_counters *ou
 // the pinned staging block; the caller synchronises once.
 int stage_err_counters(hpmc_ctx *c, cudaStream_t s, bool counters)
 {
-    CK(cudaMemcpyAsync(c->h_pin + kPinErr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->h_pin + kPinErr, c->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     if (counters)
         CK(cudaMemcpyAsync(c->h_pin + kPinHead, c->d_counters,
                            sizeof(unsigned long long) * counter_words(c), cudaMemcpyDeviceToHost, s));
@@ -1027,9 +1133,14 @@ int stage_err_counters(hpmc_ctx *c, cudaStream_t s, bool counters)
 int staged_err(const hpmc_ctx *c)
 {
     const int e = *reinterpret_cast<const int *>(c->h_pin + kPinErr);
+    const int detail = reinterpret_cast<const int *>(c->h_pin + kPinErr)[1];
     if (e && getenv("HPMC_VERBOSE"))
-        fprintf(stderr, "hpmc: device error %d (%s)\n", e,
-                e == kErrCandCap ? "neighbourhood or lens capacity" : "cell bin capacity");
+        fprintf(stderr, "hpmc: device error %d (%s), detail %d\n", e,
+                e == kErrCandCap ? "neighbourhood or lens capacity"
+                : e == kErrTimeout ? "a bounded wait ran out"
+                : e == kErrCheck ? "a check of the checked build failed" : "cell bin capacity",
+                detail);
+    if (e == kErrTimeout) return HPMC_ERR_TIMEOUT;
     return e ? HPMC_ERR_DEVICE : HPMC_OK;
 }
 
@@ -1071,6 +1182,12 @@ int create_ctx(hpmc_ctx **out, const std::vector<RepHost> &reps, uint64_t seed, 
         return HPMC_ERR_CAP;
     }
     c->n_total = (int)tot;
+    // performance knob of the persistent colour phases (results do not
+    // depend on it): work items taken per ticket atomic
+    if (const char *e = getenv("HPMC_TICKET_CHUNK")) {
+        const int v = atoi(e);
+        if (v >= 1 && v <= 1024) c->ticket_chunk = v;
+    }
     DeviceGuard g(device);
     int rc = alloc_ctx(c);
     if (rc != HPMC_OK) {
@@ -1260,12 +1377,29 @@ int hpmc_set_cells(hpmc_ctx *c, int n_cell)
     return HPMC_OK;
 }
 
-int hpmc_set_launch(hpmc_ctx *c, int warps_per_colloid, int attempts_per_thread)
+int hpmc_set_launch(hpmc_ctx *c, int warps_per_colloid, int phase_schedule)
 {
     if (!c || warps_per_colloid < 1 || warps_per_colloid > kMaxThreads / 32) return HPMC_ERR_ARG;
-    if (attempts_per_thread < 1 || attempts_per_thread > 2) return HPMC_ERR_ARG;
+    if (phase_schedule != HPMC_PHASES_LAUNCHES && phase_schedule != HPMC_PHASES_PERSISTENT)
+        return HPMC_ERR_ARG;
     c->prm.warps = warps_per_colloid;
-    c->prm.ilp = attempts_per_thread;
+    c->prm.schedule = phase_schedule;
+    c->dirty = true;
+    return HPMC_OK;
+}
+
+int hpmc_set_wait_limit(hpmc_ctx *c, double seconds)
+{
+    if (!c || !(seconds >= 1e-6) || !(seconds <= 60.0)) return HPMC_ERR_ARG;
+    c->wait_s = seconds;
+    c->dirty = true;
+    return HPMC_OK;
+}
+
+int hpmc_debug_withhold_cell(hpmc_ctx *c, int cell)
+{
+    if (!c || cell < -1) return HPMC_ERR_ARG;
+    c->withhold = cell;
     c->dirty = true;
     return HPMC_OK;
 }
@@ -1306,7 +1440,7 @@ int hpmc_autotune(hpmc_ctx *c, const int *warps, int nw, const int *cells, int n
         CK(cudaMemcpy(c->d_quat, sq, sizeof(double4) * (size_t)n, cudaMemcpyDeviceToDevice));
         CK(cudaMemcpy(c->d_counters, sc, cnt_bytes, cudaMemcpyDeviceToDevice));
         CK(cudaMemcpy(c->d_sweep, &sweep0, sizeof sweep0, cudaMemcpyHostToDevice));
-        CK(cudaMemset(c->d_err, 0, sizeof(int)));
+        CK(cudaMemset(c->d_err, 0, 2 * sizeof(int)));
         c->state_dirty = true;   // cell populations are rebuilt before the next sweep
         return HPMC_OK;
     };
@@ -1381,14 +1515,31 @@ int hpmc_sweep(hpmc_ctx *c, int n_sweeps, void *stream)
         int rc = c->dirty ? prepare(c) : check_config(c);
         if (rc != HPMC_OK) return rc;
     }
+    // NVTX: one range per call, and (timing mode, kernels launched one by
+    // one) one per sweep with nested ranges for the cell lists, the lens
+    // kernel and each colour phase
+    nvtxRangePushA("hpmc_sweep");
     if (c->timing) {
         for (int k = 0; k < n_sweeps; ++k) {
+            nvtxRangePushA("sweep");
             int rc = enqueue_sweep_timed(c, s);
-            if (rc != HPMC_OK) return rc;
+            nvtxRangePop();
+            if (rc != HPMC_OK) {
+                nvtxRangePop();
+                return rc;
+            }
         }
+        nvtxRangePop();
         return HPMC_OK;
     }
-    for (int k = 0; k < n_sweeps; ++k) CK(cudaGraphLaunch(c->exec, s));
+    for (int k = 0; k < n_sweeps; ++k) {
+        const cudaError_t e = cudaGraphLaunch(c->exec, s);
+        if (e != cudaSuccess) {
+            nvtxRangePop();
+            return cuda_fail(e, "cudaGraphLaunch");
+        }
+    }
+    nvtxRangePop();
     return HPMC_OK;
 }
 
@@ -1617,6 +1768,16 @@ int hpmc_cell_list(int n, double box_l, int n_cell, const double *pos_dev, uint6
     cudaFreeAsync(cell_of, s);
     cudaFreeAsync(count, s);
     return rc;
+}
+
+int hpmc_kernel_arch(int *binary_version, int *ptx_version)
+{
+    if (!binary_version && !ptx_version) return HPMC_ERR_ARG;
+    cudaFuncAttributes a;
+    CK(cudaFuncGetAttributes(&a, k_philox));
+    if (binary_version) *binary_version = a.binaryVersion;
+    if (ptx_version) *ptx_version = a.ptxVersion;
+    return HPMC_OK;
 }
 
 int hpmc_philox(int n, const uint32_t *ctr_dev, const uint32_t *key_dev, uint32_t *out_dev,
@@ -1873,6 +2034,9 @@ void hpmc_destroy(hpmc_ctx *c)
     cudaFree(c->d_counters);
     cudaFree(c->d_err);
     cudaFree(c->d_flag);
+    cudaFree(c->d_done);
+    cudaFree(c->d_epoch);
+    cudaFree(c->d_ticket);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->h_pin) cudaFreeHost(c->h_pin);
     cudaFree(c->d_n_live);

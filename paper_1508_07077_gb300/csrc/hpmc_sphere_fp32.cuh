@@ -601,7 +601,8 @@ __global__ void __launch_bounds__(128, 8) k_lens_sphere_fp32(const __grid_consta
     // colloid's bin slot, where the colour phase reads them with the cell list
     __syncwarp();
     pdl_wait();
-    const int bp = P.binpos[g];
+    int bp = P.binpos[g];
+    if (HPMC_CHECK_FAILS(P, bp < P.n_cells * P.cap, 9)) bp = -1;
     if (bp >= 0) {
         if (lane == 0) {
             P.mv_bin[bp] = s_mv[wl];
@@ -730,16 +731,23 @@ __device__ __forceinline__ bool cta_any(bool p)
 }
 
 // ---------------------------------------------------------------------------
-// One colour phase (FP32 form): a CTA per active cell.  The CTA stages its
-// 27-cell neighbourhood, the cell's colloids (ascending index), their
-// displacements and their lens points in shared memory, then moves the
-// colloids one after another.  CB: configurational bias on (n_trial > 0) or
-// off.  WARP: the CTA is a single warp (barriers become warp operations).
-// CAP: capacity of a cell bin (the cell list's stride).
+// Per-cell work of a colour phase (FP32 form), shared by the per-phase kernel
+// and the persistent sweep kernel.  The CTA stages its 27-cell neighbourhood,
+// the cell's colloids (ascending index), their displacements and their lens
+// points in shared memory, then moves the colloids one after another.
+// tk: the task-table entry of the cell (global cell, replica, coordinates,
+// n_c and count parity); the cell is not empty.  CB: configurational bias on
+// (n_trial > 0) or off.  WARP: the CTA is a single warp (barriers become warp
+// operations).  CAP: capacity of a cell bin (the cell list's stride).
+// PERSIST: instead of waiting for the whole previous phase (programmatic
+// dependent launch), wait only for the non-empty stencil cells of earlier
+// phases of this sweep, through their readiness counters (epoch: the value a
+// counter holds once its cell is done in this sweep); if a wait runs out,
+// record HPMC's timeout error and return without moving (the caller still
+// publishes the cell as done, so no other wait depends on it).
 // ---------------------------------------------------------------------------
-template <bool CB, bool WARP, int CAP, bool SOFT = false>
-__global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? ((CB || SOFT) ? 16 : 32) : 1)
-    k_phase_sphere_fp32(const __grid_constant__ SimParams P, int phase)
+template <bool CB, bool WARP, int CAP, bool SOFT, bool PERSIST>
+__device__ __forceinline__ void phase_cell(const SimParams &P, int phase, int4 tk, uint32_t epoch)
 {
     __shared__ float4 s_cpos[cand_cap(CAP)];  // candidates relative to this cell's origin; index in .w
     __shared__ float4 s_nb[max_nb(CAP)];      // neighbours relative to the new position; index in .w
@@ -761,40 +769,9 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? ((CB || SOFT) 
         sh.f = s_dyn;
         sh.k = (int *)(s_dyn + nthr);
     }
-    // The phases are launched with programmatic dependent launch: the next
-    // phase's CTAs may start while this one drains.  Everything read before
-    // pdl_wait() is fixed for the whole sweep (task table, populations, replica
-    // record, lens headers, displacements and lens points); positions (bins,
-    // FP64 state) are read and written only after it.
-    pdl_trigger();
-    if (phase == 7 && blockIdx.x == 0 && tid == 0) atomicAdd(P.sweep, 1ull);
-    // the CTA's cell (task table of this sweep, fullest cells first):
-    // everything needed to start loading the stencil without the replica
-    // record
-    int cls = 0, idx = blockIdx.x;
-    {
-        const int4 cc = reinterpret_cast<const int4 *>(P.cls_count)[phase];
-        if (idx >= cc.x) {
-            idx -= cc.x;
-            cls = 1;
-            if (idx >= cc.y) {
-                idx -= cc.y;
-                cls = 2;
-                if (idx >= cc.z) {
-                    idx -= cc.z;
-                    cls = 3;
-                }
-            }
-        }
-    }
-    const int4 tk = P.task_ord[(size_t)(phase * 4 + cls) * P.n_cta + idx];
     const int cell = tk.x, r = tk.y;
     const int cx = tk.z & 1023, cy = (tk.z >> 10) & 1023, cz = tk.z >> 20;
     const int nc = tk.w & 0xFFFF, par = tk.w >> 16;
-    if (cls == 3) {               // an empty cell: only its next-sweep population
-        if (tid == 0) P.count[par ^ 1][cell] = 0;
-        return;
-    }
     const int ns = nc == 2 ? 2 : 3, n_st = ns * ns * ns;
     const int t_own = ns == 3 ? 13 : cx + 2 * cy + 4 * cz;
     const int cell_off = cell - (cx + nc * (cy + nc * cz));
@@ -806,31 +783,43 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? ((CB || SOFT) 
                 m_cell = R.m_cell, nb_cut2 = R.nb_cut2_32, T_dep = R.T_dep32,
                 T_contact = R.T_contact32;
     const int has_dep = R.has_dep;
-    if (tid == 0) P.count[par ^ 1][cell] = 0;   // this cell's population of the next sweep
+    // this cell's population of the next sweep (the persistent kernel clears
+    // the whole next-sweep buffer itself)
+    if (!PERSIST && tid == 0) P.count[par ^ 1][cell] = 0;
 
-    // one round of loads: every stencil cell's population, and for the own
-    // cell the displacements, headers and inline lens points of its first two
-    // slots (speculatively: most cells hold at most two colloids)
+    // Loads, most of them before the wait for the neighbours (everything
+    // about the own cell is fixed for the sweep or written only by this CTA):
+    // round 1, every stencil cell's population (lanes 0..26) and, on spare
+    // lanes, the own cell's first two bin entries, displacements, headers and
+    // inline lens points (speculatively: most cells hold at most two
+    // colloids); round 2 (only for more colloids) the rest of the own cell's
+    // slots, one lane each; after the wait one round for the neighbour cells'
+    // entries (up to four per cell at once).
     int c_nb = 0, m_nb = 0, dx = 0, dy = 0, dz = 0;
-    float4 e_a = make_float4(0.f, 0.f, 0.f, 0.f), e_b = e_a;
+    const size_t own0 = (size_t)cell * P.cap;
+    float4 p_a = make_float4(0.f, 0.f, 0.f, 0.f), p_b = p_a;
+    int4 h_a = make_int4(0, 0, 0, 0), h_b = h_a;
     if (tid < n_st) {
         c_nb = stencil_cell_nc(nc, cell_off, tid, cx, cy, cz, dx, dy, dz);
-        const size_t b0 = (size_t)c_nb * P.cap;
-        m_nb = count[c_nb];
-        if (tid == t_own) {
+        if (HPMC_CHECK_FAILS(P, c_nb >= cell_off && c_nb < cell_off + nc * nc * nc &&
+                                    c_nb < P.n_cells, 1))
+            c_nb = cell;
+        m_nb = min(count[c_nb], P.cap);
+    } else if (tid == 27) {
+        p_a = P.bins[own0];
+        p_b = P.bins[own0 + 1];
+    } else if (tid == 28) {
+        p_a = P.mv_bin[own0];
+        p_b = P.mv_bin[own0 + 1];
+        h_a = P.hdr_bin[own0];
+        h_b = P.hdr_bin[own0 + 1];
+    } else if (tid == 29 || tid == 30) {
+        const float4 *src = P.lens_bin + (own0 + (size_t)(tid - 29)) * kLensInline;
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                s_mv[s] = P.mv_bin[b0 + s];
-                s_hdr[s] = P.hdr_bin[b0 + s];
-#pragma unroll
-                for (int j = 0; j < kLensInline; ++j)
-                    s_lin[s][j] = P.lens_bin[(b0 + s) * kLensInline + j];
-            }
-        }
-        m_nb = min(m_nb, P.cap);
+        for (int j = 0; j < kLensInline; ++j) s_lin[tid - 29][j] = src[j];
     }
     const Sched *S = P.sched + r;
-    int n_own = 0, M = 0, base = 0;
+    int n_own = 0, M = 0, base = 0, base_own = 0;
     if (tid < 32) {
         n_own = __shfl_sync(kFull, m_nb, t_own);
         int incl = m_nb;
@@ -841,15 +830,18 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? ((CB || SOFT) 
         }
         base = incl - m_nb;
         M = __shfl_sync(kFull, incl, 31);
+        base_own = __shfl_sync(kFull, base, t_own);
         if (!WARP && tid == 0) {
             s_ncand = M;
             s_nacc = n_own;
+            s_acc = base_own;
         }
     }
     if (!WARP) {
         __syncthreads();
         M = s_ncand;
         n_own = s_nacc;
+        base_own = s_acc;
         __syncthreads();
     }
     if (n_own == 0) return;
@@ -857,35 +849,31 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? ((CB || SOFT) 
         if (tid == 0) atomicCAS(P.err, kErrNone, kErrCandCap);
         return;
     }
-    const uint32_t sweep = S->sweep;
-    // the previous phase's moves are visible from here on
-    pdl_wait();
-    if (tid < n_st) {
-        const size_t b0 = (size_t)c_nb * P.cap;
-        e_a = P.bins[b0];
-        e_b = P.bins[b0 + 1];
+    // the own cell's slots (its candidates, in bin order) and their move data
+    if (tid == 27) {
+        s_cpos[base_own] = p_a;
+        s_tmp_i[0] = __float_as_int(p_a.w);
+        s_tmp_slot[0] = base_own;
+        if (n_own > 1) {
+            s_cpos[base_own + 1] = p_b;
+            s_tmp_i[1] = __float_as_int(p_b.w);
+            s_tmp_slot[1] = base_own + 1;
+        }
+    } else if (tid == 28) {
+        s_mv[0] = p_a;
+        s_hdr[0] = h_a;
+        s_mv[1] = p_b;
+        s_hdr[1] = h_b;
+    }
+    for (int q = 2 + tid; q < n_own; q += nthr) {
+        const float4 e = P.bins[own0 + q];
+        s_mv[q] = P.mv_bin[own0 + q];
+        s_hdr[q] = P.hdr_bin[own0 + q];
+        s_cpos[base_own + q] = e;
+        s_tmp_i[q] = __float_as_int(e.w);
+        s_tmp_slot[q] = base_own + q;
     }
     if (tid == 0) s_nacc = 0;
-    // candidates relative to this cell's origin (entries beyond the first two
-    // in a second, rarely needed, round)
-    if (tid < n_st) {
-        const float fx = (float)dx * w32, fy = (float)dy * w32, fz = (float)dz * w32;
-        const bool own = tid == t_own;
-        const size_t b0 = (size_t)c_nb * P.cap;
-        for (int s = 0; s < m_nb; ++s) {
-            const float4 e = s == 0 ? e_a : (s == 1 ? e_b : P.bins[b0 + s]);
-            const int slot = base + s;
-            s_cpos[slot] = make_float4(fx + e.x, fy + e.y, fz + e.z, e.w);
-            if (own) {
-                s_tmp_i[s] = __float_as_int(e.w);
-                s_tmp_slot[s] = slot;
-                if (s >= 2) {
-                    s_mv[s] = P.mv_bin[b0 + s];
-                    s_hdr[s] = P.hdr_bin[b0 + s];
-                }
-            }
-        }
-    }
     cta_sync<WARP>();
     // the cell's colloids in ascending index (the order they move in), and
     // where each one's lens points go in shared memory (bin order)
@@ -893,6 +881,7 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? ((CB || SOFT) 
         const int v = s_tmp_i[q];
         int rk = 0;
         for (int u = 0; u < n_own; ++u) rk += s_tmp_i[u] < v ? 1 : 0;
+        if (HPMC_CHECK_FAILS(P, rk < n_own && n_own <= CAP, 6)) continue;
         s_own[rk] = v;
         s_own_slot[rk] = s_tmp_slot[q];
         s_own_bin[rk] = q;
@@ -910,9 +899,9 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? ((CB || SOFT) 
         }
     }
     cta_sync<WARP>();
-    // lens points: the first kLensInline of slots 0 and 1 came with the bin
-    // entries; other short lists are beside their bin slots, long ones in the
-    // lens array
+    // lens points: the first kLensInline of slots 0 and 1 came in round 1;
+    // other short lists are beside their bin slots, long ones in the lens
+    // array
     if (has_dep) {
         for (int q = 0; q < n_own; ++q) {
             const int n = s_hdr[q].z, o = s_loff[q];
@@ -920,14 +909,70 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? ((CB || SOFT) 
             if (n <= kLensInline && q < 2) {
                 if (tid < n) s_lens[o + tid] = s_lin[q][tid];
             } else if (n <= kLensInline) {
-                if (tid < n) s_lens[o + tid] = P.lens_bin[((size_t)cell * P.cap + q) * kLensInline + tid];
+                if (tid < n) s_lens[o + tid] = P.lens_bin[(own0 + q) * kLensInline + tid];
             } else {
                 const float4 *src = P.lens + (size_t)s_tmp_i[q] * P.lens_cap;
                 for (int m = tid; m < n; m += nthr) s_lens[o + m] = src[m];
             }
         }
-        cta_sync<WARP>();
     }
+    const uint32_t sweep = S->sweep;
+    if (PERSIST) {
+        // the non-empty stencil cells of earlier phases of this sweep must be
+        // done (their moves committed) before this cell reads them; those of
+        // later phases wait for this one in turn, so no cell reads what
+        // another writes while it writes (Sec. III.E)
+        bool need = false;
+        if (tid < n_st && m_nb > 0 && tid != t_own) {
+            const int col = ((cx + dx) & 1) | (((cy + dy) & 1) << 1) | (((cz + dz) & 1) << 2);
+            need = (int)((S->phase_of >> (4 * col)) & 15u) < phase;
+        }
+        // (each waiting lane's acquire load, then the warp barrier, order this
+        // warp's later loads after the neighbours' released writes; the bins
+        // are read through L2)
+        const bool ok = !need || wait_ready(P.done + c_nb, epoch, P.wait_ns);
+        if (!__all_sync(kFull, ok)) {
+            if (tid == 0) atomicCAS(P.err, kErrNone, kErrTimeout);
+            return;
+        }
+    } else {
+        // the previous phase's moves are visible from here on
+        pdl_wait();
+    }
+    // the neighbour cells' entries, relative to this cell's origin: up to four
+    // per cell in one round, any further ones after it
+    if (tid < n_st && tid != t_own) {
+        const float fx = (float)dx * w32, fy = (float)dy * w32, fz = (float)dz * w32;
+        const float4 *b = P.bins + (size_t)c_nb * P.cap;
+        auto stage = [&](const float4 v, int s) {
+            const int slot = base + s;
+            if (kChecked) {
+                const int j = __float_as_int(v.w);
+                // a candidate of this replica, binned in this very cell this sweep
+                if (HPMC_CHECK_FAILS(P, slot < cand_cap(CAP), 2)) return;
+                (void)HPMC_CHECK_FAILS(P, j >= R.off && j < R.off + R.n, 3);
+                (void)HPMC_CHECK_FAILS(P, P.binpos == nullptr || (j >= 0 && j < P.n_total &&
+                                                            P.binpos[j] / P.cap == c_nb), 4);
+                // Sec. III.E: no other cell of the neighbourhood is active in
+                // this phase (the own cell is staged above)
+                const int col = ((cx + dx) & 1) | (((cy + dy) & 1) << 1) | (((cz + dz) & 1) << 2);
+                const int own_col = (cx & 1) | ((cy & 1) << 1) | ((cz & 1) << 2);
+                (void)HPMC_CHECK_FAILS(P, col != own_col, 5);
+            }
+            s_cpos[slot] = make_float4(fx + v.x, fy + v.y, fz + v.z, v.w);
+        };
+        float4 e0 = make_float4(0.f, 0.f, 0.f, 0.f), e1 = e0, e2 = e0, e3 = e0;
+        if (m_nb > 0) e0 = __ldcg(b);
+        if (m_nb > 1) e1 = __ldcg(b + 1);
+        if (m_nb > 2) e2 = __ldcg(b + 2);
+        if (m_nb > 3) e3 = __ldcg(b + 3);
+        if (m_nb > 0) stage(e0, 0);
+        if (m_nb > 1) stage(e1, 1);
+        if (m_nb > 2) stage(e2, 2);
+        if (m_nb > 3) stage(e3, 3);
+        for (int s = 4; s < m_nb; ++s) stage(__ldcg(b + s), s);
+    }
+    cta_sync<WARP>();
 
     uint32_t c_acc = 0, c_cell = 0, c_ov = 0, c_dep = 0, c_cb = 0, c_eval = 0, c_block = 0,
              c_fwd = 0, c_rev = 0, c_cap = 0, c_rck = 0;
@@ -1029,7 +1074,10 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? ((CB || SOFT) 
             DepOutcome o = {1.0, 0, 0, 0u, 0u, 0u, 0u, 0u, 0u};
             // a6: the lens points in depletant order; one free of every
             // neighbour blocks the move (or enters the CB weight)
-            const int n_lens = hd.z;
+            int n_lens = hd.z;
+            if (HPMC_CHECK_FAILS(P, n_lens >= 0 && n_lens <= P.lens_cap &&
+                                        (s_loff[qb] < 0 || s_loff[qb] + n_lens <= kMaxLensCTA), 7))
+                n_lens = 0;
             const float4 *lens = s_loff[qb] >= 0 ? s_lens + s_loff[qb]
                                                 : P.lens + (size_t)i * P.lens_cap;
             if (!CB && !WARP) {
@@ -1177,6 +1225,7 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? ((CB || SOFT) 
     const int nacc = s_nacc;
     for (int a = tid; a < nacc; a += nthr) {
         const int j = s_accl[a];
+        if (HPMC_CHECK_FAILS(P, a < CAP && j >= R.off && j < R.off + R.n, 8)) continue;
         P.pos[j] = P.prop_pos[j];
     }
 
@@ -1198,6 +1247,132 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? ((CB || SOFT) 
     cnt[kCapHits] = c_cap;
     cnt[kRechecks] = c_rck;
     flush_counters(P, r, cnt);
+}
+
+// One colour phase (FP32 form): a CTA per active cell, the cells of every
+// replica in the task table's order (fullest cells first).
+template <bool CB, bool WARP, int CAP, bool SOFT = false>
+__global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? ((CB || SOFT) ? 16 : 32) : 1)
+    k_phase_sphere_fp32(const __grid_constant__ SimParams P, int phase)
+{
+    // The phases are launched with programmatic dependent launch: the next
+    // phase's CTAs may start while this one drains.  Everything read before
+    // pdl_wait() is fixed for the whole sweep (task table, populations, replica
+    // record, lens headers, displacements and lens points); positions (bins,
+    // FP64 state) are read and written only after it.
+    pdl_trigger();
+    if (phase == 7 && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(P.sweep, 1ull);
+    int cls = 0, idx = blockIdx.x;
+    {
+        const int4 cc = reinterpret_cast<const int4 *>(P.cls_count)[phase];
+        if (idx >= cc.x) {
+            idx -= cc.x;
+            cls = 1;
+            if (idx >= cc.y) {
+                idx -= cc.y;
+                cls = 2;
+                if (idx >= cc.z) {
+                    idx -= cc.z;
+                    cls = 3;
+                }
+            }
+        }
+    }
+    const int4 tk = P.task_ord[(size_t)(phase * 4 + cls) * P.n_cta + idx];
+    if (cls == 3) {               // an empty cell: only its next-sweep population
+        if (threadIdx.x == 0) P.count[(tk.w >> 16) ^ 1][tk.x] = 0;
+        return;
+    }
+    phase_cell<CB, WARP, CAP, SOFT, false>(P, phase, tk, 0u);
+}
+
+// All eight colour phases of a sweep in one persistent launch of one-warp
+// CTAs.  The work items are the non-empty active cells, in phase order and,
+// within a phase, fullest cells first; a CTA takes the next item from a
+// ticket counter and waits only for the non-empty stencil cells of earlier
+// phases (readiness counters, bounded waits), so a cell of phase p + 1 starts
+// as soon as its own neighbourhood has finished phase p instead of after the
+// whole grid has.  Deadlock-free for any grid size and residency: an item
+// waits only for items with smaller tickets, all taken earlier by CTAs that
+// are running (a CTA works through its chunk in order), and the smallest
+// unfinished item never waits.
+template <bool CB, int CAP, bool SOFT = false>
+__global__ void __launch_bounds__(32, (CB || SOFT) ? 16 : 32)
+    k_sweep_sphere_fp32(const __grid_constant__ SimParams P)
+{
+    const int lane = threadIdx.x;
+    pdl_wait();
+    const uint32_t epoch0 = ld_acquire_u32(P.epoch);
+    const int par = (int)(P.sched[0].sweep & 1u);
+    // the next sweep's cell populations start from zero
+    int *next = P.count[par ^ 1];
+    for (int c = blockIdx.x * 32 + lane; c < P.n_cells; c += gridDim.x * 32) next[c] = 0;
+    if (blockIdx.x == 0 && lane == 0) atomicAdd(P.sweep, 1ull);
+    // non-empty tasks per phase (population classes 0..2): their exclusive
+    // prefix over the phases and the first two class sizes, kept in shared
+    // memory (registers are the phase work's)
+    __shared__ int s_start[9], s_n0[8], s_n1[8];
+    __shared__ uint32_t s_epoch;
+    __shared__ int s_cell;
+    {
+        int ne = 0;
+        int4 cc = make_int4(0, 0, 0, 0);
+        if (lane < 8) {
+            cc = reinterpret_cast<const int4 *>(P.cls_count)[lane];
+            ne = cc.x + cc.y + cc.z;
+        }
+        int incl = ne;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane < 8) {
+            s_start[lane + 1] = incl;
+            s_n0[lane] = cc.x;
+            s_n1[lane] = cc.y;
+        }
+        if (lane == 0) {
+            s_start[0] = 0;
+            s_epoch = epoch0;
+        }
+        __syncwarp();
+    }
+    // tickets are taken in chunks of P.ticket_chunk consecutive items (one
+    // atomic per chunk: the counter is a single hot address), processed in
+    // order, which keeps the schedule deadlock-free; the next chunk is
+    // claimed while the current item runs (its atomic's latency hidden)
+    const int chunk = P.ticket_chunk;
+    int t = 0, t_end = 0, t_ahead = 0;
+    if (lane == 0) t_ahead = atomicAdd(P.ticket, chunk);
+    while (true) {
+        if (t == t_end) {
+            t = __shfl_sync(kFull, t_ahead, 0);
+            t_end = t + chunk;
+            if (lane == 0 && t < s_start[8]) t_ahead = atomicAdd(P.ticket, chunk);
+        }
+        if (t >= s_start[8]) break;
+        // the ticket's phase: the number of phases that end at or before t
+        const int phase = __popc(__ballot_sync(kFull, lane < 8 && s_start[lane + 1] <= t));
+        int idx = t - s_start[phase], cls = 0;
+        const int n0 = s_n0[phase], n1 = s_n1[phase];
+        if (idx >= n0) {
+            idx -= n0;
+            cls = 1;
+            if (idx >= n1) {
+                idx -= n1;
+                cls = 2;
+            }
+        }
+        const int4 tk = P.task_ord[(size_t)(phase * 4 + cls) * P.n_cta + idx];
+        if (lane == 0) s_cell = tk.x;
+        phase_cell<CB, true, CAP, SOFT, true>(P, phase, tk, s_epoch);
+        // publish the cell: every lane's writes first, then its readiness
+        // (a cell withheld for a test of the bounded waits is never published)
+        __syncwarp();
+        if (lane == 0 && s_cell != P.withhold) st_release_u32(P.done + s_cell, s_epoch);
+        ++t;
+    }
 }
 
 // Configuration check (positions in the box, no overlapping pair), FP32

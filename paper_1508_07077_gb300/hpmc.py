@@ -16,21 +16,25 @@ import numpy as np
 
 _LIBDIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib")
 LIB_PATH = os.path.join(_LIBDIR, "libhpmc_dep.so")
+# the same library with bounds and checkerboard-invariant checks (HPMC_CHECKED)
+CHECKED_LIB_PATH = os.path.join(_LIBDIR, "libhpmc_dep_checked.so")
 
 HPMC_OK = 0
 HPMC_SPHERE, HPMC_HEMISPHERE, HPMC_SPHEROID = 0, 1, 2
 HPMC_FP64, HPMC_FP32_RECHECK = 0, 1
 HPMC_HOST, HPMC_DEVICE = 0, 1
 HPMC_V0_CIRCUMSPHERE, HPMC_V0_SHELL, HPMC_V0_CUBE = 0, 1, 2
+HPMC_PHASES_LAUNCHES, HPMC_PHASES_PERSISTENT = 0, 1
 
 EXPORTS = ("hpmc_init", "hpmc_init_batch", "hpmc_get_replica", "hpmc_set_replica_moves",
            "hpmc_set_shape", "hpmc_set_depletant", "hpmc_set_moves",
-           "hpmc_set_cells", "hpmc_set_launch", "hpmc_autotune", "hpmc_set_fp32_margin",
+           "hpmc_set_cells", "hpmc_set_launch", "hpmc_set_wait_limit",
+           "hpmc_debug_withhold_cell", "hpmc_autotune", "hpmc_set_fp32_margin",
            "hpmc_set_v0", "hpmc_set_soft", "hpmc_set_live", "hpmc_get_live", "hpmc_gibbs_exchange",
            "hpmc_get_gibbs", "hpmc_set_timing",
            "hpmc_get_timing", "hpmc_sweep", "hpmc_get_state",
            "hpmc_set_state", "hpmc_reset_counters", "hpmc_sync", "hpmc_cell_list",
-           "hpmc_cell_list_noalloc", "hpmc_philox", "hpmc_free_volume", "hpmc_get_size", "hpmc_strerror",
+           "hpmc_cell_list_noalloc", "hpmc_philox", "hpmc_kernel_arch", "hpmc_free_volume", "hpmc_get_size", "hpmc_strerror",
            "hpmc_destroy")
 
 
@@ -62,6 +66,7 @@ class hpmc_counters(ctypes.Structure):
 
 
 _lib = None
+_lib_path = LIB_PATH
 
 
 def load(path: str = LIB_PATH):
@@ -85,6 +90,8 @@ def load(path: str = LIB_PATH):
     L.hpmc_set_moves.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.hpmc_set_cells.argtypes = [vp, ip]
     L.hpmc_set_launch.argtypes = [vp, ip, ip]
+    L.hpmc_set_wait_limit.argtypes = [vp, ctypes.c_double]
+    L.hpmc_debug_withhold_cell.argtypes = [vp, ip]
     L.hpmc_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ip, ctypes.POINTER(ctypes.c_int),
                                 ip, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_double)]
@@ -109,6 +116,7 @@ def load(path: str = LIB_PATH):
                                  ctypes.c_uint32, ctypes.c_uint64, vp, vp, vp]
     L.hpmc_cell_list_noalloc.argtypes = L.hpmc_cell_list.argtypes
     L.hpmc_philox.argtypes = [ip, vp, vp, vp, ip, vp]
+    L.hpmc_kernel_arch.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.hpmc_free_volume.argtypes = [vp, ip, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
                                    ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
     L.hpmc_get_size.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
@@ -119,8 +127,20 @@ def load(path: str = LIB_PATH):
     for name in EXPORTS:
         if name not in ("hpmc_strerror", "hpmc_destroy"):
             getattr(L, name).restype = ctypes.c_int
+    global _lib_path
     _lib = L
+    _lib_path = path
     return L
+
+
+def use(path: str = LIB_PATH):
+    """Make the binding call the library at `path` (e.g. CHECKED_LIB_PATH)
+    from now on; returns the path it used before."""
+    global _lib, _lib_path
+    prev = _lib_path
+    _lib = None
+    load(path)
+    return prev
 
 
 def strerror(code: int) -> str:
@@ -251,9 +271,17 @@ def hpmc_free_volume(ctx, q, *, replica=0, seed=7, sample=0, n_probe=1000000):
     return out.value, int(n_probe)
 
 
-def hpmc_set_launch(ctx, warps_per_colloid, attempts_per_thread=1):
-    _check(load().hpmc_set_launch(ctx, int(warps_per_colloid), int(attempts_per_thread)),
+def hpmc_set_launch(ctx, warps_per_colloid, phase_schedule=HPMC_PHASES_LAUNCHES):
+    _check(load().hpmc_set_launch(ctx, int(warps_per_colloid), int(phase_schedule)),
            "hpmc_set_launch")
+
+
+def hpmc_set_wait_limit(ctx, seconds):
+    _check(load().hpmc_set_wait_limit(ctx, float(seconds)), "hpmc_set_wait_limit")
+
+
+def hpmc_debug_withhold_cell(ctx, cell):
+    _check(load().hpmc_debug_withhold_cell(ctx, int(cell)), "hpmc_debug_withhold_cell")
 
 
 def hpmc_set_fp32_margin(ctx, margin):
@@ -449,6 +477,14 @@ def hpmc_philox(ctr_dev, key_dev, out_dev, variant=0, stream=None):
                               int(variant), _stream(stream)), "hpmc_philox")
 
 
+def hpmc_kernel_arch():
+    """(binary version, PTX version) of the library's kernels on the current
+    device, as the CUDA runtime reports them."""
+    b, p = ctypes.c_int(), ctypes.c_int()
+    _check(load().hpmc_kernel_arch(ctypes.byref(b), ctypes.byref(p)), "hpmc_kernel_arch")
+    return b.value, p.value
+
+
 def hpmc_destroy(ctx):
     if ctx:
         load().hpmc_destroy(ctx)
@@ -459,7 +495,8 @@ class Sampler:
 
     def __init__(self, pos, box_l, *, quat=None, shape=HPMC_SPHERE, shape_params=(1.0,),
                  q=0.0, n_r=0.0, n_trial=0, d_max=0.1, a_max=0.0, p_translate=1.0,
-                 seed=1, replica=0, precision=HPMC_FP64, n_cell=0, warps=1, ilp=1, device=0,
+                 seed=1, replica=0, precision=HPMC_FP64, n_cell=0, warps=1,
+                 schedule=HPMC_PHASES_LAUNCHES, device=0,
                  v0=HPMC_V0_CIRCUMSPHERE, soft_eps=0.0):
         pos = np.ascontiguousarray(pos, dtype=np.float64) if isinstance(pos, np.ndarray) else pos
         if isinstance(quat, np.ndarray):
@@ -472,7 +509,7 @@ class Sampler:
             hpmc_set_depletant(self.ctx, q, n_r, n_trial)
             hpmc_set_moves(self.ctx, d_max, a_max, p_translate)
             hpmc_set_cells(self.ctx, n_cell)
-            hpmc_set_launch(self.ctx, warps, ilp)
+            hpmc_set_launch(self.ctx, warps, schedule)
             if v0 != HPMC_V0_CIRCUMSPHERE:
                 hpmc_set_v0(self.ctx, v0)
             if soft_eps:

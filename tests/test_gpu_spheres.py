@@ -27,10 +27,11 @@ def lib():
 PRECISIONS = [0, 1]   # HPMC_FP64, HPMC_FP32_RECHECK
 
 
-def _compare(oracle, lib, s, sweeps, *, n_trial=0, d_max=0.05, warps=1, ilp=1, n_cell=0,
+def _compare(oracle, lib, s, sweeps, *, n_trial=0, d_max=0.05, warps=1, schedule=1, n_cell=0,
              seed=1, precision=0, sweep0=0, margin=0.0):
     smp = lib.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, n_trial=n_trial, d_max=d_max,
-                      seed=seed, warps=warps, ilp=ilp, n_cell=n_cell, precision=precision)
+                      seed=seed, warps=warps, schedule=schedule, n_cell=n_cell,
+                      precision=precision)
     if margin:
         lib.hpmc_set_fp32_margin(smp.ctx, margin)
     if sweep0:
@@ -99,10 +100,10 @@ def test_many_reinsertion_trials(oracle, lib, warps, precision):
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
-@pytest.mark.parametrize("warps,ilp", [(1, 1), (1, 2), (3, 2), (8, 1), (8, 2)])
-def test_launch_shape_does_not_change_results(oracle, lib, warps, ilp, precision):
+@pytest.mark.parametrize("warps,schedule", [(1, 1), (1, 0), (3, 1), (8, 1), (8, 0)])
+def test_launch_shape_does_not_change_results(oracle, lib, warps, schedule, precision):
     for n_trial in (0, 2):
-        _compare(oracle, lib, W.spheres_256(), 10, warps=warps, ilp=ilp, n_trial=n_trial,
+        _compare(oracle, lib, W.spheres_256(), 10, warps=warps, schedule=schedule, n_trial=n_trial,
                  precision=precision)
 
 
@@ -156,15 +157,17 @@ def test_fp32_margin_below_bound_rejected(lib):
     smp.close()
 
 
-def test_timing_mode_counts_launches(lib):
+@pytest.mark.parametrize("schedule,phase_launches", [(0, 8), (1, 1)])
+def test_timing_mode_counts_launches(lib, schedule, phase_launches):
+    """Eight colour-phase launches per sweep, or one persistent launch."""
     s = W.spheres_256()
-    smp = lib.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, precision=1)
+    smp = lib.Sampler(s.pos, s.L, q=s.q, n_r=s.n_r, precision=1, schedule=schedule)
     smp.sweep(1)
     lib.hpmc_set_timing(smp.ctx, True)
     smp.sweep(3)
     ms, n = lib.hpmc_get_timing(smp.ctx)
     smp.close()
-    assert n == [3, 24, 3] and ms[0] > 0 and ms[1] > 0 and ms[2] > 0
+    assert n == [3, 3 * phase_launches, 3] and ms[0] > 0 and ms[1] > 0 and ms[2] > 0
 
 
 def test_resume_and_device_io(oracle, lib):
