@@ -68,3 +68,11 @@ def test_empty_and_invalid(lib):
     k = torch.zeros((2, 2), dtype=torch.int32, device="cuda")
     with pytest.raises(lib.HPMCError):
         lib.hpmc_philox(c, k, torch.zeros_like(c), variant=2)
+
+
+def test_library_kernels_are_sm103(lib):
+    """The runtime reports the kernels' binary as compiled for compute
+    capability 10.3 (sm_103a) from the 10.3 virtual architecture."""
+    binary, ptx = lib.hpmc_kernel_arch()
+    assert binary == 103
+    assert ptx in (0, 103)
