@@ -2,23 +2,34 @@
 """Throughput of the implicit-depletant HPMC hot path on one or more GB300s.
 
 Metric: colloid trial moves/s (whole job), with depletant insertions/s (drawn
-and evaluated) alongside, at fixed (phi_c, q, eta_r).
+and evaluated) alongside, at fixed state points (phi_c, q, eta_r).
 
-Workload: 16384 hard spheres, phi_c = 0.30, depletant size ratio q = 0.15,
-reservoir packing fraction eta_r in {0.1, 0.2, 0.3, 0.4} (four independent
-systems), translation step tuned (untimed) to ~30% acceptance, n_trial = 0,
-FP32 + certified-margin form (``--precision fp64`` for the plain FP64 form).
-One step = one checkerboard sweep of each of the four systems (4 x 16384
-trial moves), run as one batch of four independent replicas.  Synthetic,
-seeded inputs (fcc start, melted during tuning).
+Headline workload (default, ``--workload batched``): 128 independent
+hard-sphere replicas, N log-uniform in [500, 20000] (sum 621288 colloids),
+phi_c U[0.1, 0.45], q in {0.1, 0.15, 0.2}, eta_r U[0.05, 0.4], all from one
+seed, in one batch (one set of launches per sweep, recorded as a CUDA graph),
+FP32 certified form with FP64 re-checks, n_trial = 0.  A step is one
+checkerboard sweep of every replica.  Before timing, a fixed step-size
+procedure runs (from the fcc starts, TUNE_ROUNDS rounds of TUNE_SWEEPS
+sweeps, each replica's d_max scaled from its own acceptance counters towards
+30%), then W warm-up sweeps.  The procedure uses only trajectory counters, so
+any implementation of the method that reproduces the trajectories (the CPU
+oracle does, bit for bit) arrives at the same step sizes and the same start.
 
-Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on
-the launching stream, with a 256 MB buffer written between steps to flush L2
-(the working set itself is L2-resident).  Multi-GPU (torchrun): every rank
-runs its own replicas (weak scaling); barrier + max over ranks.
+Beside the headline, on the same JSON line (N = 1): the same replicas one at
+a time, the 4 x 16384-sphere workload (FP32 form, shell V_0, plain FP64 form),
+32768 hemispheres and 65536 discoids with rotations.
 
-``--impl reference`` times the CPU oracle (oracle/) on this host on a bounded
-sample of the same workload: it is the reference arm of this repository.
+Timing: W untimed warm-up steps, then the K-step loop bracketed by CUDA
+events on the launching stream with a 256 MB buffer written between steps
+(L2 flush); the K-step loop is repeated until the timed region has lasted
+at least a second (``repeats``), so that the clock sampler sees the load.
+Multi-GPU (torchrun): every rank runs its own 128 replicas (weak scaling);
+barrier + max over ranks.
+
+``--impl reference`` times the CPU oracle (oracle/) on this host's cores on
+the same workload, after the same step-size procedure: the reference arm of
+this repository.
 """
 from __future__ import annotations
 
@@ -30,43 +41,69 @@ import statistics
 import subprocess
 import sys
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-ETAS = (0.1, 0.2, 0.3, 0.4)
-N, PHI, Q = 16384, 0.30, 0.15
-WORKLOAD = "spheres_16384_phi0.30_q0.15_eta0.1-0.4"
-# Translation steps giving ~30% acceptance at each eta_r (from the untimed
-# tuner on the GPU); the reference arm uses them as fixed values.
-D_MAX_TUNED = {0.1: 0.0160, 0.2: 0.0080, 0.3: 0.0053, 0.4: 0.0040}
 ACC_TARGET = 0.30
+TUNE_ROUNDS, TUNE_SWEEPS, D_START = 8, 5, 0.01
+N_REPLICAS = 128
+BATCHED = "batched_128_spheres_N500-20000_phi0.10-0.45_q0.10-0.20_eta0.05-0.40"
 
-# Algorithmic ALU lane-operations (roofline):
-#  lens kernel, per depletant drawn: 6/pi attempts x (Philox4x32-10: 40,
-#  point in the cube + ball test: 11) + old-pose test (8); per move: move and
-#  Poisson Philox (2 x 40), proposal and cell check (20), Poisson search (12)
-OPS_PER_DEP = 6.0 / math.pi * (40.0 + 11.0) + 8.0
-OPS_PER_MOVE_LENS = 2 * 40.0 + 20.0 + 12.0
-#  colour-phase kernel, per move: proposal and cell check (20), ~25 neighbour
-#  candidates x 8 (overlap test)
-OPS_PER_MOVE_PHASE = 20.0 + 25 * 8.0
-#  FP64 plain form (one kernel): everything above per evaluated depletant
-OPS_PER_MOVE = 2 * 40.0 + 20.0 + 12.0 + 25 * 8.0
-ISSUE_LANES_PER_SM = 128        # 4 SM sub-partitions x 32 lanes, one instruction / clock
-BYTES_PER_MOVE = 2 * 32 + 16 + 2 * 4   # pos (double4) read + cell-local copy + cell list ids
-# DRAM bytes (read + write) per launch from one ncu capture of the current kernel
-# build on the four-state-point 16384-sphere batch, in the timed steps' conditions
-# (ncu --cache-control none; the mean over the 8 phases of a sweep that starts
-# after the 256 MB L2 flush; profiles/k_phase_sphere_fp32_*.md).
-MEASURED_TRAFFIC = {"k_phase_sphere_fp32": 5.44e6, "k_lens_sphere_fp32": 11.88e6}
+# Algorithmic ALU lane-operations per unit of work (the method's required
+# arithmetic, counted from its operations, not from what a kernel skips):
+#  Philox4x32-10 with the round keys precomputed: 10 rounds x (two 32x32
+#  multiplies giving both halves of the product, two three-input XORs)
+OPS_PHILOX = 40.0
+#  an attempt of a depletant stream: one Philox call, three coordinates from
+#  the words (3 x 3) and the ball test (3 FMA-type ops + compare): 13 more
+OPS_ATTEMPT = OPS_PHILOX + 13.0
+#  an accepted point: the new- and old-pose tests (difference, squared length,
+#  compare)
+OPS_DEP = 8.0
+#  per move in the lens kernel: the move and Poisson draws, the proposal and
+#  its cell test, the Poisson table search
+OPS_MOVE_LENS = 2 * OPS_PHILOX + 20.0 + 12.0
+#  per move in the colour phases: cell test, ~25 neighbour-pair tests (8
+#  ops), the lens points against the neighbours near the move (~5 x 8)
+OPS_MOVE_PHASE = 20.0 + 25 * 8.0 + 5 * 8.0
+#  mean attempts per point of the ball: the cube-to-ball volume ratio
+ATTEMPTS_PER_POINT = 6.0 / math.pi
+#  FP64 form: FP64 instructions per attempt (coordinates 3 x 2, ball test 5)
+#  and per accepted point (the pose tests, 2 x 5)
+FP64_PER_ATTEMPT, FP64_PER_DEP = 11.0, 10.0
+# Algorithmic HBM bytes per move: the FP64 pose read and written (2 x 32),
+# the FP32 cell-relative copy (16), the cell-list entries (2 x 4)
+BYTES_PER_MOVE = 2 * 32 + 16 + 2 * 4
+# DRAM bytes (read + write) per launch of the headline's dominant kernel from
+# the committed ncu capture of the current build (profiles/), or None.
+MEASURED_TRAFFIC: dict = {}
 
 
 def _dist():
     from paper_1508_07077_gb300 import replicas
     return replicas.world()
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 class ClockSampler:
@@ -79,6 +116,7 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.lines = []
 
     def __enter__(self):
         try:
@@ -123,50 +161,147 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sms)}
 
 
-def cpu_oracle_rate(systems, d_max, sweeps, first_sweep=0, v0_mode=0, soft_eps=0.0):
-    """Moves/s and insertions/s of the serial oracle on this host (1 core)."""
-    from oracle import oracle as O
-    O.build()
+# --- the step-size procedure (identical on every implementation) -------------
+
+def cell_width(L: float, q: float) -> float:
+    """Width of the largest even checkerboard grid with cells >= 1 + q."""
+    nc = int(L / (1.0 + q))
+    nc -= nc & 1
+    return L / nc
+
+
+def tune_update(d: float, accept: int, moves: int, w: float) -> float:
+    """One round of the step-size rule: scale towards 30% acceptance (at most
+    a factor 2 either way), kept in [1e-4, w / 4]."""
+    acc = accept / max(1, moves)
+    d = d * min(2.0, max(0.5, (acc + 0.02) / (ACC_TARGET + 0.02)))
+    return min(max(d, 1e-4), 0.25 * w)
+
+
+def batched_workload(rank: int = 0):
+    from paper_1508_07077_gb300 import replicas as R, workloads as W
+    reps = W.batched_replicas(N_REPLICAS, seed=1)
+    keys = R.replica_ids(N_REPLICAS, rank)
+    widths = [cell_width(s.L, s.q) for s in reps]
+    return reps, keys, widths
+
+
+# --- CPU oracle legs ------------------------------------------------------------
+
+class OracleBatch:
+    """The 128 replicas advanced by the CPU oracle, one replica per task on a
+    pool of host threads (replicas are independent; the oracle's C code runs
+    without the interpreter lock), or serially on one core."""
+
+    def __init__(self, reps, keys, cores):
+        from oracle import oracle as O
+        O.build()
+        self.O = O
+        self.reps, self.keys, self.cores = reps, keys, cores
+        self.pos = [s.pos.copy() for s in reps]
+        self.sweep = 0
+
+    def run(self, d, n_sweeps, cores=None):
+        """n_sweeps sweeps of every replica with step sizes d; returns the
+        per-replica counters."""
+        cores = self.cores if cores is None else cores
+        s0 = self.sweep
+
+        def one(r):
+            s = self.reps[r]
+            p, _, c, _ = self.O.run(self.pos[r], s.L, q=s.q, n_r=s.n_r, d_max=d[r], seed=1,
+                                    replica=self.keys[r], sweep0=s0, n_sweeps=n_sweeps)
+            return p, c
+
+        order = sorted(range(len(self.reps)), key=lambda r: -self.reps[r].n)
+        if cores > 1:
+            with ThreadPoolExecutor(max_workers=cores) as ex:
+                res = dict(zip(order, ex.map(one, order)))
+        else:
+            res = {r: one(r) for r in order}
+        self.sweep += n_sweeps
+        cnts = []
+        for r in range(len(self.reps)):
+            self.pos[r] = res[r][0]
+            cnts.append(res[r][1])
+        return cnts
+
+    def tune(self, widths):
+        d = [D_START] * len(self.reps)
+        for _ in range(TUNE_ROUNDS):
+            cnts = self.run(d, TUNE_SWEEPS)
+            d = [tune_update(d[r], c["accept"], c["moves"], widths[r]) for r, c in enumerate(cnts)]
+        return d
+
+
+def cpu_baseline_batched(d_gpu, warmup, rank):
+    """The oracle on this host: the step-size procedure and the warm-up sweeps
+    on all cores, then one sweep of every replica on all cores (timed, 3
+    times) and the same first sweep on one core (timed); the one-core and
+    all-core results must be identical."""
+    reps, keys, widths = batched_workload(rank)
+    cores = os.cpu_count() or 1
+    ob = OracleBatch(reps, keys, cores)
     t0 = time.perf_counter()
-    moves = drawn = evaluated = 0
-    for s in systems:
-        _, _, c, _ = O.run(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=d_max[s.extra["eta_r"]],
-                           seed=s.seed, replica=s.replica, n_sweeps=sweeps, sweep0=first_sweep,
-                           v0_mode=v0_mode, soft_eps=soft_eps)
-        moves += c["moves"]
-        drawn += c["dep_drawn"]
-        evaluated += c["dep_evaluated"]
-    dt = time.perf_counter() - t0
-    return moves / dt, drawn / dt, evaluated / dt, dt, moves
+    d = ob.tune(widths)
+    ob.run(d, warmup)
+    prep_s = time.perf_counter() - t0
+    start = [p.copy() for p in ob.pos]
+    t0 = time.perf_counter()
+    c_all = ob.run(d, 1)
+    t_first = time.perf_counter() - t0
+    after_first = [p.copy() for p in ob.pos]
+    t0 = time.perf_counter()
+    ob.run(d, 2)
+    t_all = t_first + (time.perf_counter() - t0)
+    moves_all = 3 * sum(s.n for s in reps)
+    # one core, the same first sweep from the same state
+    ob.pos, ob.sweep = start, ob.sweep - 3
+    t0 = time.perf_counter()
+    c_one = ob.run(d, 1, cores=1)
+    t_one = time.perf_counter() - t0
+    identical = all(np.array_equal(a, b) for a, b in zip(ob.pos, after_first)) and all(
+        a == b for a, b in zip(c_all, c_one))
+    moves_one = sum(c["moves"] for c in c_one)
+    drawn = sum(c["dep_drawn"] for c in c_one)
+    return {
+        "value": moves_all / t_all, "unit": "moves/s", "cores": cores, "kind": "oracle",
+        "cpu": cpu_model(),
+        "sample": "the headline workload after the same step-size procedure and %d warm-up "
+                  "sweeps (%.1f s on %d cores): 3 sweeps of all 128 replicas on %d cores "
+                  "(%d moves, %.1f s), the first of them again on 1 core"
+                  % (warmup, prep_s, cores, cores, moves_all, t_all),
+        "one_core": {"value": moves_one / t_one, "unit": "moves/s", "cores": 1,
+                     "seconds": t_one, "insertions_drawn_per_s": drawn / t_one},
+        "one_core_equals_all_cores": bool(identical),
+        "step_sizes_equal_gpu": bool(d_gpu is not None and np.array_equal(np.array(d),
+                                                                          np.array(d_gpu))),
+    }
 
 
 def run_reference(args, ws, rank):
-    from paper_1508_07077_gb300 import workloads as W
+    """--impl reference: the oracle on this host's cores, same workload, same
+    step-size procedure and warm-up, K timed steps of one sweep of every
+    replica (replicas on a pool of threads)."""
     if rank != 0:
         return
-    systems = [W.spheres_16384(eta, seed=1) for eta in ETAS]
-    for s in systems:
-        s.extra["eta_r"] = round(s.extra["eta_r"], 1)
-    # each step: one sweep of one of the four systems (bounded CPU sample)
-    times, moves = [], 0
-    drawn = evaluated = 0
-    from oracle import oracle as O
-    O.build()
-    pos = {s.extra["eta_r"]: s.pos.copy() for s in systems}
-    for step in range(args.warmup + args.steps):
-        s = systems[step % len(systems)]
-        eta = s.extra["eta_r"]
+    if args.workload != "batched":
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the reference arm covers the headline workload (batched) only"}))
+        return
+    reps, keys, widths = batched_workload(0)
+    cores = os.cpu_count() or 1
+    ob = OracleBatch(reps, keys, cores)
+    d = ob.tune(widths)
+    ob.run(d, args.warmup)
+    times, moves, drawn, evaluated = [], 0, 0, 0
+    for _ in range(args.steps):
         t0 = time.perf_counter()
-        p, _, c, _ = O.run(pos[eta], s.L, q=s.q, n_r=s.n_r, d_max=D_MAX_TUNED[eta], seed=1,
-                           n_sweeps=1, sweep0=step // len(systems),
-                           v0_mode=1 if args.v0 == "shell" else 0)
-        dt = time.perf_counter() - t0
-        pos[eta] = p
-        if step >= args.warmup:
-            times.append(dt)
-            moves += c["moves"]
-            drawn += c["dep_drawn"]
-            evaluated += c["dep_evaluated"]
+        cnts = ob.run(d, 1)
+        times.append(time.perf_counter() - t0)
+        moves += sum(c["moves"] for c in cnts)
+        drawn += sum(c["dep_drawn"] for c in cnts)
+        evaluated += sum(c["dep_evaluated"] for c in cnts)
     total = sum(times)
     value = moves / total
     line = {
@@ -174,175 +309,419 @@ def run_reference(args, ws, rank):
         "unit": "moves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": "serial CPU oracle", "v0": args.v0,
-                   "step": "one sweep of one of the four eta_r systems (16384 moves)"},
+        "config": batched_config(),
         "insertions_drawn_per_s": drawn / total,
         "insertions_evaluated_per_s": evaluated / total,
-        "cpu_baseline": {"value": value, "unit": "moves/s", "cores": 1, "kind": "oracle",
-                         "sample": "%d sweeps x 16384 spheres, eta_r cycling 0.1..0.4"
-                                   % args.steps},
+        "cpu_baseline": {"value": value, "unit": "moves/s", "cores": cores, "kind": "oracle",
+                         "cpu": cpu_model(),
+                         "sample": "%d steps, each one sweep of all 128 replicas (%d moves), "
+                                   "replicas on %d threads" % (args.steps, moves, cores)},
         "e2e": {"value": value, "unit": "moves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
 
 
-def tune_batch(ctx, hpmc, d0, ns, rounds=12, sweeps=15):
-    """Untimed: melt the lattice starts and tune each replica's d_max to ~30%
-    acceptance (per-replica counters)."""
-    d = list(d0)
-    for _ in range(rounds):
-        for r, dr in enumerate(d):
-            hpmc.hpmc_set_replica_moves(ctx, r, dr, 0.0, 1.0)
-        hpmc.hpmc_reset_counters(ctx)
-        hpmc.hpmc_sweep(ctx, sweeps)
-        for r, n in enumerate(ns):
-            _, _, cnt = hpmc.hpmc_get_replica(ctx, r, n)
-            acc = cnt["accept"] / max(1, cnt["moves"])
-            d[r] = d[r] * min(2.0, max(0.5, (acc + 0.02) / (ACC_TARGET + 0.02)))
-    for r, dr in enumerate(d):
-        hpmc.hpmc_set_replica_moves(ctx, r, dr, 0.0, 1.0)
-    return d
+def batched_config():
+    return {"workload": BATCHED, "replicas": N_REPLICAS, "colloids": 621288,
+            "form": "FP32+FP64 recheck", "n_trial": 0,
+            "step": "1 sweep of every replica (621288 moves), one batch",
+            "start": "fcc starts, %d rounds x %d sweeps of the step-size rule (d_max from %g "
+                     "towards 30%% acceptance, per replica), then the warm-up sweeps"
+                     % (TUNE_ROUNDS, TUNE_SWEEPS, D_START),
+            "l2": "flushed between steps (256 MB write)"}
 
 
-def run_batched(args, ws, rank, local):
-    """128 independent sphere replicas (N log-uniform in [500, 20000], phi_c
-    U[0.1, 0.45], q in {0.1, 0.15, 0.2}, eta_r U[0.05, 0.4]) as one batch, vs the
-    same replicas one at a time (each in its own context, one stream)."""
-    import torch
-    import torch.distributed as dist
-    from paper_1508_07077_gb300 import build, hpmc, replicas as R, workloads as W
+# --- GPU helpers ---------------------------------------------------------------
 
-    if ws > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
+def load_lib():
+    from paper_1508_07077_gb300 import build, hpmc
     try:
         hpmc.load()
     except ImportError:
         build.build()
         hpmc.load()
-    prec = hpmc.HPMC_FP32_RECHECK if args.precision == "fp32" else hpmc.HPMC_FP64
-    stream = torch.cuda.current_stream()
-    reps = W.batched_replicas(128, seed=1)
-    descs = [{"n": s.n, "box_l": s.L, "pos": s.pos, "q": s.q, "n_r": s.n_r, "n_trial": 0,
-              "d_max": 0.01, "replica": R.replica_ids(128, rank)[k]}
-             for k, s in enumerate(reps)]
-    ctx = hpmc.hpmc_init_batch(descs, seed=1, precision=prec, device=local)
-    ns = [s.n for s in reps]
-    dtuned = tune_batch(ctx, hpmc, [0.01] * len(reps), ns, rounds=8, sweeps=10)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        hpmc.hpmc_sweep(ctx, 1, stream)
-    hpmc.hpmc_reset_counters(ctx)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
+    return hpmc
+
+
+def timed_steps(step, K, stream, flush, min_ms=0.0, ws=1):
+    """K steps bracketed by CUDA events (L2 flushed before each); the K-step
+    loop is repeated until min_ms of timed time (the same count on every
+    rank).  Returns (total ms, repeats)."""
+    import torch
+    import torch.distributed as dist
+
+    def one():
+        a = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        b = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        for k in range(K):
             flush.zero_()
             a[k].record(stream)
-            hpmc.hpmc_sweep(ctx, 1, stream)
+            step()
             b[k].record(stream)
         torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        return sum(x.elapsed_time(y) for x, y in zip(a, b))
+
+    from paper_1508_07077_gb300 import replicas as R
+    first = one()
+    reps = 1 if first >= min_ms else int(math.ceil(min_ms / max(first, 1e-3)))
+    reps = int(R.reduce_max([reps], "cuda")[0]) if ws > 1 else reps
+    total = first
+    for _ in range(reps - 1):
+        total += one()
+    return total, reps
+
+
+def kernel_times(hpmc, ctx, step, flush, n):
+    """Per-kernel milliseconds over n steps (kernels launched one by one with
+    events around them): (ms per kind, launches per kind, counters)."""
+    hpmc.hpmc_reset_counters(ctx)
+    hpmc.hpmc_set_timing(ctx, True)
+    for _ in range(n):
+        flush.zero_()
+        step()
+    km, kn = hpmc.hpmc_get_timing(ctx)
+    hpmc.hpmc_set_timing(ctx, False)
+    _, tc = hpmc.hpmc_get_state(ctx)
+    return km, kn, tc
+
+
+def lens_ops(tc):
+    """Algorithmic lane-ops of the lens kernel for counters tc."""
+    attempts = ATTEMPTS_PER_POINT * tc["dep_drawn"]
+    return OPS_ATTEMPT * attempts + OPS_DEP * tc["dep_drawn"] + OPS_MOVE_LENS * tc["moves"]
+
+
+def fp32_rooflines(km, kn, tc, pk):
+    """Per-kernel achieved lane-ops/s and fractions of the measured ceilings
+    (FP32 form): the lens kernel against the measured Philox-pipe ceiling
+    (round-key Philox calls/s x 40 lane-ops), the colour phases against the
+    measured FP32 issue ceiling (FFMA/s)."""
+    out = {}
+    philox_peak = pk["philox_rk_calls_per_s"] * OPS_PHILOX / 1e12
+    fp32_peak = pk["ffma_per_s"] / 1e12
+    if kn[2]:
+        a = lens_ops(tc) / (km[2] * 1e-3) / 1e12
+        out["k_lens_sphere_fp32"] = {"ms": km[2], "achieved": a, "peak": philox_peak,
+                                     "frac": a / philox_peak,
+                                     "peak_basis": "measured Philox4x32-10 (round keys) calls/s "
+                                                   "x 40 lane-ops"}
+    if kn[1]:
+        a = OPS_MOVE_PHASE * tc["moves"] / (km[1] * 1e-3) / 1e12
+        out["colour_phases"] = {"ms": km[1], "achieved": a, "peak": fp32_peak,
+                                "frac": a / fp32_peak,
+                                "hbm_gbs": BYTES_PER_MOVE * tc["moves"] / (km[1] * 1e-3) / 1e9,
+                                "peak_basis": "measured FP32 FMA/s (lane-ops)"}
+    return out
+
+
+# --- headline: 128 batched replicas -----------------------------------------------
+
+def run_batched(args, ws, rank, local):
+    import torch
+    import torch.distributed as dist
+    from paper_1508_07077_gb300 import peaks, replicas as R
+
     if ws > 1:
-        dist.barrier()
-    ms = sum(x.elapsed_time(y) for x, y in zip(a, b))
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    hpmc = load_lib()
+    pk = peaks.measure()
+    stream = torch.cuda.current_stream()
+    reps, keys, widths = batched_workload(rank)
+    ns = [s.n for s in reps]
+    n_all = sum(ns)
+    descs = [{"n": s.n, "box_l": s.L, "pos": s.pos, "q": s.q, "n_r": s.n_r, "n_trial": 0,
+              "d_max": D_START, "replica": keys[k]} for k, s in enumerate(reps)]
+    ctx = hpmc.hpmc_init_batch(descs, seed=1, precision=hpmc.HPMC_FP32_RECHECK, device=local)
+    hpmc.hpmc_set_launch(ctx, 1, args.schedule)
+    # the step-size procedure (the same rule the oracle legs replay)
+    d = [D_START] * len(reps)
+    for _ in range(TUNE_ROUNDS):
+        for r, dr in enumerate(d):
+            hpmc.hpmc_set_replica_moves(ctx, r, dr, 0.0, 1.0)
+        hpmc.hpmc_reset_counters(ctx)
+        hpmc.hpmc_sweep(ctx, TUNE_SWEEPS, stream)
+        cnts = [hpmc.hpmc_get_replica(ctx, r, n)[2] for r, n in enumerate(ns)]
+        d = [tune_update(d[r], c["accept"], c["moves"], widths[r]) for r, c in enumerate(cnts)]
+    for r, dr in enumerate(d):
+        hpmc.hpmc_set_replica_moves(ctx, r, dr, 0.0, 1.0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        hpmc.hpmc_sweep(ctx, 1, stream)
+
+    for _ in range(args.warmup):
+        step()
+    hpmc.hpmc_reset_counters(ctx)
+    with ClockSampler(local) as clk:
+        ms, repeats = timed_steps(step, args.steps, stream, flush, min_ms=1000.0, ws=ws)
     _, cnt = hpmc.hpmc_get_state(ctx)
-    # end to end through the C ABI with host buffers (pinned), copies timed
-    host_pos = torch.empty((sum(ns), 3), dtype=torch.float64).pin_memory().numpy()
-    sweep_e, _ = hpmc.hpmc_get_state(ctx, host_pos)
+    km, kn, tc = kernel_times(hpmc, ctx, step, flush, min(args.steps, 20))
+    # end to end through the C ABI with host (pinned) buffers: every step uploads
+    # all positions (checked), sweeps, and reads all positions and counters back
+    host_pos = torch.empty((n_all, 3), dtype=torch.float64).pin_memory().numpy()
+    sweep_now, _ = hpmc.hpmc_get_state(ctx, host_pos)
     e2e_steps = max(3, min(args.steps, 50) // 2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
-        hpmc.hpmc_set_state(ctx, host_pos, None, sweep_e + k, stream)
+        hpmc.hpmc_set_state(ctx, host_pos, None, sweep_now + k, stream)
         hpmc.hpmc_sweep(ctx, 1, stream)
         hpmc.hpmc_get_state(ctx, host_pos, None, stream)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    # one at a time
-    allpos = np.empty((sum(ns), 3))
-    sweep_now, _ = hpmc.hpmc_get_state(ctx, allpos)
-    singles, off = [], 0
-    for k, s in enumerate(reps):
-        smp = hpmc.Sampler(allpos[off:off + s.n].copy(), s.L, q=s.q, n_r=s.n_r,
-                           d_max=dtuned[k], seed=1, replica=descs[k]["replica"],
-                           precision=prec, device=local)
-        smp.sweep(1)
-        singles.append(smp)
-        off += s.n
-    torch.cuda.synchronize()
-    seq_steps = min(args.steps, 10)
-    sa = [torch.cuda.Event(enable_timing=True) for _ in range(seq_steps)]
-    sb = [torch.cuda.Event(enable_timing=True) for _ in range(seq_steps)]
-    for k in range(seq_steps):
-        flush.zero_()
-        sa[k].record(stream)
+    # the other schedule of the colour phases, same state (context)
+    other = None
+    if not args.no_extras:
+        hpmc.hpmc_set_launch(ctx, 1, 1 - args.schedule)
+        for _ in range(3):
+            step()
+        o_ms, _ = timed_steps(step, args.steps, stream, flush)
+        other = {"schedule": "eight launches per sweep" if args.schedule == 1
+                 else "one persistent launch per sweep",
+                 "value": args.steps * n_all / (o_ms * 1e-3), "ms_per_step": o_ms / args.steps}
+        hpmc.hpmc_set_launch(ctx, 1, args.schedule)
+    # the same replicas one at a time (each in its own context, one stream)
+    seq = None
+    if not args.no_extras:
+        allpos = np.empty((n_all, 3))
+        sweep_now, _ = hpmc.hpmc_get_state(ctx, allpos)
+        singles, off = [], 0
+        for k, s in enumerate(reps):
+            smp = hpmc.Sampler(allpos[off:off + s.n].copy(), s.L, q=s.q, n_r=s.n_r, d_max=d[k],
+                               seed=1, replica=keys[k], precision=hpmc.HPMC_FP32_RECHECK,
+                               schedule=args.schedule, device=local)
+            smp.sweep(1)
+            singles.append(smp)
+            off += s.n
+
+        def seq_step():
+            for smp in singles:
+                smp.sweep(1, stream)
+
+        seq_ms, _ = timed_steps(seq_step, min(args.steps, 10), stream, flush)
         for smp in singles:
-            smp.sweep(1, stream)
-        sb[k].record(stream)
-    torch.cuda.synchronize()
-    seq_ms = sum(x.elapsed_time(y) for x, y in zip(sa, sb))
-    for smp in singles:
-        smp.close()
-    # whole job: every rank's units over the slowest rank's time
-    ms, seq_ms, e2e_s = R.reduce_max([ms, seq_ms, e2e_s], "cuda")
+            smp.close()
+        seq = min(args.steps, 10) * n_all / (seq_ms * 1e-3)
+    hpmc.hpmc_destroy(ctx)
+
+    ms, e2e_s = R.reduce_max([ms, e2e_s], "cuda")
     moves_all, drawn_all, eval_all = R.reduce_sum(
         [cnt["moves"], cnt["dep_drawn"], cnt["dep_evaluated"]], "cuda")
+    line = None
     if rank == 0:
+        roof = fp32_rooflines(km, kn, tc, pk)
+        dominant = max(roof, key=lambda k: roof[k]["ms"])
+        dom = roof[dominant]
         value = moves_all / (ms * 1e-3)
+        # kind 0 is the cell-list pair of launches (bins, task order)
+        launches_per_step = (2 * kn[0] + kn[1] + kn[2]) / max(1, min(args.steps, 20))
         line = {
             "metric": "colloid trial moves/s", "value": value, "unit": "moves/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
-            "config": {"workload": "batched_128_spheres_N500-20000",
-                       "replicas": len(reps), "colloids": sum(ns),
-                       "step": "1 sweep of every replica, one batch (one set of launches)",
-                       "l2": "flushed between steps (256 MB write)"},
-            "one_at_a_time_moves_per_s": ws * seq_steps * sum(ns) / (seq_ms * 1e-3),
-            "e2e": {"value": ws * e2e_steps * sum(ns) / e2e_s, "unit": "moves/s",
-                    "h2d_bytes_per_step": int(host_pos.nbytes),
-                    "d2h_bytes_per_step": int(host_pos.nbytes)},
+            "ms_per_step": ms / (args.steps * repeats), "repeats": repeats,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": dict(batched_config(), schedule="persistent colour phases"
+                           if args.schedule == 1 else "eight phase launches per sweep",
+                           timed_region="the K-step loop repeated %d times (>= 1 s)" % repeats),
             "insertions_drawn_per_s": drawn_all / (ms * 1e-3),
             "insertions_evaluated_per_s": eval_all / (ms * 1e-3),
             "acceptance": cnt["accept"] / max(1, cnt["moves"]),
-            "gpu_launches": args.steps * (1 + (1 if prec == 1 else 0) + 8),
+            "fp64_rechecks_per_move": cnt["rechecks"] / max(1, cnt["moves"]),
+            "step_sizes": {"min": min(d), "median": statistics.median(d), "max": max(d)},
+            "gpu_launches": int(round(launches_per_step * args.steps * repeats)),
+            "kernels": {"cells_ms_per_step": km[0] / max(1, min(args.steps, 20)),
+                        "lens_ms_per_step": km[2] / max(1, min(args.steps, 20)),
+                        "phases_ms_per_step": km[1] / max(1, min(args.steps, 20)),
+                        "share": {"cells": km[0] / sum(km), "lens": km[2] / sum(km),
+                                  "phases": km[1] / sum(km)},
+                        "rooflines": roof},
+            "roofline": {"bound": "alu", "achieved": dom["achieved"], "peak": dom["peak"],
+                         "unit": "Tops/s", "frac": dom["frac"],
+                         "traffic": MEASURED_TRAFFIC.get(dominant), "kernel": dominant,
+                         "peak_basis": dom["peak_basis"] + " (of measured)"},
+            "pipe_peaks_measured": pk,
             "clocks": clk.summary(),
+            "e2e": {"value": ws * e2e_steps * n_all / e2e_s, "unit": "moves/s",
+                    "h2d_bytes_per_step": int(host_pos.nbytes),
+                    "d2h_bytes_per_step": int(host_pos.nbytes) + 8 * 16},
         }
-        print(json.dumps(line))
-    hpmc.hpmc_destroy(ctx)
+        if other is not None:
+            line["other_schedule"] = other
+        if seq is not None:
+            line["one_at_a_time_moves_per_s"] = seq
     if ws > 1:
         dist.destroy_process_group()
+    return line, d
 
+
+# --- extras: the single-system workloads ------------------------------------------
+
+def spheres_16384(args, local, pk):
+    """The four 16384-sphere state points (phi_c 0.30, q 0.15, eta_r 0.1..0.4)
+    as one batch: FP32 form (and its shell V_0), plain FP64 form; oracle on all
+    cores for 2 sweeps from the same tuned state."""
+    import torch
+    from paper_1508_07077_gb300 import workloads as W
+    hpmc = load_lib()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    etas = (0.1, 0.2, 0.3, 0.4)
+    systems = [W.spheres_16384(eta, seed=1) for eta in etas]
+    widths = [cell_width(s.L, s.q) for s in systems]
+    out = {"workload": "spheres_16384_phi0.30_q0.15_eta0.1-0.4 (4 x 16384, one batch)"}
+    K = min(args.steps, 20)
+    for prec in (1, 0):
+        descs = [{"n": s.n, "box_l": s.L, "pos": s.pos, "q": s.q, "n_r": s.n_r,
+                  "d_max": D_START, "replica": k} for k, s in enumerate(systems)]
+        ctx = hpmc.hpmc_init_batch(descs, seed=1, precision=prec, device=local)
+        d = [D_START] * 4
+        for _ in range(TUNE_ROUNDS):
+            for r, dr in enumerate(d):
+                hpmc.hpmc_set_replica_moves(ctx, r, dr, 0.0, 1.0)
+            hpmc.hpmc_reset_counters(ctx)
+            hpmc.hpmc_sweep(ctx, TUNE_SWEEPS, stream)
+            cnts = [hpmc.hpmc_get_replica(ctx, r, s.n)[2] for r, s in enumerate(systems)]
+            d = [tune_update(d[r], c["accept"], c["moves"], widths[r])
+                 for r, c in enumerate(cnts)]
+        for r, dr in enumerate(d):
+            hpmc.hpmc_set_replica_moves(ctx, r, dr, 0.0, 1.0)
+
+        def step():
+            hpmc.hpmc_sweep(ctx, 1, stream)
+
+        for _ in range(3):
+            step()
+        hpmc.hpmc_reset_counters(ctx)
+        ms, _ = timed_steps(step, K, stream, flush)
+        _, cnt = hpmc.hpmc_get_state(ctx)
+        km, kn, tc = kernel_times(hpmc, ctx, step, flush, K)
+        res = {"value": cnt["moves"] / (ms * 1e-3), "unit": "moves/s", "ms_per_step": ms / K,
+               "insertions_drawn_per_s": cnt["dep_drawn"] / (ms * 1e-3),
+               "acceptance": cnt["accept"] / max(1, cnt["moves"]),
+               "d_max": [round(x, 5) for x in d],
+               "kernel_ms_per_step": {"cells": km[0] / K, "phases": km[1] / K, "lens": km[2] / K}}
+        if prec == 1:
+            res["fp64_rechecks_per_move"] = cnt["rechecks"] / max(1, cnt["moves"])
+            res["rooflines"] = fp32_rooflines(km, kn, tc, pk)
+            hpmc.hpmc_set_v0(ctx, hpmc.HPMC_V0_SHELL)
+            for _ in range(3):
+                step()
+            hpmc.hpmc_reset_counters(ctx)
+            sms, _ = timed_steps(step, K, stream, flush)
+            _, sc = hpmc.hpmc_get_state(ctx)
+            res["shell_v0"] = {"value": sc["moves"] / (sms * 1e-3), "ms_per_step": sms / K,
+                               "insertions_drawn_per_s": sc["dep_drawn"] / (sms * 1e-3),
+                               "acceptance": sc["accept"] / max(1, sc["moves"])}
+            hpmc.hpmc_set_v0(ctx, hpmc.HPMC_V0_CIRCUMSPHERE)
+            out["fp32"] = res
+            # the oracle on all cores (cells of a colour phase on threads) from
+            # the same start and step sizes, 2 sweeps of each system
+            if not args.no_cpu_baseline:
+                from oracle import oracle as O
+                O.build()
+                cores = os.cpu_count() or 1
+                t0 = time.perf_counter()
+                moves = 0
+                for k, s in enumerate(systems):
+                    _, _, c, _ = O.run(s.pos, s.L, q=s.q, n_r=s.n_r, d_max=D_START, seed=1,
+                                       replica=k, n_sweeps=2, threads=cores)
+                    moves += c["moves"]
+                dt = time.perf_counter() - t0
+                out["cpu_oracle_all_cores"] = {"value": moves / dt, "unit": "moves/s",
+                                               "cores": cores,
+                                               "sample": "2 sweeps of each system from the "
+                                                         "fcc start at d_max %g" % D_START}
+        else:
+            fp64_peak = pk["dfma_per_s"] / 1e12
+            ops = (FP64_PER_ATTEMPT * ATTEMPTS_PER_POINT + FP64_PER_DEP) * tc["dep_evaluated"]
+            a = ops / (km[1] * 1e-3) / 1e12
+            res["roofline_fp64"] = {"kernel": "k_phase_sphere_fp64", "achieved": a,
+                                    "peak": fp64_peak, "unit": "T FP64 inst/s",
+                                    "frac": a / fp64_peak,
+                                    "peak_basis": "measured FP64 FMA/s (instructions)"}
+            out["fp64"] = res
+        hpmc.hpmc_destroy(ctx)
+    return out
+
+
+def shape_system(args, local, kind, pk):
+    """32768 hemispheres or 65536 discoids with rotations (a_max 0.2 rad,
+    p_translate 0.5), step size tuned, warps per colloid and cell count from
+    the autotuner, FP32 form."""
+    import torch
+    from paper_1508_07077_gb300 import workloads as W
+    hpmc = load_lib()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    s = W.hemispheres_32768(seed=1) if kind == "hemispheres" else W.discoids_65536(seed=1)
+    smp = hpmc.Sampler(s.pos, s.L, quat=s.quat, shape=s.shape, shape_params=s.shape_params,
+                       q=s.q, n_r=s.n_r, d_max=0.02, a_max=s.a_max, p_translate=s.p_translate,
+                       seed=1, precision=hpmc.HPMC_FP32_RECHECK, device=local)
+    ctx = smp.ctx
+    d = 0.02
+    for _ in range(6):
+        hpmc.hpmc_set_moves(ctx, d, s.a_max, s.p_translate)
+        hpmc.hpmc_reset_counters(ctx)
+        hpmc.hpmc_sweep(ctx, 5)
+        _, c = hpmc.hpmc_get_state(ctx)
+        d = min(0.1, d * min(2.0, max(0.5, (c["accept"] / max(1, c["moves"]) + 0.02) /
+                                      (ACC_TARGET + 0.02))))
+    hpmc.hpmc_set_moves(ctx, d, s.a_max, s.p_translate)
+    nc_auto = int(s.L / (1.0 + s.q)) & ~1
+    cells = (0, nc_auto - 2) if nc_auto > 4 else (0,)
+    warps, ncell, tuned_ms = hpmc.hpmc_autotune(ctx, warps=(1, 2), cells=cells, n_sweeps=3)
+
+    def step():
+        hpmc.hpmc_sweep(ctx, 1, stream)
+
+    K = min(args.steps, 10)
+    for _ in range(3):
+        step()
+    hpmc.hpmc_reset_counters(ctx)
+    ms, _ = timed_steps(step, K, stream, flush)
+    _, cnt = hpmc.hpmc_get_state(ctx)
+    km, kn, tc = kernel_times(hpmc, ctx, step, flush, K)
+    smp.close()
+    return {"workload": "%s_%d_phi%.2f_q%.2f_eta%.2f" % (kind, s.n, s.extra["phi_c"], s.q,
+                                                        s.extra["eta_r"]),
+            "value": cnt["moves"] / (ms * 1e-3), "unit": "moves/s", "ms_per_step": ms / K,
+            "insertions_drawn_per_s": cnt["dep_drawn"] / (ms * 1e-3),
+            "acceptance": cnt["accept"] / max(1, cnt["moves"]),
+            "fp64_rechecks_per_move": cnt["rechecks"] / max(1, cnt["moves"]),
+            "d_max": round(d, 5), "autotuned": {"warps_per_colloid": warps, "n_cell": ncell,
+                                                "ms_per_sweep": tuned_ms},
+            "kernel_ms_per_step": {"cells": km[0] / K, "phases": km[1] / K, "lens": km[2] / K}}
+
+
+# --- Gibbs-ensemble exchange (separate workload) ------------------------------------
 
 # Gibbs exchange kernel, per attempt of a depletant or CB-trial stream:
-# Philox (40) + ball test (11) + ~6 colloids within reach x 8 (point test).
-OPS_PER_GIBBS_TRIAL = 40.0 + 11.0 + 6 * 8.0
+# Philox, the ball test, ~6 colloids within reach x 8 (point test).
+OPS_PER_GIBBS_TRIAL = OPS_ATTEMPT + 6 * 8.0
 
 
 def run_gibbs(args, ws, rank, local):
     """Gibbs-ensemble coexistence runs (Sec. IV.B): 152 pairs (one CTA per
     pair) of two boxes of 512 spheres at phi_c = 0.12, q = 0.8, eta_r from
-    0.80 to 1.00 across the pairs (a scan through coexistence), n_trial =
-    100.  One step = 1 sweep of every box + 100 exchange attempts per pair.
-    (512 per box: with q = 0.8 the cell width must exceed 1.8, and 256
-    spheres would leave cells too wide for the cell-bin capacity.)"""
+    0.80 to 1.00 across the pairs, n_trial = 100.  One step = 1 sweep of
+    every box + 100 exchange attempts per pair."""
     import torch
     import torch.distributed as dist
-    from paper_1508_07077_gb300 import build, hpmc, replicas as R, workloads as W
+    from paper_1508_07077_gb300 import peaks, replicas as R, workloads as W
 
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
-    try:
-        hpmc.load()
-    except ImportError:
-        build.build()
-        hpmc.load()
-    prec = hpmc.HPMC_FP32_RECHECK if args.precision == "fp32" else hpmc.HPMC_FP64
+    hpmc = load_lib()
+    pk = peaks.measure()
     stream = torch.cuda.current_stream()
     n_pairs, N, phi, q, n_trial, n_ex = 152, 512, 0.12, 0.8, 100, 100
     etas = np.linspace(0.80, 1.00, n_pairs)
@@ -355,9 +734,8 @@ def run_gibbs(args, ws, rank, local):
         boxes.append((a, b))
     pairs = [((a.pos, a.L), (b.pos, b.L), {"q": q, "n_r": a.n_r, "n_trial": n_trial,
                                            "d_max": 0.15}) for a, b in boxes]
-    gp = hpmc.GibbsPairs(pairs, seed=1, precision=prec, device=local, replica0=base)
-    if args.warps != 1:
-        hpmc.hpmc_set_launch(gp.ctx, args.warps, 1)
+    gp = hpmc.GibbsPairs(pairs, seed=1, precision=hpmc.HPMC_FP32_RECHECK, device=local,
+                         replica0=base)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         gp.cycle(1, n_ex, stream)
@@ -385,9 +763,6 @@ def run_gibbs(args, ws, rank, local):
     g1 = [hpmc.hpmc_get_gibbs(gp.ctx, p)[1] for p in range(n_pairs)]
     gd = {k: sum(b[k] - a[k] for a, b in zip(g0, g1)) for k in g1[0]}
     live = hpmc.hpmc_get_live(gp.ctx, 2 * n_pairs)
-    # end to end through the C ABI with host buffers (pinned), copies timed:
-    # every box's slots uploaded (and checked), one sweep and the exchanges,
-    # the slots and counters read back
     n_slots = sum(rep["n"] for rep in gp.reps)
     host_pos = torch.empty((n_slots, 3), dtype=torch.float64).pin_memory().numpy()
     sweep_now, _ = hpmc.hpmc_get_state(gp.ctx, host_pos)
@@ -400,9 +775,6 @@ def run_gibbs(args, ws, rank, local):
         hpmc.hpmc_get_state(gp.ctx, host_pos, None, stream)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    # the replica counters hold the sweeps' blocking depletants too: the
-    # exchange's own rate per attempt from two more steps (untimed), the
-    # counters read between the sweep and the exchanges
     ex_blk = 0
     for _ in range(2):
         hpmc.hpmc_sweep(gp.ctx, 1, stream)
@@ -416,18 +788,14 @@ def run_gibbs(args, ws, rank, local):
     attempts_all, moves_all, blocking_all = R.reduce_sum(
         [gd["attempts"], cnt["moves"], blk_per_attempt * gd["attempts"]], "cuda")
     if rank == 0:
-        clocks = clk.summary()
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        peak = sms * ISSUE_LANES_PER_SM * 2070.0e6 / 1e12
-        # exchange kernel: depletant streams and 2 n_trial - 1 CB trials per
-        # blocking depletant of an exchange, 6/pi attempts per point in the ball
-        trials = 6.0 / math.pi * (gd["dep_drawn"] + blocking_all * (2 * n_trial - 1))
+        peak = pk["philox_rk_calls_per_s"] * OPS_PHILOX / 1e12
+        trials = ATTEMPTS_PER_POINT * (gd["dep_drawn"] + blocking_all * (2 * n_trial - 1))
         achieved = OPS_PER_GIBBS_TRIAL * trials / (ex_ms * 1e-3) / 1e12
         line = {
             "metric": "Gibbs exchange attempts/s", "value": attempts_all / (ms * 1e-3),
             "unit": "attempts/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "gibbs_152_pairs_2x512_spheres_phi0.12_q0.8_eta0.8-1.0",
                        "n_trial": n_trial, "exchanges_per_pair_per_step": n_ex,
                        "step": "1 sweep of every box + 100 exchange attempts per pair",
@@ -442,11 +810,12 @@ def run_gibbs(args, ws, rank, local):
                     "h2d_bytes_per_step": int(host_pos.nbytes),
                     "d2h_bytes_per_step": int(host_pos.nbytes)},
             "box_populations": {"min": min(live), "max": max(live)},
-            "gpu_launches": args.steps * (1 + (1 if prec == 1 else 0) + 8 + 1),
+            "gpu_launches": args.steps * (4 + 1),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "k_gibbs_exchange",
-                         "peak_basis": "%d SMs x 128 lanes x 2070 MHz (issue rate)" % sms},
-            "clocks": clocks,
+                         "peak_basis": "measured Philox4x32-10 (round keys) calls/s x 40 "
+                                       "lane-ops (of measured)"},
+            "clocks": clk.summary(),
         }
         if not args.no_cpu_baseline:
             from oracle import oracle as O
@@ -460,6 +829,7 @@ def run_gibbs(args, ws, rank, local):
             dt = time.perf_counter() - t0
             line["cpu_baseline"] = {
                 "value": g["attempts"] / dt, "unit": "attempts/s", "cores": 1, "kind": "oracle",
+                "cpu": cpu_model(),
                 "sample": "%d steps of pair 0 (eta_r 0.80) from the start (%d attempts, "
                           "%.1f s)" % (args.cpu_cycles_gibbs, g["attempts"], dt)}
         print(json.dumps(line))
@@ -467,442 +837,44 @@ def run_gibbs(args, ws, rank, local):
         dist.destroy_process_group()
 
 
-# Anisotropic lens kernel, per depletant drawn: the sphere work plus the two
-# body-frame tests (rotation 15 + shape test 15 lane-ops), the old-pose one
-# for the ~55% that overlap the new pose; per move: two frames (2 x 20) more.
-OPS_PER_DEP_ANISO = 6.0 / math.pi * (40.0 + 11.0) + 30.0 + 0.55 * 30.0
-OPS_PER_MOVE_LENS_ANISO = 2 * 40.0 + 20.0 + 12.0 + 40.0
-# Phase kernel, per move: ~25 candidates x 8 (bounding test) and ~4 near
-# candidates through the FP32 portal refinement (~20 steps x 80 lane-ops).
-OPS_PER_MOVE_PHASE_ANISO = 25 * 8.0 + 4 * 20 * 80.0
-
-
-def run_shape(args, ws, rank, local):
-    """One anisotropic system: 32768 hemispheres (phi_c 0.25, q 0.10, eta_r
-    0.30) or 65536 discoids (phi_c 0.30, q 0.10, eta_r 0.25), translation and
-    rotation moves (a_max 0.2 rad, p_translate 0.5), d_max tuned to ~30%
-    acceptance, warps per colloid and cell size from the autotuner."""
-    import torch
-    import torch.distributed as dist
-    from paper_1508_07077_gb300 import build, hpmc, replicas as R, workloads as W
-
-    if ws > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    try:
-        hpmc.load()
-    except ImportError:
-        build.build()
-        hpmc.load()
-    prec = hpmc.HPMC_FP32_RECHECK if args.precision == "fp32" else hpmc.HPMC_FP64
-    sysf = W.hemispheres_32768 if args.workload == "hemispheres" else W.discoids_65536
-    s = sysf(seed=1)
-    stream = torch.cuda.current_stream()
-    smp = hpmc.Sampler(s.pos, s.L, quat=s.quat, shape=s.shape, shape_params=s.shape_params,
-                       q=s.q, n_r=s.n_r, d_max=0.02, a_max=s.a_max, p_translate=s.p_translate,
-                       seed=1, replica=R.replica_ids(1, rank)[0], precision=prec,
-                       device=local)
-    ctx = smp.ctx
-    d = 0.02
-    for _ in range(10 if not args.no_tune else 0):
-        hpmc.hpmc_set_moves(ctx, d, s.a_max, s.p_translate)
-        hpmc.hpmc_reset_counters(ctx)
-        hpmc.hpmc_sweep(ctx, 10)
-        _, cnt = hpmc.hpmc_get_state(ctx)
-        acc = cnt["accept"] / max(1, cnt["moves"])
-        d = min(0.1, d * min(2.0, max(0.5, (acc + 0.02) / (ACC_TARGET + 0.02))))
-    hpmc.hpmc_set_moves(ctx, d, s.a_max, s.p_translate)
-    nc_auto = int(s.L / (1.0 + s.q)) & ~1
-    cells = (0, nc_auto - 2) if nc_auto > 4 else (0,)
-    warps, ncell, tuned_ms = hpmc.hpmc_autotune(ctx, warps=(1, 2, 4), cells=cells, n_sweeps=3)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        hpmc.hpmc_sweep(ctx, 1, stream)
-    hpmc.hpmc_reset_counters(ctx)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.zero_()
-            a[k].record(stream)
-            hpmc.hpmc_sweep(ctx, 1, stream)
-            b[k].record(stream)
-        torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    ms = sum(x.elapsed_time(y) for x, y in zip(a, b))
-    _, cnt = hpmc.hpmc_get_state(ctx)
-    # per-kernel times (kernels launched one by one, events around each)
-    hpmc.hpmc_set_timing(ctx, 1)
-    hpmc.hpmc_reset_counters(ctx)
-    tsweeps = min(args.steps, 10)
-    hpmc.hpmc_sweep(ctx, tsweeps, stream)
-    kern_ms, kern_n = hpmc.hpmc_get_timing(ctx)
-    _, tc = hpmc.hpmc_get_state(ctx)
-    hpmc.hpmc_set_timing(ctx, 0)
-    # end to end through the C ABI with host buffers
-    host_pos = torch.empty((s.n, 3), dtype=torch.float64).pin_memory().numpy()
-    host_q = torch.empty((s.n, 4), dtype=torch.float64).pin_memory().numpy()
-    sweep_now, _ = hpmc.hpmc_get_state(ctx, host_pos, host_q)
-    e2e_steps = max(3, min(args.steps, 20) // 2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(e2e_steps):
-        hpmc.hpmc_set_state(ctx, host_pos, host_q, sweep_now + k, stream)
-        hpmc.hpmc_sweep(ctx, 1, stream)
-        hpmc.hpmc_get_state(ctx, host_pos, host_q, stream)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    ms, e2e_s = R.reduce_max([ms, e2e_s], "cuda")
-    moves_all, drawn_all, eval_all = R.reduce_sum(
-        [cnt["moves"], cnt["dep_drawn"], cnt["dep_evaluated"]], "cuda")
-    if rank == 0:
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        peak = sms * ISSUE_LANES_PER_SM * 2070.0e6 / 1e12
-        cand = {}
-        if kern_n[2]:
-            lens_ops = (OPS_PER_DEP_ANISO * tc["dep_drawn"] + OPS_PER_MOVE_LENS_ANISO * tc["moves"])
-            cand["k_lens_aniso_fp32"] = (kern_ms[2], lens_ops / (kern_ms[2] * 1e-3) / 1e12)
-        ph_ops = OPS_PER_MOVE_PHASE_ANISO * tc["moves"]
-        ph_name = "k_phase_aniso_fp32" if prec == 1 else "k_phase_aniso_fp64"
-        cand[ph_name] = (kern_ms[1], ph_ops / (kern_ms[1] * 1e-3) / 1e12)
-        dominant = max(cand, key=lambda k: cand[k][0])
-        achieved = cand[dominant][1]
-        line = {
-            "metric": "colloid trial moves/s", "value": moves_all / (ms * 1e-3),
-            "unit": "moves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
-            "config": {"workload": s.name + "_phi%.2f_q%.2f_eta%.2f" % (
-                           s.extra["phi_c"], s.q, s.extra["eta_r"]),
-                       "form": "FP32+FP64 recheck" if prec == 1 else "FP64",
-                       "n_trial": 0, "a_max": s.a_max, "p_translate": s.p_translate,
-                       "d_max": round(d, 5), "step": "1 sweep (%d moves)" % s.n,
-                       "autotuned": {"warps_per_colloid": warps, "n_cell": ncell,
-                                     "ms_per_sweep": tuned_ms},
-                       "l2": "flushed between steps (256 MB write)"},
-            "insertions_drawn_per_s": drawn_all / (ms * 1e-3),
-            "insertions_evaluated_per_s": eval_all / (ms * 1e-3),
-            "acceptance": cnt["accept"] / max(1, cnt["moves"]),
-            "translate_fraction": cnt["translate"] / max(1, cnt["moves"]),
-            "fp64_rechecks_per_move": cnt["rechecks"] / max(1, cnt["moves"]),
-            "gpu_launches": args.steps * (1 + (2 if prec == 1 else 0) + 8),
-            "kernels": {"phase_ms_per_sweep": kern_ms[1] / tsweeps,
-                        "lens_ms_per_sweep": kern_ms[2] / tsweeps,
-                        "cells_ms_per_sweep": kern_ms[0] / tsweeps,
-                        "achieved_tops": {k: v[1] for k, v in cand.items()}},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": dominant,
-                         "peak_basis": "%d SMs x 128 lanes x 2070 MHz (issue rate)" % sms},
-            "clocks": clk.summary(),
-            "e2e": {"value": ws * e2e_steps * s.n / e2e_s, "unit": "moves/s",
-                    "h2d_bytes_per_step": s.n * 7 * 8, "d2h_bytes_per_step": s.n * 7 * 8 + 128},
-        }
-        if not args.no_cpu_baseline:
-            from oracle import oracle as O
-            O.build()
-            pos, quat, _, _ = smp.state(with_quat=True)
-            t0 = time.perf_counter()
-            _, _, oc, _ = O.run(pos, s.L, shape=s.shape, shape_params=s.shape_params, quat=quat,
-                                q=s.q, n_r=s.n_r, d_max=d, a_max=s.a_max,
-                                p_translate=s.p_translate, seed=1, n_cell=ncell,
-                                n_sweeps=args.cpu_sweeps_shape, sweep0=sweep_now + e2e_steps)
-            dt = time.perf_counter() - t0
-            line["cpu_baseline"] = {"value": oc["moves"] / dt, "unit": "moves/s", "cores": 1,
-                                    "kind": "oracle",
-                                    "sample": "%d sweeps of the system (%d moves, %.1f s)"
-                                              % (args.cpu_sweeps_shape, oc["moves"], dt)}
-        print(json.dumps(line))
-    smp.close()
-    if ws > 1:
-        dist.destroy_process_group()
-
-
-def run_ours(args, ws, rank, local):
-    import torch
-    import torch.distributed as dist
-    from paper_1508_07077_gb300 import build, hpmc, replicas as R, workloads as W
-
-    if ws > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    torch.cuda.set_device(local)
-    try:
-        hpmc.load()
-    except ImportError:
-        build.build()
-        hpmc.load()
-    prec = hpmc.HPMC_FP32_RECHECK if args.precision == "fp32" else hpmc.HPMC_FP64
-    stream = torch.cuda.current_stream()
-
-    # the four state points as one batch (independent replicas, one set of
-    # launches per sweep); this rank's replicas are keyed by its rank
-    systems = [W.spheres_16384(eta, seed=1) for eta in ETAS]
-    etas = [round(s.extra["eta_r"], 1) for s in systems]
-    descs = [{"n": s.n, "box_l": s.L, "pos": s.pos, "q": s.q, "n_r": s.n_r, "n_trial": 0,
-              "d_max": D_MAX_TUNED[e], "replica": R.replica_ids(len(systems), rank)[k]}
-             for k, (s, e) in enumerate(zip(systems, etas))]
-    ctx = hpmc.hpmc_init_batch(descs, seed=1, precision=prec, device=local)
-    hpmc.hpmc_set_launch(ctx, args.warps, args.ilp)
-    if args.v0 == "shell":
-        hpmc.hpmc_set_v0(ctx, hpmc.HPMC_V0_SHELL)
-    if args.soft > 0.0:
-        hpmc.hpmc_set_soft(ctx, args.soft)
-    ns = [s.n for s in systems]
-    d0 = [D_MAX_TUNED[e] for e in etas]
-    dtuned = d0 if args.no_tune else tune_batch(ctx, hpmc, d0, ns)
-    dmax = dict(zip(etas, dtuned))
-    torch.cuda.synchronize()
-
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    def step():
-        hpmc.hpmc_sweep(ctx, 1, stream)
-
-    for _ in range(args.warmup):
-        step()
-    hpmc.hpmc_reset_counters(ctx)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    with ClockSampler(local) as clk:
-        time.sleep(0.25)
-        for k in range(args.steps):
-            flush.zero_()
-            starts[k].record(stream)
-            step()
-            ends[k].record(stream)
-        torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
-    _, cnt = hpmc.hpmc_get_state(ctx)
-    moves, drawn, evaluated = cnt["moves"], cnt["dep_drawn"], cnt["dep_evaluated"]
-    rechecks, accept = cnt["rechecks"], cnt["accept"]
-
-    # per-kernel durations (events around each launch, kernels launched one by one)
-    hpmc.hpmc_reset_counters(ctx)
-    hpmc.hpmc_set_timing(ctx, True)
-    timing_steps = min(args.steps, 50)
-    for k in range(timing_steps):
-        flush.zero_()
-        step()
-    kern_ms, kern_n = hpmc.hpmc_get_timing(ctx)
-    hpmc.hpmc_set_timing(ctx, False)
-    _, tc = hpmc.hpmc_get_state(ctx)
-    t_moves, t_eval, t_drawn = tc["moves"], tc["dep_evaluated"], tc["dep_drawn"]
-
-    # the same batch with the shell-restricted V_0 (Sec. III.C remark), same
-    # step sizes: reported beside the headline, which keeps the circumsphere
-    shell = None
-    if args.v0 == "circumsphere" and not args.no_shell and args.soft == 0.0:
-        hpmc.hpmc_set_v0(ctx, hpmc.HPMC_V0_SHELL)
-        for _ in range(args.warmup):
-            step()
-        hpmc.hpmc_reset_counters(ctx)
-        torch.cuda.synchronize()
-        sh_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        sh_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        for k in range(args.steps):
-            flush.zero_()
-            sh_a[k].record(stream)
-            step()
-            sh_b[k].record(stream)
-        torch.cuda.synchronize()
-        sh_ms = sum(a.elapsed_time(b) for a, b in zip(sh_a, sh_b))
-        _, sc = hpmc.hpmc_get_state(ctx)
-        hpmc.hpmc_reset_counters(ctx)
-        hpmc.hpmc_set_timing(ctx, True)
-        for k in range(timing_steps):
-            flush.zero_()
-            step()
-        sk_ms, sk_n = hpmc.hpmc_get_timing(ctx)
-        hpmc.hpmc_set_timing(ctx, False)
-        hpmc.hpmc_set_v0(ctx, hpmc.HPMC_V0_CIRCUMSPHERE)
-        sh_ms = R.reduce_max([sh_ms], "cuda")[0]
-        sh_moves, sh_drawn = R.reduce_sum([sc["moves"], sc["dep_drawn"]], "cuda")
-        shell = {"value": sh_moves / (sh_ms * 1e-3), "unit": "moves/s",
-                 "ms_per_step": sh_ms / args.steps, "steps": args.steps,
-                 "insertions_drawn_per_s": sh_drawn / (sh_ms * 1e-3),
-                 "acceptance": sc["accept"] / max(1, sc["moves"]),
-                 "fp64_rechecks_per_move": sc["rechecks"] / max(1, sc["moves"]),
-                 "lens_ms_per_launch": sk_ms[2] / max(1, sk_n[2]),
-                 "phase_ms_per_launch": sk_ms[1] / max(1, sk_n[1]),
-                 "note": "V_0 = the excluded-volume shell of the move's level; same "
-                         "acceptance probabilities, fewer depletants per move"}
-
-    # the same four systems one at a time (separate contexts, one stream)
-    allpos = np.empty((sum(ns), 3))
-    sweep_now, _ = hpmc.hpmc_get_state(ctx, allpos)
-    singles = []
-    off = 0
-    for k, s in enumerate(systems):
-        smp = hpmc.Sampler(allpos[off:off + s.n].copy(), s.L, q=s.q, n_r=s.n_r,
-                           d_max=dtuned[k], seed=1, replica=descs[k]["replica"],
-                           precision=prec, warps=args.warps, ilp=args.ilp, device=local,
-                           soft_eps=args.soft)
-        hpmc.hpmc_set_state(smp.ctx, allpos[off:off + s.n].copy(), None, sweep_now)
-        smp.sweep(1)
-        singles.append(smp)
-        off += s.n
-    torch.cuda.synchronize()
-    seq_steps = min(args.steps, 50)
-    sa = [torch.cuda.Event(enable_timing=True) for _ in range(seq_steps)]
-    sb = [torch.cuda.Event(enable_timing=True) for _ in range(seq_steps)]
-    for k in range(seq_steps):
-        flush.zero_()
-        sa[k].record(stream)
-        for smp in singles:
-            smp.sweep(1, stream)
-        sb[k].record(stream)
-    torch.cuda.synchronize()
-    seq_ms = sum(a.elapsed_time(b) for a, b in zip(sa, sb))
-    for smp in singles:
-        smp.close()
-
-    # end to end through the C ABI with host buffers (pinned), copies timed
-    host_pos = torch.empty((sum(ns), 3), dtype=torch.float64).pin_memory().numpy()
-    sweep_now, _ = hpmc.hpmc_get_state(ctx, host_pos)
-    torch.cuda.synchronize()
-    e2e_steps = max(3, min(args.steps, 200) // 2)
-    t0 = time.perf_counter()
-    for k in range(e2e_steps):
-        hpmc.hpmc_set_state(ctx, host_pos, None, sweep_now + k, stream)
-        hpmc.hpmc_sweep(ctx, 1, stream)
-        hpmc.hpmc_get_state(ctx, host_pos, None, stream)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-
-    # max over ranks
-    ms, e2e_s, seq_ms = R.reduce_max([ms, e2e_s, seq_ms], "cuda")
-    moves_all, drawn_all, eval_all = R.reduce_sum([moves, drawn, evaluated], "cuda")
-
-    if rank == 0:
-        clocks = clk.summary()
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        phase_launch_ms = kern_ms[1] / max(1, kern_n[1])
-        lens_launch_ms = kern_ms[2] / max(1, kern_n[2])
-        f_peak = 2070.0e6
-        peak = sms * ISSUE_LANES_PER_SM * f_peak / 1e12
-        if kern_n[2]:
-            lens_ops = (OPS_PER_DEP * t_drawn + OPS_PER_MOVE_LENS * t_moves) / kern_n[2]
-            phase_ops = OPS_PER_MOVE_PHASE * t_moves / max(1, kern_n[1])
-            cand = {"k_lens_sphere_fp32": (kern_ms[2], lens_ops / (lens_launch_ms * 1e-3) / 1e12),
-                    "k_phase_sphere_fp32": (kern_ms[1],
-                                            phase_ops / (phase_launch_ms * 1e-3) / 1e12)}
-        else:
-            ops = (OPS_PER_DEP * t_eval + OPS_PER_MOVE * t_moves) / max(1, kern_n[1])
-            cand = {"k_phase_sphere_fp64": (kern_ms[1], ops / (phase_launch_ms * 1e-3) / 1e12)}
-        dominant = max(cand, key=lambda k: cand[k][0])
-        achieved = cand[dominant][1]
-        bytes_per_launch = BYTES_PER_MOVE * t_moves / max(1, kern_n[1])
-        value = moves_all / (ms * 1e-3)
-        e2e_moves = ws * e2e_steps * sum(ns)
-        line = {
-            "metric": "colloid trial moves/s", "value": value, "unit": "moves/s",
-            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": "FP32+FP64 recheck" if prec == 1 else "FP64",
-                       "v0": args.v0,
-                       "colloid_depletant": ("Hertz eps=%g kT" % args.soft) if args.soft else "hard",
-                       "n_trial": 0, "step": "1 sweep of each of 4 systems (65536 moves)",
-                       "schedule": "4 systems as one batch (one set of launches per sweep)",
-                       "d_max": {str(k): round(v, 5) for k, v in dmax.items()},
-                       "l2": "flushed between steps (256 MB write)",
-                       "warps_per_colloid": args.warps, "attempts_per_thread": args.ilp},
-            "one_at_a_time_moves_per_s": ws * seq_steps * sum(ns) / (seq_ms * 1e-3),
-            "insertions_drawn_per_s": drawn_all / (ms * 1e-3),
-            "insertions_evaluated_per_s": eval_all / (ms * 1e-3),
-            "acceptance": accept / max(1, moves),
-            "fp64_rechecks_per_move": rechecks / max(1, moves),
-            "gpu_launches": args.steps * (1 + (1 if prec == 1 else 0) + 8),
-            "kernels": {"phase_ms_per_launch": phase_launch_ms,
-                        "lens_ms_per_launch": lens_launch_ms,
-                        "cells_ms_per_sweep": kern_ms[0] / max(1, kern_n[0]),
-                        "share": {"cells": kern_ms[0] / max(1e-9, sum(kern_ms)),
-                                  "phase": kern_ms[1] / max(1e-9, sum(kern_ms)),
-                                  "lens": kern_ms[2] / max(1e-9, sum(kern_ms))},
-                        "achieved_tops": {k: v[1] for k, v in cand.items()}},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak,
-                         "traffic": MEASURED_TRAFFIC.get(dominant), "kernel": dominant,
-                         "peak_basis": "%d SMs x 128 lanes x 2070 MHz (issue rate)" % sms,
-                         "hbm_achieved_gbs": bytes_per_launch / (phase_launch_ms * 1e-3) / 1e9},
-            "clocks": clocks,
-            "e2e": {"value": e2e_moves / e2e_s, "unit": "moves/s",
-                    "h2d_bytes_per_step": sum(ns) * 3 * 8,
-                    "d2h_bytes_per_step": sum(ns) * 3 * 8 + 8 * 16},
-        }
-        if shell is not None:
-            line["shell_v0"] = shell
-        if not args.no_cpu_baseline:
-            # the oracle on the host on a bounded sample of the same workload
-            for s in systems:
-                s.extra["eta_r"] = round(s.extra["eta_r"], 1)
-            mv, dr, ev, dt, nm = cpu_oracle_rate(systems, dmax, args.cpu_sweeps,
-                                                 v0_mode=1 if args.v0 == "shell" else 0,
-                                                 soft_eps=args.soft)
-            line["cpu_baseline"] = {
-                "value": mv, "unit": "moves/s", "cores": 1, "kind": "oracle",
-                "sample": "%d sweep(s) of each of the 4 systems from the fcc start "
-                          "(%d moves, %.1f s)" % (args.cpu_sweeps, nm, dt),
-                "insertions_evaluated_per_s": ev}
-        print(json.dumps(line))
-    hpmc.hpmc_destroy(ctx)
-    if ws > 1:
-        dist.destroy_process_group()
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
-    ap.add_argument("--warps", type=int, default=1)
-    ap.add_argument("--ilp", type=int, default=1)
-    ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--workload", choices=("spheres_16384", "batched", "hemispheres", "discoids",
-                                           "gibbs"),
-                    default="spheres_16384",
-                    help="spheres_16384: the headline four-state-point workload; batched: "
-                         "128 replicas of uneven size and state point; hemispheres / "
-                         "discoids: 32768 hemispheres or 65536 discoids with rotations; "
-                         "gibbs: 152 Gibbs-ensemble pairs (exchange attempts/s)")
-    ap.add_argument("--cpu-cycles-gibbs", type=int, default=40)
-    ap.add_argument("--v0", choices=("circumsphere", "shell"), default="circumsphere",
-                    help="depletant region V_0 of the spheres workload: the new pose's "
-                         "circumsphere (the paper's; default, with a shell measurement "
-                         "alongside) or the excluded-volume shell of the move")
-    ap.add_argument("--soft", type=float, default=0.0,
-                    help="Hertz colloid-depletant interaction of this strength (kT), "
-                         "in either form")
-    ap.add_argument("--no-shell", action="store_true",
-                    help="skip the shell-V_0 measurement beside the headline")
-    ap.add_argument("--cpu-sweeps-shape", type=int, default=3)
+    ap.add_argument("--workload", choices=("batched", "gibbs"), default="batched",
+                    help="batched: the headline 128-replica workload, with the single-system "
+                         "workloads beside it; gibbs: 152 Gibbs-ensemble pairs (exchange "
+                         "attempts/s)")
+    ap.add_argument("--schedule", type=int, choices=(0, 1), default=0,
+                    help="colour phases: 0 eight launches per sweep, 1 one persistent launch")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="the headline only (no one-at-a-time run, other schedule or "
+                         "single-system workloads)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sweeps", type=int, default=40)
+    ap.add_argument("--cpu-cycles-gibbs", type=int, default=40)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank)
-    elif args.workload == "batched":
-        run_batched(args, ws, rank, local)
-    elif args.workload in ("hemispheres", "discoids"):
-        run_shape(args, ws, rank, local)
-    elif args.workload == "gibbs":
+        return
+    if args.workload == "gibbs":
         run_gibbs(args, ws, rank, local)
-    else:
-        run_ours(args, ws, rank, local)
+        return
+    line, d = run_batched(args, ws, rank, local)
+    if rank != 0:
+        return
+    if ws == 1 and not args.no_extras:
+        pk = line["pipe_peaks_measured"]
+        line["extra"] = {"spheres_16384": spheres_16384(args, local, pk),
+                         "hemispheres_32768": shape_system(args, local, "hemispheres", pk),
+                         "discoids_65536": shape_system(args, local, "discoids", pk)}
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_batched(d, args.warmup, rank)
+    print(json.dumps(line))
 
 
 if __name__ == "__main__":
