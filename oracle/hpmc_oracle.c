@@ -135,8 +135,51 @@ static double u53(uint32_t w0, uint32_t w1)
            (1.0 / 9007199254740992.0);
 }
 
+/* uniform in (-1,1) from a 21-bit integer: (a + 1/2) 2^-20 - 1 (exact) */
+static double s21(uint32_t a) { return ((double)a + 0.5) * (1.0 / 1048576.0) - 1.0; }
+
+/* Paired points of a depletant stream (hard interactions, circumsphere or
+ * cube V_0): one Philox call gives the coordinates of two attempts.  The
+ * attempts come in blocks of 64: attempt t is half h = floor(t / 32) mod 2 of
+ * call 32 floor(t / 64) + (t mod 32), so attempts 64b .. 64b + 31 are the
+ * first halves of calls 32b .. 32b + 31 and the next 32 attempts their second
+ * halves.  Half 0 is the top 21 bits of words 0, 1, 2; half 1 is, for
+ * coordinate d, the low 11 bits of word d below bits 10d .. 10d + 9 of word 3
+ * (126 bits, each used once).  Coordinate d of the point is R_s s21(a_d). */
+static void paired_fields(const uint32_t w[4], uint32_t h, uint32_t a[3])
+{
+    for (int d = 0; d < 3; ++d) {
+        if (h == 0) a[d] = w[d] >> 11;
+        else a[d] = (w[d] & 0x7FFu) | (((w[3] >> (10 * d)) & 0x3FFu) << 11);
+    }
+}
+
+static void paired_point(okey key, double R_s, uint32_t sweep, uint32_t tag, uint32_t t,
+                         double e[3])
+{
+    uint32_t w[4], a[3];
+    draw(key, sweep, tag, P_DEP, 0, 32u * (t >> 6) + (t & 31u), w);
+    paired_fields(w, (t >> 5) & 1u, a);
+    e[0] = R_s * s21(a[0]);
+    e[1] = R_s * s21(a[1]);
+    e[2] = R_s * s21(a[2]);
+}
+
 double oracle_u01(uint32_t w) { return u01(w); }
 double oracle_s11(uint32_t w) { return s11(w); }
+double oracle_s21(uint32_t a) { return s21(a); }
+
+/* The paired points of attempts t = 0 .. n_att - 1 of stream (sweep, tag)
+ * under key (seed), radius R_s: all of them into e (3 per attempt), for the
+ * tests of the stream. */
+void oracle_paired_points(double R_s, uint64_t seed, uint32_t sweep, uint32_t tag,
+                          uint32_t n_att, double *e)
+{
+    okey key;
+    key.k[0] = (uint32_t)seed;
+    key.k[1] = (uint32_t)(seed >> 32);
+    for (uint32_t t = 0; t < n_att; ++t) paired_point(key, R_s, sweep, tag, t, e + 3 * (size_t)t);
+}
 double oracle_u53(uint32_t w0, uint32_t w1) { return u53(w0, w1); }
 
 /* ------------------------------------------------------------------------ */
@@ -785,6 +828,19 @@ static int next_in_ball(const osim *S, uint32_t sweep, uint32_t tag,
     return next_in_ball_w(S, sweep, tag, purpose, sub, t, t_max, e, NULL);
 }
 
+/* The same for the paired depletant stream of a trial move. */
+static int next_in_ball_paired(const osim *S, uint32_t sweep, uint32_t tag, uint32_t *t,
+                               uint32_t t_max, double e[3])
+{
+    while (*t < t_max) {
+        paired_point(S->key, S->R_s, sweep, tag, *t, e);
+        *t += 1;
+        double r2 = (e[0] * e[0] + e[1] * e[1]) + e[2] * e[2];
+        if (r2 < S->R_s2) return 1;
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Shell-restricted V_0 (Sec. III.C, the closing remark): for a sphere      */
 /* translated by D, a depletant overlapping the new pose but not the old     */
@@ -1011,14 +1067,22 @@ static int accept_move(const osim *S, uint32_t sweep, int i, const double xn[3],
         double e[3];
         int got;
         uint32_t w3 = 0;
-        if (S->v0_mode == 2) {
+        if (S->v0_mode == 2 && S->soft_eps > 0.0) {
             cube_point(S, sweep, tag, t, e, &w3);
+            t += 1;
+            got = 1;
+        } else if (S->v0_mode == 2) {
+            /* hard, cube: the paired stream, every attempt a depletant */
+            paired_point(S->key, S->R_s, sweep, tag, t, e);
             t += 1;
             got = 1;
         } else if (lvl > 0) {
             got = next_in_shell(S, lvl, sweep, tag, &t, t_max, e);
-        } else {
+        } else if (S->soft_eps > 0.0) {
+            /* soft: one point per call, its fourth word decides blocking */
             got = next_in_ball_w(S, sweep, tag, P_DEP, 0, &t, t_max, e, &w3);
+        } else {
+            got = next_in_ball_paired(S, sweep, tag, &t, t_max, e);
         }
         if (!got) {
             cnt[C_CAP]++;

@@ -118,6 +118,11 @@ def lib():
             L.oracle_rotation_proposal.restype = ctypes.c_int
             L.oracle_shell_level.argtypes = [u32p]
             L.oracle_shell_level.restype = ctypes.c_int
+            L.oracle_s21.argtypes = [ctypes.c_uint32]
+            L.oracle_s21.restype = ctypes.c_double
+            L.oracle_paired_points.argtypes = [ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                                               ctypes.c_uint32, ctypes.c_uint32, dp]
+            L.oracle_paired_points.restype = None
             L.oracle_shell_lambda.argtypes = [ctypes.c_double] * 3
             L.oracle_shell_lambda.restype = ctypes.c_double
             L.oracle_shell_points.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -287,6 +292,19 @@ def shell_level(w0, w1, w2):
     """Shell level (1..32) of a translation drawn from move words w0..w2."""
     w = np.array([w0, w1, w2], dtype=np.uint32)
     return lib().oracle_shell_level(_p(w, ctypes.c_uint32))
+
+
+def s21(a):
+    return lib().oracle_s21(int(a))
+
+
+def paired_points(R_s, n_att, *, seed=1, sweep=0, tag=0):
+    """The points (n_att x 3) of attempts 0 .. n_att - 1 of a paired depletant
+    stream (two attempts per Philox call), in or out of the ball."""
+    e = np.zeros((max(n_att, 1), 3))
+    lib().oracle_paired_points(float(R_s), int(seed), int(sweep), int(tag), int(n_att),
+                               _p(e, ctypes.c_double))
+    return e[:n_att].copy()
 
 
 def shell_lambda(R_s, R_in, n_r):

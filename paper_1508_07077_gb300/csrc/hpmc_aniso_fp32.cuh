@@ -77,13 +77,16 @@ __device__ __forceinline__ void pose_now(const SimParams &P, int j, const int *a
 // against i's new pose (target 0), i's old pose (target 1) or neighbour j
 // (target 2).
 __device__ __noinline__ bool exact_dep_aniso(const SimParams &P, const Rep &R, int i, uint4 w,
-                                             int base, int target, int j, const int *acc, int nacc)
+                                             int base, int target, int j, const int *acc, int nacc,
+                                             int half = -1)
 {
     const double4 xn = P.prop_pos[i];
     const double4 xo = P.pos[i];
     const Vec3 o = v3(min_image(xo.x - xn.x, R.L, R.half_L), min_image(xo.y - xn.y, R.L, R.half_L),
                       min_image(xo.z - xn.z, R.L, R.half_L));
-    Vec3 v = v3(R.R_s * s11(w.x), R.R_s * s11(w.y), R.R_s * s11(w.z));
+    double p0, p1, p2;
+    point64(R, w, half, p0, p1, p2);
+    Vec3 v = v3(p0, p1, p2);
     if (base == 1) v = v3(o.x + v.x, o.y + v.y, o.z + v.z);
     if (target == 0) return dep_aniso(R, v, P.prop_quat[i]);
     if (target == 1) return dep_aniso(R, v3(v.x - o.x, v.y - o.y, v.z - o.z), P.quat[i]);
@@ -176,11 +179,14 @@ __global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__
         uint4 w = make_uint4(0, 0, 0, 0);
         float e0 = 0.f, e1 = 0.f, e2 = 0.f;
         int in = 0;
+        // the paired stream: attempt t is half paired_half(t) of call paired_call(t)
+        const int half = (int)paired_half(t);
         if (t < t_max) {
-            w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, t);
-            e0 = coord32(w.x, R.R_s32);
-            e1 = coord32(w.y, R.R_s32);
-            e2 = coord32(w.z, R.R_s32);
+            w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, paired_call(t));
+            const uint3 f = paired_fields(w, (uint32_t)half);
+            e0 = s21f(f.x) * R.R_s32;
+            e1 = s21f(f.y) * R.R_s32;
+            e2 = s21f(f.z) * R.R_s32;
             in = R.v0_cube ? 1 : tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
         }
         {
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__
             if (__any_sync(kFull, unsure)) {
                 if (unsure) {
                     ++rck;
-                    in = exact_ball(P, R, w) ? 1 : 0;
+                    in = exact_ball(P, R, w, half) ? 1 : 0;
                 }
             }
         }
@@ -203,7 +209,7 @@ __global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__
             if (__any_sync(kFull, unsure)) {
                 if (unsure) {
                     ++rck;
-                    tn = exact_dep_aniso(P, R, g, w, 0, 0, 0, nullptr, 0) ? 1 : 0;
+                    tn = exact_dep_aniso(P, R, g, w, 0, 0, 0, nullptr, 0, half) ? 1 : 0;
                 }
             }
         }
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__
             if (__any_sync(kFull, unsure)) {
                 if (unsure) {
                     ++rck;
-                    to = exact_dep_aniso(P, R, g, w, 0, 1, 0, nullptr, 0) ? 1 : 0;
+                    to = exact_dep_aniso(P, R, g, w, 0, 1, 0, nullptr, 0, half) ? 1 : 0;
                 }
             }
         }
@@ -345,9 +351,12 @@ __device__ __noinline__ bool exact_free_nb_aniso(const SimParams &P, const Rep &
                                                  uint32_t t, const Nb32 *nb, int nnb, const int *acc,
                                                  int nacc)
 {
-    const uint4 w = draw(R.key0, R.key1, sweep, (uint32_t)(i - R.off), kPDep, 0, t);
+    // (the paired stream)
+    const uint4 w = draw(R.key0, R.key1, sweep, (uint32_t)(i - R.off), kPDep, 0, paired_call(t));
     for (int a = 0; a < nnb; ++a)
-        if (exact_dep_aniso(P, R, i, w, 0, 2, __float_as_int(nb[a].d.w), acc, nacc)) return false;
+        if (exact_dep_aniso(P, R, i, w, 0, 2, __float_as_int(nb[a].d.w), acc, nacc,
+                            (int)paired_half(t)))
+            return false;
     return true;
 }
 

@@ -217,10 +217,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 double e0 = 0.0, e1 = 0.0, e2 = 0.0;
                 bool inside = false;
                 if (t < t_max) {
-                    const uint4 w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, t);
-                    e0 = R.R_s * s11(w.x);
-                    e1 = R.R_s * s11(w.y);
-                    e2 = R.R_s * s11(w.z);
+                    // the paired stream (hard interactions)
+                    paired_point64(R.key0, R.key1, R.R_s, sweep, tag, t, e0, e1, e2);
                     inside = R.v0_cube || norm2(e0, e1, e2) < R.R_s2;
                 }
                 const unsigned bal = __ballot_sync(kFull, inside);

@@ -124,6 +124,49 @@ __device__ __forceinline__ double u53(uint32_t a, uint32_t b)
     return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6)) * 0x1p-53;
 }
 
+// Paired depletant points.  The depletant stream of a trial move with hard
+// colloid-depletant interactions and the circumsphere or cube V_0 takes two
+// attempts from each Philox call, in blocks of 64 attempts: attempt t is half
+// (t >> 5) & 1 of call 32 (t >> 6) + (t & 31), so a warp's 32 lanes draw 32
+// calls and take first their first halves, then their second halves.  Half 0
+// is the top 21 bits of words 0, 1, 2; half 1 is, for coordinate d, the low
+// 11 bits of word d below bits 10d .. 10d + 9 of word 3 (126 bits, each used
+// once).  Coordinate d is R_s s21(a_d) with s21(a) = (a + 1/2) 2^-20 - 1,
+// exact in FP64 and in FP32.
+__host__ __device__ __forceinline__ uint32_t paired_call(uint32_t t) { return 32u * (t >> 6) + (t & 31u); }
+__host__ __device__ __forceinline__ uint32_t paired_half(uint32_t t) { return (t >> 5) & 1u; }
+__host__ __device__ __forceinline__ uint3 paired_fields(uint4 w, uint32_t h)
+{
+    if (h == 0u) return make_uint3(w.x >> 11, w.y >> 11, w.z >> 11);
+    return make_uint3((w.x & 0x7FFu) | ((w.w & 0x3FFu) << 11),
+                      (w.y & 0x7FFu) | (((w.w >> 10) & 0x3FFu) << 11),
+                      (w.z & 0x7FFu) | (((w.w >> 20) & 0x3FFu) << 11));
+}
+__device__ __forceinline__ double s21(uint32_t a) { return ((double)a + 0.5) * 0x1p-20 - 1.0; }
+// the same value in FP32: a + 1/2 has at most 22 significant bits, the
+// scaling is exact and so is the subtraction (the result is a multiple of
+// 2^-21 below 1 in magnitude)
+__device__ __forceinline__ float s21f(uint32_t a) { return ((float)a + 0.5f) * 0x1p-20f - 1.0f; }
+// The same value without an integer-to-float conversion: f = 1 + a 2^-21 has
+// a as its mantissa's top 21 bits, and 2 f + (2^-21 - 3) = (2a + 1 - 2^21)
+// 2^-21 is a multiple of 2^-21 below 1 in magnitude, so the fused
+// multiply-add is exact.
+__device__ __forceinline__ float s21f_bits(uint32_t a)
+{
+    return __fmaf_rn(__uint_as_float(0x3F800000u | (a << 2)), 2.0f, 0x1p-21f - 3.0f);
+}
+
+// FP64 point of attempt t of colloid `tag`'s paired depletant stream.
+__device__ __forceinline__ void paired_point64(uint32_t k0, uint32_t k1, double R_s, uint32_t sweep,
+                                               uint32_t tag, uint32_t t, double &e0, double &e1,
+                                               double &e2)
+{
+    const uint3 a = paired_fields(draw(k0, k1, sweep, tag, kPDep, 0, paired_call(t)), paired_half(t));
+    e0 = R_s * s21(a.x);
+    e1 = R_s * s21(a.y);
+    e2 = R_s * s21(a.z);
+}
+
 // ---------------------------------------------------------------------------
 // Parameters.  A context is a batch of independent replica systems (one for a
 // single system); every kernel covers all replicas of the batch in one launch.

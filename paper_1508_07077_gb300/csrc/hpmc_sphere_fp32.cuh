@@ -86,9 +86,28 @@ __device__ __noinline__ bool exact_pair(const SimParams &P, const Rep &R, uint32
     return norm2(c0, c1, c2) < R.contact2;
 }
 
-__device__ __noinline__ bool exact_ball(const SimParams &P, const Rep &R, uint4 w)
+// FP64 coordinates of a point from its Philox words: half < 0, one point per
+// call (R_s s11 of words 0..2: CB trials, the soft interaction's depletants);
+// half 0 or 1, that half of a paired call (the hard depletant streams).
+__device__ __forceinline__ void point64(const Rep &R, uint4 w, int half, double &e0, double &e1,
+                                        double &e2)
 {
-    const double e0 = R.R_s * s11(w.x), e1 = R.R_s * s11(w.y), e2 = R.R_s * s11(w.z);
+    if (half < 0) {
+        e0 = R.R_s * s11(w.x);
+        e1 = R.R_s * s11(w.y);
+        e2 = R.R_s * s11(w.z);
+    } else {
+        const uint3 a = paired_fields(w, (uint32_t)half);
+        e0 = R.R_s * s21(a.x);
+        e1 = R.R_s * s21(a.y);
+        e2 = R.R_s * s21(a.z);
+    }
+}
+
+__device__ __noinline__ bool exact_ball(const SimParams &P, const Rep &R, uint4 w, int half = -1)
+{
+    double e0, e1, e2;
+    point64(R, w, half, e0, e1, e2);
     return norm2(e0, e1, e2) < R.R_s2;
 }
 
@@ -97,13 +116,14 @@ __device__ __noinline__ bool exact_ball(const SimParams &P, const Rep &R, uint4 
 //   what 1: forward CB trial y = o + e (around the old reference point) vs the new pose
 //   what 2: point e vs neighbour j
 //   what 3: forward CB trial y = o + e vs neighbour j
-// e = R_s (s11(w.x), s11(w.y), s11(w.z)): a circumsphere point (a depletant
-// with the circumsphere V_0, or a CB trial).
+// e: the point of words w (half as in point64): a circumsphere point (a
+// depletant with the circumsphere V_0, or a CB trial).
 __device__ __noinline__ bool exact_dep(const SimParams &P, const Rep &R, uint32_t sweep, int i, uint4 w, int what,
-                                       int j, const int *acc, int nacc)
+                                       int j, const int *acc, int nacc, int half = -1)
 {
     const Move64 m = move64(P, R, sweep, i);
-    const double e0 = R.R_s * s11(w.x), e1 = R.R_s * s11(w.y), e2 = R.R_s * s11(w.z);
+    double e0, e1, e2;
+    point64(R, w, half, e0, e1, e2);
     double v0 = e0, v1 = e1, v2 = e2;
     if (what == 1 || what == 3) {
         v0 = m.o0 + e0;
@@ -139,20 +159,19 @@ __device__ __noinline__ bool exact_dep_shell(const SimParams &P, const Rep &R, u
 }
 
 // A lens point (attempt t of the depletant stream) free of every neighbour?
+// (hard interactions: the shell's own points, else the paired stream)
 __device__ __noinline__ bool exact_free_nb(const SimParams &P, const Rep &R, uint32_t sweep, int i, uint32_t t,
                                            const float4 *nb, int nnb, const int *acc, int nacc)
 {
-    const uint4 w = draw(R.key0, R.key1, sweep, (uint32_t)(i - R.off), kPDep, 0, t);
     double e0, e1, e2;
     if (R.v0_shell) {
+        const uint4 w = draw(R.key0, R.key1, sweep, (uint32_t)(i - R.off), kPDep, 0, t);
         const double3 e = shell_dep_point64(R, sweep, i, w);
         e0 = e.x;
         e1 = e.y;
         e2 = e.z;
     } else {
-        e0 = R.R_s * s11(w.x);
-        e1 = R.R_s * s11(w.y);
-        e2 = R.R_s * s11(w.z);
+        paired_point64(R.key0, R.key1, R.R_s, sweep, (uint32_t)(i - R.off), t, e0, e1, e2);
     }
     const Move64 m = move64(P, R, sweep, i);
     for (int a = 0; a < nnb; ++a) {
@@ -480,10 +499,96 @@ __device__ __forceinline__ bool cb_pass(DepShared &sh, int tid, int nslots, bool
 // stream, lens points, FP64 re-takes), the same in every lane.  SOFT: the
 // soft interaction keeps the points neither of whose early exits is certain
 // in FP32 (instead of those outside the old pose).
+// lens_of_move for hard interactions with the circumsphere (V0 = 0) or cube
+// (V0 = 2) V_0: the paired depletant stream.  A pass covers a block of 64
+// attempts: each lane draws one Philox call and the warp takes the first
+// halves (attempts t0 + lane), then the second halves (t0 + 32 + lane), each
+// sub-pass ranked by ballot as the one-point form ranks its passes.  Same
+// output as lens_of_move.
+template <int V0>
+__device__ __forceinline__ int4 lens_of_move_paired(const SimParams &P, const Rep &R, int g,
+                                                    uint32_t sweep, float4 *mv, float4 *sdst,
+                                                    int room, float4 *gdst)
+{
+    constexpr bool CUBE = V0 == 2;
+    const int lane = threadIdx.x & 31;
+    const int i = g;
+    const uint32_t tag = (uint32_t)(g - R.off);
+    const RoundKeys K = round_keys(R.key0, R.key1);
+    // the move's words (lane 0) and its Poisson words (lane 1) in one
+    // evaluation of the generator, then shared
+    const uint4 wl = philox_rk(make_uint4(sweep, tag, (lane == 1 ? kPPoisson : kPMove) << 24, 0u), K);
+    const uint32_t wm0 = __shfl_sync(kFull, wl.x, 0), wm1 = __shfl_sync(kFull, wl.y, 0),
+                   wm2 = __shfl_sync(kFull, wl.z, 0);
+    const uint32_t wp0 = __shfl_sync(kFull, wl.x, 1), wp1 = __shfl_sync(kFull, wl.y, 1);
+    const float D0 = coord32(wm0, R.d_max32);
+    const float D1 = coord32(wm1, R.d_max32);
+    const float D2 = coord32(wm2, R.d_max32);
+    if (lane == 0) *mv = make_float4(D0, D1, D2, 0.0f);
+    if (!R.has_dep) return make_int4(0, 0, 0, 0);
+    uint32_t rck = 0;
+    const float o0 = -D0, o1 = -D1, o2 = -D2;
+    const int n_p = poisson_count(P.T + R.t_off, R.nF, u53_int(wp0, wp1), lane);
+    const uint32_t t_max = 64u * (uint32_t)(n_p + 1);   // a multiple of 64: whole blocks
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t t0 = 0;
+    int k0 = 0, m = 0;
+    while (k0 < n_p && t0 < t_max) {
+        const uint4 w = philox_rk(make_uint4(sweep, tag, kPDep << 24, (t0 >> 1) + (uint32_t)lane), K);
+#pragma unroll 1
+        for (int h = 0; h < 2 && k0 < n_p; ++h) {
+            const uint32_t t = t0 + 32u * (uint32_t)h + (uint32_t)lane;
+            const uint3 f = paired_fields(w, (uint32_t)h);
+            const float e0 = s21f_bits(f.x) * R.R_s32, e1 = s21f_bits(f.y) * R.R_s32,
+                        e2 = s21f_bits(f.z) * R.R_s32;
+            // in the sampling region (the ball; the cube takes every point)
+            int in = CUBE ? 1 : tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
+            // overlaps the new pose (the cube's points only inside the ball;
+            // for the ball it is the same test) and the old pose: 1 yes, 0
+            // no, -1 within the margin; one vote for every uncertain decision
+            int tn = CUBE ? tri(norm2f(e0, e1, e2), R.T_dep32, R.m_r2) : 1;
+            int to = in != 0 && tn != 0 ? tri(norm2f(e0 - o0, e1 - o1, e2 - o2), R.T_dep32, R.m_r2)
+                                        : 1;
+            if (__any_sync(kFull, in == -1 || tn == -1 || to == -1)) {
+                if (in == -1) {
+                    ++rck;
+                    in = exact_ball(P, R, w, h) ? 1 : 0;
+                }
+                if (CUBE && tn == -1) {
+                    ++rck;
+                    tn = exact_ball(P, R, w, h) ? 1 : 0;
+                }
+                if (to == -1 && in == 1 && tn == 1) {
+                    ++rck;
+                    to = exact_dep(P, R, sweep, i, w, 0, 0, nullptr, 0, h) ? 1 : 0;
+                }
+            }
+            const unsigned bal = __ballot_sync(kFull, in == 1);
+            const int k = k0 + __popc(bal & lt);
+            const bool dep = in == 1 && k < n_p && tn == 1;
+            const bool lens = dep && to == 0;
+            const unsigned lb = __ballot_sync(kFull, lens);
+            const int slot = m + __popc(lb & lt);
+            if (lens) {
+                const float4 v = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
+                if (slot < room) sdst[slot] = v;
+                else if (slot < P.lens_cap) gdst[slot] = v;
+            }
+            m += __popc(lb);
+            k0 += __popc(bal);
+        }
+        t0 += 64u;
+    }
+    if (lane == 0 && m > P.lens_cap) atomicCAS(P.err, kErrNone, kErrCandCap);
+    rck = __reduce_add_sync(kFull, rck);
+    return make_int4(n_p, min(k0, n_p), min(m, P.lens_cap), (int)rck);
+}
+
 template <int V0, bool SOFT>
 __device__ __forceinline__ int4 lens_of_move(const SimParams &P, const Rep &R, int g, uint32_t sweep, float4 *mv,
                                           float4 *sdst, int room, float4 *gdst)
 {
+    if constexpr (!SOFT) return lens_of_move_paired<V0>(P, R, g, sweep, mv, sdst, room, gdst);
     static_assert(V0 == 0 || V0 == 2, "circumsphere or cube");
     constexpr bool CUBE = V0 == 2;
     const int lane = threadIdx.x & 31;

@@ -283,13 +283,19 @@ __global__ void __launch_bounds__(kMaxThreads)
                 bool inside = false;
                 uint4 w = make_uint4(0, 0, 0, 0);
                 if (t < t_max) {
-                    w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, t);
                     if (lvl > 0) {
+                        w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, t);
                         inside = shell_point64(R, lvl, w, e0, e1, e2);
-                    } else {
+                    } else if (R.soft_eps > 0.0) {
+                        // soft: one point per call, its fourth word decides blocking
+                        w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, t);
                         e0 = R.R_s * s11(w.x);
                         e1 = R.R_s * s11(w.y);
                         e2 = R.R_s * s11(w.z);
+                        inside = R.v0_cube || norm2(e0, e1, e2) < R.R_s2;
+                    } else {
+                        // hard: the paired stream
+                        paired_point64(R.key0, R.key1, R.R_s, sweep, tag, t, e0, e1, e2);
                         inside = R.v0_cube || norm2(e0, e1, e2) < R.R_s2;
                     }
                 }
