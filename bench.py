@@ -58,15 +58,20 @@ BATCHED = "batched_128_spheres_N500-20000_phi0.10-0.45_q0.10-0.20_eta0.05-0.40"
 #  Philox4x32-10 with the round keys precomputed: 10 rounds x (two 32x32
 #  multiplies giving both halves of the product, two three-input XORs)
 OPS_PHILOX = 40.0
-#  an attempt of a depletant stream: one Philox call, three coordinates from
-#  the words (3 x 3) and the ball test (3 FMA-type ops + compare): 13 more
+#  an attempt of a one-point stream (CB trials, the Gibbs exchange): one
+#  Philox call, three coordinates from the words (3 x 3) and the ball test
+#  (3 FMA-type ops + compare): 13 more
 OPS_ATTEMPT = OPS_PHILOX + 13.0
+#  an attempt of a move's paired depletant stream: half a Philox call (two
+#  points per call), the same coordinates and ball test
+OPS_ATTEMPT_PAIRED = 0.5 * OPS_PHILOX + 13.0
 #  an accepted point: the new- and old-pose tests (difference, squared length,
 #  compare)
 OPS_DEP = 8.0
-#  per move in the lens kernel: the move and Poisson draws, the proposal and
-#  its cell test, the Poisson table search
-OPS_MOVE_LENS = 2 * OPS_PHILOX + 20.0 + 12.0
+#  per move in the lens kernel: the move and Poisson draws (one Philox
+#  evaluation: lanes draw different counters), the proposal and its cell
+#  test, the Poisson table search
+OPS_MOVE_LENS = OPS_PHILOX + 20.0 + 12.0
 #  per move in the colour phases: cell test, ~25 neighbour-pair tests (8
 #  ops), the lens points against the neighbours near the move (~5 x 8)
 OPS_MOVE_PHASE = 20.0 + 25 * 8.0 + 5 * 8.0
@@ -178,10 +183,12 @@ def tune_update(d: float, accept: int, moves: int, w: float) -> float:
     return min(max(d, 1e-4), 0.25 * w)
 
 
-def batched_workload(rank: int = 0):
+def batched_workload(rank: int = 0, count: int = N_REPLICAS):
+    """The batch (its first `count` replicas: a smaller case of the same
+    workload, for profiler captures)."""
     from paper_1508_07077_gb300 import replicas as R, workloads as W
-    reps = W.batched_replicas(N_REPLICAS, seed=1)
-    keys = R.replica_ids(N_REPLICAS, rank)
+    reps = W.batched_replicas(N_REPLICAS, seed=1)[:count]
+    keys = R.replica_ids(N_REPLICAS, rank)[:count]
     widths = [cell_width(s.L, s.q) for s in reps]
     return reps, keys, widths
 
@@ -189,7 +196,7 @@ def batched_workload(rank: int = 0):
 # --- CPU oracle legs ------------------------------------------------------------
 
 class OracleBatch:
-    """The 128 replicas advanced by the CPU oracle, one replica per task on a
+    """The batch's replicas advanced by the CPU oracle, one replica per task on a
     pool of host threads (replicas are independent; the oracle's C code runs
     without the interpreter lock), or serially on one core."""
 
@@ -234,12 +241,12 @@ class OracleBatch:
         return d
 
 
-def cpu_baseline_batched(d_gpu, warmup, rank):
+def cpu_baseline_batched(d_gpu, warmup, rank, count=N_REPLICAS):
     """The oracle on this host: the step-size procedure and the warm-up sweeps
     on all cores, then one sweep of every replica on all cores (timed, 3
     times) and the same first sweep on one core (timed); the one-core and
     all-core results must be identical."""
-    reps, keys, widths = batched_workload(rank)
+    reps, keys, widths = batched_workload(rank, count)
     cores = os.cpu_count() or 1
     ob = OracleBatch(reps, keys, cores)
     t0 = time.perf_counter()
@@ -268,7 +275,7 @@ def cpu_baseline_batched(d_gpu, warmup, rank):
         "value": moves_all / t_all, "unit": "moves/s", "cores": cores, "kind": "oracle",
         "cpu": cpu_model(),
         "sample": "the headline workload after the same step-size procedure and %d warm-up "
-                  "sweeps (%.1f s on %d cores): 3 sweeps of all 128 replicas on %d cores "
+                  "sweeps (%.1f s on %d cores): 3 sweeps of every replica on %d cores "
                   "(%d moves, %.1f s), the first of them again on 1 core"
                   % (warmup, prep_s, cores, cores, moves_all, t_all),
         "one_core": {"value": moves_one / t_one, "unit": "moves/s", "cores": 1,
@@ -289,7 +296,7 @@ def run_reference(args, ws, rank):
         print(json.dumps({"impl": "reference", "unavailable":
                           "the reference arm covers the headline workload (batched) only"}))
         return
-    reps, keys, widths = batched_workload(0)
+    reps, keys, widths = batched_workload(0, args.replicas)
     cores = os.cpu_count() or 1
     ob = OracleBatch(reps, keys, cores)
     d = ob.tune(widths)
@@ -309,12 +316,12 @@ def run_reference(args, ws, rank):
         "unit": "moves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": batched_config(),
+        "config": batched_config(args.replicas, sum(s.n for s in reps)),
         "insertions_drawn_per_s": drawn / total,
         "insertions_evaluated_per_s": evaluated / total,
         "cpu_baseline": {"value": value, "unit": "moves/s", "cores": cores, "kind": "oracle",
                          "cpu": cpu_model(),
-                         "sample": "%d steps, each one sweep of all 128 replicas (%d moves), "
+                         "sample": "%d steps, each one sweep of every replica (%d moves), "
                                    "replicas on %d threads" % (args.steps, moves, cores)},
         "e2e": {"value": value, "unit": "moves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -322,10 +329,11 @@ def run_reference(args, ws, rank):
     print(json.dumps(line))
 
 
-def batched_config():
-    return {"workload": BATCHED, "replicas": N_REPLICAS, "colloids": 621288,
+def batched_config(count: int = N_REPLICAS, colloids: int = 621288):
+    name = BATCHED if count == N_REPLICAS else BATCHED + "_first%d" % count
+    return {"workload": name, "replicas": count, "colloids": colloids,
             "form": "FP32+FP64 recheck", "n_trial": 0,
-            "step": "1 sweep of every replica (621288 moves), one batch",
+            "step": "1 sweep of every replica (%d moves), one batch" % colloids,
             "start": "fcc starts, %d rounds x %d sweeps of the step-size rule (d_max from %g "
                      "towards 30%% acceptance, per replica), then the warm-up sweeps"
                      % (TUNE_ROUNDS, TUNE_SWEEPS, D_START),
@@ -394,7 +402,7 @@ def kernel_times(hpmc, ctx, step, flush, n):
 def lens_ops(tc):
     """Algorithmic lane-ops of the lens kernel for counters tc."""
     attempts = ATTEMPTS_PER_POINT * tc["dep_drawn"]
-    return OPS_ATTEMPT * attempts + OPS_DEP * tc["dep_drawn"] + OPS_MOVE_LENS * tc["moves"]
+    return OPS_ATTEMPT_PAIRED * attempts + OPS_DEP * tc["dep_drawn"] + OPS_MOVE_LENS * tc["moves"]
 
 
 def fp32_rooflines(km, kn, tc, pk):
@@ -407,10 +415,17 @@ def fp32_rooflines(km, kn, tc, pk):
     fp32_peak = pk["ffma_per_s"] / 1e12
     if kn[2]:
         a = lens_ops(tc) / (km[2] * 1e-3) / 1e12
+        # the generator's own share: one call per two attempts and one per move
+        calls = 0.5 * ATTEMPTS_PER_POINT * tc["dep_drawn"] + tc["moves"]
+        calls_rate = calls / (km[2] * 1e-3)
         out["k_lens_sphere_fp32"] = {"ms": km[2], "achieved": a, "peak": philox_peak,
                                      "frac": a / philox_peak,
                                      "peak_basis": "measured Philox4x32-10 (round keys) calls/s "
-                                                   "x 40 lane-ops"}
+                                                   "x 40 lane-ops",
+                                     "depletants_drawn_per_s": tc["dep_drawn"] / (km[2] * 1e-3),
+                                     "philox_calls_per_s": calls_rate,
+                                     "philox_frac_of_measured": calls_rate /
+                                     pk["philox_rk_calls_per_s"]}
     if kn[1]:
         a = OPS_MOVE_PHASE * tc["moves"] / (km[1] * 1e-3) / 1e12
         out["colour_phases"] = {"ms": km[1], "achieved": a, "peak": fp32_peak,
@@ -433,7 +448,7 @@ def run_batched(args, ws, rank, local):
     hpmc = load_lib()
     pk = peaks.measure()
     stream = torch.cuda.current_stream()
-    reps, keys, widths = batched_workload(rank)
+    reps, keys, widths = batched_workload(rank, args.replicas)
     ns = [s.n for s in reps]
     n_all = sum(ns)
     descs = [{"n": s.n, "box_l": s.L, "pos": s.pos, "q": s.q, "n_r": s.n_r, "n_trial": 0,
@@ -528,7 +543,7 @@ def run_batched(args, ws, rank, local):
             "ms_per_step": ms / (args.steps * repeats), "repeats": repeats,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": dict(batched_config(), schedule="persistent colour phases"
+            "config": dict(batched_config(args.replicas, n_all), schedule="persistent colour phases"
                            if args.schedule == 1 else "eight phase launches per sweep",
                            timed_region="the K-step loop repeated %d times (>= 1 s)" % repeats),
             "insertions_drawn_per_s": drawn_all / (ms * 1e-3),
@@ -621,6 +636,18 @@ def spheres_16384(args, local, pk):
                                "insertions_drawn_per_s": sc["dep_drawn"] / (sms * 1e-3),
                                "acceptance": sc["accept"] / max(1, sc["moves"])}
             hpmc.hpmc_set_v0(ctx, hpmc.HPMC_V0_CIRCUMSPHERE)
+            # the soft (Hertz, eps = 10 kT) colloid-depletant interaction,
+            # same systems and steps
+            hpmc.hpmc_set_soft(ctx, 10.0)
+            for _ in range(3):
+                step()
+            hpmc.hpmc_reset_counters(ctx)
+            fms, _ = timed_steps(step, K, stream, flush)
+            _, fc = hpmc.hpmc_get_state(ctx)
+            res["soft_eps10"] = {"value": fc["moves"] / (fms * 1e-3), "ms_per_step": fms / K,
+                                 "acceptance": fc["accept"] / max(1, fc["moves"]),
+                                 "fp64_rechecks_per_move": fc["rechecks"] / max(1, fc["moves"])}
+            hpmc.hpmc_set_soft(ctx, 0.0)
             out["fp32"] = res
             # the oracle on all cores (cells of a colour phase on threads) from
             # the same start and step sizes, 2 sweeps of each system
@@ -849,6 +876,9 @@ def main():
                          "attempts/s)")
     ap.add_argument("--schedule", type=int, choices=(0, 1), default=0,
                     help="colour phases: 0 eight launches per sweep, 1 one persistent launch")
+    ap.add_argument("--replicas", type=int, default=N_REPLICAS,
+                    help="the first R replicas of the batch (a smaller case of the same "
+                         "workload, e.g. for profiler captures); 128 is the headline")
     ap.add_argument("--no-extras", action="store_true",
                     help="the headline only (no one-at-a-time run, other schedule or "
                          "single-system workloads)")
@@ -857,6 +887,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if not 1 <= args.replicas <= N_REPLICAS:
+        ap.error("--replicas must be in 1..%d" % N_REPLICAS)
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, ws, rank)
@@ -873,7 +905,7 @@ def main():
                          "hemispheres_32768": shape_system(args, local, "hemispheres", pk),
                          "discoids_65536": shape_system(args, local, "discoids", pk)}
     if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_batched(d, args.warmup, rank)
+        line["cpu_baseline"] = cpu_baseline_batched(d, args.warmup, rank, args.replicas)
     print(json.dumps(line))
 
 
