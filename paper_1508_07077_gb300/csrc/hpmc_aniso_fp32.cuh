@@ -174,19 +174,23 @@ __global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__
     const unsigned lt = (1u << lane) - 1u;
     uint32_t t0 = 0;
     int k0 = 0, m = 0;
+    uint4 wc = make_uint4(0, 0, 0, 0);
     while (k0 < n_p && t0 < t_max) {
         const uint32_t t = t0 + (uint32_t)lane;
-        uint4 w = make_uint4(0, 0, 0, 0);
         float e0 = 0.f, e1 = 0.f, e2 = 0.f;
         int in = 0;
-        // the paired stream: attempt t is half paired_half(t) of call paired_call(t)
+        // the paired stream: attempt t is half paired_half(t) of call
+        // paired_call(t); a pass of 32 attempts takes one half of the lanes'
+        // 32 calls, so the words are drawn on the first half's pass and kept
+        // for the second (t_max is a multiple of 64: whole blocks)
         const int half = (int)paired_half(t);
+        if ((t0 & 32u) == 0u) wc = draw(R.key0, R.key1, sweep, tag, kPDep, 0, paired_call(t));
+        const uint4 w = wc;
         if (t < t_max) {
-            w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, paired_call(t));
             const uint3 f = paired_fields(w, (uint32_t)half);
-            e0 = s21f(f.x) * R.R_s32;
-            e1 = s21f(f.y) * R.R_s32;
-            e2 = s21f(f.z) * R.R_s32;
+            e0 = s21f_bits(f.x) * R.R_s32;
+            e1 = s21f_bits(f.y) * R.R_s32;
+            e2 = s21f_bits(f.z) * R.R_s32;
             in = R.v0_cube ? 1 : tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
         }
         {

@@ -142,7 +142,9 @@ __host__ __device__ __forceinline__ uint3 paired_fields(uint4 w, uint32_t h)
                       (w.y & 0x7FFu) | (((w.w >> 10) & 0x3FFu) << 11),
                       (w.z & 0x7FFu) | (((w.w >> 20) & 0x3FFu) << 11));
 }
-__device__ __forceinline__ double s21(uint32_t a) { return ((double)a + 0.5) * 0x1p-20 - 1.0; }
+// (as one fused multiply-add: a 2^-20 + (2^-21 - 1) is exactly representable,
+// so the single rounding is exact and the value is (a + 1/2) 2^-20 - 1)
+__device__ __forceinline__ double s21(uint32_t a) { return __fma_rn((double)a, 0x1p-20, 0x1p-21 - 1.0); }
 // the same value in FP32: a + 1/2 has at most 22 significant bits, the
 // scaling is exact and so is the subtraction (the result is a multiple of
 // 2^-21 below 1 in magnitude)
