@@ -365,11 +365,15 @@ def timed_steps(step, K, stream, flush, min_ms=0.0, ws=1):
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
+        # an NVTX range over the timed launches, so that a profiler can be
+        # limited to them (ncu --nvtx --nvtx-include "timed steps/")
+        torch.cuda.nvtx.range_push("timed steps")
         for k in range(K):
             flush.zero_()
             a[k].record(stream)
             step()
             b[k].record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
@@ -649,8 +653,8 @@ def spheres_16384(args, local, pk):
                                  "fp64_rechecks_per_move": fc["rechecks"] / max(1, fc["moves"])}
             hpmc.hpmc_set_soft(ctx, 0.0)
             out["fp32"] = res
-            # the oracle on all cores (cells of a colour phase on threads) from
-            # the same start and step sizes, 2 sweeps of each system
+            # the oracle on all cores (cells of a colour phase on threads), 2
+            # sweeps of each system from the fcc start at the starting step size
             if not args.no_cpu_baseline:
                 from oracle import oracle as O
                 O.build()
@@ -773,6 +777,7 @@ def run_gibbs(args, ws, rank, local):
         dist.barrier()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed steps")
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
@@ -780,6 +785,7 @@ def run_gibbs(args, ws, rank, local):
             ev[k][1].record(stream)
             hpmc.hpmc_gibbs_exchange(gp.ctx, n_ex, stream)
             ev[k][2].record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -864,16 +870,39 @@ def run_gibbs(args, ws, rank, local):
         dist.destroy_process_group()
 
 
+SINGLE = ("spheres_16384", "hemispheres_32768", "discoids_65536")
+
+
+def single_entry(args, local, name, pk):
+    if name == "spheres_16384":
+        return spheres_16384(args, local, pk)
+    return shape_system(args, local, name.split("_")[0], pk)
+
+
+def run_single(args, ws, rank, local):
+    """One single-system workload on its own (rank 0 of a 1-GPU run): its
+    entry of the headline line's "extra" object, printed as one JSON line."""
+    import torch
+    from paper_1508_07077_gb300 import peaks
+    if ws > 1:
+        raise SystemExit("--workload %s runs on one GPU" % args.workload)
+    torch.cuda.set_device(local)
+    entry = single_entry(args, local, args.workload, peaks.measure())
+    print(json.dumps({"workload": args.workload, "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "data": "synthetic", **entry}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("batched", "gibbs"), default="batched",
+    ap.add_argument("--workload", choices=("batched", "gibbs") + SINGLE, default="batched",
                     help="batched: the headline 128-replica workload, with the single-system "
                          "workloads beside it; gibbs: 152 Gibbs-ensemble pairs (exchange "
-                         "attempts/s)")
+                         "attempts/s); a single-system name runs that entry alone (e.g. for "
+                         "profiler captures)")
     ap.add_argument("--schedule", type=int, choices=(0, 1), default=0,
                     help="colour phases: 0 eight launches per sweep, 1 one persistent launch")
     ap.add_argument("--replicas", type=int, default=N_REPLICAS,
@@ -896,14 +925,15 @@ def main():
     if args.workload == "gibbs":
         run_gibbs(args, ws, rank, local)
         return
+    if args.workload in SINGLE:
+        run_single(args, ws, rank, local)
+        return
     line, d = run_batched(args, ws, rank, local)
     if rank != 0:
         return
     if ws == 1 and not args.no_extras:
         pk = line["pipe_peaks_measured"]
-        line["extra"] = {"spheres_16384": spheres_16384(args, local, pk),
-                         "hemispheres_32768": shape_system(args, local, "hemispheres", pk),
-                         "discoids_65536": shape_system(args, local, "discoids", pk)}
+        line["extra"] = {name: single_entry(args, local, name, pk) for name in SINGLE}
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_batched(d, args.warmup, rank, args.replicas)
     print(json.dumps(line))

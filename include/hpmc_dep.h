@@ -176,6 +176,17 @@ int hpmc_set_cells(hpmc_ctx *ctx, int n_cell);
  * identical for every value.  HPMC_ERR_ARG for an unknown schedule. */
 int hpmc_set_launch(hpmc_ctx *ctx, int warps_per_colloid, int phase_schedule);
 
+/* Grid of each colour-phase launch (HPMC_PHASES_LAUNCHES, HPMC_FP32_RECHECK
+ * form of spheres, one warp per colloid): 0 launches one CTA per cell of the
+ * phase; 1..64 launches that many waves of resident one-warp CTAs, each
+ * taking every grid-th non-empty cell of the phase in turn (fewer CTA
+ * launches where a phase has many cells per SM, at 24 instead of 32
+ * resident CTAs per SM); -1 (the default) chooses 2 when a phase has more
+ * cells than one wave of the one-CTA-per-cell grid, else 0.  A performance knob only:
+ * results are identical for every value.  Takes effect at the next sweep.
+ * HPMC_ERR_ARG outside -1..64. */
+int hpmc_set_phase_waves(hpmc_ctx *ctx, int waves);
+
 /* Bound of every device-side wait of the persistent colour phases, in
  * seconds of GPU global time (default 1; 1e-6 .. 60).  A wait that runs out
  * records HPMC_ERR_TIMEOUT (reported by the next synchronising call, as

@@ -146,6 +146,9 @@ __global__ void k_task_order(const __grid_constant__ SimParams P)
         const int phase = t / P.n_cta;
         tk = P.task[t];
         const int n = P.count[tk.w >> 16][tk.x];
+        // every cell is one task: its population of the next sweep starts
+        // from zero (nothing reads that buffer before the next binning)
+        P.count[(tk.w >> 16) ^ 1][tk.x] = 0;
         // persistent colour phases: one class of non-empty cells, kept close
         // to the table's spatial order (blocks run in roughly increasing
         // order), so that a cell's neighbours of the previous phase sit about

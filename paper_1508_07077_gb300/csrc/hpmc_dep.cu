@@ -105,6 +105,7 @@ struct hpmc_ctx {
     double wait_s = 1.0;      // bound of every device-side wait
     int withhold = -1;        // test only: a cell whose readiness is never published
     int ticket_chunk = 1;     // persistent colour phases: work items per ticket atomic
+    int phase_waves = -1;     // FP32 sphere phases: CTA waves per launch (0: a CTA per cell; -1 automatic)
 
     bool timing = false;
     std::vector<cudaEvent_t> tev;   // pairs (start, stop)
@@ -562,6 +563,43 @@ void launch_pdl1(K kernel, int grid, int block, cudaStream_t s, const SimParams 
     cudaLaunchKernelEx(&cfg, kernel, P);
 }
 
+// CTAs of a kernel resident on the whole GPU at once.
+template <typename K>
+int resident_ctas(K kernel, int threads, size_t dyn)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, dyn);
+    return sms * std::max(1, per_sm);
+}
+
+// Waves of the looping FP32 sphere colour phases (0: a CTA per cell).  Set:
+// c->phase_waves; automatic (-1): two waves when a phase has more cells than
+// one wave of the one-CTA-per-cell kernel holds (CTA launches are then a
+// large part of a phase), else none.
+template <typename K>
+int phase_waves(const hpmc_ctx *c, K single, int threads, size_t dyn)
+{
+    if (c->phase_waves >= 0) return c->phase_waves;
+    return c->n_cta > resident_ctas(single, threads, dyn) ? 2 : 0;
+}
+
+// One FP32 sphere colour phase of the one-warp kernel: a CTA per cell, or
+// waves of looping CTAs (identical results: any grid size is correct).
+template <typename K1, typename KL>
+void launch_phase_sphere32(const hpmc_ctx *c, K1 single, KL loop, size_t dyn, cudaStream_t s,
+                           const SimParams &P, int phase)
+{
+    const int w = phase_waves(c, single, 32, dyn);
+    if (w <= 0) {
+        launch_pdl(single, c->n_cta, 32, dyn, s, P, phase);
+        return;
+    }
+    const long long g = (long long)w * resident_ctas(loop, 32, dyn);
+    launch_pdl(loop, (int)std::max(1LL, std::min((long long)c->n_cta, g)), 32, dyn, s, P, phase);
+}
+
 template <int CAP>
 void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s)
 {
@@ -586,13 +624,16 @@ void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s
     } else if (c->precision == HPMC_FP32_RECHECK) {
         const bool warp = threads == 32;
         if (cb) {
-            if (warp) launch_pdl(k_phase_sphere_fp32<true, true, CAP>, c->n_cta, threads, dyn, s, P, phase);
+            if (warp) launch_phase_sphere32(c, k_phase_sphere_fp32<true, true, CAP>,
+                                            k_phase_sphere_fp32<true, true, CAP, false, true>, dyn, s, P, phase);
             else launch_pdl(k_phase_sphere_fp32<true, false, CAP>, c->n_cta, threads, dyn, s, P, phase);
         } else if (c->prm.soft_eps > 0.0) {
-            if (warp) launch_pdl(k_phase_sphere_fp32<false, true, CAP, true>, c->n_cta, threads, dyn, s, P, phase);
+            if (warp) launch_phase_sphere32(c, k_phase_sphere_fp32<false, true, CAP, true>,
+                                            k_phase_sphere_fp32<false, true, CAP, true, true>, dyn, s, P, phase);
             else launch_pdl(k_phase_sphere_fp32<false, false, CAP, true>, c->n_cta, threads, dyn, s, P, phase);
         } else {
-            if (warp) launch_pdl(k_phase_sphere_fp32<false, true, CAP>, c->n_cta, threads, dyn, s, P, phase);
+            if (warp) launch_phase_sphere32(c, k_phase_sphere_fp32<false, true, CAP>,
+                                            k_phase_sphere_fp32<false, true, CAP, false, true>, dyn, s, P, phase);
             else launch_pdl(k_phase_sphere_fp32<false, false, CAP>, c->n_cta, threads, dyn, s, P, phase);
         }
     } else if (c->prm.shape == HPMC_SPHERE) {
@@ -1188,6 +1229,11 @@ int create_ctx(hpmc_ctx **out, const std::vector<RepHost> &reps, uint64_t seed, 
         const int v = atoi(e);
         if (v >= 1 && v <= 1024) c->ticket_chunk = v;
     }
+    // and of the FP32 sphere colour phases (hpmc_set_phase_waves)
+    if (const char *e = getenv("HPMC_PHASE_WAVES")) {
+        const int v = atoi(e);
+        if (v >= -1 && v <= 64) c->phase_waves = v;
+    }
     DeviceGuard g(device);
     int rc = alloc_ctx(c);
     if (rc != HPMC_OK) {
@@ -1384,6 +1430,14 @@ int hpmc_set_launch(hpmc_ctx *c, int warps_per_colloid, int phase_schedule)
         return HPMC_ERR_ARG;
     c->prm.warps = warps_per_colloid;
     c->prm.schedule = phase_schedule;
+    c->dirty = true;
+    return HPMC_OK;
+}
+
+int hpmc_set_phase_waves(hpmc_ctx *c, int waves)
+{
+    if (!c || waves < -1 || waves > 64) return HPMC_ERR_ARG;
+    c->phase_waves = waves;
     c->dirty = true;
     return HPMC_OK;
 }

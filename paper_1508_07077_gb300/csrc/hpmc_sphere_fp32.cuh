@@ -888,9 +888,6 @@ __device__ __forceinline__ void phase_cell(const SimParams &P, int phase, int4 t
                 m_cell = R.m_cell, nb_cut2 = R.nb_cut2_32, T_dep = R.T_dep32,
                 T_contact = R.T_contact32;
     const int has_dep = R.has_dep;
-    // this cell's population of the next sweep (the persistent kernel clears
-    // the whole next-sweep buffer itself)
-    if (!PERSIST && tid == 0) P.count[par ^ 1][cell] = 0;
 
     // Loads, most of them before the wait for the neighbours (everything
     // about the own cell is fixed for the sweep or written only by this CTA):
@@ -1354,10 +1351,34 @@ __device__ __forceinline__ void phase_cell(const SimParams &P, int phase, int4 t
     flush_counters(P, r, cnt);
 }
 
-// One colour phase (FP32 form): a CTA per active cell, the cells of every
-// replica in the task table's order (fullest cells first).
-template <bool CB, bool WARP, int CAP, bool SOFT = false>
-__global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? ((CB || SOFT) ? 16 : 32) : 1)
+// Sizes of a phase's four population classes (the task ordering kernel's
+// counts), by a load the compiler keeps where it stands.
+__device__ __forceinline__ int4 ld_cls_count(const SimParams &P, int phase)
+{
+    int4 v;
+    asm volatile("ld.global.nc.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(P.cls_count + 4 * phase));
+    return v;
+}
+
+__device__ __forceinline__ int cls_busy(const SimParams &P, int phase)
+{
+    const int4 v = ld_cls_count(P, phase);
+    return v.x + v.y + v.z;
+}
+
+// One colour phase (FP32 form): the non-empty cells of every replica in the
+// task table's order (fullest cells first); empty cells have no work (the
+// task ordering kernel cleared their next-sweep populations).  LOOP false: a
+// CTA per cell of the phase (grid n_cta; CTAs past the non-empty cells return
+// at once).  LOOP true: a few waves of resident one-warp CTAs, CTA b taking
+// cells b, b + gridDim, ... (the cells of a phase are independent), which
+// saves a CTA launch per cell where a phase has many cells per SM; the loop
+// needs more registers per thread (24 resident CTAs per SM instead of 32).
+template <bool CB, bool WARP, int CAP, bool SOFT = false, bool LOOP = false>
+__global__ void __launch_bounds__(WARP ? 32 : kMaxThreads,
+                                  WARP ? ((CB || SOFT) ? 16 : (LOOP ? 24 : 32)) : 1)
     k_phase_sphere_fp32(const __grid_constant__ SimParams P, int phase)
 {
     // The phases are launched with programmatic dependent launch: the next
@@ -1367,28 +1388,30 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? ((CB || SOFT) 
     // FP64 state) are read and written only after it.
     pdl_trigger();
     if (phase == 7 && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(P.sweep, 1ull);
-    int cls = 0, idx = blockIdx.x;
-    {
-        const int4 cc = reinterpret_cast<const int4 *>(P.cls_count)[phase];
+    // this grid must not complete before its predecessor, even with no cell
+    // to move (a later phase's wait covers only this grid)
+    if (blockIdx.x == 0 && cls_busy(P, phase) == 0) pdl_wait();
+#pragma unroll 1
+    for (int b = blockIdx.x;; b += gridDim.x) {
+        // the class sizes are re-read for every cell (an L1 hit) rather than
+        // kept across the cell's work, which needs every register
+        const int4 cc = ld_cls_count(P, phase);
+        if (b >= cc.x + cc.y + cc.z) break;
+        int idx = b, cls = 0;
         if (idx >= cc.x) {
             idx -= cc.x;
             cls = 1;
             if (idx >= cc.y) {
                 idx -= cc.y;
                 cls = 2;
-                if (idx >= cc.z) {
-                    idx -= cc.z;
-                    cls = 3;
-                }
             }
         }
+        const int4 tk = P.task_ord[(size_t)(phase * 4 + cls) * P.n_cta + idx];
+        phase_cell<CB, WARP, CAP, SOFT, false>(P, phase, tk, 0u);
+        if (!LOOP) break;
+        // the shared-memory stage is the next cell's
+        cta_sync<WARP>();
     }
-    const int4 tk = P.task_ord[(size_t)(phase * 4 + cls) * P.n_cta + idx];
-    if (cls == 3) {               // an empty cell: only its next-sweep population
-        if (threadIdx.x == 0) P.count[(tk.w >> 16) ^ 1][tk.x] = 0;
-        return;
-    }
-    phase_cell<CB, WARP, CAP, SOFT, false>(P, phase, tk, 0u);
 }
 
 // All eight colour phases of a sweep in one persistent launch of one-warp
@@ -1408,10 +1431,6 @@ __global__ void __launch_bounds__(32, (CB || SOFT) ? 16 : 32)
     const int lane = threadIdx.x;
     pdl_wait();
     const uint32_t epoch0 = ld_acquire_u32(P.epoch);
-    const int par = (int)(P.sched[0].sweep & 1u);
-    // the next sweep's cell populations start from zero
-    int *next = P.count[par ^ 1];
-    for (int c = blockIdx.x * 32 + lane; c < P.n_cells; c += gridDim.x * 32) next[c] = 0;
     if (blockIdx.x == 0 && lane == 0) atomicAdd(P.sweep, 1ull);
     // non-empty tasks per phase (population classes 0..2): their exclusive
     // prefix over the phases and the first two class sizes, kept in shared

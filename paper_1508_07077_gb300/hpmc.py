@@ -28,7 +28,7 @@ HPMC_PHASES_LAUNCHES, HPMC_PHASES_PERSISTENT = 0, 1
 
 EXPORTS = ("hpmc_init", "hpmc_init_batch", "hpmc_get_replica", "hpmc_set_replica_moves",
            "hpmc_set_shape", "hpmc_set_depletant", "hpmc_set_moves",
-           "hpmc_set_cells", "hpmc_set_launch", "hpmc_set_wait_limit",
+           "hpmc_set_cells", "hpmc_set_launch", "hpmc_set_phase_waves", "hpmc_set_wait_limit",
            "hpmc_debug_withhold_cell", "hpmc_autotune", "hpmc_set_fp32_margin",
            "hpmc_set_v0", "hpmc_set_soft", "hpmc_set_live", "hpmc_get_live", "hpmc_gibbs_exchange",
            "hpmc_get_gibbs", "hpmc_set_timing",
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH):
     L.hpmc_set_cells.argtypes = [vp, ip]
     L.hpmc_set_launch.argtypes = [vp, ip, ip]
     L.hpmc_set_wait_limit.argtypes = [vp, ctypes.c_double]
+    L.hpmc_set_phase_waves.argtypes = [vp, ip]
     L.hpmc_debug_withhold_cell.argtypes = [vp, ip]
     L.hpmc_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ip, ctypes.POINTER(ctypes.c_int),
                                 ip, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -274,6 +275,10 @@ def hpmc_free_volume(ctx, q, *, replica=0, seed=7, sample=0, n_probe=1000000):
 def hpmc_set_launch(ctx, warps_per_colloid, phase_schedule=HPMC_PHASES_LAUNCHES):
     _check(load().hpmc_set_launch(ctx, int(warps_per_colloid), int(phase_schedule)),
            "hpmc_set_launch")
+
+
+def hpmc_set_phase_waves(ctx, waves):
+    _check(load().hpmc_set_phase_waves(ctx, int(waves)), "hpmc_set_phase_waves")
 
 
 def hpmc_set_wait_limit(ctx, seconds):

@@ -1,6 +1,7 @@
 """The persistent colour-phase schedule (all eight phases of a sweep in one
-launch, per-cell readiness counters) against the eight-launch schedule, and
-its bounded waits.
+launch, per-cell readiness counters) and the looping phase grids (waves of
+resident CTAs sharing a phase's cells) against the eight-launch schedule
+with a CTA per cell, and the persistent schedule's bounded waits.
 
 Both schedules run the same per-cell work in an order Sec. III.E allows (a
 cell moves only after the non-empty cells of its neighbourhood that belong to
@@ -36,6 +37,7 @@ def _run(lib, reps, schedule, sweeps, **kw):
     ctx = lib.hpmc_init_batch(reps, seed=kw.get("seed", 1), precision=1)
     try:
         lib.hpmc_set_launch(ctx, 1, schedule)
+        lib.hpmc_set_phase_waves(ctx, kw.get("waves", -1))
         if kw.get("soft"):
             lib.hpmc_set_soft(ctx, kw["soft"])
         if kw.get("v0"):
@@ -80,6 +82,42 @@ def test_persistent_equals_launches_batched(lib, n_trial, soft, v0):
                  "n_trial": n_trial, "d_max": 0.08, "replica": 24})
     a = _run(lib, reps, 1, 8, soft=soft, v0=v0)
     b = _run(lib, reps, 0, 8, soft=soft, v0=v0)
+    assert np.array_equal(a[0], b[0])
+    for k in a[2]:
+        assert a[2][k] == b[2][k], k
+
+
+@pytest.mark.parametrize("waves", [1, 3, -1])
+def test_phase_waves_equal_a_cta_per_cell_full_size(lib, waves):
+    """4 x 16384 spheres: 8788 cells per phase, so one wave of the looping
+    grid (24 CTAs per SM) gives some CTAs two cells or more."""
+    systems = [W.spheres_16384(eta, seed=1) for eta in BENCH_DMAX]
+    reps = [{"n": s.n, "box_l": s.L, "pos": s.pos, "q": s.q, "n_r": s.n_r,
+             "d_max": BENCH_DMAX[eta], "replica": k}
+            for k, (s, eta) in enumerate(zip(systems, BENCH_DMAX))]
+    a = _run(lib, reps, 0, 6, waves=waves)
+    b = _run(lib, reps, 0, 6, waves=0)
+    assert np.array_equal(a[0], b[0])
+    for k in a[2]:
+        assert a[2][k] == b[2][k], k
+    assert a[3] == b[3]
+
+
+@pytest.mark.parametrize("n_trial,soft,v0", [(3, 0.0, 0), (0, 10.0, 0), (0, 0.0, 1)])
+def test_phase_waves_equal_a_cta_per_cell_batched(lib, n_trial, soft, v0):
+    """96 uneven replicas (N 200..3000, down to two cells per side) with CB,
+    the soft interaction and the shell V_0, one wave against a CTA per
+    cell."""
+    rng = np.random.default_rng(13)
+    sys = [W.make_system("w%d" % k, W.SPHERE, int(rng.integers(200, 3000)),
+                         float(rng.uniform(0.1, 0.3)), float(rng.choice([0.1, 0.15, 0.2])),
+                         float(rng.uniform(0.05, 0.25)), seed=13, replica=k) for k in range(95)]
+    reps = [{"n": s.n, "box_l": s.L, "pos": s.pos, "q": s.q, "n_r": s.n_r, "n_trial": n_trial,
+             "d_max": 0.05, "replica": k} for k, s in enumerate(sys)]
+    reps.append({"n": 8, "box_l": 2.6, "pos": W.tiny_spheres(8, 2.6), "q": 0.2, "n_r": 30.0,
+                 "n_trial": n_trial, "d_max": 0.08, "replica": 95})
+    a = _run(lib, reps, 0, 6, soft=soft, v0=v0, waves=1)
+    b = _run(lib, reps, 0, 6, soft=soft, v0=v0, waves=0)
     assert np.array_equal(a[0], b[0])
     for k in a[2]:
         assert a[2][k] == b[2][k], k
@@ -133,5 +171,10 @@ def test_wait_limit_arguments(lib):
             lib.hpmc_debug_withhold_cell(smp.ctx, -2)
         with pytest.raises(lib.HPMCError):
             lib.hpmc_set_launch(smp.ctx, 1, 2)
+        for bad in (-2, 65):
+            with pytest.raises(lib.HPMCError):
+                lib.hpmc_set_phase_waves(smp.ctx, bad)
+        lib.hpmc_set_phase_waves(smp.ctx, 64)
+        lib.hpmc_sweep(smp.ctx, 1)
     finally:
         smp.close()
