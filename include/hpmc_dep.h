@@ -181,8 +181,9 @@ int hpmc_set_launch(hpmc_ctx *ctx, int warps_per_colloid, int phase_schedule);
  * phase; 1..64 launches that many waves of resident one-warp CTAs, each
  * taking every grid-th non-empty cell of the phase in turn (fewer CTA
  * launches where a phase has many cells per SM, at 24 instead of 32
- * resident CTAs per SM); -1 (the default) chooses 2 when a phase has more
- * cells than one wave of the one-CTA-per-cell grid, else 0.  A performance knob only:
+ * resident CTAs per SM); -1 (the default) chooses 2 for hard interactions
+ * without CB when a phase has more cells than one wave of the
+ * one-CTA-per-cell grid, else 0.  A performance knob only:
  * results are identical for every value.  Takes effect at the next sweep.
  * HPMC_ERR_ARG outside -1..64. */
 int hpmc_set_phase_waves(hpmc_ctx *ctx, int waves);

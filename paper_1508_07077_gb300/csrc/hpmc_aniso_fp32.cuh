@@ -440,16 +440,16 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
     int c_nb = 0, m_nb = 0, dx = 0, dy = 0, dz = 0;
     if (tid < n_st) {
         c_nb = stencil_cell_nc(nc, cell_off, tid, cx, cy, cz, dx, dy, dz);
-        const size_t b0 = (size_t)c_nb * P.cap;
         m_nb = count[c_nb];
         if (tid == t_own) {
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
-                s_mv[s] = P.mv_bin[b0 + s];
-                s_hdr[s] = P.hdr_bin[b0 + s];
+                const size_t bs = bin_at(P, c_nb, s);
+                s_mv[s] = P.mv_bin[bs];
+                s_hdr[s] = P.hdr_bin[bs];
 #pragma unroll
                 for (int j = 0; j < kLensInline; ++j)
-                    s_lin[s][j] = P.lens_bin[(b0 + s) * kLensInline + j];
+                    s_lin[s][j] = P.lens_bin[bs * kLensInline + j];
             }
         }
         m_nb = min(m_nb, P.cap);
@@ -490,18 +490,18 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
     if (tid < n_st) {
         const float fx = (float)dx * w32, fy = (float)dy * w32, fz = (float)dz * w32;
         const bool own = tid == t_own;
-        const size_t b0 = (size_t)c_nb * P.cap;
         for (int s = 0; s < m_nb; ++s) {
-            const float4 e = P.bins[b0 + s];
+            const size_t bs = bin_at(P, c_nb, s);
+            const float4 e = P.bins[bs];
             const int slot = base + s;
             s_cpos[slot] = make_float4(fx + e.x, fy + e.y, fz + e.z, e.w);
-            s_cq[slot] = P.bin_q[b0 + s];
+            s_cq[slot] = P.bin_q[bs];
             if (own) {
                 s_tmp_i[s] = __float_as_int(e.w);
                 s_tmp_slot[s] = slot;
                 if (s >= 2) {
-                    s_mv[s] = P.mv_bin[b0 + s];
-                    s_hdr[s] = P.hdr_bin[b0 + s];
+                    s_mv[s] = P.mv_bin[bs];
+                    s_hdr[s] = P.hdr_bin[bs];
                 }
             }
         }
@@ -537,7 +537,7 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
             if (n <= kLensInline && q < 2) {
                 if (tid < n) s_lens[o + tid] = s_lin[q][tid];
             } else if (n <= kLensInline) {
-                if (tid < n) s_lens[o + tid] = P.lens_bin[((size_t)cell * P.cap + q) * kLensInline + tid];
+                if (tid < n) s_lens[o + tid] = P.lens_bin[bin_at(P, cell, q) * kLensInline + tid];
             } else {
                 const float4 *src = P.lens + (size_t)s_tmp_i[q] * P.lens_cap;
                 for (int m = tid; m < n; m += nthr) s_lens[o + m] = src[m];
@@ -794,8 +794,8 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
                 const float4 rnew = make_float4(rn0, rn1, rn2, __int_as_float(i));
                 s_cpos[s_own_slot[q]] = rnew;
                 s_cq[s_own_slot[q]] = qn32;
-                if (translate) P.bins[(size_t)cell * P.cap + qb] = rnew;
-                else P.bin_q[(size_t)cell * P.cap + qb] = qn32;
+                if (translate) P.bins[bin_at(P, cell, qb)] = rnew;
+                else P.bin_q[bin_at(P, cell, qb)] = qn32;
                 s_accl[nacc] = i;
                 s_nacc = nacc + 1;
             }

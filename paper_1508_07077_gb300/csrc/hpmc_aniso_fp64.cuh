@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         const int m = min(T.count[c], P.cap);
         for (int s = 0; s < m; ++s) {
             const int slot = atomicAdd(&s_ncand, 1);
-            if (slot < kMaxCand) s_cand[slot] = __float_as_int(P.bins[(size_t)c * P.cap + s].w);
+            if (slot < kMaxCand) s_cand[slot] = __float_as_int(P.bins[bin_at(P, c, s)].w);
         }
     }
     __syncthreads();
@@ -362,7 +362,7 @@ __global__ void k_check_aniso(const __grid_constant__ SimParams P, int *flag)
         const int c = stencil_cell(R, t, cx, cy, cz, dx, dy, dz);
         const int m = min(count[c], P.cap);
         for (int s = 0; s < m; ++s) {
-            const int j = __float_as_int(P.bins[(size_t)c * P.cap + s].w);
+            const int j = __float_as_int(P.bins[bin_at(P, c, s)].w);
             if (j == g) continue;
             const double4 pj = P.pos[j];
             const Vec3 d = v3(min_image(pj.x - pi.x, R.L, R.half_L),

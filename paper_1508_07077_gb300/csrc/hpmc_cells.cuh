@@ -112,12 +112,12 @@ __global__ void k_cells_bin(const __grid_constant__ SimParams P, int full)
                                   cell_rel(p.y, sigma[1], R.L, R.w, cy),
                                   cell_rel(p.z, sigma[2], R.L, R.w, cz), __int_as_float(g));
     const int slot = atomicAdd(P.count[sweep & 1u] + c, 1);
-    if (slot < P.cap) P.bins[(size_t)c * P.cap + slot] = rl;
+    if (slot < P.cap) P.bins[bin_at(P, c, slot)] = rl;
     else atomicCAS(P.err, kErrNone, kErrCellCap);
-    if (P.binpos) P.binpos[g] = slot < P.cap ? c * P.cap + slot : -1;
+    if (P.binpos) P.binpos[g] = slot < P.cap ? (int)bin_at(P, c, slot) : -1;
     if (P.bin_q && slot < P.cap) {
         const double4 q = P.quat[g];
-        P.bin_q[(size_t)c * P.cap + slot] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
+        P.bin_q[bin_at(P, c, slot)] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
     }
     P.rel[g] = rl;
     // FP32 sphere form: the exact proposal of this sweep (translation), for

@@ -280,8 +280,8 @@ struct SimParams {
     double4 *quat;
     float4 *rel;           // FP32 position relative to the origin of its cell (this sweep)
     int *count[2];         // per-cell populations, double-buffered by sweep parity
-    float4 *bins;          // [cell][cap] (FP32 offset from the cell origin, global index bits
-                           // in .w), unordered within a cell
+    float4 *bins;          // [cap][cell] (FP32 offset from the cell origin, global index bits
+                           // in .w), unordered within a cell; see bin_at
     const unsigned long long *T;   // Poisson CDF tables as integers ceil(F[k] 2^53)
     // per-colloid depletant "lens" lists of this sweep (FP32 form):
     // lens[g][0..n) = (e, (t << 16) | k) of the depletants that overlap the new
@@ -293,7 +293,7 @@ struct SimParams {
     double4 *prop_quat;    // and orientation
     // per-sweep tables written by the cell-list kernel for the FP32 sphere
     // phases: task[phase][cta] = (global cell, replica, cx | cy << 10 | cz << 20);
-    // binpos[g] = cell * cap + slot of colloid g; the lens kernel's header
+    // binpos[g] = bin_at(cell, slot) of colloid g; the lens kernel's header
     // (N_p, obtained, n_lens) and displacement of each bin slot
     int4 *task;
     // the same tasks per phase in four classes of the cell's population
@@ -534,13 +534,29 @@ __device__ __forceinline__ void clear_next(const SimParams &P, uint32_t sweep, i
     if (threadIdx.x == 0) P.count[(sweep + 1u) & 1u][cell] = 0;
 }
 
+// Flat index of slot s of global cell c in the per-slot arrays (bins, bin_q,
+// hdr_bin, mv_bin; lens_bin in units of kLensInline points): slot-major, so
+// that the first slots of neighbouring cells share cache lines (most cells
+// hold one or two colloids; a cell-major layout gave every cell's few used
+// slots a cache line of their own in each array).
+__device__ __forceinline__ size_t bin_at(const SimParams &P, int c, int s)
+{
+    return (size_t)s * (size_t)P.n_cells + (size_t)c;
+}
+
+// The global cell of a flat slot index.
+__device__ __forceinline__ int bin_cell(const SimParams &P, int bp)
+{
+    return bp % P.n_cells;
+}
+
 // Sort the own cell's members into s_own[0..n) ascending (n <= kMaxCellCap).
 __device__ __forceinline__ void own_members_sorted(const SimParams &P, int cell, int n, int *s_tmp,
                                                    int *s_own)
 {
     const int tid = threadIdx.x;
     for (int t = tid; t < n; t += blockDim.x)
-        s_tmp[t] = __float_as_int(P.bins[(size_t)cell * P.cap + t].w);
+        s_tmp[t] = __float_as_int(P.bins[bin_at(P, cell, t)].w);
     __syncthreads();
     for (int t = tid; t < n; t += blockDim.x) {
         const int v = s_tmp[t];

@@ -575,13 +575,16 @@ int resident_ctas(K kernel, int threads, size_t dyn)
 }
 
 // Waves of the looping FP32 sphere colour phases (0: a CTA per cell).  Set:
-// c->phase_waves; automatic (-1): two waves when a phase has more cells than
-// one wave of the one-CTA-per-cell kernel holds (CTA launches are then a
-// large part of a phase), else none.
+// c->phase_waves; automatic (-1), for hard interactions without CB: two
+// waves when a phase has more cells than one wave of the one-CTA-per-cell
+// kernel holds (CTA launches are then a large part of a phase), else none.
+// (With CB or the soft interaction a cell's work is longer and the looping
+// grid measured slower: none.)
 template <typename K>
-int phase_waves(const hpmc_ctx *c, K single, int threads, size_t dyn)
+int phase_waves(const hpmc_ctx *c, K single, int threads, size_t dyn, bool long_cells)
 {
     if (c->phase_waves >= 0) return c->phase_waves;
+    if (long_cells) return 0;
     return c->n_cta > resident_ctas(single, threads, dyn) ? 2 : 0;
 }
 
@@ -589,9 +592,9 @@ int phase_waves(const hpmc_ctx *c, K single, int threads, size_t dyn)
 // waves of looping CTAs (identical results: any grid size is correct).
 template <typename K1, typename KL>
 void launch_phase_sphere32(const hpmc_ctx *c, K1 single, KL loop, size_t dyn, cudaStream_t s,
-                           const SimParams &P, int phase)
+                           const SimParams &P, int phase, bool long_cells)
 {
-    const int w = phase_waves(c, single, 32, dyn);
+    const int w = phase_waves(c, single, 32, dyn, long_cells);
     if (w <= 0) {
         launch_pdl(single, c->n_cta, 32, dyn, s, P, phase);
         return;
@@ -625,15 +628,18 @@ void launch_phase_cap(hpmc_ctx *c, const SimParams &P, int phase, cudaStream_t s
         const bool warp = threads == 32;
         if (cb) {
             if (warp) launch_phase_sphere32(c, k_phase_sphere_fp32<true, true, CAP>,
-                                            k_phase_sphere_fp32<true, true, CAP, false, true>, dyn, s, P, phase);
+                                            k_phase_sphere_fp32<true, true, CAP, false, true>, dyn, s, P,
+                                            phase, true);
             else launch_pdl(k_phase_sphere_fp32<true, false, CAP>, c->n_cta, threads, dyn, s, P, phase);
         } else if (c->prm.soft_eps > 0.0) {
             if (warp) launch_phase_sphere32(c, k_phase_sphere_fp32<false, true, CAP, true>,
-                                            k_phase_sphere_fp32<false, true, CAP, true, true>, dyn, s, P, phase);
+                                            k_phase_sphere_fp32<false, true, CAP, true, true>, dyn, s, P,
+                                            phase, true);
             else launch_pdl(k_phase_sphere_fp32<false, false, CAP, true>, c->n_cta, threads, dyn, s, P, phase);
         } else {
             if (warp) launch_phase_sphere32(c, k_phase_sphere_fp32<false, true, CAP>,
-                                            k_phase_sphere_fp32<false, true, CAP, false, true>, dyn, s, P, phase);
+                                            k_phase_sphere_fp32<false, true, CAP, false, true>, dyn, s, P,
+                                            phase, false);
             else launch_pdl(k_phase_sphere_fp32<false, false, CAP>, c->n_cta, threads, dyn, s, P, phase);
         }
     } else if (c->prm.shape == HPMC_SPHERE) {

@@ -31,7 +31,7 @@ __global__ void k_check_spheres(const __grid_constant__ SimParams P, int *flag)
         const int c = stencil_cell(R, t, cx, cy, cz, dx, dy, dz);
         const int m = min(count[c], P.cap);
         for (int s = 0; s < m; ++s) {
-            const int j = __float_as_int(P.bins[(size_t)c * P.cap + s].w);
+            const int j = __float_as_int(P.bins[bin_at(P, c, s)].w);
             if (j == g) continue;
             const double4 pj = P.pos[j];
             const double r2 = norm2(min_image(pj.x - pi.x, R.L, R.half_L),

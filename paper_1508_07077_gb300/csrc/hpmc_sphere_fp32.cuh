@@ -898,7 +898,7 @@ __device__ __forceinline__ void phase_cell(const SimParams &P, int phase, int4 t
     // slots, one lane each; after the wait one round for the neighbour cells'
     // entries (up to four per cell at once).
     int c_nb = 0, m_nb = 0, dx = 0, dy = 0, dz = 0;
-    const size_t own0 = (size_t)cell * P.cap;
+    const size_t own0 = bin_at(P, cell, 0), own1 = bin_at(P, cell, 1);
     float4 p_a = make_float4(0.f, 0.f, 0.f, 0.f), p_b = p_a;
     int4 h_a = make_int4(0, 0, 0, 0), h_b = h_a;
     if (tid < n_st) {
@@ -909,14 +909,14 @@ __device__ __forceinline__ void phase_cell(const SimParams &P, int phase, int4 t
         m_nb = min(count[c_nb], P.cap);
     } else if (tid == 27) {
         p_a = P.bins[own0];
-        p_b = P.bins[own0 + 1];
+        p_b = P.bins[own1];
     } else if (tid == 28) {
         p_a = P.mv_bin[own0];
-        p_b = P.mv_bin[own0 + 1];
+        p_b = P.mv_bin[own1];
         h_a = P.hdr_bin[own0];
-        h_b = P.hdr_bin[own0 + 1];
+        h_b = P.hdr_bin[own1];
     } else if (tid == 29 || tid == 30) {
-        const float4 *src = P.lens_bin + (own0 + (size_t)(tid - 29)) * kLensInline;
+        const float4 *src = P.lens_bin + (tid == 29 ? own0 : own1) * kLensInline;
 #pragma unroll
         for (int j = 0; j < kLensInline; ++j) s_lin[tid - 29][j] = src[j];
     }
@@ -968,9 +968,10 @@ __device__ __forceinline__ void phase_cell(const SimParams &P, int phase, int4 t
         s_hdr[1] = h_b;
     }
     for (int q = 2 + tid; q < n_own; q += nthr) {
-        const float4 e = P.bins[own0 + q];
-        s_mv[q] = P.mv_bin[own0 + q];
-        s_hdr[q] = P.hdr_bin[own0 + q];
+        const size_t oq = bin_at(P, cell, q);
+        const float4 e = P.bins[oq];
+        s_mv[q] = P.mv_bin[oq];
+        s_hdr[q] = P.hdr_bin[oq];
         s_cpos[base_own + q] = e;
         s_tmp_i[q] = __float_as_int(e.w);
         s_tmp_slot[q] = base_own + q;
@@ -1011,7 +1012,7 @@ __device__ __forceinline__ void phase_cell(const SimParams &P, int phase, int4 t
             if (n <= kLensInline && q < 2) {
                 if (tid < n) s_lens[o + tid] = s_lin[q][tid];
             } else if (n <= kLensInline) {
-                if (tid < n) s_lens[o + tid] = P.lens_bin[(own0 + q) * kLensInline + tid];
+                if (tid < n) s_lens[o + tid] = P.lens_bin[bin_at(P, cell, q) * kLensInline + tid];
             } else {
                 const float4 *src = P.lens + (size_t)s_tmp_i[q] * P.lens_cap;
                 for (int m = tid; m < n; m += nthr) s_lens[o + m] = src[m];
@@ -1045,7 +1046,9 @@ __device__ __forceinline__ void phase_cell(const SimParams &P, int phase, int4 t
     // per cell in one round, any further ones after it
     if (tid < n_st && tid != t_own) {
         const float fx = (float)dx * w32, fy = (float)dy * w32, fz = (float)dz * w32;
-        const float4 *b = P.bins + (size_t)c_nb * P.cap;
+        // slot s of the cell at b[s * ncs]
+        const float4 *b = P.bins + c_nb;
+        const size_t ncs = (size_t)P.n_cells;
         auto stage = [&](const float4 v, int s) {
             const int slot = base + s;
             if (kChecked) {
@@ -1054,7 +1057,7 @@ __device__ __forceinline__ void phase_cell(const SimParams &P, int phase, int4 t
                 if (HPMC_CHECK_FAILS(P, slot < cand_cap(CAP), 2)) return;
                 (void)HPMC_CHECK_FAILS(P, j >= R.off && j < R.off + R.n, 3);
                 (void)HPMC_CHECK_FAILS(P, P.binpos == nullptr || (j >= 0 && j < P.n_total &&
-                                                            P.binpos[j] / P.cap == c_nb), 4);
+                                                            bin_cell(P, P.binpos[j]) == c_nb), 4);
                 // Sec. III.E: no other cell of the neighbourhood is active in
                 // this phase (the own cell is staged above)
                 const int col = ((cx + dx) & 1) | (((cy + dy) & 1) << 1) | (((cz + dz) & 1) << 2);
@@ -1065,14 +1068,14 @@ __device__ __forceinline__ void phase_cell(const SimParams &P, int phase, int4 t
         };
         float4 e0 = make_float4(0.f, 0.f, 0.f, 0.f), e1 = e0, e2 = e0, e3 = e0;
         if (m_nb > 0) e0 = __ldcg(b);
-        if (m_nb > 1) e1 = __ldcg(b + 1);
-        if (m_nb > 2) e2 = __ldcg(b + 2);
-        if (m_nb > 3) e3 = __ldcg(b + 3);
+        if (m_nb > 1) e1 = __ldcg(b + ncs);
+        if (m_nb > 2) e2 = __ldcg(b + 2 * ncs);
+        if (m_nb > 3) e3 = __ldcg(b + 3 * ncs);
         if (m_nb > 0) stage(e0, 0);
         if (m_nb > 1) stage(e1, 1);
         if (m_nb > 2) stage(e2, 2);
         if (m_nb > 3) stage(e3, 3);
-        for (int s = 4; s < m_nb; ++s) stage(__ldcg(b + s), s);
+        for (int s = 4; s < m_nb; ++s) stage(__ldcg(b + s * ncs), s);
     }
     cta_sync<WARP>();
 
@@ -1315,7 +1318,7 @@ __device__ __forceinline__ void phase_cell(const SimParams &P, int phase, int4 t
             if (tid == 0) {
                 const float4 rnew = make_float4(rn0, rn1, rn2, __int_as_float(i));
                 s_cpos[s_own_slot[q]] = rnew;
-                P.bins[(size_t)cell * P.cap + s_own_bin[q]] = rnew;
+                P.bins[bin_at(P, cell, s_own_bin[q])] = rnew;
                 s_accl[nacc] = i;
                 s_nacc = nacc + 1;
             }
@@ -1525,7 +1528,7 @@ __global__ void k_check_spheres32(const __grid_constant__ SimParams P, int *flag
     if (t >= ns * ns * ns) return;
     const int bp = P.binpos[g];
     if (bp < 0) return;   // a full cell: the cell-list kernel has flagged it
-    const int cl = bp / P.cap - R.cell_off;
+    const int cl = bin_cell(P, bp) - R.cell_off;
     const int cx = cl % nc, cy = (cl / nc) % nc, cz = cl / (nc * nc);
     const float4 ri = P.bins[bp];
     const Sched &S = P.sched[r];
@@ -1536,7 +1539,7 @@ __global__ void k_check_spheres32(const __grid_constant__ SimParams P, int *flag
     const int m = min(count[c], P.cap);
     const float fx = (float)dx * w32 - ri.x, fy = (float)dy * w32 - ri.y, fz = (float)dz * w32 - ri.z;
     for (int s = 0; s < m; ++s) {
-        const float4 e = P.bins[(size_t)c * P.cap + s];
+        const float4 e = P.bins[bin_at(P, c, s)];
         const int j = __float_as_int(e.w);
         if (j == g) continue;
         float d0 = fx + e.x, d1 = fy + e.y, d2 = fz + e.z;

@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kMaxThreads)
         const int m = min(T.count[c], P.cap);
         for (int s = 0; s < m; ++s) {
             const int slot = atomicAdd(&s_ncand, 1);
-            if (slot < kMaxCand) s_cand[slot] = __float_as_int(P.bins[(size_t)c * P.cap + s].w);
+            if (slot < kMaxCand) s_cand[slot] = __float_as_int(P.bins[bin_at(P, c, s)].w);
         }
     }
     __syncthreads();
