@@ -84,8 +84,11 @@ FP64_PER_ATTEMPT, FP64_PER_DEP = 11.0, 10.0
 # the FP32 cell-relative copy (16), the cell-list entries (2 x 4)
 BYTES_PER_MOVE = 2 * 32 + 16 + 2 * 4
 # DRAM bytes (read + write) per launch of the headline's dominant kernel from
-# the committed ncu capture of the current build (profiles/), or None.
-MEASURED_TRAFFIC: dict = {}
+# the committed ncu capture of the current build (profiles/), keyed by
+# (kernel, replicas, schedule): the mean over the 16 colour-phase launches of
+# two timed sweeps of the 128-replica batch (L2 flushed before each step, ncu
+# without cache control), or None for other cases.
+MEASURED_TRAFFIC: dict = {("colour_phases", 128, 0): 43.9e6}
 
 
 def _dist():
@@ -564,7 +567,10 @@ def run_batched(args, ws, rank, local):
                         "rooflines": roof},
             "roofline": {"bound": "alu", "achieved": dom["achieved"], "peak": dom["peak"],
                          "unit": "Tops/s", "frac": dom["frac"],
-                         "traffic": MEASURED_TRAFFIC.get(dominant), "kernel": dominant,
+                         "traffic": MEASURED_TRAFFIC.get((dominant, args.replicas, args.schedule)),
+                         "traffic_algorithmic": BYTES_PER_MOVE * n_all / 8.0
+                         if dominant == "colour_phases" else None,
+                         "kernel": dominant,
                          "peak_basis": dom["peak_basis"] + " (of measured)"},
             "pipe_peaks_measured": pk,
             "clocks": clk.summary(),
