@@ -402,19 +402,22 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
     // orientations (bins, FP64 state) only after it.
     pdl_trigger();
     if (phase == 7 && blockIdx.x == 0 && tid == 0) atomicAdd(P.sweep, 1ull);
+    // the phase's non-empty cells come first in the task order; an empty cell
+    // has no work (its next-sweep population was cleared by the task ordering
+    // kernel), so CTAs past them return at once; this grid must still not
+    // complete before its predecessor when no cell has work (a later phase's
+    // wait covers only this grid)
     int cls = 0, idx = blockIdx.x;
     {
         const int4 cc = reinterpret_cast<const int4 *>(P.cls_count)[phase];
+        if (blockIdx.x == 0 && cc.x + cc.y + cc.z == 0) pdl_wait();
+        if (idx >= cc.x + cc.y + cc.z) return;
         if (idx >= cc.x) {
             idx -= cc.x;
             cls = 1;
             if (idx >= cc.y) {
                 idx -= cc.y;
                 cls = 2;
-                if (idx >= cc.z) {
-                    idx -= cc.z;
-                    cls = 3;
-                }
             }
         }
     }
@@ -422,10 +425,6 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
     const int cell = tk.x, r = tk.y;
     const int cx = tk.z & 1023, cy = (tk.z >> 10) & 1023, cz = tk.z >> 20;
     const int nc = tk.w & 0xFFFF, par = tk.w >> 16;
-    if (cls == 3) {               // an empty cell: only its next-sweep population
-        if (tid == 0) P.count[par ^ 1][cell] = 0;
-        return;
-    }
     const int ns = nc == 2 ? 2 : 3, n_st = ns * ns * ns;
     const int t_own = ns == 3 ? 13 : cx + 2 * cy + 4 * cz;
     const int cell_off = cell - (cx + nc * (cy + nc * cz));
@@ -434,7 +433,6 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
     const float w32 = R.w32;
     const int has_dep = R.has_dep;
     const Sched *S = P.sched + r;
-    if (tid == 0) P.count[par ^ 1][cell] = 0;
 
     // populations of the stencil; the own cell's lens data (slots 0 and 1)
     int c_nb = 0, m_nb = 0, dx = 0, dy = 0, dz = 0;
