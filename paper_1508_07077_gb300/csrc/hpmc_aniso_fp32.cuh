@@ -229,12 +229,16 @@ __global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__
                 }
             }
         }
+        // lens points are rare: their list slots are ranked only in a pass
+        // that has one
         const bool lens = tn == 1 && to == 0;
-        const unsigned lb = __ballot_sync(kFull, lens);
-        const int slot = m + __popc(lb & lt);
-        if (lens && slot < P.lens_cap)
-            out[slot] = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
-        m += __popc(lb);
+        if (__any_sync(kFull, lens)) {
+            const unsigned lb = __ballot_sync(kFull, lens);
+            const int slot = m + __popc(lb & lt);
+            if (lens && slot < P.lens_cap)
+                out[slot] = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
+            m += __popc(lb);
+        }
         k0 += __popc(bal);
         t0 += 32u;
     }

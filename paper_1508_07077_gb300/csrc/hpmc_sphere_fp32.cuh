@@ -564,17 +564,22 @@ __device__ __forceinline__ int4 lens_of_move_paired(const SimParams &P, const Re
                 }
             }
             const unsigned bal = __ballot_sync(kFull, in == 1);
-            const int k = k0 + __popc(bal & lt);
-            const bool dep = in == 1 && k < n_p && tn == 1;
-            const bool lens = dep && to == 0;
-            const unsigned lb = __ballot_sync(kFull, lens);
-            const int slot = m + __popc(lb & lt);
-            if (lens) {
-                const float4 v = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
-                if (slot < room) sdst[slot] = v;
-                else if (slot < P.lens_cap) gdst[slot] = v;
+            // lens candidates are rare (a few per move against ~9 sub-passes):
+            // their depletant index and list slot are ranked only in a
+            // sub-pass that has one
+            const bool cand = in == 1 && tn == 1 && to == 0;
+            if (__any_sync(kFull, cand)) {
+                const int k = k0 + __popc(bal & lt);
+                const bool lens = cand && k < n_p;
+                const unsigned lb = __ballot_sync(kFull, lens);
+                const int slot = m + __popc(lb & lt);
+                if (lens) {
+                    const float4 v = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
+                    if (slot < room) sdst[slot] = v;
+                    else if (slot < P.lens_cap) gdst[slot] = v;
+                }
+                m += __popc(lb);
             }
-            m += __popc(lb);
             k0 += __popc(bal);
         }
         t0 += 64u;
@@ -664,14 +669,17 @@ __device__ __forceinline__ int4 lens_of_move(const SimParams &P, const Rep &R, i
             }
             lens = dep && to == 0;
         }
-        const unsigned lb = __ballot_sync(kFull, lens);
-        const int slot = m + __popc(lb & lt);
-        if (lens) {
-            const float4 v = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
-            if (slot < room) sdst[slot] = v;
-            else if (slot < P.lens_cap) gdst[slot] = v;
+        // (list slots are ranked only in a pass that has a lens point)
+        if (__any_sync(kFull, lens)) {
+            const unsigned lb = __ballot_sync(kFull, lens);
+            const int slot = m + __popc(lb & lt);
+            if (lens) {
+                const float4 v = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
+                if (slot < room) sdst[slot] = v;
+                else if (slot < P.lens_cap) gdst[slot] = v;
+            }
+            m += __popc(lb);
         }
-        m += __popc(lb);
         k0 += __popc(bal);
         t0 += 32u;
     }
