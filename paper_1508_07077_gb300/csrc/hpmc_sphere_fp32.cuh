@@ -541,6 +541,19 @@ __device__ __forceinline__ int4 lens_of_move_paired(const SimParams &P, const Re
             const uint3 f = paired_fields(w, (uint32_t)h);
             const float e0 = s21f_bits(f.x) * R.R_s32, e1 = s21f_bits(f.y) * R.R_s32,
                         e2 = s21f_bits(f.z) * R.R_s32;
+            if constexpr (!CUBE) {
+                // the common case first: every decision certain and no lens
+                // candidate (each point in the ball certainly overlaps the
+                // old pose), where a sub-pass only counts its ball points
+                const float r2 = norm2f(e0, e1, e2);
+                const float r2o = norm2f(e0 - o0, e1 - o1, e2 - o2);
+                const bool in_c = r2 < R.T_s32 - R.m_r2, out_c = r2 > R.T_s32 + R.m_r2;
+                const bool ov_c = r2o < R.T_dep32 - R.m_r2;
+                if (!__any_sync(kFull, !(in_c || out_c) || (in_c && !ov_c))) {
+                    k0 += __popc(__ballot_sync(kFull, in_c));
+                    continue;
+                }
+            }
             // in the sampling region (the ball; the cube takes every point)
             int in = CUBE ? 1 : tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
             // overlaps the new pose (the cube's points only inside the ball;
