@@ -88,11 +88,11 @@ BYTES_PER_MOVE = 2 * 32 + 16 + 2 * 4
 # (kernel, replicas, schedule): the mean over the 16 colour-phase launches of
 # two timed sweeps of the 128-replica batch (L2 flushed before each step, ncu
 # without cache control), or None for other cases.
-MEASURED_TRAFFIC: dict = {("colour_phases", 128, 0): 43.8e6}
+MEASURED_TRAFFIC: dict = {("colour_phases", 128, 0): 44.0e6}
 # The same without the flush buffer's write-back: the first phase after the
-# flush writes back the flush's dirty lines (17.8 MB against 2.5 MB for the
+# flush writes back the flush's dirty lines (18.0 MB against 2.5 MB for the
 # other phases); with its writes taken as the others' mean.
-MEASURED_TRAFFIC_NO_WRITEBACK: dict = {("colour_phases", 128, 0): 41.9e6}
+MEASURED_TRAFFIC_NO_WRITEBACK: dict = {("colour_phases", 128, 0): 42.0e6}
 
 
 def _dist():

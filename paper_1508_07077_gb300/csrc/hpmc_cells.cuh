@@ -119,7 +119,8 @@ __global__ void k_cells_bin(const __grid_constant__ SimParams P, int full)
         const double4 q = P.quat[g];
         P.bin_q[bin_at(P, c, slot)] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
     }
-    P.rel[g] = rl;
+    // (the cell-relative copy is read only by the anisotropic lens kernel)
+    if (P.bin_q) P.rel[g] = rl;
     // FP32 sphere form: the exact proposal of this sweep (translation), for
     // the colour phases' commit and exact re-takes
     if (full && P.task && R.shape == 0) {
