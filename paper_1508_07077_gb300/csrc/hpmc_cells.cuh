@@ -29,18 +29,17 @@ __device__ __forceinline__ int4 phase_task(const Rep &R, int r, const int perm[8
                      nc | (int)((sweep & 1u) << 16));
 }
 
-// One thread per colloid of the batch.  The first colloid of each replica
-// also writes that replica's schedule.  When the task table is allocated,
-// threads also fill it (one entry per phase and CTA), so that the colour
-// phases start from their cell without recomputing the schedule.
 // cell_coord without the FP64 division in all but rare cases: the FP32
 // quotient (s and 1/w rounded to float, one product: relative error < 4u)
 // decides floor(s / w) when it is more than 8u q + 2^-40 away from an
 // integer, since then the exact quotient and its FP64 rounding lie in the
 // same unit interval; otherwise the FP64 quotient decides.  (GB300 issues
 // FP64 at 1/64 of FP32: the division was most of this kernel's time.)
-__device__ __forceinline__ int cell_coord_fast(double x, double sigma, double L, double w, float iw32,
-                                               int nc)
+// ... and the colloid's FP32 offset from that cell's origin, rounded from
+// the FP64 difference, both from one wrapped difference s = x - sigma (FP64
+// is most of this kernel's cost).
+__device__ __forceinline__ int cell_coord_rel(double x, double sigma, double L, double w, float iw32,
+                                              int nc, float &rel)
 {
     double s = x - sigma;
     if (s < 0.0) s = s + L;
@@ -52,9 +51,14 @@ __device__ __forceinline__ int cell_coord_fast(double x, double sigma, double L,
     else c = (int)(s / w);
     if (c >= nc) c = nc - 1;
     if (c < 0) c = 0;
+    rel = (float)(s - (double)c * w);
     return c;
 }
 
+// One thread per colloid of the batch.  The first colloid of each replica
+// also writes that replica's schedule.  When the task table is allocated,
+// threads also fill it (one entry per phase and CTA), so that the colour
+// phases start from their cell without recomputing the schedule.
 // full = 0: the bins, populations and schedules only (a configuration
 // check), without the phase task table and the exact proposals.
 __global__ void k_cells_bin(const __grid_constant__ SimParams P, int full)
@@ -103,14 +107,13 @@ __global__ void k_cells_bin(const __grid_constant__ SimParams P, int full)
     const double4 p = P.pos[g];
     const int nc = R.nc;
     const float iw32 = 1.0f / R.w32;
-    const int cx = cell_coord_fast(p.x, sigma[0], R.L, R.w, iw32, nc);
-    const int cy = cell_coord_fast(p.y, sigma[1], R.L, R.w, iw32, nc);
-    const int cz = cell_coord_fast(p.z, sigma[2], R.L, R.w, iw32, nc);
+    float4 rl;
+    const int cx = cell_coord_rel(p.x, sigma[0], R.L, R.w, iw32, nc, rl.x);
+    const int cy = cell_coord_rel(p.y, sigma[1], R.L, R.w, iw32, nc, rl.y);
+    const int cz = cell_coord_rel(p.z, sigma[2], R.L, R.w, iw32, nc, rl.z);
+    rl.w = __int_as_float(g);
     const int c = R.cell_off + cx + nc * (cy + nc * cz);
     if (HPMC_CHECK_FAILS(P, c >= R.cell_off && c < R.cell_off + nc * nc * nc, 10)) return;
-    const float4 rl = make_float4(cell_rel(p.x, sigma[0], R.L, R.w, cx),
-                                  cell_rel(p.y, sigma[1], R.L, R.w, cy),
-                                  cell_rel(p.z, sigma[2], R.L, R.w, cz), __int_as_float(g));
     const int slot = atomicAdd(P.count[sweep & 1u] + c, 1);
     if (slot < P.cap) P.bins[bin_at(P, c, slot)] = rl;
     else atomicCAS(P.err, kErrNone, kErrCellCap);

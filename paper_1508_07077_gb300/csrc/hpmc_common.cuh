@@ -399,14 +399,6 @@ __device__ __forceinline__ int cell_coord(double x, double sigma, double L, doub
     return c;
 }
 
-// Offset of x from the origin of its cell c (FP32 working copy only).
-__device__ __forceinline__ float cell_rel(double x, double sigma, double L, double w, int c)
-{
-    double s = x - sigma;
-    if (s < 0.0) s = s + L;
-    return (float)(s - (double)c * w);
-}
-
 __device__ __forceinline__ double min_image(double d, double L, double half_L)
 {
     if (d > half_L) d = d - L;
