@@ -1058,6 +1058,10 @@ int prepare(hpmc_ctx *c)
 // mapped, as every pinned allocation is under unified addressing), else
 // null: such buffers are read and written in place by the layout kernels,
 // with no staging copy.
+// read-backs of at least this many bytes take the staging copy (see
+// hpmc_get_state)
+constexpr size_t kDmaReadBytes = (size_t)4 << 20;
+
 const double *mapped_host(const double *p)
 {
     cudaPointerAttributes a;
@@ -1673,7 +1677,12 @@ int hpmc_get_state(hpmc_ctx *c, double *pos, double *quat, int mem, uint64_t *sw
     } else {
         bool staged = false;
         if (pos) {
-            double *dst = const_cast<double *>(mapped_host(pos));
+            // a large read-back goes through the staging buffer and one DMA
+            // copy (measured faster than the layout kernel's writes across
+            // the host link: 0.15 against 0.25 ms for 621 288 positions); a
+            // small one is written in place
+            double *dst = (size_t)n * 3 * sizeof(double) >= kDmaReadBytes
+                              ? nullptr : const_cast<double *>(mapped_host(pos));
             if (dst) {
                 k_pack<<<nb, 256, 0, s>>>(n, c->d_pos, nullptr, dst, nullptr);
                 CK(cudaGetLastError());

@@ -1528,8 +1528,13 @@ __global__ void __launch_bounds__(32, (CB || SOFT) ? 16 : 32)
 // kernel filed in the bins (its bin slot from binpos), decided with the
 // certified margin and re-taken in FP64 (the positions, minimum image) only
 // inside it.  One thread per (colloid, stencil cell): every thread's loads
-// are two dependent rounds (the cell's population, then its entries).
-constexpr int kCheckStencil = 27;
+// are two dependent rounds (the cell's population, then its entries).  Each
+// pair is tested once: from the colloid's own cell (partners of higher
+// index) and the 13 stencil cells that follow it in stencil order (every
+// partner; the other 13 are the preceding cells, whose colloids test this
+// one); with two cells per side, where the stencil is the whole box, every
+// cell with partners of higher index.
+constexpr int kCheckStencil = 14;
 
 __global__ void k_check_spheres32(const __grid_constant__ SimParams P, int *flag)
 {
@@ -1546,7 +1551,9 @@ __global__ void k_check_spheres32(const __grid_constant__ SimParams P, int *flag
     }
     const int nc = R.nc;
     const int ns = nc == 2 ? 2 : 3;
-    if (t >= ns * ns * ns) return;
+    if (ns == 2 && t >= 8) return;
+    const int ts = ns == 3 ? 13 + t : t;      // the stencil cell
+    const bool higher = ns == 2 || ts == 13;  // partners of higher index only
     const int bp = P.binpos[g];
     if (bp < 0) return;   // a full cell: the cell-list kernel has flagged it
     const int cl = bin_cell(P, bp) - R.cell_off;
@@ -1556,13 +1563,13 @@ __global__ void k_check_spheres32(const __grid_constant__ SimParams P, int *flag
     const int *count = P.count[S.sweep & 1u];
     const float w32 = R.w32, L32 = R.L32, half_L32 = R.half_L32;
     int dx, dy, dz;
-    const int c = stencil_cell_nc(nc, R.cell_off, t, cx, cy, cz, dx, dy, dz);
+    const int c = stencil_cell_nc(nc, R.cell_off, ts, cx, cy, cz, dx, dy, dz);
     const int m = min(count[c], P.cap);
     const float fx = (float)dx * w32 - ri.x, fy = (float)dy * w32 - ri.y, fz = (float)dz * w32 - ri.z;
     for (int s = 0; s < m; ++s) {
         const float4 e = P.bins[bin_at(P, c, s)];
         const int j = __float_as_int(e.w);
-        if (j == g) continue;
+        if (j == g || (higher && j < g)) continue;
         float d0 = fx + e.x, d1 = fy + e.y, d2 = fz + e.z;
         if (nc == 2) {
             if (d0 > half_L32) d0 -= L32; else if (d0 < -half_L32) d0 += L32;

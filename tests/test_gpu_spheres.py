@@ -206,6 +206,35 @@ def test_errors_are_reported(lib):
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
+def test_configuration_check_finds_a_pair_in_any_direction(lib, precision):
+    """The start check finds one overlapping pair wherever its partner sits
+    relative to the colloid (the FP32 check tests each pair from one side:
+    the own cell and the stencil cells after it), in a box of six cells per
+    side and in one of two cells per side (the whole box is the stencil)."""
+    rng = np.random.default_rng(21)
+    for L, base in ((None, None), (2.6, W.tiny_spheres(8, 2.6))):
+        if base is None:
+            s = W.spheres_256(seed=5)
+            base, L, q, n_r = s.pos, s.L, s.q, s.n_r
+        else:
+            q, n_r = 0.2, 30.0
+        for trial in range(12):
+            pos = base.copy()
+            i, j = rng.choice(len(pos), size=2, replace=False)
+            u = rng.normal(size=3)
+            pos[j] = (pos[i] + 0.9 * u / np.linalg.norm(u)) % L
+            smp = lib.Sampler(pos, L, q=q, n_r=n_r, d_max=0.05, precision=precision)
+            with pytest.raises(lib.HPMCError) as e:
+                smp.sweep(1)
+            assert e.value.code == -2, (L, trial)
+            smp.close()
+        # and the unmodified configuration passes
+        smp = lib.Sampler(base, L, q=q, n_r=n_r, d_max=0.05, precision=precision)
+        smp.sweep(1)
+        smp.close()
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_configuration_check_at_contact(oracle, lib, precision):
     """The start check: a pair closer than contact (by 1e-12) is an overlap,
     one at contact (by 1e-12) is not; a position outside the box is an
