@@ -172,8 +172,55 @@ __global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__
     const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
     float4 *out = P.lens + (size_t)g * P.lens_cap;
     const unsigned lt = (1u << lane) - 1u;
+    // The shape tests dominate: a pass queues its depletants (ball points of
+    // index k < N_p, in depletant order) in shared memory, and the tests run
+    // on full batches of 32 queued points (the last batch partial), so every
+    // lane tests a depletant instead of half of them testing nothing.  Lens
+    // points leave the queue in depletant order, as the list needs them.
+    __shared__ float4 s_q[4][64];   // (e, (t << 16) | k) per queued depletant
+    int m = 0;
+    auto test_batch = [&](int nb) {
+        const bool act = lane < nb;
+        const float4 v = act ? s_q[wib][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t tk = (uint32_t)__float_as_int(v.w);
+        const uint32_t t = tk >> 16;
+        // overlaps the new pose?
+        int tn = act ? dep_tri32(R, make_float3(v.x, v.y, v.z), Fn) : 0;
+        {
+            const bool unsure = tn == -1;
+            if (__any_sync(kFull, unsure)) {
+                if (unsure) {
+                    ++rck;
+                    const uint4 w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, paired_call(t));
+                    tn = exact_dep_aniso(P, R, g, w, 0, 0, 0, nullptr, 0, (int)paired_half(t)) ? 1 : 0;
+                }
+            }
+        }
+        // and not the old pose?
+        int to = 1;
+        if (tn == 1) to = dep_tri32(R, make_float3(v.x - o0, v.y - o1, v.z - o2), Fo);
+        {
+            const bool unsure = to == -1;
+            if (__any_sync(kFull, unsure)) {
+                if (unsure) {
+                    ++rck;
+                    const uint4 w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, paired_call(t));
+                    to = exact_dep_aniso(P, R, g, w, 0, 1, 0, nullptr, 0, (int)paired_half(t)) ? 1 : 0;
+                }
+            }
+        }
+        // lens points are rare: their list slots are ranked only in a batch
+        // that has one
+        const bool lens = tn == 1 && to == 0;
+        if (__any_sync(kFull, lens)) {
+            const unsigned lb = __ballot_sync(kFull, lens);
+            const int slot = m + __popc(lb & lt);
+            if (lens && slot < P.lens_cap) out[slot] = v;
+            m += __popc(lb);
+        }
+    };
     uint32_t t0 = 0;
-    int k0 = 0, m = 0;
+    int k0 = 0, qn = 0;
     uint4 wc = make_uint4(0, 0, 0, 0);
     while (k0 < n_p && t0 < t_max) {
         const uint32_t t = t0 + (uint32_t)lane;
@@ -205,43 +252,26 @@ __global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__
         const unsigned bal = __ballot_sync(kFull, in == 1);
         const int k = k0 + __popc(bal & lt);
         const bool dep = in == 1 && k < n_p;
-        // overlaps the new pose?
-        int tn = 0;
-        if (dep) tn = dep_tri32(R, make_float3(e0, e1, e2), Fn);
-        {
-            const bool unsure = tn == -1;
-            if (__any_sync(kFull, unsure)) {
-                if (unsure) {
-                    ++rck;
-                    tn = exact_dep_aniso(P, R, g, w, 0, 0, 0, nullptr, 0, half) ? 1 : 0;
-                }
-            }
-        }
-        // and not the old pose?
-        int to = 1;
-        if (tn == 1) to = dep_tri32(R, make_float3(e0 - o0, e1 - o1, e2 - o2), Fo);
-        {
-            const bool unsure = to == -1;
-            if (__any_sync(kFull, unsure)) {
-                if (unsure) {
-                    ++rck;
-                    to = exact_dep_aniso(P, R, g, w, 0, 1, 0, nullptr, 0, half) ? 1 : 0;
-                }
-            }
-        }
-        // lens points are rare: their list slots are ranked only in a pass
-        // that has one
-        const bool lens = tn == 1 && to == 0;
-        if (__any_sync(kFull, lens)) {
-            const unsigned lb = __ballot_sync(kFull, lens);
-            const int slot = m + __popc(lb & lt);
-            if (lens && slot < P.lens_cap)
-                out[slot] = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
-            m += __popc(lb);
-        }
+        const unsigned db = __ballot_sync(kFull, dep);
+        if (dep) s_q[wib][qn + __popc(db & lt)] = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
+        qn += __popc(db);
         k0 += __popc(bal);
         t0 += 32u;
+        __syncwarp();
+        if (qn >= 32) {
+            test_batch(32);
+            // the rest (fewer than 32) to the front of the queue
+            const int rest = qn - 32;
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+            __syncwarp();
+            if (lane < rest) x = s_q[wib][32 + lane];
+            __syncwarp();
+            if (lane < rest) s_q[wib][lane] = x;
+            __syncwarp();
+            qn = rest;
+        }
     }
+    if (qn > 0) test_batch(qn);
     __syncwarp();
     if (bp >= 0) {
         if (lane == 0) P.hdr_bin[bp] = make_int4(n_p, min(k0, n_p), min(m, P.lens_cap), 0);
