@@ -606,99 +606,124 @@ template <int V0, bool SOFT>
 __device__ __forceinline__ int4 lens_of_move(const SimParams &P, const Rep &R, int g, uint32_t sweep, float4 *mv,
                                           float4 *sdst, int room, float4 *gdst)
 {
-    if constexpr (!SOFT) return lens_of_move_paired<V0>(P, R, g, sweep, mv, sdst, room, gdst);
-    static_assert(V0 == 0 || V0 == 2, "circumsphere or cube");
-    constexpr bool CUBE = V0 == 2;
-    const int lane = threadIdx.x & 31;
-    const int i = g;   // global colloid index (the helpers take global indices)
-    const uint32_t tag = (uint32_t)(g - R.off);
-    const uint4 wm = draw(R.key0, R.key1, sweep, tag, kPMove, 0, 0);
-    const float D0 = coord32(wm.x, R.d_max32);
-    const float D1 = coord32(wm.y, R.d_max32);
-    const float D2 = coord32(wm.z, R.d_max32);
-    if (lane == 0) *mv = make_float4(D0, D1, D2, 0.0f);
-    if (!R.has_dep) return make_int4(0, 0, 0, 0);
-    uint32_t rck = 0;
-    const float o0 = -D0, o1 = -D1, o2 = -D2;
-    const uint4 wp = draw(R.key0, R.key1, sweep, tag, kPPoisson, 0, 0);
-    const int n_p = poisson_count(P.T + R.t_off, R.nF, u53_int(wp.x, wp.y), lane);
-    const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
-    const RoundKeys K = round_keys(R.key0, R.key1);
-    const unsigned lt = (1u << lane) - 1u;
-    uint32_t t0 = 0;
-    int k0 = 0, m = 0;
-    while (k0 < n_p && t0 < t_max) {
-        const uint32_t t = t0 + (uint32_t)lane;
-        uint4 w = make_uint4(0, 0, 0, 0);
-        float e0 = 0.f, e1 = 0.f, e2 = 0.f;
-        int in = 0;
-        if (t < t_max) {
-            w = philox_rk(make_uint4(sweep, tag, kPDep << 24, t), K);
-            e0 = coord32(w.x, R.R_s32);
-            e1 = coord32(w.y, R.R_s32);
-            e2 = coord32(w.z, R.R_s32);
-            in = CUBE ? 1 : tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
-        }
-        {
-            const bool unsure = in == -1;
-            if (__any_sync(kFull, unsure)) {
-                if (unsure) {
-                    ++rck;
-                    in = exact_ball(P, R, w) ? 1 : 0;
+    if constexpr (!SOFT) {
+        return lens_of_move_paired<V0>(P, R, g, sweep, mv, sdst, room, gdst);
+    } else {
+        static_assert(V0 == 0 || V0 == 2, "circumsphere or cube");
+        constexpr bool CUBE = V0 == 2;
+        const int lane = threadIdx.x & 31;
+        const uint32_t tag = (uint32_t)(g - R.off);
+        const uint4 wm = draw(R.key0, R.key1, sweep, tag, kPMove, 0, 0);
+        const float D0 = coord32(wm.x, R.d_max32);
+        const float D1 = coord32(wm.y, R.d_max32);
+        const float D2 = coord32(wm.z, R.d_max32);
+        if (lane == 0) *mv = make_float4(D0, D1, D2, 0.0f);
+        if (!R.has_dep) return make_int4(0, 0, 0, 0);
+        uint32_t rck = 0;
+        const float o0 = -D0, o1 = -D1, o2 = -D2;
+        const uint4 wp = draw(R.key0, R.key1, sweep, tag, kPPoisson, 0, 0);
+        const int n_p = poisson_count(P.T + R.t_off, R.nF, u53_int(wp.x, wp.y), lane);
+        const uint32_t t_max = 64u * (uint32_t)(n_p + 1);
+        const RoundKeys K = round_keys(R.key0, R.key1);
+        const unsigned lt = (1u << lane) - 1u;
+        uint32_t t0 = 0;
+        int k0 = 0, m = 0, qn = 0;
+        // The soft tests (the early exits' exponentials) dominate: a pass queues
+        // its depletants (ball points of index k < N_p) in shared memory and the
+        // tests run on full batches of 32 queued points, so every lane tests a
+        // depletant; the queue is in depletant order, as the list needs.
+        __shared__ float4 s_q[4][64];      // (e, (t << 16) | k)
+        __shared__ uint32_t s_w3[4][64];   // the attempt's fourth word
+        const int wq = (threadIdx.x >> 5) & 3;
+        auto test_batch = [&](int nb) {
+            const bool act = lane < nb;
+            const float4 v = act ? s_q[wq][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const uint32_t w3 = act ? s_w3[wq][lane] : 0u;
+            // the points that may block (neither early exit of the FP64
+            // statement certain in FP32); the phases decide them
+            const bool lens = act && soft_may_block32(R, w3, v.x, v.y, v.z, o0, o1, o2);
+            // (list slots are ranked only in a batch that has a lens point)
+            if (__any_sync(kFull, lens)) {
+                const unsigned lb = __ballot_sync(kFull, lens);
+                const int slot = m + __popc(lb & lt);
+                if (lens) {
+                    if (slot < room) sdst[slot] = v;
+                    else if (slot < P.lens_cap) gdst[slot] = v;
                 }
+                m += __popc(lb);
             }
-        }
-        const unsigned bal = __ballot_sync(kFull, in == 1);
-        const int k = k0 + __popc(bal & lt);
-        bool dep = in == 1 && k < n_p;
-        if (CUBE) {
-            // a cube point overlaps the new pose only inside the circumsphere
-            int tn = dep ? tri(norm2f(e0, e1, e2), R.T_dep32, R.m_r2) : 1;
-            const bool unsure = tn == -1;
-            if (__any_sync(kFull, unsure)) {
-                if (unsure) {
-                    ++rck;
-                    tn = exact_ball(P, R, w) ? 1 : 0;
-                }
+        };
+        while (k0 < n_p && t0 < t_max) {
+            const uint32_t t = t0 + (uint32_t)lane;
+            uint4 w = make_uint4(0, 0, 0, 0);
+            float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+            int in = 0;
+            if (t < t_max) {
+                w = philox_rk(make_uint4(sweep, tag, kPDep << 24, t), K);
+                e0 = coord32(w.x, R.R_s32);
+                e1 = coord32(w.y, R.R_s32);
+                e2 = coord32(w.z, R.R_s32);
+                in = CUBE ? 1 : tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
             }
-            dep = dep && tn == 1;
-        }
-        bool lens;
-        if (SOFT) {
-            // soft: the points that may block (neither early exit of the
-            // FP64 statement certain in FP32); the phases decide them
-            lens = dep && soft_may_block32(R, w.w, e0, e1, e2, o0, o1, o2);
-        } else {
-            int to = 1;  // overlaps the old pose: 1 yes, 0 no, -1 within the margin
-            if (dep) to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), R.T_dep32, R.m_r2);
             {
-                const bool unsure = to == -1;
+                const bool unsure = in == -1;
                 if (__any_sync(kFull, unsure)) {
                     if (unsure) {
                         ++rck;
-                        to = exact_dep(P, R, sweep, i, w, 0, 0, nullptr, 0) ? 1 : 0;
+                        in = exact_ball(P, R, w) ? 1 : 0;
                     }
                 }
             }
-            lens = dep && to == 0;
-        }
-        // (list slots are ranked only in a pass that has a lens point)
-        if (__any_sync(kFull, lens)) {
-            const unsigned lb = __ballot_sync(kFull, lens);
-            const int slot = m + __popc(lb & lt);
-            if (lens) {
-                const float4 v = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
-                if (slot < room) sdst[slot] = v;
-                else if (slot < P.lens_cap) gdst[slot] = v;
+            const unsigned bal = __ballot_sync(kFull, in == 1);
+            const int k = k0 + __popc(bal & lt);
+            bool dep = in == 1 && k < n_p;
+            if (CUBE) {
+                // a cube point overlaps the new pose only inside the circumsphere
+                int tn = dep ? tri(norm2f(e0, e1, e2), R.T_dep32, R.m_r2) : 1;
+                const bool unsure = tn == -1;
+                if (__any_sync(kFull, unsure)) {
+                    if (unsure) {
+                        ++rck;
+                        tn = exact_ball(P, R, w) ? 1 : 0;
+                    }
+                }
+                dep = dep && tn == 1;
             }
-            m += __popc(lb);
+            const unsigned db = __ballot_sync(kFull, dep);
+            if (dep) {
+                const int qi = qn + __popc(db & lt);
+                s_q[wq][qi] = make_float4(e0, e1, e2, __int_as_float((int)((t << 16) | (uint32_t)k)));
+                s_w3[wq][qi] = w.w;
+            }
+            qn += __popc(db);
+            k0 += __popc(bal);
+            t0 += 32u;
+            __syncwarp();
+            if (qn >= 32) {
+                test_batch(32);
+                // the rest (fewer than 32) to the front of the queue
+                const int rest = qn - 32;
+                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                uint32_t xw = 0u;
+                __syncwarp();
+                if (lane < rest) {
+                    x = s_q[wq][32 + lane];
+                    xw = s_w3[wq][32 + lane];
+                }
+                __syncwarp();
+                if (lane < rest) {
+                    s_q[wq][lane] = x;
+                    s_w3[wq][lane] = xw;
+                }
+                __syncwarp();
+                qn = rest;
+            }
         }
-        k0 += __popc(bal);
-        t0 += 32u;
+        if (qn > 0) test_batch(qn);
+        if (lane == 0 && m > P.lens_cap) atomicCAS(P.err, kErrNone, kErrCandCap);
+        rck = __reduce_add_sync(kFull, rck);
+        return make_int4(n_p, min(k0, n_p), min(m, P.lens_cap), (int)rck);
     }
-    if (lane == 0 && m > P.lens_cap) atomicCAS(P.err, kErrNone, kErrCandCap);
-    rck = __reduce_add_sync(kFull, rck);
-    return make_int4(n_p, min(k0, n_p), min(m, P.lens_cap), (int)rck);
 }
 
 // The lens lists of all moves of the sweep, one warp per colloid, filed under
