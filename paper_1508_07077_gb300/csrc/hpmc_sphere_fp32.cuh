@@ -937,10 +937,10 @@ __device__ __forceinline__ void phase_cell(const SimParams &P, int phase, int4 t
 
     // Loads, most of them before the wait for the neighbours (everything
     // about the own cell is fixed for the sweep or written only by this CTA):
-    // round 1, every stencil cell's population (lanes 0..26) and, on spare
+    // first load, every stencil cell's population (lanes 0..26) and, on spare
     // lanes, the own cell's first two bin entries, displacements, headers and
     // inline lens points (speculatively: most cells hold at most two
-    // colloids); round 2 (only for more colloids) the rest of the own cell's
+    // colloids); a second load (only for more colloids) the rest of the own cell's
     // slots, one lane each; after the wait one round for the neighbour cells'
     // entries (up to four per cell at once).
     int c_nb = 0, m_nb = 0, dx = 0, dy = 0, dz = 0;
@@ -1048,7 +1048,7 @@ __device__ __forceinline__ void phase_cell(const SimParams &P, int phase, int4 t
         }
     }
     cta_sync<WARP>();
-    // lens points: the first kLensInline of slots 0 and 1 came in round 1;
+    // lens points: the first kLensInline of slots 0 and 1 came with the first load;
     // other short lists are beside their bin slots, long ones in the lens
     // array
     if (has_dep) {
