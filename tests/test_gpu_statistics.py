@@ -9,6 +9,10 @@ chains advanced together in one batch.
   distribution unchanged.
 * The hard-sphere limit z_p = 0: the pressure from the contact value,
   Z = 1 + 4 phi g(1+), against Carnahan-Starling at phi = 0.2 and 0.3.
+* The many-body reduction: 32 spheres at q = 0.15 (below 2/sqrt(3) - 1, where
+  no point lies in three excluded spheres) sample the pairwise
+  Asakura-Oosawa fluid; pair counts near contact against an independent
+  Metropolis chain of that pair potential (tests/pairwise_ao.py).
 * The state point of the 16384-sphere workload (phi_c 0.30, q 0.15, eta_r 0.2)
   at a size the oracle runs in seconds: acceptance rate and g(r) of
   independent GPU chains against independent oracle chains; the acceptance
@@ -26,6 +30,7 @@ from concurrent.futures import ThreadPoolExecutor
 import numpy as np
 import pytest
 
+import pairwise_ao as PA
 from paper_1508_07077_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -192,6 +197,46 @@ def test_hard_sphere_pressure_carnahan_starling_long_run(lib, phi):
     # statistical error plus 0.5% for the contact extrapolation and N = 256
     # (the oracle's own chains, binned every sweep, land within 0.15%)
     assert abs(z_mean - z_cs) < 3.0 * z_se + 0.005 * z_cs, (z_mean, z_se, z_cs)
+
+
+# --- many-body reduction: the pairwise Asakura-Oosawa fluid -----------------
+
+@pytest.fixture(scope="module")
+def pairwise_reference():
+    return PA.pairwise_counts()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_many_body_reduction_to_pairwise_ao_long_run(lib, pairwise_reference, precision):
+    """32 spheres at q = 0.15, below 2/sqrt(3) - 1, where the implicit model is
+    exactly the pairwise Asakura-Oosawa fluid: the pair counts from contact to
+    r = 1.2 of 64 independent CUDA chains (FP32 certified form and plain FP64,
+    16 groups of 4) against a Metropolis chain of the pair potential that
+    shares nothing with the library (chi^2 of the four bins below its 0.999
+    quantile)."""
+    L, z_p, pos0 = PA.system()
+    m, n = 64, PA.N
+    burn, sweeps, every = 4000, 12000, 10
+    reps = [{"n": n, "box_l": L, "pos": pos0, "q": PA.Q, "n_r": z_p, "d_max": 0.03,
+             "replica": k} for k in range(m)]
+    ctx = lib.hpmc_init_batch(reps, seed=5, precision=precision)
+    edges_t = torch.tensor(np.linspace(0.0, PA.RMAX, PA.BINS + 1)[PA.LO:], device="cuda")
+    pos = torch.empty((m * n, 3), dtype=torch.float64, device="cuda")
+    hist = torch.zeros((m, PA.BINS - PA.LO), dtype=torch.float64, device="cuda")
+    try:
+        lib.hpmc_sweep(ctx, burn)
+        for _ in range(sweeps // every):
+            lib.hpmc_sweep(ctx, every)
+            lib.hpmc_get_state(ctx, pos)
+            hist += _pair_hist_device(pos, m, n, L, edges_t)
+        _, cnt = lib.hpmc_get_state(ctx)
+    finally:
+        lib.hpmc_destroy(ctx)
+    assert cnt["moves"] == m * n * (burn + sweeps)
+    got = hist.cpu().numpy() / (sweeps // every * n)
+    got = got.reshape(PA.GROUPS, m // PA.GROUPS, -1).mean(1)
+    chi2, z = PA.chi2(got, pairwise_reference)
+    assert chi2 < PA.CHI2_999, z
 
 
 # --- the 16384-sphere state point: GPU chains against oracle chains ----------

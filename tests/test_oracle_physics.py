@@ -23,6 +23,7 @@ from concurrent.futures import ThreadPoolExecutor
 import numpy as np
 import pytest
 
+import pairwise_ao as PA
 from paper_1508_07077_gb300 import workloads as W
 
 Q, R_S, Z_P, L2 = 0.2, 0.6, 47.7464829275686, 2.4
@@ -132,91 +133,35 @@ def test_single_colloid_free_volume_exact(oracle):
     assert abs(alpha - exact) < 4.0 * math.sqrt(exact * (1 - exact) / 400000)
 
 
-# many-body reduction: 32 spheres at phi = 0.2, q = 0.15 (below 2/sqrt(3) - 1),
-# eta_r = 0.05 (z_p = 28.3, beta U_AO(1) = -0.55)
-MB_N, MB_PHI, MB_Q, MB_ETA = 32, 0.2, 0.15, 0.05
-MB_BINS, MB_RMAX, MB_LO = 24, 1.2, 20     # bins of 0.05 from contact to 1.2
-MB_GROUPS = 16
-
-
-def _mb_system():
-    L = (MB_N * math.pi / 6.0 / MB_PHI) ** (1.0 / 3.0)
-    z_p = 6.0 * MB_ETA / (math.pi * MB_Q ** 3)
-    return L, z_p, W.fcc_positions(MB_N, L, 1)
-
-
 def _mb_oracle(oracle, z_p, n_eq=4000, n_run=12000):
-    """Pair counts per colloid and sweep in the bins near contact, one row per
-    independent oracle chain (seeds 1..16, from the same start)."""
-    L, _, pos0 = _mb_system()
+    """Pair counts per colloid and sweep in the bins from contact to 1.2, one
+    row per independent oracle chain (seeds 1..16, from the same start)."""
+    L, _, pos0 = PA.system()
 
     def chain(seed):
-        p, _, _, _ = oracle.run(pos0, L, q=MB_Q, n_r=z_p, d_max=0.03, n_sweeps=n_eq, seed=seed)
-        _, _, _, h = oracle.run(p, L, q=MB_Q, n_r=z_p, d_max=0.03, n_sweeps=n_run, seed=seed,
-                                sweep0=n_eq, hist_bins=MB_BINS, hist_rmax=MB_RMAX)
-        return h[MB_LO:].astype(float) / (n_run * MB_N)
+        p, _, _, _ = oracle.run(pos0, L, q=PA.Q, n_r=z_p, d_max=0.03, n_sweeps=n_eq, seed=seed)
+        _, _, _, h = oracle.run(p, L, q=PA.Q, n_r=z_p, d_max=0.03, n_sweeps=n_run, seed=seed,
+                                sweep0=n_eq, hist_bins=PA.BINS, hist_rmax=PA.RMAX)
+        return h[PA.LO:].astype(float) / (n_run * PA.N)
 
     with ThreadPoolExecutor(max_workers=8) as ex:
-        return np.array(list(ex.map(chain, range(1, MB_GROUPS + 1))))
-
-
-def _mb_pairwise(n_rep=32, n_eq=400, n_run=1600, d_max=0.08, seed=7):
-    """The same pair counts from a Metropolis chain of the pairwise potential
-    beta U(r) = -z_p V_lens(r) (hard core below r = 1), n_rep independent
-    replicas moved together; one row per group of replicas."""
-    L, z_p, pos0 = _mb_system()
-    R_s = 0.5 + MB_Q / 2.0
-    rng = np.random.default_rng(seed)
-    X = np.repeat(pos0[None], n_rep, axis=0).copy()
-    edges = np.linspace(0.0, MB_RMAX, MB_BINS + 1)[MB_LO:]
-    iu = np.triu_indices(MB_N, 1)
-    H = np.zeros((n_rep, MB_BINS - MB_LO))
-    samples = 0
-    for sweep in range(n_eq + n_run):
-        for i in range(MB_N):
-            xo = X[:, i, :]
-            xn = xo + rng.uniform(-d_max, d_max, size=(n_rep, 3))
-            do = X - xo[:, None, :]
-            do -= L * np.round(do / L)
-            dn = X - xn[:, None, :]
-            dn -= L * np.round(dn / L)
-            ro = np.sqrt((do ** 2).sum(-1))
-            rn = np.sqrt((dn ** 2).sum(-1))
-            ro[:, i] = np.inf
-            rn[:, i] = np.inf
-            dU = -z_p * (lens(rn, R_s).sum(1) - lens(ro, R_s).sum(1))
-            ok = ~(rn < 1.0).any(1) & (rng.random(n_rep) < np.exp(-dU))
-            X[ok, i, :] = xn[ok] % L
-        if sweep >= n_eq and sweep % 2 == 0:
-            d = X[:, :, None, :] - X[:, None, :, :]
-            d -= L * np.round(d / L)
-            r = np.sqrt((d ** 2).sum(-1))[:, iu[0], iu[1]]
-            for b in range(MB_BINS - MB_LO):
-                H[:, b] += ((r >= edges[b]) & (r < edges[b + 1])).sum(1)
-            samples += 1
-    H /= samples * MB_N
-    return H.reshape(MB_GROUPS, -1, MB_BINS - MB_LO).mean(1)
-
-
-def _chi2(a, b):
-    z = (a.mean(0) - b.mean(0)) / np.sqrt(a.var(0, ddof=1) / len(a) + b.var(0, ddof=1) / len(b))
-    return float(np.sum(z ** 2)), z
+        return np.array(list(ex.map(chain, range(1, PA.GROUPS + 1))))
 
 
 def test_many_body_reduction_to_pairwise_asakura_oosawa(oracle):
     """Below q = 2/sqrt(3) - 1 the implicit-depletant chain of 32 spheres has
     the pair statistics of the pairwise Asakura-Oosawa fluid (chi^2 of the four
-    bins from contact to r = 1.2 below its 0.999 quantile, 18.5).  Two
-    controls: the attraction is visible (the contact bin well above the hard
-    spheres'), and the test has the power to reject a wrong potential (the
-    oracle at 0.75 z_p fails it)."""
-    L, z_p, _ = _mb_system()
-    ref = _mb_pairwise()
+    bins from contact to r = 1.2 below its 0.999 quantile).  Two controls: the
+    attraction is visible (the contact bin well above the hard spheres'), and
+    the test has the power to reject a wrong potential (the oracle at
+    0.75 z_p fails it)."""
+    _, z_p, _ = PA.system()
+    ref = PA.pairwise_counts()
     got = _mb_oracle(oracle, z_p)
-    chi2, z = _chi2(got, ref)
-    assert chi2 < 18.5, z
+    chi2, z = PA.chi2(got, ref)
+    assert chi2 < PA.CHI2_999, z
     hard = _mb_oracle(oracle, 0.0, n_eq=1000, n_run=4000)
     assert got.mean(0)[0] > 1.2 * hard.mean(0)[0], (got.mean(0), hard.mean(0))
     wrong = _mb_oracle(oracle, 0.75 * z_p)
-    chi2_w, z_w = _chi2(wrong, ref)
+    chi2_w, z_w = PA.chi2(wrong, ref)
     assert chi2_w > 30.0, z_w
