@@ -550,6 +550,13 @@ __device__ __forceinline__ int4 lens_of_move_paired(const SimParams &P, const Re
                 const bool in_c = r2 < R.T_s32 - R.m_r2, out_c = r2 > R.T_s32 + R.m_r2;
                 const bool ov_c = r2o < R.T_dep32 - R.m_r2;
                 if (!__any_sync(kFull, !(in_c || out_c) || (in_c && !ov_c))) {
+                    if constexpr (kChecked) {
+                        // the decisions taken as certain, against the FP64
+                        // statement: in the ball, and (in it) over the old pose
+                        (void)HPMC_CHECK_FAILS(P, exact_ball(P, R, w, h) == in_c, 11);
+                        if (in_c)
+                            (void)HPMC_CHECK_FAILS(P, exact_dep(P, R, sweep, i, w, 0, 0, nullptr, 0, h), 12);
+                    }
                     k0 += __popc(__ballot_sync(kFull, in_c));
                     continue;
                 }
@@ -562,6 +569,14 @@ __device__ __forceinline__ int4 lens_of_move_paired(const SimParams &P, const Re
             int tn = CUBE ? tri(norm2f(e0, e1, e2), R.T_dep32, R.m_r2) : 1;
             int to = in != 0 && tn != 0 ? tri(norm2f(e0 - o0, e1 - o1, e2 - o2), R.T_dep32, R.m_r2)
                                         : 1;
+            if constexpr (kChecked) {
+                // every decision taken as certain, against the FP64 statement
+                if (!CUBE && in != -1) (void)HPMC_CHECK_FAILS(P, exact_ball(P, R, w, h) == (in == 1), 11);
+                if (CUBE && tn != -1) (void)HPMC_CHECK_FAILS(P, exact_ball(P, R, w, h) == (tn == 1), 11);
+                if (in == 1 && tn == 1 && to != -1)
+                    (void)HPMC_CHECK_FAILS(
+                        P, exact_dep(P, R, sweep, i, w, 0, 0, nullptr, 0, h) == (to == 1), 12);
+            }
             if (__any_sync(kFull, in == -1 || tn == -1 || to == -1)) {
                 if (in == -1) {
                     ++rck;
@@ -1146,6 +1161,9 @@ __device__ __forceinline__ void phase_cell(const SimParams &P, int phase, int4 t
         if (!out && edge) {
             exits = exact_cell_exit(P, R, S, sweep, i, cx, cy, cz);
             if (tid == 0) ++c_rck;
+        } else if (kChecked && tid == 0) {
+            // the decision taken as certain, against the FP64 statement
+            (void)HPMC_CHECK_FAILS(P, exact_cell_exit(P, R, S, sweep, i, cx, cy, cz) == out, 13);
         }
         if (exits) {
             ++c_cell;
@@ -1185,6 +1203,10 @@ __device__ __forceinline__ void phase_cell(const SimParams &P, int phase, int4 t
                     r2 = norm2f(d0, d1, d2);
                     t = tri(r2, T_contact, m_r2);
                 }
+            }
+            if constexpr (kChecked) {
+                if (pj >= 0 && t != -1)
+                    (void)HPMC_CHECK_FAILS(P, exact_pair(P, R, sweep, i, pj, s_accl, nacc) == (t == 1), 14);
             }
             const bool unsure = t == -1;
             if (__any_sync(kFull, unsure)) {
@@ -1263,6 +1285,12 @@ __device__ __forceinline__ void phase_cell(const SimParams &P, int phase, int4 t
                         unsure = unsure || tn == -1;
                     }
                     cls = hit ? 0 : (unsure ? -1 : 1);
+                    if constexpr (kChecked) {
+                        // a class taken as certain, against the FP64 statement
+                        if (cls != -1)
+                            (void)HPMC_CHECK_FAILS(
+                                P, exact_free_nb(P, R, sweep, i, tt, s_nb, nnb, s_accl, nacc) == (cls == 1), 15);
+                    }
                 }
                 {
                     const bool unsure = cls == -1;

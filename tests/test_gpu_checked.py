@@ -2,7 +2,11 @@
 systems of the FP32 sphere path: every cell, bin, neighbour, shared-memory
 and colloid index is bounds-checked, and every colloid a move reads is
 checked to sit in its own cell or in a cell that is not active in the same
-colour phase (Sec. III.E), in both colour-phase schedules.  The error word
+colour phase (Sec. III.E), in both colour-phase schedules; and every
+decision FP32 takes as certain (ball, new and old pose, cell exit, colloid
+pair, lens point against the neighbours) is re-taken in FP64 and must agree,
+which checks the certified margins on every test, not only on those that
+reach the trajectory.  The error word
 must stay zero and the trajectories must be the oracle's, bit for bit (the
 checks observe, they change nothing)."""
 import numpy as np
