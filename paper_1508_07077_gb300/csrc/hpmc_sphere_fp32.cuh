@@ -329,6 +329,12 @@ __device__ __forceinline__ bool free_nb32(const SimParams &P, const Rep &R, floa
     for (int a = 0; a < nnb; ++a) {
         const float4 d = nb[a];
         const int t = tri(norm2f(v0 - d.x, v1 - d.y, v2 - d.z), R.T_dep32, R.m_r2);
+        if constexpr (kChecked) {
+            // a decision taken as certain, against the FP64 statement
+            if (t != -1)
+                (void)HPMC_CHECK_FAILS(
+                    P, exact_dep(P, R, sweep, i, w, kind, __float_as_int(d.w), acc, nacc) == (t == 1), 16);
+        }
         if (t == 1) return false;
         if (t == -1) {
             ++rck;
@@ -336,28 +342,6 @@ __device__ __forceinline__ bool free_nb32(const SimParams &P, const Rep &R, floa
         }
     }
     return true;
-}
-
-// Next point of an attempt stream inside the sampling ball.
-__device__ __forceinline__ bool next_in_ball32(const SimParams &P, const Rep &R, uint32_t sweep, uint32_t tag,
-                                               uint32_t purpose, uint32_t sub, uint32_t &t,
-                                               uint32_t t_max, uint4 &w, float &e0, float &e1,
-                                               float &e2, uint32_t &rck)
-{
-    while (t < t_max) {
-        w = draw(R.key0, R.key1, sweep, tag, purpose, sub, t);
-        ++t;
-        e0 = coord32(w.x, R.R_s32);
-        e1 = coord32(w.y, R.R_s32);
-        e2 = coord32(w.z, R.R_s32);
-        int in = tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
-        if (in == -1) {
-            ++rck;
-            in = exact_ball(P, R, w) ? 1 : 0;
-        }
-        if (in) return true;
-    }
-    return false;
 }
 
 struct CbResult32 {
@@ -398,6 +382,9 @@ __device__ __noinline__ CbResult32 cb_factor_warp32(const SimParams &P, const Re
                 e1 = coord32(w.y, R.R_s32);
                 e2 = coord32(w.z, R.R_s32);
                 in = tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
+                if constexpr (kChecked) {
+                    if (in != -1) (void)HPMC_CHECK_FAILS(P, exact_ball(P, R, w) == (in == 1), 11);
+                }
                 if (in == -1) {
                     ++r.rck;
                     in = exact_ball(P, R, w) ? 1 : 0;
@@ -410,6 +397,10 @@ __device__ __noinline__ CbResult32 cb_factor_warp32(const SimParams &P, const Re
                     // forward trial around the old pose: must miss the new pose
                     const float y0 = o0 + e0, y1 = o1 + e1, y2 = o2 + e2;
                     int tn = tri(norm2f(y0, y1, y2), R.T_dep32, R.m_r2);
+                    if constexpr (kChecked) {
+                        if (tn != -1)
+                            (void)HPMC_CHECK_FAILS(P, exact_dep(P, R, sweep, i, w, 1, 0, acc, nacc) == (tn == 1), 12);
+                    }
                     if (tn == -1) {
                         ++r.rck;
                         tn = exact_dep(P, R, sweep, i, w, 1, 0, acc, nacc) ? 1 : 0;
@@ -418,6 +409,10 @@ __device__ __noinline__ CbResult32 cb_factor_warp32(const SimParams &P, const Re
                 } else {
                     // reverse trial around the new pose: must miss the old pose
                     int to = tri(norm2f(e0 - o0, e1 - o1, e2 - o2), R.T_dep32, R.m_r2);
+                    if constexpr (kChecked) {
+                        if (to != -1)
+                            (void)HPMC_CHECK_FAILS(P, exact_dep(P, R, sweep, i, w, 0, 0, acc, nacc) == (to == 1), 12);
+                    }
                     if (to == -1) {
                         ++r.rck;
                         to = exact_dep(P, R, sweep, i, w, 0, 0, acc, nacc) ? 1 : 0;

@@ -4,7 +4,8 @@ and colloid index is bounds-checked, and every colloid a move reads is
 checked to sit in its own cell or in a cell that is not active in the same
 colour phase (Sec. III.E), in both colour-phase schedules; and every
 decision FP32 takes as certain (ball, new and old pose, cell exit, colloid
-pair, lens point against the neighbours) is re-taken in FP64 and must agree,
+pair, lens point against the neighbours, CB trials) is re-taken in FP64 and
+must agree,
 which checks the certified margins on every test, not only on those that
 reach the trajectory.  The error word
 must stay zero and the trajectories must be the oracle's, bit for bit (the
