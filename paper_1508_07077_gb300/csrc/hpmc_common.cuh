@@ -45,9 +45,8 @@ enum DevError { kErrNone = 0, kErrCandCap = 1, kErrCellCap = 2, kErrTimeout = 3,
 // FP64 every decision of the hard-sphere path that FP32 took as certain (the
 // ball and pose tests of the lens kernel, the cell-exit, pair and lens-point
 // tests of the colour phases, the CB trials' tests) and compares the two.  A
-// failed check
-// records kErrCheck, with the check's number in the second error word, and
-// the access is skipped; nothing traps.  In the regular build every check
+// failed check records kErrCheck, with the check's number in the second
+// error word, and the access is skipped; nothing traps.  In the regular build every check
 // compiles away.
 #ifdef HPMC_CHECKED
 constexpr bool kChecked = true;
