@@ -186,6 +186,14 @@ __global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__
         const uint32_t t = tk >> 16;
         // overlaps the new pose?
         int tn = act ? dep_tri32(R, make_float3(v.x, v.y, v.z), Fn) : 0;
+        if constexpr (kChecked) {
+            // a decision taken as certain, against the FP64 statement
+            if (act && tn != -1) {
+                const uint4 w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, paired_call(t));
+                (void)HPMC_CHECK_FAILS(
+                    P, exact_dep_aniso(P, R, g, w, 0, 0, 0, nullptr, 0, (int)paired_half(t)) == (tn == 1), 17);
+            }
+        }
         {
             const bool unsure = tn == -1;
             if (__any_sync(kFull, unsure)) {
@@ -199,6 +207,13 @@ __global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__
         // and not the old pose?
         int to = 1;
         if (tn == 1) to = dep_tri32(R, make_float3(v.x - o0, v.y - o1, v.z - o2), Fo);
+        if constexpr (kChecked) {
+            if (act && tn == 1 && to != -1) {
+                const uint4 w = draw(R.key0, R.key1, sweep, tag, kPDep, 0, paired_call(t));
+                (void)HPMC_CHECK_FAILS(
+                    P, exact_dep_aniso(P, R, g, w, 0, 1, 0, nullptr, 0, (int)paired_half(t)) == (to == 1), 17);
+            }
+        }
         {
             const bool unsure = to == -1;
             if (__any_sync(kFull, unsure)) {
@@ -239,6 +254,9 @@ __global__ void __launch_bounds__(128) k_lens_aniso_fp32(const __grid_constant__
             e1 = s21f_bits(f.y) * R.R_s32;
             e2 = s21f_bits(f.z) * R.R_s32;
             in = R.v0_cube ? 1 : tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
+            if constexpr (kChecked) {
+                if (!R.v0_cube && in != -1) (void)HPMC_CHECK_FAILS(P, exact_ball(P, R, w, half) == (in == 1), 11);
+            }
         }
         {
             const bool unsure = in == -1;
@@ -299,6 +317,11 @@ __device__ __forceinline__ bool free_nb_aniso32(const SimParams &P, const Rep &R
     for (int a = 0; a < nnb; ++a) {
         const float4 d = nb[a].d;
         const int t = dep_tri32(R, make_float3(y.x - d.x, y.y - d.y, y.z - d.z), nb[a].F);
+        if constexpr (kChecked) {
+            if (t != -1)
+                (void)HPMC_CHECK_FAILS(
+                    P, exact_dep_aniso(P, R, i, w, base, 2, __float_as_int(d.w), acc, nacc) == (t == 1), 20);
+        }
         if (t == 1) return false;
         if (t == -1) {
             ++rck;
@@ -312,6 +335,10 @@ __device__ __forceinline__ int dep_self32(const SimParams &P, const Rep &R, floa
                                           int i, uint4 w, int base, int target, uint32_t &rck)
 {
     int t = dep_tri32(R, v, F);
+    if constexpr (kChecked) {
+        if (t != -1)
+            (void)HPMC_CHECK_FAILS(P, exact_dep_aniso(P, R, i, w, base, target, 0, nullptr, 0) == (t == 1), 20);
+    }
     if (t == -1) {
         ++rck;
         t = exact_dep_aniso(P, R, i, w, base, target, 0, nullptr, 0) ? 1 : 0;
@@ -350,6 +377,9 @@ __device__ __noinline__ CbResult32 cb_factor_aniso32(const SimParams &P, const R
                 e1 = coord32(w.y, R.R_s32);
                 e2 = coord32(w.z, R.R_s32);
                 in = tri(norm2f(e0, e1, e2), R.T_s32, R.m_r2);
+                if constexpr (kChecked) {
+                    if (in != -1) (void)HPMC_CHECK_FAILS(P, exact_ball(P, R, w) == (in == 1), 11);
+                }
                 if (in == -1) {
                     ++r.rck;
                     in = exact_ball(P, R, w) ? 1 : 0;
@@ -657,10 +687,22 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
                         B.x = make_float3(d0, d1, d2);
                         const PairTri pt = pair_tri32(R, A, B);
                         t = pt.res;
+                        if constexpr (kChecked) {
+                            // a decision taken as certain, against the FP64 statement
+                            uint32_t st = 0;
+                            if (t != -1)
+                                (void)HPMC_CHECK_FAILS(
+                                    P, exact_pair_aniso(P, R, i, pj, s_accl, nacc, pt.n, st) == (t == 1), 18);
+                        }
                         if (t == -1) {
                             ++c_rck;
                             t = exact_pair_aniso(P, R, i, pj, s_accl, nacc, pt.n, st3) ? 1 : 0;
                         }
+                    } else if (kChecked) {
+                        // apart by more than the circumspheres and the margin
+                        uint32_t st = 0;
+                        (void)HPMC_CHECK_FAILS(P, !exact_pair_aniso(P, R, i, pj, s_accl, nacc,
+                                                                    make_float3(-d0, -d1, -d2), st), 18);
                     }
                 }
             }
@@ -728,6 +770,11 @@ __global__ void __launch_bounds__(WARP ? 32 : kMaxThreads, WARP ? 8 : 1)
                         unsure = unsure || tn == -1;
                     }
                     cls = hit ? 0 : (unsure ? -1 : 1);
+                    if constexpr (kChecked) {
+                        if (cls != -1)
+                            (void)HPMC_CHECK_FAILS(
+                                P, exact_free_nb_aniso(P, R, sweep, i, tt, s_nb, nnb, s_accl, nacc) == (cls == 1), 19);
+                    }
                 }
                 {
                     const bool unsure = cls == -1;

@@ -42,9 +42,10 @@ enum DevError { kErrNone = 0, kErrCandCap = 1, kErrCellCap = 2, kErrTimeout = 3,
 // cell, bin, neighbour, shared-memory and colloid indices and the
 // checkerboard invariant (Sec. III.E: a move reads only colloids of its own
 // cell and of cells that are not active in the same phase), and re-takes in
-// FP64 every decision of the hard-sphere path that FP32 took as certain (the
-// ball and pose tests of the lens kernel, the cell-exit, pair and lens-point
-// tests of the colour phases, the CB trials' tests) and compares the two.  A
+// FP64 every decision that FP32 took as certain on the hard-interaction paths
+// of spheres and of the anisotropic shapes (the ball and pose tests of the
+// lens kernels, the cell-exit, pair and lens-point tests of the colour
+// phases, the CB trials' tests) and compares the two.  A
 // failed check records kErrCheck, with the check's number in the second
 // error word, and the access is skipped; nothing traps.  In the regular build every check
 // compiles away.

@@ -1,15 +1,15 @@
 """The checked build (libhpmc_dep_checked.so, -DHPMC_CHECKED) on small
-systems of the FP32 sphere path: every cell, bin, neighbour, shared-memory
-and colloid index is bounds-checked, and every colloid a move reads is
-checked to sit in its own cell or in a cell that is not active in the same
-colour phase (Sec. III.E), in both colour-phase schedules; and every
-decision FP32 takes as certain (ball, new and old pose, cell exit, colloid
-pair, lens point against the neighbours, CB trials) is re-taken in FP64 and
-must agree,
+systems of the FP32 form, spheres and (last test) hemispheres and discoids.
+On the sphere path every cell, bin, neighbour, shared-memory and colloid
+index is bounds-checked, and every colloid a move reads is checked to sit in
+its own cell or in a cell that is not active in the same colour phase
+(Sec. III.E), in both colour-phase schedules.  On every path each decision
+FP32 takes as certain (ball, new and old pose, cell exit, colloid pair, lens
+point against the neighbours, CB trials) is re-taken in FP64 and must agree,
 which checks the certified margins on every test, not only on those that
-reach the trajectory.  The error word
-must stay zero and the trajectories must be the oracle's, bit for bit (the
-checks observe, they change nothing)."""
+reach the trajectory.  The error word must stay zero and the trajectories
+must be the oracle's, bit for bit (the checks observe, they change
+nothing)."""
 import numpy as np
 import pytest
 
@@ -88,3 +88,35 @@ def test_checked_build_batched_variants(oracle, lib, soft, v0):
         assert np.array_equal(got[k][0], ref), k
         for name in oracle.PARITY_COUNTERS:
             assert got[k][2][name] == rc[name], (k, name)
+
+
+ANISO = [(W.HEMISPHERE, 0.25, 0.10, 0.30), (W.SPHEROID, 0.30, 0.10, 0.25)]
+
+
+@pytest.mark.parametrize("shape,phi,q,eta", ANISO)
+@pytest.mark.parametrize("n_trial", [0, 3])
+def test_checked_build_anisotropic(oracle, lib, shape, phi, q, eta, n_trial):
+    """Hemispheres and discoids with rotation moves in the FP32 form: every
+    shape decision FP32 takes as certain (ball, new and old pose in the lens
+    kernel, colloid pairs, lens points against the neighbours, CB trials) is
+    re-taken in FP64 and must agree; the trajectory is the oracle's."""
+    s = W.make_system("small", shape, 256, phi, q, eta, seed=1)
+    smp = lib.Sampler(s.pos, s.L, quat=s.quat, shape=s.shape, shape_params=s.shape_params,
+                      q=s.q, n_r=s.n_r, n_trial=n_trial, d_max=0.08, a_max=0.2, p_translate=0.5,
+                      seed=2, precision=1)
+    try:
+        smp.sweep(4)
+        lib.hpmc_sync(smp.ctx)            # raises on a recorded check
+        pos, quat, sweep, cnt = smp.state(with_quat=True)
+    finally:
+        smp.close()
+    ref, refq, rc, _ = oracle.run(s.pos, s.L, shape=s.shape, shape_params=s.shape_params,
+                                  quat=s.quat, q=s.q, n_r=s.n_r, n_trial=n_trial, d_max=0.08,
+                                  a_max=0.2, p_translate=0.5, seed=2, n_sweeps=4)
+    assert sweep == 4
+    assert np.array_equal(pos, ref)
+    assert np.array_equal(quat, refq)
+    for k in oracle.PARITY_COUNTERS:
+        assert cnt[k] == rc[k], k
+    # (with CB a blocked move counts as a CB rejection)
+    assert cnt["reject_depletant"] + cnt["reject_cb"] > 0 and cnt["reject_overlap"] > 0
