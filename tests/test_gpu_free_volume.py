@@ -2,7 +2,6 @@
 brute-force probe count: same probe stream, same FP64 tests, so the number
 of free probes must be identical, for spheres, hemispheres and discoids, at
 the start and after sweeps."""
-import numpy as np
 import pytest
 
 from paper_1508_07077_gb300 import workloads as W

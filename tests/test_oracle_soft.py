@@ -19,7 +19,7 @@ import numpy as np
 import pytest
 from scipy import integrate
 
-from tests.test_oracle_physics import L2, Q, R_S, Z_P, _pair, lens
+from tests.test_oracle_physics import L2, Q, R_S, _pair
 
 SIGMA = R_S          # contact distance colloid-depletant: (d + q) / 2
 
