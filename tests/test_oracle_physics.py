@@ -10,6 +10,10 @@ statistical mechanics fix.
 * The hard-sphere limit z_p = 0: contact value vs Carnahan-Starling, and the
   scaled-particle-theory free-volume fraction (Sec. IV.A observable).
 * The exact free-volume fraction of a single colloid.
+* Detailed balance with three spheres whose excluded spheres share a region
+  (q = 0.4): the acceptance ratio of a move and its reverse is
+  exp(z_p Delta V_f), V_f from inclusion-exclusion with the triple-overlap
+  volume, which the pairwise prediction misses.
 * The many-body reduction: for q < 2/sqrt(3) - 1 no point lies in three
   excluded spheres, so the free volume is V minus the excluded spheres plus
   their pairwise lens overlaps, and the implicit-depletant chain samples
@@ -165,3 +169,49 @@ def test_many_body_reduction_to_pairwise_asakura_oosawa(oracle):
     wrong = _mb_oracle(oracle, 0.75 * z_p)
     chi2_w, z_w = PA.chi2(wrong, ref)
     assert chi2_w > 30.0, z_w
+
+
+# three spheres whose excluded spheres (radius 0.7 at q = 0.4) share a region;
+# colloid i moves away from the other two and the shared region shrinks
+Q3, L3, Z3 = 0.4, 4.0, 20.0
+R3 = 0.5 + Q3 / 2.0
+J3, K3 = np.array([1.4, 1.5, 2.0]), np.array([2.5, 1.5, 2.0])
+I3_OLD, I3_NEW = np.array([1.95, 2.45, 2.0]), np.array([1.95, 2.55, 2.0])
+
+
+def _triple_volume(a, b, c, m=20):
+    """Volume common to three spheres of radius R3 about a, b, c: the fraction
+    of 2^m scrambled Sobol points of the box around the common part that lie
+    in all three."""
+    from scipy.stats import qmc
+    lo = np.maximum(np.maximum(a, b), c) - R3
+    hi = np.minimum(np.minimum(a, b), c) + R3
+    if np.any(hi <= lo):
+        return 0.0
+    x = qmc.Sobol(3, scramble=True, seed=5).random_base2(m) * (hi - lo) + lo
+    inside = np.ones(len(x), dtype=bool)
+    for centre in (a, b, c):
+        inside &= ((x - centre) ** 2).sum(1) < R3 * R3
+    return float(inside.mean() * np.prod(hi - lo))
+
+
+@pytest.mark.parametrize("n_trial", [0, 3])
+def test_detailed_balance_with_a_triple_overlap(oracle, n_trial):
+    """P_acc(M->M')/P_acc(M'->M) = exp(z_p [V_f(M') - V_f(M)]) when three
+    excluded spheres overlap: V_f = V - |union|, |union| = sum of spheres -
+    sum of pair lenses + triple volume (exact lenses, the triple volume by
+    quasi-Monte Carlo).  Without and with CB.  The pairwise prediction (the
+    triple volume dropped) is rejected: the test sees the many-body term."""
+    def lens3(x, y):
+        return float(lens(np.linalg.norm(x - y), R3))
+    d_pair = (lens3(I3_NEW, J3) + lens3(I3_NEW, K3)) - (lens3(I3_OLD, J3) + lens3(I3_OLD, K3))
+    d_tri = _triple_volume(I3_OLD, J3, K3) - _triple_volume(I3_NEW, J3, K3)
+    f, _ = oracle.acceptance(np.array([J3, K3, I3_OLD]), L3, 2, I3_NEW, q=Q3, n_r=Z3,
+                             n_trial=n_trial, n_rep=150000)
+    b, _ = oracle.acceptance(np.array([J3, K3, I3_NEW]), L3, 2, I3_OLD, q=Q3, n_r=Z3,
+                             n_trial=n_trial, n_rep=150000, sweep0=10 ** 7)
+    ratio = f / b
+    se = ratio * math.sqrt(1.0 / f + 1.0 / b)
+    expect = math.exp(Z3 * (d_pair + d_tri))
+    assert abs(ratio - expect) < 4.0 * se, (ratio, expect, se)
+    assert abs(ratio - math.exp(Z3 * d_pair)) > 6.0 * se, (ratio, math.exp(Z3 * d_pair), se)
